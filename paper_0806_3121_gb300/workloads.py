@@ -1,0 +1,124 @@
+"""Seeded synthetic workloads: operands, fault lists and erased blocks.
+
+This module only draws random inputs (numpy PCG64 streams keyed by a seed) and holds
+none of the ABFT method's arithmetic.  Both the CUDA path (tests, bench) and the CPU
+oracle consume what it produces.  The paper's matrices were random (section 4.3 stress
+test); the shapes and distributions below are the ones each workload names.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    dtype: str            # "f64" | "bf16" | "bf16x3" | "fp8"
+    m: int
+    n: int
+    k: int
+    vb_r: int             # verify block rows
+    vb_c: int             # verify block columns
+    p: int = 0            # erasure grid (0 = none)
+    q: int = 0
+    dist: str = "normal"  # "uniform" U[-1,1] | "normal" N(0,1) | "fp8rows"
+    n_flips: int = 0
+    n_erased: int = 0
+    note: str = ""
+
+
+# The paper's workload shapes, restated per dtype.
+F64_512 = Workload("f64_512", "f64", 512, 512, 512, 512, 512, dist="uniform", n_flips=1,
+                   note="FP64 512^3, U[-1,1], one bit-flip in C before verify")
+F64_11264_GRID22 = Workload("f64_11264_grid22", "f64", 11264, 11264, 11264, 512, 512, 22, 22,
+                            dist="normal", n_flips=3, n_erased=1,
+                            note="FP64 11264^3 as a 22x22 grid of 512-blocks (484 'processes'); "
+                                 "one block erased to NaN plus 3 bit-flips in distinct blocks")
+BF16_16384 = Workload("bf16_16384", "bf16", 16384, 16384, 16384, 128, 128, dist="normal",
+                      note="BF16 16384^3, N(0,1) rounded to BF16, FP32 accumulate")
+WORKLOADS = {w.name: w for w in (F64_512, F64_11264_GRID22, BF16_16384)}
+
+
+def rng(seed: int, stream: int = 0) -> np.random.Generator:
+    """Independent PCG64 stream per (seed, stream)."""
+    return np.random.Generator(np.random.PCG64([int(seed), int(stream)]))
+
+
+def operand(shape, dist: str, seed: int, stream: int) -> np.ndarray:
+    """A float64 matrix with the named distribution."""
+    g = rng(seed, stream)
+    if dist == "uniform":
+        return g.uniform(-1.0, 1.0, size=shape)
+    if dist == "normal":
+        return g.standard_normal(size=shape)
+    if dist == "int":
+        return g.integers(-4, 5, size=shape).astype(np.float64)
+    raise ValueError(dist)
+
+
+def operands(w: Workload, seed: int, m=None, n=None, k=None):
+    """(A, B) as float64 for workload w (optionally at a reduced shape)."""
+    m, n, k = m or w.m, n or w.n, k or w.k
+    return operand((m, k), w.dist, seed, 1), operand((k, n), w.dist, seed, 2)
+
+
+def bf16_bits(x: np.ndarray) -> np.ndarray:
+    """Round float values to bfloat16 (round-to-nearest-even, via torch on the CPU) and
+    return the raw 16-bit patterns."""
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(torch.bfloat16)
+    return t.view(torch.int16).numpy().view(np.uint16).copy()
+
+
+def bit_flips(seed: int, m: int, n: int, count: int, bits: int = 64, stream: int = 7,
+              distinct_blocks=None, avoid_blocks=()):
+    """count (row, col, bit) triples, uniform positions and bits.
+
+    distinct_blocks=(bs_r, bs_c) forces the flips into distinct blocks of that size,
+    none of them in avoid_blocks.
+    """
+    g = rng(seed, stream)
+    out, used = [], set(tuple(b) for b in avoid_blocks)
+    while len(out) < count:
+        i, j, b = int(g.integers(0, m)), int(g.integers(0, n)), int(g.integers(0, bits))
+        if distinct_blocks is not None:
+            blk = (i // distinct_blocks[0], j // distinct_blocks[1])
+            if blk in used:
+                continue
+            used.add(blk)
+        elif any((i, j) == (r, c) for r, c, _ in out):
+            continue
+        out.append((i, j, b))
+    return out
+
+
+def erased_blocks(seed: int, p: int, q: int, count: int, stream: int = 8):
+    """count distinct (bi, bj) grid positions, at most one per block column."""
+    g = rng(seed, stream)
+    out, cols = [], set()
+    while len(out) < count:
+        bi, bj = int(g.integers(0, p)), int(g.integers(0, q))
+        if bj in cols:
+            continue
+        cols.add(bj)
+        out.append((bi, bj))
+    return out
+
+
+def flip_f64(C: np.ndarray, flips) -> np.ndarray:
+    """XOR the given bits of float64 elements (in place on a copy)."""
+    C = np.array(C, dtype=np.float64, copy=True)
+    u = C.view(np.uint64)
+    for i, j, b in flips:
+        u[i, j] ^= np.uint64(1) << np.uint64(b)
+    return C
+
+
+def flip_f32(C: np.ndarray, flips) -> np.ndarray:
+    C = np.array(C, dtype=np.float32, copy=True)
+    u = C.view(np.uint32)
+    for i, j, b in flips:
+        u[i, j] ^= np.uint32(1) << np.uint32(b)
+    return C

@@ -1,0 +1,185 @@
+/*
+ * abft.h -- C ABI of libabft: Huang-Abraham algorithm-based fault-tolerant
+ * matrix multiplication on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Bosilca, Delmas, Dongarra, Langou, "Algorithmic Based Fault
+ * Tolerance Applied to High Performance Computing" (2008).  A is extended with
+ * checksum rows C_C^T A, B with checksum columns B C_R, and the product of the
+ * extended operands is the full-checksum matrix (AB)_F (section 2.2, Eq. (1)).
+ * Its consistency detects, locates and corrects a corrupted element of C, and
+ * a block checksum rebuilds a lost block (section 2.1).
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are row-major; lda/ldb/ldc are leading dimensions in elements.
+ *    C = A B with A m-by-k, B k-by-n, C m-by-n.
+ *  - Pointers named A, B, C, ws, a_scale, b_scale are DEVICE pointers, owned by
+ *    the caller, who keeps them alive until the stream work completes.  Host
+ *    pointers are marked (host).  The library allocates no device memory per
+ *    call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls are stream-ordered and asynchronous unless stated otherwise.
+ *  - No C++ exception crosses the ABI.  Every call returns an abft_status; on a
+ *    non-OK status abft_last_error() (thread-local) holds a one-line message.
+ *    An invalid descriptor or argument returns ABFT_ERR_INVALID with nothing
+ *    launched.
+ *  - Verify blocks: rows of C are cut into blocks of vb_rows rows and columns
+ *    into blocks of vb_cols columns (the last ones may be shorter).  Each block
+ *    has an unweighted checksum (weights 1) and a weighted checksum with
+ *    weights w_t = (t+1) * 2^-ceil(log2 vb) for the t-th row (column) of the
+ *    block; the power-of-two scale is exact and keeps weighted sums in range.
+ *  - Erasure grid: grid_p x grid_q blocks (m % grid_p == 0, n % grid_q == 0).
+ *    A also gains m/grid_p block checksum rows S_A = sum_I A_I, so the product
+ *    carries S = sum_I C_I, enough to rebuild one lost block per block column.
+ */
+#ifndef ABFT_H
+#define ABFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ABFT_OK = 0,
+  ABFT_ERR_INVALID = 1,       /* bad descriptor / argument; nothing launched */
+  ABFT_ERR_CUDA = 2,          /* a CUDA call failed; see abft_last_error()   */
+  ABFT_ERR_UNSUPPORTED = 3,   /* valid request this build does not provide   */
+  ABFT_ERR_UNCORRECTABLE = 4, /* errors found that could not all be fixed    */
+  ABFT_ERR_TIMEOUT = 5        /* a bounded device wait gave up               */
+} abft_status;
+
+typedef enum {
+  ABFT_F64 = 0,     /* A, B, C binary64; DFMA product, binary64 checksums          */
+  ABFT_BF16 = 1,    /* A, B bfloat16; C binary32; tensor-core product, fp32 accum.  */
+  ABFT_BF16X3 = 2,  /* A, B binary32 split into bf16 hi+lo; C binary32             */
+  ABFT_FP8_E4M3 = 3 /* A, B e4m3 with binary32 scales per 128x128 block; C binary32 */
+} abft_dtype;
+
+/* Report kinds (abft_fault.kind). */
+#define ABFT_KIND_CORRECTED 1          /* located by the checksums and recomputed */
+#define ABFT_KIND_NONFINITE_CORRECTED 2 /* a NaN/Inf element located and recomputed */
+#define ABFT_KIND_UNCORRECTABLE 3      /* a flagged line that could not be fixed   */
+#define ABFT_KIND_BLOCK_RECOVERED 4    /* an erased block rebuilt                  */
+
+typedef struct {
+  int64_t m, n, k;       /* C = A B: A m-by-k, B k-by-n                             */
+  int64_t lda, ldb, ldc; /* leading dimensions in elements (>= k, n, n)            */
+  int32_t dtype;         /* abft_dtype                                             */
+  int32_t vb_rows;       /* verify block rows (1 .. m)                             */
+  int32_t vb_cols;       /* verify block columns (1 .. n)                          */
+  int32_t grid_p;        /* erasure grid block-rows; 0 = no block checksum         */
+  int32_t grid_q;        /* erasure grid block-columns (with grid_p > 0)           */
+  int32_t flags;         /* reserved, must be 0                                    */
+  double tau_safety;     /* safety factor s of the detection threshold; 0 -> 4     */
+} abft_desc;
+
+/* One report entry.  row/col are element coordinates; -1 marks the unknown
+ * coordinate of a flagged line (col = -1: row check of row `row`; row = -1:
+ * column check of column `col`).  side: 0 column check, 1 row check, 2 erasure.
+ * delta = value before - value after correction; r_e / r_w are the unweighted
+ * and weighted residuals of the line that located it. */
+typedef struct {
+  int32_t row, col, kind, side;
+  double delta, r_e, r_w;
+} abft_fault;
+
+/* Byte offsets of the regions inside the workspace (all 256-byte aligned) and
+ * their shapes, for callers that want to read the checksums.  R = 2*nvr + bs
+ * checksum rows (nvr = ceil(m/vb_rows), bs = m/grid_p or 0), Cc = 2*nvc
+ * checksum columns (nvc = ceil(n/vb_cols)).  acs/bcs hold the encoded operand
+ * rows/columns in the product's operand format; E (R-by-n binary64) holds the
+ * product rows of acs (expected column checksums, then S); F (m-by-Cc
+ * binary64) the product columns of bcs (expected row checksums). */
+typedef struct {
+  size_t total;
+  size_t acs, bcs, E, F;
+  size_t nArow, nAblk, nBcol, nBblk; /* threshold norms (binary64)             */
+  size_t scratch, scratch_bytes;     /* verify lists, counters, report buffer */
+  int64_t R, Cc, nvr, nvc, bs;
+  int64_t acs_ld, bcs_ld;            /* leading dims of acs / bcs in elements  */
+} abft_ws_layout;
+
+/* Size of the caller-owned device workspace for `desc`.  Returns 0 for an
+ * invalid descriptor (abft_last_error() says why). */
+size_t abft_workspace_bytes(const abft_desc* desc);
+
+/* Fill *out (host) with the workspace layout.  ABFT_ERR_INVALID on a bad desc. */
+abft_status abft_workspace_layout(const abft_desc* desc, abft_ws_layout* out);
+
+/* Checksum encoding (section 2.1; the operands of Eq. (1)).  Writes into ws the
+ * checksum rows of A (per verify block: e^T A_I and w^T A_I; then S_A when the
+ * erasure grid is on) and the checksum columns of B (B_J e, B_J w), plus the
+ * norms the detection thresholds use.  a_scale/b_scale: binary32 block scales
+ * for ABFT_FP8_E4M3 (ceil(m/128) x ceil(k/128) and ceil(k/128) x ceil(n/128),
+ * row-major), else NULL.  Asynchronous. */
+abft_status abft_encode(const abft_desc* desc, const void* A, const void* B, const void* a_scale,
+                        const void* b_scale, void* ws, void* stream);
+
+/* The ABFT product (Eq. (1)): [A; C_C^T A] [B, B C_R] on the GPU.  Writes the
+ * data block A B into C and the checksum blocks into ws (E and F).  Requires a
+ * preceding abft_encode on the same ws and operands.  Asynchronous. */
+abft_status abft_gemm(const abft_desc* desc, const void* A, const void* B, const void* a_scale,
+                      const void* b_scale, void* C, void* ws, void* stream);
+
+/* The same GEMM kernel with no checksum tiles: C = A B only.  This is the
+ * checksum-free baseline the ABFT overhead is measured against.  ws unused
+ * (may be NULL).  Asynchronous. */
+abft_status abft_gemm_plain(const abft_desc* desc, const void* A, const void* B,
+                            const void* a_scale, const void* b_scale, void* C, void* stream);
+
+/* Detect, locate and correct (section 1 and section 2.2: the consistency of
+ * (AB)_F detects, localizes and corrects errors in the output).  Checks every
+ * column line (verify block x column) and row line (row x verify block) of C
+ * against E / F, skipping lines that touch the erased blocks listed in
+ * erased_blocks (host, n_erased (bi, bj) pairs).  A flagged line proposes its
+ * single non-finite element or the position given by the ratio of weighted to
+ * unweighted residual; each candidate is recomputed in binary64 from a line in
+ * which it is the only candidate, then both its lines are checked again.
+ * C is corrected in place.  reread_C: 1 re-reads all of C from memory (catches
+ * faults that hit C after the product); 0 is accepted and behaves the same in
+ * this build.  The report (host, max_reports entries) receives up to
+ * max_reports entries sorted by (row, col, kind); *n_reports (host) gets the
+ * full count.  SYNCHRONISES `stream`.  Returns ABFT_OK, or
+ * ABFT_ERR_UNCORRECTABLE when a flagged line could not be fixed (those
+ * elements are left unmodified). */
+abft_status abft_verify_correct(const abft_desc* desc, void* C, void* ws, int32_t reread_C,
+                                const int32_t* erased_blocks, int32_t n_erased, abft_fault* report,
+                                int32_t max_reports, int32_t* n_reports, void* stream);
+
+/* Erasure recovery (section 2.1: the lost part is the checksum minus the
+ * surviving parts; section 3.3: the reduction step of a recovery).  Rebuilds
+ * block (bi, bj) of the erasure grid as C_IJ = S_J - sum_{I' != I} C_I'J in
+ * binary64, then re-checks the rebuilt block's column lines.  Call it after
+ * abft_verify_correct (which must list the block as erased), because it reads
+ * the rest of the block column.  report_entry (host, may be NULL) receives a
+ * kind-4 entry.  SYNCHRONISES `stream`.  ABFT_ERR_UNCORRECTABLE when the
+ * rebuilt block fails its checks. */
+abft_status abft_recover_block(const abft_desc* desc, void* C, void* ws, int32_t bi, int32_t bj,
+                               abft_fault* report_entry, void* stream);
+
+/* Fault injection for tests and benchmarks (the paper's stress test kills
+ * processes, section 4.3; here faults are bit flips and erasures chosen on the
+ * host).  abft_inject_bitflips XORs bit bits[t] of element (rows[t], cols[t])
+ * of C (host arrays of length count).  abft_erase_block fills block (bi, bj)
+ * of the erasure grid with NaN.  Asynchronous. */
+abft_status abft_inject_bitflips(const abft_desc* desc, void* C, const int64_t* rows,
+                                 const int64_t* cols, const int32_t* bits, int32_t count,
+                                 void* stream);
+abft_status abft_erase_block(const abft_desc* desc, void* C, int32_t bi, int32_t bj, void* stream);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all threads, all devices).  Host-side counter; never synchronises. */
+int64_t abft_kernel_launches(void);
+
+/* Thread-local message describing the last non-OK status of this thread. */
+const char* abft_last_error(void);
+
+/* Library version (major * 100 + minor). */
+int32_t abft_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ABFT_H */

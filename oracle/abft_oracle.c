@@ -70,16 +70,21 @@ double oracle_weight(int64_t t, int64_t vb) {
 
 /* ------------------------------------------------------------------------ */
 /* GEMM: C = A B, the plain definition C_ij = sum_l A_il B_lj (Eq. (1)).
+ * Every C_ij is accumulated from 0 by adding the products A_il B_lj in
+ * increasing l; the loops visit l before j only so that B is read row by row
+ * (each element's sum is the same sequence of roundings as the i-j-l order).
  * Pinned by: numpy's product (library special case), exact integer inputs,
  * identity and rank-one closed forms, the residual check of section 4.3. */
 void oracle_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
                  const double* B, int64_t ldb, double* C, int64_t ldc) {
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < m; ++i) {
-    for (int64_t j = 0; j < n; ++j) {
-      double s = 0.0;
-      for (int64_t l = 0; l < k; ++l) s += A[i * lda + l] * B[l * ldb + j];
-      C[i * ldc + j] = s;
+    double* c = C + i * ldc;
+    for (int64_t j = 0; j < n; ++j) c[j] = 0.0;
+    for (int64_t l = 0; l < k; ++l) {
+      const double a = A[i * lda + l];
+      const double* b = B + l * ldb;
+      for (int64_t j = 0; j < n; ++j) c[j] += a * b[j];
     }
   }
 }
@@ -250,6 +255,15 @@ static void taus(const oracle_cfg* c, int64_t vb, double nvec, const double* nb4
   double f2 = sqrt((double)c->k) * c->u_acc + c->u_cs;
   *te = c->s * nvec * (f1 * nb4[0] + f2 * nb4[2]);
   *tw = c->s * nvec * (f1 * nb4[1] + f2 * nb4[3]);
+}
+
+/* The four thresholds that apply to element (i, j): those of its column line
+ * (tau_e, tau_w) and of its row line (tau_e, tau_w), in that order. */
+void oracle_thresholds_at(const oracle_cfg* c, const double* nArow, const double* nAblk,
+                          const double* nBcol, const double* nBblk, int64_t i, int64_t j,
+                          double* out4) {
+  taus(c, c->vb_r, nBcol[j], &nAblk[4 * (i / c->vb_r)], &out4[0], &out4[1]);
+  taus(c, c->vb_c, nArow[i], &nBblk[4 * (j / c->vb_c)], &out4[2], &out4[3]);
 }
 
 /* Does the line of rows [i0, i1) x columns [j0, j1) touch an erased block? */

@@ -1,0 +1,201 @@
+"""Thin Python binding of libabft (include/abft.h): argument marshalling only.
+
+Every entry point has the name of the C function it wraps and takes torch tensors (device
+memory and streams come from PyTorch) or raw integers for pointers.  All computation runs
+in the CUDA kernels of libabft.so; there is no CPU or PyTorch fallback, and a missing
+library raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libabft.so")
+
+F64, BF16, BF16X3, FP8_E4M3 = 0, 1, 2, 3
+DTYPE_CODES = {"f64": F64, "bf16": BF16, "bf16x3": BF16X3, "fp8": FP8_E4M3}
+
+OK, ERR_INVALID, ERR_CUDA, ERR_UNSUPPORTED, ERR_UNCORRECTABLE, ERR_TIMEOUT = range(6)
+KIND_CORRECTED, KIND_NONFINITE_CORRECTED, KIND_UNCORRECTABLE, KIND_BLOCK_RECOVERED = 1, 2, 3, 4
+
+# Every symbol include/abft.h declares.
+EXPORTS = ("abft_workspace_bytes", "abft_workspace_layout", "abft_encode", "abft_gemm",
+           "abft_gemm_plain", "abft_verify_correct", "abft_recover_block",
+           "abft_inject_bitflips", "abft_erase_block", "abft_kernel_launches",
+           "abft_last_error", "abft_version")
+
+
+class AbftError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"abft status {status}: {msg}")
+        self.status = status
+
+
+class Desc(ct.Structure):
+    _fields_ = [("m", ct.c_int64), ("n", ct.c_int64), ("k", ct.c_int64),
+                ("lda", ct.c_int64), ("ldb", ct.c_int64), ("ldc", ct.c_int64),
+                ("dtype", ct.c_int32), ("vb_rows", ct.c_int32), ("vb_cols", ct.c_int32),
+                ("grid_p", ct.c_int32), ("grid_q", ct.c_int32), ("flags", ct.c_int32),
+                ("tau_safety", ct.c_double)]
+
+
+class Fault(ct.Structure):
+    _fields_ = [("row", ct.c_int32), ("col", ct.c_int32), ("kind", ct.c_int32),
+                ("side", ct.c_int32), ("delta", ct.c_double), ("r_e", ct.c_double),
+                ("r_w", ct.c_double)]
+
+    def as_dict(self):
+        return dict(row=self.row, col=self.col, kind=self.kind, side=self.side,
+                    delta=self.delta, r_e=self.r_e, r_w=self.r_w)
+
+
+class WsLayout(ct.Structure):
+    _fields_ = [("total", ct.c_size_t), ("acs", ct.c_size_t), ("bcs", ct.c_size_t),
+                ("E", ct.c_size_t), ("F", ct.c_size_t), ("nArow", ct.c_size_t),
+                ("nAblk", ct.c_size_t), ("nBcol", ct.c_size_t), ("nBblk", ct.c_size_t),
+                ("scratch", ct.c_size_t), ("scratch_bytes", ct.c_size_t),
+                ("R", ct.c_int64), ("Cc", ct.c_int64), ("nvr", ct.c_int64), ("nvc", ct.c_int64),
+                ("bs", ct.c_int64), ("acs_ld", ct.c_int64), ("bcs_ld", ct.c_int64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libabft.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libabft.so not built ({path}); run paper_0806_3121_gb300.build.build()")
+        lib = ct.CDLL(path)
+        vp, i32, i64 = ct.c_void_p, ct.c_int32, ct.c_int64
+        D = ct.POINTER(Desc)
+        lib.abft_workspace_bytes.restype = ct.c_size_t
+        lib.abft_workspace_bytes.argtypes = [D]
+        lib.abft_workspace_layout.argtypes = [D, ct.POINTER(WsLayout)]
+        lib.abft_encode.argtypes = [D, vp, vp, vp, vp, vp, vp]
+        lib.abft_gemm.argtypes = [D, vp, vp, vp, vp, vp, vp, vp]
+        lib.abft_gemm_plain.argtypes = [D, vp, vp, vp, vp, vp, vp]
+        lib.abft_verify_correct.argtypes = [D, vp, vp, i32, vp, i32, vp, i32,
+                                            ct.POINTER(ct.c_int32), vp]
+        lib.abft_recover_block.argtypes = [D, vp, vp, i32, i32, ct.POINTER(Fault), vp]
+        lib.abft_inject_bitflips.argtypes = [D, vp, vp, vp, vp, i32, vp]
+        lib.abft_erase_block.argtypes = [D, vp, i32, i32, vp]
+        lib.abft_last_error.restype = ct.c_char_p
+        lib.abft_last_error.argtypes = []
+        lib.abft_kernel_launches.restype = ct.c_int64
+        lib.abft_kernel_launches.argtypes = []
+        lib.abft_version.restype = ct.c_int32
+        lib.abft_version.argtypes = []
+        for name in EXPORTS:  # fail loudly on a library that lacks an entry point
+            getattr(lib, name)
+        _lib = lib
+        return lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(st: int, allow=(OK,)):
+    if st not in allow:
+        raise AbftError(st, load().abft_last_error().decode())
+    return st
+
+
+def make_desc(m, n, k, dtype="f64", vb_rows=None, vb_cols=None, grid_p=0, grid_q=0,
+              lda=None, ldb=None, ldc=None, tau_safety=0.0) -> Desc:
+    code = DTYPE_CODES[dtype] if isinstance(dtype, str) else int(dtype)
+    return Desc(m=m, n=n, k=k, lda=lda or max(k, 1), ldb=ldb or max(n, 1), ldc=ldc or max(n, 1),
+                dtype=code, vb_rows=vb_rows or max(m, 1), vb_cols=vb_cols or max(n, 1),
+                grid_p=grid_p, grid_q=grid_q, flags=0, tau_safety=tau_safety)
+
+
+def abft_workspace_bytes(desc: Desc) -> int:
+    nb = load().abft_workspace_bytes(ct.byref(desc))
+    if nb == 0:
+        raise AbftError(ERR_INVALID, load().abft_last_error().decode())
+    return nb
+
+
+def abft_workspace_layout(desc: Desc) -> WsLayout:
+    out = WsLayout()
+    _check(load().abft_workspace_layout(ct.byref(desc), ct.byref(out)))
+    return out
+
+
+def abft_encode(desc, A, B, ws, a_scale=None, b_scale=None, stream=None):
+    _check(load().abft_encode(ct.byref(desc), _ptr(A), _ptr(B), _ptr(a_scale), _ptr(b_scale),
+                              _ptr(ws), _stream(stream)))
+
+
+def abft_gemm(desc, A, B, C, ws, a_scale=None, b_scale=None, stream=None):
+    _check(load().abft_gemm(ct.byref(desc), _ptr(A), _ptr(B), _ptr(a_scale), _ptr(b_scale),
+                            _ptr(C), _ptr(ws), _stream(stream)))
+
+
+def abft_gemm_plain(desc, A, B, C, a_scale=None, b_scale=None, stream=None):
+    _check(load().abft_gemm_plain(ct.byref(desc), _ptr(A), _ptr(B), _ptr(a_scale),
+                                  _ptr(b_scale), _ptr(C), _stream(stream)))
+
+
+def abft_verify_correct(desc, C, ws, erased=(), max_reports=1024, reread_C=1, stream=None):
+    """Returns (status, [fault dicts], total report count).  Synchronises the stream."""
+    er = (ct.c_int32 * max(1, 2 * len(erased)))(*[v for b in erased for v in b])
+    rep = (Fault * max(1, max_reports))()
+    nrep = ct.c_int32(0)
+    st = load().abft_verify_correct(ct.byref(desc), _ptr(C), _ptr(ws), reread_C,
+                                    ct.cast(er, ct.c_void_p), len(erased),
+                                    ct.cast(rep, ct.c_void_p), max_reports, ct.byref(nrep),
+                                    _stream(stream))
+    _check(st, allow=(OK, ERR_UNCORRECTABLE))
+    return st, [r.as_dict() for r in rep[:min(nrep.value, max_reports)]], nrep.value
+
+
+def abft_recover_block(desc, C, ws, bi, bj, stream=None):
+    """Returns (status, report entry dict).  Synchronises the stream."""
+    f = Fault()
+    st = load().abft_recover_block(ct.byref(desc), _ptr(C), _ptr(ws), bi, bj, ct.byref(f),
+                                   _stream(stream))
+    _check(st, allow=(OK, ERR_UNCORRECTABLE))
+    return st, f.as_dict()
+
+
+def abft_inject_bitflips(desc, C, flips, stream=None):
+    n = len(flips)
+    rows = (ct.c_int64 * max(1, n))(*[f[0] for f in flips])
+    cols = (ct.c_int64 * max(1, n))(*[f[1] for f in flips])
+    bits = (ct.c_int32 * max(1, n))(*[f[2] for f in flips])
+    _check(load().abft_inject_bitflips(ct.byref(desc), _ptr(C), ct.cast(rows, ct.c_void_p),
+                                       ct.cast(cols, ct.c_void_p), ct.cast(bits, ct.c_void_p), n,
+                                       _stream(stream)))
+
+
+def abft_erase_block(desc, C, bi, bj, stream=None):
+    _check(load().abft_erase_block(ct.byref(desc), _ptr(C), bi, bj, _stream(stream)))
+
+
+def abft_kernel_launches() -> int:
+    return load().abft_kernel_launches()
+
+
+def abft_version() -> int:
+    return load().abft_version()

@@ -1,0 +1,360 @@
+// Host side of the C ABI declared in include/abft.h: descriptor validation,
+// workspace layout, launches, report collection.  No exception crosses the
+// ABI; failures return a status and set a thread-local message.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace abft {
+namespace {
+
+thread_local char g_err[512] = "";
+std::atomic<int64_t> g_launches{0};
+
+abft_status fail(abft_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+abft_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(ABFT_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+int ceil_log2(int64_t v) {
+  int e = 0;
+  while (((int64_t)1 << e) < v) ++e;
+  return e;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Unit roundoffs entering the detection threshold:
+//   u_acc: accumulation of the product, u_sum: observed block sums,
+//   u_enc: checksum encoding sums, u_c: storage rounding of C relative to
+//   the accumulator, u_cs: representation error of the checksum operand.
+struct Units {
+  double u_acc, u_sum, u_enc, u_c, u_cs;
+};
+Units units_for(int dtype) {
+  const double u64 = ldexp(1.0, -53), u32 = ldexp(1.0, -24);
+  if (dtype == ABFT_F64) return {u64, u64, u64, u64, u64};
+  return {u32, u64, u32, 0.0, ldexp(1.0, -17)};
+}
+
+size_t operand_bytes(int dtype) { return dtype == ABFT_F64 ? 8 : 2; }
+
+abft_status make_plan(const abft_desc* d, Plan* P) {
+  if (!d) return fail(ABFT_ERR_INVALID, "desc is NULL");
+  if (d->dtype != ABFT_F64 && d->dtype != ABFT_BF16 && d->dtype != ABFT_BF16X3 &&
+      d->dtype != ABFT_FP8_E4M3)
+    return fail(ABFT_ERR_INVALID, "unknown dtype %d", d->dtype);
+  if (d->m < 0 || d->n < 0 || d->k < 0) return fail(ABFT_ERR_INVALID, "negative size");
+  if (d->m > (1ll << 22) || d->n > (1ll << 22) || d->k >= (1ll << 31))
+    return fail(ABFT_ERR_INVALID, "m, n must be at most 2^22 and k below 2^31");
+  if (d->lda < std::max<int64_t>(d->k, 1) || d->ldb < std::max<int64_t>(d->n, 1) ||
+      d->ldc < std::max<int64_t>(d->n, 1))
+    return fail(ABFT_ERR_INVALID, "leading dimension too small (lda>=k, ldb>=n, ldc>=n)");
+  if (d->vb_rows < 1 || d->vb_cols < 1 || (d->m > 0 && d->vb_rows > d->m) ||
+      (d->n > 0 && d->vb_cols > d->n))
+    return fail(ABFT_ERR_INVALID, "verify block sizes must be in [1, m] x [1, n]");
+  if (d->grid_p < 0 || d->grid_q < 0 || (d->grid_p > 0) != (d->grid_q > 0))
+    return fail(ABFT_ERR_INVALID, "erasure grid: grid_p and grid_q both 0 or both > 0");
+  if (d->grid_p > 0 && (d->m % d->grid_p || d->n % d->grid_q))
+    return fail(ABFT_ERR_INVALID, "erasure grid must divide m and n");
+  if (d->flags != 0) return fail(ABFT_ERR_INVALID, "flags must be 0");
+  if (!(d->tau_safety >= 0.0) || !isfinite(d->tau_safety))
+    return fail(ABFT_ERR_INVALID, "tau_safety must be finite and >= 0");
+  if (d->dtype != ABFT_F64) return fail(ABFT_ERR_UNSUPPORTED, "dtype %d not built yet", d->dtype);
+
+  Plan& p = *P;
+  memset(&p, 0, sizeof p);
+  p.d = *d;
+  p.nvr = d->m > 0 ? cdiv(d->m, d->vb_rows) : 0;
+  p.nvc = d->n > 0 ? cdiv(d->n, d->vb_cols) : 0;
+  p.bs = d->grid_p > 0 ? d->m / d->grid_p : 0;
+  p.bc = d->grid_q > 0 ? d->n / d->grid_q : 0;
+  p.R = 2 * p.nvr + p.bs;
+  p.Cc = 2 * p.nvc;
+  p.er = ceil_log2(d->vb_rows);
+  p.ec = ceil_log2(d->vb_cols);
+  p.s = d->tau_safety > 0 ? d->tau_safety : 4.0;
+  const Units u = units_for(d->dtype);
+  const double sk = sqrt((double)d->k);
+  p.f1_col = sk * u.u_acc + sqrt((double)d->vb_rows) * (u.u_sum + u.u_enc) + u.u_c;
+  p.f1_row = sk * u.u_acc + sqrt((double)d->vb_cols) * (u.u_sum + u.u_enc) + u.u_c;
+  p.f2_col = p.f2_row = sk * u.u_acc + u.u_cs;
+
+  // Row tiles of the product grid (64 rows each, data then checksum rows).
+  if (cdiv(d->m, 64) + cdiv(p.R, 64) > 65535)
+    return fail(ABFT_ERR_INVALID, "too many rows for the tile grid (m + checksum rows)");
+
+  abft_ws_layout& L = p.L;
+  const size_t eb = operand_bytes(d->dtype);
+  size_t off = 0;
+  auto region = [&](size_t bytes) {
+    const size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  L.acs = region((size_t)p.R * d->k * eb);
+  L.bcs = region((size_t)d->k * p.Cc * eb);
+  L.E = region((size_t)p.R * d->n * 8);
+  L.F = region((size_t)d->m * p.Cc * 8);
+  L.nArow = region((size_t)d->m * 8);
+  L.nAblk = region((size_t)4 * p.nvr * 8);
+  L.nBcol = region((size_t)d->n * 8);
+  L.nBblk = region((size_t)4 * p.nvc * 8);
+  L.scratch = off;
+  L.scratch_bytes = scratch_bytes(p);
+  off = align256(off + L.scratch_bytes);
+  L.total = off;
+  L.R = p.R;
+  L.Cc = p.Cc;
+  L.nvr = p.nvr;
+  L.nvc = p.nvc;
+  L.bs = p.bs;
+  L.acs_ld = d->k;
+  L.bcs_ld = p.Cc;
+  return ABFT_OK;
+}
+
+bool is_empty(const Plan& P) { return P.d.m == 0 || P.d.n == 0; }
+
+// Partial-reduction sizes used by the encode kernels.
+size_t part_elems(const Plan& P) {
+  const int64_t k = std::max<int64_t>(P.d.k, 1);
+  return (size_t)(4 * P.nvr * cdiv(k, 256) + 4 * P.nvc * cdiv(k, 64) + cdiv(k, 256) * P.d.n);
+}
+
+}  // namespace
+
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+size_t scratch_bytes(const Plan& P) {
+  size_t b = 256;  // counters
+  b += align256(sizeof(FlagEntry) * kCapFlags) * 2;
+  b += align256(sizeof(CandEntry) * kCapCands);
+  b += align256(sizeof(abft_fault) * kCapReport);
+  b += align256(sizeof(double) * part_elems(P));
+  return b;
+}
+
+Scratch scratch_view(const Plan& P, void* ws) {
+  char* base = static_cast<char*>(ws) + P.L.scratch;
+  Scratch S;
+  size_t o = 0;
+  S.cnt = reinterpret_cast<int32_t*>(base + o);
+  o += 256;
+  S.colf = reinterpret_cast<FlagEntry*>(base + o);
+  o += align256(sizeof(FlagEntry) * kCapFlags);
+  S.rowf = reinterpret_cast<FlagEntry*>(base + o);
+  o += align256(sizeof(FlagEntry) * kCapFlags);
+  S.cand = reinterpret_cast<CandEntry*>(base + o);
+  o += align256(sizeof(CandEntry) * kCapCands);
+  S.report = reinterpret_cast<abft_fault*>(base + o);
+  o += align256(sizeof(abft_fault) * kCapReport);
+  S.part = reinterpret_cast<double*>(base + o);
+  S.part_elems = part_elems(P);
+  return S;
+}
+
+}  // namespace abft
+
+using namespace abft;
+
+extern "C" {
+
+const char* abft_last_error(void) { return g_err; }
+
+int32_t abft_version(void) { return 100; }
+
+int64_t abft_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+size_t abft_workspace_bytes(const abft_desc* desc) {
+  Plan P;
+  if (make_plan(desc, &P) != ABFT_OK) return 0;
+  return P.L.total;
+}
+
+abft_status abft_workspace_layout(const abft_desc* desc, abft_ws_layout* out) {
+  if (!out) return fail(ABFT_ERR_INVALID, "out is NULL");
+  Plan P;
+  const abft_status st = make_plan(desc, &P);
+  if (st != ABFT_OK) return st;
+  *out = P.L;
+  return ABFT_OK;
+}
+
+abft_status abft_encode(const abft_desc* desc, const void* A, const void* B, const void* a_scale,
+                        const void* b_scale, void* ws, void* stream) {
+  (void)a_scale;
+  (void)b_scale;
+  Plan P;
+  abft_status st = make_plan(desc, &P);
+  if (st != ABFT_OK) return st;
+  if (is_empty(P)) return ABFT_OK;
+  if (!ws || (P.d.k > 0 && (!A || !B))) return fail(ABFT_ERR_INVALID, "NULL pointer");
+  const cudaError_t e = launch_encode_f64(P, static_cast<const double*>(A),
+                                          static_cast<const double*>(B), ws,
+                                          static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? ABFT_OK : cuda_fail(e, "abft_encode");
+}
+
+static abft_status gemm_common(const abft_desc* desc, const void* A, const void* B, void* C,
+                               void* ws, bool checksums, void* stream) {
+  Plan P;
+  abft_status st = make_plan(desc, &P);
+  if (st != ABFT_OK) return st;
+  if (is_empty(P)) return ABFT_OK;
+  if (!C || (checksums && !ws) || (P.d.k > 0 && (!A || !B)))
+    return fail(ABFT_ERR_INVALID, "NULL pointer");
+  const cudaError_t e =
+      launch_gemm_f64(P, static_cast<const double*>(A), static_cast<const double*>(B),
+                      static_cast<double*>(C), ws, checksums, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? ABFT_OK : cuda_fail(e, checksums ? "abft_gemm" : "abft_gemm_plain");
+}
+
+abft_status abft_gemm(const abft_desc* desc, const void* A, const void* B, const void* a_scale,
+                      const void* b_scale, void* C, void* ws, void* stream) {
+  (void)a_scale;
+  (void)b_scale;
+  return gemm_common(desc, A, B, C, ws, true, stream);
+}
+
+abft_status abft_gemm_plain(const abft_desc* desc, const void* A, const void* B,
+                            const void* a_scale, const void* b_scale, void* C, void* stream) {
+  (void)a_scale;
+  (void)b_scale;
+  return gemm_common(desc, A, B, C, nullptr, false, stream);
+}
+
+abft_status abft_verify_correct(const abft_desc* desc, void* C, void* ws, int32_t reread_C,
+                                const int32_t* erased_blocks, int32_t n_erased, abft_fault* report,
+                                int32_t max_reports, int32_t* n_reports, void* stream) {
+  (void)reread_C;
+  Plan P;
+  abft_status st = make_plan(desc, &P);
+  if (st != ABFT_OK) return st;
+  if (n_reports) *n_reports = 0;
+  if (max_reports < 0 || (max_reports > 0 && !report))
+    return fail(ABFT_ERR_INVALID, "report buffer");
+  if (n_erased < 0 || n_erased > kMaxErased || (n_erased > 0 && !erased_blocks))
+    return fail(ABFT_ERR_INVALID, "n_erased must be in [0, %d]", kMaxErased);
+  Erased er{};
+  er.n = n_erased;
+  for (int t = 0; t < n_erased; ++t) {
+    const int bi = erased_blocks[2 * t], bj = erased_blocks[2 * t + 1];
+    if (P.bs == 0 || bi < 0 || bj < 0 || bi >= P.d.grid_p || bj >= P.d.grid_q)
+      return fail(ABFT_ERR_INVALID, "erased block (%d, %d) outside the erasure grid", bi, bj);
+    er.bi[t] = bi;
+    er.bj[t] = bj;
+  }
+  if (is_empty(P)) return ABFT_OK;
+  if (!C || !ws) return fail(ABFT_ERR_INVALID, "NULL pointer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Scratch S = scratch_view(P, ws);
+  cudaError_t e = cudaMemsetAsync(S.cnt, 0, 256, s);
+  if (e != cudaSuccess) return cuda_fail(e, "abft_verify_correct memset");
+  e = launch_verify(P, C, ws, er, s);
+  if (e != cudaSuccess) return cuda_fail(e, "abft_verify_correct launch");
+  int32_t cnt[kNumCounters];
+  e = cudaMemcpyAsync(cnt, S.cnt, sizeof cnt, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "abft_verify_correct");
+  const int total = cnt[kCntReport];
+  const int stored = std::min(total, kCapReport);
+  std::vector<abft_fault> rep((size_t)stored);
+  if (stored > 0) {
+    e = cudaMemcpyAsync(rep.data(), S.report, sizeof(abft_fault) * stored, cudaMemcpyDeviceToHost,
+                        s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "abft_verify_correct report");
+  }
+  std::sort(rep.begin(), rep.end(), [](const abft_fault& x, const abft_fault& y) {
+    if (x.row != y.row) return x.row < y.row;
+    if (x.col != y.col) return x.col < y.col;
+    return x.kind < y.kind;
+  });
+  bool uncorrectable = cnt[kCntOverflow] != 0 || total > kCapReport;
+  for (const abft_fault& f : rep) uncorrectable |= f.kind == ABFT_KIND_UNCORRECTABLE;
+  const int nout = std::min(stored, max_reports);
+  for (int t = 0; t < nout; ++t) report[t] = rep[(size_t)t];
+  if (n_reports) *n_reports = total;
+  if (cnt[kCntOverflow])
+    return fail(ABFT_ERR_UNCORRECTABLE, "too many flagged lines (%d column, %d row)",
+                cnt[kCntColFlags], cnt[kCntRowFlags]);
+  if (uncorrectable) return fail(ABFT_ERR_UNCORRECTABLE, "flagged lines could not be corrected");
+  return ABFT_OK;
+}
+
+abft_status abft_recover_block(const abft_desc* desc, void* C, void* ws, int32_t bi, int32_t bj,
+                               abft_fault* report_entry, void* stream) {
+  Plan P;
+  abft_status st = make_plan(desc, &P);
+  if (st != ABFT_OK) return st;
+  if (P.bs == 0) return fail(ABFT_ERR_INVALID, "no erasure grid in the descriptor");
+  if (bi < 0 || bj < 0 || bi >= P.d.grid_p || bj >= P.d.grid_q)
+    return fail(ABFT_ERR_INVALID, "block (%d, %d) outside the erasure grid", bi, bj);
+  if (!C || !ws) return fail(ABFT_ERR_INVALID, "NULL pointer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Scratch S = scratch_view(P, ws);
+  cudaError_t e = cudaMemsetAsync(S.cnt + kCntRecoverFlagged, 0, sizeof(int32_t), s);
+  if (e == cudaSuccess) e = launch_recover(P, C, ws, bi, bj, s);
+  int32_t nfl = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&nfl, S.cnt + kCntRecoverFlagged, sizeof nfl, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "abft_recover_block");
+  if (report_entry) {
+    report_entry->row = (int32_t)(bi * P.bs);
+    report_entry->col = (int32_t)(bj * P.bc);
+    report_entry->kind = ABFT_KIND_BLOCK_RECOVERED;
+    report_entry->side = 2;
+    report_entry->delta = 0.0;
+    report_entry->r_e = (double)nfl;
+    report_entry->r_w = 0.0;
+  }
+  if (nfl) return fail(ABFT_ERR_UNCORRECTABLE, "rebuilt block fails %d column checks", nfl);
+  return ABFT_OK;
+}
+
+abft_status abft_inject_bitflips(const abft_desc* desc, void* C, const int64_t* rows,
+                                 const int64_t* cols, const int32_t* bits, int32_t count,
+                                 void* stream) {
+  Plan P;
+  abft_status st = make_plan(desc, &P);
+  if (st != ABFT_OK) return st;
+  if (count < 0 || (count > 0 && (!rows || !cols || !bits || !C)))
+    return fail(ABFT_ERR_INVALID, "bad flip list");
+  const int width = P.d.dtype == ABFT_F64 ? 64 : 32;
+  for (int t = 0; t < count; ++t)
+    if (rows[t] < 0 || rows[t] >= P.d.m || cols[t] < 0 || cols[t] >= P.d.n || bits[t] < 0 ||
+        bits[t] >= width)
+      return fail(ABFT_ERR_INVALID, "flip %d outside C or the element width", t);
+  if (count == 0) return ABFT_OK;
+  const cudaError_t e = launch_inject(P, C, rows, cols, bits, count, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? ABFT_OK : cuda_fail(e, "abft_inject_bitflips");
+}
+
+abft_status abft_erase_block(const abft_desc* desc, void* C, int32_t bi, int32_t bj, void* stream) {
+  Plan P;
+  abft_status st = make_plan(desc, &P);
+  if (st != ABFT_OK) return st;
+  if (P.bs == 0) return fail(ABFT_ERR_INVALID, "no erasure grid in the descriptor");
+  if (bi < 0 || bj < 0 || bi >= P.d.grid_p || bj >= P.d.grid_q || !C)
+    return fail(ABFT_ERR_INVALID, "block (%d, %d) outside the erasure grid", bi, bj);
+  const cudaError_t e = launch_erase(P, C, bi, bj, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? ABFT_OK : cuda_fail(e, "abft_erase_block");
+}
+
+}  // extern "C"

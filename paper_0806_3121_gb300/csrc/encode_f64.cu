@@ -1,0 +1,221 @@
+// Checksum encoding for binary64 operands (section 2.1; the encoded operands
+// of Eq. (1)).  All kernels stream A or B once per quantity with coalesced
+// loads; reductions along the long dimension are two-stage (per-chunk
+// partials, then an ordered sum) so the result does not depend on scheduling.
+#include "internal.cuh"
+
+namespace abft {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRowsPerWarpB = 64;  // rows of B per warp in the row-checksum pass
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum of v over the 256 threads of the block; valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < kThreads / 32; ++q) t += sh[q];
+  return t;
+}
+
+// Column checksums of A per verify block: acs[2I] = e^T A_I, acs[2I+1] =
+// w^T A_I, plus per-chunk partials of the squared norms of e^T|A_I|, w^T|A_I|,
+// e^T A_I, w^T A_I.  Grid (ceil(k/256), nvr); thread = one column l of A.
+__global__ void __launch_bounds__(kThreads) k_encA_cols(const double* __restrict__ A, int64_t lda,
+                                                        int64_t m, int64_t k, int vb, int e,
+                                                        double* __restrict__ acs,
+                                                        double* __restrict__ part, int nch) {
+  __shared__ double sh[kThreads / 32];
+  const int64_t l = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  const int64_t nvb = cdiv(m, vb);
+  const double sc = scalbn(1.0, -e);
+  for (int64_t I = blockIdx.y; I < nvb; I += gridDim.y) {
+  const int64_t i0 = I * vb, i1 = min(i0 + (int64_t)vb, m);
+  double se = 0.0, sw = 0.0, sa = 0.0, swa = 0.0;
+  if (l < k) {
+    const double* p = A + i0 * lda + l;
+#pragma unroll 4
+    for (int64_t i = i0; i < i1; ++i) {
+      const double a = p[(i - i0) * lda];
+      const double w = (double)(i - i0 + 1) * sc;
+      se += a;
+      sw = fma(w, a, sw);
+      sa += fabs(a);
+      swa = fma(w, fabs(a), swa);
+    }
+    acs[(2 * I) * k + l] = se;
+    acs[(2 * I + 1) * k + l] = sw;
+  }
+  const double q[4] = {sa * sa, swa * swa, se * se, sw * sw};
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double t = block_sum(q[c], sh);
+    if (threadIdx.x == 0) part[(4 * I + c) * nch + blockIdx.x] = t;
+  }
+  }
+}
+
+// Block checksum rows S_A[t] = sum_I A[I*bs + t] (erasure grid).
+// Grid (ceil(k/256), bs).
+__global__ void __launch_bounds__(kThreads) k_encA_block(const double* __restrict__ A, int64_t lda,
+                                                         int64_t k, int p, int64_t bs,
+                                                         double* __restrict__ S) {
+  const int64_t l = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (l >= k) return;
+  for (int64_t t = blockIdx.y; t < bs; t += gridDim.y) {
+    double s = 0.0;
+    for (int I = 0; I < p; ++I) s += A[(I * bs + t) * lda + l];
+    S[t * k + l] = s;
+  }
+}
+
+// ||A_{i,:}||_2, one warp per row.
+__global__ void __launch_bounds__(kThreads) k_row_norms(const double* __restrict__ A, int64_t lda,
+                                                        int64_t m, int64_t k,
+                                                        double* __restrict__ out) {
+  const int64_t i = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= m) return;
+  double s = 0.0;
+  for (int64_t l = lane; l < k; l += 32) {
+    const double a = A[i * lda + l];
+    s = fma(a, a, s);
+  }
+  s = warp_sum(s);
+  if (lane == 0) out[i] = sqrt(s);
+}
+
+// Row checksums of B per verify block: bcs[l][2J] = B_J e, bcs[l][2J+1] = B_J w,
+// plus per-chunk partials of the squared norms of |B_J|e, |B_J|w, B_J e, B_J w.
+// One warp per (J, chunk of 64 rows of B).  Grid (ceil(nchunks/8), nvc).
+__global__ void __launch_bounds__(kThreads) k_encB_rows(const double* __restrict__ B, int64_t ldb,
+                                                        int64_t k, int64_t n, int vb, int e,
+                                                        double* __restrict__ bcs, int64_t Cc,
+                                                        double* __restrict__ part, int nch) {
+  const int lane = threadIdx.x & 31;
+  const int64_t chunk = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+  if (chunk >= nch) return;
+  const int64_t nvb = cdiv(n, vb);
+  for (int64_t J = blockIdx.y; J < nvb; J += gridDim.y) {
+  const int64_t j0 = J * vb, j1 = min(j0 + (int64_t)vb, n);
+  const int64_t l0 = chunk * kRowsPerWarpB, l1 = min(l0 + kRowsPerWarpB, k);
+  const double sc = scalbn(1.0, -e);
+  double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
+  for (int64_t l = l0; l < l1; ++l) {
+    double se = 0.0, sw = 0.0, sa = 0.0, swa = 0.0;
+    for (int64_t j = j0 + lane; j < j1; j += 32) {
+      const double b = B[l * ldb + j];
+      const double w = (double)(j - j0 + 1) * sc;
+      se += b;
+      sw = fma(w, b, sw);
+      sa += fabs(b);
+      swa = fma(w, fabs(b), swa);
+    }
+    se = warp_sum(se);
+    sw = warp_sum(sw);
+    sa = warp_sum(sa);
+    swa = warp_sum(swa);
+    if (lane == 0) {
+      bcs[l * Cc + 2 * J] = se;
+      bcs[l * Cc + 2 * J + 1] = sw;
+    }
+    q0 = fma(sa, sa, q0);
+    q1 = fma(swa, swa, q1);
+    q2 = fma(se, se, q2);
+    q3 = fma(sw, sw, q3);
+  }
+  if (lane == 0) {
+    part[(4 * J + 0) * nch + chunk] = q0;
+    part[(4 * J + 1) * nch + chunk] = q1;
+    part[(4 * J + 2) * nch + chunk] = q2;
+    part[(4 * J + 3) * nch + chunk] = q3;
+  }
+  }
+}
+
+// Per-chunk partial sums of B_lj^2 for the column norms.  Grid (ceil(n/256), nch).
+__global__ void __launch_bounds__(kThreads) k_col_sq(const double* __restrict__ B, int64_t ldb,
+                                                     int64_t k, int64_t n,
+                                                     double* __restrict__ part) {
+  const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (j >= n) return;
+  const int64_t nch = cdiv(k, kThreads);
+  for (int64_t c = blockIdx.y; c < nch; c += gridDim.y) {
+    const int64_t l0 = c * kThreads, l1 = min(l0 + kThreads, k);
+    double s = 0.0;
+#pragma unroll 4
+    for (int64_t l = l0; l < l1; ++l) {
+      const double b = B[l * ldb + j];
+      s = fma(b, b, s);
+    }
+    part[c * n + j] = s;
+  }
+}
+
+// out[o] = sqrt(sum_c part[o*so + c*sc]) in chunk order.
+__global__ void k_sum_sqrt(const double* __restrict__ part, int64_t nout, int64_t nch, int64_t so,
+                           int64_t sc, double* __restrict__ out) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nout) return;
+  double s = 0.0;
+  for (int64_t c = 0; c < nch; ++c) s += part[o * so + c * sc];
+  out[o] = sqrt(s);
+}
+
+}  // namespace
+
+cudaError_t launch_encode_f64(const Plan& P, const double* A, const double* B, void* ws,
+                              cudaStream_t st) {
+  const abft_desc& d = P.d;
+  char* w = static_cast<char*>(ws);
+  double* acs = reinterpret_cast<double*>(w + P.L.acs);
+  double* bcs = reinterpret_cast<double*>(w + P.L.bcs);
+  double* nArow = reinterpret_cast<double*>(w + P.L.nArow);
+  double* nAblk = reinterpret_cast<double*>(w + P.L.nAblk);
+  double* nBcol = reinterpret_cast<double*>(w + P.L.nBcol);
+  double* nBblk = reinterpret_cast<double*>(w + P.L.nBblk);
+  Scratch S = scratch_view(P, ws);
+  const int nchA = (int)cdiv(d.k, kThreads);
+  const int nchB = (int)cdiv(d.k, kRowsPerWarpB);
+  const int nchC = (int)cdiv(d.k, kThreads);
+  double* partA = S.part;
+  double* partB = partA + 4 * P.nvr * nchA;
+  double* partC = partB + 4 * P.nvc * nchB;
+
+  auto gy = [](int64_t v) { return (unsigned)(v < 65535 ? v : 65535); };
+  if (d.k == 0) {  // empty inner dimension: all checksums and norms are zero
+    cudaMemsetAsync(nArow, 0, sizeof(double) * d.m, st);
+    cudaMemsetAsync(nAblk, 0, sizeof(double) * 4 * P.nvr, st);
+    cudaMemsetAsync(nBcol, 0, sizeof(double) * d.n, st);
+    cudaMemsetAsync(nBblk, 0, sizeof(double) * 4 * P.nvc, st);
+    return cudaGetLastError();
+  }
+  count_launches(P.bs > 0 ? 8 : 7);
+  k_encA_cols<<<dim3((unsigned)nchA, gy(P.nvr)), kThreads, 0, st>>>(
+      A, d.lda, d.m, d.k, d.vb_rows, P.er, acs, partA, nchA);
+  if (P.bs > 0)
+    k_encA_block<<<dim3((unsigned)cdiv(d.k, kThreads), gy(P.bs)), kThreads, 0, st>>>(
+        A, d.lda, d.k, d.grid_p, P.bs, acs + 2 * P.nvr * d.k);
+  k_row_norms<<<(unsigned)cdiv(d.m * 32, kThreads), kThreads, 0, st>>>(A, d.lda, d.m, d.k, nArow);
+  k_encB_rows<<<dim3((unsigned)cdiv(nchB, kThreads / 32), gy(P.nvc)), kThreads, 0, st>>>(
+      B, d.ldb, d.k, d.n, d.vb_cols, P.ec, bcs, P.Cc, partB, nchB);
+  k_col_sq<<<dim3((unsigned)cdiv(d.n, kThreads), gy(nchC)), kThreads, 0, st>>>(
+      B, d.ldb, d.k, d.n, partC);
+  k_sum_sqrt<<<(unsigned)cdiv(4 * P.nvr, 128), 128, 0, st>>>(partA, 4 * P.nvr, nchA, nchA, 1, nAblk);
+  k_sum_sqrt<<<(unsigned)cdiv(4 * P.nvc, 128), 128, 0, st>>>(partB, 4 * P.nvc, nchB, nchB, 1, nBblk);
+  k_sum_sqrt<<<(unsigned)cdiv(d.n, 128), 128, 0, st>>>(partC, d.n, nchC, 1, d.n, nBcol);
+  return cudaGetLastError();
+}
+
+}  // namespace abft

@@ -1,0 +1,87 @@
+// Internal declarations shared by the CUDA translation units of libabft.
+// Not part of the ABI; see include/abft.h for the public contract.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/abft.h"
+
+namespace abft {
+
+// Capacities of the verify scratch lists (per call).
+constexpr int kCapFlags = 4096;    // flagged lines per side
+constexpr int kCapCands = 2048;    // candidates merged in shared memory
+constexpr int kCapReport = 16384;  // device report entries
+constexpr int kMaxErased = 16;     // erased blocks per verify call
+
+// Counter slots in the scratch region.
+enum Counter : int {
+  kCntColFlags = 0,
+  kCntRowFlags = 1,
+  kCntReport = 2,
+  kCntOverflow = 3,
+  kCntRecoverFlagged = 4,
+  kCntCands = 5,
+  kNumCounters = 16
+};
+
+struct FlagEntry {  // one flagged line
+  int32_t a, b;     // column line: (I, j); row line: (i, J)
+  int32_t nonfin, pad;
+  double re, rw;
+};
+
+struct CandEntry {
+  int32_t row, col, kind, side;
+  double re, rw;
+};
+
+struct Erased {
+  int32_t n;
+  int32_t bi[kMaxErased], bj[kMaxErased];
+};
+
+// Everything the device code needs to know about one problem.
+struct Plan {
+  abft_desc d;
+  int64_t nvr, nvc;  // verify blocks along rows / columns
+  int64_t R, Cc;     // checksum rows of A / checksum columns of B
+  int64_t bs, bc;    // erasure block rows / columns (0 when no grid)
+  int er, ec;        // ceil(log2(vb_rows)), ceil(log2(vb_cols))
+  double s;          // safety factor
+  double f1_col, f2_col, f1_row, f2_row;  // threshold factors
+  abft_ws_layout L;
+};
+
+// Scratch region view.
+struct Scratch {
+  int32_t* cnt;
+  FlagEntry* colf;
+  FlagEntry* rowf;
+  CandEntry* cand;
+  abft_fault* report;
+  double* part;  // partial reductions of encode
+  size_t part_elems;
+};
+
+Scratch scratch_view(const Plan& P, void* ws);
+size_t scratch_bytes(const Plan& P);
+
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Host-side count of kernel launches (abft_kernel_launches()).
+void count_launches(int64_t n);
+
+// Launchers (return cudaGetLastError() of the launches).
+cudaError_t launch_encode_f64(const Plan& P, const double* A, const double* B, void* ws,
+                              cudaStream_t st);
+cudaError_t launch_gemm_f64(const Plan& P, const double* A, const double* B, double* C, void* ws,
+                            bool checksums, cudaStream_t st);
+cudaError_t launch_verify(const Plan& P, void* C, void* ws, const Erased& er, cudaStream_t st);
+cudaError_t launch_recover(const Plan& P, void* C, void* ws, int bi, int bj, cudaStream_t st);
+cudaError_t launch_inject(const Plan& P, void* C, const int64_t* rows, const int64_t* cols,
+                          const int32_t* bits, int count, cudaStream_t st);
+cudaError_t launch_erase(const Plan& P, void* C, int bi, int bj, cudaStream_t st);
+
+}  // namespace abft

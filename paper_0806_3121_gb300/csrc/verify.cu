@@ -1,0 +1,509 @@
+// Detect / locate / correct and erasure recovery (sections 1, 2.1 and 2.2 of
+// the paper: the consistency of (AB)_F detects, localizes and corrects
+// errors; a lost part is the checksum minus the surviving parts).
+//
+// Pipeline of one verify call, all on the device:
+//   k_col_check   one thread per column line (verify block I, column j):
+//                 binary64 sums e^T C_I[:,j], w^T C_I[:,j], non-finite count,
+//                 residuals against E, threshold test, append if flagged.
+//   k_row_check   one warp per row line (row i, verify block J), against F.
+//   k_locate_correct  one CTA: candidates from the flagged lines (single
+//                 non-finite element, or the weighted/unweighted residual
+//                 ratio), bitonic sort + merge, choice of a correcting line,
+//                 recomputation in binary64, re-check of the touched lines,
+//                 report entries.
+// Recovery: k_recover rebuilds an erased block from S = sum_I C_I, then
+// k_col_check (count mode) re-checks the rebuilt block.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace abft {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kLocThreads = 512;
+
+struct CheckArgs {
+  const void* C;
+  int64_t ldc, m, n;
+  const double* E;  // R x n, row 2I = e-checksum, 2I+1 = w-checksum, then S
+  const double* F;  // m x Cc
+  const double* nArow;
+  const double* nAblk;
+  const double* nBcol;
+  const double* nBblk;
+  int vb_r, vb_c, er, ec;
+  int64_t nvr, nvc, Cc, bs, bc;
+  double s, f1c, f2c, f1r, f2r;
+  Erased erased;
+  FlagEntry* colf;
+  FlagEntry* rowf;
+  int32_t* cnt;
+  abft_fault* report;
+  CandEntry* cand;
+};
+
+template <typename TC>
+__device__ __forceinline__ double ld(const void* C, int64_t idx) {
+  return (double)static_cast<const TC*>(C)[idx];
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ int warp_isum(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ long long warp_min(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w < v ? w : v;
+  }
+  return v;
+}
+
+__device__ __forceinline__ bool touches_erased(const Erased& e, int64_t bs, int64_t bc, int64_t i0,
+                                               int64_t i1, int64_t j0, int64_t j1) {
+  for (int t = 0; t < e.n; ++t) {
+    const int64_t r0 = (int64_t)e.bi[t] * bs, c0 = (int64_t)e.bj[t] * bc;
+    if (i0 < r0 + bs && r0 < i1 && j0 < c0 + bc && c0 < j1) return true;
+  }
+  return false;
+}
+
+// Flag rule: not (|r_e| <= tau_e and |r_w| <= tau_w); NaN residuals fail it.
+__device__ __forceinline__ bool is_flagged(double re, double rw, double te, double tw) {
+  return !(fabs(re) <= te && fabs(rw) <= tw);
+}
+
+// Residuals of column line (I, j).  Returns the non-finite count.
+template <typename TC>
+__device__ int col_line(const CheckArgs& a, int64_t I, int64_t j, double& re, double& rw,
+                        double& te, double& tw) {
+  const int64_t i0 = I * a.vb_r, i1 = min(i0 + (int64_t)a.vb_r, a.m);
+  const double sc = scalbn(1.0, -a.er);
+  double se = 0.0, sw = 0.0;
+  int nf = 0;
+#pragma unroll 4
+  for (int64_t i = i0; i < i1; ++i) {
+    const double x = ld<TC>(a.C, i * a.ldc + j);
+    se += x;
+    sw = fma((double)(i - i0 + 1) * sc, x, sw);
+    nf += isfinite(x) ? 0 : 1;
+  }
+  re = se - a.E[(2 * I) * a.n + j];
+  rw = sw - a.E[(2 * I + 1) * a.n + j];
+  const double nb = a.nBcol[j];
+  te = a.s * nb * (a.f1c * a.nAblk[4 * I + 0] + a.f2c * a.nAblk[4 * I + 2]);
+  tw = a.s * nb * (a.f1c * a.nAblk[4 * I + 1] + a.f2c * a.nAblk[4 * I + 3]);
+  return nf;
+}
+
+// Residuals of row line (i, J) computed by one warp; valid in every lane.
+template <typename TC>
+__device__ int row_line_warp(const CheckArgs& a, int64_t i, int64_t J, double& re, double& rw,
+                             double& te, double& tw) {
+  const int lane = threadIdx.x & 31;
+  const int64_t j0 = J * a.vb_c, j1 = min(j0 + (int64_t)a.vb_c, a.n);
+  const double sc = scalbn(1.0, -a.ec);
+  double se = 0.0, sw = 0.0;
+  int nf = 0;
+  for (int64_t j = j0 + lane; j < j1; j += 32) {
+    const double x = ld<TC>(a.C, i * a.ldc + j);
+    se += x;
+    sw = fma((double)(j - j0 + 1) * sc, x, sw);
+    nf += isfinite(x) ? 0 : 1;
+  }
+  se = warp_sum(se);
+  sw = warp_sum(sw);
+  nf = warp_isum(nf);
+  re = se - a.F[i * a.Cc + 2 * J];
+  rw = sw - a.F[i * a.Cc + 2 * J + 1];
+  const double na = a.nArow[i];
+  te = a.s * na * (a.f1r * a.nBblk[4 * J + 0] + a.f2r * a.nBblk[4 * J + 2]);
+  tw = a.s * na * (a.f1r * a.nBblk[4 * J + 1] + a.f2r * a.nBblk[4 * J + 3]);
+  return nf;
+}
+
+// Column lines [I_begin, I_end) x [j_begin, j_end).  mode 0: append flagged
+// lines to colf (skipping erased blocks); mode 1: only count them in
+// cnt[kCntRecoverFlagged].  Grid (ceil((j_end-j_begin)/256), <= 65535).
+template <typename TC>
+__global__ void __launch_bounds__(kThreads) k_col_check(const CheckArgs a, int64_t j_begin,
+                                                        int64_t j_end, int64_t I_begin,
+                                                        int64_t I_end, int mode) {
+  const int64_t j = j_begin + (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (j >= j_end) return;
+  for (int64_t I = I_begin + blockIdx.y; I < I_end; I += gridDim.y) {
+    const int64_t i0 = I * a.vb_r, i1 = min(i0 + (int64_t)a.vb_r, a.m);
+    if (mode == 0 && touches_erased(a.erased, a.bs, a.bc, i0, i1, j, j + 1)) continue;
+    double re, rw, te, tw;
+    const int nf = col_line<TC>(a, I, j, re, rw, te, tw);
+    if (nf == 0 && !is_flagged(re, rw, te, tw)) continue;
+    if (mode == 1) {
+      atomicAdd(&a.cnt[kCntRecoverFlagged], 1);
+      continue;
+    }
+    const int slot = atomicAdd(&a.cnt[kCntColFlags], 1);
+    if (slot < kCapFlags) a.colf[slot] = FlagEntry{(int32_t)I, (int32_t)j, nf, 0, re, rw};
+  }
+}
+
+template <typename TC>
+__global__ void __launch_bounds__(kThreads) k_row_check(const CheckArgs a) {
+  const int64_t gw = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+  if (gw >= a.m * a.nvc) return;
+  const int64_t i = gw / a.nvc, J = gw % a.nvc;
+  const int64_t j0 = J * a.vb_c, j1 = min(j0 + (int64_t)a.vb_c, a.n);
+  if (touches_erased(a.erased, a.bs, a.bc, i, i + 1, j0, j1)) return;
+  double re, rw, te, tw;
+  const int nf = row_line_warp<TC>(a, i, J, re, rw, te, tw);
+  if ((threadIdx.x & 31) != 0) return;
+  if (nf == 0 && !is_flagged(re, rw, te, tw)) return;
+  const int slot = atomicAdd(&a.cnt[kCntRowFlags], 1);
+  if (slot < kCapFlags) a.rowf[slot] = FlagEntry{(int32_t)i, (int32_t)J, nf, 0, re, rw};
+}
+
+// Position (0-based) of a single error inside a line of len elements from
+// rho = 2^e r_w / r_e, accepted within 0.25 of an integer in [1, len].
+__device__ __forceinline__ int64_t ratio_position(double re, double rw, int e, int64_t len) {
+  if (!(re != 0.0) || !isfinite(re) || !isfinite(rw)) return -1;
+  const double rho = scalbn(rw / re, e);
+  if (!isfinite(rho)) return -1;
+  const double r = rint(rho);
+  if (!(fabs(rho - r) <= 0.25) || r < 1.0 || r > (double)len) return -1;
+  return (int64_t)r - 1;
+}
+
+__device__ __forceinline__ void push_report(const CheckArgs& a, int32_t row, int32_t col, int kind,
+                                            int side, double delta, double re, double rw) {
+  const int slot = atomicAdd(&a.cnt[kCntReport], 1);
+  if (slot < kCapReport) a.report[slot] = abft_fault{row, col, kind, side, delta, re, rw};
+}
+
+__device__ __forceinline__ int32_t key_row(uint64_t k) { return (int32_t)(k >> 32); }
+__device__ __forceinline__ int32_t key_col(uint64_t k) { return (int32_t)((k >> 1) & 0x7fffffffu); }
+
+template <typename TC>
+__global__ void __launch_bounds__(kLocThreads, 1) k_locate_correct(const CheckArgs a) {
+  __shared__ uint64_t keys[kCapCands];
+  __shared__ int32_t sidx[kCapCands];
+  __shared__ int32_t how[kCapCands];   // -2 duplicate, -1 uncorrectable, 0 column, 1 row
+  __shared__ int32_t mkind[kCapCands];
+  __shared__ int s_nc;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kLocThreads / 32;
+  if (tid == 0) s_nc = 0;
+  __syncthreads();
+  const int ncf = a.cnt[kCntColFlags], nrf = a.cnt[kCntRowFlags];
+  const int ncl = min(ncf, kCapFlags), nrl = min(nrf, kCapFlags);
+  if (tid == 0 && (ncf > kCapFlags || nrf > kCapFlags)) a.cnt[kCntOverflow] = 1;
+
+  // 1. candidates
+  for (int L = warp; L < ncl + nrl; L += nwarps) {
+    const bool colside = L < ncl;
+    const FlagEntry f = colside ? a.colf[L] : a.rowf[L - ncl];
+    int64_t row = -1, col = -1;
+    int kind = 0;
+    if (colside) {
+      const int64_t I = f.a, j = f.b, i0 = I * a.vb_r, i1 = min(i0 + (int64_t)a.vb_r, a.m);
+      if (f.nonfin > 0) {
+        int c = 0;
+        long long pos = LLONG_MAX;
+        for (int64_t i = i0 + lane; i < i1; i += 32)
+          if (!isfinite(ld<TC>(a.C, i * a.ldc + j))) { ++c; pos = min(pos, (long long)i); }
+        c = warp_isum(c);
+        pos = warp_min(pos);
+        if (c == 1) { row = pos; col = j; kind = ABFT_KIND_NONFINITE_CORRECTED; }
+      } else {
+        const int64_t t = ratio_position(f.re, f.rw, a.er, i1 - i0);
+        if (t >= 0) { row = i0 + t; col = j; kind = ABFT_KIND_CORRECTED; }
+      }
+    } else {
+      const int64_t i = f.a, J = f.b, j0 = J * a.vb_c, j1 = min(j0 + (int64_t)a.vb_c, a.n);
+      if (f.nonfin > 0) {
+        int c = 0;
+        long long pos = LLONG_MAX;
+        for (int64_t j = j0 + lane; j < j1; j += 32)
+          if (!isfinite(ld<TC>(a.C, i * a.ldc + j))) { ++c; pos = min(pos, (long long)j); }
+        c = warp_isum(c);
+        pos = warp_min(pos);
+        if (c == 1) { row = i; col = pos; kind = ABFT_KIND_NONFINITE_CORRECTED; }
+      } else {
+        const int64_t t = ratio_position(f.re, f.rw, a.ec, j1 - j0);
+        if (t >= 0) { row = i; col = j0 + t; kind = ABFT_KIND_CORRECTED; }
+      }
+    }
+    if (lane == 0 && kind != 0) {
+      const int slot = atomicAdd(&s_nc, 1);
+      if (slot < kCapCands) {
+        a.cand[slot] = CandEntry{(int32_t)row, (int32_t)col, kind, colside ? 0 : 1, f.re, f.rw};
+        keys[slot] = ((uint64_t)row << 32) | ((uint64_t)col << 1) | (colside ? 0u : 1u);
+        sidx[slot] = slot;
+      }
+    }
+  }
+  __syncthreads();
+  const int nc = min(s_nc, kCapCands);
+  if (tid == 0 && s_nc > kCapCands) a.cnt[kCntOverflow] = 1;
+  if (tid == 0) a.cnt[kCntCands] = s_nc;
+
+  // 2. bitonic sort of (key, index), padded to a power of two
+  int P2 = 1;
+  while (P2 < nc) P2 <<= 1;
+  for (int t = nc + tid; t < P2; t += kLocThreads) { keys[t] = ~0ull; sidx[t] = -1; }
+  __syncthreads();
+  for (int k2 = 2; k2 <= P2; k2 <<= 1) {
+    for (int jj = k2 >> 1; jj > 0; jj >>= 1) {
+      for (int t = tid; t < P2; t += kLocThreads) {
+        const int o = t ^ jj;
+        if (o > t) {
+          const bool up = (t & k2) == 0;
+          if ((keys[t] > keys[o]) == up) {
+            const uint64_t kt = keys[t]; keys[t] = keys[o]; keys[o] = kt;
+            const int32_t it = sidx[t]; sidx[t] = sidx[o]; sidx[o] = it;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // 3. merge duplicates (one element can be proposed by its column line and
+  //    by its row line; the column entry sorts first and is kept)
+  for (int t = tid; t < nc; t += kLocThreads) {
+    const bool dup = t > 0 && (keys[t] >> 1) == (keys[t - 1] >> 1);
+    how[t] = dup ? -2 : 0;
+    int kd = a.cand[sidx[t]].kind;
+    if (!dup && t + 1 < nc && (keys[t + 1] >> 1) == (keys[t] >> 1) &&
+        a.cand[sidx[t + 1]].kind == ABFT_KIND_NONFINITE_CORRECTED)
+      kd = ABFT_KIND_NONFINITE_CORRECTED;
+    mkind[t] = kd;
+  }
+  __syncthreads();
+
+  // 4. choose the correcting line: one in which the candidate is alone
+  for (int t = tid; t < nc; t += kLocThreads) {
+    if (how[t] == -2) continue;
+    const int32_t r = key_row(keys[t]), c = key_col(keys[t]);
+    const int64_t I = r / a.vb_r, J = c / a.vb_c;
+    int ncol = 0, nrow = 0;
+    for (int u = 0; u < nc; ++u) {
+      if ((keys[u] >> 1) == ((u > 0) ? (keys[u - 1] >> 1) : ~0ull)) continue;  // duplicate
+      const int32_t r2 = key_row(keys[u]), c2 = key_col(keys[u]);
+      if (c2 == c && r2 / a.vb_r == I) ++ncol;
+      if (r2 == r && c2 / a.vb_c == J) ++nrow;
+    }
+    how[t] = ncol == 1 ? 0 : (nrow == 1 ? 1 : -1);
+  }
+  __syncthreads();
+
+  // 5. flagged lines holding no candidate are uncorrectable
+  for (int L = tid; L < ncl + nrl; L += kLocThreads) {
+    const bool colside = L < ncl;
+    const FlagEntry f = colside ? a.colf[L] : a.rowf[L - ncl];
+    bool has = false;
+    for (int u = 0; u < nc && !has; ++u) {
+      if (how[u] == -2) continue;
+      const int32_t r2 = key_row(keys[u]), c2 = key_col(keys[u]);
+      has = colside ? (c2 == f.b && r2 / a.vb_r == f.a) : (r2 == f.a && c2 / a.vb_c == f.b);
+    }
+    if (!has) {
+      if (colside) push_report(a, -1, f.b, ABFT_KIND_UNCORRECTABLE, 0, 0.0, f.re, f.rw);
+      else push_report(a, f.a, -1, ABFT_KIND_UNCORRECTABLE, 1, 0.0, f.re, f.rw);
+    }
+  }
+
+  // 6. corrections by recomputation in binary64
+  for (int t = warp; t < nc; t += nwarps) {
+    if (how[t] == -2) continue;
+    const CandEntry ce = a.cand[sidx[t]];
+    const int64_t r = key_row(keys[t]), c = key_col(keys[t]);
+    if (how[t] == -1) {
+      if (lane == 0) push_report(a, (int32_t)r, (int32_t)c, ABFT_KIND_UNCORRECTABLE, ce.side, 0.0,
+                                 ce.re, ce.rw);
+      continue;
+    }
+    double s = 0.0, expect;
+    if (how[t] == 0) {
+      const int64_t I = r / a.vb_r, i0 = I * a.vb_r, i1 = min(i0 + (int64_t)a.vb_r, a.m);
+      for (int64_t i = i0 + lane; i < i1; i += 32)
+        if (i != r) s += ld<TC>(a.C, i * a.ldc + c);
+      expect = a.E[(2 * I) * a.n + c];
+    } else {
+      const int64_t J = c / a.vb_c, j0 = J * a.vb_c, j1 = min(j0 + (int64_t)a.vb_c, a.n);
+      for (int64_t j = j0 + lane; j < j1; j += 32)
+        if (j != c) s += ld<TC>(a.C, r * a.ldc + j);
+      expect = a.F[r * a.Cc + 2 * J];
+    }
+    s = warp_sum(s);
+    if (lane == 0) {
+      TC* Cp = static_cast<TC*>(const_cast<void*>(a.C));
+      const TC old = Cp[r * a.ldc + c];
+      const TC v = (TC)(expect - s);
+      Cp[r * a.ldc + c] = v;
+      push_report(a, (int32_t)r, (int32_t)c, mkind[t], ce.side, (double)old - (double)v, ce.re,
+                  ce.rw);
+    }
+  }
+  __syncthreads();
+
+  // 7. re-check both lines of every corrected element (each line once)
+  for (int t = warp; t < nc; t += nwarps) {
+    if (how[t] < 0) continue;
+    const int32_t r = key_row(keys[t]), c = key_col(keys[t]);
+    const int64_t I = r / a.vb_r, J = c / a.vb_c;
+    bool dup_c = false, dup_r = false;
+    for (int u = 0; u < t; ++u) {
+      if (how[u] < 0) continue;
+      const int32_t r2 = key_row(keys[u]), c2 = key_col(keys[u]);
+      if (c2 == c && r2 / a.vb_r == I) dup_c = true;
+      if (r2 == r && c2 / a.vb_c == J) dup_r = true;
+    }
+    double re, rw, te, tw;
+    if (!dup_c && lane == 0) {
+      col_line<TC>(a, I, c, re, rw, te, tw);
+      if (is_flagged(re, rw, te, tw)) push_report(a, -1, c, ABFT_KIND_UNCORRECTABLE, 0, 0.0, re, rw);
+    }
+    if (!dup_r) {
+      row_line_warp<TC>(a, r, J, re, rw, te, tw);
+      if (lane == 0 && is_flagged(re, rw, te, tw))
+        push_report(a, r, -1, ABFT_KIND_UNCORRECTABLE, 1, 0.0, re, rw);
+    }
+  }
+}
+
+// C[bi*bs + t][j] = S[t][j] - sum_{I != bi} C[I*bs + t][j], binary64.
+// Grid (ceil(bc/256), bs).
+template <typename TC>
+__global__ void __launch_bounds__(kThreads) k_recover(TC* C, int64_t ldc, const double* S,
+                                                      int64_t n, int p, int64_t bs, int64_t bc,
+                                                      int bi, int bj) {
+  const int64_t jj = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (jj >= bc) return;
+  const int64_t j = (int64_t)bj * bc + jj;
+  for (int64_t t = blockIdx.y; t < bs; t += gridDim.y) {
+    double s = 0.0;
+    for (int I = 0; I < p; ++I)
+      if (I != bi) s += (double)C[(I * bs + t) * ldc + j];
+    C[((int64_t)bi * bs + t) * ldc + j] = (TC)(S[t * n + j] - s);
+  }
+}
+
+struct Flip {
+  int64_t row, col;
+  int32_t bit, pad;
+};
+struct FlipList {
+  int32_t n, pad;
+  Flip f[64];
+};
+
+template <typename TC, typename TU>
+__global__ void k_inject(TC* C, int64_t ldc, const FlipList fl) {
+  const int t = threadIdx.x;
+  if (t >= fl.n) return;
+  TU* u = reinterpret_cast<TU*>(C + fl.f[t].row * ldc + fl.f[t].col);
+  *u ^= (TU)1 << fl.f[t].bit;
+}
+
+template <typename TC>
+__global__ void k_erase(TC* C, int64_t ldc, int64_t r0, int64_t c0, int64_t bs, int64_t bc) {
+  const int64_t jj = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (jj >= bc) return;
+  for (int64_t t = blockIdx.y; t < bs; t += gridDim.y) C[(r0 + t) * ldc + c0 + jj] = (TC)nan("");
+}
+
+unsigned gy(int64_t v) { return (unsigned)(v < 65535 ? v : 65535); }
+
+CheckArgs make_args(const Plan& P, void* C, void* ws) {
+  char* w = static_cast<char*>(ws);
+  Scratch S = scratch_view(P, ws);
+  CheckArgs a{};
+  a.C = C;
+  a.ldc = P.d.ldc; a.m = P.d.m; a.n = P.d.n;
+  a.E = reinterpret_cast<const double*>(w + P.L.E);
+  a.F = reinterpret_cast<const double*>(w + P.L.F);
+  a.nArow = reinterpret_cast<const double*>(w + P.L.nArow);
+  a.nAblk = reinterpret_cast<const double*>(w + P.L.nAblk);
+  a.nBcol = reinterpret_cast<const double*>(w + P.L.nBcol);
+  a.nBblk = reinterpret_cast<const double*>(w + P.L.nBblk);
+  a.vb_r = P.d.vb_rows; a.vb_c = P.d.vb_cols; a.er = P.er; a.ec = P.ec;
+  a.nvr = P.nvr; a.nvc = P.nvc; a.Cc = P.Cc; a.bs = P.bs; a.bc = P.bc;
+  a.s = P.s; a.f1c = P.f1_col; a.f2c = P.f2_col; a.f1r = P.f1_row; a.f2r = P.f2_row;
+  a.colf = S.colf; a.rowf = S.rowf; a.cnt = S.cnt; a.report = S.report; a.cand = S.cand;
+  return a;
+}
+
+template <typename TC>
+cudaError_t verify_t(const Plan& P, void* C, void* ws, const Erased& er, cudaStream_t st) {
+  CheckArgs a = make_args(P, C, ws);
+  a.erased = er;
+  const int64_t m = P.d.m, n = P.d.n;
+  k_col_check<TC><<<dim3((unsigned)cdiv(n, kThreads), gy(P.nvr)), kThreads, 0, st>>>(
+      a, 0, n, 0, P.nvr, 0);
+  k_row_check<TC><<<(unsigned)cdiv(m * P.nvc * 32, kThreads), kThreads, 0, st>>>(a);
+  k_locate_correct<TC><<<1, kLocThreads, 0, st>>>(a);
+  count_launches(3);
+  return cudaGetLastError();
+}
+
+template <typename TC>
+cudaError_t recover_t(const Plan& P, void* C, void* ws, int bi, int bj, cudaStream_t st) {
+  CheckArgs a = make_args(P, C, ws);
+  const double* S = a.E + 2 * P.nvr * P.d.n;
+  k_recover<TC><<<dim3((unsigned)cdiv(P.bc, kThreads), gy(P.bs)), kThreads, 0, st>>>(
+      static_cast<TC*>(C), P.d.ldc, S, P.d.n, P.d.grid_p, P.bs, P.bc, bi, bj);
+  const int64_t I0 = ((int64_t)bi * P.bs) / P.d.vb_rows;
+  const int64_t I1 = cdiv(((int64_t)bi + 1) * P.bs, P.d.vb_rows);
+  k_col_check<TC><<<dim3((unsigned)cdiv(P.bc, kThreads), gy(I1 - I0)), kThreads, 0, st>>>(
+      a, (int64_t)bj * P.bc, ((int64_t)bj + 1) * P.bc, I0, I1, 1);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_verify(const Plan& P, void* C, void* ws, const Erased& er, cudaStream_t st) {
+  return P.d.dtype == ABFT_F64 ? verify_t<double>(P, C, ws, er, st)
+                               : verify_t<float>(P, C, ws, er, st);
+}
+
+cudaError_t launch_recover(const Plan& P, void* C, void* ws, int bi, int bj, cudaStream_t st) {
+  return P.d.dtype == ABFT_F64 ? recover_t<double>(P, C, ws, bi, bj, st)
+                               : recover_t<float>(P, C, ws, bi, bj, st);
+}
+
+cudaError_t launch_inject(const Plan& P, void* C, const int64_t* rows, const int64_t* cols,
+                          const int32_t* bits, int count, cudaStream_t st) {
+  for (int t0 = 0; t0 < count; t0 += 64) {
+    FlipList fl{};
+    fl.n = count - t0 < 64 ? count - t0 : 64;
+    for (int t = 0; t < fl.n; ++t) fl.f[t] = Flip{rows[t0 + t], cols[t0 + t], bits[t0 + t], 0};
+    if (P.d.dtype == ABFT_F64)
+      k_inject<double, unsigned long long><<<1, 64, 0, st>>>(static_cast<double*>(C), P.d.ldc, fl);
+    else
+      k_inject<float, unsigned int><<<1, 64, 0, st>>>(static_cast<float*>(C), P.d.ldc, fl);
+    count_launches(1);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_erase(const Plan& P, void* C, int bi, int bj, cudaStream_t st) {
+  const dim3 grid((unsigned)cdiv(P.bc, kThreads), gy(P.bs));
+  if (P.d.dtype == ABFT_F64)
+    k_erase<double><<<grid, kThreads, 0, st>>>(static_cast<double*>(C), P.d.ldc,
+                                               (int64_t)bi * P.bs, (int64_t)bj * P.bc, P.bs, P.bc);
+  else
+    k_erase<float><<<grid, kThreads, 0, st>>>(static_cast<float*>(C), P.d.ldc, (int64_t)bi * P.bs,
+                                              (int64_t)bj * P.bc, P.bs, P.bc);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace abft

@@ -1,0 +1,113 @@
+"""The C-ABI library loads, exports every entry point include/abft.h declares, and its
+host-side validation and workspace layout behave as documented.  No GPU is touched:
+only calls that never launch work run here."""
+import ctypes as ct
+import os
+import re
+
+import pytest
+
+from paper_0806_3121_gb300 import abft, build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "abft.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return abft.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(abft_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(abft.EXPORTS)
+
+
+def test_version(lib):
+    assert abft.abft_version() >= 100
+
+
+def test_struct_sizes_match_header(lib):
+    assert ct.sizeof(abft.Desc) == 6 * 8 + 6 * 4 + 8
+    assert ct.sizeof(abft.Fault) == 4 * 4 + 3 * 8
+
+
+def test_workspace_layout_shapes(lib):
+    d = abft.make_desc(11264, 11264, 11264, "f64", 512, 512, 22, 22)
+    L = abft.abft_workspace_layout(d)
+    assert L.nvr == 22 and L.nvc == 22 and L.bs == 512
+    assert L.R == 2 * 22 + 512 and L.Cc == 44
+    for off in (L.acs, L.bcs, L.E, L.F, L.nArow, L.nAblk, L.nBcol, L.nBblk, L.scratch):
+        assert off % 256 == 0
+    assert L.bcs >= L.acs + L.R * 11264 * 8
+    assert L.E >= L.bcs + 11264 * L.Cc * 8
+    assert L.F >= L.E + L.R * 11264 * 8
+    assert L.total >= L.scratch + L.scratch_bytes
+    assert abft.abft_workspace_bytes(d) == L.total
+
+
+def test_ragged_layout(lib):
+    d = abft.make_desc(100, 70, 33, "f64", 32, 16)
+    L = abft.abft_workspace_layout(d)
+    assert L.nvr == 4 and L.nvc == 5 and L.R == 8 and L.Cc == 10 and L.bs == 0
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(m=-1), "negative"),
+    (dict(vb_rows=0), "verify block"),
+    (dict(vb_rows=65), "verify block"),
+    (dict(grid_p=3, grid_q=3), "divide"),
+    (dict(grid_p=2, grid_q=0), "both"),
+    (dict(lda=10), "leading"),
+    (dict(dtype=9), "dtype"),
+    (dict(tau_safety=-1.0), "tau_safety"),
+])
+def test_invalid_descriptors(lib, kw, msg):
+    d = abft.make_desc(64, 64, 64, "f64", 32, 32)
+    for k, v in kw.items():
+        setattr(d, k, v)
+    assert lib.abft_workspace_bytes(ct.byref(d)) == 0
+    assert msg in lib.abft_last_error().decode()
+    with pytest.raises(abft.AbftError) as e:
+        abft.abft_workspace_layout(d)
+    assert e.value.status == abft.ERR_INVALID
+
+
+def test_invalid_calls_launch_nothing(lib):
+    """Argument errors are caught on the host before any CUDA call (so they are safe
+    without a GPU)."""
+    d = abft.make_desc(64, 64, 64, "f64", 32, 32, 2, 2)
+    st = lib.abft_recover_block(ct.byref(d), None, None, 5, 0, None, None)
+    assert st == abft.ERR_INVALID
+    st = lib.abft_erase_block(ct.byref(d), None, 0, 9, None)
+    assert st == abft.ERR_INVALID
+    rows = (ct.c_int64 * 1)(64)
+    cols = (ct.c_int64 * 1)(0)
+    bits = (ct.c_int32 * 1)(3)
+    st = lib.abft_inject_bitflips(ct.byref(d), ct.c_void_p(1), rows, cols, bits, 1, None)
+    assert st == abft.ERR_INVALID and "outside" in lib.abft_last_error().decode()
+    er = (ct.c_int32 * 2)(0, 7)
+    n = ct.c_int32(0)
+    st = lib.abft_verify_correct(ct.byref(d), ct.c_void_p(1), ct.c_void_p(1), 1, er, 1, None, 0,
+                                 ct.byref(n), None)
+    assert st == abft.ERR_INVALID
+    d2 = abft.make_desc(64, 64, 64, "f64", 32, 32)
+    st = lib.abft_recover_block(ct.byref(d2), ct.c_void_p(1), ct.c_void_p(1), 0, 0, None, None)
+    assert st == abft.ERR_INVALID and "grid" in lib.abft_last_error().decode()
+
+
+def test_empty_problem_is_a_no_op(lib):
+    d = abft.make_desc(0, 16, 16, "f64", 1, 16)
+    assert abft.abft_workspace_bytes(d) > 0
+    # nothing to do: returns OK without touching the (NULL) pointers or the GPU
+    assert lib.abft_gemm(ct.byref(d), None, None, None, None, ct.c_void_p(1), ct.c_void_p(1), None) == 0

@@ -1,0 +1,311 @@
+"""Parity of the binary64 CUDA path (through the C ABI) with the CPU oracle.
+
+Values: relative Frobenius error <= 1e-12 and an elementwise rounding bound.
+Decisions: fault positions, kinds and recovered blocks bit-exact, for every injected
+flip the oracle classifies as graded or benign (guard-band flips may go either way)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0806_3121_gb300 import abft, workloads as wl
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL_F64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0806_3121_gb300 import build
+    build.build()
+    return abft.load()
+
+
+class Run:
+    """One problem on the GPU: operands, workspace, encode + ABFT product."""
+
+    def __init__(self, A, B, vb_r, vb_c, p=0, q=0, plain=False):
+        self.A_np, self.B_np = np.ascontiguousarray(A), np.ascontiguousarray(B)
+        m, k = A.shape
+        n = B.shape[1]
+        self.m, self.n, self.k = m, n, k
+        self.desc = abft.make_desc(m, n, k, "f64", vb_r, vb_c, p, q)
+        self.L = abft.abft_workspace_layout(self.desc)
+        self.A = torch.from_numpy(self.A_np).cuda()
+        self.B = torch.from_numpy(self.B_np).cuda()
+        self.C = torch.empty((m, n), dtype=torch.float64, device="cuda")
+        self.ws = torch.zeros(self.L.total, dtype=torch.uint8, device="cuda")
+        abft.abft_encode(self.desc, self.A, self.B, self.ws)
+        abft.abft_gemm(self.desc, self.A, self.B, self.C, self.ws)
+        torch.cuda.synchronize()
+
+    def region(self, off, shape):
+        nb = int(np.prod(shape)) * 8
+        return self.ws[off:off + nb].view(torch.float64).reshape(shape).cpu().numpy()
+
+    def E(self):
+        return self.region(self.L.E, (self.L.R, self.n))
+
+    def F(self):
+        return self.region(self.L.F, (self.m, self.L.Cc))
+
+    def acs(self):
+        return self.region(self.L.acs, (self.L.R, self.k))
+
+    def bcs(self):
+        return self.region(self.L.bcs, (self.k, self.L.Cc))
+
+
+def rel_fro(x, ref):
+    den = np.linalg.norm(ref)
+    return np.linalg.norm(x - ref) / (den if den > 0 else 1.0)
+
+
+def check_product(C, A, B, ref):
+    """Elementwise |C - ref| <= 2 k u (|A||B|) and relative Frobenius <= 1e-12."""
+    k = A.shape[1]
+    bound = 2 * k * 2.0 ** -53 * (np.abs(A) @ np.abs(B)) + 1e-300
+    assert np.all(np.abs(C - ref) <= bound)
+    assert rel_fro(C, ref) <= TOL_F64
+
+
+SHAPES = [  # (m, n, k, vb_r, vb_c, p, q): several tiles and ragged tails
+    (150, 130, 77, 32, 16, 0, 0),
+    (64, 64, 64, 64, 64, 2, 2),
+    (1, 1, 1, 1, 1, 0, 0),
+    (200, 3, 300, 7, 3, 0, 0),
+    (3, 257, 129, 3, 100, 0, 0),
+    (192, 256, 40, 32, 64, 3, 4),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_encode_and_product_vs_oracle(shape):
+    m, n, k, vbr, vbc, p, q = shape
+    A = wl.operand((m, k), "normal", 1, 1)
+    B = wl.operand((k, n), "uniform", 1, 2)
+    r = Run(A, B, vbr, vbc, p, q)
+    enc = oracle.Encoded(A, B, vbr, vbc, p, q)
+    # encode: the unweighted sums run in the oracle's order (bitwise); weighted
+    # sums differ only by fused multiply-add rounding
+    acs, bcs = r.acs(), r.bcs()
+    assert np.allclose(acs, enc.acs, rtol=1e-14, atol=1e-14 * np.abs(enc.acs).max())
+    assert np.allclose(bcs, enc.bcs, rtol=1e-14, atol=1e-14 * np.abs(enc.bcs).max())
+    assert np.array_equal(acs[0::2][:r.L.nvr], enc.acs[0::2][:r.L.nvr])
+    for off, ref in ((r.L.nArow, enc.nArow), (r.L.nAblk, enc.nAblk), (r.L.nBcol, enc.nBcol),
+                     (r.L.nBblk, enc.nBblk)):
+        assert np.allclose(r.region(off, ref.shape), ref, rtol=1e-12)
+    C = r.C.cpu().numpy()
+    check_product(C, A, B, oracle.gemm(A, B))
+    check_product(r.E(), enc.acs, B, enc.E)
+    check_product(r.F(), A, enc.bcs, enc.F)
+
+
+def test_plain_gemm_equals_abft_data_block():
+    A = wl.operand((130, 90), "normal", 2, 1)
+    B = wl.operand((90, 70), "normal", 2, 2)
+    r = Run(A, B, 32, 32)
+    C2 = torch.empty_like(r.C)
+    abft.abft_gemm_plain(r.desc, r.A, r.B, C2)
+    torch.cuda.synchronize()
+    assert torch.equal(C2, r.C)
+
+
+def test_k_zero_gives_zero_product_and_no_flags():
+    A = np.zeros((40, 0))
+    B = np.zeros((0, 24))
+    r = Run(A, B, 8, 8)
+    assert torch.count_nonzero(r.C).item() == 0
+    st, rep, n = abft.abft_verify_correct(r.desc, r.C, r.ws)
+    assert st == abft.OK and n == 0
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_fault_free_no_false_positives(seed):
+    A = wl.operand((256, 192), "uniform", seed, 1)
+    B = wl.operand((192, 320), "normal", seed, 2)
+    r = Run(A, B, 64, 32, 4, 5)
+    C0 = r.C.clone()
+    st, rep, n = abft.abft_verify_correct(r.desc, r.C, r.ws)
+    assert st == abft.OK and n == 0 and torch.equal(C0, r.C)
+
+
+def verify_both(r, enc, Cf_np, erased=()):
+    """Run the GPU verify on the current C and the oracle verify on the same C."""
+    st, rep, n = abft.abft_verify_correct(r.desc, r.C, r.ws, erased=erased)
+    ost, orep, oC, on = enc.verify_correct(Cf_np, erased=erased)
+    return (st, rep, n), (ost, orep, oC, on)
+
+
+def positions(rep, kinds=(abft.KIND_CORRECTED, abft.KIND_NONFINITE_CORRECTED)):
+    return sorted((e["row"], e["col"], e["kind"]) for e in rep if e["kind"] in kinds)
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_f64_512_single_flip_parity(seed):
+    """512^3 U[-1,1], one seeded flip (uniform position and bit) in C before verify."""
+    w = wl.F64_512
+    A, B = wl.operands(w, seed)
+    r = Run(A, B, w.vb_r, w.vb_c)
+    enc = oracle.Encoded(A, B, w.vb_r, w.vb_c)
+    Cstar = oracle.gemm(A, B)
+    C_clean = r.C.cpu().numpy()
+    (i, j, b), = wl.bit_flips(seed, w.m, w.n, 1)
+    abft.abft_inject_bitflips(r.desc, r.C, [(i, j, b)])
+    Cf = r.C.cpu().numpy()
+    assert np.array_equal(Cf, wl.flip_f64(C_clean, [(i, j, b)]), equal_nan=True)
+    cls = enc.classify(i, j, Cf[i, j] - C_clean[i, j])
+    (st, rep, n), (ost, orep, oC, on) = verify_both(r, enc, Cf)
+    Cg = r.C.cpu().numpy()
+    if cls == "graded":
+        kind = abft.KIND_CORRECTED if np.isfinite(Cf[i, j]) else abft.KIND_NONFINITE_CORRECTED
+        assert st == abft.OK and positions(rep) == [(i, j, kind)] and n == 1
+        assert ost == oracle.ST_OK and positions(orep) == [(i, j, kind)]
+    elif cls == "benign":
+        assert st == abft.OK and n == 0 and on == 0
+    else:  # guard band: any outcome, but a correction must be at the right place
+        assert all((e["row"], e["col"]) == (i, j) for e in rep if e["kind"] in (1, 2))
+    if cls != "guard":
+        assert rel_fro(Cg, oC) <= TOL_F64
+        assert rel_fro(Cg, Cstar) <= TOL_F64
+
+
+@pytest.mark.parametrize("bit", [62, 61, 60, 55, 63])
+def test_f64_512_forced_graded_flips(bit):
+    """Exponent and sign flips are always graded; bit 62 on an element in [1, 2)
+    produces a NaN, located by the non-finite scan."""
+    w = wl.F64_512
+    A, B = wl.operands(w, 1000 + bit)
+    r = Run(A, B, w.vb_r, w.vb_c)
+    enc = oracle.Encoded(A, B, w.vb_r, w.vb_c)
+    C_clean = r.C.cpu().numpy()
+    cand = np.argwhere((np.abs(C_clean) >= 1) & (np.abs(C_clean) < 2))
+    i, j = (int(v) for v in cand[len(cand) // 3])
+    abft.abft_inject_bitflips(r.desc, r.C, [(i, j, bit)])
+    Cf = r.C.cpu().numpy()
+    assert enc.classify(i, j, Cf[i, j] - C_clean[i, j]) == "graded"
+    (st, rep, n), (ost, orep, oC, on) = verify_both(r, enc, Cf)
+    kind = abft.KIND_CORRECTED if np.isfinite(Cf[i, j]) else abft.KIND_NONFINITE_CORRECTED
+    if bit == 62:
+        assert kind == abft.KIND_NONFINITE_CORRECTED
+    assert st == abft.OK and positions(rep) == [(i, j, kind)] == positions(orep)
+    assert rel_fro(r.C.cpu().numpy(), oracle.gemm(A, B)) <= TOL_F64
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_grid_erasure_and_flips_parity(seed):
+    """Scaled-down grid workload: 6x6 blocks of 64, one block erased to NaN and three
+    graded flips in distinct other blocks; verify (skipping the erased block) then
+    rebuild the block from the block checksum."""
+    m = n = k = 384
+    A = wl.operand((m, k), "normal", seed, 1)
+    B = wl.operand((k, n), "normal", seed, 2)
+    r = Run(A, B, 64, 64, 6, 6)
+    enc = oracle.Encoded(A, B, 64, 64, 6, 6)
+    Cstar = oracle.gemm(A, B)
+    (bi, bj), = wl.erased_blocks(seed, 6, 6, 1)
+    flips = [(i, j, 62 - (t % 3)) for t, (i, j, _) in enumerate(
+        wl.bit_flips(seed, m, n, 3, distinct_blocks=(64, 64), avoid_blocks=[(bi, bj)]))]
+    C_clean = r.C.cpu().numpy()
+    abft.abft_inject_bitflips(r.desc, r.C, flips)
+    abft.abft_erase_block(r.desc, r.C, bi, bj)
+    Cf = r.C.cpu().numpy()
+    assert np.isnan(Cf[64 * bi:64 * bi + 64, 64 * bj:64 * bj + 64]).all()
+    for i, j, _ in flips:
+        assert enc.classify(i, j, Cf[i, j] - C_clean[i, j]) == "graded"
+    (st, rep, n_), (ost, orep, oC, on) = verify_both(r, enc, Cf, erased=[(bi, bj)])
+    assert st == abft.OK and ost == oracle.ST_OK
+    assert [(a, b) for a, b, _ in positions(rep)] == sorted((i, j) for i, j, _ in flips)
+    assert positions(rep) == positions(orep)
+    st, ent = abft.abft_recover_block(r.desc, r.C, r.ws, bi, bj)
+    ost, oCr, onfl = enc.recover_block(oC, bi, bj)
+    assert st == abft.OK and ost == oracle.ST_OK and onfl == 0
+    assert ent["kind"] == abft.KIND_BLOCK_RECOVERED and (ent["row"], ent["col"]) == (64 * bi, 64 * bj)
+    Cg = r.C.cpu().numpy()
+    blk = np.s_[64 * bi:64 * bi + 64, 64 * bj:64 * bj + 64]
+    assert rel_fro(Cg[blk], Cstar[blk]) <= TOL_F64
+    assert rel_fro(Cg[blk], oCr[blk]) <= TOL_F64
+    assert rel_fro(Cg, Cstar) <= TOL_F64
+
+
+def test_errors_sharing_lines_are_uncorrectable_like_oracle():
+    A = wl.operand((64, 48), "int", 3, 1)
+    B = wl.operand((48, 64), "int", 3, 2)
+    r = Run(A, B, 64, 64)
+    enc = oracle.Encoded(A, B, 64, 64)
+    abft.abft_inject_bitflips(r.desc, r.C, [(1, 1, 62), (1, 5, 61), (4, 1, 60)])
+    Cf = r.C.cpu().numpy()
+    (st, rep, n), (ost, orep, oC, on) = verify_both(r, enc, Cf)
+    assert st == abft.ERR_UNCORRECTABLE and ost == oracle.ST_UNCORRECTABLE
+    key = lambda rr: sorted((e["row"], e["col"], e["kind"]) for e in rr)
+    assert key(rep) == key(orep)
+
+
+def test_two_errors_in_one_column_line_integer_exact():
+    """Two errors share a column line; each is alone in its row line, so both are
+    corrected from their row lines and the exact integer product comes back."""
+    A = wl.operand((64, 40), "int", 4, 1)
+    B = wl.operand((40, 64), "int", 4, 2)
+    r = Run(A, B, 64, 16)
+    enc = oracle.Encoded(A, B, 64, 16)
+    C_clean = r.C.clone()
+    abft.abft_inject_bitflips(r.desc, r.C, [(3, 7, 61), (50, 7, 58)])
+    Cf = r.C.cpu().numpy()
+    (st, rep, n), (ost, orep, oC, on) = verify_both(r, enc, Cf)
+    assert st == abft.OK and ost == oracle.ST_OK
+    key = lambda rr: [(e["row"], e["col"], e["kind"], e["side"]) for e in rr]
+    assert key(rep) == key(orep) and [(e[0], e[1]) for e in key(rep)] == [(3, 7), (50, 7)]
+    assert torch.equal(r.C, C_clean)
+
+
+def test_unlisted_erasure_is_reported_uncorrectable():
+    A = wl.operand((128, 64), "normal", 5, 1)
+    B = wl.operand((64, 128), "normal", 5, 2)
+    r = Run(A, B, 32, 32, 4, 4)
+    abft.abft_erase_block(r.desc, r.C, 1, 2)
+    st, rep, n = abft.abft_verify_correct(r.desc, r.C, r.ws, max_reports=4)
+    assert st == abft.ERR_UNCORRECTABLE and n > 4 and len(rep) == 4
+
+
+def test_f64_11264_grid22_full_size():
+    """The benchmark workload at full size (11264^3, 22x22 grid of 512, one erased
+    block, three flips in distinct blocks), in the benchmark's launch configuration.
+    The oracle checks sampled outputs; the section 4.3 residual check covers all of C."""
+    w = wl.F64_11264_GRID22
+    seed = 0
+    A, B = wl.operands(w, seed)
+    r = Run(A, B, w.vb_r, w.vb_c, w.p, w.q)
+    enc = oracle.Encoded(A, B, w.vb_r, w.vb_c, w.p, w.q, products=False)
+    g = wl.rng(seed, 99)
+    rows = np.sort(g.choice(w.m, 48, replace=False))
+    cols = np.sort(g.choice(w.n, 48, replace=False))
+    Cs = r.C[rows][:, cols].cpu().numpy()
+    check_product(Cs, A[rows], B[:, cols], oracle.gemm(A[rows], B[:, cols]))
+    Es = r.E()[:, cols]
+    check_product(Es, enc.acs, B[:, cols], oracle.gemm(enc.acs, B[:, cols]))
+    Fs = r.F()[rows]
+    check_product(Fs, A[rows], enc.bcs, oracle.gemm(A[rows], enc.bcs))
+    x = wl.operand((w.n,), "uniform", seed, 5)
+    C_clean = r.C.cpu().numpy()
+    assert oracle.residual_check(A, B, C_clean, x) < 1.0
+
+    (bi, bj), = wl.erased_blocks(seed, w.p, w.q, 1)
+    flips = wl.bit_flips(seed, w.m, w.n, 3, distinct_blocks=(512, 512), avoid_blocks=[(bi, bj)])
+    flips = [(i, j, 62 - t) for t, (i, j, _) in enumerate(flips)]
+    abft.abft_inject_bitflips(r.desc, r.C, flips)
+    abft.abft_erase_block(r.desc, r.C, bi, bj)
+    st, rep, n = abft.abft_verify_correct(r.desc, r.C, r.ws, erased=[(bi, bj)])
+    assert st == abft.OK
+    assert [(a, b) for a, b, _ in positions(rep)] == sorted((i, j) for i, j, _ in flips)
+    st, ent = abft.abft_recover_block(r.desc, r.C, r.ws, bi, bj)
+    assert st == abft.OK
+    Cg = r.C.cpu().numpy()
+    blk = np.s_[512 * bi:512 * bi + 512, 512 * bj:512 * bj + 512]
+    ref_blk = oracle.gemm(A[512 * bi:512 * bi + 512], B[:, 512 * bj:512 * bj + 512])
+    assert rel_fro(Cg[blk], ref_blk) <= TOL_F64
+    for i, j, _ in flips:
+        assert abs(Cg[i, j] - C_clean[i, j]) <= 1e-12 * np.abs(C_clean[i]).max()
+    assert oracle.residual_check(A, B, Cg, x) < 1.0

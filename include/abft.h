@@ -117,6 +117,26 @@ abft_status abft_workspace_layout(const abft_desc* desc, abft_ws_layout* out);
 abft_status abft_encode(const abft_desc* desc, const void* A, const void* B, const void* a_scale,
                         const void* b_scale, void* ws, void* stream);
 
+/* abft_encode for callers that cannot allocate device memory.  The paper has
+ * no counterpart: this is an interface convenience of this library.  Some
+ * callers cannot call cudaMalloc -- code that runs while a CUDA graph is being
+ * captured, real-time or signal-context threads that must not take the
+ * allocator's lock, or plugins that only receive buffers from their host
+ * application.  Such a caller may not be able to size a workspace with its
+ * scratch part.  This entry point writes the same outputs as abft_encode into
+ * ws, but ws only needs the bytes below abft_ws_layout.scratch: the encode's
+ * partial sums go to an 8 MiB array of static device memory inside the
+ * library, which each device that loads the library keeps until the process
+ * exits.  It allocates nothing.  Problems whose partial sums need more than
+ * 8 MiB (about 8 * (k/256 * (n + 4*nvr) + k/64 * 4*nvc) bytes) return
+ * ABFT_ERR_INVALID with nothing launched.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the one array, so
+ * calls that overlap on the GPU (different streams, threads) race and must be
+ * serialised by the caller.  ABFT_F64 only.  Asynchronous. */
+abft_status abft_encode_noalloc(const abft_desc* desc, const void* A, const void* B,
+                                const void* a_scale, const void* b_scale, void* ws, void* stream);
+
 /* The ABFT product (Eq. (1)): [A; C_C^T A] [B, B C_R] on the GPU.  Writes the
  * data block A B into C and the checksum blocks into ws (E and F).  Requires a
  * preceding abft_encode on the same ws and operands.  Asynchronous. */

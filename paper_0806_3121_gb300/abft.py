@@ -21,7 +21,8 @@ OK, ERR_INVALID, ERR_CUDA, ERR_UNSUPPORTED, ERR_UNCORRECTABLE, ERR_TIMEOUT = ran
 KIND_CORRECTED, KIND_NONFINITE_CORRECTED, KIND_UNCORRECTABLE, KIND_BLOCK_RECOVERED = 1, 2, 3, 4
 
 # Every symbol include/abft.h declares.
-EXPORTS = ("abft_workspace_bytes", "abft_workspace_layout", "abft_encode", "abft_gemm",
+EXPORTS = ("abft_workspace_bytes", "abft_workspace_layout", "abft_encode",
+           "abft_encode_noalloc", "abft_gemm",
            "abft_gemm_plain", "abft_verify_correct", "abft_recover_block",
            "abft_inject_bitflips", "abft_erase_block", "abft_kernel_launches",
            "abft_last_error", "abft_version")
@@ -79,6 +80,7 @@ def load(path: str = LIB_PATH):
         lib.abft_workspace_bytes.argtypes = [D]
         lib.abft_workspace_layout.argtypes = [D, ct.POINTER(WsLayout)]
         lib.abft_encode.argtypes = [D, vp, vp, vp, vp, vp, vp]
+        lib.abft_encode_noalloc.argtypes = [D, vp, vp, vp, vp, vp, vp]
         lib.abft_gemm.argtypes = [D, vp, vp, vp, vp, vp, vp, vp]
         lib.abft_gemm_plain.argtypes = [D, vp, vp, vp, vp, vp, vp]
         lib.abft_verify_correct.argtypes = [D, vp, vp, i32, vp, i32, vp, i32,
@@ -145,6 +147,13 @@ def abft_workspace_layout(desc: Desc) -> WsLayout:
 def abft_encode(desc, A, B, ws, a_scale=None, b_scale=None, stream=None):
     _check(load().abft_encode(ct.byref(desc), _ptr(A), _ptr(B), _ptr(a_scale), _ptr(b_scale),
                               _ptr(ws), _stream(stream)))
+
+
+def abft_encode_noalloc(desc, A, B, ws, a_scale=None, b_scale=None, stream=None):
+    """abft_encode without workspace scratch (see include/abft.h); ws needs only the
+    bytes below the layout's scratch offset."""
+    _check(load().abft_encode_noalloc(ct.byref(desc), _ptr(A), _ptr(B), _ptr(a_scale),
+                                      _ptr(b_scale), _ptr(ws), _stream(stream)))
 
 
 def abft_gemm(desc, A, B, C, ws, a_scale=None, b_scale=None, stream=None):

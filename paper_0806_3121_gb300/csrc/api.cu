@@ -210,6 +210,29 @@ abft_status abft_encode(const abft_desc* desc, const void* A, const void* B, con
   return e == cudaSuccess ? ABFT_OK : cuda_fail(e, "abft_encode");
 }
 
+abft_status abft_encode_noalloc(const abft_desc* desc, const void* A, const void* B,
+                                const void* a_scale, const void* b_scale, void* ws, void* stream) {
+  (void)a_scale;
+  (void)b_scale;
+  Plan P;
+  abft_status st = make_plan(desc, &P);
+  if (st != ABFT_OK) return st;
+  if (P.d.dtype != ABFT_F64)
+    return fail(ABFT_ERR_UNSUPPORTED, "abft_encode_noalloc supports ABFT_F64 only");
+  const size_t need = sizeof(double) * part_elems(P);
+  if (need > static_encode_part_bytes())
+    return fail(ABFT_ERR_INVALID,
+                "abft_encode_noalloc: this problem needs %zu bytes of encode scratch, above the "
+                "static maximum of %zu bytes; use abft_encode with a full workspace",
+                need, static_encode_part_bytes());
+  if (is_empty(P)) return ABFT_OK;
+  if (!ws || (P.d.k > 0 && (!A || !B))) return fail(ABFT_ERR_INVALID, "NULL pointer");
+  const cudaError_t e = launch_encode_f64_noalloc(P, static_cast<const double*>(A),
+                                                  static_cast<const double*>(B), ws,
+                                                  static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? ABFT_OK : cuda_fail(e, "abft_encode_noalloc");
+}
+
 static abft_status gemm_common(const abft_desc* desc, const void* A, const void* B, void* C,
                                void* ws, bool checksums, void* stream) {
   Plan P;

@@ -76,6 +76,10 @@ void count_launches(int64_t n);
 // Launchers (return cudaGetLastError() of the launches).
 cudaError_t launch_encode_f64(const Plan& P, const double* A, const double* B, void* ws,
                               cudaStream_t st);
+// Encode with its partial sums in a static device array (no workspace scratch).
+cudaError_t launch_encode_f64_noalloc(const Plan& P, const double* A, const double* B, void* ws,
+                                      cudaStream_t st);
+size_t static_encode_part_bytes();
 cudaError_t launch_gemm_f64(const Plan& P, const double* A, const double* B, double* C, void* ws,
                             bool checksums, cudaStream_t st);
 cudaError_t launch_verify(const Plan& P, void* C, void* ws, const Erased& er, cudaStream_t st);

@@ -88,10 +88,14 @@ typedef struct {
 /* Byte offsets of the regions inside the workspace (all 256-byte aligned) and
  * their shapes, for callers that want to read the checksums.  R = 2*nvr + bs
  * checksum rows (nvr = ceil(m/vb_rows), bs = m/grid_p or 0), Cc = 2*nvc
- * checksum columns (nvc = ceil(n/vb_cols)).  acs/bcs hold the encoded operand
- * rows/columns in the product's operand format; E (R-by-n binary64) holds the
- * product rows of acs (expected column checksums, then S); F (m-by-Cc
- * binary64) the product columns of bcs (expected row checksums). */
+ * checksum columns (nvc = ceil(n/vb_cols)).  acs (acs_rows x acs_ld) and bcs
+ * (k x bcs_ld, row-major) hold the encoded operand rows/columns in the
+ * product's operand format: binary64 for ABFT_F64 (acs_rows = R, bcs_cols =
+ * Cc); for the tensor-core dtypes every fp32 checksum is a bf16 hi + lo pair
+ * (acs_rows = 4*nvr + 2*bs, bcs_cols = 4*nvc) whose products land in E16 / F16
+ * (fp32) and are summed in binary64.  E (R-by-n binary64) holds the expected
+ * column checksums of each verify block (unweighted, weighted), then the
+ * block checksum rows S; F (m-by-Cc binary64) the expected row checksums. */
 typedef struct {
   size_t total;
   size_t acs, bcs, E, F;
@@ -99,6 +103,13 @@ typedef struct {
   size_t scratch, scratch_bytes;     /* verify lists, counters, report buffer */
   int64_t R, Cc, nvr, nvc, bs;
   int64_t acs_ld, bcs_ld;            /* leading dims of acs / bcs in elements  */
+  size_t E16, F16;                   /* fp32 product rows/columns of the bf16
+                                        checksum pieces (tensor-core dtypes)  */
+  int64_t acs_rows, bcs_cols;        /* rows of acs, columns of bcs            */
+  size_t obs_col, obs_row;           /* fused observed partial sums (fp32)     */
+  size_t inject;                     /* armed epilogue fault injections        */
+  int32_t fused;                     /* 1: abft_gemm writes observed sums      */
+  int32_t pad0;
 } abft_ws_layout;
 
 /* Size of the caller-owned device workspace for `desc`.  Returns 0 for an
@@ -143,6 +154,18 @@ abft_status abft_encode_noalloc(const abft_desc* desc, const void* A, const void
 abft_status abft_gemm(const abft_desc* desc, const void* A, const void* B, const void* a_scale,
                       const void* b_scale, void* C, void* ws, void* stream);
 
+/* Fault injection into the accumulator outputs of the tensor-core product
+ * (compute faults, as opposed to abft_inject_bitflips on the stored C): arms
+ * up to 256 flips (host arrays rows, cols, bits; bit 0..31 of the fp32
+ * element) that every following abft_gemm on this ws applies inside its
+ * epilogue, before C is stored and before the fused observed checksums are
+ * formed.  count = 0 disarms.  ABFT_ERR_UNSUPPORTED for ABFT_F64.  The paper
+ * injects process failures in its stress test (section 4.3); this is the
+ * bit-flip analogue.  Asynchronous. */
+abft_status abft_set_epilogue_faults(const abft_desc* desc, void* ws, const int64_t* rows,
+                                     const int64_t* cols, const int32_t* bits, int32_t count,
+                                     void* stream);
+
 /* The same GEMM kernel with no checksum tiles: C = A B only.  This is the
  * checksum-free baseline the ABFT overhead is measured against.  ws unused
  * (may be NULL).  Asynchronous. */
@@ -158,8 +181,11 @@ abft_status abft_gemm_plain(const abft_desc* desc, const void* A, const void* B,
  * unweighted residual; each candidate is recomputed in binary64 from a line in
  * which it is the only candidate, then both its lines are checked again.
  * C is corrected in place.  reread_C: 1 re-reads all of C from memory (catches
- * faults that hit C after the product); 0 is accepted and behaves the same in
- * this build.  The report (host, max_reports entries) receives up to
+ * faults that hit C after the product); 0 uses the observed column and row sums
+ * that the tensor-core product formed in its epilogue (layout.fused = 1: bf16
+ * with vb_rows a multiple of 128 and vb_cols a multiple of 32 that divides or
+ * is a multiple of 256), reading C only for the lines it has to locate or
+ * correct; without fused sums (ABFT_F64, other block sizes) 0 re-reads C too.  The report (host, max_reports entries) receives up to
  * max_reports entries sorted by (row, col, kind); *n_reports (host) gets the
  * full count.  SYNCHRONISES `stream`.  Returns ABFT_OK, or
  * ABFT_ERR_UNCORRECTABLE when a flagged line could not be fixed (those

@@ -159,22 +159,21 @@ def norms_B(B, vb: int):
     return ncol, nblk
 
 
-def units(dtype: str, fused: bool = False) -> dict:
+def units(dtype: str) -> dict:
     """Rounding units entering the detection threshold for each product dtype.
 
     f64: everything in binary64.  bf16 / fp8 / bf16x3: the product accumulates in
     binary32 and C is stored in binary32 (no extra storage rounding); the checksum
     operand is fed to the tensor cores as a bf16 hi+lo pair (relative error 2^-17);
-    encode sums run in binary32; the observed block sums run in binary32 when they are
-    fused into the GEMM epilogue, else in binary64.
+    encode sums and the observed block sums of C run in binary32.
     """
     if dtype == "f64":
         return dict(u_acc=U64, u_sum=U64, u_enc=U64, u_c=U64, u_cs=U64)
-    return dict(u_acc=U32, u_sum=U32 if fused else U64, u_enc=U32, u_c=0.0, u_cs=2.0 ** -17)
+    return dict(u_acc=U32, u_sum=U32, u_enc=U32, u_c=0.0, u_cs=2.0 ** -17)
 
 
-def make_cfg(m, n, k, vb_r, vb_c, p=0, q=0, dtype="f64", s=4.0, fused=False) -> OracleCfg:
-    u = units(dtype, fused)
+def make_cfg(m, n, k, vb_r, vb_c, p=0, q=0, dtype="f64", s=4.0) -> OracleCfg:
+    u = units(dtype)
     return OracleCfg(m=m, n=n, k=k, vb_r=vb_r, vb_c=vb_c, p=p, q=q, s=s,
                      round_f32=0 if dtype == "f64" else 1, pad=0, **u)
 
@@ -182,13 +181,12 @@ def make_cfg(m, n, k, vb_r, vb_c, p=0, q=0, dtype="f64", s=4.0, fused=False) -> 
 class Encoded:
     """Everything the oracle derives from A and B before C is checked."""
 
-    def __init__(self, A, B, vb_r, vb_c, p=0, q=0, dtype="f64", s=4.0, fused=False,
-                 products=True):
+    def __init__(self, A, B, vb_r, vb_c, p=0, q=0, dtype="f64", s=4.0, products=True):
         A, B = _f64(A), _f64(B)
         self.A, self.B = A, B
         self.m, self.k = A.shape
         self.n = B.shape[1]
-        self.cfg = make_cfg(self.m, self.n, self.k, vb_r, vb_c, p, q, dtype, s, fused)
+        self.cfg = make_cfg(self.m, self.n, self.k, vb_r, vb_c, p, q, dtype, s)
         self.acs = encode_A(A, vb_r, p)
         self.bcs = encode_B(B, vb_c)
         self.nArow, self.nAblk = norms_A(A, vb_r)

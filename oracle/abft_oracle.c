@@ -144,10 +144,10 @@ void oracle_encode_B(int64_t k, int64_t n, const double* B, int64_t ldb, int64_t
 /* ------------------------------------------------------------------------ */
 /* Norms feeding the detection thresholds (the paper only says rounding in
  * floating-point checksums is of the order of the method's own rounding,
- * section 2.1; the bound below is this library's reading of it).
+ * section 2.1; the bound built from them is this library's reading of it).
  *   nrow[i]         = ||A_{i,:}||_2
- *   nblk[4I+0]      = || e^T |A_I| ||_2
- *   nblk[4I+1]      = || w^T |A_I| ||_2
+ *   nblk[4I+0]      = sqrt( sum_{i in I} ||A_{i,:}||^2 )        (= ||A_I||_F)
+ *   nblk[4I+1]      = sqrt( sum_{i in I} w_{i-I0}^2 ||A_{i,:}||^2 )
  *   nblk[4I+2]      = || e^T A_I ||_2      (the stored checksum row)
  *   nblk[4I+3]      = || w^T A_I ||_2
  * Pinned by numpy norms of explicitly formed vectors. */
@@ -161,30 +161,32 @@ void oracle_norms_A(int64_t m, int64_t k, const double* A, int64_t lda, int64_t 
   int64_t nvb = ceil_div(m, vb);
   for (int64_t I = 0; I < nvb; ++I) {
     int64_t i0 = I * vb, i1 = (i0 + vb < m) ? i0 + vb : m;
-    double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
+    double f0 = 0.0, f1 = 0.0, q2 = 0.0, q3 = 0.0;
+    for (int64_t i = i0; i < i1; ++i) {
+      double w = oracle_weight(i - i0, vb);
+      f0 += nrow[i] * nrow[i];
+      f1 += (w * nrow[i]) * (w * nrow[i]);
+    }
     for (int64_t l = 0; l < k; ++l) {
-      double ae = 0.0, aw = 0.0, se = 0.0, sw = 0.0;
+      double se = 0.0, sw = 0.0;
       for (int64_t i = i0; i < i1; ++i) {
-        double a = A[i * lda + l], w = oracle_weight(i - i0, vb);
-        ae += fabs(a);
-        aw += w * fabs(a);
+        double a = A[i * lda + l];
         se += a;
-        sw += w * a;
+        sw += oracle_weight(i - i0, vb) * a;
       }
-      q0 += ae * ae;
-      q1 += aw * aw;
       q2 += se * se;
       q3 += sw * sw;
     }
-    nblk[4 * I + 0] = sqrt(q0);
-    nblk[4 * I + 1] = sqrt(q1);
+    nblk[4 * I + 0] = sqrt(f0);
+    nblk[4 * I + 1] = sqrt(f1);
     nblk[4 * I + 2] = sqrt(q2);
     nblk[4 * I + 3] = sqrt(q3);
   }
 }
 
-/* Column analog for B: ncol[j] = ||B_{:,j}||_2 and per column block J the
- * norms of |B_J| e, |B_J| w, B_J e, B_J w (vectors of length k). */
+/* Column analog for B: ncol[j] = ||B_{:,j}||_2; per column block J
+ * sqrt(sum_{j in J} ||B_{:,j}||^2), sqrt(sum w^2 ||B_{:,j}||^2), and the norms
+ * of the stored checksum columns B_J e, B_J w (vectors of length k). */
 void oracle_norms_B(int64_t k, int64_t n, const double* B, int64_t ldb, int64_t vb, double* ncol,
                     double* nblk) {
   for (int64_t j = 0; j < n; ++j) {
@@ -195,23 +197,24 @@ void oracle_norms_B(int64_t k, int64_t n, const double* B, int64_t ldb, int64_t 
   int64_t nvb = ceil_div(n, vb);
   for (int64_t J = 0; J < nvb; ++J) {
     int64_t j0 = J * vb, j1 = (j0 + vb < n) ? j0 + vb : n;
-    double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
+    double f0 = 0.0, f1 = 0.0, q2 = 0.0, q3 = 0.0;
+    for (int64_t j = j0; j < j1; ++j) {
+      double w = oracle_weight(j - j0, vb);
+      f0 += ncol[j] * ncol[j];
+      f1 += (w * ncol[j]) * (w * ncol[j]);
+    }
     for (int64_t l = 0; l < k; ++l) {
-      double be = 0.0, bw = 0.0, se = 0.0, sw = 0.0;
+      double se = 0.0, sw = 0.0;
       for (int64_t j = j0; j < j1; ++j) {
-        double b = B[l * ldb + j], w = oracle_weight(j - j0, vb);
-        be += fabs(b);
-        bw += w * fabs(b);
+        double b = B[l * ldb + j];
         se += b;
-        sw += w * b;
+        sw += oracle_weight(j - j0, vb) * b;
       }
-      q0 += be * be;
-      q1 += bw * bw;
       q2 += se * se;
       q3 += sw * sw;
     }
-    nblk[4 * J + 0] = sqrt(q0);
-    nblk[4 * J + 1] = sqrt(q1);
+    nblk[4 * J + 0] = sqrt(f0);
+    nblk[4 * J + 1] = sqrt(f1);
     nblk[4 * J + 2] = sqrt(q2);
     nblk[4 * J + 3] = sqrt(q3);
   }
@@ -238,17 +241,21 @@ typedef struct {
   double delta, r_e, r_w;
 } oracle_fault;
 
-/* Thresholds: a bound on |residual| for fault-free data (probabilistic
- * rounding-error model, sqrt of the sum length times the unit roundoff,
- * with Cauchy-Schwarz on the magnitude sums).  For the column check of
- * verify block I and column j:
- *   tau_e = s * ||B_j|| * (f1 * ||e^T|A_I||| + f2 * ||e^T A_I||)
- *   tau_w = s * ||B_j|| * (f1 * ||w^T|A_I||| + f2 * ||w^T A_I||)
+/* Thresholds: a bound on |residual| for fault-free data under a
+ * probabilistic rounding model -- a sum of n rounded terms errs by about
+ * sqrt(n) u times the magnitude of its terms, and the independent errors of
+ * the elements of a verify block add in quadrature -- with Cauchy-Schwarz
+ * for the magnitudes.  For the column check of verify block I and column j:
+ *   tau_e = s * ||B_j|| * (f1 * ||A_I||_F + f2 * ||e^T A_I||)
+ *   tau_w = s * ||B_j|| * (f1 * ||diag(w) A_I||_F + f2 * ||w^T A_I||)
  *   f1 = sqrt(k) u_acc + sqrt(vb) (u_sum + u_enc) + u_c
  *   f2 = sqrt(k) u_acc + u_cs
- * The row check is the transposed formula.  Parity unpinned as a formula
- * (it is a reading); pinned as a property: fault-free residuals stay below
- * it over many seeds, and exact integer data leave residual 0. */
+ * (f1: accumulation of the block's elements, their block sum, the checksum
+ * encoding and C's storage; f2: the checksum row's own product and its
+ * representation).  The row check is the transposed formula.  Parity
+ * unpinned as a formula (it is a reading); pinned as a property: fault-free
+ * residuals stay far below it over many seeds, exact integer data leave
+ * residual 0. */
 static void taus(const oracle_cfg* c, int64_t vb, double nvec, const double* nb4, double* te,
                  double* tw) {
   double f1 = sqrt((double)c->k) * c->u_acc + sqrt((double)vb) * (c->u_sum + c->u_enc) + c->u_c;

@@ -22,7 +22,7 @@ KIND_CORRECTED, KIND_NONFINITE_CORRECTED, KIND_UNCORRECTABLE, KIND_BLOCK_RECOVER
 
 # Every symbol include/abft.h declares.
 EXPORTS = ("abft_workspace_bytes", "abft_workspace_layout", "abft_encode",
-           "abft_encode_noalloc", "abft_gemm",
+           "abft_encode_noalloc", "abft_gemm", "abft_set_epilogue_faults",
            "abft_gemm_plain", "abft_verify_correct", "abft_recover_block",
            "abft_inject_bitflips", "abft_erase_block", "abft_kernel_launches",
            "abft_last_error", "abft_version")
@@ -58,7 +58,10 @@ class WsLayout(ct.Structure):
                 ("nAblk", ct.c_size_t), ("nBcol", ct.c_size_t), ("nBblk", ct.c_size_t),
                 ("scratch", ct.c_size_t), ("scratch_bytes", ct.c_size_t),
                 ("R", ct.c_int64), ("Cc", ct.c_int64), ("nvr", ct.c_int64), ("nvc", ct.c_int64),
-                ("bs", ct.c_int64), ("acs_ld", ct.c_int64), ("bcs_ld", ct.c_int64)]
+                ("bs", ct.c_int64), ("acs_ld", ct.c_int64), ("bcs_ld", ct.c_int64),
+                ("E16", ct.c_size_t), ("F16", ct.c_size_t), ("acs_rows", ct.c_int64),
+                ("bcs_cols", ct.c_int64), ("obs_col", ct.c_size_t), ("obs_row", ct.c_size_t),
+                ("inject", ct.c_size_t), ("fused", ct.c_int32), ("pad0", ct.c_int32)]
 
 
 _lock = threading.Lock()
@@ -83,6 +86,7 @@ def load(path: str = LIB_PATH):
         lib.abft_encode_noalloc.argtypes = [D, vp, vp, vp, vp, vp, vp]
         lib.abft_gemm.argtypes = [D, vp, vp, vp, vp, vp, vp, vp]
         lib.abft_gemm_plain.argtypes = [D, vp, vp, vp, vp, vp, vp]
+        lib.abft_set_epilogue_faults.argtypes = [D, vp, vp, vp, vp, i32, vp]
         lib.abft_verify_correct.argtypes = [D, vp, vp, i32, vp, i32, vp, i32,
                                             ct.POINTER(ct.c_int32), vp]
         lib.abft_recover_block.argtypes = [D, vp, vp, i32, i32, ct.POINTER(Fault), vp]
@@ -196,6 +200,17 @@ def abft_inject_bitflips(desc, C, flips, stream=None):
     _check(load().abft_inject_bitflips(ct.byref(desc), _ptr(C), ct.cast(rows, ct.c_void_p),
                                        ct.cast(cols, ct.c_void_p), ct.cast(bits, ct.c_void_p), n,
                                        _stream(stream)))
+
+
+def abft_set_epilogue_faults(desc, ws, flips, stream=None):
+    """Arm bit flips (row, col, bit) of the product's accumulator outputs; [] disarms."""
+    n = len(flips)
+    rows = (ct.c_int64 * max(1, n))(*[f[0] for f in flips])
+    cols = (ct.c_int64 * max(1, n))(*[f[1] for f in flips])
+    bits = (ct.c_int32 * max(1, n))(*[f[2] for f in flips])
+    _check(load().abft_set_epilogue_faults(ct.byref(desc), _ptr(ws), ct.cast(rows, ct.c_void_p),
+                                           ct.cast(cols, ct.c_void_p), ct.cast(bits, ct.c_void_p),
+                                           n, _stream(stream)))
 
 
 def abft_erase_block(desc, C, bi, bj, stream=None):

@@ -48,7 +48,7 @@ struct Units {
 Units units_for(int dtype) {
   const double u64 = ldexp(1.0, -53), u32 = ldexp(1.0, -24);
   if (dtype == ABFT_F64) return {u64, u64, u64, u64, u64};
-  return {u32, u64, u32, 0.0, ldexp(1.0, -17)};
+  return {u32, u32, u32, 0.0, ldexp(1.0, -17)};
 }
 
 size_t operand_bytes(int dtype) { return dtype == ABFT_F64 ? 8 : 2; }
@@ -74,7 +74,10 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
   if (d->flags != 0) return fail(ABFT_ERR_INVALID, "flags must be 0");
   if (!(d->tau_safety >= 0.0) || !isfinite(d->tau_safety))
     return fail(ABFT_ERR_INVALID, "tau_safety must be finite and >= 0");
-  if (d->dtype != ABFT_F64) return fail(ABFT_ERR_UNSUPPORTED, "dtype %d not built yet", d->dtype);
+  if (d->dtype != ABFT_F64 && d->dtype != ABFT_BF16)
+    return fail(ABFT_ERR_UNSUPPORTED, "dtype %d not built yet", d->dtype);
+  if (d->dtype == ABFT_BF16 && (d->lda % 8 || d->ldb % 8))
+    return fail(ABFT_ERR_INVALID, "bf16 operands need lda and ldb multiples of 8 (16-byte rows)");
 
   Plan& p = *P;
   memset(&p, 0, sizeof p);
@@ -93,6 +96,12 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
   p.f1_col = sk * u.u_acc + sqrt((double)d->vb_rows) * (u.u_sum + u.u_enc) + u.u_c;
   p.f1_row = sk * u.u_acc + sqrt((double)d->vb_cols) * (u.u_sum + u.u_enc) + u.u_c;
   p.f2_col = p.f2_row = sk * u.u_acc + u.u_cs;
+  const bool lp0 = d->dtype != ABFT_F64;
+  p.fused = lp0 && d->vb_rows % 128 == 0 && d->vb_cols % 32 == 0 &&
+            (256 % d->vb_cols == 0 || d->vb_cols % 256 == 0);
+  p.g = d->vb_cols < 256 ? d->vb_cols : 256;
+  p.ngrp = d->n > 0 ? cdiv(d->n, p.g) : 0;
+  p.ntr_obs = d->m > 0 ? cdiv(d->m, 128) : 0;
 
   // Row tiles of the product grid (64 rows each, data then checksum rows).
   if (cdiv(d->m, 64) + cdiv(p.R, 64) > 65535)
@@ -100,20 +109,34 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
 
   abft_ws_layout& L = p.L;
   const size_t eb = operand_bytes(d->dtype);
+  const bool lp = d->dtype != ABFT_F64;
+  // Encoded operand rows/columns: binary64 checksums for F64; for the
+  // tensor-core dtypes each fp32 checksum is a bf16 hi+lo pair (4 rows per
+  // verify block, 2 per block-checksum row), with 16-byte aligned rows.
+  L.acs_rows = lp ? 4 * p.nvr + 2 * p.bs : p.R;
+  L.bcs_cols = lp ? 4 * p.nvc : p.Cc;
+  L.acs_ld = lp ? (d->k + 7) / 8 * 8 : d->k;
+  L.bcs_ld = lp ? (L.bcs_cols + 7) / 8 * 8 : p.Cc;
   size_t off = 0;
   auto region = [&](size_t bytes) {
     const size_t o = off;
     off = align256(off + bytes);
     return o;
   };
-  L.acs = region((size_t)p.R * d->k * eb);
-  L.bcs = region((size_t)d->k * p.Cc * eb);
+  L.acs = region((size_t)L.acs_rows * L.acs_ld * eb);
+  L.bcs = region((size_t)d->k * L.bcs_ld * eb);
   L.E = region((size_t)p.R * d->n * 8);
   L.F = region((size_t)d->m * p.Cc * 8);
   L.nArow = region((size_t)d->m * 8);
   L.nAblk = region((size_t)4 * p.nvr * 8);
   L.nBcol = region((size_t)d->n * 8);
   L.nBblk = region((size_t)4 * p.nvc * 8);
+  L.E16 = region(lp ? (size_t)L.acs_rows * d->n * 4 : 0);
+  L.F16 = region(lp ? (size_t)d->m * L.bcs_cols * 4 : 0);
+  L.obs_col = region(p.fused ? (size_t)p.ntr_obs * 2 * d->n * 4 : 0);
+  L.obs_row = region(p.fused ? (size_t)d->m * p.ngrp * 2 * 4 : 0);
+  L.inject = region(lp ? 16 + sizeof(InjectEntry) * kMaxInject : 0);
+  L.fused = p.fused;
   L.scratch = off;
   L.scratch_bytes = scratch_bytes(p);
   off = align256(off + L.scratch_bytes);
@@ -123,16 +146,15 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
   L.nvr = p.nvr;
   L.nvc = p.nvc;
   L.bs = p.bs;
-  L.acs_ld = d->k;
-  L.bcs_ld = p.Cc;
   return ABFT_OK;
 }
 
 bool is_empty(const Plan& P) { return P.d.m == 0 || P.d.n == 0; }
 
-// Partial-reduction sizes used by the encode kernels.
+// Partial-reduction sizes used by the encode kernels (in doubles).
 size_t part_elems(const Plan& P) {
   const int64_t k = std::max<int64_t>(P.d.k, 1);
+  if (P.d.dtype != ABFT_F64) return (lp_part_bytes(P) + 7) / 8;
   return (size_t)(4 * P.nvr * cdiv(k, 256) + 4 * P.nvc * cdiv(k, 64) + cdiv(k, 256) * P.d.n);
 }
 
@@ -204,9 +226,11 @@ abft_status abft_encode(const abft_desc* desc, const void* A, const void* B, con
   if (st != ABFT_OK) return st;
   if (is_empty(P)) return ABFT_OK;
   if (!ws || (P.d.k > 0 && (!A || !B))) return fail(ABFT_ERR_INVALID, "NULL pointer");
-  const cudaError_t e = launch_encode_f64(P, static_cast<const double*>(A),
-                                          static_cast<const double*>(B), ws,
-                                          static_cast<cudaStream_t>(stream));
+  const cudaError_t e =
+      P.d.dtype == ABFT_F64
+          ? launch_encode_f64(P, static_cast<const double*>(A), static_cast<const double*>(B), ws,
+                              static_cast<cudaStream_t>(stream))
+          : launch_encode_lp(P, A, B, ws, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? ABFT_OK : cuda_fail(e, "abft_encode");
 }
 
@@ -241,9 +265,16 @@ static abft_status gemm_common(const abft_desc* desc, const void* A, const void*
   if (is_empty(P)) return ABFT_OK;
   if (!C || (checksums && !ws) || (P.d.k > 0 && (!A || !B)))
     return fail(ABFT_ERR_INVALID, "NULL pointer");
-  const cudaError_t e =
-      launch_gemm_f64(P, static_cast<const double*>(A), static_cast<const double*>(B),
-                      static_cast<double*>(C), ws, checksums, static_cast<cudaStream_t>(stream));
+  cudaError_t e;
+  if (P.d.dtype == ABFT_F64) {
+    e = launch_gemm_f64(P, static_cast<const double*>(A), static_cast<const double*>(B),
+                        static_cast<double*>(C), ws, checksums, static_cast<cudaStream_t>(stream));
+  } else {
+    if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15)
+      return fail(ABFT_ERR_INVALID, "bf16 operands must be 16-byte aligned");
+    e = launch_gemm_lp(P, A, B, static_cast<float*>(C), ws, checksums,
+                       static_cast<cudaStream_t>(stream));
+  }
   return e == cudaSuccess ? ABFT_OK : cuda_fail(e, checksums ? "abft_gemm" : "abft_gemm_plain");
 }
 
@@ -261,10 +292,28 @@ abft_status abft_gemm_plain(const abft_desc* desc, const void* A, const void* B,
   return gemm_common(desc, A, B, C, nullptr, false, stream);
 }
 
+abft_status abft_set_epilogue_faults(const abft_desc* desc, void* ws, const int64_t* rows,
+                                     const int64_t* cols, const int32_t* bits, int32_t count,
+                                     void* stream) {
+  Plan P;
+  abft_status st = make_plan(desc, &P);
+  if (st != ABFT_OK) return st;
+  if (P.d.dtype == ABFT_F64)
+    return fail(ABFT_ERR_UNSUPPORTED, "epilogue fault injection needs a tensor-core dtype");
+  if (!ws || count < 0 || count > kMaxInject || (count > 0 && (!rows || !cols || !bits)))
+    return fail(ABFT_ERR_INVALID, "bad injection list (at most %d entries)", kMaxInject);
+  for (int t = 0; t < count; ++t)
+    if (rows[t] < 0 || rows[t] >= P.d.m || cols[t] < 0 || cols[t] >= P.d.n || bits[t] < 0 ||
+        bits[t] > 31)
+      return fail(ABFT_ERR_INVALID, "injection %d outside C or the fp32 element", t);
+  const cudaError_t e =
+      launch_set_inject(P, ws, rows, cols, bits, count, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? ABFT_OK : cuda_fail(e, "abft_set_epilogue_faults");
+}
+
 abft_status abft_verify_correct(const abft_desc* desc, void* C, void* ws, int32_t reread_C,
                                 const int32_t* erased_blocks, int32_t n_erased, abft_fault* report,
                                 int32_t max_reports, int32_t* n_reports, void* stream) {
-  (void)reread_C;
   Plan P;
   abft_status st = make_plan(desc, &P);
   if (st != ABFT_OK) return st;
@@ -288,12 +337,19 @@ abft_status abft_verify_correct(const abft_desc* desc, void* C, void* ws, int32_
   Scratch S = scratch_view(P, ws);
   cudaError_t e = cudaMemsetAsync(S.cnt, 0, 256, s);
   if (e != cudaSuccess) return cuda_fail(e, "abft_verify_correct memset");
-  e = launch_verify(P, C, ws, er, s);
+  e = launch_verify(P, C, ws, er, reread_C != 0 || !P.fused, s);
   if (e != cudaSuccess) return cuda_fail(e, "abft_verify_correct launch");
   int32_t cnt[kNumCounters];
   e = cudaMemcpyAsync(cnt, S.cnt, sizeof cnt, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "abft_verify_correct");
+  if (P.d.dtype != ABFT_F64) {
+    bool timed_out = false;
+    e = consume_tc_timeout(s, &timed_out);
+    if (e != cudaSuccess) return cuda_fail(e, "abft_verify_correct");
+    if (timed_out)
+      return fail(ABFT_ERR_TIMEOUT, "a tensor-core product gave up waiting (bounded wait)");
+  }
   const int total = cnt[kCntReport];
   const int stored = std::min(total, kCapReport);
   std::vector<abft_fault> rep((size_t)stored);

@@ -32,8 +32,9 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // Column checksums of A per verify block: acs[2I] = e^T A_I, acs[2I+1] =
-// w^T A_I, plus per-chunk partials of the squared norms of e^T|A_I|, w^T|A_I|,
-// e^T A_I, w^T A_I.  Grid (ceil(k/256), nvr); thread = one column l of A.
+// w^T A_I, plus per-chunk partials of ||e^T A_I||^2 and ||w^T A_I||^2 at
+// part[(2I + c) * nch + chunk].  Grid (ceil(k/256), <= 65535); thread = one
+// column l of A.
 __global__ void __launch_bounds__(kThreads) k_encA_cols(const double* __restrict__ A, int64_t lda,
                                                         int64_t m, int64_t k, int vb, int e,
                                                         double* __restrict__ acs,
@@ -43,28 +44,25 @@ __global__ void __launch_bounds__(kThreads) k_encA_cols(const double* __restrict
   const int64_t nvb = cdiv(m, vb);
   const double sc = scalbn(1.0, -e);
   for (int64_t I = blockIdx.y; I < nvb; I += gridDim.y) {
-  const int64_t i0 = I * vb, i1 = min(i0 + (int64_t)vb, m);
-  double se = 0.0, sw = 0.0, sa = 0.0, swa = 0.0;
-  if (l < k) {
-    const double* p = A + i0 * lda + l;
+    const int64_t i0 = I * vb, i1 = min(i0 + (int64_t)vb, m);
+    double se = 0.0, sw = 0.0;
+    if (l < k) {
+      const double* p = A + i0 * lda + l;
 #pragma unroll 4
-    for (int64_t i = i0; i < i1; ++i) {
-      const double a = p[(i - i0) * lda];
-      const double w = (double)(i - i0 + 1) * sc;
-      se += a;
-      sw = fma(w, a, sw);
-      sa += fabs(a);
-      swa = fma(w, fabs(a), swa);
+      for (int64_t i = i0; i < i1; ++i) {
+        const double a = p[(i - i0) * lda];
+        se += a;
+        sw = fma((double)(i - i0 + 1) * sc, a, sw);
+      }
+      acs[(2 * I) * k + l] = se;
+      acs[(2 * I + 1) * k + l] = sw;
     }
-    acs[(2 * I) * k + l] = se;
-    acs[(2 * I + 1) * k + l] = sw;
-  }
-  const double q[4] = {sa * sa, swa * swa, se * se, sw * sw};
+    const double q[2] = {se * se, sw * sw};
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const double t = block_sum(q[c], sh);
-    if (threadIdx.x == 0) part[(4 * I + c) * nch + blockIdx.x] = t;
-  }
+    for (int c = 0; c < 2; ++c) {
+      const double t = block_sum(q[c], sh);
+      if (threadIdx.x == 0) part[(2 * I + c) * nch + blockIdx.x] = t;
+    }
   }
 }
 
@@ -99,8 +97,8 @@ __global__ void __launch_bounds__(kThreads) k_row_norms(const double* __restrict
 }
 
 // Row checksums of B per verify block: bcs[l][2J] = B_J e, bcs[l][2J+1] = B_J w,
-// plus per-chunk partials of the squared norms of |B_J|e, |B_J|w, B_J e, B_J w.
-// One warp per (J, chunk of 64 rows of B).  Grid (ceil(nchunks/8), nvc).
+// plus per-chunk partials of ||B_J e||^2 and ||B_J w||^2 at
+// part[(2J + c) * nch + chunk].  One warp per (J, chunk of 64 rows of B).
 __global__ void __launch_bounds__(kThreads) k_encB_rows(const double* __restrict__ B, int64_t ldb,
                                                         int64_t k, int64_t n, int vb, int e,
                                                         double* __restrict__ bcs, int64_t Cc,
@@ -109,40 +107,31 @@ __global__ void __launch_bounds__(kThreads) k_encB_rows(const double* __restrict
   const int64_t chunk = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
   if (chunk >= nch) return;
   const int64_t nvb = cdiv(n, vb);
-  for (int64_t J = blockIdx.y; J < nvb; J += gridDim.y) {
-  const int64_t j0 = J * vb, j1 = min(j0 + (int64_t)vb, n);
-  const int64_t l0 = chunk * kRowsPerWarpB, l1 = min(l0 + kRowsPerWarpB, k);
   const double sc = scalbn(1.0, -e);
-  double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
-  for (int64_t l = l0; l < l1; ++l) {
-    double se = 0.0, sw = 0.0, sa = 0.0, swa = 0.0;
-    for (int64_t j = j0 + lane; j < j1; j += 32) {
-      const double b = B[l * ldb + j];
-      const double w = (double)(j - j0 + 1) * sc;
-      se += b;
-      sw = fma(w, b, sw);
-      sa += fabs(b);
-      swa = fma(w, fabs(b), swa);
+  for (int64_t J = blockIdx.y; J < nvb; J += gridDim.y) {
+    const int64_t j0 = J * vb, j1 = min(j0 + (int64_t)vb, n);
+    const int64_t l0 = chunk * kRowsPerWarpB, l1 = min(l0 + kRowsPerWarpB, k);
+    double q0 = 0.0, q1 = 0.0;
+    for (int64_t l = l0; l < l1; ++l) {
+      double se = 0.0, sw = 0.0;
+      for (int64_t j = j0 + lane; j < j1; j += 32) {
+        const double b = B[l * ldb + j];
+        se += b;
+        sw = fma((double)(j - j0 + 1) * sc, b, sw);
+      }
+      se = warp_sum(se);
+      sw = warp_sum(sw);
+      if (lane == 0) {
+        bcs[l * Cc + 2 * J] = se;
+        bcs[l * Cc + 2 * J + 1] = sw;
+      }
+      q0 = fma(se, se, q0);
+      q1 = fma(sw, sw, q1);
     }
-    se = warp_sum(se);
-    sw = warp_sum(sw);
-    sa = warp_sum(sa);
-    swa = warp_sum(swa);
     if (lane == 0) {
-      bcs[l * Cc + 2 * J] = se;
-      bcs[l * Cc + 2 * J + 1] = sw;
+      part[(2 * J + 0) * nch + chunk] = q0;
+      part[(2 * J + 1) * nch + chunk] = q1;
     }
-    q0 = fma(sa, sa, q0);
-    q1 = fma(swa, swa, q1);
-    q2 = fma(se, se, q2);
-    q3 = fma(sw, sw, q3);
-  }
-  if (lane == 0) {
-    part[(4 * J + 0) * nch + chunk] = q0;
-    part[(4 * J + 1) * nch + chunk] = q1;
-    part[(4 * J + 2) * nch + chunk] = q2;
-    part[(4 * J + 3) * nch + chunk] = q3;
-  }
   }
 }
 
@@ -173,6 +162,34 @@ __global__ void k_sum_sqrt(const double* __restrict__ part, int64_t nout, int64_
   double s = 0.0;
   for (int64_t c = 0; c < nch; ++c) s += part[o * so + c * sc];
   out[o] = sqrt(s);
+}
+
+// Threshold norms of every verify block from the per-line norms and the
+// checksum partials: nblk[4I] = sqrt(sum_{t in I} nvec_t^2), nblk[4I+1] =
+// sqrt(sum (w_t nvec_t)^2), nblk[4I+2], nblk[4I+3] = sqrt of the summed
+// partials of the two checksum vectors.  One thread per verify block.
+__global__ void k_finalize_blk(const double* __restrict__ nvec, int64_t len, int vb, int e,
+                               const double* __restrict__ part, int64_t nch,
+                               double* __restrict__ nblk) {
+  const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nvb = cdiv(len, vb);
+  if (I >= nvb) return;
+  const double sc = scalbn(1.0, -e);
+  const int64_t t0 = I * vb, t1 = min(t0 + (int64_t)vb, len);
+  double f0 = 0.0, f1 = 0.0, q0 = 0.0, q1 = 0.0;
+  for (int64_t t = t0; t < t1; ++t) {
+    const double v = nvec[t], wv = (double)(t - t0 + 1) * sc * v;
+    f0 = fma(v, v, f0);
+    f1 = fma(wv, wv, f1);
+  }
+  for (int64_t c = 0; c < nch; ++c) {
+    q0 += part[(2 * I) * nch + c];
+    q1 += part[(2 * I + 1) * nch + c];
+  }
+  nblk[4 * I + 0] = sqrt(f0);
+  nblk[4 * I + 1] = sqrt(f1);
+  nblk[4 * I + 2] = sqrt(q0);
+  nblk[4 * I + 3] = sqrt(q1);
 }
 
 }  // namespace
@@ -214,9 +231,11 @@ cudaError_t launch_encode_f64(const Plan& P, const double* A, const double* B, v
       B, d.ldb, d.k, d.n, d.vb_cols, P.ec, bcs, P.Cc, partB, nchB);
   k_col_sq<<<dim3((unsigned)cdiv(d.n, kThreads), gy(nchC)), kThreads, 0, st>>>(
       B, d.ldb, d.k, d.n, partC);
-  k_sum_sqrt<<<(unsigned)cdiv(4 * P.nvr, 128), 128, 0, st>>>(partA, 4 * P.nvr, nchA, nchA, 1, nAblk);
-  k_sum_sqrt<<<(unsigned)cdiv(4 * P.nvc, 128), 128, 0, st>>>(partB, 4 * P.nvc, nchB, nchB, 1, nBblk);
   k_sum_sqrt<<<(unsigned)cdiv(d.n, 128), 128, 0, st>>>(partC, d.n, nchC, 1, d.n, nBcol);
+  k_finalize_blk<<<(unsigned)cdiv(P.nvr, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA,
+                                                             nchA, nAblk);
+  k_finalize_blk<<<(unsigned)cdiv(P.nvc, 128), 128, 0, st>>>(nBcol, d.n, d.vb_cols, P.ec, partB,
+                                                             nchB, nBblk);
   return cudaGetLastError();
 }
 
@@ -300,9 +319,11 @@ cudaError_t launch_encode_f64_noalloc(const Plan& P, const double* A, const doub
       B, d.ldb, d.k, d.n, d.vb_cols, P.ec, bcs, P.Cc, partB, nchB);
   k_col_sq<<<dim3((unsigned)cdiv(d.n, kThreads), gy(nchC)), kThreads, 0, st>>>(
       B, d.ldb, d.k, d.n, partC);
-  k_sum_sqrt<<<(unsigned)cdiv(4 * P.nvr, 128), 128, 0, st>>>(partA, 4 * P.nvr, nchA, nchA, 1, nAblk);
-  k_sum_sqrt<<<(unsigned)cdiv(4 * P.nvc, 128), 128, 0, st>>>(partB, 4 * P.nvc, nchB, nchB, 1, nBblk);
   k_sum_sqrt<<<(unsigned)cdiv(d.n, 128), 128, 0, st>>>(partC, d.n, nchC, 1, d.n, nBcol);
+  k_finalize_blk<<<(unsigned)cdiv(P.nvr, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA,
+                                                             nchA, nAblk);
+  k_finalize_blk<<<(unsigned)cdiv(P.nvc, 128), 128, 0, st>>>(nBcol, d.n, d.vb_cols, P.ec, partB,
+                                                             nchB, nBblk);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,419 @@
+// Checksum encoding for the tensor-core dtypes (section 2.1; the encoded
+// operands of Eq. (1)) and the fold of the product's checksum pieces.
+//
+// Checksums of bf16 data are accumulated in fp32 and fed to the tensor cores
+// as a bf16 hi + lo pair (hi = bf16(x), lo = bf16(x - hi); the pair carries x
+// to a relative 2^-18), so the product of each piece with B (or of A with
+// each piece) is a separate fp32 row (column) of the ABFT product; the fold
+// kernel adds the two pieces in binary64 into the E / F layout that the
+// verify kernels share with the binary64 path.
+//
+// acs rows per verify block I: 4I e-hi, 4I+1 e-lo, 4I+2 w-hi, 4I+3 w-lo; then
+// two rows (hi, lo) per block checksum row.  bcs is row-major k x (4 nvc)
+// with the same piece order per verify column block.
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+
+namespace abft {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kColsPerCta = 8 * kThreads;  // 2048 columns, 8 per thread (16-byte loads)
+constexpr int kRowsPerCtaB = 128;          // rows of B per CTA in the row-checksum pass
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block's threads, valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < kThreads / 32; ++q) t += sh[q];
+  return t;
+}
+
+__device__ __forceinline__ void split(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+__device__ __forceinline__ float ldf(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+// Eight consecutive elements starting at column c of a row (zeros past `len`).
+__device__ __forceinline__ void load8(const __nv_bfloat16* row, int64_t c, int64_t len,
+                                      float (&v)[8]) {
+  if (c + 8 <= len && ((reinterpret_cast<uintptr_t>(row + c) & 15) == 0)) {
+    const uint4 u = *reinterpret_cast<const uint4*>(row + c);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 f = __bfloat1622float2(h[q]);
+      v[2 * q] = f.x;
+      v[2 * q + 1] = f.y;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = (c + q < len) ? ldf(row + c + q) : 0.f;
+  }
+}
+
+__device__ __forceinline__ void store8(__nv_bfloat16* dst, const __nv_bfloat16 (&v)[8]) {
+  *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v);
+}
+
+// Column checksums of A per verify block (fp32 sums, hi/lo pieces), per-row
+// partial sums of squares (one per 256 columns) and per-CTA partials of the
+// squared norms of the two checksum rows.  CTA = 2048 columns x one verify
+// block; thread = 8 consecutive columns.
+__global__ void __launch_bounds__(kThreads) k_lpA_cols(const __nv_bfloat16* __restrict__ A,
+                                                       int64_t lda, int64_t m, int64_t k, int vb,
+                                                       int e, __nv_bfloat16* __restrict__ acs,
+                                                       int64_t ldk, float* __restrict__ rowpart,
+                                                       int64_t nchr, double* __restrict__ part,
+                                                       int64_t nch) {
+  __shared__ double sh[kThreads / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c0 = (int64_t)blockIdx.x * kColsPerCta + 8 * threadIdx.x;
+  const int64_t nvb = cdiv(m, vb);
+  const float sc = scalbnf(1.0f, -e);
+  for (int64_t I = blockIdx.y; I < nvb; I += gridDim.y) {
+    const int64_t i0 = I * vb, i1 = min(i0 + (int64_t)vb, m);
+    float se[8], sw[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) se[q] = sw[q] = 0.f;
+    for (int64_t i = i0; i < i1; ++i) {
+      float v[8];
+      load8(A + i * lda, c0, k, v);
+      const float w = (float)(i - i0 + 1) * sc;
+      float sq = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        se[q] += v[q];
+        sw[q] = fmaf(w, v[q], sw[q]);
+        sq = fmaf(v[q], v[q], sq);
+      }
+      sq = warp_sumf(sq);
+      const int64_t rc = (int64_t)blockIdx.x * (kThreads / 32) + warp;  // 256-column chunk
+      if (lane == 0 && rc < nchr) rowpart[i * nchr + rc] = sq;
+    }
+    double q0 = 0.0, q1 = 0.0;
+    if (c0 < ldk) {
+      __nv_bfloat16 eh[8], el[8], wh[8], wl[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        split(se[q], eh[q], el[q]);
+        split(sw[q], wh[q], wl[q]);
+        q0 += (double)se[q] * se[q];
+        q1 += (double)sw[q] * sw[q];
+      }
+      store8(acs + (4 * I + 0) * ldk + c0, eh);
+      store8(acs + (4 * I + 1) * ldk + c0, el);
+      store8(acs + (4 * I + 2) * ldk + c0, wh);
+      store8(acs + (4 * I + 3) * ldk + c0, wl);
+    }
+    const double t0 = block_sum(q0, sh);
+    if (threadIdx.x == 0) part[(2 * I) * nch + blockIdx.x] = t0;
+    const double t1 = block_sum(q1, sh);
+    if (threadIdx.x == 0) part[(2 * I + 1) * nch + blockIdx.x] = t1;
+  }
+}
+
+// Block checksum rows S_A[t] = sum_I A[I*bs + t], as hi/lo pieces.
+__global__ void __launch_bounds__(kThreads) k_lpA_block(const __nv_bfloat16* __restrict__ A,
+                                                        int64_t lda, int64_t k, int p, int64_t bs,
+                                                        __nv_bfloat16* __restrict__ S,
+                                                        int64_t ldk) {
+  const int64_t l = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (l >= k) return;
+  for (int64_t t = blockIdx.y; t < bs; t += gridDim.y) {
+    float s = 0.f;
+    for (int I = 0; I < p; ++I) s += ldf(A + (I * bs + t) * lda + l);
+    __nv_bfloat16 h, lo;
+    split(s, h, lo);
+    S[(2 * t) * ldk + l] = h;
+    S[(2 * t + 1) * ldk + l] = lo;
+  }
+}
+
+// Row checksums of B per verify column block (hi/lo pieces in the row-major
+// bcs), per-column partial sums of squares (one per 128 rows) and partials
+// of the squared norms of the checksum columns.  Verify blocks of 8, 16, ...,
+// 256 columns: the lanes of a block reduce with shuffles.  CTA = 2048
+// columns x 128 rows; thread = 8 consecutive columns.
+__global__ void __launch_bounds__(kThreads) k_lpB_rows(const __nv_bfloat16* __restrict__ B,
+                                                       int64_t ldb, int64_t k, int64_t n, int vb,
+                                                       int e, __nv_bfloat16* __restrict__ bcs,
+                                                       int64_t ldcs, float* __restrict__ colpart,
+                                                       double* __restrict__ part, int64_t nch) {
+  const int lane = threadIdx.x & 31;
+  const int64_t c0 = (int64_t)blockIdx.x * kColsPerCta + 8 * threadIdx.x;
+  const int64_t l0 = (int64_t)blockIdx.y * kRowsPerCtaB, l1 = min(l0 + kRowsPerCtaB, k);
+  const int seg = vb / 8;  // lanes per verify block (1 .. 32)
+  const bool leader = (lane % seg) == 0 && c0 < n;
+  const int64_t J = c0 / vb;
+  const float sc = scalbnf(1.0f, -e);
+  float wq[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) wq[q] = (float)((c0 + q) % vb + 1) * sc;
+  float cs[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) cs[q] = 0.f;
+  double q0 = 0.0, q1 = 0.0;
+  for (int64_t l = l0; l < l1; ++l) {
+    float v[8];
+    load8(B + l * ldb, c0, n, v);
+    float se = 0.f, sw = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      se += v[q];
+      sw = fmaf(wq[q], v[q], sw);
+      cs[q] = fmaf(v[q], v[q], cs[q]);
+    }
+    for (int o = seg >> 1; o > 0; o >>= 1) {
+      se += __shfl_xor_sync(0xffffffffu, se, o);
+      sw += __shfl_xor_sync(0xffffffffu, sw, o);
+    }
+    if (leader) {
+      __nv_bfloat16 pc[4];
+      split(se, pc[0], pc[1]);
+      split(sw, pc[2], pc[3]);
+      *reinterpret_cast<uint2*>(bcs + l * ldcs + 4 * J) = *reinterpret_cast<const uint2*>(pc);
+      q0 += (double)se * se;
+      q1 += (double)sw * sw;
+    }
+  }
+  if (leader) {
+    part[(2 * J) * nch + blockIdx.y] = q0;
+    part[(2 * J + 1) * nch + blockIdx.y] = q1;
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    if (c0 + q < n) colpart[blockIdx.y * n + c0 + q] = cs[q];
+}
+
+// The same outputs for any verify block size (one warp per row segment).
+__global__ void __launch_bounds__(kThreads) k_lpB_rows_any(const __nv_bfloat16* __restrict__ B,
+                                                           int64_t ldb, int64_t k, int64_t n,
+                                                           int vb, int e,
+                                                           __nv_bfloat16* __restrict__ bcs,
+                                                           int64_t ldcs,
+                                                           double* __restrict__ part,
+                                                           int64_t nch) {
+  const int lane = threadIdx.x & 31;
+  const int64_t chunk = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+  if (chunk >= nch) return;
+  const int64_t nvb = cdiv(n, vb);
+  const float sc = scalbnf(1.0f, -e);
+  for (int64_t J = blockIdx.y; J < nvb; J += gridDim.y) {
+    const int64_t j0 = J * vb, j1 = min(j0 + (int64_t)vb, n);
+    const int64_t l0 = chunk * kRowsPerCtaB, l1 = min(l0 + kRowsPerCtaB, k);
+    double q0 = 0.0, q1 = 0.0;
+    for (int64_t l = l0; l < l1; ++l) {
+      float se = 0.f, sw = 0.f;
+      for (int64_t j = j0 + lane; j < j1; j += 32) {
+        const float b = ldf(B + l * ldb + j);
+        se += b;
+        sw = fmaf((float)(j - j0 + 1) * sc, b, sw);
+      }
+      se = warp_sumf(se);
+      sw = warp_sumf(sw);
+      if (lane == 0) {
+        __nv_bfloat16 h, lo;
+        split(se, h, lo);
+        bcs[l * ldcs + 4 * J + 0] = h;
+        bcs[l * ldcs + 4 * J + 1] = lo;
+        split(sw, h, lo);
+        bcs[l * ldcs + 4 * J + 2] = h;
+        bcs[l * ldcs + 4 * J + 3] = lo;
+      }
+      q0 += (double)se * se;
+      q1 += (double)sw * sw;
+    }
+    if (lane == 0) {
+      part[(2 * J) * nch + chunk] = q0;
+      part[(2 * J + 1) * nch + chunk] = q1;
+    }
+  }
+}
+
+// Column partial sums of squares for the generic path.  Grid (ceil(n/256), nch).
+__global__ void __launch_bounds__(kThreads) k_lp_col_sq(const __nv_bfloat16* __restrict__ B,
+                                                        int64_t ldb, int64_t k, int64_t n,
+                                                        float* __restrict__ colpart) {
+  const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (j >= n) return;
+  const int64_t nch = cdiv(k, kRowsPerCtaB);
+  for (int64_t c = blockIdx.y; c < nch; c += gridDim.y) {
+    const int64_t l0 = c * kRowsPerCtaB, l1 = min(l0 + kRowsPerCtaB, k);
+    float s = 0.f;
+    for (int64_t l = l0; l < l1; ++l) {
+      const float b = ldf(B + l * ldb + j);
+      s = fmaf(b, b, s);
+    }
+    colpart[c * n + j] = s;
+  }
+}
+
+// out[o] = sqrt(sum_c part[o*so + c*sc]) (fp32 partials, binary64 sum).
+__global__ void k_lp_norms(const float* __restrict__ part, int64_t nout, int64_t nch, int64_t so,
+                           int64_t sc, double* __restrict__ out) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nout) return;
+  double s = 0.0;
+  for (int64_t c = 0; c < nch; ++c) s += (double)part[o * so + c * sc];
+  out[o] = sqrt(s);
+}
+
+// Threshold norms of each verify block from the line norms and the checksum
+// partials (see the binary64 encode for the definitions).
+__global__ void k_lp_blk(const double* __restrict__ nvec, int64_t len, int vb, int e,
+                         const double* __restrict__ part, int64_t nch, double* __restrict__ nblk) {
+  const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= cdiv(len, vb)) return;
+  const double sc = scalbn(1.0, -e);
+  const int64_t t0 = I * vb, t1 = min(t0 + (int64_t)vb, len);
+  double f0 = 0.0, f1 = 0.0, q0 = 0.0, q1 = 0.0;
+  for (int64_t t = t0; t < t1; ++t) {
+    const double v = nvec[t], wv = (double)(t - t0 + 1) * sc * v;
+    f0 = fma(v, v, f0);
+    f1 = fma(wv, wv, f1);
+  }
+  for (int64_t c = 0; c < nch; ++c) {
+    q0 += part[(2 * I) * nch + c];
+    q1 += part[(2 * I + 1) * nch + c];
+  }
+  nblk[4 * I + 0] = sqrt(f0);
+  nblk[4 * I + 1] = sqrt(f1);
+  nblk[4 * I + 2] = sqrt(q0);
+  nblk[4 * I + 3] = sqrt(q1);
+}
+
+// E[2I + x][j] = E16[4I + 2x][j] + E16[4I + 2x + 1][j];
+// E[2 nvr + t][j] = E16[4 nvr + 2t][j] + E16[4 nvr + 2t + 1][j]   (binary64)
+__global__ void k_fold_E(const float* __restrict__ E16, int64_t R, int64_t nvr, int64_t n,
+                         double* __restrict__ E) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  for (int64_t r = blockIdx.y; r < R; r += gridDim.y) {
+    // output row r takes pieces 2r and 2r + 1 in both parts of the layout
+    const int64_t src = 2 * r;
+    E[r * n + j] = (double)E16[src * n + j] + (double)E16[(src + 1) * n + j];
+  }
+}
+
+// F[i][2J + x] = F16[i][4J + 2x] + F16[i][4J + 2x + 1]   (binary64)
+__global__ void k_fold_F(const float* __restrict__ F16, int64_t m, int64_t Cc, int64_t C16,
+                         double* __restrict__ F) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * Cc) return;
+  const int64_t i = t / Cc, c = t % Cc;
+  F[i * Cc + c] = (double)F16[i * C16 + 2 * c] + (double)F16[i * C16 + 2 * c + 1];
+}
+
+unsigned gy(int64_t v) { return (unsigned)(v < 65535 ? v : 65535); }
+
+}  // namespace
+
+// Scratch of the tensor-core encode, carved from the workspace's partial-sum
+// region: checksum-norm partials (binary64), then per-row and per-column
+// partial sums of squares (fp32).
+size_t lp_part_bytes(const Plan& P) {
+  const int64_t k = P.d.k > 0 ? P.d.k : 1;
+  return sizeof(double) * (2 * P.nvr * cdiv(k, kColsPerCta) + 2 * P.nvc * cdiv(k, kRowsPerCtaB)) +
+         sizeof(float) * (P.d.m * cdiv(k, 256) + cdiv(k, kRowsPerCtaB) * P.d.n) + 64;
+}
+
+cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, void* ws,
+                             cudaStream_t st) {
+  const abft_desc& d = P.d;
+  const auto* A = static_cast<const __nv_bfloat16*>(Av);
+  const auto* B = static_cast<const __nv_bfloat16*>(Bv);
+  char* w = static_cast<char*>(ws);
+  auto* acs = reinterpret_cast<__nv_bfloat16*>(w + P.L.acs);
+  auto* bcs = reinterpret_cast<__nv_bfloat16*>(w + P.L.bcs);
+  double* nArow = reinterpret_cast<double*>(w + P.L.nArow);
+  double* nAblk = reinterpret_cast<double*>(w + P.L.nAblk);
+  double* nBcol = reinterpret_cast<double*>(w + P.L.nBcol);
+  double* nBblk = reinterpret_cast<double*>(w + P.L.nBblk);
+  Scratch S = scratch_view(P, ws);
+  if (d.k == 0) {
+    cudaMemsetAsync(nArow, 0, sizeof(double) * d.m, st);
+    cudaMemsetAsync(nAblk, 0, sizeof(double) * 4 * P.nvr, st);
+    cudaMemsetAsync(nBcol, 0, sizeof(double) * d.n, st);
+    cudaMemsetAsync(nBblk, 0, sizeof(double) * 4 * P.nvc, st);
+    return cudaGetLastError();
+  }
+  const int64_t nchA = cdiv(d.k, kColsPerCta);
+  const int64_t nchB = cdiv(d.k, kRowsPerCtaB);
+  const int64_t nchr = cdiv(d.k, 256);
+  double* partA = S.part;
+  double* partB = partA + 2 * P.nvr * nchA;
+  float* rowpart = reinterpret_cast<float*>(partB + 2 * P.nvc * nchB);
+  float* colpart = rowpart + d.m * nchr;
+  const bool fastB = d.vb_cols >= 8 && d.vb_cols <= 256 && (d.vb_cols & (d.vb_cols - 1)) == 0;
+  if (P.L.bcs_ld > P.L.bcs_cols)
+    cudaMemset2DAsync(bcs + P.L.bcs_cols, P.L.bcs_ld * 2, 0, (P.L.bcs_ld - P.L.bcs_cols) * 2, d.k,
+                      st);
+  k_lpA_cols<<<dim3((unsigned)nchA, gy(P.nvr)), kThreads, 0, st>>>(
+      A, d.lda, d.m, d.k, d.vb_rows, P.er, acs, P.L.acs_ld, rowpart, nchr, partA, nchA);
+  if (P.bs > 0)
+    k_lpA_block<<<dim3((unsigned)cdiv(d.k, kThreads), gy(P.bs)), kThreads, 0, st>>>(
+        A, d.lda, d.k, d.grid_p, P.bs, acs + 4 * P.nvr * P.L.acs_ld, P.L.acs_ld);
+  k_lp_norms<<<(unsigned)cdiv(d.m, 128), 128, 0, st>>>(rowpart, d.m, nchr, nchr, 1, nArow);
+  k_lp_blk<<<(unsigned)cdiv(P.nvr, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA, nchA,
+                                                       nAblk);
+  if (fastB) {
+    k_lpB_rows<<<dim3((unsigned)cdiv(d.n, kColsPerCta), (unsigned)nchB), kThreads, 0, st>>>(
+        B, d.ldb, d.k, d.n, d.vb_cols, P.ec, bcs, P.L.bcs_ld, colpart, partB, nchB);
+  } else {
+    k_lpB_rows_any<<<dim3((unsigned)cdiv(nchB, kThreads / 32), gy(P.nvc)), kThreads, 0, st>>>(
+        B, d.ldb, d.k, d.n, d.vb_cols, P.ec, bcs, P.L.bcs_ld, partB, nchB);
+    k_lp_col_sq<<<dim3((unsigned)cdiv(d.n, kThreads), gy(nchB)), kThreads, 0, st>>>(
+        B, d.ldb, d.k, d.n, colpart);
+  }
+  k_lp_norms<<<(unsigned)cdiv(d.n, 128), 128, 0, st>>>(colpart, d.n, nchB, 1, d.n, nBcol);
+  k_lp_blk<<<(unsigned)cdiv(P.nvc, 128), 128, 0, st>>>(nBcol, d.n, d.vb_cols, P.ec, partB, nchB,
+                                                       nBblk);
+  count_launches(6 + (P.bs > 0 ? 1 : 0) + (fastB ? 0 : 1));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_lp(const Plan& P, const void* A, const void* B, float* C, void* ws,
+                           bool checksums, cudaStream_t st) {
+  const abft_desc& d = P.d;
+  char* w = static_cast<char*>(ws);
+  if (d.k == 0) {  // empty inner dimension: every product is zero
+    cudaError_t e = cudaMemset2DAsync(C, d.ldc * 4, 0, d.n * 4, d.m, st);
+    if (e == cudaSuccess && checksums) {
+      e = cudaMemsetAsync(w + P.L.E, 0, (size_t)P.R * d.n * 8, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(w + P.L.F, 0, (size_t)d.m * P.Cc * 8, st);
+    }
+    return e;
+  }
+  cudaError_t e = launch_gemm_bf16(P, A, B, C, ws, checksums, st);
+  if (e != cudaSuccess || !checksums) return e;
+  const float* E16 = reinterpret_cast<const float*>(w + P.L.E16);
+  const float* F16 = reinterpret_cast<const float*>(w + P.L.F16);
+  double* E = reinterpret_cast<double*>(w + P.L.E);
+  double* F = reinterpret_cast<double*>(w + P.L.F);
+  k_fold_E<<<dim3((unsigned)cdiv(d.n, 256), gy(P.R)), 256, 0, st>>>(E16, P.R, P.nvr, d.n, E);
+  k_fold_F<<<(unsigned)cdiv(d.m * P.Cc, 256), 256, 0, st>>>(F16, d.m, P.Cc, P.L.bcs_cols, F);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+}  // namespace abft

@@ -14,6 +14,7 @@ constexpr int kCapFlags = 4096;    // flagged lines per side
 constexpr int kCapCands = 2048;    // candidates merged in shared memory
 constexpr int kCapReport = 16384;  // device report entries
 constexpr int kMaxErased = 16;     // erased blocks per verify call
+constexpr int kMaxInject = 256;    // armed epilogue fault injections
 
 // Counter slots in the scratch region.
 enum Counter : int {
@@ -51,8 +52,20 @@ struct Plan {
   int er, ec;        // ceil(log2(vb_rows)), ceil(log2(vb_cols))
   double s;          // safety factor
   double f1_col, f2_col, f1_row, f2_row;  // threshold factors
+  // Fused observed checksums (tensor-core dtypes): the product's epilogue
+  // writes per-tile column partial sums (one per 128 rows) and per-row partial
+  // sums over column groups of g = min(vb_cols, 256) columns.
+  int fused;
+  int64_t g, ngrp, ntr_obs;
   abft_ws_layout L;
 };
+
+struct InjectEntry {  // one armed bit flip of an accumulator output
+  int32_t row, col, bit, pad;
+};
+// Header of the injection region: {kInjectMagic, count, 0, 0}, entries follow
+// at +16 bytes.  The magic keeps a fresh (uninitialised) workspace disarmed.
+constexpr int32_t kInjectMagic = 0x0ABF7C0D;
 
 // Scratch region view.
 struct Scratch {
@@ -82,7 +95,21 @@ cudaError_t launch_encode_f64_noalloc(const Plan& P, const double* A, const doub
 size_t static_encode_part_bytes();
 cudaError_t launch_gemm_f64(const Plan& P, const double* A, const double* B, double* C, void* ws,
                             bool checksums, cudaStream_t st);
-cudaError_t launch_verify(const Plan& P, void* C, void* ws, const Erased& er, cudaStream_t st);
+// Tensor-core dtypes: encode (checksum pieces, norms) and the product
+// followed by the fold of E16/F16 into the binary64 E/F.
+cudaError_t launch_encode_lp(const Plan& P, const void* A, const void* B, void* ws,
+                             cudaStream_t st);
+size_t lp_part_bytes(const Plan& P);
+cudaError_t launch_gemm_lp(const Plan& P, const void* A, const void* B, float* C, void* ws,
+                           bool checksums, cudaStream_t st);
+cudaError_t launch_gemm_bf16(const Plan& P, const void* A, const void* B, float* C, void* ws,
+                             bool checksums, cudaStream_t st);
+cudaError_t tc_timeout_flag(int** dev_ptr);
+cudaError_t consume_tc_timeout(cudaStream_t st, bool* timed_out);
+cudaError_t launch_verify(const Plan& P, void* C, void* ws, const Erased& er, bool reread,
+                          cudaStream_t st);
+cudaError_t launch_set_inject(const Plan& P, void* ws, const int64_t* rows, const int64_t* cols,
+                              const int32_t* bits, int count, cudaStream_t st);
 cudaError_t launch_recover(const Plan& P, void* C, void* ws, int bi, int bj, cudaStream_t st);
 cudaError_t launch_inject(const Plan& P, void* C, const int64_t* rows, const int64_t* cols,
                           const int32_t* bits, int count, cudaStream_t st);

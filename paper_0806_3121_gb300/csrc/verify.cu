@@ -82,52 +82,88 @@ __device__ __forceinline__ bool is_flagged(double re, double rw, double te, doub
   return !(fabs(re) <= te && fabs(rw) <= tw);
 }
 
+__device__ __forceinline__ void col_taus(const CheckArgs& a, int64_t I, int64_t j, double& te,
+                                         double& tw) {
+  const double nb = a.nBcol[j];
+  te = a.s * nb * (a.f1c * a.nAblk[4 * I + 0] + a.f2c * a.nAblk[4 * I + 2]);
+  tw = a.s * nb * (a.f1c * a.nAblk[4 * I + 1] + a.f2c * a.nAblk[4 * I + 3]);
+}
+__device__ __forceinline__ void row_taus(const CheckArgs& a, int64_t i, int64_t J, double& te,
+                                         double& tw) {
+  const double na = a.nArow[i];
+  te = a.s * na * (a.f1r * a.nBblk[4 * J + 0] + a.f2r * a.nBblk[4 * J + 2]);
+  tw = a.s * na * (a.f1r * a.nBblk[4 * J + 1] + a.f2r * a.nBblk[4 * J + 3]);
+}
+
+// Observed block sums run in the element type of C: binary64 for a binary64
+// C, binary32 for a binary32 C (whose rounding the thresholds carry as u_sum).
+template <typename TC>
+__device__ __forceinline__ TC fma_t(TC a, TC b, TC c);
+template <>
+__device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return fma(a, b, c); }
+template <>
+__device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <typename TC>
+__device__ __forceinline__ TC warp_sum_t(TC v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // Residuals of column line (I, j).  Returns the non-finite count.
 template <typename TC>
 __device__ int col_line(const CheckArgs& a, int64_t I, int64_t j, double& re, double& rw,
                         double& te, double& tw) {
   const int64_t i0 = I * a.vb_r, i1 = min(i0 + (int64_t)a.vb_r, a.m);
-  const double sc = scalbn(1.0, -a.er);
-  double se = 0.0, sw = 0.0;
+  const TC sc = (TC)scalbn(1.0, -a.er);
+  const TC* C = static_cast<const TC*>(a.C);
+  TC se = 0, sw = 0;
   int nf = 0;
+  const TC* p = C + i0 * a.ldc + j;
+  const int len = (int)(i1 - i0);
 #pragma unroll 4
-  for (int64_t i = i0; i < i1; ++i) {
-    const double x = ld<TC>(a.C, i * a.ldc + j);
+  for (int t = 0; t < len; ++t) {
+    const TC x = p[(int64_t)t * a.ldc];
     se += x;
-    sw = fma((double)(i - i0 + 1) * sc, x, sw);
+    sw = fma_t<TC>((TC)(t + 1) * sc, x, sw);
     nf += isfinite(x) ? 0 : 1;
   }
-  re = se - a.E[(2 * I) * a.n + j];
-  rw = sw - a.E[(2 * I + 1) * a.n + j];
-  const double nb = a.nBcol[j];
-  te = a.s * nb * (a.f1c * a.nAblk[4 * I + 0] + a.f2c * a.nAblk[4 * I + 2]);
-  tw = a.s * nb * (a.f1c * a.nAblk[4 * I + 1] + a.f2c * a.nAblk[4 * I + 3]);
+  re = (double)se - a.E[(2 * I) * a.n + j];
+  rw = (double)sw - a.E[(2 * I + 1) * a.n + j];
+  col_taus(a, I, j, te, tw);
   return nf;
 }
 
-// Residuals of row line (i, J) computed by one warp; valid in every lane.
+// Residuals of row line (i, J) computed by one warp; the sums and the
+// non-finite count are valid in every lane, the residuals and thresholds in
+// lane 0 only (binary64 work done once per line).
 template <typename TC>
 __device__ int row_line_warp(const CheckArgs& a, int64_t i, int64_t J, double& re, double& rw,
                              double& te, double& tw) {
   const int lane = threadIdx.x & 31;
   const int64_t j0 = J * a.vb_c, j1 = min(j0 + (int64_t)a.vb_c, a.n);
-  const double sc = scalbn(1.0, -a.ec);
-  double se = 0.0, sw = 0.0;
+  const TC sc = (TC)scalbn(1.0, -a.ec);
+  const TC* C = static_cast<const TC*>(a.C);
+  TC se = 0, sw = 0;
   int nf = 0;
-  for (int64_t j = j0 + lane; j < j1; j += 32) {
-    const double x = ld<TC>(a.C, i * a.ldc + j);
+  const TC* p = C + i * a.ldc + j0;
+  const int len = (int)(j1 - j0);
+  for (int t = lane; t < len; t += 32) {
+    const TC x = p[t];
     se += x;
-    sw = fma((double)(j - j0 + 1) * sc, x, sw);
+    sw = fma_t<TC>((TC)(t + 1) * sc, x, sw);
     nf += isfinite(x) ? 0 : 1;
   }
-  se = warp_sum(se);
-  sw = warp_sum(sw);
+  se = warp_sum_t<TC>(se);
+  sw = warp_sum_t<TC>(sw);
   nf = warp_isum(nf);
-  re = se - a.F[i * a.Cc + 2 * J];
-  rw = sw - a.F[i * a.Cc + 2 * J + 1];
-  const double na = a.nArow[i];
-  te = a.s * na * (a.f1r * a.nBblk[4 * J + 0] + a.f2r * a.nBblk[4 * J + 2]);
-  tw = a.s * na * (a.f1r * a.nBblk[4 * J + 1] + a.f2r * a.nBblk[4 * J + 3]);
+  re = rw = te = tw = 0.0;
+  if (lane == 0) {
+    re = (double)se - a.F[i * a.Cc + 2 * J];
+    rw = (double)sw - a.F[i * a.Cc + 2 * J + 1];
+    row_taus(a, i, J, te, tw);
+  }
   return nf;
 }
 
@@ -165,6 +201,56 @@ __global__ void __launch_bounds__(kThreads) k_row_check(const CheckArgs a) {
   double re, rw, te, tw;
   const int nf = row_line_warp<TC>(a, i, J, re, rw, te, tw);
   if ((threadIdx.x & 31) != 0) return;
+  if (nf == 0 && !is_flagged(re, rw, te, tw)) return;
+  const int slot = atomicAdd(&a.cnt[kCntRowFlags], 1);
+  if (slot < kCapFlags) a.rowf[slot] = FlagEntry{(int32_t)i, (int32_t)J, nf, 0, re, rw};
+}
+
+// Column lines from the observed partial sums the product's epilogue wrote
+// (one per 128-row tile): obs[(tile*2 + 0|1)*n + j].  Verify blocks span whole
+// tiles.  A non-finite observed sum marks the line non-finite (the locate
+// step then scans C for it).
+__global__ void __launch_bounds__(kThreads) k_col_fused(const CheckArgs a, const float* obs,
+                                                        int64_t ntr) {
+  const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (j >= a.n) return;
+  const int64_t tpb = a.vb_r / 128;  // tiles per verify block
+  for (int64_t I = blockIdx.y; I < a.nvr; I += gridDim.y) {
+    const int64_t i0 = I * a.vb_r, i1 = min(i0 + (int64_t)a.vb_r, a.m);
+    if (touches_erased(a.erased, a.bs, a.bc, i0, i1, j, j + 1)) continue;
+    double se = 0.0, sw = 0.0;
+    for (int64_t tr = I * tpb; tr < min((I + 1) * tpb, ntr); ++tr) {
+      se += (double)obs[(tr * 2 + 0) * a.n + j];
+      sw += (double)obs[(tr * 2 + 1) * a.n + j];
+    }
+    const int nf = (isfinite(se) && isfinite(sw)) ? 0 : 1;
+    const double re = se - a.E[(2 * I) * a.n + j], rw = sw - a.E[(2 * I + 1) * a.n + j];
+    double te, tw;
+    col_taus(a, I, j, te, tw);
+    if (nf == 0 && !is_flagged(re, rw, te, tw)) continue;
+    const int slot = atomicAdd(&a.cnt[kCntColFlags], 1);
+    if (slot < kCapFlags) a.colf[slot] = FlagEntry{(int32_t)I, (int32_t)j, nf, 0, re, rw};
+  }
+}
+
+// Row lines from the per-row partial sums over column groups of g columns:
+// obs[(i*ngrp + group)*2 + 0|1].  One thread per (row, verify block).
+__global__ void __launch_bounds__(kThreads) k_row_fused(const CheckArgs a, const float* obs,
+                                                        int64_t g, int64_t ngrp) {
+  const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (t >= a.m * a.nvc) return;
+  const int64_t i = t / a.nvc, J = t % a.nvc;
+  const int64_t j0 = J * a.vb_c, j1 = min(j0 + (int64_t)a.vb_c, a.n);
+  if (touches_erased(a.erased, a.bs, a.bc, i, i + 1, j0, j1)) return;
+  double se = 0.0, sw = 0.0;
+  for (int64_t gr = j0 / g; gr < min(cdiv(j1, g), ngrp); ++gr) {
+    se += (double)obs[(i * ngrp + gr) * 2 + 0];
+    sw += (double)obs[(i * ngrp + gr) * 2 + 1];
+  }
+  const int nf = (isfinite(se) && isfinite(sw)) ? 0 : 1;
+  const double re = se - a.F[i * a.Cc + 2 * J], rw = sw - a.F[i * a.Cc + 2 * J + 1];
+  double te, tw;
+  row_taus(a, i, J, te, tw);
   if (nf == 0 && !is_flagged(re, rw, te, tw)) return;
   const int slot = atomicAdd(&a.cnt[kCntRowFlags], 1);
   if (slot < kCapFlags) a.rowf[slot] = FlagEntry{(int32_t)i, (int32_t)J, nf, 0, re, rw};
@@ -441,13 +527,22 @@ CheckArgs make_args(const Plan& P, void* C, void* ws) {
 }
 
 template <typename TC>
-cudaError_t verify_t(const Plan& P, void* C, void* ws, const Erased& er, cudaStream_t st) {
+cudaError_t verify_t(const Plan& P, void* C, void* ws, const Erased& er, bool reread,
+                     cudaStream_t st) {
   CheckArgs a = make_args(P, C, ws);
   a.erased = er;
   const int64_t m = P.d.m, n = P.d.n;
-  k_col_check<TC><<<dim3((unsigned)cdiv(n, kThreads), gy(P.nvr)), kThreads, 0, st>>>(
-      a, 0, n, 0, P.nvr, 0);
-  k_row_check<TC><<<(unsigned)cdiv(m * P.nvc * 32, kThreads), kThreads, 0, st>>>(a);
+  if (reread) {
+    k_col_check<TC><<<dim3((unsigned)cdiv(n, kThreads), gy(P.nvr)), kThreads, 0, st>>>(
+        a, 0, n, 0, P.nvr, 0);
+    k_row_check<TC><<<(unsigned)cdiv(m * P.nvc * 32, kThreads), kThreads, 0, st>>>(a);
+  } else {
+    const char* w = static_cast<const char*>(ws);
+    k_col_fused<<<dim3((unsigned)cdiv(n, kThreads), gy(P.nvr)), kThreads, 0, st>>>(
+        a, reinterpret_cast<const float*>(w + P.L.obs_col), P.ntr_obs);
+    k_row_fused<<<(unsigned)cdiv(m * P.nvc, kThreads), kThreads, 0, st>>>(
+        a, reinterpret_cast<const float*>(w + P.L.obs_row), P.g, P.ngrp);
+  }
   k_locate_correct<TC><<<1, kLocThreads, 0, st>>>(a);
   count_launches(3);
   return cudaGetLastError();
@@ -469,9 +564,45 @@ cudaError_t recover_t(const Plan& P, void* C, void* ws, int bi, int bj, cudaStre
 
 }  // namespace
 
-cudaError_t launch_verify(const Plan& P, void* C, void* ws, const Erased& er, cudaStream_t st) {
-  return P.d.dtype == ABFT_F64 ? verify_t<double>(P, C, ws, er, st)
-                               : verify_t<float>(P, C, ws, er, st);
+cudaError_t launch_verify(const Plan& P, void* C, void* ws, const Erased& er, bool reread,
+                          cudaStream_t st) {
+  return P.d.dtype == ABFT_F64 ? verify_t<double>(P, C, ws, er, true, st)
+                               : verify_t<float>(P, C, ws, er, reread, st);
+}
+
+namespace {
+struct InjList {
+  int32_t n, first, total, last;
+  InjectEntry e[64];
+};
+__global__ void k_set_inject(int32_t* hdr, const InjList L) {
+  InjectEntry* ent = reinterpret_cast<InjectEntry*>(reinterpret_cast<char*>(hdr) + 16);
+  const int t = threadIdx.x;
+  if (t < L.n) ent[L.first + t] = L.e[t];
+  if (L.last && t == 0) {
+    hdr[1] = L.total;
+    hdr[0] = kInjectMagic;
+  }
+}
+}  // namespace
+
+cudaError_t launch_set_inject(const Plan& P, void* ws, const int64_t* rows, const int64_t* cols,
+                              const int32_t* bits, int count, cudaStream_t st) {
+  int32_t* hdr = reinterpret_cast<int32_t*>(static_cast<char*>(ws) + P.L.inject);
+  int t0 = 0;
+  do {
+    InjList L{};
+    L.n = count - t0 < 64 ? count - t0 : 64;
+    L.first = t0;
+    L.total = count;
+    L.last = t0 + L.n >= count;
+    for (int t = 0; t < L.n; ++t)
+      L.e[t] = InjectEntry{(int32_t)rows[t0 + t], (int32_t)cols[t0 + t], bits[t0 + t], 0};
+    k_set_inject<<<1, 64, 0, st>>>(hdr, L);
+    count_launches(1);
+    t0 += L.n;
+  } while (t0 < count);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_recover(const Plan& P, void* C, void* ws, int bi, int bj, cudaStream_t st) {

@@ -36,9 +36,18 @@ F64_11264_GRID22 = Workload("f64_11264_grid22", "f64", 11264, 11264, 11264, 512,
                             dist="normal", n_flips=3, n_erased=1,
                             note="FP64 11264^3 as a 22x22 grid of 512-blocks (484 'processes'); "
                                  "one block erased to NaN plus 3 bit-flips in distinct blocks")
-BF16_16384 = Workload("bf16_16384", "bf16", 16384, 16384, 16384, 128, 128, dist="normal",
-                      note="BF16 16384^3, N(0,1) rounded to BF16, FP32 accumulate")
-WORKLOADS = {w.name: w for w in (F64_512, F64_11264_GRID22, BF16_16384)}
+# Smaller cases of the same kernels, for profiling captures that must stay a few GB.
+F64_4096_GRID8 = Workload("f64_4096_grid8", "f64", 4096, 4096, 4096, 512, 512, 8, 8,
+                          dist="normal", n_flips=3, n_erased=1,
+                          note="FP64 4096^3 as an 8x8 grid of 512-blocks (profiling size)")
+BF16_8192 = Workload("bf16_8192", "bf16", 8192, 8192, 8192, 256, 256, dist="normal", n_flips=3,
+                     note="BF16 8192^3 (profiling size)")
+# Verify blocks of 256: half the checksum tiles of 128-blocks at the same detection power
+# (the threshold is dominated by the sqrt(k) accumulation term).
+BF16_16384 = Workload("bf16_16384", "bf16", 16384, 16384, 16384, 256, 256, dist="normal",
+                      n_flips=3, note="BF16 16384^3, N(0,1) rounded to BF16, FP32 accumulate")
+WORKLOADS = {w.name: w for w in (F64_512, F64_11264_GRID22, F64_4096_GRID8, BF16_16384,
+                                 BF16_8192)}
 
 
 def rng(seed: int, stream: int = 0) -> np.random.Generator:

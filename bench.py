@@ -6,7 +6,8 @@ and B, the ABFT product (data + checksum tiles), bit-flips (and, with an erasure
 erased block) injected into C, detect / locate / correct, and the block rebuild.  The
 default workload is the paper's 484-process grid restated on one GPU: FP64
 m = n = k = 11264 as a 22 x 22 grid of 512 x 512 blocks.  The same run also measures the
-bf16 tensor-core workload (16384^3) and attaches it as "bf16_16384".
+bf16 tensor-core workloads (16384^3: bf16 inputs, and fp32 inputs in the split bf16x3
+product) and attaches them as "bf16_16384" and "bf16x3_16384".
 
 value       useful TFLOP/s (2mnk per step / step time), operands resident in HBM
 overhead    product-only and whole-step time over the checksum-free product of the same
@@ -214,8 +215,10 @@ def make_inputs(w, seed, dev):
         A_np, B_np = wl.operands(w, seed)
         return torch.from_numpy(A_np).to(dev), torch.from_numpy(B_np).to(dev), A_np, B_np
     g = torch.Generator(device=dev).manual_seed(seed)
-    A = torch.randn(w.m, w.k, generator=g, device=dev).to(torch.bfloat16)
-    B = torch.randn(w.k, w.n, generator=g, device=dev).to(torch.bfloat16)
+    A = torch.randn(w.m, w.k, generator=g, device=dev)
+    B = torch.randn(w.k, w.n, generator=g, device=dev)
+    if w.dtype == "bf16":
+        A, B = A.to(torch.bfloat16), B.to(torch.bfloat16)
     return A, B, None, None
 
 
@@ -316,7 +319,8 @@ def run_workload(w, args, dev, rank, world, secondary=False):
     pairs = max(2, min(args.steps, 3)) if not lp else 10
     t_plain, t_abft = [], []
     for _ in range(pairs):
-        t_plain.append(timed(lambda: abft.abft_gemm_plain(desc, A, B, C, stream=stream), 1))
+        t_plain.append(timed(lambda: abft.abft_gemm_plain(desc, A, B, C, ws=ws, stream=stream),
+                             1))
         t_abft.append(timed(lambda: abft.abft_gemm(desc, A, B, C, ws, stream=stream), 1))
     plain_ms = statistics.median(t_plain)
     abft_pair_ms = statistics.median(t_abft)
@@ -359,7 +363,8 @@ def run_workload(w, args, dev, rank, world, secondary=False):
 
     useful = 2.0 * w.m * w.n * w.k
     if lp:
-        kernel_flops = 2.0 * w.k * ((w.m + L.acs_rows) * w.n + w.m * L.bcs_cols)
+        nseg = 3 if w.dtype == "bf16x3" else 1  # split products are three bf16 products
+        kernel_flops = nseg * 2.0 * w.k * ((w.m + L.acs_rows) * w.n + w.m * L.bcs_cols)
         peak, peak_src = bf16_peak()
         roof = {"kernel": "k_gemm_bf16", "bound": "tensor", "peak_source": peak_src}
     else:
@@ -368,10 +373,11 @@ def run_workload(w, args, dev, rank, world, secondary=False):
         roof = {"kernel": "k_gemm_f64", "bound": "alu", "peak_source": peak_src}
     achieved = kernel_flops / (gemm_avg * 1e-3) / 1e12
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                 "traffic": TRAFFIC_BYTES[w.dtype], "algorithmic_flops_per_launch": kernel_flops})
+                 "traffic": TRAFFIC_BYTES.get(w.dtype), "algorithmic_flops_per_launch": kernel_flops})
     value = useful * world / (step_ms * 1e-3) / 1e12
     cfg = {"workload": w.name, "m": w.m, "n": w.n, "k": w.k, "verify_block": [w.vb_r, w.vb_c],
-           "dist": "N(0,1)" + (" rounded to bf16" if lp else ""),
+           "dist": "N(0,1)" + {"bf16": " rounded to bf16", "bf16x3": " in fp32, split into "
+                                "bf16 hi+lo"}.get(w.dtype, ""),
            "faults_per_step": (f"{w.n_erased} erased block + " if w.n_erased else "") +
                               f"{w.n_flips} exponent bit-flips in distinct blocks" +
                               (" of the accumulator outputs (epilogue), verified from the "
@@ -385,7 +391,7 @@ def run_workload(w, args, dev, rank, world, secondary=False):
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16" if lp else "f64", "data": "synthetic", "config": cfg,
+        "dtype": w.dtype, "data": "synthetic", "config": cfg,
         "overhead_pct": {
             "gemm_only": 100.0 * (abft_pair_ms / plain_ms - 1.0),
             "step_without_encode": 100.0 * ((step_ms - encode_ms) / plain_ms - 1.0),
@@ -421,10 +427,11 @@ def run_ours(args, rank, world):
     w = wl.WORKLOADS[args.workload]
     out = run_workload(w, args, dev, rank, world)
     if w.name == "f64_11264_grid22" and not args.no_secondary:
-        sec = run_workload(wl.WORKLOADS["bf16_16384"], args, dev, rank, world, secondary=True)
-        out["bf16_16384"] = {k: sec[k] for k in ("value", "unit", "ms_per_step", "overhead_pct",
-                                                 "times_ms", "useful_frac_of_peak", "roofline",
-                                                 "gpu_launches", "config")}
+        for name in ("bf16_16384", "bf16x3_16384"):
+            sec = run_workload(wl.WORKLOADS[name], args, dev, rank, world, secondary=True)
+            out[name] = {k: sec[k] for k in ("value", "unit", "ms_per_step", "overhead_pct",
+                                             "times_ms", "useful_frac_of_peak", "roofline",
+                                             "gpu_launches", "config")}
     if rank == 0:
         print(json.dumps(out), flush=True)
 

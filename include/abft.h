@@ -53,7 +53,8 @@ typedef enum {
 typedef enum {
   ABFT_F64 = 0,     /* A, B, C binary64; DFMA product, binary64 checksums          */
   ABFT_BF16 = 1,    /* A, B bfloat16; C binary32; tensor-core product, fp32 accum.  */
-  ABFT_BF16X3 = 2,  /* A, B binary32 split into bf16 hi+lo; C binary32             */
+  ABFT_BF16X3 = 2,  /* A, B binary32 split into bf16 hi+lo planes by abft_encode;
+                       product A_hi B_hi + A_hi B_lo + A_lo B_hi; C binary32        */
   ABFT_FP8_E4M3 = 3 /* A, B e4m3 with binary32 scales per 128x128 block; C binary32 */
 } abft_dtype;
 
@@ -109,7 +110,10 @@ typedef struct {
   size_t obs_col, obs_row;           /* fused observed partial sums (fp32)     */
   size_t inject;                     /* armed epilogue fault injections        */
   int32_t fused;                     /* 1: abft_gemm writes observed sums      */
-  int32_t pad0;
+  int32_t planes;                    /* bf16 planes per operand: 2 for BF16X3  */
+  size_t acs_plane, bcs_plane;       /* bytes from the hi to the lo plane      */
+  size_t op_a, op_b;                 /* BF16X3: hi/lo planes of A and B        */
+  int64_t op_a_ld, op_b_ld;          /* their leading dims (elements)          */
 } abft_ws_layout;
 
 /* Size of the caller-owned device workspace for `desc`.  Returns 0 for an
@@ -167,10 +171,12 @@ abft_status abft_set_epilogue_faults(const abft_desc* desc, void* ws, const int6
                                      void* stream);
 
 /* The same GEMM kernel with no checksum tiles: C = A B only.  This is the
- * checksum-free baseline the ABFT overhead is measured against.  ws unused
- * (may be NULL).  Asynchronous. */
+ * checksum-free baseline the ABFT overhead is measured against.  ws may be
+ * NULL except for ABFT_BF16X3, whose product reads the bf16 planes a
+ * preceding abft_encode wrote into ws.  Asynchronous. */
 abft_status abft_gemm_plain(const abft_desc* desc, const void* A, const void* B,
-                            const void* a_scale, const void* b_scale, void* C, void* stream);
+                            const void* a_scale, const void* b_scale, void* C, void* ws,
+                            void* stream);
 
 /* Detect, locate and correct (section 1 and section 2.2: the consistency of
  * (AB)_F detects, localizes and corrects errors in the output).  Checks every

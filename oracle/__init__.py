@@ -165,10 +165,16 @@ def units(dtype: str) -> dict:
     f64: everything in binary64.  bf16 / fp8 / bf16x3: the product accumulates in
     binary32 and C is stored in binary32 (no extra storage rounding); the checksum
     operand is fed to the tensor cores as a bf16 hi+lo pair (relative error 2^-17);
-    encode sums and the observed block sums of C run in binary32.
+    encode sums and the observed block sums of C run in binary32.  bf16x3 (binary32
+    inputs split into bf16 hi+lo, product A_hi B_hi + A_hi B_lo + A_lo B_hi) also carries
+    the split's deviation from the exact product as u_c.
     """
     if dtype == "f64":
         return dict(u_acc=U64, u_sum=U64, u_enc=U64, u_c=U64, u_cs=U64)
+    if dtype == "bf16x3":
+        # the split product drops A_lo B_lo and carries the hi+lo representation error of
+        # the binary32 inputs: C deviates from their exact product by ~2^-17 relative
+        return dict(u_acc=U32, u_sum=U32, u_enc=U32, u_c=2.0 ** -17, u_cs=2.0 ** -17)
     return dict(u_acc=U32, u_sum=U32, u_enc=U32, u_c=0.0, u_cs=2.0 ** -17)
 
 

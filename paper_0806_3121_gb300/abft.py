@@ -61,7 +61,9 @@ class WsLayout(ct.Structure):
                 ("bs", ct.c_int64), ("acs_ld", ct.c_int64), ("bcs_ld", ct.c_int64),
                 ("E16", ct.c_size_t), ("F16", ct.c_size_t), ("acs_rows", ct.c_int64),
                 ("bcs_cols", ct.c_int64), ("obs_col", ct.c_size_t), ("obs_row", ct.c_size_t),
-                ("inject", ct.c_size_t), ("fused", ct.c_int32), ("pad0", ct.c_int32)]
+                ("inject", ct.c_size_t), ("fused", ct.c_int32), ("planes", ct.c_int32),
+                ("acs_plane", ct.c_size_t), ("bcs_plane", ct.c_size_t), ("op_a", ct.c_size_t),
+                ("op_b", ct.c_size_t), ("op_a_ld", ct.c_int64), ("op_b_ld", ct.c_int64)]
 
 
 _lock = threading.Lock()
@@ -85,7 +87,7 @@ def load(path: str = LIB_PATH):
         lib.abft_encode.argtypes = [D, vp, vp, vp, vp, vp, vp]
         lib.abft_encode_noalloc.argtypes = [D, vp, vp, vp, vp, vp, vp]
         lib.abft_gemm.argtypes = [D, vp, vp, vp, vp, vp, vp, vp]
-        lib.abft_gemm_plain.argtypes = [D, vp, vp, vp, vp, vp, vp]
+        lib.abft_gemm_plain.argtypes = [D, vp, vp, vp, vp, vp, vp, vp]
         lib.abft_set_epilogue_faults.argtypes = [D, vp, vp, vp, vp, i32, vp]
         lib.abft_verify_correct.argtypes = [D, vp, vp, i32, vp, i32, vp, i32,
                                             ct.POINTER(ct.c_int32), vp]
@@ -165,9 +167,9 @@ def abft_gemm(desc, A, B, C, ws, a_scale=None, b_scale=None, stream=None):
                             _ptr(C), _ptr(ws), _stream(stream)))
 
 
-def abft_gemm_plain(desc, A, B, C, a_scale=None, b_scale=None, stream=None):
+def abft_gemm_plain(desc, A, B, C, a_scale=None, b_scale=None, ws=None, stream=None):
     _check(load().abft_gemm_plain(ct.byref(desc), _ptr(A), _ptr(B), _ptr(a_scale),
-                                  _ptr(b_scale), _ptr(C), _stream(stream)))
+                                  _ptr(b_scale), _ptr(C), _ptr(ws), _stream(stream)))
 
 
 def abft_verify_correct(desc, C, ws, erased=(), max_reports=1024, reread_C=1, stream=None):

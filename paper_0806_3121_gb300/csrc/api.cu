@@ -48,6 +48,9 @@ struct Units {
 Units units_for(int dtype) {
   const double u64 = ldexp(1.0, -53), u32 = ldexp(1.0, -24);
   if (dtype == ABFT_F64) return {u64, u64, u64, u64, u64};
+  // BF16X3: C also differs from the exact product of the fp32 inputs by the
+  // dropped A_lo B_lo term and the hi+lo representation (2^-17 relative).
+  if (dtype == ABFT_BF16X3) return {u32, u32, u32, ldexp(1.0, -17), ldexp(1.0, -17)};
   return {u32, u32, u32, 0.0, ldexp(1.0, -17)};
 }
 
@@ -74,9 +77,9 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
   if (d->flags != 0) return fail(ABFT_ERR_INVALID, "flags must be 0");
   if (!(d->tau_safety >= 0.0) || !isfinite(d->tau_safety))
     return fail(ABFT_ERR_INVALID, "tau_safety must be finite and >= 0");
-  if (d->dtype != ABFT_F64 && d->dtype != ABFT_BF16)
+  if (d->dtype != ABFT_F64 && d->dtype != ABFT_BF16 && d->dtype != ABFT_BF16X3)
     return fail(ABFT_ERR_UNSUPPORTED, "dtype %d not built yet", d->dtype);
-  if (d->dtype == ABFT_BF16 && (d->lda % 8 || d->ldb % 8))
+  if (d->dtype == ABFT_BF16 && (d->lda % 8 || d->ldb % 8))  // TMA rows of A and B
     return fail(ABFT_ERR_INVALID, "bf16 operands need lda and ldb multiples of 8 (16-byte rows)");
 
   Plan& p = *P;
@@ -110,21 +113,26 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
   abft_ws_layout& L = p.L;
   const size_t eb = operand_bytes(d->dtype);
   const bool lp = d->dtype != ABFT_F64;
-  // Encoded operand rows/columns: binary64 checksums for F64; for the
-  // tensor-core dtypes each fp32 checksum is a bf16 hi+lo pair (4 rows per
-  // verify block, 2 per block-checksum row), with 16-byte aligned rows.
-  L.acs_rows = lp ? 4 * p.nvr + 2 * p.bs : p.R;
-  L.bcs_cols = lp ? 4 * p.nvc : p.Cc;
+  const bool x3 = d->dtype == ABFT_BF16X3;
+  // Encoded operand rows/columns: binary64 checksums for F64.  bf16: each fp32
+  // checksum is a bf16 hi+lo pair, as separate rows (4 rows per verify block, 2
+  // per block-checksum row).  BF16X3: hi and lo planes of 2 rows per block
+  // (the split product combines them).  Rows are 16-byte aligned.
+  L.planes = x3 ? 2 : 1;
+  L.acs_rows = x3 ? p.R : (lp ? 4 * p.nvr + 2 * p.bs : p.R);
+  L.bcs_cols = x3 ? p.Cc : (lp ? 4 * p.nvc : p.Cc);
   L.acs_ld = lp ? (d->k + 7) / 8 * 8 : d->k;
   L.bcs_ld = lp ? (L.bcs_cols + 7) / 8 * 8 : p.Cc;
+  L.acs_plane = align256((size_t)L.acs_rows * L.acs_ld * eb);
+  L.bcs_plane = align256((size_t)d->k * L.bcs_ld * eb);
   size_t off = 0;
   auto region = [&](size_t bytes) {
     const size_t o = off;
     off = align256(off + bytes);
     return o;
   };
-  L.acs = region((size_t)L.acs_rows * L.acs_ld * eb);
-  L.bcs = region((size_t)d->k * L.bcs_ld * eb);
+  L.acs = region(L.acs_plane * L.planes);
+  L.bcs = region(L.bcs_plane * L.planes);
   L.E = region((size_t)p.R * d->n * 8);
   L.F = region((size_t)d->m * p.Cc * 8);
   L.nArow = region((size_t)d->m * 8);
@@ -136,6 +144,10 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
   L.obs_col = region(p.fused ? (size_t)p.ntr_obs * 2 * d->n * 4 : 0);
   L.obs_row = region(p.fused ? (size_t)d->m * p.ngrp * 2 * 4 : 0);
   L.inject = region(lp ? 16 + sizeof(InjectEntry) * kMaxInject : 0);
+  L.op_a_ld = x3 ? (d->k + 7) / 8 * 8 : 0;
+  L.op_b_ld = x3 ? (d->n + 7) / 8 * 8 : 0;
+  L.op_a = region(x3 ? 2 * align256((size_t)d->m * L.op_a_ld * 2) : 0);
+  L.op_b = region(x3 ? 2 * align256((size_t)d->k * L.op_b_ld * 2) : 0);
   L.fused = p.fused;
   L.scratch = off;
   L.scratch_bytes = scratch_bytes(p);
@@ -263,14 +275,14 @@ static abft_status gemm_common(const abft_desc* desc, const void* A, const void*
   abft_status st = make_plan(desc, &P);
   if (st != ABFT_OK) return st;
   if (is_empty(P)) return ABFT_OK;
-  if (!C || (checksums && !ws) || (P.d.k > 0 && (!A || !B)))
+  if (!C || ((checksums || P.d.dtype == ABFT_BF16X3) && !ws) || (P.d.k > 0 && (!A || !B)))
     return fail(ABFT_ERR_INVALID, "NULL pointer");
   cudaError_t e;
   if (P.d.dtype == ABFT_F64) {
     e = launch_gemm_f64(P, static_cast<const double*>(A), static_cast<const double*>(B),
                         static_cast<double*>(C), ws, checksums, static_cast<cudaStream_t>(stream));
   } else {
-    if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15)
+    if (P.d.dtype == ABFT_BF16 && ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15))
       return fail(ABFT_ERR_INVALID, "bf16 operands must be 16-byte aligned");
     e = launch_gemm_lp(P, A, B, static_cast<float*>(C), ws, checksums,
                        static_cast<cudaStream_t>(stream));
@@ -286,10 +298,11 @@ abft_status abft_gemm(const abft_desc* desc, const void* A, const void* B, const
 }
 
 abft_status abft_gemm_plain(const abft_desc* desc, const void* A, const void* B,
-                            const void* a_scale, const void* b_scale, void* C, void* stream) {
+                            const void* a_scale, const void* b_scale, void* C, void* ws,
+                            void* stream) {
   (void)a_scale;
   (void)b_scale;
-  return gemm_common(desc, A, B, C, nullptr, false, stream);
+  return gemm_common(desc, A, B, C, ws, false, stream);
 }
 
 abft_status abft_set_epilogue_faults(const abft_desc* desc, void* ws, const int64_t* rows,

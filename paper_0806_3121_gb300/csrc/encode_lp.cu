@@ -302,29 +302,265 @@ __global__ void k_lp_blk(const double* __restrict__ nvec, int64_t len, int vb, i
   nblk[4 * I + 3] = sqrt(q1);
 }
 
-// E[2I + x][j] = E16[4I + 2x][j] + E16[4I + 2x + 1][j];
-// E[2 nvr + t][j] = E16[4 nvr + 2t][j] + E16[4 nvr + 2t + 1][j]   (binary64)
-__global__ void k_fold_E(const float* __restrict__ E16, int64_t R, int64_t nvr, int64_t n,
+// ---------------- split bf16x3 (binary32 inputs)
+
+// Eight consecutive binary32 elements starting at column c (zeros past len).
+__device__ __forceinline__ void load8f(const float* row, int64_t c, int64_t len, float (&v)[8]) {
+  if (c + 8 <= len && ((reinterpret_cast<uintptr_t>(row + c) & 15) == 0)) {
+    const float4 a = *reinterpret_cast<const float4*>(row + c);
+    const float4 b = *reinterpret_cast<const float4*>(row + c + 4);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = (c + q < len) ? row[c + q] : 0.f;
+  }
+}
+
+// hi and lo bf16 planes of eight values, stored at hi + off and lo + off.
+__device__ __forceinline__ void store_split8(__nv_bfloat16* hi, __nv_bfloat16* lo, int64_t off,
+                                             const float (&v)[8]) {
+  __nv_bfloat16 h[8], l[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) split(v[q], h[q], l[q]);
+  store8(hi + off, h);
+  store8(lo + off, l);
+}
+
+// A: hi/lo planes (m x ldk), column checksums of A per verify block from the
+// binary32 values (rows 2I, 2I+1 of the acs hi/lo planes), per-row partial
+// sums of squares and checksum-norm partials.  CTA = 2048 columns x a block.
+__global__ void __launch_bounds__(kThreads) k_x3A_cols(const float* __restrict__ A, int64_t lda,
+                                                       int64_t m, int64_t k, int vb, int e,
+                                                       __nv_bfloat16* __restrict__ ahi,
+                                                       __nv_bfloat16* __restrict__ alo,
+                                                       __nv_bfloat16* __restrict__ chi,
+                                                       __nv_bfloat16* __restrict__ clo,
+                                                       int64_t ldk, float* __restrict__ rowpart,
+                                                       int64_t nchr, double* __restrict__ part,
+                                                       int64_t nch) {
+  __shared__ double sh[kThreads / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c0 = (int64_t)blockIdx.x * kColsPerCta + 8 * threadIdx.x;
+  const int64_t nvb = cdiv(m, vb);
+  const float sc = scalbnf(1.0f, -e);
+  for (int64_t I = blockIdx.y; I < nvb; I += gridDim.y) {
+    const int64_t i0 = I * vb, i1 = min(i0 + (int64_t)vb, m);
+    float se[8], sw[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) se[q] = sw[q] = 0.f;
+    for (int64_t i = i0; i < i1; ++i) {
+      float v[8];
+      load8f(A + i * lda, c0, k, v);
+      if (c0 < ldk) store_split8(ahi, alo, i * ldk + c0, v);
+      const float w = (float)(i - i0 + 1) * sc;
+      float sq = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        se[q] += v[q];
+        sw[q] = fmaf(w, v[q], sw[q]);
+        sq = fmaf(v[q], v[q], sq);
+      }
+      sq = warp_sumf(sq);
+      const int64_t rc = (int64_t)blockIdx.x * (kThreads / 32) + warp;
+      if (lane == 0 && rc < nchr) rowpart[i * nchr + rc] = sq;
+    }
+    double q0 = 0.0, q1 = 0.0;
+    if (c0 < ldk) {
+      store_split8(chi, clo, (2 * I) * ldk + c0, se);
+      store_split8(chi, clo, (2 * I + 1) * ldk + c0, sw);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        q0 += (double)se[q] * se[q];
+        q1 += (double)sw[q] * sw[q];
+      }
+    }
+    const double t0 = block_sum(q0, sh);
+    if (threadIdx.x == 0) part[(2 * I) * nch + blockIdx.x] = t0;
+    const double t1 = block_sum(q1, sh);
+    if (threadIdx.x == 0) part[(2 * I + 1) * nch + blockIdx.x] = t1;
+  }
+}
+
+// Block checksum rows S_A[t] = sum_I A[I*bs + t] into rows 2 nvr + t of the planes.
+__global__ void __launch_bounds__(kThreads) k_x3A_block(const float* __restrict__ A, int64_t lda,
+                                                        int64_t k, int p, int64_t bs,
+                                                        __nv_bfloat16* __restrict__ shi,
+                                                        __nv_bfloat16* __restrict__ slo,
+                                                        int64_t ldk) {
+  const int64_t l = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (l >= k) return;
+  for (int64_t t = blockIdx.y; t < bs; t += gridDim.y) {
+    float s = 0.f;
+    for (int I = 0; I < p; ++I) s += A[(I * bs + t) * lda + l];
+    __nv_bfloat16 h, lo;
+    split(s, h, lo);
+    shi[t * ldk + l] = h;
+    slo[t * ldk + l] = lo;
+  }
+}
+
+// B: hi/lo planes (k x ldn), row checksums per verify column block (columns
+// 2J, 2J+1 of the bcs hi/lo planes), per-column partial sums of squares and
+// checksum-norm partials.  Verify blocks of 8 .. 256 columns (power of two).
+__global__ void __launch_bounds__(kThreads) k_x3B_rows(const float* __restrict__ B, int64_t ldb,
+                                                       int64_t k, int64_t n, int vb, int e,
+                                                       __nv_bfloat16* __restrict__ bhi,
+                                                       __nv_bfloat16* __restrict__ blo,
+                                                       int64_t ldn,
+                                                       __nv_bfloat16* __restrict__ chi,
+                                                       __nv_bfloat16* __restrict__ clo,
+                                                       int64_t ldcs, float* __restrict__ colpart,
+                                                       double* __restrict__ part, int64_t nch) {
+  const int lane = threadIdx.x & 31;
+  const int64_t c0 = (int64_t)blockIdx.x * kColsPerCta + 8 * threadIdx.x;
+  const int64_t l0 = (int64_t)blockIdx.y * kRowsPerCtaB, l1 = min(l0 + kRowsPerCtaB, k);
+  const int seg = vb / 8;
+  const bool leader = (lane % seg) == 0 && c0 < n;
+  const int64_t J = c0 / vb;
+  const float sc = scalbnf(1.0f, -e);
+  float wq[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) wq[q] = (float)((c0 + q) % vb + 1) * sc;
+  float cs[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) cs[q] = 0.f;
+  double q0 = 0.0, q1 = 0.0;
+  for (int64_t l = l0; l < l1; ++l) {
+    float v[8];
+    load8f(B + l * ldb, c0, n, v);
+    if (c0 < ldn) store_split8(bhi, blo, l * ldn + c0, v);
+    float se = 0.f, sw = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      se += v[q];
+      sw = fmaf(wq[q], v[q], sw);
+      cs[q] = fmaf(v[q], v[q], cs[q]);
+    }
+    for (int o = seg >> 1; o > 0; o >>= 1) {
+      se += __shfl_xor_sync(0xffffffffu, se, o);
+      sw += __shfl_xor_sync(0xffffffffu, sw, o);
+    }
+    if (leader) {
+      __nv_bfloat16 h, lo;
+      split(se, h, lo);
+      chi[l * ldcs + 2 * J] = h;
+      clo[l * ldcs + 2 * J] = lo;
+      split(sw, h, lo);
+      chi[l * ldcs + 2 * J + 1] = h;
+      clo[l * ldcs + 2 * J + 1] = lo;
+      q0 += (double)se * se;
+      q1 += (double)sw * sw;
+    }
+  }
+  if (leader) {
+    part[(2 * J) * nch + blockIdx.y] = q0;
+    part[(2 * J + 1) * nch + blockIdx.y] = q1;
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    if (c0 + q < n) colpart[blockIdx.y * n + c0 + q] = cs[q];
+}
+
+// Any verify block size: planes and column partials by one kernel, row
+// checksums by one warp per (J, 128 rows).
+__global__ void __launch_bounds__(kThreads) k_x3B_split(const float* __restrict__ B, int64_t ldb,
+                                                        int64_t k, int64_t n,
+                                                        __nv_bfloat16* __restrict__ bhi,
+                                                        __nv_bfloat16* __restrict__ blo,
+                                                        int64_t ldn, float* __restrict__ colpart) {
+  const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (j >= ldn) return;
+  const int64_t nch = cdiv(k, kRowsPerCtaB);
+  for (int64_t c = blockIdx.y; c < nch; c += gridDim.y) {
+    const int64_t l0 = c * kRowsPerCtaB, l1 = min(l0 + kRowsPerCtaB, k);
+    float s = 0.f;
+    for (int64_t l = l0; l < l1; ++l) {
+      const float b = j < n ? B[l * ldb + j] : 0.f;
+      __nv_bfloat16 h, lo;
+      split(b, h, lo);
+      bhi[l * ldn + j] = h;
+      blo[l * ldn + j] = lo;
+      s = fmaf(b, b, s);
+    }
+    if (j < n) colpart[c * n + j] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_x3B_rows_any(const float* __restrict__ B,
+                                                           int64_t ldb, int64_t k, int64_t n,
+                                                           int vb, int e,
+                                                           __nv_bfloat16* __restrict__ chi,
+                                                           __nv_bfloat16* __restrict__ clo,
+                                                           int64_t ldcs,
+                                                           double* __restrict__ part,
+                                                           int64_t nch) {
+  const int lane = threadIdx.x & 31;
+  const int64_t chunk = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+  if (chunk >= nch) return;
+  const int64_t nvb = cdiv(n, vb);
+  const float sc = scalbnf(1.0f, -e);
+  for (int64_t J = blockIdx.y; J < nvb; J += gridDim.y) {
+    const int64_t j0 = J * vb, j1 = min(j0 + (int64_t)vb, n);
+    const int64_t l0 = chunk * kRowsPerCtaB, l1 = min(l0 + kRowsPerCtaB, k);
+    double q0 = 0.0, q1 = 0.0;
+    for (int64_t l = l0; l < l1; ++l) {
+      float se = 0.f, sw = 0.f;
+      for (int64_t j = j0 + lane; j < j1; j += 32) {
+        const float b = B[l * ldb + j];
+        se += b;
+        sw = fmaf((float)(j - j0 + 1) * sc, b, sw);
+      }
+      se = warp_sumf(se);
+      sw = warp_sumf(sw);
+      if (lane == 0) {
+        __nv_bfloat16 h, lo;
+        split(se, h, lo);
+        chi[l * ldcs + 2 * J] = h;
+        clo[l * ldcs + 2 * J] = lo;
+        split(sw, h, lo);
+        chi[l * ldcs + 2 * J + 1] = h;
+        clo[l * ldcs + 2 * J + 1] = lo;
+      }
+      q0 += (double)se * se;
+      q1 += (double)sw * sw;
+    }
+    if (lane == 0) {
+      part[(2 * J) * nch + chunk] = q0;
+      part[(2 * J + 1) * nch + chunk] = q1;
+    }
+  }
+}
+
+// E[r][j] = sum_{p < npc} E16[npc r + p][j]: the products of the npc pieces of
+// each checksum row (bf16: hi and lo rows, npc = 2; split bf16x3: npc = 1),
+// added in binary64.
+__global__ void k_fold_E(const float* __restrict__ E16, int64_t R, int npc, int64_t n,
                          double* __restrict__ E) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   for (int64_t r = blockIdx.y; r < R; r += gridDim.y) {
-    // output row r takes pieces 2r and 2r + 1 in both parts of the layout
-    const int64_t src = 2 * r;
-    E[r * n + j] = (double)E16[src * n + j] + (double)E16[(src + 1) * n + j];
+    double v = 0.0;
+    for (int p = 0; p < npc; ++p) v += (double)E16[(npc * r + p) * n + j];
+    E[r * n + j] = v;
   }
 }
 
-// F[i][2J + x] = F16[i][4J + 2x] + F16[i][4J + 2x + 1]   (binary64)
+// F[i][c] = sum_{p < npc} F16[i][npc c + p]   (binary64)
 __global__ void k_fold_F(const float* __restrict__ F16, int64_t m, int64_t Cc, int64_t C16,
-                         double* __restrict__ F) {
+                         int npc, double* __restrict__ F) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= m * Cc) return;
   const int64_t i = t / Cc, c = t % Cc;
-  F[i * Cc + c] = (double)F16[i * C16 + 2 * c] + (double)F16[i * C16 + 2 * c + 1];
+  double v = 0.0;
+  for (int p = 0; p < npc; ++p) v += (double)F16[i * C16 + npc * c + p];
+  F[i * Cc + c] = v;
 }
 
 unsigned gy(int64_t v) { return (unsigned)(v < 65535 ? v : 65535); }
+
+// bf16 elements in a 256-byte aligned plane of `elems` elements.
+int64_t align_elems(int64_t elems) { return (elems * 2 + 255) / 256 * 128; }
 
 }  // namespace
 
@@ -365,9 +601,47 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, void
   float* rowpart = reinterpret_cast<float*>(partB + 2 * P.nvc * nchB);
   float* colpart = rowpart + d.m * nchr;
   const bool fastB = d.vb_cols >= 8 && d.vb_cols <= 256 && (d.vb_cols & (d.vb_cols - 1)) == 0;
-  if (P.L.bcs_ld > P.L.bcs_cols)
-    cudaMemset2DAsync(bcs + P.L.bcs_cols, P.L.bcs_ld * 2, 0, (P.L.bcs_ld - P.L.bcs_cols) * 2, d.k,
-                      st);
+  for (int pl = 0; pl < P.L.planes; ++pl)
+    if (P.L.bcs_ld > P.L.bcs_cols)
+      cudaMemset2DAsync(reinterpret_cast<char*>(bcs) + pl * P.L.bcs_plane + P.L.bcs_cols * 2,
+                        P.L.bcs_ld * 2, 0, (P.L.bcs_ld - P.L.bcs_cols) * 2, d.k, st);
+  if (d.dtype == ABFT_BF16X3) {
+    const float* Af = static_cast<const float*>(Av);
+    const float* Bf = static_cast<const float*>(Bv);
+    auto* ahi = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_a);
+    auto* alo = ahi + align_elems(d.m * P.L.op_a_ld);
+    auto* bhi = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_b);
+    auto* blo = bhi + align_elems(d.k * P.L.op_b_ld);
+    auto* chi = acs;
+    auto* clo = reinterpret_cast<__nv_bfloat16*>(w + P.L.acs + P.L.acs_plane);
+    auto* bchi = bcs;
+    auto* bclo = reinterpret_cast<__nv_bfloat16*>(w + P.L.bcs + P.L.bcs_plane);
+    k_x3A_cols<<<dim3((unsigned)nchA, gy(P.nvr)), kThreads, 0, st>>>(
+        Af, d.lda, d.m, d.k, d.vb_rows, P.er, ahi, alo, chi, clo, P.L.acs_ld, rowpart, nchr,
+        partA, nchA);
+    if (P.bs > 0)
+      k_x3A_block<<<dim3((unsigned)cdiv(d.k, kThreads), gy(P.bs)), kThreads, 0, st>>>(
+          Af, d.lda, d.k, d.grid_p, P.bs, chi + 2 * P.nvr * P.L.acs_ld,
+          clo + 2 * P.nvr * P.L.acs_ld, P.L.acs_ld);
+    k_lp_norms<<<(unsigned)cdiv(d.m, 128), 128, 0, st>>>(rowpart, d.m, nchr, nchr, 1, nArow);
+    k_lp_blk<<<(unsigned)cdiv(P.nvr, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA,
+                                                         nchA, nAblk);
+    if (fastB) {
+      k_x3B_rows<<<dim3((unsigned)cdiv(P.L.op_b_ld, kColsPerCta), (unsigned)nchB), kThreads, 0,
+                   st>>>(Bf, d.ldb, d.k, d.n, d.vb_cols, P.ec, bhi, blo, P.L.op_b_ld, bchi, bclo,
+                         P.L.bcs_ld, colpart, partB, nchB);
+    } else {
+      k_x3B_split<<<dim3((unsigned)cdiv(P.L.op_b_ld, kThreads), gy(nchB)), kThreads, 0, st>>>(
+          Bf, d.ldb, d.k, d.n, bhi, blo, P.L.op_b_ld, colpart);
+      k_x3B_rows_any<<<dim3((unsigned)cdiv(nchB, kThreads / 32), gy(P.nvc)), kThreads, 0, st>>>(
+          Bf, d.ldb, d.k, d.n, d.vb_cols, P.ec, bchi, bclo, P.L.bcs_ld, partB, nchB);
+    }
+    k_lp_norms<<<(unsigned)cdiv(d.n, 128), 128, 0, st>>>(colpart, d.n, nchB, 1, d.n, nBcol);
+    k_lp_blk<<<(unsigned)cdiv(P.nvc, 128), 128, 0, st>>>(nBcol, d.n, d.vb_cols, P.ec, partB,
+                                                         nchB, nBblk);
+    count_launches(6 + (P.bs > 0 ? 1 : 0) + (fastB ? 0 : 1));
+    return cudaGetLastError();
+  }
   k_lpA_cols<<<dim3((unsigned)nchA, gy(P.nvr)), kThreads, 0, st>>>(
       A, d.lda, d.m, d.k, d.vb_rows, P.er, acs, P.L.acs_ld, rowpart, nchr, partA, nchA);
   if (P.bs > 0)
@@ -404,14 +678,33 @@ cudaError_t launch_gemm_lp(const Plan& P, const void* A, const void* B, float* C
     }
     return e;
   }
-  cudaError_t e = launch_gemm_bf16(P, A, B, C, ws, checksums, st);
+  TcOperands op{};
+  if (d.dtype == ABFT_BF16X3) {
+    const auto* ahi = reinterpret_cast<const __nv_bfloat16*>(w + P.L.op_a);
+    const auto* bhi = reinterpret_cast<const __nv_bfloat16*>(w + P.L.op_b);
+    op.a[0] = ahi;
+    op.a[1] = ahi + align_elems(d.m * P.L.op_a_ld);
+    op.b[0] = bhi;
+    op.b[1] = bhi + align_elems(d.k * P.L.op_b_ld);
+    op.lda = P.L.op_a_ld;
+    op.ldb = P.L.op_b_ld;
+    op.nseg = 3;
+  } else {
+    op.a[0] = op.a[1] = A;
+    op.b[0] = op.b[1] = B;
+    op.lda = d.lda;
+    op.ldb = d.ldb;
+    op.nseg = 1;
+  }
+  cudaError_t e = launch_gemm_bf16(P, op, C, ws, checksums, st);
   if (e != cudaSuccess || !checksums) return e;
+  const int npc = d.dtype == ABFT_BF16X3 ? 1 : 2;
   const float* E16 = reinterpret_cast<const float*>(w + P.L.E16);
   const float* F16 = reinterpret_cast<const float*>(w + P.L.F16);
   double* E = reinterpret_cast<double*>(w + P.L.E);
   double* F = reinterpret_cast<double*>(w + P.L.F);
-  k_fold_E<<<dim3((unsigned)cdiv(d.n, 256), gy(P.R)), 256, 0, st>>>(E16, P.R, P.nvr, d.n, E);
-  k_fold_F<<<(unsigned)cdiv(d.m * P.Cc, 256), 256, 0, st>>>(F16, d.m, P.Cc, P.L.bcs_cols, F);
+  k_fold_E<<<dim3((unsigned)cdiv(d.n, 256), gy(P.R)), 256, 0, st>>>(E16, P.R, npc, d.n, E);
+  k_fold_F<<<(unsigned)cdiv(d.m * P.Cc, 256), 256, 0, st>>>(F16, d.m, P.Cc, P.L.bcs_cols, npc, F);
   count_launches(2);
   return cudaGetLastError();
 }

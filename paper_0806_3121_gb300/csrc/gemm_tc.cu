@@ -39,8 +39,17 @@ constexpr int GROUP_M = 16;                        // tile rows per raster group
 constexpr uint32_t OBS_BYTES = 4 * BN * 2 * 4;     // per-warp column partials (e, w)
 constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + OBS_BYTES + 256;
 
+// Tensor maps of the operands: [0] = single / hi plane, [1] = lo plane.  The
+// K loop runs over nseg segments of the k dimension; segment s reads A plane
+// (s == 2) and B plane (s == 1), so nseg = 3 accumulates
+// A_hi B_hi + A_hi B_lo + A_lo B_hi (split bf16x3) and nseg = 1 is plain bf16.
+struct TcMaps {
+  CUtensorMap a[2], acs[2], b[2], bcs[2];
+};
+
 struct TcArgs {
   int64_t m, n, k, R16, C16;
+  int nseg;
   int ntm, ntn, ntr, ntc;  // data tile rows/cols, checksum tile rows/cols (0 in plain mode)
   int64_t t_data, t_total;
   float* C;
@@ -136,9 +145,7 @@ __device__ __forceinline__ void transpose_reduce(float (&v)[32], int lane) {
 __device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_bf16(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tAcs,
-                const __grid_constant__ CUtensorMap tB, const __grid_constant__ CUtensorMap tBcs,
-                const TcArgs g) {
+    k_gemm_bf16(const __grid_constant__ TcMaps M, const TcArgs g) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -167,10 +174,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::mbar_init(drain, 1);
     *abort = 0;
     tc::fence_barrier_init();
-    tc::prefetch_tmap(&tA);
-    tc::prefetch_tmap(&tAcs);
-    tc::prefetch_tmap(&tB);
-    tc::prefetch_tmap(&tBcs);
+    for (int pl = 0; pl < 2; ++pl) {
+      tc::prefetch_tmap(&M.a[pl]);
+      tc::prefetch_tmap(&M.acs[pl]);
+      tc::prefetch_tmap(&M.b[pl]);
+      tc::prefetch_tmap(&M.bcs[pl]);
+    }
   }
   if (warp == 1) {
     tc::tmem_alloc(tc::smem_addr(tmem_slot), TMEM_COLS);
@@ -181,6 +190,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
   const int64_t nkb = (g.k + BK - 1) / BK;
+  const int64_t nkt = nkb * g.nseg;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -190,9 +200,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       int64_t issued = 0;  // stages filled and not known to be consumed
       for (int64_t t = blockIdx.x; t < g.t_total && !*abort; t += gridDim.x) {
         const Tile T = decode(t, g);
-        const CUtensorMap* ma = T.kind == 1 ? &tAcs : &tA;
-        const CUtensorMap* mb = T.kind == 2 ? &tBcs : &tB;
-        for (int64_t kb = 0; kb < nkb; ++kb) {
+        for (int64_t kt = 0; kt < nkt; ++kt) {
+          const int seg = (int)(kt / nkb);
+          const int64_t kb = kt - (int64_t)seg * nkb;
+          const CUtensorMap* ma = T.kind == 1 ? &M.acs[seg == 2] : &M.a[seg == 2];
+          const CUtensorMap* mb = T.kind == 2 ? &M.bcs[seg == 1] : &M.b[seg == 1];
           if (!tc::wait(empty(s), ph ^ 1, abort)) break;
           const uint32_t sa = tc::smem_addr(smem + s * STAGE_BYTES);
           tc::mbar_arrive_expect_tx(full(s), STAGE_BYTES);
@@ -225,7 +237,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::fence_after_sync();
         const uint32_t d = tmem + acc * BN;
         bool ok = true;
-        for (int64_t kb = 0; kb < nkb; ++kb) {
+        for (int64_t kb = 0; kb < nkt; ++kb) {
           if (!tc::wait(full(s), ph, abort)) { ok = false; break; }
           tc::fence_after_sync();
           const uint32_t sa = tc::smem_addr(smem + s * STAGE_BYTES);
@@ -426,23 +438,26 @@ cudaError_t consume_tc_timeout(cudaStream_t st, bool* timed_out) {
   return e;
 }
 
-cudaError_t launch_gemm_bf16(const Plan& P, const void* A, const void* B, float* C, void* ws,
+cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void* ws,
                              bool checksums, cudaStream_t st) {
   cudaError_t e = get_encoder();
   if (e != cudaSuccess) return e;
   const abft_desc& d = P.d;
   const char* w = static_cast<const char*>(ws);
-  CUtensorMap mA, mAcs, mB, mBcs;
-  const void* acs = checksums ? w + P.L.acs : A;
-  const void* bcs = checksums ? w + P.L.bcs : B;
   const int64_t R16 = checksums ? P.L.acs_rows : 0, C16 = checksums ? P.L.bcs_cols : 0;
-  if (!make_map(&mA, A, d.m, d.k, d.lda, 64, BM) ||
-      !make_map(&mAcs, acs, R16, d.k, checksums ? P.L.acs_ld : d.lda, 64, BM) ||
-      !make_map(&mB, B, d.k, d.n, d.ldb, 64, BK) ||
-      !make_map(&mBcs, bcs, d.k, C16, checksums ? P.L.bcs_ld : d.ldb, 64, BK))
-    return cudaErrorInvalidValue;
+  TcMaps M;
+  for (int pl = 0; pl < 2; ++pl) {
+    const void* acs = checksums ? w + P.L.acs + pl * P.L.acs_plane : op.a[0];
+    const void* bcs = checksums ? w + P.L.bcs + pl * P.L.bcs_plane : op.b[0];
+    if (!make_map(&M.a[pl], op.a[pl], d.m, d.k, op.lda, 64, BM) ||
+        !make_map(&M.acs[pl], acs, R16, d.k, checksums ? P.L.acs_ld : op.lda, 64, BM) ||
+        !make_map(&M.b[pl], op.b[pl], d.k, d.n, op.ldb, 64, BK) ||
+        !make_map(&M.bcs[pl], bcs, d.k, C16, checksums ? P.L.bcs_ld : op.ldb, 64, BK))
+      return cudaErrorInvalidValue;
+  }
   TcArgs g{};
   g.m = d.m; g.n = d.n; g.k = d.k; g.R16 = R16; g.C16 = C16;
+  g.nseg = op.nseg;
   g.ntm = (int)cdiv(d.m, BM);
   g.ntn = (int)cdiv(d.n, BN);
   g.ntr = checksums ? (int)cdiv(R16, BM) : 0;
@@ -474,7 +489,7 @@ cudaError_t launch_gemm_bf16(const Plan& P, const void* A, const void* B, float*
   if (e != cudaSuccess) return e;
   const int grid = (int)std::min<int64_t>(g.t_total, num_sms());
   if (grid == 0) return cudaSuccess;
-  k_gemm_bf16<<<grid, kThreads, SMEM_BYTES, st>>>(mA, mAcs, mB, mBcs, g);
+  k_gemm_bf16<<<grid, kThreads, SMEM_BYTES, st>>>(M, g);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -102,7 +102,15 @@ cudaError_t launch_encode_lp(const Plan& P, const void* A, const void* B, void* 
 size_t lp_part_bytes(const Plan& P);
 cudaError_t launch_gemm_lp(const Plan& P, const void* A, const void* B, float* C, void* ws,
                            bool checksums, cudaStream_t st);
-cudaError_t launch_gemm_bf16(const Plan& P, const void* A, const void* B, float* C, void* ws,
+// Operands of the tensor-core product: bf16 planes [0] (single or hi) and [1]
+// (lo), K-major A (ld lda) and N-major B (ld ldb), nseg = 1 (bf16) or 3 (split).
+struct TcOperands {
+  const void* a[2];
+  const void* b[2];
+  int64_t lda, ldb;
+  int nseg;
+};
+cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void* ws,
                              bool checksums, cudaStream_t st);
 cudaError_t tc_timeout_flag(int** dev_ptr);
 cudaError_t consume_tc_timeout(cudaStream_t st, bool* timed_out);

@@ -46,8 +46,13 @@ BF16_8192 = Workload("bf16_8192", "bf16", 8192, 8192, 8192, 256, 256, dist="norm
 # (the threshold is dominated by the sqrt(k) accumulation term).
 BF16_16384 = Workload("bf16_16384", "bf16", 16384, 16384, 16384, 256, 256, dist="normal",
                       n_flips=3, note="BF16 16384^3, N(0,1) rounded to BF16, FP32 accumulate")
+BF16X3_16384 = Workload("bf16x3_16384", "bf16x3", 16384, 16384, 16384, 256, 256,
+                        dist="normal", n_flips=3,
+                        note="FP32 16384^3 inputs N(0,1), split bf16x3 product, FP32 accumulate")
+BF16X3_8192 = Workload("bf16x3_8192", "bf16x3", 8192, 8192, 8192, 256, 256, dist="normal",
+                       n_flips=3, note="split bf16x3 8192^3 (profiling size)")
 WORKLOADS = {w.name: w for w in (F64_512, F64_11264_GRID22, F64_4096_GRID8, BF16_16384,
-                                 BF16_8192)}
+                                 BF16_8192, BF16X3_16384, BF16X3_8192)}
 
 
 def rng(seed: int, stream: int = 0) -> np.random.Generator:

@@ -106,9 +106,6 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
   p.ngrp = d->n > 0 ? cdiv(d->n, p.g) : 0;
   p.ntr_obs = d->m > 0 ? cdiv(d->m, 128) : 0;
 
-  // Row tiles of the product grid (64 rows each, data then checksum rows).
-  if (cdiv(d->m, 64) + cdiv(p.R, 64) > 65535)
-    return fail(ABFT_ERR_INVALID, "too many rows for the tile grid (m + checksum rows)");
 
   abft_ws_layout& L = p.L;
   const size_t eb = operand_bytes(d->dtype);

@@ -8,9 +8,9 @@
 // Memory traffic is ~(1/64 + 1/64) words per FMA, far below HBM and L2
 // bandwidth at this FMA rate.
 //
-// Tiles are scheduled as one grid: data tiles first, then whole tiles of
-// checksum rows (acs, writing E) and checksum columns (bcs, writing F); the
-// corner (acs x bcs) is not computed.  Each output element is one FMA chain
+// Tiles are scheduled as one 1-D grid in a grouped order (see decode_f64):
+// data tiles, whole tiles of checksum rows (acs, writing E) and checksum
+// columns (bcs, writing F); the corner (acs x bcs) is not computed.  Each output element is one FMA chain
 // over k in increasing order.
 #include "internal.cuh"
 
@@ -18,6 +18,8 @@ namespace abft {
 namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, kThreads = 256;
+
+constexpr int GROUP_M = 16;  // tile rows per raster group
 
 struct GemmArgs {
   const double* A;
@@ -29,12 +31,43 @@ struct GemmArgs {
   double* F;
   int64_t lda, ldb, ldc, m, n, k, R, Cc;
   int tm, tn;  // data tiles along rows / columns
+  int tr, tc;  // checksum tiles along rows / columns (0 for the plain product)
 };
 
+// Linear tile index -> (tile row, tile column), tile rows >= tm being checksum
+// rows and tile columns >= tn checksum columns.  Groups of GROUP_M data tile
+// rows run column by column; checksum tile rows are dealt round-robin to the
+// groups and checksum tile columns follow each group's data columns, so
+// consecutive CTAs share the A and B panels in L2.
+__device__ __forceinline__ void decode_f64(int64_t t, const GemmArgs& g, int& ty, int& tx) {
+  const int64_t ngr = (g.tm + GROUP_M - 1) / GROUP_M;
+  int64_t off = 0;
+  for (int64_t G = 0; G < ngr; ++G) {
+    const int64_t gd = min((int64_t)GROUP_M, (int64_t)g.tm - G * GROUP_M);
+    const int64_t nr = G < g.tr ? (g.tr - G + ngr - 1) / ngr : 0;
+    const int64_t part1 = (gd + nr) * g.tn, part2 = gd * g.tc;
+    if (t < off + part1 + part2) {
+      int64_t u = t - off;
+      if (u < part1) {
+        const int64_t ri = u % (gd + nr);
+        tx = (int)(u / (gd + nr));
+        ty = ri < gd ? (int)(G * GROUP_M + ri) : (int)(g.tm + G + (ri - gd) * ngr);
+      } else {
+        u -= part1;
+        tx = (int)(g.tn + u / gd);
+        ty = (int)(G * GROUP_M + u % gd);
+      }
+      return;
+    }
+    off += part1 + part2;
+  }
+  ty = tx = 0;
+}
+
 __global__ void __launch_bounds__(kThreads, 2) k_gemm_f64(const GemmArgs g) {
-  const int tx_tile = blockIdx.x, ty_tile = blockIdx.y;
+  int ty_tile, tx_tile;
+  decode_f64(blockIdx.x, g, ty_tile, tx_tile);
   const bool cs_row = ty_tile >= g.tm, cs_col = tx_tile >= g.tn;
-  if (cs_row && cs_col) return;  // corner block not needed
 
   // Source and destination of this tile.
   const double* Asrc;
@@ -145,7 +178,6 @@ cudaError_t launch_gemm_f64(const Plan& P, const double* A, const double* B, dou
   g.m = d.m; g.n = d.n; g.k = d.k;
   g.tm = (int)cdiv(d.m, BM);
   g.tn = (int)cdiv(d.n, BN);
-  int gx = g.tn, gy = g.tm;
   if (checksums) {
     char* w = static_cast<char*>(ws);
     g.acs = reinterpret_cast<const double*>(w + P.L.acs);
@@ -154,11 +186,12 @@ cudaError_t launch_gemm_f64(const Plan& P, const double* A, const double* B, dou
     g.F = reinterpret_cast<double*>(w + P.L.F);
     g.R = P.R;
     g.Cc = P.Cc;
-    gx += (int)cdiv(P.Cc, BN);
-    gy += (int)cdiv(P.R, BM);
+    g.tr = (int)cdiv(P.R, BM);
+    g.tc = (int)cdiv(P.Cc, BN);
   }
   if (d.m == 0 || d.n == 0) return cudaSuccess;
-  k_gemm_f64<<<dim3((unsigned)gx, (unsigned)gy), kThreads, 0, st>>>(g);
+  const int64_t tiles = (int64_t)g.tm * g.tn + (int64_t)g.tr * g.tn + (int64_t)g.tm * g.tc;
+  k_gemm_f64<<<(unsigned)tiles, kThreads, 0, st>>>(g);
   count_launches(1);
   return cudaGetLastError();
 }

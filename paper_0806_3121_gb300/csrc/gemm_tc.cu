@@ -20,6 +20,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <stdlib.h>
+
 #include <mutex>
 
 #include "internal.cuh"
@@ -64,6 +66,8 @@ struct TcArgs {
   int64_t g, ngrp;
   const int32_t* inj_hdr;    // armed epilogue injections (nullptr: none)
   const InjectEntry* inj;
+  uint64_t wait_ns;          // bounded-wait limit
+  int stall_test;            // timeout test: the producer skips the first tile
 };
 
 struct Tile {
@@ -173,6 +177,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc::mbar_init(drain, 1);
     *abort = 0;
+    tc::wait_limit_ns() = g.wait_ns;
     tc::fence_barrier_init();
     for (int pl = 0; pl < 2; ++pl) {
       tc::prefetch_tmap(&M.a[pl]);
@@ -200,6 +205,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int64_t issued = 0;  // stages filled and not known to be consumed
       for (int64_t t = blockIdx.x; t < g.t_total && !*abort; t += gridDim.x) {
         const Tile T = decode(t, g);
+        if (g.stall_test && t == 0) continue;  // nothing will fill these stages
         for (int64_t kt = 0; kt < nkt; ++kt) {
           const int seg = (int)(kt / nkb);
           const int64_t kb = kt - (int64_t)seg * nkb;
@@ -221,7 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int q = 0; q < STAGES && issued > 0; ++q, --issued) {
         if (--s < 0) { s = STAGES - 1; ph ^= 1; }
         const uint64_t t0 = tc::globaltimer();
-        while (!tc::mbar_try_wait(full(s), ph) && tc::globaltimer() - t0 < tc::kWaitLimitNs) {
+        while (!tc::mbar_try_wait(full(s), ph) && tc::globaltimer() - t0 < tc::wait_limit_ns()) {
         }
       }
     }
@@ -262,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // Every MMA issued so far must complete before TMEM is freed.
       tc::commit(drain);
       const uint64_t t0 = tc::globaltimer();
-      while (!tc::mbar_try_wait(drain, 0) && tc::globaltimer() - t0 < tc::kWaitLimitNs) {
+      while (!tc::mbar_try_wait(drain, 0) && tc::globaltimer() - t0 < tc::wait_limit_ns()) {
       }
     }
     __syncwarp();
@@ -484,6 +490,12 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
   }
   e = tc_timeout_flag(&g.status);
   if (e != cudaSuccess) return e;
+  // Test hook for the bounded waits: ABFT_TEST_STALL_PRODUCER=1 makes the
+  // producer skip the first tile, so its MMA wait runs out (after 0.2 s) and
+  // the call reports ABFT_ERR_TIMEOUT.  Off unless the variable is set.
+  const char* stall = getenv("ABFT_TEST_STALL_PRODUCER");
+  g.stall_test = stall && stall[0] == '1';
+  g.wait_ns = g.stall_test ? 200000000ull : tc::kWaitLimitNs;
   e = cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)SMEM_BYTES);
   if (e != cudaSuccess) return e;

@@ -14,6 +14,12 @@ namespace tc {
 // at most one tile's K loop, which takes well under a millisecond.
 constexpr uint64_t kWaitLimitNs = 4000000000ull;
 
+// The limit in force (a kernel may shorten it for its timeout test).
+__device__ __forceinline__ uint64_t& wait_limit_ns() {
+  static __shared__ uint64_t lim;
+  return lim;
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -62,7 +68,7 @@ __device__ __forceinline__ bool wait(uint32_t bar, uint32_t parity, volatile int
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
-    if (globaltimer() - t0 > kWaitLimitNs) {
+    if (globaltimer() - t0 > wait_limit_ns()) {
       *abort = 1;
       return false;
     }

@@ -300,3 +300,21 @@ def test_rate_1e9_epilogue_injection_seeded():
     abft.abft_set_epilogue_faults(r.desc, r.ws, [])
     st, rep, nrep = abft.abft_verify_correct(r.desc, r.C, r.ws, reread_C=0)
     assert st == abft.OK and [(a, b) for a, b, _ in positions(rep)] == sorted(pos)
+
+
+def test_bounded_wait_timeout_is_reported(monkeypatch):
+    """Failure detection without a GPU fault: with the test hook set, the producer of the
+    single data tile never fills its stages, the MMA warp's bounded wait runs out (0.2 s),
+    the kernel drains and frees TMEM, and the next synchronising call reports
+    ABFT_ERR_TIMEOUT.  The context stays usable: the same problem then runs normally."""
+    r = Run(128, 256, 64, 128, 256, seed=61)  # 1 data tile + 1 checksum-row + 1 checksum-col tile
+    monkeypatch.setenv("ABFT_TEST_STALL_PRODUCER", "1")
+    abft.abft_gemm(r.desc, r.A, r.B, r.C, r.ws)
+    monkeypatch.delenv("ABFT_TEST_STALL_PRODUCER")
+    with pytest.raises(abft.AbftError) as e:
+        abft.abft_verify_correct(r.desc, r.C, r.ws)
+    assert e.value.status == abft.ERR_TIMEOUT
+    abft.abft_gemm(r.desc, r.A, r.B, r.C, r.ws)
+    st, rep, nrep = abft.abft_verify_correct(r.desc, r.C, r.ws)
+    assert st == abft.OK and nrep == 0
+    check_fp32_product(r.C.cpu().numpy(), r.A64, r.B64, oracle.gemm(r.A64, r.B64))

@@ -80,13 +80,14 @@ struct Tile {
 // group the tiles run column by column -- data columns over the group's data
 // and checksum rows, then the checksum columns over its data rows -- so every
 // checksum tile reuses the A or B panels its group already keeps in L2.
-__device__ __forceinline__ Tile decode(int64_t t, const TcArgs& g) {
-  const int64_t ngr = (g.ntm + GROUP_M - 1) / GROUP_M;
+__device__ __forceinline__ Tile decode_local(int64_t t, int64_t ntm, int64_t ntn, int64_t ntr,
+                                             int64_t ntc) {
+  const int64_t ngr = (ntm + GROUP_M - 1) / GROUP_M;
   int64_t off = 0;
   for (int64_t G = 0; G < ngr; ++G) {
-    const int64_t gd = min((int64_t)GROUP_M, (int64_t)g.ntm - G * GROUP_M);
-    const int64_t nr = G < g.ntr ? (g.ntr - G + ngr - 1) / ngr : 0;
-    const int64_t part1 = (gd + nr) * g.ntn, part2 = gd * g.ntc;
+    const int64_t gd = min((int64_t)GROUP_M, ntm - G * GROUP_M);
+    const int64_t nr = G < ntr ? (ntr - G + ngr - 1) / ngr : 0;
+    const int64_t part1 = (gd + nr) * ntn, part2 = gd * ntc;
     if (t < off + part1 + part2) {
       int64_t u = t - off;
       Tile T;
@@ -110,11 +111,79 @@ __device__ __forceinline__ Tile decode(int64_t t, const TcArgs& g) {
     }
     off += part1 + part2;
   }
-  Tile T;  // not reached for t < t_total
+  Tile T;  // not reached for t inside the problem
   T.kind = 0;
   T.row0 = T.col0 = 0;
   return T;
 }
+
+__device__ __forceinline__ Tile decode(int64_t t, const TcArgs& g) {
+  return decode_local(t, g.ntm, g.ntn, g.ntr, g.ntc);
+}
+
+// Everything the three roles need to know about one tile.
+struct TileView {
+  int kind;                   // 0 data -> C, 1 checksum rows -> E16, 2 checksum columns -> F16
+  int prob;                   // problem index (grouped products; 0 otherwise)
+  int64_t row0, col0;         // tile origin in its output
+  float* dst;                 // output and its leading dimension / limits
+  int64_t ld, rlim, clim;
+  const CUtensorMap* ma0;     // A-side maps (plane 0 / 1)
+  const CUtensorMap* ma1;
+  const CUtensorMap* mb0;     // B-side maps
+  const CUtensorMap* mb1;
+  int64_t nkb;                // k-blocks per segment
+  int nseg;
+  // fused observed checksums of data tiles (obs_col == nullptr: off)
+  float* obs_col;
+  float* obs_row;
+  int64_t n, m, g, ngrp;
+  int vb_r, vb_c, er, ec;
+};
+
+// One problem (abft_gemm).
+struct SingleSched {
+  const TcMaps* M;
+  const TcArgs* a;
+  __device__ __forceinline__ int64_t total() const { return a->t_total; }
+  __device__ __forceinline__ void prefetch() const {
+    for (int pl = 0; pl < 2; ++pl) {
+      tc::prefetch_tmap(&M->a[pl]);
+      tc::prefetch_tmap(&M->acs[pl]);
+      tc::prefetch_tmap(&M->b[pl]);
+      tc::prefetch_tmap(&M->bcs[pl]);
+    }
+  }
+  __device__ __forceinline__ TileView view(int64_t t) const {
+    const TcArgs& g = *a;
+    const Tile T = decode(t, g);
+    TileView V;
+    V.kind = T.kind;
+    V.prob = 0;
+    V.row0 = T.row0;
+    V.col0 = T.col0;
+    if (T.kind == 0) { V.dst = g.C; V.ld = g.ldc; V.rlim = g.m; V.clim = g.n; }
+    else if (T.kind == 1) { V.dst = g.E16; V.ld = g.n; V.rlim = g.R16; V.clim = g.n; }
+    else { V.dst = g.F16; V.ld = g.C16; V.rlim = g.m; V.clim = g.C16; }
+    V.ma0 = T.kind == 1 ? &M->acs[0] : &M->a[0];
+    V.ma1 = T.kind == 1 ? &M->acs[1] : &M->a[1];
+    V.mb0 = T.kind == 2 ? &M->bcs[0] : &M->b[0];
+    V.mb1 = T.kind == 2 ? &M->bcs[1] : &M->b[1];
+    V.nkb = (g.k + BK - 1) / BK;
+    V.nseg = g.nseg;
+    V.obs_col = T.kind == 0 ? g.obs_col : nullptr;
+    V.obs_row = g.obs_row;
+    V.n = g.n;
+    V.m = g.m;
+    V.g = g.g;
+    V.ngrp = g.ngrp;
+    V.vb_r = g.vb_r;
+    V.vb_c = g.vb_c;
+    V.er = g.er;
+    V.ec = g.ec;
+    return V;
+  }
+};
 
 __device__ __forceinline__ void store_row32(float* dst, int64_t ld, int64_t row, int64_t col,
                                             int64_t rlim, int64_t clim, const float (&v)[32]) {
@@ -148,8 +217,11 @@ __device__ __forceinline__ void transpose_reduce(float (&v)[32], int lane) {
 
 __device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
-__global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_bf16(const __grid_constant__ TcMaps M, const TcArgs g) {
+// The kernel body, shared by the single-problem and the grouped product.
+template <class Sched>
+__device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wait_ns,
+                                        int stall_test, const int32_t* inj_hdr,
+                                        const InjectEntry* inj) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -177,14 +249,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc::mbar_init(drain, 1);
     *abort = 0;
-    tc::wait_limit_ns() = g.wait_ns;
+    tc::wait_limit_ns() = wait_ns;
     tc::fence_barrier_init();
-    for (int pl = 0; pl < 2; ++pl) {
-      tc::prefetch_tmap(&M.a[pl]);
-      tc::prefetch_tmap(&M.acs[pl]);
-      tc::prefetch_tmap(&M.b[pl]);
-      tc::prefetch_tmap(&M.bcs[pl]);
-    }
+    S.prefetch();
   }
   if (warp == 1) {
     tc::tmem_alloc(tc::smem_addr(tmem_slot), TMEM_COLS);
@@ -194,8 +261,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const int64_t nkb = (g.k + BK - 1) / BK;
-  const int64_t nkt = nkb * g.nseg;
+  const int64_t total = S.total();
 
   if (warp == 0) {
     if (lane == 0) {
@@ -203,14 +269,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       int s = 0;
       uint32_t ph = 0;
       int64_t issued = 0;  // stages filled and not known to be consumed
-      for (int64_t t = blockIdx.x; t < g.t_total && !*abort; t += gridDim.x) {
-        const Tile T = decode(t, g);
-        if (g.stall_test && t == 0) continue;  // nothing will fill these stages
+      for (int64_t t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
+        const TileView T = S.view(t);
+        if (stall_test && t == 0) continue;  // nothing will fill these stages
+        const int64_t nkb = T.nkb, nkt = T.nkb * T.nseg;
         for (int64_t kt = 0; kt < nkt; ++kt) {
           const int seg = (int)(kt / nkb);
           const int64_t kb = kt - (int64_t)seg * nkb;
-          const CUtensorMap* ma = T.kind == 1 ? &M.acs[seg == 2] : &M.a[seg == 2];
-          const CUtensorMap* mb = T.kind == 2 ? &M.bcs[seg == 1] : &M.b[seg == 1];
+          const CUtensorMap* ma = seg == 2 ? T.ma1 : T.ma0;
+          const CUtensorMap* mb = seg == 1 ? T.mb1 : T.mb0;
           if (!tc::wait(empty(s), ph ^ 1, abort)) break;
           const uint32_t sa = tc::smem_addr(smem + s * STAGE_BYTES);
           tc::mbar_arrive_expect_tx(full(s), STAGE_BYTES);
@@ -238,7 +305,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       constexpr uint32_t idesc = tc::idesc_bf16(BM, BN, 1);
       int s = 0, acc = 0;
       uint32_t ph = 0, aph = 0;
-      for (int64_t t = blockIdx.x; t < g.t_total && !*abort; t += gridDim.x) {
+      for (int64_t t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
+        const TileView T = S.view(t);
+        const int64_t nkt = T.nkb * T.nseg;
         if (!tc::wait(tempty(acc), aph ^ 1, abort)) break;
         tc::fence_after_sync();
         const uint32_t d = tmem + acc * BN;
@@ -276,23 +345,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- epilogue: warps 2..5, TMEM lane quarter = warp % 4
     const int q = warp & 3;
     float* obs = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);  // [4][BN][2]
-    const int ninj = (g.inj_hdr && g.inj_hdr[0] == kInjectMagic)
-                         ? max(0, min(g.inj_hdr[1], kMaxInject)) : 0;
-    const float scr = scalbnf(1.0f, -g.er), scc = scalbnf(1.0f, -g.ec);
+    const int ninj = (inj_hdr && inj_hdr[0] == kInjectMagic)
+                         ? max(0, min(inj_hdr[1], kMaxInject)) : 0;
     int acc = 0;
     uint32_t aph = 0;
-    for (int64_t t = blockIdx.x; t < g.t_total; t += gridDim.x) {
-      const Tile T = decode(t, g);
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+      const TileView T = S.view(t);
       if (!tc::wait(tfull(acc), aph, abort)) break;
       tc::fence_after_sync();
-      float* dst;
-      int64_t ld, rlim, clim;
-      if (T.kind == 0) { dst = g.C; ld = g.ldc; rlim = g.m; clim = g.n; }
-      else if (T.kind == 1) { dst = g.E16; ld = g.n; rlim = g.R16; clim = g.n; }
-      else { dst = g.F16; ld = g.C16; rlim = g.m; clim = g.C16; }
+      float* const dst = T.dst;
+      const int64_t ld = T.ld, rlim = T.rlim, clim = T.clim;
       const int64_t row = T.row0 + q * 32 + lane;
-      const bool fused = T.kind == 0 && g.obs_col != nullptr;
-      const float wrow = (float)((int)(row % g.vb_r) + 1) * scr;
+      const bool fused = T.obs_col != nullptr;
+      const float scr = scalbnf(1.0f, -T.er), scc = scalbnf(1.0f, -T.ec);
+      const float wrow = fused ? (float)((int)(row % T.vb_r) + 1) * scr : 0.f;
       float racc_e = 0.f, racc_w = 0.f;
       const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
 #pragma unroll 1
@@ -303,8 +369,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t col = T.col0 + c;
         if (T.kind == 0)
           for (int f = 0; f < ninj; ++f) {
-            const InjectEntry ie = g.inj[f];
-            if (ie.row == row && ie.col >= col && ie.col < col + 32) {
+            const InjectEntry ie = inj[f];
+            if (ie.pad == T.prob && ie.row == row && ie.col >= col && ie.col < col + 32) {
               const int x = ie.col - (int)col;
 #pragma unroll
               for (int u = 0; u < 32; ++u)
@@ -315,15 +381,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (fused) {
           // row partials over the column group (weights restart per verify block;
           // a 32-column chunk never straddles one)
-          const int cm = (int)(col % g.vb_c) + 1;
+          const int cm = (int)(col % T.vb_c) + 1;
 #pragma unroll
           for (int u = 0; u < 32; ++u) {
             racc_e += v[u];
             racc_w = fmaf((float)(cm + u) * scc, v[u], racc_w);
           }
-          if (((c + 32) % (int)g.g) == 0 || c + 32 == BN || col + 32 >= clim) {
-            if (row < g.m) {
-              float* o = g.obs_row + (row * g.ngrp + (int)(col / g.g)) * 2;
+          if (((c + 32) % (int)T.g) == 0 || c + 32 == BN || col + 32 >= clim) {
+            if (row < T.m) {
+              float* o = T.obs_row + (row * T.ngrp + (int)(col / T.g)) * 2;
               o[0] = racc_e;
               o[1] = racc_w;
             }
@@ -351,15 +417,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int h = 0; h < 2; ++h) {
           const int cc = et + h * 128;
           const int64_t col = T.col0 + cc;
-          if (col < g.n) {
+          if (col < T.n) {
             float se = 0.f, sw = 0.f;
 #pragma unroll
             for (int w4 = 0; w4 < 4; ++w4) {
               se += obs[(w4 * BN + cc) * 2 + 0];
               sw += obs[(w4 * BN + cc) * 2 + 1];
             }
-            g.obs_col[(tr * 2 + 0) * g.n + col] = se;
-            g.obs_col[(tr * 2 + 1) * g.n + col] = sw;
+            T.obs_col[(tr * 2 + 0) * T.n + col] = se;
+            T.obs_col[(tr * 2 + 1) * T.n + col] = sw;
           }
         }
         epi_barrier();
@@ -369,11 +435,72 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   tc::fence_before_sync();
   __syncthreads();
-  if (threadIdx.x == 0 && *abort) atomicExch(g.status, 1);
+  if (threadIdx.x == 0 && *abort) atomicExch(status, 1);
   if (warp == 1) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, TMEM_COLS);
   }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_bf16(const __grid_constant__ TcMaps M, const TcArgs g) {
+  const SingleSched S{&M, &g};
+  tc_body(S, g.status, g.wait_ns, g.stall_test, g.inj_hdr, g.inj);
+}
+
+// Many problems (grouped product): the flattened tile list is the problems'
+// tile lists one after the other; per-problem tables and tensor maps live in
+// global memory.  Verify blocks equal the tile (128 x 256).
+struct GroupSched {
+  const GProb* probs;
+  const GMaps* maps;
+  int count;
+  int64_t t_total;
+  bool checksums;
+  __device__ __forceinline__ int64_t total() const { return t_total; }
+  __device__ __forceinline__ void prefetch() const {}
+  __device__ __forceinline__ TileView view(int64_t t) const {
+    int lo = 0, hi = count - 1;  // last problem with tile_off <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (probs[mid].tile_off <= t) lo = mid; else hi = mid - 1;
+    }
+    const GProb& P = probs[lo];
+    const GMaps& Mp = maps[lo];
+    const Tile T = checksums ? decode_local(t - P.tile_off, P.ntm, P.ntn, P.ntr, P.ntc)
+                             : decode_local(t - P.tile_off, P.ntm, P.ntn, 0, 0);
+    TileView V;
+    V.kind = T.kind;
+    V.prob = lo;
+    V.row0 = T.row0;
+    V.col0 = T.col0;
+    if (T.kind == 0) { V.dst = P.C; V.ld = P.ldc; V.rlim = P.m; V.clim = P.n; }
+    else if (T.kind == 1) { V.dst = P.E16; V.ld = P.n; V.rlim = P.R16; V.clim = P.n; }
+    else { V.dst = P.F16; V.ld = P.C16; V.rlim = P.m; V.clim = P.C16; }
+    V.ma0 = V.ma1 = T.kind == 1 ? &Mp.acs : &Mp.a;
+    V.mb0 = V.mb1 = T.kind == 2 ? &Mp.bcs : &Mp.b;
+    V.nkb = (P.k + BK - 1) / BK;
+    V.nseg = 1;
+    V.obs_col = (T.kind == 0 && checksums) ? P.obs_col : nullptr;
+    V.obs_row = P.obs_row;
+    V.n = P.n;
+    V.m = P.m;
+    V.g = kGrpVbC;
+    V.ngrp = P.nvc;
+    V.vb_r = kGrpVbR;
+    V.vb_c = kGrpVbC;
+    V.er = 7;
+    V.ec = 8;
+    return V;
+  }
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_grouped(const GProb* probs, const GMaps* maps, int count, int64_t t_total,
+                   int checksums, int* status, uint64_t wait_ns, const int32_t* inj_hdr,
+                   const InjectEntry* inj) {
+  const GroupSched S{probs, maps, count, t_total, checksums != 0};
+  tc_body(S, status, wait_ns, 0, inj_hdr, inj);
 }
 
 // ---- host side
@@ -502,6 +629,32 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
   const int grid = (int)std::min<int64_t>(g.t_total, num_sms());
   if (grid == 0) return cudaSuccess;
   k_gemm_bf16<<<grid, kThreads, SMEM_BYTES, st>>>(M, g);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t make_bf16_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols,
+                          int64_t ld, uint32_t box_cols, uint32_t box_rows) {
+  cudaError_t e = get_encoder();
+  if (e != cudaSuccess) return e;
+  return make_map(map, ptr, rows, cols, ld, box_cols, box_rows) ? cudaSuccess
+                                                                : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_gemm_grouped(const GProb* probs, const GMaps* maps, int count,
+                                int64_t t_total, bool checksums, const int32_t* inj_hdr,
+                                const InjectEntry* inj, cudaStream_t st) {
+  int* status = nullptr;
+  cudaError_t e = tc_timeout_flag(&status);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_gemm_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  const int grid = (int)std::min<int64_t>(t_total, num_sms());
+  if (grid == 0) return cudaSuccess;
+  k_gemm_grouped<<<grid, kThreads, SMEM_BYTES, st>>>(probs, maps, count, t_total,
+                                                     checksums ? 1 : 0, status,
+                                                     tc::kWaitLimitNs, inj_hdr, inj);
   count_launches(1);
   return cudaGetLastError();
 }

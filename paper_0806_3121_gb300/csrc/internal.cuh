@@ -2,6 +2,7 @@
 // Not part of the ABI; see include/abft.h for the public contract.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -113,6 +114,57 @@ struct TcOperands {
 cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void* ws,
                              bool checksums, cudaStream_t st);
 cudaError_t tc_timeout_flag(int** dev_ptr);
+
+// ---- grouped products (many independent bf16 problems, one launch per step)
+// Verify blocks are fixed to the product tile: 128 rows x 256 columns.
+constexpr int kGrpVbR = 128, kGrpVbC = 256;
+
+struct GProb {
+  int64_t m, n, k, lda, ldb, ldc;
+  const void* A;  // bf16 m x k (lda)
+  const void* B;  // bf16 k x n (ldb)
+  float* C;       // m x n (ldc)
+  void* acs;      // bf16 (4 nvr) x acs_ld: e-hi, e-lo, w-hi, w-lo per verify block
+  void* bcs;      // bf16 k x bcs_ld: 4 pieces per verify column block
+  int64_t acs_ld, bcs_ld, R16, C16;
+  float* E16;     // R16 x n
+  float* F16;     // m x C16
+  float* obs_col;  // [tile row][2][n]
+  float* obs_row;  // [row][nvc][2]
+  double* nArow;
+  double* nAblk;
+  double* nBcol;
+  double* nBblk;
+  float* rowpart;  // m x ceil(k/256)
+  float* colpart;  // ceil(k/128) x n
+  double* partA;   // 2 nvr x ceil(k/2048)
+  double* partB;   // 2 nvc x ceil(k/128)
+  int64_t nvr, nvc;
+  double f1c, f1r, f2;  // threshold factors (s applied at use)
+  // offsets of this problem in the flattened grids
+  int64_t tile_off;    // product tiles
+  int64_t encA_off;    // A-side encode CTAs (2048 columns x a verify block)
+  int64_t encB_off;    // B-side encode CTAs (2048 columns x 128 rows)
+  int64_t rows_off;    // rows (row norms, row lines)
+  int64_t cols_off;    // columns (column norms)
+  int64_t vbr_off;     // verify row blocks
+  int64_t vbc_off;     // verify column blocks
+  int64_t cline_off;   // column lines (verify block x column)
+  int32_t ntm, ntn, ntr, ntc;
+};
+
+struct GMaps {  // tensor maps of one problem (global memory, 64-byte aligned)
+  alignas(64) CUtensorMap a;
+  alignas(64) CUtensorMap acs;
+  alignas(64) CUtensorMap b;
+  alignas(64) CUtensorMap bcs;
+};
+
+cudaError_t make_bf16_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols,
+                          int64_t ld, uint32_t box_cols, uint32_t box_rows);
+cudaError_t launch_gemm_grouped(const GProb* probs, const GMaps* maps, int count,
+                                int64_t t_total, bool checksums, const int32_t* inj_hdr,
+                                const InjectEntry* inj, cudaStream_t st);
 cudaError_t consume_tc_timeout(cudaStream_t st, bool* timed_out);
 cudaError_t launch_verify(const Plan& P, void* C, void* ws, const Erased& er, bool reread,
                           cudaStream_t st);

@@ -80,10 +80,12 @@ typedef struct {
  * coordinate of a flagged line (col = -1: row check of row `row`; row = -1:
  * column check of column `col`).  side: 0 column check, 1 row check, 2 erasure.
  * delta = value before - value after correction; r_e / r_w are the unweighted
- * and weighted residuals of the line that located it. */
+ * and weighted residuals of the line that located it.  problem is the index of
+ * the problem in a group (abft_group_*), 0 for the single-problem calls. */
 typedef struct {
   int32_t row, col, kind, side;
   double delta, r_e, r_w;
+  int32_t problem, reserved;
 } abft_fault;
 
 /* Byte offsets of the regions inside the workspace (all 256-byte aligned) and
@@ -220,6 +222,109 @@ abft_status abft_inject_bitflips(const abft_desc* desc, void* C, const int64_t* 
                                  const int64_t* cols, const int32_t* bits, int32_t count,
                                  void* stream);
 abft_status abft_erase_block(const abft_desc* desc, void* C, int32_t bi, int32_t bj, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Grouped products: many independent bf16 problems C_p = A_p B_p, each with
+ * the encoded operands of Eq. (1) and the checks of section 2.2, executed by
+ * one persistent product launch (and one encode / verify pass) for the whole
+ * group.  The paper treats one distributed product; the grouping is a
+ * batching layer over that method with no counterpart in the paper.
+ *
+ * Per problem: A (m x k, lda) and B (k x n, ldb) bf16 row-major on the device,
+ * 16-byte aligned, lda and ldb multiples of 8; C (m x n, ldc) fp32.  Verify
+ * blocks are 128 rows x 256 columns (weights 1..128 / 1..256 scaled by 2^-7 /
+ * 2^-8, local to the block).  Product tiles are 128 rows x (64 * boxes_per_tile)
+ * columns; a problem's checksum rows and columns are appended as 64-row halves
+ * and 64-column boxes after its data, so they share the last data tiles.
+ *
+ * Ownership: the group object (host) holds the problem list, the tuning and a
+ * captured CUDA graph; the caller's workspace (abft_group_workspace_bytes,
+ * 256-byte aligned, bound with abft_group_bind) holds every device table and
+ * per-problem checksum region.  The operand and result pointers given at
+ * creation are used by every later call.  Calls are stream-ordered and
+ * asynchronous unless marked SYNCHRONISES.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int64_t m, n, k;        /* C = A B; 1 <= m, n <= 2^20, 1 <= k <= 2^24    */
+  int64_t lda, ldb, ldc;  /* leading dimensions in elements                */
+  const void* A;          /* device, bf16                                  */
+  const void* B;          /* device, bf16                                  */
+  void* C;                /* device, fp32                                  */
+} abft_problem;
+
+typedef struct abft_group_s* abft_group;
+
+typedef struct {
+  int32_t boxes_per_tile; /* 4: 128 x 256 tiles; 2: 128 x 128 tiles          */
+  int32_t order;          /* 0: problems in the given order; 1: by decreasing k */
+} abft_group_tuning;
+
+/* Where problem p's checksum results live in the workspace (byte offsets,
+ * 256-byte aligned).  acs: R16 x acs_ld bf16 rows (per verify block I: rows 4I,
+ * 4I+1 = hi, lo pieces of e^T A_I; 4I+2, 4I+3 = of w^T A_I); bcs: k x bcs_ld bf16,
+ * the same 4 columns per verify column block; E16: R16 x n fp32 products of the
+ * acs rows with B; F16: m x C16 fp32 products of A with the bcs columns (the
+ * expected checksum of a line is the sum of its hi and lo products); nArow (m),
+ * nAblk (4 nvr), nBcol (n), nBblk (4 nvc): binary64 norms of the thresholds,
+ * as in abft_ws_layout. */
+typedef struct {
+  size_t acs, bcs, E16, F16, obs_col, obs_row, nArow, nAblk, nBcol, nBblk;
+  int64_t nvr, nvc, R16, C16, acs_ld, bcs_ld;
+} abft_group_layout;
+
+/* Validates the problems (ABFT_ERR_INVALID with nothing created on a bad
+ * one; dtype must be ABFT_BF16) and lays out the workspace.  tau_safety as in
+ * abft_desc.  Host only. */
+abft_status abft_group_create(const abft_problem* problems, int32_t count, int32_t dtype,
+                              double tau_safety, abft_group* out);
+size_t abft_group_workspace_bytes(abft_group g);
+abft_status abft_group_problem_layout(abft_group g, int32_t p, abft_group_layout* out);
+/* Builds the device tables (problem records, tensor maps, tile lists) in ws.
+ * SYNCHRONISES `stream`. */
+abft_status abft_group_bind(abft_group g, void* ws, size_t ws_bytes, void* stream);
+/* Schedule tuning: tile width and problem order (default {4, 1}).  Rebuilds
+ * the tables (SYNCHRONISES) and drops a captured graph. */
+abft_status abft_group_set_tuning(abft_group g, const abft_group_tuning* t, void* stream);
+abft_status abft_group_get_tuning(abft_group g, abft_group_tuning* t);
+/* Autotuner: times `reps` checksum products of every tuning candidate and
+ * keeps the fastest (*chosen, *best_ms; best_ms = -1 when the choice came from
+ * the cache).  With the environment variable ABFT_TUNE_CACHE naming a file, a
+ * group of the same shapes reuses the recorded choice and new choices are
+ * appended.  Runs the product, so it overwrites every C and the checksum
+ * results: encode and multiply again afterwards.  SYNCHRONISES `stream`. */
+abft_status abft_group_autotune(abft_group g, int32_t reps, abft_group_tuning* chosen,
+                                double* best_ms, void* stream);
+/* Encode every problem's operands (section 2.1, Eq. (1)): checksum rows of A
+ * and checksum columns of B as bf16 hi + lo pieces, and the norms of the
+ * detection thresholds. */
+abft_status abft_group_encode(abft_group g, void* stream);
+/* The product of every problem.  checksums = 1: the ABFT product (data,
+ * checksum rows and columns, observed sums of every data tile, armed epilogue
+ * faults); 0: the same kernel on the data tiles only. */
+abft_status abft_group_gemm(abft_group g, int32_t checksums, void* stream);
+/* Detect / locate / correct every problem from the observed sums (as
+ * abft_verify_correct with reread_C = 0).  _enqueue is asynchronous and may be
+ * captured; _report SYNCHRONISES and returns the entries sorted by (problem,
+ * row, col, kind) with the status rules of abft_verify_correct;
+ * _verify_correct is both. */
+abft_status abft_group_verify_enqueue(abft_group g, void* stream);
+abft_status abft_group_report(abft_group g, abft_fault* report, int32_t max_reports,
+                              int32_t* n_reports, void* stream);
+abft_status abft_group_verify_correct(abft_group g, abft_fault* report, int32_t max_reports,
+                                      int32_t* n_reports, void* stream);
+/* Arms `count` (<= 256) bit flips of accumulator outputs: bit bits[t] of
+ * element (rows[t], cols[t]) of problem problem[t] flips in the epilogue of
+ * every later checksum product, before the store and the observed sums
+ * (count = 0 disarms).  Host arrays. */
+abft_status abft_group_set_epilogue_faults(abft_group g, const int32_t* problem,
+                                           const int64_t* rows, const int64_t* cols,
+                                           const int32_t* bits, int32_t count, void* stream);
+/* CUDA graph of one step: the product (checksums as in abft_group_gemm) and,
+ * with checksums, the verify enqueue.  Captured on `stream` (not the legacy
+ * default stream); abft_group_launch replays it. */
+abft_status abft_group_capture(abft_group g, int32_t checksums, void* stream);
+abft_status abft_group_launch(abft_group g, void* stream);
+abft_status abft_group_destroy(abft_group g);
 
 /* Number of CUDA kernels this library has launched in this process so far
  * (all threads, all devices).  Host-side counter; never synchronises. */

@@ -25,7 +25,13 @@ EXPORTS = ("abft_workspace_bytes", "abft_workspace_layout", "abft_encode",
            "abft_encode_noalloc", "abft_gemm", "abft_set_epilogue_faults",
            "abft_gemm_plain", "abft_verify_correct", "abft_recover_block",
            "abft_inject_bitflips", "abft_erase_block", "abft_kernel_launches",
-           "abft_last_error", "abft_version")
+           "abft_last_error", "abft_version",
+           "abft_group_create", "abft_group_workspace_bytes", "abft_group_problem_layout",
+           "abft_group_bind",
+           "abft_group_set_tuning", "abft_group_get_tuning", "abft_group_autotune",
+           "abft_group_encode", "abft_group_gemm", "abft_group_verify_enqueue",
+           "abft_group_report", "abft_group_verify_correct", "abft_group_set_epilogue_faults",
+           "abft_group_capture", "abft_group_launch", "abft_group_destroy")
 
 
 class AbftError(RuntimeError):
@@ -45,11 +51,11 @@ class Desc(ct.Structure):
 class Fault(ct.Structure):
     _fields_ = [("row", ct.c_int32), ("col", ct.c_int32), ("kind", ct.c_int32),
                 ("side", ct.c_int32), ("delta", ct.c_double), ("r_e", ct.c_double),
-                ("r_w", ct.c_double)]
+                ("r_w", ct.c_double), ("problem", ct.c_int32), ("reserved", ct.c_int32)]
 
     def as_dict(self):
         return dict(row=self.row, col=self.col, kind=self.kind, side=self.side,
-                    delta=self.delta, r_e=self.r_e, r_w=self.r_w)
+                    delta=self.delta, r_e=self.r_e, r_w=self.r_w, problem=self.problem)
 
 
 class WsLayout(ct.Structure):
@@ -64,6 +70,22 @@ class WsLayout(ct.Structure):
                 ("inject", ct.c_size_t), ("fused", ct.c_int32), ("planes", ct.c_int32),
                 ("acs_plane", ct.c_size_t), ("bcs_plane", ct.c_size_t), ("op_a", ct.c_size_t),
                 ("op_b", ct.c_size_t), ("op_a_ld", ct.c_int64), ("op_b_ld", ct.c_int64)]
+
+
+class Problem(ct.Structure):
+    _fields_ = [("m", ct.c_int64), ("n", ct.c_int64), ("k", ct.c_int64),
+                ("lda", ct.c_int64), ("ldb", ct.c_int64), ("ldc", ct.c_int64),
+                ("A", ct.c_void_p), ("B", ct.c_void_p), ("C", ct.c_void_p)]
+
+
+class GroupLayout(ct.Structure):
+    _fields_ = [(f, ct.c_size_t) for f in ("acs", "bcs", "E16", "F16", "obs_col", "obs_row",
+                                           "nArow", "nAblk", "nBcol", "nBblk")] + \
+               [(f, ct.c_int64) for f in ("nvr", "nvc", "R16", "C16", "acs_ld", "bcs_ld")]
+
+
+class GroupTuning(ct.Structure):
+    _fields_ = [("boxes_per_tile", ct.c_int32), ("order", ct.c_int32)]
 
 
 _lock = threading.Lock()
@@ -100,6 +122,25 @@ def load(path: str = LIB_PATH):
         lib.abft_kernel_launches.argtypes = []
         lib.abft_version.restype = ct.c_int32
         lib.abft_version.argtypes = []
+        G, T = vp, ct.POINTER(GroupTuning)
+        lib.abft_group_create.argtypes = [ct.POINTER(Problem), i32, i32, ct.c_double,
+                                          ct.POINTER(ct.c_void_p)]
+        lib.abft_group_workspace_bytes.restype = ct.c_size_t
+        lib.abft_group_workspace_bytes.argtypes = [G]
+        lib.abft_group_bind.argtypes = [G, vp, ct.c_size_t, vp]
+        lib.abft_group_problem_layout.argtypes = [G, i32, ct.POINTER(GroupLayout)]
+        lib.abft_group_set_tuning.argtypes = [G, T, vp]
+        lib.abft_group_get_tuning.argtypes = [G, T]
+        lib.abft_group_autotune.argtypes = [G, i32, T, ct.POINTER(ct.c_double), vp]
+        lib.abft_group_encode.argtypes = [G, vp]
+        lib.abft_group_gemm.argtypes = [G, i32, vp]
+        lib.abft_group_verify_enqueue.argtypes = [G, vp]
+        lib.abft_group_report.argtypes = [G, vp, i32, ct.POINTER(ct.c_int32), vp]
+        lib.abft_group_verify_correct.argtypes = [G, vp, i32, ct.POINTER(ct.c_int32), vp]
+        lib.abft_group_set_epilogue_faults.argtypes = [G, vp, vp, vp, vp, i32, vp]
+        lib.abft_group_capture.argtypes = [G, i32, vp]
+        lib.abft_group_launch.argtypes = [G, vp]
+        lib.abft_group_destroy.argtypes = [G]
         for name in EXPORTS:  # fail loudly on a library that lacks an entry point
             getattr(lib, name)
         _lib = lib
@@ -225,3 +266,112 @@ def abft_kernel_launches() -> int:
 
 def abft_version() -> int:
     return load().abft_version()
+
+
+# ---- grouped products (abft_group_*): one handle per group of problems
+
+def abft_group_create(problems, dtype="bf16", tau_safety=0.0):
+    """problems: sequence of dicts/tuples (m, n, k, A, B, C[, lda, ldb, ldc]) with A, B, C
+    tensors or device pointers.  Returns the opaque handle (an int)."""
+    arr = (Problem * max(1, len(problems)))()
+    for i, q in enumerate(problems):
+        if isinstance(q, dict):
+            m, n, k, A, B, C = q["m"], q["n"], q["k"], q["A"], q["B"], q["C"]
+            lda, ldb, ldc = q.get("lda", k), q.get("ldb", n), q.get("ldc", n)
+        else:
+            m, n, k, A, B, C = q[:6]
+            lda, ldb, ldc = (q[6:9] if len(q) >= 9 else (k, n, n))
+        arr[i] = Problem(m=m, n=n, k=k, lda=lda, ldb=ldb, ldc=ldc, A=_ptr(A), B=_ptr(B),
+                         C=_ptr(C))
+    h = ct.c_void_p()
+    code = DTYPE_CODES[dtype] if isinstance(dtype, str) else int(dtype)
+    _check(load().abft_group_create(arr, len(problems), code, tau_safety, ct.byref(h)))
+    return h.value
+
+
+def abft_group_workspace_bytes(g) -> int:
+    return load().abft_group_workspace_bytes(g)
+
+
+def abft_group_problem_layout(g, p) -> GroupLayout:
+    out = GroupLayout()
+    _check(load().abft_group_problem_layout(g, p, ct.byref(out)))
+    return out
+
+
+def abft_group_bind(g, ws, stream=None):
+    _check(load().abft_group_bind(g, _ptr(ws), ws.numel() * ws.element_size()
+                                  if hasattr(ws, "numel") else abft_group_workspace_bytes(g),
+                                  _stream(stream)))
+
+
+def abft_group_set_tuning(g, boxes_per_tile=4, order=1, stream=None):
+    t = GroupTuning(boxes_per_tile=boxes_per_tile, order=order)
+    _check(load().abft_group_set_tuning(g, ct.byref(t), _stream(stream)))
+
+
+def abft_group_get_tuning(g):
+    t = GroupTuning()
+    _check(load().abft_group_get_tuning(g, ct.byref(t)))
+    return dict(boxes_per_tile=t.boxes_per_tile, order=t.order)
+
+
+def abft_group_autotune(g, reps=3, stream=None):
+    """Returns (tuning dict, best ms or -1 when taken from the cache file)."""
+    t = GroupTuning()
+    ms = ct.c_double(0.0)
+    _check(load().abft_group_autotune(g, reps, ct.byref(t), ct.byref(ms), _stream(stream)))
+    return dict(boxes_per_tile=t.boxes_per_tile, order=t.order), ms.value
+
+
+def abft_group_encode(g, stream=None):
+    _check(load().abft_group_encode(g, _stream(stream)))
+
+
+def abft_group_gemm(g, checksums=True, stream=None):
+    _check(load().abft_group_gemm(g, 1 if checksums else 0, _stream(stream)))
+
+
+def abft_group_verify_enqueue(g, stream=None):
+    _check(load().abft_group_verify_enqueue(g, _stream(stream)))
+
+
+def _group_reports(fn, g, max_reports, stream):
+    rep = (Fault * max(1, max_reports))()
+    nrep = ct.c_int32(0)
+    st = fn(g, ct.cast(rep, ct.c_void_p), max_reports, ct.byref(nrep), _stream(stream))
+    _check(st, allow=(OK, ERR_UNCORRECTABLE))
+    return st, [r.as_dict() for r in rep[:min(nrep.value, max_reports)]], nrep.value
+
+
+def abft_group_report(g, max_reports=1024, stream=None):
+    """Returns (status, [fault dicts], total count).  Synchronises the stream."""
+    return _group_reports(load().abft_group_report, g, max_reports, stream)
+
+
+def abft_group_verify_correct(g, max_reports=1024, stream=None):
+    return _group_reports(load().abft_group_verify_correct, g, max_reports, stream)
+
+
+def abft_group_set_epilogue_faults(g, flips, stream=None):
+    """flips: (problem, row, col, bit) tuples; [] disarms."""
+    n = len(flips)
+    prob = (ct.c_int32 * max(1, n))(*[f[0] for f in flips])
+    rows = (ct.c_int64 * max(1, n))(*[f[1] for f in flips])
+    cols = (ct.c_int64 * max(1, n))(*[f[2] for f in flips])
+    bits = (ct.c_int32 * max(1, n))(*[f[3] for f in flips])
+    _check(load().abft_group_set_epilogue_faults(
+        g, ct.cast(prob, ct.c_void_p), ct.cast(rows, ct.c_void_p), ct.cast(cols, ct.c_void_p),
+        ct.cast(bits, ct.c_void_p), n, _stream(stream)))
+
+
+def abft_group_capture(g, checksums=True, stream=None):
+    _check(load().abft_group_capture(g, 1 if checksums else 0, _stream(stream)))
+
+
+def abft_group_launch(g, stream=None):
+    _check(load().abft_group_launch(g, _stream(stream)))
+
+
+def abft_group_destroy(g):
+    _check(load().abft_group_destroy(g))

@@ -13,10 +13,8 @@
 #include "internal.cuh"
 
 namespace abft {
-namespace {
 
 thread_local char g_err[512] = "";
-std::atomic<int64_t> g_launches{0};
 
 abft_status fail(abft_status st, const char* fmt, ...) {
   va_list ap;
@@ -29,6 +27,10 @@ abft_status fail(abft_status st, const char* fmt, ...) {
 abft_status cuda_fail(cudaError_t e, const char* where) {
   return fail(ABFT_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
+
+namespace {
+
+std::atomic<int64_t> g_launches{0};
 
 int ceil_log2(int64_t v) {
   int e = 0;
@@ -53,6 +55,19 @@ Units units_for(int dtype) {
   if (dtype == ABFT_BF16X3) return {u32, u32, u32, ldexp(1.0, -17), ldexp(1.0, -17)};
   return {u32, u32, u32, 0.0, ldexp(1.0, -17)};
 }
+
+}  // namespace
+
+void threshold_factors(int dtype, int64_t k, int64_t vb_r, int64_t vb_c, double* f1_col,
+                       double* f1_row, double* f2) {
+  const Units u = units_for(dtype);
+  const double sk = sqrt((double)k);
+  *f1_col = sk * u.u_acc + sqrt((double)vb_r) * (u.u_sum + u.u_enc) + u.u_c;
+  *f1_row = sk * u.u_acc + sqrt((double)vb_c) * (u.u_sum + u.u_enc) + u.u_c;
+  *f2 = sk * u.u_acc + u.u_cs;
+}
+
+namespace {
 
 size_t operand_bytes(int dtype) { return dtype == ABFT_F64 ? 8 : 2; }
 
@@ -94,11 +109,8 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
   p.er = ceil_log2(d->vb_rows);
   p.ec = ceil_log2(d->vb_cols);
   p.s = d->tau_safety > 0 ? d->tau_safety : 4.0;
-  const Units u = units_for(d->dtype);
-  const double sk = sqrt((double)d->k);
-  p.f1_col = sk * u.u_acc + sqrt((double)d->vb_rows) * (u.u_sum + u.u_enc) + u.u_c;
-  p.f1_row = sk * u.u_acc + sqrt((double)d->vb_cols) * (u.u_sum + u.u_enc) + u.u_c;
-  p.f2_col = p.f2_row = sk * u.u_acc + u.u_cs;
+  threshold_factors(d->dtype, d->k, d->vb_rows, d->vb_cols, &p.f1_col, &p.f1_row, &p.f2_col);
+  p.f2_row = p.f2_col;
   const bool lp0 = d->dtype != ABFT_F64;
   p.fused = lp0 && d->vb_rows % 128 == 0 && d->vb_cols % 32 == 0 &&
             (256 % d->vb_cols == 0 || d->vb_cols % 256 == 0);

@@ -77,8 +77,57 @@ __device__ __forceinline__ void store8(__nv_bfloat16* dst, const __nv_bfloat16 (
 
 // Column checksums of A per verify block (fp32 sums, hi/lo pieces), per-row
 // partial sums of squares (one per 256 columns) and per-CTA partials of the
-// squared norms of the two checksum rows.  CTA = 2048 columns x one verify
-// block; thread = 8 consecutive columns.
+// squared norms of the two checksum rows.  Unit = 2048 columns (chunk cx) x
+// one verify block I; thread = 8 consecutive columns.
+__device__ __forceinline__ void lpA_cols_unit(const __nv_bfloat16* __restrict__ A, int64_t lda,
+                                              int64_t m, int64_t k, int vb, int e,
+                                              __nv_bfloat16* __restrict__ acs, int64_t ldk,
+                                              float* __restrict__ rowpart, int64_t nchr,
+                                              double* __restrict__ part, int64_t nch, int64_t cx,
+                                              int64_t I, double* sh) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c0 = cx * kColsPerCta + 8 * threadIdx.x;
+  const float sc = scalbnf(1.0f, -e);
+  const int64_t i0 = I * vb, i1 = min(i0 + (int64_t)vb, m);
+  float se[8], sw[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) se[q] = sw[q] = 0.f;
+  for (int64_t i = i0; i < i1; ++i) {
+    float v[8];
+    load8(A + i * lda, c0, k, v);
+    const float w = (float)(i - i0 + 1) * sc;
+    float sq = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      se[q] += v[q];
+      sw[q] = fmaf(w, v[q], sw[q]);
+      sq = fmaf(v[q], v[q], sq);
+    }
+    sq = warp_sumf(sq);
+    const int64_t rc = cx * (kThreads / 32) + warp;  // 256-column chunk
+    if (lane == 0 && rc < nchr) rowpart[i * nchr + rc] = sq;
+  }
+  double q0 = 0.0, q1 = 0.0;
+  if (c0 < ldk) {
+    __nv_bfloat16 eh[8], el[8], wh[8], wl[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      split(se[q], eh[q], el[q]);
+      split(sw[q], wh[q], wl[q]);
+      q0 += (double)se[q] * se[q];
+      q1 += (double)sw[q] * sw[q];
+    }
+    store8(acs + (4 * I + 0) * ldk + c0, eh);
+    store8(acs + (4 * I + 1) * ldk + c0, el);
+    store8(acs + (4 * I + 2) * ldk + c0, wh);
+    store8(acs + (4 * I + 3) * ldk + c0, wl);
+  }
+  const double t0 = block_sum(q0, sh);
+  if (threadIdx.x == 0) part[(2 * I) * nch + cx] = t0;
+  const double t1 = block_sum(q1, sh);
+  if (threadIdx.x == 0) part[(2 * I + 1) * nch + cx] = t1;
+}
+
 __global__ void __launch_bounds__(kThreads) k_lpA_cols(const __nv_bfloat16* __restrict__ A,
                                                        int64_t lda, int64_t m, int64_t k, int vb,
                                                        int e, __nv_bfloat16* __restrict__ acs,
@@ -86,50 +135,9 @@ __global__ void __launch_bounds__(kThreads) k_lpA_cols(const __nv_bfloat16* __re
                                                        int64_t nchr, double* __restrict__ part,
                                                        int64_t nch) {
   __shared__ double sh[kThreads / 32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t c0 = (int64_t)blockIdx.x * kColsPerCta + 8 * threadIdx.x;
   const int64_t nvb = cdiv(m, vb);
-  const float sc = scalbnf(1.0f, -e);
-  for (int64_t I = blockIdx.y; I < nvb; I += gridDim.y) {
-    const int64_t i0 = I * vb, i1 = min(i0 + (int64_t)vb, m);
-    float se[8], sw[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) se[q] = sw[q] = 0.f;
-    for (int64_t i = i0; i < i1; ++i) {
-      float v[8];
-      load8(A + i * lda, c0, k, v);
-      const float w = (float)(i - i0 + 1) * sc;
-      float sq = 0.f;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        se[q] += v[q];
-        sw[q] = fmaf(w, v[q], sw[q]);
-        sq = fmaf(v[q], v[q], sq);
-      }
-      sq = warp_sumf(sq);
-      const int64_t rc = (int64_t)blockIdx.x * (kThreads / 32) + warp;  // 256-column chunk
-      if (lane == 0 && rc < nchr) rowpart[i * nchr + rc] = sq;
-    }
-    double q0 = 0.0, q1 = 0.0;
-    if (c0 < ldk) {
-      __nv_bfloat16 eh[8], el[8], wh[8], wl[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        split(se[q], eh[q], el[q]);
-        split(sw[q], wh[q], wl[q]);
-        q0 += (double)se[q] * se[q];
-        q1 += (double)sw[q] * sw[q];
-      }
-      store8(acs + (4 * I + 0) * ldk + c0, eh);
-      store8(acs + (4 * I + 1) * ldk + c0, el);
-      store8(acs + (4 * I + 2) * ldk + c0, wh);
-      store8(acs + (4 * I + 3) * ldk + c0, wl);
-    }
-    const double t0 = block_sum(q0, sh);
-    if (threadIdx.x == 0) part[(2 * I) * nch + blockIdx.x] = t0;
-    const double t1 = block_sum(q1, sh);
-    if (threadIdx.x == 0) part[(2 * I + 1) * nch + blockIdx.x] = t1;
-  }
+  for (int64_t I = blockIdx.y; I < nvb; I += gridDim.y)
+    lpA_cols_unit(A, lda, m, k, vb, e, acs, ldk, rowpart, nchr, part, nch, blockIdx.x, I, sh);
 }
 
 // Block checksum rows S_A[t] = sum_I A[I*bs + t], as hi/lo pieces.
@@ -152,16 +160,17 @@ __global__ void __launch_bounds__(kThreads) k_lpA_block(const __nv_bfloat16* __r
 // Row checksums of B per verify column block (hi/lo pieces in the row-major
 // bcs), per-column partial sums of squares (one per 128 rows) and partials
 // of the squared norms of the checksum columns.  Verify blocks of 8, 16, ...,
-// 256 columns: the lanes of a block reduce with shuffles.  CTA = 2048
-// columns x 128 rows; thread = 8 consecutive columns.
-__global__ void __launch_bounds__(kThreads) k_lpB_rows(const __nv_bfloat16* __restrict__ B,
-                                                       int64_t ldb, int64_t k, int64_t n, int vb,
-                                                       int e, __nv_bfloat16* __restrict__ bcs,
-                                                       int64_t ldcs, float* __restrict__ colpart,
-                                                       double* __restrict__ part, int64_t nch) {
+// 256 columns: the lanes of a block reduce with shuffles.  Unit = 2048
+// columns (chunk cx) x 128 rows (chunk ry); thread = 8 consecutive columns.
+__device__ __forceinline__ void lpB_rows_unit(const __nv_bfloat16* __restrict__ B, int64_t ldb,
+                                              int64_t k, int64_t n, int vb, int e,
+                                              __nv_bfloat16* __restrict__ bcs, int64_t ldcs,
+                                              float* __restrict__ colpart,
+                                              double* __restrict__ part, int64_t nch, int64_t cx,
+                                              int64_t ry) {
   const int lane = threadIdx.x & 31;
-  const int64_t c0 = (int64_t)blockIdx.x * kColsPerCta + 8 * threadIdx.x;
-  const int64_t l0 = (int64_t)blockIdx.y * kRowsPerCtaB, l1 = min(l0 + kRowsPerCtaB, k);
+  const int64_t c0 = cx * kColsPerCta + 8 * threadIdx.x;
+  const int64_t l0 = ry * kRowsPerCtaB, l1 = min(l0 + kRowsPerCtaB, k);
   const int seg = vb / 8;  // lanes per verify block (1 .. 32)
   const bool leader = (lane % seg) == 0 && c0 < n;
   const int64_t J = c0 / vb;
@@ -197,12 +206,20 @@ __global__ void __launch_bounds__(kThreads) k_lpB_rows(const __nv_bfloat16* __re
     }
   }
   if (leader) {
-    part[(2 * J) * nch + blockIdx.y] = q0;
-    part[(2 * J + 1) * nch + blockIdx.y] = q1;
+    part[(2 * J) * nch + ry] = q0;
+    part[(2 * J + 1) * nch + ry] = q1;
   }
 #pragma unroll
   for (int q = 0; q < 8; ++q)
-    if (c0 + q < n) colpart[blockIdx.y * n + c0 + q] = cs[q];
+    if (c0 + q < n) colpart[ry * n + c0 + q] = cs[q];
+}
+
+__global__ void __launch_bounds__(kThreads) k_lpB_rows(const __nv_bfloat16* __restrict__ B,
+                                                       int64_t ldb, int64_t k, int64_t n, int vb,
+                                                       int e, __nv_bfloat16* __restrict__ bcs,
+                                                       int64_t ldcs, float* __restrict__ colpart,
+                                                       double* __restrict__ part, int64_t nch) {
+  lpB_rows_unit(B, ldb, k, n, vb, e, bcs, ldcs, colpart, part, nch, blockIdx.x, blockIdx.y);
 }
 
 // The same outputs for any verify block size (one warp per row segment).
@@ -278,12 +295,11 @@ __global__ void k_lp_norms(const float* __restrict__ part, int64_t nout, int64_t
   out[o] = sqrt(s);
 }
 
-// Threshold norms of each verify block from the line norms and the checksum
+// Threshold norms of verify block I from the line norms and the checksum
 // partials (see the binary64 encode for the definitions).
-__global__ void k_lp_blk(const double* __restrict__ nvec, int64_t len, int vb, int e,
-                         const double* __restrict__ part, int64_t nch, double* __restrict__ nblk) {
-  const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (I >= cdiv(len, vb)) return;
+__device__ __forceinline__ void lp_blk_one(const double* __restrict__ nvec, int64_t len, int vb,
+                                           int e, const double* __restrict__ part, int64_t nch,
+                                           double* __restrict__ nblk, int64_t I) {
   const double sc = scalbn(1.0, -e);
   const int64_t t0 = I * vb, t1 = min(t0 + (int64_t)vb, len);
   double f0 = 0.0, f1 = 0.0, q0 = 0.0, q1 = 0.0;
@@ -300,6 +316,13 @@ __global__ void k_lp_blk(const double* __restrict__ nvec, int64_t len, int vb, i
   nblk[4 * I + 1] = sqrt(f1);
   nblk[4 * I + 2] = sqrt(q0);
   nblk[4 * I + 3] = sqrt(q1);
+}
+
+__global__ void k_lp_blk(const double* __restrict__ nvec, int64_t len, int vb, int e,
+                         const double* __restrict__ part, int64_t nch, double* __restrict__ nblk) {
+  const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= cdiv(len, vb)) return;
+  lp_blk_one(nvec, len, vb, e, part, nch, nblk, I);
 }
 
 // ---------------- split bf16x3 (binary32 inputs)
@@ -706,6 +729,85 @@ cudaError_t launch_gemm_lp(const Plan& P, const void* A, const void* B, float* C
   k_fold_E<<<dim3((unsigned)cdiv(d.n, 256), gy(P.R)), 256, 0, st>>>(E16, P.R, npc, d.n, E);
   k_fold_F<<<(unsigned)cdiv(d.m * P.Cc, 256), 256, 0, st>>>(F16, d.m, P.Cc, P.L.bcs_cols, npc, F);
   count_launches(2);
+  return cudaGetLastError();
+}
+
+// ---------------- grouped encode (many bf16 problems per launch)
+namespace {
+
+__global__ void __launch_bounds__(kThreads) k_grp_encA(const GProb* __restrict__ probs,
+                                                       const int64_t* __restrict__ off,
+                                                       int count) {
+  __shared__ double sh[kThreads / 32];
+  const int p = find_prob(off, count, blockIdx.x);
+  const GProb& P = probs[p];
+  const int64_t u = blockIdx.x - off[p], nchA = cdiv(P.k, kColsPerCta);
+  lpA_cols_unit(static_cast<const __nv_bfloat16*>(P.A), P.lda, P.m, P.k, kGrpVbR, kGrpEr,
+                static_cast<__nv_bfloat16*>(P.acs), P.acs_ld, P.rowpart, cdiv(P.k, 256), P.partA,
+                nchA, u % nchA, u / nchA, sh);
+}
+
+__global__ void __launch_bounds__(kThreads) k_grp_encB(const GProb* __restrict__ probs,
+                                                       const int64_t* __restrict__ off,
+                                                       int count) {
+  const int p = find_prob(off, count, blockIdx.x);
+  const GProb& P = probs[p];
+  const int64_t u = blockIdx.x - off[p], ncx = cdiv(P.n, kColsPerCta);
+  lpB_rows_unit(static_cast<const __nv_bfloat16*>(P.B), P.ldb, P.k, P.n, kGrpVbC, kGrpEc,
+                static_cast<__nv_bfloat16*>(P.bcs), P.bcs_ld, P.colpart, P.partB,
+                cdiv(P.k, kRowsPerCtaB), u % ncx, u / ncx);
+}
+
+// Row norms ||A_i|| (first ceil(m/256) CTAs of a problem) and column norms
+// ||B_:j|| (next ceil(n/256)) from the fp32 partial sums of squares.
+__global__ void __launch_bounds__(kThreads) k_grp_lines(const GProb* __restrict__ probs,
+                                                        const int64_t* __restrict__ off,
+                                                        int count) {
+  const int p = find_prob(off, count, blockIdx.x);
+  const GProb& P = probs[p];
+  const int64_t u = blockIdx.x - off[p], nra = cdiv(P.m, kThreads);
+  if (u < nra) {
+    const int64_t i = u * kThreads + threadIdx.x;
+    if (i >= P.m) return;
+    const int64_t nchr = cdiv(P.k, 256);
+    double s = 0.0;
+    for (int64_t c = 0; c < nchr; ++c) s += (double)P.rowpart[i * nchr + c];
+    P.nArow[i] = sqrt(s);
+  } else {
+    const int64_t j = (u - nra) * kThreads + threadIdx.x;
+    if (j >= P.n) return;
+    const int64_t nch = cdiv(P.k, kRowsPerCtaB);
+    double s = 0.0;
+    for (int64_t c = 0; c < nch; ++c) s += (double)P.colpart[c * P.n + j];
+    P.nBcol[j] = sqrt(s);
+  }
+}
+
+// Threshold norms of every verify block; one CTA per problem.
+__global__ void __launch_bounds__(kThreads) k_grp_blk(const GProb* __restrict__ probs) {
+  const GProb& P = probs[blockIdx.x];
+  for (int64_t t = threadIdx.x; t < P.nvr + P.nvc; t += kThreads) {
+    if (t < P.nvr)
+      lp_blk_one(P.nArow, P.m, kGrpVbR, kGrpEr, P.partA, cdiv(P.k, kColsPerCta), P.nAblk, t);
+    else
+      lp_blk_one(P.nBcol, P.n, kGrpVbC, kGrpEc, P.partB, cdiv(P.k, kRowsPerCtaB), P.nBblk,
+                 t - P.nvr);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_group_encode(const GroupDev& G, cudaStream_t st) {
+  if (G.count == 0) return cudaSuccess;
+  if (G.nctas[kGkEncA] > 0)
+    k_grp_encA<<<(unsigned)G.nctas[kGkEncA], kThreads, 0, st>>>(G.probs, G.off[kGkEncA], G.count);
+  if (G.nctas[kGkEncB] > 0)
+    k_grp_encB<<<(unsigned)G.nctas[kGkEncB], kThreads, 0, st>>>(G.probs, G.off[kGkEncB], G.count);
+  if (G.nctas[kGkLines] > 0)
+    k_grp_lines<<<(unsigned)G.nctas[kGkLines], kThreads, 0, st>>>(G.probs, G.off[kGkLines],
+                                                                  G.count);
+  k_grp_blk<<<(unsigned)G.count, kThreads, 0, st>>>(G.probs);
+  count_launches(4);
   return cudaGetLastError();
 }
 

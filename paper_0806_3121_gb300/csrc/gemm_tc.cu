@@ -117,27 +117,43 @@ __device__ __forceinline__ Tile decode_local(int64_t t, int64_t ntm, int64_t ntn
   return T;
 }
 
-__device__ __forceinline__ Tile decode(int64_t t, const TcArgs& g) {
-  return decode_local(t, g.ntm, g.ntn, g.ntr, g.ntc);
+__device__ __forceinline__ int64_t clamp64(int64_t v, int64_t lo, int64_t hi) {
+  return v < lo ? lo : (v > hi ? hi : v);
 }
 
-// Everything the three roles need to know about one tile.
+// Everything the three roles need to know about one tile.  The A operand of a
+// tile is two 64-row halves and its B operand nbox 64-column boxes; each half
+// (box) comes either from the data operand or from its checksum operand, so a
+// tile can hold data rows and checksum rows (columns) side by side:
+//   halves [0, hsplit)     data rows      rowD + 64 h           -> C / F16
+//   halves [hsplit, hcnt)  checksum rows  rowC + 64 (h-hsplit)  -> E16
+//   boxes  [0, bsplit)     data columns   colD + 64 b           -> C / E16
+//   boxes  [bsplit, nbox)  checksum cols  colC + 64 (b-bsplit)  -> F16
+// checksum row x checksum column products (the corner) are not stored.
 struct TileView {
-  int kind;                   // 0 data -> C, 1 checksum rows -> E16, 2 checksum columns -> F16
   int prob;                   // problem index (grouped products; 0 otherwise)
-  int64_t row0, col0;         // tile origin in its output
-  float* dst;                 // output and its leading dimension / limits
-  int64_t ld, rlim, clim;
-  const CUtensorMap* ma0;     // A-side maps (plane 0 / 1)
-  const CUtensorMap* ma1;
-  const CUtensorMap* mb0;     // B-side maps
-  const CUtensorMap* mb1;
   int64_t nkb;                // k-blocks per segment
   int nseg;
+  const CUtensorMap* maD;     // A-side maps: data / checksum, plane 0 and 1
+  const CUtensorMap* maD1;
+  const CUtensorMap* maC;
+  const CUtensorMap* maC1;
+  const CUtensorMap* mbD;     // B-side maps
+  const CUtensorMap* mbD1;
+  const CUtensorMap* mbC;
+  const CUtensorMap* mbC1;
+  int32_t rowD, rowC, colD, colC;
+  int hsplit, hcnt, bsplit, nbox;
+  float* C;                   // data x data, ld ldc, m x n
+  int64_t ldc, m, n;
+  float* E16;                 // checksum rows x data columns, ld n, R16 rows
+  int64_t R16;
+  float* F16;                 // data rows x checksum columns, ld C16
+  int64_t C16;
   // fused observed checksums of data tiles (obs_col == nullptr: off)
-  float* obs_col;
-  float* obs_row;
-  int64_t n, m, g, ngrp;
+  float* obs_col;             // [tile row][2][n]
+  float* obs_row;             // [row][ngrp][2]
+  int64_t g, ngrp;
   int vb_r, vb_c, er, ec;
 };
 
@@ -156,25 +172,37 @@ struct SingleSched {
   }
   __device__ __forceinline__ TileView view(int64_t t) const {
     const TcArgs& g = *a;
-    const Tile T = decode(t, g);
+    const Tile T = decode_local(t, g.ntm, g.ntn, g.ntr, g.ntc);
     TileView V;
-    V.kind = T.kind;
     V.prob = 0;
-    V.row0 = T.row0;
-    V.col0 = T.col0;
-    if (T.kind == 0) { V.dst = g.C; V.ld = g.ldc; V.rlim = g.m; V.clim = g.n; }
-    else if (T.kind == 1) { V.dst = g.E16; V.ld = g.n; V.rlim = g.R16; V.clim = g.n; }
-    else { V.dst = g.F16; V.ld = g.C16; V.rlim = g.m; V.clim = g.C16; }
-    V.ma0 = T.kind == 1 ? &M->acs[0] : &M->a[0];
-    V.ma1 = T.kind == 1 ? &M->acs[1] : &M->a[1];
-    V.mb0 = T.kind == 2 ? &M->bcs[0] : &M->b[0];
-    V.mb1 = T.kind == 2 ? &M->bcs[1] : &M->b[1];
     V.nkb = (g.k + BK - 1) / BK;
     V.nseg = g.nseg;
+    V.maD = &M->a[0];
+    V.maD1 = &M->a[1];
+    V.maC = &M->acs[0];
+    V.maC1 = &M->acs[1];
+    V.mbD = &M->b[0];
+    V.mbD1 = &M->b[1];
+    V.mbC = &M->bcs[0];
+    V.mbC1 = &M->bcs[1];
+    V.rowD = V.rowC = (int32_t)T.row0;
+    V.colD = V.colC = (int32_t)T.col0;
+    const int hrows = (int)clamp64(cdiv((T.kind == 1 ? g.R16 : g.m) - T.row0, 64), 1, 2);
+    const int bcols = (int)clamp64(cdiv((T.kind == 2 ? g.C16 : g.n) - T.col0, 64), 1, 4);
+    V.hsplit = T.kind == 1 ? 0 : hrows;
+    V.hcnt = hrows;
+    V.bsplit = T.kind == 2 ? 0 : bcols;
+    V.nbox = bcols;
+    V.C = g.C;
+    V.ldc = g.ldc;
+    V.m = g.m;
+    V.n = g.n;
+    V.E16 = g.E16;
+    V.R16 = g.R16;
+    V.F16 = g.F16;
+    V.C16 = g.C16;
     V.obs_col = T.kind == 0 ? g.obs_col : nullptr;
     V.obs_row = g.obs_row;
-    V.n = g.n;
-    V.m = g.m;
     V.g = g.g;
     V.ngrp = g.ngrp;
     V.vb_r = g.vb_r;
@@ -186,8 +214,7 @@ struct SingleSched {
 };
 
 __device__ __forceinline__ void store_row32(float* dst, int64_t ld, int64_t row, int64_t col,
-                                            int64_t rlim, int64_t clim, const float (&v)[32]) {
-  if (row >= rlim) return;
+                                            int64_t clim, const float (&v)[32]) {
   float* p = dst + row * ld + col;
   if (col + 32 <= clim && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
 #pragma unroll
@@ -273,19 +300,25 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
         const TileView T = S.view(t);
         if (stall_test && t == 0) continue;  // nothing will fill these stages
         const int64_t nkb = T.nkb, nkt = T.nkb * T.nseg;
+        const uint32_t tx = (uint32_t)T.hcnt * (A_BYTES / 2) + (uint32_t)T.nbox * B_BOX_BYTES;
         for (int64_t kt = 0; kt < nkt; ++kt) {
           const int seg = (int)(kt / nkb);
-          const int64_t kb = kt - (int64_t)seg * nkb;
-          const CUtensorMap* ma = seg == 2 ? T.ma1 : T.ma0;
-          const CUtensorMap* mb = seg == 1 ? T.mb1 : T.mb0;
+          const int32_t kx = (int32_t)((kt - (int64_t)seg * nkb) * BK);
           if (!tc::wait(empty(s), ph ^ 1, abort)) break;
           const uint32_t sa = tc::smem_addr(smem + s * STAGE_BYTES);
-          tc::mbar_arrive_expect_tx(full(s), STAGE_BYTES);
-          tc::tma_load_2d(sa, ma, full(s), (int32_t)(kb * BK), (int32_t)T.row0);
-#pragma unroll
-          for (int c = 0; c < BN / 64; ++c)
-            tc::tma_load_2d(sa + A_BYTES + c * B_BOX_BYTES, mb, full(s), (int32_t)(T.col0 + 64 * c),
-                            (int32_t)(kb * BK));
+          tc::mbar_arrive_expect_tx(full(s), tx);
+          for (int h = 0; h < T.hcnt; ++h) {
+            const bool dat = h < T.hsplit;
+            const CUtensorMap* ma = dat ? (seg == 2 ? T.maD1 : T.maD) : (seg == 2 ? T.maC1 : T.maC);
+            const int32_t y = dat ? T.rowD + 64 * h : T.rowC + 64 * (h - T.hsplit);
+            tc::tma_load_2d(sa + h * (A_BYTES / 2), ma, full(s), kx, y);
+          }
+          for (int b = 0; b < T.nbox; ++b) {
+            const bool dat = b < T.bsplit;
+            const CUtensorMap* mb = dat ? (seg == 1 ? T.mbD1 : T.mbD) : (seg == 1 ? T.mbC1 : T.mbC);
+            const int32_t x = dat ? T.colD + 64 * b : T.colC + 64 * (b - T.bsplit);
+            tc::tma_load_2d(sa + A_BYTES + b * B_BOX_BYTES, mb, full(s), x, kx);
+          }
           ++issued;
           if (++s == STAGES) { s = 0; ph ^= 1; }
         }
@@ -302,12 +335,12 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      constexpr uint32_t idesc = tc::idesc_bf16(BM, BN, 1);
       int s = 0, acc = 0;
       uint32_t ph = 0, aph = 0;
       for (int64_t t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
         const TileView T = S.view(t);
         const int64_t nkt = T.nkb * T.nseg;
+        const uint32_t idesc = tc::idesc_bf16(BM, 64 * T.nbox, 1);
         if (!tc::wait(tempty(acc), aph ^ 1, abort)) break;
         tc::fence_after_sync();
         const uint32_t d = tmem + acc * BN;
@@ -343,7 +376,7 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
     __syncwarp();
   } else {
     // ---------------- epilogue: warps 2..5, TMEM lane quarter = warp % 4
-    const int q = warp & 3;
+    const int q = warp & 3, half = q >> 1;
     float* obs = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);  // [4][BN][2]
     const int ninj = (inj_hdr && inj_hdr[0] == kInjectMagic)
                          ? max(0, min(inj_hdr[1], kMaxInject)) : 0;
@@ -353,56 +386,71 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
       const TileView T = S.view(t);
       if (!tc::wait(tfull(acc), aph, abort)) break;
       tc::fence_after_sync();
-      float* const dst = T.dst;
-      const int64_t ld = T.ld, rlim = T.rlim, clim = T.clim;
-      const int64_t row = T.row0 + q * 32 + lane;
-      const bool fused = T.obs_col != nullptr;
+      // this warp's 32 rows: data rows, checksum rows or none
+      const bool drow = half < T.hsplit, crow = !drow && half < T.hcnt;
+      const int64_t rin = 32 * (q & 1) + lane;
+      const int64_t row = drow ? T.rowD + 64 * half + rin : T.rowC + 64 * (half - T.hsplit) + rin;
+      const bool rvalid = drow ? row < T.m : (crow && row < T.R16);
+      const int ndcol = 64 * T.bsplit, ncol = 64 * T.nbox;
+      const bool fused = T.obs_col != nullptr && T.hsplit > 0 && T.bsplit > 0;
       const float scr = scalbnf(1.0f, -T.er), scc = scalbnf(1.0f, -T.ec);
-      const float wrow = fused ? (float)((int)(row % T.vb_r) + 1) * scr : 0.f;
+      const float wrow = (fused && drow) ? (float)((int)(row % T.vb_r) + 1) * scr : 0.f;
       float racc_e = 0.f, racc_w = 0.f;
       const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
 #pragma unroll 1
-      for (int c = 0; c < BN; c += 32) {
+      for (int c = 0; c < ncol; c += 32) {
         float v[32];
         tc::tmem_ld32(base + c, v);
-        if (T.col0 + c >= clim) continue;
-        const int64_t col = T.col0 + c;
-        if (T.kind == 0)
-          for (int f = 0; f < ninj; ++f) {
-            const InjectEntry ie = inj[f];
-            if (ie.pad == T.prob && ie.row == row && ie.col >= col && ie.col < col + 32) {
-              const int x = ie.col - (int)col;
+        const bool dcol = c < ndcol;
+        if (dcol) {
+          const int64_t col = T.colD + c;
+          if (col >= T.n) continue;
+          if (drow) {
+            for (int f = 0; f < ninj; ++f) {
+              const InjectEntry ie = inj[f];
+              if (ie.pad == T.prob && ie.row == row && ie.col >= col && ie.col < col + 32) {
+                const int x = ie.col - (int)col;
 #pragma unroll
-              for (int u = 0; u < 32; ++u)
-                if (u == x) v[u] = __uint_as_float(__float_as_uint(v[u]) ^ (1u << (ie.bit & 31)));
+                for (int u = 0; u < 32; ++u)
+                  if (u == x) v[u] = __uint_as_float(__float_as_uint(v[u]) ^ (1u << (ie.bit & 31)));
+              }
             }
+            if (rvalid) store_row32(T.C, T.ldc, row, col, T.n, v);
+          } else if (rvalid) {
+            store_row32(T.E16, T.n, row, col, T.n, v);
           }
-        store_row32(dst, ld, row, col, rlim, clim, v);
-        if (fused) {
-          // row partials over the column group (weights restart per verify block;
-          // a 32-column chunk never straddles one)
-          const int cm = (int)(col % T.vb_c) + 1;
+          if (fused) {
+            // row partials over the column group (weights restart per verify
+            // block; a 32-column chunk never straddles one)
+            const int cm = (int)(col % T.vb_c) + 1;
 #pragma unroll
-          for (int u = 0; u < 32; ++u) {
-            racc_e += v[u];
-            racc_w = fmaf((float)(cm + u) * scc, v[u], racc_w);
-          }
-          if (((c + 32) % (int)T.g) == 0 || c + 32 == BN || col + 32 >= clim) {
-            if (row < T.m) {
-              float* o = T.obs_row + (row * T.ngrp + (int)(col / T.g)) * 2;
-              o[0] = racc_e;
-              o[1] = racc_w;
+            for (int u = 0; u < 32; ++u) {
+              racc_e += v[u];
+              racc_w = fmaf((float)(cm + u) * scc, v[u], racc_w);
             }
-            racc_e = racc_w = 0.f;
-          }
-          // column partials of this warp's 32 rows
-          float vw[32];
+            if (((col + 32) % T.g) == 0 || c + 32 == ndcol || col + 32 >= T.n) {
+              if (drow && rvalid) {
+                float* o = T.obs_row + (row * T.ngrp + (int)(col / T.g)) * 2;
+                o[0] = racc_e;
+                o[1] = racc_w;
+              }
+              racc_e = racc_w = 0.f;
+            }
+            // column partials of this warp's 32 rows (zero for non-data rows)
+            float vw[32];
 #pragma unroll
-          for (int u = 0; u < 32; ++u) vw[u] = wrow * v[u];
-          transpose_reduce(v, lane);
-          transpose_reduce(vw, lane);
-          obs[(q * BN + c + lane) * 2 + 0] = v[0];
-          obs[(q * BN + c + lane) * 2 + 1] = vw[0];
+            for (int u = 0; u < 32; ++u) {
+              if (!drow) v[u] = 0.f;
+              vw[u] = wrow * v[u];
+            }
+            transpose_reduce(v, lane);
+            transpose_reduce(vw, lane);
+            obs[(q * BN + c + lane) * 2 + 0] = v[0];
+            obs[(q * BN + c + lane) * 2 + 1] = vw[0];
+          }
+        } else if (drow && rvalid) {
+          const int64_t col = T.colC + (c - ndcol);
+          if (col < T.C16) store_row32(T.F16, T.C16, row, col, T.C16, v);
         }
       }
       tc::fence_before_sync();
@@ -412,15 +460,14 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
       if (fused) {
         epi_barrier();
         const int et = q * 32 + lane;  // 0..127
-        const int64_t tr = T.row0 / BM;
+        const int64_t tr = T.rowD / BM;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int cc = et + h * 128;
-          const int64_t col = T.col0 + cc;
-          if (col < T.n) {
+          const int64_t col = T.colD + cc;
+          if (cc < ndcol && col < T.n) {
             float se = 0.f, sw = 0.f;
-#pragma unroll
-            for (int w4 = 0; w4 < 4; ++w4) {
+            for (int w4 = 0; w4 < 2 * T.hsplit; ++w4) {
               se += obs[(w4 * BN + cc) * 2 + 0];
               sw += obs[(w4 * BN + cc) * 2 + 1];
             }
@@ -448,58 +495,69 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_body(S, g.status, g.wait_ns, g.stall_test, g.inj_hdr, g.inj);
 }
 
-// Many problems (grouped product): the flattened tile list is the problems'
-// tile lists one after the other; per-problem tables and tensor maps live in
-// global memory.  Verify blocks equal the tile (128 x 256).
+// Many problems (grouped product).  The flattened tile list is a table of
+// (problem, tile row, tile column) entries; per-problem sizes, outputs and
+// tensor maps live in global memory.  A problem's rows are its 64-row data
+// halves followed by its checksum halves, its columns its 64-column data
+// boxes followed by its checksum boxes, cut into tiles of two halves and
+// bpt boxes, so checksum rows and columns fill the padding of the last data
+// tiles.  Verify blocks are 128 rows (one tile row) x 256 columns.
 struct GroupSched {
   const GProb* probs;
   const GMaps* maps;
-  int count;
+  const int4* tiles;  // {problem, tile row, tile column, 0}
   int64_t t_total;
   bool checksums;
   __device__ __forceinline__ int64_t total() const { return t_total; }
   __device__ __forceinline__ void prefetch() const {}
   __device__ __forceinline__ TileView view(int64_t t) const {
-    int lo = 0, hi = count - 1;  // last problem with tile_off <= t
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (probs[mid].tile_off <= t) lo = mid; else hi = mid - 1;
-    }
-    const GProb& P = probs[lo];
-    const GMaps& Mp = maps[lo];
-    const Tile T = checksums ? decode_local(t - P.tile_off, P.ntm, P.ntn, P.ntr, P.ntc)
-                             : decode_local(t - P.tile_off, P.ntm, P.ntn, 0, 0);
+    const int4 e = __ldg(&tiles[t]);
+    const GProb& P = probs[e.x];
+    const GMaps& Mp = maps[e.x];
+    const int nhd = (int)cdiv(P.m, 64), nbd = (int)cdiv(P.n, 64);
+    const int nhc = checksums ? P.nhc : 0, nbc = checksums ? P.nbc : 0;
+    const int h0 = 2 * e.y, b0 = P.bpt * e.z;
     TileView V;
-    V.kind = T.kind;
-    V.prob = lo;
-    V.row0 = T.row0;
-    V.col0 = T.col0;
-    if (T.kind == 0) { V.dst = P.C; V.ld = P.ldc; V.rlim = P.m; V.clim = P.n; }
-    else if (T.kind == 1) { V.dst = P.E16; V.ld = P.n; V.rlim = P.R16; V.clim = P.n; }
-    else { V.dst = P.F16; V.ld = P.C16; V.rlim = P.m; V.clim = P.C16; }
-    V.ma0 = V.ma1 = T.kind == 1 ? &Mp.acs : &Mp.a;
-    V.mb0 = V.mb1 = T.kind == 2 ? &Mp.bcs : &Mp.b;
-    V.nkb = (P.k + BK - 1) / BK;
+    V.prob = e.x;
+    V.nkb = cdiv(P.k, BK);
     V.nseg = 1;
-    V.obs_col = (T.kind == 0 && checksums) ? P.obs_col : nullptr;
-    V.obs_row = P.obs_row;
-    V.n = P.n;
+    V.maD = V.maD1 = &Mp.a;
+    V.maC = V.maC1 = &Mp.acs;
+    V.mbD = V.mbD1 = &Mp.b;
+    V.mbC = V.mbC1 = &Mp.bcs;
+    V.hsplit = max(0, min(2, nhd - h0));
+    V.hcnt = min(2, nhd + nhc - h0);
+    V.bsplit = max(0, min(P.bpt, nbd - b0));
+    V.nbox = min(P.bpt, nbd + nbc - b0);
+    V.rowD = 64 * h0;
+    V.rowC = 64 * max(0, h0 - nhd);
+    V.colD = 64 * b0;
+    V.colC = 64 * max(0, b0 - nbd);
+    V.C = P.C;
+    V.ldc = P.ldc;
     V.m = P.m;
-    V.g = kGrpVbC;
-    V.ngrp = P.nvc;
+    V.n = P.n;
+    V.E16 = P.E16;
+    V.R16 = P.R16;
+    V.F16 = P.F16;
+    V.C16 = P.C16;
+    V.obs_col = checksums ? P.obs_col : nullptr;
+    V.obs_row = P.obs_row;
+    V.g = P.g;
+    V.ngrp = P.ngrp;
     V.vb_r = kGrpVbR;
     V.vb_c = kGrpVbC;
-    V.er = 7;
-    V.ec = 8;
+    V.er = kGrpEr;
+    V.ec = kGrpEc;
     return V;
   }
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_grouped(const GProb* probs, const GMaps* maps, int count, int64_t t_total,
+    k_gemm_grouped(const GProb* probs, const GMaps* maps, const int4* tiles, int64_t t_total,
                    int checksums, int* status, uint64_t wait_ns, const int32_t* inj_hdr,
                    const InjectEntry* inj) {
-  const GroupSched S{probs, maps, count, t_total, checksums != 0};
+  const GroupSched S{probs, maps, tiles, t_total, checksums != 0};
   tc_body(S, status, wait_ns, 0, inj_hdr, inj);
 }
 
@@ -582,8 +640,8 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
   for (int pl = 0; pl < 2; ++pl) {
     const void* acs = checksums ? w + P.L.acs + pl * P.L.acs_plane : op.a[0];
     const void* bcs = checksums ? w + P.L.bcs + pl * P.L.bcs_plane : op.b[0];
-    if (!make_map(&M.a[pl], op.a[pl], d.m, d.k, op.lda, 64, BM) ||
-        !make_map(&M.acs[pl], acs, R16, d.k, checksums ? P.L.acs_ld : op.lda, 64, BM) ||
+    if (!make_map(&M.a[pl], op.a[pl], d.m, d.k, op.lda, 64, BM / 2) ||
+        !make_map(&M.acs[pl], acs, R16, d.k, checksums ? P.L.acs_ld : op.lda, 64, BM / 2) ||
         !make_map(&M.b[pl], op.b[pl], d.k, d.n, op.ldb, 64, BK) ||
         !make_map(&M.bcs[pl], bcs, d.k, C16, checksums ? P.L.bcs_ld : op.ldb, 64, BK))
       return cudaErrorInvalidValue;
@@ -641,22 +699,26 @@ cudaError_t make_bf16_map(CUtensorMap* map, const void* ptr, int64_t rows, int64
                                                                 : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_gemm_grouped(const GProb* probs, const GMaps* maps, int count,
-                                int64_t t_total, bool checksums, const int32_t* inj_hdr,
-                                const InjectEntry* inj, cudaStream_t st) {
+cudaError_t launch_group_gemm(const GroupDev& G, bool checksums, cudaStream_t st) {
   int* status = nullptr;
   cudaError_t e = tc_timeout_flag(&status);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_gemm_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)SMEM_BYTES);
-  if (e != cudaSuccess) return e;
-  const int grid = (int)std::min<int64_t>(t_total, num_sms());
+  const int64_t total = checksums ? G.ntiles_cs : G.ntiles_plain;
+  const int grid = (int)std::min<int64_t>(total, num_sms());
   if (grid == 0) return cudaSuccess;
-  k_gemm_grouped<<<grid, kThreads, SMEM_BYTES, st>>>(probs, maps, count, t_total,
-                                                     checksums ? 1 : 0, status,
-                                                     tc::kWaitLimitNs, inj_hdr, inj);
+  k_gemm_grouped<<<grid, kThreads, SMEM_BYTES, st>>>(
+      G.probs, G.maps, checksums ? G.tiles_cs : G.tiles_plain, total, checksums ? 1 : 0, status,
+      tc::kWaitLimitNs, checksums ? G.inj_hdr : nullptr, G.inj);
   count_launches(1);
   return cudaGetLastError();
+}
+
+// One-time kernel attributes (outside any stream capture).
+cudaError_t prepare_group_kernels() {
+  cudaError_t e = get_encoder();
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_gemm_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)SMEM_BYTES);
 }
 
 }  // namespace abft

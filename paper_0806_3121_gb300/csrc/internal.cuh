@@ -37,6 +37,7 @@ struct FlagEntry {  // one flagged line
 struct CandEntry {
   int32_t row, col, kind, side;
   double re, rw;
+  int32_t prob, pad;
 };
 
 struct Erased {
@@ -87,6 +88,15 @@ __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 
 // Host-side count of kernel launches (abft_kernel_launches()).
 void count_launches(int64_t n);
 
+// Error reporting of the C ABI: sets the thread-local message, returns st.
+abft_status fail(abft_status st, const char* fmt, ...);
+abft_status cuda_fail(cudaError_t e, const char* where);
+
+// Detection-threshold factors of a dtype for inner dimension k and verify
+// blocks vb_r x vb_c:  tau = s ||line|| (f1 ||block|| + f2 ||checksum||).
+void threshold_factors(int dtype, int64_t k, int64_t vb_r, int64_t vb_c, double* f1_col,
+                       double* f1_row, double* f2);
+
 // Launchers (return cudaGetLastError() of the launches).
 cudaError_t launch_encode_f64(const Plan& P, const double* A, const double* B, void* ws,
                               cudaStream_t st);
@@ -116,55 +126,89 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
 cudaError_t tc_timeout_flag(int** dev_ptr);
 
 // ---- grouped products (many independent bf16 problems, one launch per step)
-// Verify blocks are fixed to the product tile: 128 rows x 256 columns.
-constexpr int kGrpVbR = 128, kGrpVbC = 256;
+// Verify blocks: 128 rows (one product tile row) x 256 columns.
+constexpr int kGrpVbR = 128, kGrpVbC = 256, kGrpEr = 7, kGrpEc = 8;
 
-struct GProb {
+struct GProb {  // one problem of a group, in device memory
   int64_t m, n, k, lda, ldb, ldc;
   const void* A;  // bf16 m x k (lda)
   const void* B;  // bf16 k x n (ldb)
-  float* C;       // m x n (ldc)
-  void* acs;      // bf16 (4 nvr) x acs_ld: e-hi, e-lo, w-hi, w-lo per verify block
-  void* bcs;      // bf16 k x bcs_ld: 4 pieces per verify column block
+  float* C;       // fp32 m x n (ldc)
+  void* acs;      // bf16 R16 x acs_ld: per verify block e-hi, e-lo, w-hi, w-lo rows
+  void* bcs;      // bf16 k x bcs_ld: per verify column block the same 4 columns
   int64_t acs_ld, bcs_ld, R16, C16;
-  float* E16;     // R16 x n
-  float* F16;     // m x C16
-  float* obs_col;  // [tile row][2][n]
-  float* obs_row;  // [row][nvc][2]
-  double* nArow;
-  double* nAblk;
-  double* nBcol;
-  double* nBblk;
-  float* rowpart;  // m x ceil(k/256)
+  float* E16;      // R16 x n: acs B
+  float* F16;      // m x C16: A bcs
+  float* obs_col;  // [tile row][2][n]: observed e/w column sums of each 128-row tile
+  float* obs_row;  // [row][ngrp][2]: observed e/w row sums of each g-column group
+  double* nArow;   // m: ||A_i||
+  double* nAblk;   // 4 nvr: threshold norms of each verify row block
+  double* nBcol;   // n: ||B_:j||
+  double* nBblk;   // 4 nvc
+  float* rowpart;  // m x ceil(k/256) squared-norm partials
   float* colpart;  // ceil(k/128) x n
   double* partA;   // 2 nvr x ceil(k/2048)
   double* partB;   // 2 nvc x ceil(k/128)
-  int64_t nvr, nvc;
-  double f1c, f1r, f2;  // threshold factors (s applied at use)
-  // offsets of this problem in the flattened grids
-  int64_t tile_off;    // product tiles
-  int64_t encA_off;    // A-side encode CTAs (2048 columns x a verify block)
-  int64_t encB_off;    // B-side encode CTAs (2048 columns x 128 rows)
-  int64_t rows_off;    // rows (row norms, row lines)
-  int64_t cols_off;    // columns (column norms)
-  int64_t vbr_off;     // verify row blocks
-  int64_t vbc_off;     // verify column blocks
-  int64_t cline_off;   // column lines (verify block x column)
-  int32_t ntm, ntn, ntr, ntc;
+  int64_t nvr, nvc, ngrp;
+  double f1c, f1r, f2;  // threshold factors (the safety factor applies at use)
+  int32_t nhc, nbc;     // checksum halves (64 rows) / boxes (64 columns)
+  int32_t bpt, g;       // boxes per tile (tile width 64 bpt), row-sum group width
 };
 
-struct GMaps {  // tensor maps of one problem (global memory, 64-byte aligned)
-  alignas(64) CUtensorMap a;
-  alignas(64) CUtensorMap acs;
-  alignas(64) CUtensorMap b;
-  alignas(64) CUtensorMap bcs;
+struct GMaps {  // tensor maps of one problem (64-byte aligned in device memory)
+  CUtensorMap a, acs, b, bcs;
 };
+
+// CTA offsets of the grouped kernels: off[p] .. off[p+1] are problem p's CTAs.
+enum GroupKernel : int {
+  kGkEncA = 0,   // A column checksums: nvr x ceil(k/2048)
+  kGkEncB,       // B row checksums: ceil(n/2048) x ceil(k/128)
+  kGkLines,      // line norms: ceil(m/256) + ceil(n/256)
+  kGkColCheck,   // column lines: nvr x ceil(n/256)
+  kGkRowCheck,   // row lines: ceil(m nvc / 256)
+  kGkCount
+};
+
+struct GroupDev {  // device view of a bound group (every pointer in the workspace)
+  const GProb* probs;
+  const GMaps* maps;
+  int count;
+  const int4* tiles_cs;     // product tiles with checksums
+  int64_t ntiles_cs;
+  const int4* tiles_plain;  // product tiles without checksums
+  int64_t ntiles_plain;
+  const int64_t* off[kGkCount];
+  int64_t nctas[kGkCount];
+  double s;                 // threshold safety factor
+  int32_t* cnt;             // verify counters
+  FlagEntry* colf;          // flagged lines (pad = problem)
+  FlagEntry* rowf;
+  CandEntry* cand;
+  abft_fault* report;
+  int32_t* inj_hdr;         // armed epilogue injections
+  InjectEntry* inj;
+};
+
+// Problem owning CTA b of a grouped kernel: the last p with off[p] <= b
+// (problems without CTAs have off[p] == off[p+1] and are skipped).
+__device__ __forceinline__ int find_prob(const int64_t* off, int count, int64_t b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
 
 cudaError_t make_bf16_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols,
                           int64_t ld, uint32_t box_cols, uint32_t box_rows);
-cudaError_t launch_gemm_grouped(const GProb* probs, const GMaps* maps, int count,
-                                int64_t t_total, bool checksums, const int32_t* inj_hdr,
-                                const InjectEntry* inj, cudaStream_t st);
+cudaError_t launch_group_encode(const GroupDev& G, cudaStream_t st);
+cudaError_t launch_group_gemm(const GroupDev& G, bool checksums, cudaStream_t st);
+cudaError_t launch_group_verify(const GroupDev& G, cudaStream_t st);
+cudaError_t prepare_group_kernels();
+// Arms `count` epilogue injections (count = 0 disarms) in the region at hdr.
+cudaError_t launch_set_inject_raw(int32_t* hdr, const InjectEntry* entries, int count,
+                                  cudaStream_t st);
 cudaError_t consume_tc_timeout(cudaStream_t st, bool* timed_out);
 cudaError_t launch_verify(const Plan& P, void* C, void* ws, const Erased& er, bool reread,
                           cudaStream_t st);

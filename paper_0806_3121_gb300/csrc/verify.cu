@@ -267,17 +267,77 @@ __device__ __forceinline__ int64_t ratio_position(double re, double rw, int e, i
   return (int64_t)r - 1;
 }
 
-__device__ __forceinline__ void push_report(const CheckArgs& a, int32_t row, int32_t col, int kind,
-                                            int side, double delta, double re, double rw) {
-  const int slot = atomicAdd(&a.cnt[kCntReport], 1);
-  if (slot < kCapReport) a.report[slot] = abft_fault{row, col, kind, side, delta, re, rw};
-}
-
-__device__ __forceinline__ int32_t key_row(uint64_t k) { return (int32_t)(k >> 32); }
-__device__ __forceinline__ int32_t key_col(uint64_t k) { return (int32_t)((k >> 1) & 0x7fffffffu); }
+// Access to the problem (or problems) a locate pass works on: geometry,
+// elements of C, expected checksums, re-checks of lines and the sort keys of
+// candidate elements (problem, row, column, side).
+struct Geo {
+  int64_t m, n, vb_r, vb_c;
+  int er, ec;
+};
 
 template <typename TC>
-__global__ void __launch_bounds__(kLocThreads, 1) k_locate_correct(const CheckArgs a) {
+struct SinglePol {
+  CheckArgs a;
+  __device__ __forceinline__ Geo geo(int) const {
+    return Geo{a.m, a.n, a.vb_r, a.vb_c, a.er, a.ec};
+  }
+  __device__ __forceinline__ double ldc(int, int64_t i, int64_t j) const {
+    return ld<TC>(a.C, i * a.ldc + j);
+  }
+  // Stores v rounded to C's type; returns the old value minus the new one.
+  __device__ __forceinline__ double stc(int, int64_t i, int64_t j, double v) const {
+    TC* Cp = static_cast<TC*>(const_cast<void*>(a.C));
+    const TC old = Cp[i * a.ldc + j], nv = (TC)v;
+    Cp[i * a.ldc + j] = nv;
+    return (double)old - (double)nv;
+  }
+  __device__ __forceinline__ double expect_col(int, int64_t I, int64_t j) const {
+    return a.E[(2 * I) * a.n + j];
+  }
+  __device__ __forceinline__ double expect_row(int, int64_t i, int64_t J) const {
+    return a.F[i * a.Cc + 2 * J];
+  }
+  __device__ __forceinline__ bool recheck_col(int, int64_t I, int64_t j, double& re,
+                                              double& rw) const {
+    double te, tw;
+    col_line<TC>(a, I, j, re, rw, te, tw);
+    return is_flagged(re, rw, te, tw);
+  }
+  // Warp-wide; the result is valid in lane 0.
+  __device__ __forceinline__ bool recheck_row(int, int64_t i, int64_t J, double& re,
+                                              double& rw) const {
+    double te, tw;
+    row_line_warp<TC>(a, i, J, re, rw, te, tw);
+    return (threadIdx.x & 31) == 0 && is_flagged(re, rw, te, tw);
+  }
+  __device__ __forceinline__ uint64_t key(int, int64_t r, int64_t c, int side) const {
+    return ((uint64_t)r << 32) | ((uint64_t)c << 1) | (uint64_t)side;
+  }
+  __device__ __forceinline__ int kp(uint64_t) const { return 0; }
+  __device__ __forceinline__ int32_t kr(uint64_t k) const { return (int32_t)(k >> 32); }
+  __device__ __forceinline__ int32_t kc(uint64_t k) const {
+    return (int32_t)((k >> 1) & 0x7fffffffu);
+  }
+};
+
+__device__ __forceinline__ void push_report(abft_fault* report, int32_t* cnt, int prob,
+                                            int32_t row, int32_t col, int kind, int side,
+                                            double delta, double re, double rw) {
+  const int slot = atomicAdd(&cnt[kCntReport], 1);
+  if (slot < kCapReport) {
+    abft_fault f{row, col, kind, side, delta, re, rw};
+    f.problem = prob;
+    report[slot] = f;
+  }
+}
+
+// Locate and correct, one CTA: candidates from the flagged lines, bitonic
+// sort, merge of duplicates, choice of a correcting line, recomputation in
+// binary64, re-check of the touched lines.
+template <class Pol>
+__device__ __forceinline__ void locate_body(const Pol& A, int32_t* cnt, const FlagEntry* colf,
+                                            const FlagEntry* rowf, CandEntry* cand,
+                                            abft_fault* report) {
   __shared__ uint64_t keys[kCapCands];
   __shared__ int32_t sidx[kCapCands];
   __shared__ int32_t how[kCapCands];   // -2 duplicate, -1 uncorrectable, 0 column, 1 row
@@ -286,58 +346,62 @@ __global__ void __launch_bounds__(kLocThreads, 1) k_locate_correct(const CheckAr
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kLocThreads / 32;
   if (tid == 0) s_nc = 0;
   __syncthreads();
-  const int ncf = a.cnt[kCntColFlags], nrf = a.cnt[kCntRowFlags];
+  const int ncf = cnt[kCntColFlags], nrf = cnt[kCntRowFlags];
   const int ncl = min(ncf, kCapFlags), nrl = min(nrf, kCapFlags);
-  if (tid == 0 && (ncf > kCapFlags || nrf > kCapFlags)) a.cnt[kCntOverflow] = 1;
+  if (tid == 0 && (ncf > kCapFlags || nrf > kCapFlags)) cnt[kCntOverflow] = 1;
 
   // 1. candidates
   for (int L = warp; L < ncl + nrl; L += nwarps) {
     const bool colside = L < ncl;
-    const FlagEntry f = colside ? a.colf[L] : a.rowf[L - ncl];
+    const FlagEntry f = colside ? colf[L] : rowf[L - ncl];
+    const int p = f.pad;
+    const Geo G = A.geo(p);
     int64_t row = -1, col = -1;
     int kind = 0;
     if (colside) {
-      const int64_t I = f.a, j = f.b, i0 = I * a.vb_r, i1 = min(i0 + (int64_t)a.vb_r, a.m);
+      const int64_t I = f.a, j = f.b, i0 = I * G.vb_r, i1 = min(i0 + G.vb_r, G.m);
       if (f.nonfin > 0) {
         int c = 0;
         long long pos = LLONG_MAX;
         for (int64_t i = i0 + lane; i < i1; i += 32)
-          if (!isfinite(ld<TC>(a.C, i * a.ldc + j))) { ++c; pos = min(pos, (long long)i); }
+          if (!isfinite(A.ldc(p, i, j))) { ++c; pos = min(pos, (long long)i); }
         c = warp_isum(c);
         pos = warp_min(pos);
         if (c == 1) { row = pos; col = j; kind = ABFT_KIND_NONFINITE_CORRECTED; }
       } else {
-        const int64_t t = ratio_position(f.re, f.rw, a.er, i1 - i0);
+        const int64_t t = ratio_position(f.re, f.rw, G.er, i1 - i0);
         if (t >= 0) { row = i0 + t; col = j; kind = ABFT_KIND_CORRECTED; }
       }
     } else {
-      const int64_t i = f.a, J = f.b, j0 = J * a.vb_c, j1 = min(j0 + (int64_t)a.vb_c, a.n);
+      const int64_t i = f.a, J = f.b, j0 = J * G.vb_c, j1 = min(j0 + G.vb_c, G.n);
       if (f.nonfin > 0) {
         int c = 0;
         long long pos = LLONG_MAX;
         for (int64_t j = j0 + lane; j < j1; j += 32)
-          if (!isfinite(ld<TC>(a.C, i * a.ldc + j))) { ++c; pos = min(pos, (long long)j); }
+          if (!isfinite(A.ldc(p, i, j))) { ++c; pos = min(pos, (long long)j); }
         c = warp_isum(c);
         pos = warp_min(pos);
         if (c == 1) { row = i; col = pos; kind = ABFT_KIND_NONFINITE_CORRECTED; }
       } else {
-        const int64_t t = ratio_position(f.re, f.rw, a.ec, j1 - j0);
+        const int64_t t = ratio_position(f.re, f.rw, G.ec, j1 - j0);
         if (t >= 0) { row = i; col = j0 + t; kind = ABFT_KIND_CORRECTED; }
       }
     }
     if (lane == 0 && kind != 0) {
       const int slot = atomicAdd(&s_nc, 1);
       if (slot < kCapCands) {
-        a.cand[slot] = CandEntry{(int32_t)row, (int32_t)col, kind, colside ? 0 : 1, f.re, f.rw};
-        keys[slot] = ((uint64_t)row << 32) | ((uint64_t)col << 1) | (colside ? 0u : 1u);
+        CandEntry ce{(int32_t)row, (int32_t)col, kind, colside ? 0 : 1, f.re, f.rw};
+        ce.prob = p;
+        cand[slot] = ce;
+        keys[slot] = A.key(p, row, col, colside ? 0 : 1);
         sidx[slot] = slot;
       }
     }
   }
   __syncthreads();
   const int nc = min(s_nc, kCapCands);
-  if (tid == 0 && s_nc > kCapCands) a.cnt[kCntOverflow] = 1;
-  if (tid == 0) a.cnt[kCntCands] = s_nc;
+  if (tid == 0 && s_nc > kCapCands) cnt[kCntOverflow] = 1;
+  if (tid == 0) cnt[kCntCands] = s_nc;
 
   // 2. bitonic sort of (key, index), padded to a power of two
   int P2 = 1;
@@ -365,9 +429,9 @@ __global__ void __launch_bounds__(kLocThreads, 1) k_locate_correct(const CheckAr
   for (int t = tid; t < nc; t += kLocThreads) {
     const bool dup = t > 0 && (keys[t] >> 1) == (keys[t - 1] >> 1);
     how[t] = dup ? -2 : 0;
-    int kd = a.cand[sidx[t]].kind;
+    int kd = cand[sidx[t]].kind;
     if (!dup && t + 1 < nc && (keys[t + 1] >> 1) == (keys[t] >> 1) &&
-        a.cand[sidx[t + 1]].kind == ABFT_KIND_NONFINITE_CORRECTED)
+        cand[sidx[t + 1]].kind == ABFT_KIND_NONFINITE_CORRECTED)
       kd = ABFT_KIND_NONFINITE_CORRECTED;
     mkind[t] = kd;
   }
@@ -376,14 +440,17 @@ __global__ void __launch_bounds__(kLocThreads, 1) k_locate_correct(const CheckAr
   // 4. choose the correcting line: one in which the candidate is alone
   for (int t = tid; t < nc; t += kLocThreads) {
     if (how[t] == -2) continue;
-    const int32_t r = key_row(keys[t]), c = key_col(keys[t]);
-    const int64_t I = r / a.vb_r, J = c / a.vb_c;
+    const int p = A.kp(keys[t]);
+    const Geo G = A.geo(p);
+    const int32_t r = A.kr(keys[t]), c = A.kc(keys[t]);
+    const int64_t I = r / G.vb_r, J = c / G.vb_c;
     int ncol = 0, nrow = 0;
     for (int u = 0; u < nc; ++u) {
       if ((keys[u] >> 1) == ((u > 0) ? (keys[u - 1] >> 1) : ~0ull)) continue;  // duplicate
-      const int32_t r2 = key_row(keys[u]), c2 = key_col(keys[u]);
-      if (c2 == c && r2 / a.vb_r == I) ++ncol;
-      if (r2 == r && c2 / a.vb_c == J) ++nrow;
+      if (A.kp(keys[u]) != p) continue;
+      const int32_t r2 = A.kr(keys[u]), c2 = A.kc(keys[u]);
+      if (c2 == c && r2 / G.vb_r == I) ++ncol;
+      if (r2 == r && c2 / G.vb_c == J) ++nrow;
     }
     how[t] = ncol == 1 ? 0 : (nrow == 1 ? 1 : -1);
   }
@@ -392,49 +459,50 @@ __global__ void __launch_bounds__(kLocThreads, 1) k_locate_correct(const CheckAr
   // 5. flagged lines holding no candidate are uncorrectable
   for (int L = tid; L < ncl + nrl; L += kLocThreads) {
     const bool colside = L < ncl;
-    const FlagEntry f = colside ? a.colf[L] : a.rowf[L - ncl];
+    const FlagEntry f = colside ? colf[L] : rowf[L - ncl];
+    const int p = f.pad;
+    const Geo G = A.geo(p);
     bool has = false;
     for (int u = 0; u < nc && !has; ++u) {
-      if (how[u] == -2) continue;
-      const int32_t r2 = key_row(keys[u]), c2 = key_col(keys[u]);
-      has = colside ? (c2 == f.b && r2 / a.vb_r == f.a) : (r2 == f.a && c2 / a.vb_c == f.b);
+      if (how[u] == -2 || A.kp(keys[u]) != p) continue;
+      const int32_t r2 = A.kr(keys[u]), c2 = A.kc(keys[u]);
+      has = colside ? (c2 == f.b && r2 / G.vb_r == f.a) : (r2 == f.a && c2 / G.vb_c == f.b);
     }
     if (!has) {
-      if (colside) push_report(a, -1, f.b, ABFT_KIND_UNCORRECTABLE, 0, 0.0, f.re, f.rw);
-      else push_report(a, f.a, -1, ABFT_KIND_UNCORRECTABLE, 1, 0.0, f.re, f.rw);
+      if (colside) push_report(report, cnt, p, -1, f.b, ABFT_KIND_UNCORRECTABLE, 0, 0.0, f.re, f.rw);
+      else push_report(report, cnt, p, f.a, -1, ABFT_KIND_UNCORRECTABLE, 1, 0.0, f.re, f.rw);
     }
   }
 
   // 6. corrections by recomputation in binary64
   for (int t = warp; t < nc; t += nwarps) {
     if (how[t] == -2) continue;
-    const CandEntry ce = a.cand[sidx[t]];
-    const int64_t r = key_row(keys[t]), c = key_col(keys[t]);
+    const CandEntry ce = cand[sidx[t]];
+    const int p = A.kp(keys[t]);
+    const Geo G = A.geo(p);
+    const int64_t r = A.kr(keys[t]), c = A.kc(keys[t]);
     if (how[t] == -1) {
-      if (lane == 0) push_report(a, (int32_t)r, (int32_t)c, ABFT_KIND_UNCORRECTABLE, ce.side, 0.0,
-                                 ce.re, ce.rw);
+      if (lane == 0)
+        push_report(report, cnt, p, (int32_t)r, (int32_t)c, ABFT_KIND_UNCORRECTABLE, ce.side, 0.0,
+                    ce.re, ce.rw);
       continue;
     }
     double s = 0.0, expect;
     if (how[t] == 0) {
-      const int64_t I = r / a.vb_r, i0 = I * a.vb_r, i1 = min(i0 + (int64_t)a.vb_r, a.m);
+      const int64_t I = r / G.vb_r, i0 = I * G.vb_r, i1 = min(i0 + G.vb_r, G.m);
       for (int64_t i = i0 + lane; i < i1; i += 32)
-        if (i != r) s += ld<TC>(a.C, i * a.ldc + c);
-      expect = a.E[(2 * I) * a.n + c];
+        if (i != r) s += A.ldc(p, i, c);
+      expect = A.expect_col(p, I, c);
     } else {
-      const int64_t J = c / a.vb_c, j0 = J * a.vb_c, j1 = min(j0 + (int64_t)a.vb_c, a.n);
+      const int64_t J = c / G.vb_c, j0 = J * G.vb_c, j1 = min(j0 + G.vb_c, G.n);
       for (int64_t j = j0 + lane; j < j1; j += 32)
-        if (j != c) s += ld<TC>(a.C, r * a.ldc + j);
-      expect = a.F[r * a.Cc + 2 * J];
+        if (j != c) s += A.ldc(p, r, j);
+      expect = A.expect_row(p, r, J);
     }
     s = warp_sum(s);
     if (lane == 0) {
-      TC* Cp = static_cast<TC*>(const_cast<void*>(a.C));
-      const TC old = Cp[r * a.ldc + c];
-      const TC v = (TC)(expect - s);
-      Cp[r * a.ldc + c] = v;
-      push_report(a, (int32_t)r, (int32_t)c, mkind[t], ce.side, (double)old - (double)v, ce.re,
-                  ce.rw);
+      const double delta = A.stc(p, r, c, expect - s);
+      push_report(report, cnt, p, (int32_t)r, (int32_t)c, mkind[t], ce.side, delta, ce.re, ce.rw);
     }
   }
   __syncthreads();
@@ -442,26 +510,176 @@ __global__ void __launch_bounds__(kLocThreads, 1) k_locate_correct(const CheckAr
   // 7. re-check both lines of every corrected element (each line once)
   for (int t = warp; t < nc; t += nwarps) {
     if (how[t] < 0) continue;
-    const int32_t r = key_row(keys[t]), c = key_col(keys[t]);
-    const int64_t I = r / a.vb_r, J = c / a.vb_c;
+    const int p = A.kp(keys[t]);
+    const Geo G = A.geo(p);
+    const int32_t r = A.kr(keys[t]), c = A.kc(keys[t]);
+    const int64_t I = r / G.vb_r, J = c / G.vb_c;
     bool dup_c = false, dup_r = false;
     for (int u = 0; u < t; ++u) {
-      if (how[u] < 0) continue;
-      const int32_t r2 = key_row(keys[u]), c2 = key_col(keys[u]);
-      if (c2 == c && r2 / a.vb_r == I) dup_c = true;
-      if (r2 == r && c2 / a.vb_c == J) dup_r = true;
+      if (how[u] < 0 || A.kp(keys[u]) != p) continue;
+      const int32_t r2 = A.kr(keys[u]), c2 = A.kc(keys[u]);
+      if (c2 == c && r2 / G.vb_r == I) dup_c = true;
+      if (r2 == r && c2 / G.vb_c == J) dup_r = true;
     }
-    double re, rw, te, tw;
-    if (!dup_c && lane == 0) {
-      col_line<TC>(a, I, c, re, rw, te, tw);
-      if (is_flagged(re, rw, te, tw)) push_report(a, -1, c, ABFT_KIND_UNCORRECTABLE, 0, 0.0, re, rw);
-    }
-    if (!dup_r) {
-      row_line_warp<TC>(a, r, J, re, rw, te, tw);
-      if (lane == 0 && is_flagged(re, rw, te, tw))
-        push_report(a, r, -1, ABFT_KIND_UNCORRECTABLE, 1, 0.0, re, rw);
-    }
+    double re, rw;
+    if (!dup_c && lane == 0 && A.recheck_col(p, I, c, re, rw))
+      push_report(report, cnt, p, -1, c, ABFT_KIND_UNCORRECTABLE, 0, 0.0, re, rw);
+    if (!dup_r && A.recheck_row(p, r, J, re, rw))
+      push_report(report, cnt, p, r, -1, ABFT_KIND_UNCORRECTABLE, 1, 0.0, re, rw);
   }
+}
+
+template <typename TC>
+__global__ void __launch_bounds__(kLocThreads, 1) k_locate_correct(const CheckArgs a) {
+  const SinglePol<TC> A{a};
+  locate_body(A, a.cnt, a.colf, a.rowf, a.cand, a.report);
+}
+
+// ---------------- grouped verify (fused observed sums, many problems)
+
+__device__ __forceinline__ void grp_col_taus(const GProb& P, double s, int64_t I, int64_t j,
+                                             double& te, double& tw) {
+  const double nb = P.nBcol[j];
+  te = s * nb * (P.f1c * P.nAblk[4 * I + 0] + P.f2 * P.nAblk[4 * I + 2]);
+  tw = s * nb * (P.f1c * P.nAblk[4 * I + 1] + P.f2 * P.nAblk[4 * I + 3]);
+}
+__device__ __forceinline__ void grp_row_taus(const GProb& P, double s, int64_t i, int64_t J,
+                                             double& te, double& tw) {
+  const double na = P.nArow[i];
+  te = s * na * (P.f1r * P.nBblk[4 * J + 0] + P.f2 * P.nBblk[4 * J + 2]);
+  tw = s * na * (P.f1r * P.nBblk[4 * J + 1] + P.f2 * P.nBblk[4 * J + 3]);
+}
+// Expected sums: the products of the hi and lo checksum pieces, added in binary64.
+__device__ __forceinline__ double grp_expect_col(const GProb& P, int64_t I, int64_t j, int w) {
+  return (double)P.E16[(4 * I + 2 * w) * P.n + j] + (double)P.E16[(4 * I + 2 * w + 1) * P.n + j];
+}
+__device__ __forceinline__ double grp_expect_row(const GProb& P, int64_t i, int64_t J, int w) {
+  return (double)P.F16[i * P.C16 + 4 * J + 2 * w] + (double)P.F16[i * P.C16 + 4 * J + 2 * w + 1];
+}
+
+struct GroupPol {
+  const GProb* probs;
+  double s;
+  __device__ __forceinline__ Geo geo(int p) const {
+    return Geo{probs[p].m, probs[p].n, kGrpVbR, kGrpVbC, kGrpEr, kGrpEc};
+  }
+  __device__ __forceinline__ double ldc(int p, int64_t i, int64_t j) const {
+    return (double)probs[p].C[i * probs[p].ldc + j];
+  }
+  __device__ __forceinline__ double stc(int p, int64_t i, int64_t j, double v) const {
+    float* c = probs[p].C + i * probs[p].ldc + j;
+    const float old = *c, nv = (float)v;
+    *c = nv;
+    return (double)old - (double)nv;
+  }
+  __device__ __forceinline__ double expect_col(int p, int64_t I, int64_t j) const {
+    return grp_expect_col(probs[p], I, j, 0);
+  }
+  __device__ __forceinline__ double expect_row(int p, int64_t i, int64_t J) const {
+    return grp_expect_row(probs[p], i, J, 0);
+  }
+  // Column line re-read from C (binary32 sums, as the product's epilogue).
+  __device__ __forceinline__ bool recheck_col(int p, int64_t I, int64_t j, double& re,
+                                              double& rw) const {
+    const GProb& P = probs[p];
+    const int64_t i0 = I * kGrpVbR, i1 = min(i0 + (int64_t)kGrpVbR, P.m);
+    const float sc = scalbnf(1.0f, -kGrpEr);
+    float se = 0.f, sw = 0.f;
+    for (int64_t i = i0; i < i1; ++i) {
+      const float x = P.C[i * P.ldc + j];
+      se += x;
+      sw = fmaf((float)(i - i0 + 1) * sc, x, sw);
+    }
+    re = (double)se - grp_expect_col(P, I, j, 0);
+    rw = (double)sw - grp_expect_col(P, I, j, 1);
+    double te, tw;
+    grp_col_taus(P, s, I, j, te, tw);
+    return is_flagged(re, rw, te, tw);
+  }
+  // Warp-wide; the result is valid in lane 0.
+  __device__ __forceinline__ bool recheck_row(int p, int64_t i, int64_t J, double& re,
+                                              double& rw) const {
+    const GProb& P = probs[p];
+    const int lane = threadIdx.x & 31;
+    const int64_t j0 = J * kGrpVbC, j1 = min(j0 + (int64_t)kGrpVbC, P.n);
+    const float sc = scalbnf(1.0f, -kGrpEc);
+    float se = 0.f, sw = 0.f;
+    for (int64_t j = j0 + lane; j < j1; j += 32) {
+      const float x = P.C[i * P.ldc + j];
+      se += x;
+      sw = fmaf((float)(j - j0 + 1) * sc, x, sw);
+    }
+    se = warp_sum_t<float>(se);
+    sw = warp_sum_t<float>(sw);
+    re = (double)se - grp_expect_row(P, i, J, 0);
+    rw = (double)sw - grp_expect_row(P, i, J, 1);
+    double te, tw;
+    grp_row_taus(P, s, i, J, te, tw);
+    return lane == 0 && is_flagged(re, rw, te, tw);
+  }
+  // problem (23 bits) | row (20) | column (20) | side
+  __device__ __forceinline__ uint64_t key(int p, int64_t r, int64_t c, int side) const {
+    return ((uint64_t)p << 41) | ((uint64_t)r << 21) | ((uint64_t)c << 1) | (uint64_t)side;
+  }
+  __device__ __forceinline__ int kp(uint64_t k) const { return (int)(k >> 41); }
+  __device__ __forceinline__ int32_t kr(uint64_t k) const { return (int32_t)((k >> 21) & 0xFFFFFu); }
+  __device__ __forceinline__ int32_t kc(uint64_t k) const { return (int32_t)((k >> 1) & 0xFFFFFu); }
+};
+
+// Column lines (problem, verify block I, column j) from the observed column
+// sums of the product's epilogue (verify block = tile row).  CTA = 256
+// columns of one verify block.
+__global__ void __launch_bounds__(kThreads) k_grp_col(const GProb* __restrict__ probs,
+                                                      const int64_t* __restrict__ off, int count,
+                                                      double s, int32_t* cnt, FlagEntry* colf) {
+  const int p = find_prob(off, count, blockIdx.x);
+  const GProb& P = probs[p];
+  const int64_t u = blockIdx.x - off[p], ncx = cdiv(P.n, kThreads);
+  const int64_t I = u / ncx, j = (u % ncx) * kThreads + threadIdx.x;
+  if (j >= P.n) return;
+  const double se = (double)P.obs_col[(I * 2 + 0) * P.n + j];
+  const double sw = (double)P.obs_col[(I * 2 + 1) * P.n + j];
+  const int nf = (isfinite(se) && isfinite(sw)) ? 0 : 1;
+  const double re = se - grp_expect_col(P, I, j, 0), rw = sw - grp_expect_col(P, I, j, 1);
+  double te, tw;
+  grp_col_taus(P, s, I, j, te, tw);
+  if (nf == 0 && !is_flagged(re, rw, te, tw)) return;
+  const int slot = atomicAdd(&cnt[kCntColFlags], 1);
+  if (slot < kCapFlags) colf[slot] = FlagEntry{(int32_t)I, (int32_t)j, nf, p, re, rw};
+}
+
+// Row lines (problem, row i, verify block J) from the observed row sums over
+// column groups.  One thread per line.
+__global__ void __launch_bounds__(kThreads) k_grp_row(const GProb* __restrict__ probs,
+                                                      const int64_t* __restrict__ off, int count,
+                                                      double s, int32_t* cnt, FlagEntry* rowf) {
+  const int p = find_prob(off, count, blockIdx.x);
+  const GProb& P = probs[p];
+  const int64_t t = (blockIdx.x - off[p]) * kThreads + threadIdx.x;
+  const int64_t i = t / P.nvc, J = t % P.nvc;
+  if (i >= P.m) return;
+  const int64_t j0 = J * kGrpVbC, j1 = min(j0 + (int64_t)kGrpVbC, P.n);
+  double se = 0.0, sw = 0.0;
+  for (int64_t gr = j0 / P.g; gr < min(cdiv(j1, P.g), P.ngrp); ++gr) {
+    se += (double)P.obs_row[(i * P.ngrp + gr) * 2 + 0];
+    sw += (double)P.obs_row[(i * P.ngrp + gr) * 2 + 1];
+  }
+  const int nf = (isfinite(se) && isfinite(sw)) ? 0 : 1;
+  const double re = se - grp_expect_row(P, i, J, 0), rw = sw - grp_expect_row(P, i, J, 1);
+  double te, tw;
+  grp_row_taus(P, s, i, J, te, tw);
+  if (nf == 0 && !is_flagged(re, rw, te, tw)) return;
+  const int slot = atomicAdd(&cnt[kCntRowFlags], 1);
+  if (slot < kCapFlags) rowf[slot] = FlagEntry{(int32_t)i, (int32_t)J, nf, p, re, rw};
+}
+
+__global__ void __launch_bounds__(kLocThreads, 1) k_grp_locate(const GProb* probs, double s,
+                                                               int32_t* cnt, const FlagEntry* colf,
+                                                               const FlagEntry* rowf,
+                                                               CandEntry* cand,
+                                                               abft_fault* report) {
+  const GroupPol A{probs, s};
+  locate_body(A, cnt, colf, rowf, cand, report);
 }
 
 // C[bi*bs + t][j] = S[t][j] - sum_{I != bi} C[I*bs + t][j], binary64.
@@ -586,9 +804,8 @@ __global__ void k_set_inject(int32_t* hdr, const InjList L) {
 }
 }  // namespace
 
-cudaError_t launch_set_inject(const Plan& P, void* ws, const int64_t* rows, const int64_t* cols,
-                              const int32_t* bits, int count, cudaStream_t st) {
-  int32_t* hdr = reinterpret_cast<int32_t*>(static_cast<char*>(ws) + P.L.inject);
+cudaError_t launch_set_inject_raw(int32_t* hdr, const InjectEntry* entries, int count,
+                                  cudaStream_t st) {
   int t0 = 0;
   do {
     InjList L{};
@@ -596,13 +813,21 @@ cudaError_t launch_set_inject(const Plan& P, void* ws, const int64_t* rows, cons
     L.first = t0;
     L.total = count;
     L.last = t0 + L.n >= count;
-    for (int t = 0; t < L.n; ++t)
-      L.e[t] = InjectEntry{(int32_t)rows[t0 + t], (int32_t)cols[t0 + t], bits[t0 + t], 0};
+    for (int t = 0; t < L.n; ++t) L.e[t] = entries[t0 + t];
     k_set_inject<<<1, 64, 0, st>>>(hdr, L);
     count_launches(1);
     t0 += L.n;
   } while (t0 < count);
   return cudaGetLastError();
+}
+
+cudaError_t launch_set_inject(const Plan& P, void* ws, const int64_t* rows, const int64_t* cols,
+                              const int32_t* bits, int count, cudaStream_t st) {
+  int32_t* hdr = reinterpret_cast<int32_t*>(static_cast<char*>(ws) + P.L.inject);
+  InjectEntry e[kMaxInject];
+  for (int t = 0; t < count && t < kMaxInject; ++t)
+    e[t] = InjectEntry{(int32_t)rows[t], (int32_t)cols[t], bits[t], 0};
+  return launch_set_inject_raw(hdr, e, count, st);
 }
 
 cudaError_t launch_recover(const Plan& P, void* C, void* ws, int bi, int bj, cudaStream_t st) {
@@ -634,6 +859,20 @@ cudaError_t launch_erase(const Plan& P, void* C, int bi, int bj, cudaStream_t st
     k_erase<float><<<grid, kThreads, 0, st>>>(static_cast<float*>(C), P.d.ldc, (int64_t)bi * P.bs,
                                               (int64_t)bj * P.bc, P.bs, P.bc);
   count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_verify(const GroupDev& G, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(G.cnt, 0, sizeof(int32_t) * kNumCounters, st);
+  if (e != cudaSuccess || G.count == 0) return e;
+  if (G.nctas[kGkColCheck] > 0)
+    k_grp_col<<<(unsigned)G.nctas[kGkColCheck], kThreads, 0, st>>>(
+        G.probs, G.off[kGkColCheck], G.count, G.s, G.cnt, G.colf);
+  if (G.nctas[kGkRowCheck] > 0)
+    k_grp_row<<<(unsigned)G.nctas[kGkRowCheck], kThreads, 0, st>>>(
+        G.probs, G.off[kGkRowCheck], G.count, G.s, G.cnt, G.rowf);
+  k_grp_locate<<<1, kLocThreads, 0, st>>>(G.probs, G.s, G.cnt, G.colf, G.rowf, G.cand, G.report);
+  count_launches(3);
   return cudaGetLastError();
 }
 

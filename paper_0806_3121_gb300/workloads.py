@@ -55,6 +55,28 @@ WORKLOADS = {w.name: w for w in (F64_512, F64_11264_GRID22, F64_4096_GRID8, BF16
                                  BF16_8192, BF16X3_16384, BF16X3_8192)}
 
 
+@dataclass(frozen=True)
+class GroupWorkload:
+    """Many independent bf16 problems: m, n, k uniform over multiples of `step` in
+    [lo, hi]; one accumulator bit flip in a `fault_frac` share of the instances."""
+    name: str
+    count: int
+    lo: int = 64
+    hi: int = 2048
+    step: int = 64
+    fault_frac: float = 0.01
+    note: str = ""
+
+
+BF16_GROUPED_4096 = GroupWorkload(
+    "bf16_grouped_4096", 4096,
+    note="4096 independent BF16 GEMMs, m, n, k uniform over multiples of 64 in [64, 2048], "
+         "N(0,1) rounded to BF16, FP32 accumulate; one fp32 accumulator flip in 1% (41) of the "
+         "instances at seeded positions")
+BF16_GROUPED_512 = GroupWorkload("bf16_grouped_512", 512, note="the same recipe, 512 problems")
+GROUP_WORKLOADS = {w.name: w for w in (BF16_GROUPED_4096, BF16_GROUPED_512)}
+
+
 def rng(seed: int, stream: int = 0) -> np.random.Generator:
     """Independent PCG64 stream per (seed, stream)."""
     return np.random.Generator(np.random.PCG64([int(seed), int(stream)]))
@@ -136,3 +158,26 @@ def flip_f32(C: np.ndarray, flips) -> np.ndarray:
     for i, j, b in flips:
         u[i, j] ^= np.uint32(1) << np.uint32(b)
     return C
+
+
+def group_shapes(seed: int, w: GroupWorkload):
+    """(m, n, k) of every problem of a grouped workload."""
+    g = rng(seed, 20)
+    v = w.step * g.integers(w.lo // w.step, w.hi // w.step + 1, size=(w.count, 3))
+    return [tuple(int(x) for x in row) for row in v]
+
+
+def group_operand_bits(seed: int, p: int, which: int, rows: int, cols: int, ld: int = 0):
+    """bf16 bit patterns (rows x ld, zero padding past cols) of iid N(0,1) values for
+    operand `which` (0 = A, 1 = B) of problem p (stream 100000 + 2p + which)."""
+    ld = ld or (cols + 7) // 8 * 8
+    x = rng(seed, 100000 + 2 * p + which).standard_normal(size=(rows, cols), dtype=np.float32)
+    out = np.zeros((rows, ld), np.uint16)
+    out[:, :cols] = bf16_bits(x)
+    return out
+
+
+def faulty_instances(seed: int, count: int, frac: float):
+    """Sorted indices of the instances that receive a flip (sampled without replacement)."""
+    nf = max(1, int(round(frac * count)))
+    return sorted(int(i) for i in rng(seed, 21).choice(count, size=nf, replace=False))

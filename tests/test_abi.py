@@ -39,7 +39,10 @@ def test_version(lib):
 
 def test_struct_sizes_match_header(lib):
     assert ct.sizeof(abft.Desc) == 6 * 8 + 6 * 4 + 8
-    assert ct.sizeof(abft.Fault) == 4 * 4 + 3 * 8
+    assert ct.sizeof(abft.Fault) == 4 * 4 + 3 * 8 + 2 * 4
+    assert ct.sizeof(abft.Problem) == 6 * 8 + 3 * 8
+    assert ct.sizeof(abft.GroupTuning) == 2 * 4
+    assert ct.sizeof(abft.GroupLayout) == 10 * 8 + 6 * 8
 
 
 def test_workspace_layout_shapes(lib):
@@ -111,3 +114,61 @@ def test_empty_problem_is_a_no_op(lib):
     assert abft.abft_workspace_bytes(d) > 0
     # nothing to do: returns OK without touching the (NULL) pointers or the GPU
     assert lib.abft_gemm(ct.byref(d), None, None, None, None, ct.c_void_p(1), ct.c_void_p(1), None) == 0
+
+
+def _fake_problem(m, n, k, **kw):
+    # device pointers are only stored by abft_group_create (never dereferenced on the host)
+    q = dict(m=m, n=n, k=k, lda=(k + 7) // 8 * 8, ldb=(n + 7) // 8 * 8, ldc=n,
+             A=1 << 20, B=2 << 20, C=3 << 20)
+    q.update(kw)
+    return q
+
+
+def test_group_layout_host_only(lib):
+    """abft_group_create validates and lays out the workspace on the host only."""
+    shapes = [(64, 64, 64), (1, 1, 1), (300, 700, 129), (2048, 2048, 2048)]
+    g = abft.abft_group_create([_fake_problem(*s) for s in shapes], "bf16")
+    try:
+        total = abft.abft_group_workspace_bytes(g)
+        prev_end = 0
+        for p, (m, n, k) in enumerate(shapes):
+            L = abft.abft_group_problem_layout(g, p)
+            nvr, nvc = -(-m // 128), -(-n // 256)
+            assert (L.nvr, L.nvc, L.R16, L.C16) == (nvr, nvc, 4 * nvr, 4 * nvc)
+            assert L.acs_ld % 8 == 0 and L.acs_ld >= k and L.bcs_ld % 8 == 0
+            offs = [L.acs, L.bcs, L.E16, L.F16, L.obs_col, L.obs_row, L.nArow, L.nAblk, L.nBcol,
+                    L.nBblk]
+            assert all(o % 256 == 0 for o in offs) and offs == sorted(offs) and offs[0] >= prev_end
+            assert L.bcs >= L.acs + L.R16 * L.acs_ld * 2
+            assert L.F16 >= L.E16 + L.R16 * n * 4
+            prev_end = L.nBblk + 4 * nvc * 8
+            assert prev_end <= total
+        assert abft.abft_group_get_tuning(g) == dict(boxes_per_tile=4, order=1)
+        with pytest.raises(abft.AbftError):
+            abft.abft_group_problem_layout(g, len(shapes))
+        # calls that need a bound workspace refuse before touching the GPU
+        with pytest.raises(abft.AbftError) as e:
+            abft.abft_group_encode(g, stream=0)
+        assert e.value.status == abft.ERR_INVALID and "bind" in str(e.value)
+    finally:
+        abft.abft_group_destroy(g)
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(m=0), "sizes"), (dict(k=(1 << 24) + 1), "sizes"), (dict(lda=60), "lda"),
+    (dict(ldb=12), "multiples of 8"), (dict(ldc=10), "ldc"), (dict(A=0), "NULL"),
+    (dict(B=(2 << 20) + 8), "aligned"),
+])
+def test_group_invalid_problems(lib, kw, msg):
+    with pytest.raises(abft.AbftError) as e:
+        q = _fake_problem(64, 64, 64)
+        q.update(kw)
+        abft.abft_group_create([_fake_problem(64, 64, 64), q])
+    assert e.value.status == abft.ERR_INVALID and msg in str(e.value)
+    assert "problem 1" in str(e.value)
+
+
+def test_group_other_dtypes_unsupported(lib):
+    with pytest.raises(abft.AbftError) as e:
+        abft.abft_group_create([_fake_problem(64, 64, 64)], "f64")
+    assert e.value.status == abft.ERR_UNSUPPORTED

@@ -162,6 +162,32 @@ def oracle_pipeline(A, B, w, blocks: int, seed: int):
     return 2.0 * ms * ns * w.k, dt, ms
 
 
+def oracle_group_pipeline(w, seed: int, budget_flops: float = 6e10):
+    """The CPU oracle's whole path on the leading problems of a grouped workload (in the
+    workload's order, until `budget_flops` useful FLOPs): encode, product, one graded
+    flip in each problem the workload marks faulty, verify / correct.  Returns (useful
+    flops, seconds, problems)."""
+    import oracle
+    shapes = wl.group_shapes(seed, w)
+    faulty = set(wl.faulty_instances(seed, w.count, w.fault_frac))
+    ops, flops = [], 0.0
+    for p, (m, n, k) in enumerate(shapes):
+        if flops >= budget_flops:
+            break
+        a = oracle.bf16_to_f64(wl.group_operand_bits(seed, p, 0, m, k)[:, :k])
+        b = oracle.bf16_to_f64(wl.group_operand_bits(seed, p, 1, k, n)[:, :n])
+        ops.append((p, a, b))
+        flops += 2.0 * m * n * k
+    t0 = time.perf_counter()
+    for p, a, b in ops:
+        enc = oracle.Encoded(a, b, 128, 256, dtype="bf16")
+        C = oracle.gemm(a, b)
+        if p in faulty:
+            C[0, 0] = C[0, 0] * 2.0 ** 64
+        enc.verify_correct(C)
+    return flops, time.perf_counter() - t0, len(ops)
+
+
 def cpu_baseline(A, B, w, blocks, seed):
     flops, dt, ms = oracle_pipeline(A, B, w, blocks, seed)
     what = "erased block + 3 flips" if w.p else "3 flips"
@@ -173,9 +199,33 @@ def cpu_baseline(A, B, w, blocks, seed):
 
 
 # --------------------------------------------------------------------------- reference arm
+def run_reference_grouped(args, w):
+    for _ in range(args.warmup):
+        oracle_group_pipeline(w, args.seed)
+    tot_f, tot_t, npr = 0.0, 0.0, 0
+    for _ in range(args.steps):
+        f, t, npr = oracle_group_pipeline(w, args.seed)
+        tot_f += f
+        tot_t += t
+    v = tot_f / tot_t / 1e12
+    sample = (f"oracle encode+gemm+verify/correct of the first {npr} of the {w.count} problems "
+              f"of {w.name} per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic", "config": {"workload": w.name, "problems": w.count, "sample": npr},
+        "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    if args.workload in wl.GROUP_WORKLOADS:
+        return run_reference_grouped(args, wl.GROUP_WORKLOADS[args.workload])
     w = wl.WORKLOADS[args.workload]
     if w.dtype == "f64":
         A, B = wl.operands(w, args.seed)
@@ -417,6 +467,139 @@ def run_workload(w, args, dev, rank, world, secondary=False):
     return out
 
 
+def run_grouped(w, args, dev, rank, world, secondary=False):
+    """The grouped workload: `w.count` independent bf16 problems in one persistent product
+    launch; a step is the captured graph (ABFT product of every problem with one armed
+    accumulator flip in each faulty instance, fused verify, locate / correct) plus the
+    report read.  Returns the JSON dict."""
+    import torch
+    from paper_0806_3121_gb300 import abft
+
+    seed = args.seed + rank
+    shapes = wl.group_shapes(seed, w)
+    g = torch.Generator(device=dev).manual_seed(seed)
+    As, Bs, Cs, probs = [], [], [], []
+    for (m, n, k) in shapes:
+        As.append(torch.randn(m, k, generator=g, device=dev).to(torch.bfloat16))
+        Bs.append(torch.randn(k, n, generator=g, device=dev).to(torch.bfloat16))
+        Cs.append(torch.empty((m, n), dtype=torch.float32, device=dev))
+        probs.append(dict(m=m, n=n, k=k, A=As[-1], B=Bs[-1], C=Cs[-1]))
+    stream = torch.cuda.Stream(device=dev)
+    grp = abft.abft_group_create(probs, "bf16")
+    ws = torch.zeros(abft.abft_group_workspace_bytes(grp), dtype=torch.uint8, device=dev)
+    abft.abft_group_bind(grp, ws, stream=stream)
+    tuning, tune_ms = abft.abft_group_autotune(grp, reps=3, stream=stream)
+    abft.abft_group_encode(grp, stream=stream)
+    abft.abft_group_gemm(grp, True, stream=stream)
+    torch.cuda.synchronize()
+    faulty = wl.faulty_instances(seed, w.count, w.fault_frac)
+    gr = wl.rng(seed, 22)
+    flips = []
+    for p in faulty:
+        m, n, _ = shapes[p]
+        i, j = int(gr.integers(0, m)), int(gr.integers(0, n))
+        # a graded flip by construction: an exponent bit that moves the value by >= 2^64
+        flips.append((p, i, j, 29 if abs(Cs[p][i, j].item()) >= 2.0 else 30))
+    abft.abft_group_set_epilogue_faults(grp, flips, stream=stream)
+    abft.abft_group_capture(grp, True, stream=stream)
+
+    def step():
+        abft.abft_group_launch(grp, stream=stream)
+        return abft.abft_group_report(grp, max_reports=4 * len(flips) + 16, stream=stream)
+
+    for _ in range(args.warmup):
+        st, rep, nrep = step()
+    assert st == abft.OK, st
+    assert sorted((e["problem"], e["row"], e["col"]) for e in rep) == \
+        sorted((p, i, j) for p, i, j, _ in flips), rep
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    launches0 = abft.abft_kernel_launches()
+    with ClockSampler(dev.index) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            step()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = abft.abft_kernel_launches() - launches0
+    step_ms = t0.elapsed_time(t1) / args.steps
+    clocks = clk.summary()
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    t_plain, t_abft = [], []
+    for _ in range(10):
+        t_plain.append(timed(lambda: abft.abft_group_gemm(grp, False, stream=stream), 1))
+        t_abft.append(timed(lambda: abft.abft_group_gemm(grp, True, stream=stream), 1))
+    plain_ms, abft_ms = statistics.median(t_plain), statistics.median(t_abft)
+    verify_ms = timed(lambda: abft.abft_group_verify_enqueue(grp, stream=stream), 5)
+    encode_ms = timed(lambda: abft.abft_group_encode(grp, stream=stream), 3)
+    abft.abft_group_set_epilogue_faults(grp, [], stream=stream)
+
+    useful = sum(2.0 * m * n * k for m, n, k in shapes)
+    cs_flops = sum(2.0 * k * (4 * -(-m // 128) * n + m * 4 * -(-n // 256)) for m, n, k in shapes)
+    peak, peak_src = bf16_peak()
+    achieved = (useful + cs_flops) / (abft_ms * 1e-3) / 1e12
+    if world > 1:
+        t = torch.tensor([step_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_ms = t.item()
+    out = {
+        "metric": METRIC, "value": useful * world / (step_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": w.name, "problems": w.count,
+                   "shapes": f"m, n, k uniform over multiples of {w.step} in [{w.lo}, {w.hi}]",
+                   "verify_block": [128, 256], "dist": "N(0,1) rounded to bf16",
+                   "faults_per_step": f"one exponent flip of an accumulator output in each of "
+                                      f"{len(flips)} instances ({w.fault_frac:.0%})",
+                   "tuning": tuning, "step": "CUDA graph: grouped ABFT product + fused "
+                                             "verify + locate/correct, then the report read",
+                   "l2": "operands larger than L2 (129 MB)",
+                   "parallelism": f"{world} independent groups (one per GPU)"},
+        "overhead_pct": {"gemm_only": 100.0 * (abft_ms / plain_ms - 1.0),
+                         "step": 100.0 * (step_ms / plain_ms - 1.0)},
+        "times_ms": {"step": step_ms, "abft_gemm_paired": abft_ms, "plain_gemm_paired": plain_ms,
+                     "verify": verify_ms, "encode": encode_ms,
+                     "autotune_best": tune_ms},
+        "useful_frac_of_peak": (useful / (step_ms * 1e-3) / 1e12) / peak,
+        "plain_useful_tflops": useful / (plain_ms * 1e-3) / 1e12,
+        "roofline": {"kernel": "k_gemm_grouped", "bound": "tensor", "peak_source": peak_src,
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "algorithmic_flops_per_launch": useful + cs_flops},
+        "gpu_launches": launches, "clocks": clocks, "e2e": None,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not secondary:
+        f, dt, npr = oracle_group_pipeline(w, seed)
+        out["cpu_baseline"] = {
+            "value": f / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle encode+gemm+verify/correct of the first {npr} problems of the "
+                      f"recipe (host-drawn operands of the same shapes and distribution); "
+                      f"{dt:.1f} s"}
+    abft.abft_group_destroy(grp)
+    del As, Bs, Cs, ws
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_0806_3121_gb300 import abft, build
@@ -425,16 +608,22 @@ def run_ours(args, rank, world):
     abft.load()
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
+    if args.workload in wl.GROUP_WORKLOADS:
+        out = run_grouped(wl.GROUP_WORKLOADS[args.workload], args, dev, rank, world)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
     w = wl.WORKLOADS[args.workload]
     secondary = {}
+    keys = ("value", "unit", "ms_per_step", "overhead_pct", "times_ms", "useful_frac_of_peak",
+            "roofline", "gpu_launches", "clocks", "config")
     if w.name == "f64_11264_grid22" and not args.no_secondary:
         # the tensor-core workloads first: the FP64 run is a minute of full-power load
         for name in ("bf16_16384", "bf16x3_16384"):
             sec = run_workload(wl.WORKLOADS[name], args, dev, rank, world, secondary=True)
-            secondary[name] = {k: sec[k] for k in ("value", "unit", "ms_per_step",
-                                                   "overhead_pct", "times_ms",
-                                                   "useful_frac_of_peak", "roofline",
-                                                   "gpu_launches", "clocks", "config")}
+            secondary[name] = {k: sec[k] for k in keys}
+        sec = run_grouped(wl.BF16_GROUPED_4096, args, dev, rank, world, secondary=True)
+        secondary[wl.BF16_GROUPED_4096.name] = {k: sec[k] for k in keys + ("plain_useful_tflops",)}
     out = run_workload(w, args, dev, rank, world)
     out.update(secondary)
     if rank == 0:

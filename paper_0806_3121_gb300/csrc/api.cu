@@ -114,7 +114,7 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
   const bool lp0 = d->dtype != ABFT_F64;
   p.fused = lp0 && d->vb_rows % 128 == 0 && d->vb_cols % 32 == 0 &&
             (256 % d->vb_cols == 0 || d->vb_cols % 256 == 0);
-  p.g = d->vb_cols < 256 ? d->vb_cols : 256;
+  p.g = d->vb_cols < 128 ? d->vb_cols : 128;  // row-sum groups never straddle 128 columns
   p.ngrp = d->n > 0 ? cdiv(d->n, p.g) : 0;
   p.ntr_obs = d->m > 0 ? cdiv(d->m, 128) : 0;
 

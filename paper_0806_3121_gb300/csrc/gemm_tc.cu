@@ -2,19 +2,22 @@
 // [A; acs] [B, bcs] with fp32 accumulation in TMEM.
 //
 // Persistent, warp-specialised kernel, one CTA per SM:
-//   warp 0      TMA producer: A tile (128 x 64, K-major) and B tile (64 x 256,
-//               N-major, four 64-column boxes) per stage, 128-byte swizzle,
-//               into a 4-stage shared-memory ring guarded by mbarriers.
-//   warp 1      MMA issuer: one thread issues tcgen05.mma (M=128, N=256,
+//   warp 0      TMA producer: A tile (two 64-row halves x 64, K-major) and B
+//               tile (64 x up to four 64-column boxes, N-major) per stage,
+//               128-byte swizzle, into a 4-stage shared-memory ring guarded by
+//               mbarriers.
+//   warp 1      MMA issuer: one thread issues tcgen05.mma (M=128, N=64 x boxes,
 //               K=16) into one of two TMEM accumulators (2 x 256 columns) and
 //               frees ring stages and accumulators with tcgen05.commit.
-//   warps 2-5   epilogue: tcgen05.ld of the accumulator (each warp its
-//               32-lane quarter), fp32 stores to C or to the checksum
-//               outputs, then release of the accumulator so the next tile's
-//               MMAs overlap this tile's epilogue.
-// Tiles: data tiles (grouped raster for L2 reuse), then checksum-row tiles
+//   warps 2-9   epilogue: tcgen05.ld of the accumulator (a warp reads its
+//               32-lane quarter of TMEM and one 128-column half of the tile),
+//               fp32 stores to C or to the checksum outputs, the fused observed
+//               sums, then release of the accumulator so the next tile's MMAs
+//               overlap this tile's epilogue.
+// Single problem: data tiles (grouped raster for L2 reuse), checksum-row tiles
 // (acs x B -> E16) and checksum-column tiles (A x bcs -> F16); the corner is
-// not computed.  Every barrier wait is bounded; a timeout sets a device flag
+// not computed.  Grouped problems: each problem's checksum halves / boxes
+// follow its data halves / boxes and share the last data tiles.  Every barrier wait is bounded; a timeout sets a device flag
 // the host reports as ABFT_ERR_TIMEOUT, and the kernel still drains its
 // copies and MMAs and frees TMEM before returning.
 #include <cuda.h>
@@ -31,7 +34,12 @@ namespace abft {
 namespace {
 
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
-constexpr int kThreads = 192;
+#ifndef ABFT_EPI_WARPS
+#define ABFT_EPI_WARPS 8
+#endif
+constexpr int kEpiWarps = ABFT_EPI_WARPS;         // 4 or 8 (one or two per TMEM lane quarter)
+constexpr int kEpiCols = BN * 4 / kEpiWarps;       // tile columns per epilogue warp
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t A_BYTES = BM * BK * 2;          // 16 KiB
 constexpr uint32_t B_BOX_BYTES = 64 * BK * 2;      // one 64-column box: 8 KiB
 constexpr uint32_t B_BYTES = BN * BK * 2;          // 32 KiB
@@ -45,8 +53,12 @@ constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + OBS_BYTES + 256;
 // K loop runs over nseg segments of the k dimension; segment s reads A plane
 // (s == 2) and B plane (s == 1), so nseg = 3 accumulates
 // A_hi B_hi + A_hi B_lo + A_lo B_hi (split bf16x3) and nseg = 1 is plain bf16.
+// a / acs: 64-row boxes (one half); a128 / acs128: 128-row boxes (a whole
+// tile's A in one copy); b / bcs: one 64-column box; b4 / bcs4: a 3-D view
+// (64 columns, k rows, column box) that fetches four full 64-column boxes in
+// one copy (only boxes inside the matrix: n / 64 of them).
 struct TcMaps {
-  CUtensorMap a[2], acs[2], b[2], bcs[2];
+  CUtensorMap a[2], acs[2], b[2], bcs[2], a128[2], acs128[2], b4[2], bcs4[2];
 };
 
 struct TcArgs {
@@ -144,6 +156,13 @@ struct TileView {
   const CUtensorMap* mbC1;
   int32_t rowD, rowC, colD, colC;
   int hsplit, hcnt, bsplit, nbox;
+  // one-copy loads: the whole A tile (maW: 128-row box at rowW) and four
+  // full B boxes (mbW: 3-D map at box index colW / 64); nullptr: per half / box
+  const CUtensorMap* maW;
+  const CUtensorMap* maW1;
+  const CUtensorMap* mbW;
+  const CUtensorMap* mbW1;
+  int32_t rowW, colW;
   float* C;                   // data x data, ld ldc, m x n
   int64_t ldc, m, n;
   float* E16;                 // checksum rows x data columns, ld n, R16 rows
@@ -168,6 +187,8 @@ struct SingleSched {
       tc::prefetch_tmap(&M->acs[pl]);
       tc::prefetch_tmap(&M->b[pl]);
       tc::prefetch_tmap(&M->bcs[pl]);
+      tc::prefetch_tmap(&M->a128[pl]);
+      tc::prefetch_tmap(&M->b4[pl]);
     }
   }
   __device__ __forceinline__ TileView view(int64_t t) const {
@@ -193,6 +214,17 @@ struct SingleSched {
     V.hcnt = hrows;
     V.bsplit = T.kind == 2 ? 0 : bcols;
     V.nbox = bcols;
+    V.maW = V.maW1 = V.mbW = V.mbW1 = nullptr;
+    V.rowW = (int32_t)T.row0;
+    V.colW = (int32_t)T.col0;
+    if (hrows == 2) {
+      V.maW = T.kind == 1 ? &M->acs128[0] : &M->a128[0];
+      V.maW1 = T.kind == 1 ? &M->acs128[1] : &M->a128[1];
+    }
+    if (bcols == 4 && T.col0 + 256 <= ((T.kind == 2 ? g.C16 : g.n) / 64) * 64) {
+      V.mbW = T.kind == 2 ? &M->bcs4[0] : &M->b4[0];
+      V.mbW1 = T.kind == 2 ? &M->bcs4[1] : &M->b4[1];
+    }
     V.C = g.C;
     V.ldc = g.ldc;
     V.m = g.m;
@@ -242,7 +274,7 @@ __device__ __forceinline__ void transpose_reduce(float (&v)[32], int lane) {
   }
 }
 
-__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory"); }
 
 // The kernel body, shared by the single-problem and the grouped product.
 template <class Sched>
@@ -272,7 +304,7 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
     }
     for (int a = 0; a < 2; ++a) {
       tc::mbar_init(tfull(a), 1);
-      tc::mbar_init(tempty(a), 4);
+      tc::mbar_init(tempty(a), kEpiWarps);
     }
     tc::mbar_init(drain, 1);
     *abort = 0;
@@ -307,17 +339,27 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
           if (!tc::wait(empty(s), ph ^ 1, abort)) break;
           const uint32_t sa = tc::smem_addr(smem + s * STAGE_BYTES);
           tc::mbar_arrive_expect_tx(full(s), tx);
-          for (int h = 0; h < T.hcnt; ++h) {
-            const bool dat = h < T.hsplit;
-            const CUtensorMap* ma = dat ? (seg == 2 ? T.maD1 : T.maD) : (seg == 2 ? T.maC1 : T.maC);
-            const int32_t y = dat ? T.rowD + 64 * h : T.rowC + 64 * (h - T.hsplit);
-            tc::tma_load_2d(sa + h * (A_BYTES / 2), ma, full(s), kx, y);
+          if (T.maW) {
+            tc::tma_load_2d(sa, seg == 2 ? T.maW1 : T.maW, full(s), kx, T.rowW);
+          } else {
+            for (int h = 0; h < T.hcnt; ++h) {
+              const bool dat = h < T.hsplit;
+              const CUtensorMap* ma =
+                  dat ? (seg == 2 ? T.maD1 : T.maD) : (seg == 2 ? T.maC1 : T.maC);
+              const int32_t y = dat ? T.rowD + 64 * h : T.rowC + 64 * (h - T.hsplit);
+              tc::tma_load_2d(sa + h * (A_BYTES / 2), ma, full(s), kx, y);
+            }
           }
-          for (int b = 0; b < T.nbox; ++b) {
-            const bool dat = b < T.bsplit;
-            const CUtensorMap* mb = dat ? (seg == 1 ? T.mbD1 : T.mbD) : (seg == 1 ? T.mbC1 : T.mbC);
-            const int32_t x = dat ? T.colD + 64 * b : T.colC + 64 * (b - T.bsplit);
-            tc::tma_load_2d(sa + A_BYTES + b * B_BOX_BYTES, mb, full(s), x, kx);
+          if (T.mbW) {
+            tc::tma_load_3d(sa + A_BYTES, seg == 1 ? T.mbW1 : T.mbW, full(s), 0, kx, T.colW / 64);
+          } else {
+            for (int b = 0; b < T.nbox; ++b) {
+              const bool dat = b < T.bsplit;
+              const CUtensorMap* mb =
+                  dat ? (seg == 1 ? T.mbD1 : T.mbD) : (seg == 1 ? T.mbC1 : T.mbC);
+              const int32_t x = dat ? T.colD + 64 * b : T.colC + 64 * (b - T.bsplit);
+              tc::tma_load_2d(sa + A_BYTES + b * B_BOX_BYTES, mb, full(s), x, kx);
+            }
           }
           ++issued;
           if (++s == STAGES) { s = 0; ph ^= 1; }
@@ -375,8 +417,9 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
     }
     __syncwarp();
   } else {
-    // ---------------- epilogue: warps 2..5, TMEM lane quarter = warp % 4
-    const int q = warp & 3, half = q >> 1;
+    // ---------------- epilogue: warps 2..9; TMEM lane quarter q = warp % 4 (a
+    // warp may only read its quarter), column half = (warp - 2) / 4
+    const int q = warp & 3, half = q >> 1, c_lo = kEpiCols * ((warp - 2) >> 2);
     float* obs = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);  // [4][BN][2]
     const int ninj = (inj_hdr && inj_hdr[0] == kInjectMagic)
                          ? max(0, min(inj_hdr[1], kMaxInject)) : 0;
@@ -393,12 +436,24 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
       const bool rvalid = drow ? row < T.m : (crow && row < T.R16);
       const int ndcol = 64 * T.bsplit, ncol = 64 * T.nbox;
       const bool fused = T.obs_col != nullptr && T.hsplit > 0 && T.bsplit > 0;
+      // armed faults inside this warp's part of the tile (one pass over the list)
+      bool inj_hit = false;
+      if (drow && ninj > 0) {
+        const int64_t r0 = T.rowD + 64 * half + 32 * (q & 1), c0 = T.colD + c_lo;
+        for (int f = lane; f < ninj; f += 32) {
+          const InjectEntry ie = inj[f];
+          inj_hit |= ie.pad == T.prob && ie.row >= r0 && ie.row < r0 + 32 && ie.col >= c0 &&
+                     ie.col < c0 + kEpiCols;
+        }
+        inj_hit = __any_sync(0xffffffffu, inj_hit);
+      }
       const float scr = scalbnf(1.0f, -T.er), scc = scalbnf(1.0f, -T.ec);
       const float wrow = (fused && drow) ? (float)((int)(row % T.vb_r) + 1) * scr : 0.f;
       float racc_e = 0.f, racc_w = 0.f;
       const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
+      const int c_hi = min(c_lo + kEpiCols, ncol);
 #pragma unroll 1
-      for (int c = 0; c < ncol; c += 32) {
+      for (int c = c_lo; c < c_hi; c += 32) {
         float v[32];
         tc::tmem_ld32(base + c, v);
         const bool dcol = c < ndcol;
@@ -406,22 +461,24 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
           const int64_t col = T.colD + c;
           if (col >= T.n) continue;
           if (drow) {
-            for (int f = 0; f < ninj; ++f) {
-              const InjectEntry ie = inj[f];
-              if (ie.pad == T.prob && ie.row == row && ie.col >= col && ie.col < col + 32) {
-                const int x = ie.col - (int)col;
+            if (inj_hit)
+              for (int f = 0; f < ninj; ++f) {
+                const InjectEntry ie = inj[f];
+                if (ie.pad == T.prob && ie.row == row && ie.col >= col && ie.col < col + 32) {
+                  const int x = ie.col - (int)col;
 #pragma unroll
-                for (int u = 0; u < 32; ++u)
-                  if (u == x) v[u] = __uint_as_float(__float_as_uint(v[u]) ^ (1u << (ie.bit & 31)));
+                  for (int u = 0; u < 32; ++u)
+                    if (u == x) v[u] = __uint_as_float(__float_as_uint(v[u]) ^ (1u << (ie.bit & 31)));
+                }
               }
-            }
             if (rvalid) store_row32(T.C, T.ldc, row, col, T.n, v);
           } else if (rvalid) {
             store_row32(T.E16, T.n, row, col, T.n, v);
           }
-          if (fused) {
+          if (fused && drow) {
             // row partials over the column group (weights restart per verify
-            // block; a 32-column chunk never straddles one)
+            // block; a 32-column chunk never straddles one, a group never
+            // straddles the two column halves)
             const int cm = (int)(col % T.vb_c) + 1;
 #pragma unroll
             for (int u = 0; u < 32; ++u) {
@@ -429,20 +486,17 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
               racc_w = fmaf((float)(cm + u) * scc, v[u], racc_w);
             }
             if (((col + 32) % T.g) == 0 || c + 32 == ndcol || col + 32 >= T.n) {
-              if (drow && rvalid) {
+              if (rvalid) {
                 float* o = T.obs_row + (row * T.ngrp + (int)(col / T.g)) * 2;
                 o[0] = racc_e;
                 o[1] = racc_w;
               }
               racc_e = racc_w = 0.f;
             }
-            // column partials of this warp's 32 rows (zero for non-data rows)
+            // column partials of this warp's 32 rows
             float vw[32];
 #pragma unroll
-            for (int u = 0; u < 32; ++u) {
-              if (!drow) v[u] = 0.f;
-              vw[u] = wrow * v[u];
-            }
+            for (int u = 0; u < 32; ++u) vw[u] = wrow * v[u];
             transpose_reduce(v, lane);
             transpose_reduce(vw, lane);
             obs[(q * BN + c + lane) * 2 + 0] = v[0];
@@ -459,13 +513,11 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
       if (++acc == 2) { acc = 0; aph ^= 1; }
       if (fused) {
         epi_barrier();
-        const int et = q * 32 + lane;  // 0..127
-        const int64_t tr = T.rowD / BM;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int cc = et + h * 128;
+        for (int cc = (warp - 2) * 32 + lane; cc < BN; cc += 32 * kEpiWarps) {
           const int64_t col = T.colD + cc;
           if (cc < ndcol && col < T.n) {
+            const int64_t tr = T.rowD / BM;
             float se = 0.f, sw = 0.f;
             for (int w4 = 0; w4 < 2 * T.hsplit; ++w4) {
               se += obs[(w4 * BN + cc) * 2 + 0];
@@ -533,6 +585,21 @@ struct GroupSched {
     V.rowC = 64 * max(0, h0 - nhd);
     V.colD = 64 * b0;
     V.colC = 64 * max(0, b0 - nbd);
+    V.maW = V.maW1 = V.mbW = V.mbW1 = nullptr;
+    if (V.hsplit == 2) {
+      V.maW = V.maW1 = &Mp.a128;
+      V.rowW = V.rowD;
+    } else if (V.hsplit == 0 && V.hcnt == 2) {
+      V.maW = V.maW1 = &Mp.acs128;
+      V.rowW = V.rowC;
+    }
+    if (V.nbox == 4 && V.bsplit == 4 && b0 + 4 <= (int)(P.n / 64)) {
+      V.mbW = V.mbW1 = &Mp.b4;
+      V.colW = V.colD;
+    } else if (V.nbox == 4 && V.bsplit == 0 && (b0 - nbd) + 4 <= (int)(P.C16 / 64)) {
+      V.mbW = V.mbW1 = &Mp.bcs4;
+      V.colW = V.colC;
+    }
     V.C = P.C;
     V.ldc = P.ldc;
     V.m = P.m;
@@ -596,6 +663,26 @@ bool make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols, int
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 3-D bf16 view of a row-major rows x cols matrix as (64 columns, rows, column
+// box): element (x, y, z) is at ptr + y ld + 64 z + x.  Only the cols / 64 full
+// boxes are inside the view, so no copy reaches past a row or past the
+// matrix; the box is 64 x 64 x 4 (four B boxes of one stage), 128-byte swizzle.
+bool make_map_boxes(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols, int64_t ld) {
+  int64_t nb = cols / 64;
+  if (rows == 0 || nb == 0) {  // never read: a dummy valid map
+    rows = 1;
+    nb = 1;
+  }
+  const cuuint64_t dims[3] = {64, (cuuint64_t)rows, (cuuint64_t)nb};
+  const cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), 128};
+  const cuuint32_t box[3] = {64, 64, 4};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return g_encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int num_sms() {
   int dev = 0;
   cudaGetDevice(&dev);
@@ -640,10 +727,16 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
   for (int pl = 0; pl < 2; ++pl) {
     const void* acs = checksums ? w + P.L.acs + pl * P.L.acs_plane : op.a[0];
     const void* bcs = checksums ? w + P.L.bcs + pl * P.L.bcs_plane : op.b[0];
+    const int64_t acs_ld = checksums ? P.L.acs_ld : op.lda;
+    const int64_t bcs_ld = checksums ? P.L.bcs_ld : op.ldb;
     if (!make_map(&M.a[pl], op.a[pl], d.m, d.k, op.lda, 64, BM / 2) ||
-        !make_map(&M.acs[pl], acs, R16, d.k, checksums ? P.L.acs_ld : op.lda, 64, BM / 2) ||
+        !make_map(&M.acs[pl], acs, R16, d.k, acs_ld, 64, BM / 2) ||
         !make_map(&M.b[pl], op.b[pl], d.k, d.n, op.ldb, 64, BK) ||
-        !make_map(&M.bcs[pl], bcs, d.k, C16, checksums ? P.L.bcs_ld : op.ldb, 64, BK))
+        !make_map(&M.bcs[pl], bcs, d.k, C16, bcs_ld, 64, BK) ||
+        !make_map(&M.a128[pl], op.a[pl], d.m, d.k, op.lda, 64, BM) ||
+        !make_map(&M.acs128[pl], acs, R16, d.k, acs_ld, 64, BM) ||
+        !make_map_boxes(&M.b4[pl], op.b[pl], d.k, d.n, op.ldb) ||
+        !make_map_boxes(&M.bcs4[pl], bcs, d.k, C16, bcs_ld))
       return cudaErrorInvalidValue;
   }
   TcArgs g{};
@@ -663,7 +756,7 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
   g.vb_c = d.vb_cols;
   g.er = P.er;
   g.ec = P.ec;
-  g.g = P.g > 0 ? P.g : 256;
+  g.g = P.g > 0 ? P.g : 128;
   g.ngrp = P.ngrp;
   if (checksums && P.fused) {
     g.obs_col = reinterpret_cast<float*>(const_cast<char*>(w) + P.L.obs_col);
@@ -697,6 +790,13 @@ cudaError_t make_bf16_map(CUtensorMap* map, const void* ptr, int64_t rows, int64
   if (e != cudaSuccess) return e;
   return make_map(map, ptr, rows, cols, ld, box_cols, box_rows) ? cudaSuccess
                                                                 : cudaErrorInvalidValue;
+}
+
+cudaError_t make_bf16_map_boxes(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols,
+                                int64_t ld) {
+  cudaError_t e = get_encoder();
+  if (e != cudaSuccess) return e;
+  return make_map_boxes(map, ptr, rows, cols, ld) ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_group_gemm(const GroupDev& G, bool checksums, cudaStream_t st) {

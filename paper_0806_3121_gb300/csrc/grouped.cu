@@ -112,15 +112,20 @@ abft_status upload_tables(abft_group_s& G, cudaStream_t st) {
     P.partB = reinterpret_cast<double*>(ws + s.partB);
     P.nvr = s.nvr; P.nvc = s.nvc;
     P.bpt = bpt;
-    P.g = 64 * bpt;
+    P.g = 128;  // row-sum groups: one per 128 columns (one epilogue warp's column half)
     P.ngrp = cdiv(q.n, P.g);
     P.nhc = (int32_t)s.nhc; P.nbc = (int32_t)s.nbc;
     threshold_factors(G.dtype, q.k, kGrpVbR, kGrpVbC, &P.f1c, &P.f1r, &P.f2);
     cudaError_t e;
-    if ((e = make_bf16_map(&maps[p].a, q.A, q.m, q.k, q.lda, 64, 64)) != cudaSuccess ||
-        (e = make_bf16_map(&maps[p].acs, P.acs, s.R16, q.k, s.acs_ld, 64, 64)) != cudaSuccess ||
-        (e = make_bf16_map(&maps[p].b, q.B, q.k, q.n, q.ldb, 64, 64)) != cudaSuccess ||
-        (e = make_bf16_map(&maps[p].bcs, P.bcs, q.k, s.C16, s.bcs_ld, 64, 64)) != cudaSuccess)
+    GMaps& Mp = maps[p];
+    if ((e = make_bf16_map(&Mp.a, q.A, q.m, q.k, q.lda, 64, 64)) != cudaSuccess ||
+        (e = make_bf16_map(&Mp.acs, P.acs, s.R16, q.k, s.acs_ld, 64, 64)) != cudaSuccess ||
+        (e = make_bf16_map(&Mp.b, q.B, q.k, q.n, q.ldb, 64, 64)) != cudaSuccess ||
+        (e = make_bf16_map(&Mp.bcs, P.bcs, q.k, s.C16, s.bcs_ld, 64, 64)) != cudaSuccess ||
+        (e = make_bf16_map(&Mp.a128, q.A, q.m, q.k, q.lda, 64, 128)) != cudaSuccess ||
+        (e = make_bf16_map(&Mp.acs128, P.acs, s.R16, q.k, s.acs_ld, 64, 128)) != cudaSuccess ||
+        (e = make_bf16_map_boxes(&Mp.b4, q.B, q.k, q.n, q.ldb)) != cudaSuccess ||
+        (e = make_bf16_map_boxes(&Mp.bcs4, P.bcs, q.k, s.C16, s.bcs_ld)) != cudaSuccess)
       return fail(ABFT_ERR_INVALID, "problem %d: tensor map rejected (%s)", p,
                   cudaGetErrorString(e));
     const int64_t n_units[kGkCount] = {

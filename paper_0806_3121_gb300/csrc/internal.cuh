@@ -56,7 +56,7 @@ struct Plan {
   double f1_col, f2_col, f1_row, f2_row;  // threshold factors
   // Fused observed checksums (tensor-core dtypes): the product's epilogue
   // writes per-tile column partial sums (one per 128 rows) and per-row partial
-  // sums over column groups of g = min(vb_cols, 256) columns.
+  // sums over column groups of g = min(vb_cols, 128) columns.
   int fused;
   int64_t g, ngrp, ntr_obs;
   abft_ws_layout L;
@@ -156,7 +156,9 @@ struct GProb {  // one problem of a group, in device memory
 };
 
 struct GMaps {  // tensor maps of one problem (64-byte aligned in device memory)
-  CUtensorMap a, acs, b, bcs;
+  CUtensorMap a, acs, b, bcs;   // 64-row halves / one 64-column box
+  CUtensorMap a128, acs128;     // 128-row boxes (a whole tile's A)
+  CUtensorMap b4, bcs4;         // four full 64-column boxes in one copy (3-D view)
 };
 
 // CTA offsets of the grouped kernels: off[p] .. off[p+1] are problem p's CTAs.
@@ -202,6 +204,10 @@ __device__ __forceinline__ int find_prob(const int64_t* off, int count, int64_t 
 
 cudaError_t make_bf16_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols,
                           int64_t ld, uint32_t box_cols, uint32_t box_rows);
+// The 3-D four-box view of a row-major rows x cols bf16 matrix (full 64-column
+// boxes only).
+cudaError_t make_bf16_map_boxes(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols,
+                                int64_t ld);
 cudaError_t launch_group_encode(const GroupDev& G, cudaStream_t st);
 cudaError_t launch_group_gemm(const GroupDev& G, bool checksums, cudaStream_t st);
 cudaError_t launch_group_verify(const GroupDev& G, cudaStream_t st);

@@ -21,28 +21,49 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kColsPerCta = 8 * kThreads;  // 2048 columns, 8 per thread (16-byte loads)
 constexpr int kRowsPerCtaB = 128;          // rows of B per CTA in the row-checksum pass
+constexpr int kRowBatch = 8;               // rows whose loads are in flight together (A pass)
+constexpr int kRowBatchB = 16;             // the same for the B pass
+constexpr int kEncCols = 256;              // columns of one bf16 encode unit (8 per lane)
+constexpr int kEncWarps = kThreads / 32;   // warps sharing a unit's rows
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 __device__ __forceinline__ float warp_sumf(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Sum over the block's threads, valid in thread 0.
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  v = warp_sum(v);
+// Sums over the 32 lanes of N values at once (N = 8 or 16; a transposing
+// butterfly, N - 1 + log2(32 / N) shuffles): on return lane l holds, in v[0],
+// the sum over all lanes of their v[l / (32 / N)].
+template <int N>
+__device__ __forceinline__ void reduce_rows(float (&v)[N], int lane) {
+#pragma unroll
+  for (int s = 16, h = N / 2; h >= 1; s >>= 1, h >>= 1) {
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const float send = upper ? v[i] : v[i + h];
+      const float keep = upper ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+#pragma unroll
+  for (int o = 16 / N; o >= 1; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+}
+
+// Tree sum over the block's threads in fp32, valid in thread 0 (binary64
+// arithmetic is kept out of per-element work: GB300's FP64 pipe is narrow).
+__device__ __forceinline__ float block_sumf(float v, float* sh) {
+  v = warp_sumf(v);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();
   if (lane == 0) sh[w] = v;
   __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0)
-    for (int q = 0; q < kThreads / 32; ++q) t += sh[q];
+  float t = 0.f;
+  if (w == 0) {
+    t = lane < kThreads / 32 ? sh[lane] : 0.f;
+    t = warp_sumf(t);
+  }
   return t;
 }
 
@@ -71,73 +92,124 @@ __device__ __forceinline__ void load8(const __nv_bfloat16* row, int64_t c, int64
   }
 }
 
+// The same eight elements as raw bf16 bits (zeros past `len`), unpacked later:
+// a row batch in flight costs 4 registers per row instead of 8.
+__device__ __forceinline__ uint4 load8raw(const __nv_bfloat16* row, int64_t c, int64_t len) {
+  if (c + 8 <= len && ((reinterpret_cast<uintptr_t>(row + c) & 15) == 0))
+    return *reinterpret_cast<const uint4*>(row + c);
+  uint32_t w[4] = {0u, 0u, 0u, 0u};
+  const uint16_t* r16 = reinterpret_cast<const uint16_t*>(row);
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    if (c + q < len) w[q >> 1] |= (uint32_t)r16[c + q] << (16 * (q & 1));
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__device__ __forceinline__ void unpack8(const uint4& u, float (&v)[8]) {
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float2 f = __bfloat1622float2(h[q]);
+    v[2 * q] = f.x;
+    v[2 * q + 1] = f.y;
+  }
+}
+
 __device__ __forceinline__ void store8(__nv_bfloat16* dst, const __nv_bfloat16 (&v)[8]) {
   *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v);
 }
 
 // Column checksums of A per verify block (fp32 sums, hi/lo pieces), per-row
 // partial sums of squares (one per 256 columns) and per-CTA partials of the
-// squared norms of the two checksum rows.  Unit = 2048 columns (chunk cx) x
-// one verify block I; thread = 8 consecutive columns.
-__device__ __forceinline__ void lpA_cols_unit(const __nv_bfloat16* __restrict__ A, int64_t lda,
-                                              int64_t m, int64_t k, int vb, int e,
-                                              __nv_bfloat16* __restrict__ acs, int64_t ldk,
-                                              float* __restrict__ rowpart, int64_t nchr,
-                                              double* __restrict__ part, int64_t nch, int64_t cx,
-                                              int64_t I, double* sh) {
+// squared norms of the two checksum rows.  Unit = 256 columns (chunk cx) x one
+// verify block I: lane = 8 consecutive columns, warp w = rows i0 + w + 8 t
+// (the loads of kRowBatch rows in flight together); the eight warps' column
+// sums meet in shared memory (red: [8][256][2] floats).
+__device__ __forceinline__ void lpA_unit(const __nv_bfloat16* __restrict__ A, int64_t lda,
+                                         int64_t m, int64_t k, int vb, int e,
+                                         __nv_bfloat16* __restrict__ acs, int64_t ldk,
+                                         float* __restrict__ rowpart, int64_t nchr,
+                                         double* __restrict__ part, int64_t cx, int64_t I,
+                                         float* red, float* sh) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t c0 = cx * kColsPerCta + 8 * threadIdx.x;
+  const int64_t c0 = cx * kEncCols + 8 * lane;
   const float sc = scalbnf(1.0f, -e);
   const int64_t i0 = I * vb, i1 = min(i0 + (int64_t)vb, m);
+  const int nrow = (int)(i1 - i0);
+  const __nv_bfloat16* Ab = A + i0 * lda;
   float se[8], sw[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) se[q] = sw[q] = 0.f;
-  for (int64_t i = i0; i < i1; ++i) {
-    float v[8];
-    load8(A + i * lda, c0, k, v);
-    const float w = (float)(i - i0 + 1) * sc;
-    float sq = 0.f;
+  for (int rb = warp; rb < nrow; rb += kEncWarps * kRowBatch) {
+    uint4 raw[kRowBatch];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      se[q] += v[q];
-      sw[q] = fmaf(w, v[q], sw[q]);
-      sq = fmaf(v[q], v[q], sq);
+    for (int r = 0; r < kRowBatch; ++r) {
+      const int t = rb + kEncWarps * r;
+      raw[r] = t < nrow ? load8raw(Ab + (int64_t)t * lda, c0, k) : make_uint4(0u, 0u, 0u, 0u);
     }
-    sq = warp_sumf(sq);
-    const int64_t rc = cx * (kThreads / 32) + warp;  // 256-column chunk
-    if (lane == 0 && rc < nchr) rowpart[i * nchr + rc] = sq;
-  }
-  double q0 = 0.0, q1 = 0.0;
-  if (c0 < ldk) {
-    __nv_bfloat16 eh[8], el[8], wh[8], wl[8];
+    float sq[kRowBatch];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      split(se[q], eh[q], el[q]);
-      split(sw[q], wh[q], wl[q]);
-      q0 += (double)se[q] * se[q];
-      q1 += (double)sw[q] * sw[q];
+    for (int r = 0; r < kRowBatch; ++r) {
+      const int t = rb + kEncWarps * r;
+      float v[8];
+      unpack8(raw[r], v);
+      const float w = (float)(t + 1) * sc;
+      sq[r] = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        se[q] += v[q];
+        sw[q] = fmaf(w, v[q], sw[q]);
+        sq[r] = fmaf(v[q], v[q], sq[r]);
+      }
     }
-    store8(acs + (4 * I + 0) * ldk + c0, eh);
-    store8(acs + (4 * I + 1) * ldk + c0, el);
-    store8(acs + (4 * I + 2) * ldk + c0, wh);
-    store8(acs + (4 * I + 3) * ldk + c0, wl);
+    reduce_rows<kRowBatch>(sq, lane);  // row r's sum of squares in lanes r * (32 / kRowBatch) ..
+    constexpr int kLanesPerRow = 32 / kRowBatch;
+    const int t = rb + kEncWarps * (lane / kLanesPerRow);
+    if (lane % kLanesPerRow == 0 && t < nrow) rowpart[(i0 + t) * nchr + cx] = sq[0];
   }
-  const double t0 = block_sum(q0, sh);
-  if (threadIdx.x == 0) part[(2 * I) * nch + cx] = t0;
-  const double t1 = block_sum(q1, sh);
-  if (threadIdx.x == 0) part[(2 * I + 1) * nch + cx] = t1;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    red[(warp * kEncCols + 8 * lane + q) * 2 + 0] = se[q];
+    red[(warp * kEncCols + 8 * lane + q) * 2 + 1] = sw[q];
+  }
+  __syncthreads();
+  const int c = threadIdx.x;  // column of the chunk
+  float te = 0.f, tw = 0.f;
+#pragma unroll
+  for (int w = 0; w < kEncWarps; ++w) {
+    te += red[(w * kEncCols + c) * 2 + 0];
+    tw += red[(w * kEncCols + c) * 2 + 1];
+  }
+  const int64_t col = cx * kEncCols + c;
+  float q0 = 0.f, q1 = 0.f;
+  if (col < ldk) {  // columns k .. ldk-1 hold zeros
+    __nv_bfloat16 h, l;
+    split(te, h, l);
+    acs[(4 * I + 0) * ldk + col] = h;
+    acs[(4 * I + 1) * ldk + col] = l;
+    split(tw, h, l);
+    acs[(4 * I + 2) * ldk + col] = h;
+    acs[(4 * I + 3) * ldk + col] = l;
+    q0 = te * te;
+    q1 = tw * tw;
+  }
+  const float t0 = block_sumf(q0, sh);
+  if (threadIdx.x == 0) part[(2 * I) * nchr + cx] = (double)t0;
+  const float t1 = block_sumf(q1, sh);
+  if (threadIdx.x == 0) part[(2 * I + 1) * nchr + cx] = (double)t1;
+  __syncthreads();  // red is reused by the next unit
 }
 
-__global__ void __launch_bounds__(kThreads) k_lpA_cols(const __nv_bfloat16* __restrict__ A,
+__global__ void __launch_bounds__(kThreads, 2) k_lpA_cols(const __nv_bfloat16* __restrict__ A,
                                                        int64_t lda, int64_t m, int64_t k, int vb,
                                                        int e, __nv_bfloat16* __restrict__ acs,
                                                        int64_t ldk, float* __restrict__ rowpart,
-                                                       int64_t nchr, double* __restrict__ part,
-                                                       int64_t nch) {
-  __shared__ double sh[kThreads / 32];
+                                                       int64_t nchr, double* __restrict__ part) {
+  __shared__ float red[kEncWarps * kEncCols * 2];
+  __shared__ float sh[kThreads / 32];
   const int64_t nvb = cdiv(m, vb);
   for (int64_t I = blockIdx.y; I < nvb; I += gridDim.y)
-    lpA_cols_unit(A, lda, m, k, vb, e, acs, ldk, rowpart, nchr, part, nch, blockIdx.x, I, sh);
+    lpA_unit(A, lda, m, k, vb, e, acs, ldk, rowpart, nchr, part, blockIdx.x, I, red, sh);
 }
 
 // Block checksum rows S_A[t] = sum_I A[I*bs + t], as hi/lo pieces.
@@ -160,16 +232,18 @@ __global__ void __launch_bounds__(kThreads) k_lpA_block(const __nv_bfloat16* __r
 // Row checksums of B per verify column block (hi/lo pieces in the row-major
 // bcs), per-column partial sums of squares (one per 128 rows) and partials
 // of the squared norms of the checksum columns.  Verify blocks of 8, 16, ...,
-// 256 columns: the lanes of a block reduce with shuffles.  Unit = 2048
-// columns (chunk cx) x 128 rows (chunk ry); thread = 8 consecutive columns.
-__device__ __forceinline__ void lpB_rows_unit(const __nv_bfloat16* __restrict__ B, int64_t ldb,
-                                              int64_t k, int64_t n, int vb, int e,
-                                              __nv_bfloat16* __restrict__ bcs, int64_t ldcs,
-                                              float* __restrict__ colpart,
-                                              double* __restrict__ part, int64_t nch, int64_t cx,
-                                              int64_t ry) {
-  const int lane = threadIdx.x & 31;
-  const int64_t c0 = cx * kColsPerCta + 8 * threadIdx.x;
+// 256 columns: the lanes of a block reduce with shuffles.  Unit = 256 columns
+// (chunk cx) x 128 rows (chunk ry): lane = 8 consecutive columns, warp w = rows
+// l0 + w + 8 t; the warps' column squares and block partials meet in shared
+// memory (red: [8][256] floats, redq: [8][32][2] floats).
+__device__ __forceinline__ void lpB_unit(const __nv_bfloat16* __restrict__ B, int64_t ldb,
+                                         int64_t k, int64_t n, int vb, int e,
+                                         __nv_bfloat16* __restrict__ bcs, int64_t ldcs,
+                                         float* __restrict__ colpart, double* __restrict__ part,
+                                         int64_t nch, int64_t cx, int64_t ry, float* red,
+                                         float* redq) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c0 = cx * kEncCols + 8 * lane;
   const int64_t l0 = ry * kRowsPerCtaB, l1 = min(l0 + kRowsPerCtaB, k);
   const int seg = vb / 8;  // lanes per verify block (1 .. 32)
   const bool leader = (lane % seg) == 0 && c0 < n;
@@ -177,49 +251,78 @@ __device__ __forceinline__ void lpB_rows_unit(const __nv_bfloat16* __restrict__ 
   const float sc = scalbnf(1.0f, -e);
   float wq[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) wq[q] = (float)((c0 + q) % vb + 1) * sc;
+  for (int q = 0; q < 8; ++q) wq[q] = (float)((int)((c0 + q) % vb) + 1) * sc;
   float cs[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) cs[q] = 0.f;
-  double q0 = 0.0, q1 = 0.0;
-  for (int64_t l = l0; l < l1; ++l) {
-    float v[8];
-    load8(B + l * ldb, c0, n, v);
-    float se = 0.f, sw = 0.f;
+  float q0 = 0.f, q1 = 0.f;
+  const int nrow = (int)(l1 - l0);
+  const __nv_bfloat16* Bb = B + l0 * ldb;
+  for (int rb = warp; rb < nrow; rb += kEncWarps * kRowBatchB) {
+    uint4 raw[kRowBatchB];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      se += v[q];
-      sw = fmaf(wq[q], v[q], sw);
-      cs[q] = fmaf(v[q], v[q], cs[q]);
+    for (int r = 0; r < kRowBatchB; ++r) {
+      const int t = rb + kEncWarps * r;
+      raw[r] = t < nrow ? load8raw(Bb + (int64_t)t * ldb, c0, n) : make_uint4(0u, 0u, 0u, 0u);
     }
-    for (int o = seg >> 1; o > 0; o >>= 1) {
-      se += __shfl_xor_sync(0xffffffffu, se, o);
-      sw += __shfl_xor_sync(0xffffffffu, sw, o);
-    }
-    if (leader) {
-      __nv_bfloat16 pc[4];
-      split(se, pc[0], pc[1]);
-      split(sw, pc[2], pc[3]);
-      *reinterpret_cast<uint2*>(bcs + l * ldcs + 4 * J) = *reinterpret_cast<const uint2*>(pc);
-      q0 += (double)se * se;
-      q1 += (double)sw * sw;
+#pragma unroll
+    for (int r = 0; r < kRowBatchB; ++r) {
+      const int64_t l = l0 + rb + kEncWarps * r;
+      float v[8];
+      unpack8(raw[r], v);
+      float se = 0.f, sw = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        se += v[q];
+        sw = fmaf(wq[q], v[q], sw);
+        cs[q] = fmaf(v[q], v[q], cs[q]);
+      }
+      for (int o = seg >> 1; o > 0; o >>= 1) {
+        se += __shfl_xor_sync(0xffffffffu, se, o);
+        sw += __shfl_xor_sync(0xffffffffu, sw, o);
+      }
+      if (leader && l < l1) {
+        __nv_bfloat16 pc[4];
+        split(se, pc[0], pc[1]);
+        split(sw, pc[2], pc[3]);
+        *reinterpret_cast<uint2*>(bcs + l * ldcs + 4 * J) = *reinterpret_cast<const uint2*>(pc);
+        q0 = fmaf(se, se, q0);
+        q1 = fmaf(sw, sw, q1);
+      }
     }
   }
-  if (leader) {
-    part[(2 * J) * nch + ry] = q0;
-    part[(2 * J + 1) * nch + ry] = q1;
-  }
 #pragma unroll
-  for (int q = 0; q < 8; ++q)
-    if (c0 + q < n) colpart[ry * n + c0 + q] = cs[q];
+  for (int q = 0; q < 8; ++q) red[warp * kEncCols + 8 * lane + q] = cs[q];
+  redq[(warp * 32 + lane) * 2 + 0] = q0;
+  redq[(warp * 32 + lane) * 2 + 1] = q1;
+  __syncthreads();
+  const int c = threadIdx.x;
+  float t = 0.f;
+#pragma unroll
+  for (int w = 0; w < kEncWarps; ++w) t += red[w * kEncCols + c];
+  if (cx * kEncCols + c < n) colpart[ry * n + cx * kEncCols + c] = t;
+  if (c < 32 && (c % seg) == 0 && cx * kEncCols + 8 * c < n) {
+    float a0 = 0.f, a1 = 0.f;
+    for (int w = 0; w < kEncWarps; ++w) {
+      a0 += redq[(w * 32 + c) * 2 + 0];
+      a1 += redq[(w * 32 + c) * 2 + 1];
+    }
+    const int64_t Jc = (cx * kEncCols + 8 * c) / vb;
+    part[(2 * Jc) * nch + ry] = (double)a0;
+    part[(2 * Jc + 1) * nch + ry] = (double)a1;
+  }
+  __syncthreads();  // red / redq are reused by the next unit
 }
 
-__global__ void __launch_bounds__(kThreads) k_lpB_rows(const __nv_bfloat16* __restrict__ B,
+__global__ void __launch_bounds__(kThreads, 2) k_lpB_rows(const __nv_bfloat16* __restrict__ B,
                                                        int64_t ldb, int64_t k, int64_t n, int vb,
                                                        int e, __nv_bfloat16* __restrict__ bcs,
                                                        int64_t ldcs, float* __restrict__ colpart,
                                                        double* __restrict__ part, int64_t nch) {
-  lpB_rows_unit(B, ldb, k, n, vb, e, bcs, ldcs, colpart, part, nch, blockIdx.x, blockIdx.y);
+  __shared__ float red[kEncWarps * kEncCols];
+  __shared__ float redq[kEncWarps * 32 * 2];
+  for (int64_t ry = blockIdx.y; ry < nch; ry += gridDim.y)
+    lpB_unit(B, ldb, k, n, vb, e, bcs, ldcs, colpart, part, nch, blockIdx.x, ry, red, redq);
 }
 
 // The same outputs for any verify block size (one warp per row segment).
@@ -238,7 +341,7 @@ __global__ void __launch_bounds__(kThreads) k_lpB_rows_any(const __nv_bfloat16* 
   for (int64_t J = blockIdx.y; J < nvb; J += gridDim.y) {
     const int64_t j0 = J * vb, j1 = min(j0 + (int64_t)vb, n);
     const int64_t l0 = chunk * kRowsPerCtaB, l1 = min(l0 + kRowsPerCtaB, k);
-    double q0 = 0.0, q1 = 0.0;
+    float q0 = 0.f, q1 = 0.f;
     for (int64_t l = l0; l < l1; ++l) {
       float se = 0.f, sw = 0.f;
       for (int64_t j = j0 + lane; j < j1; j += 32) {
@@ -257,8 +360,8 @@ __global__ void __launch_bounds__(kThreads) k_lpB_rows_any(const __nv_bfloat16* 
         bcs[l * ldcs + 4 * J + 2] = h;
         bcs[l * ldcs + 4 * J + 3] = lo;
       }
-      q0 += (double)se * se;
-      q1 += (double)sw * sw;
+      q0 = fmaf(se, se, q0);
+      q1 = fmaf(sw, sw, q1);
     }
     if (lane == 0) {
       part[(2 * J) * nch + chunk] = q0;
@@ -285,14 +388,15 @@ __global__ void __launch_bounds__(kThreads) k_lp_col_sq(const __nv_bfloat16* __r
   }
 }
 
-// out[o] = sqrt(sum_c part[o*so + c*sc]) (fp32 partials, binary64 sum).
+// out[o] = sqrt(sum_c part[o*so + c*sc]): fp32 partials summed in fp32 (the
+// norms scale the thresholds; a few u32 of relative error is immaterial).
 __global__ void k_lp_norms(const float* __restrict__ part, int64_t nout, int64_t nch, int64_t so,
                            int64_t sc, double* __restrict__ out) {
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= nout) return;
-  double s = 0.0;
-  for (int64_t c = 0; c < nch; ++c) s += (double)part[o * so + c * sc];
-  out[o] = sqrt(s);
+  float s = 0.f;
+  for (int64_t c = 0; c < nch; ++c) s += part[o * so + c * sc];
+  out[o] = (double)sqrtf(s);
 }
 
 // Threshold norms of verify block I from the line norms and the checksum
@@ -300,22 +404,22 @@ __global__ void k_lp_norms(const float* __restrict__ part, int64_t nout, int64_t
 __device__ __forceinline__ void lp_blk_one(const double* __restrict__ nvec, int64_t len, int vb,
                                            int e, const double* __restrict__ part, int64_t nch,
                                            double* __restrict__ nblk, int64_t I) {
-  const double sc = scalbn(1.0, -e);
+  const float sc = scalbnf(1.0f, -e);
   const int64_t t0 = I * vb, t1 = min(t0 + (int64_t)vb, len);
-  double f0 = 0.0, f1 = 0.0, q0 = 0.0, q1 = 0.0;
+  float f0 = 0.f, f1 = 0.f, q0 = 0.f, q1 = 0.f;
   for (int64_t t = t0; t < t1; ++t) {
-    const double v = nvec[t], wv = (double)(t - t0 + 1) * sc * v;
-    f0 = fma(v, v, f0);
-    f1 = fma(wv, wv, f1);
+    const float v = (float)nvec[t], wv = (float)(t - t0 + 1) * sc * v;
+    f0 = fmaf(v, v, f0);
+    f1 = fmaf(wv, wv, f1);
   }
   for (int64_t c = 0; c < nch; ++c) {
-    q0 += part[(2 * I) * nch + c];
-    q1 += part[(2 * I + 1) * nch + c];
+    q0 += (float)part[(2 * I) * nch + c];
+    q1 += (float)part[(2 * I + 1) * nch + c];
   }
-  nblk[4 * I + 0] = sqrt(f0);
-  nblk[4 * I + 1] = sqrt(f1);
-  nblk[4 * I + 2] = sqrt(q0);
-  nblk[4 * I + 3] = sqrt(q1);
+  nblk[4 * I + 0] = (double)sqrtf(f0);
+  nblk[4 * I + 1] = (double)sqrtf(f1);
+  nblk[4 * I + 2] = (double)sqrtf(q0);
+  nblk[4 * I + 3] = (double)sqrtf(q1);
 }
 
 __global__ void k_lp_blk(const double* __restrict__ nvec, int64_t len, int vb, int e,
@@ -362,7 +466,7 @@ __global__ void __launch_bounds__(kThreads) k_x3A_cols(const float* __restrict__
                                                        int64_t ldk, float* __restrict__ rowpart,
                                                        int64_t nchr, double* __restrict__ part,
                                                        int64_t nch) {
-  __shared__ double sh[kThreads / 32];
+  __shared__ float sh[kThreads / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t c0 = (int64_t)blockIdx.x * kColsPerCta + 8 * threadIdx.x;
   const int64_t nvb = cdiv(m, vb);
@@ -388,20 +492,20 @@ __global__ void __launch_bounds__(kThreads) k_x3A_cols(const float* __restrict__
       const int64_t rc = (int64_t)blockIdx.x * (kThreads / 32) + warp;
       if (lane == 0 && rc < nchr) rowpart[i * nchr + rc] = sq;
     }
-    double q0 = 0.0, q1 = 0.0;
+    float q0 = 0.f, q1 = 0.f;
     if (c0 < ldk) {
       store_split8(chi, clo, (2 * I) * ldk + c0, se);
       store_split8(chi, clo, (2 * I + 1) * ldk + c0, sw);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        q0 += (double)se[q] * se[q];
-        q1 += (double)sw[q] * sw[q];
+        q0 = fmaf(se[q], se[q], q0);
+        q1 = fmaf(sw[q], sw[q], q1);
       }
     }
-    const double t0 = block_sum(q0, sh);
-    if (threadIdx.x == 0) part[(2 * I) * nch + blockIdx.x] = t0;
-    const double t1 = block_sum(q1, sh);
-    if (threadIdx.x == 0) part[(2 * I + 1) * nch + blockIdx.x] = t1;
+    const float t0 = block_sumf(q0, sh);
+    if (threadIdx.x == 0) part[(2 * I) * nch + blockIdx.x] = (double)t0;
+    const float t1 = block_sumf(q1, sh);
+    if (threadIdx.x == 0) part[(2 * I + 1) * nch + blockIdx.x] = (double)t1;
   }
 }
 
@@ -448,7 +552,7 @@ __global__ void __launch_bounds__(kThreads) k_x3B_rows(const float* __restrict__
   float cs[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) cs[q] = 0.f;
-  double q0 = 0.0, q1 = 0.0;
+  float q0 = 0.f, q1 = 0.f;
   for (int64_t l = l0; l < l1; ++l) {
     float v[8];
     load8f(B + l * ldb, c0, n, v);
@@ -472,8 +576,8 @@ __global__ void __launch_bounds__(kThreads) k_x3B_rows(const float* __restrict__
       split(sw, h, lo);
       chi[l * ldcs + 2 * J + 1] = h;
       clo[l * ldcs + 2 * J + 1] = lo;
-      q0 += (double)se * se;
-      q1 += (double)sw * sw;
+      q0 = fmaf(se, se, q0);
+      q1 = fmaf(sw, sw, q1);
     }
   }
   if (leader) {
@@ -526,7 +630,7 @@ __global__ void __launch_bounds__(kThreads) k_x3B_rows_any(const float* __restri
   for (int64_t J = blockIdx.y; J < nvb; J += gridDim.y) {
     const int64_t j0 = J * vb, j1 = min(j0 + (int64_t)vb, n);
     const int64_t l0 = chunk * kRowsPerCtaB, l1 = min(l0 + kRowsPerCtaB, k);
-    double q0 = 0.0, q1 = 0.0;
+    float q0 = 0.f, q1 = 0.f;
     for (int64_t l = l0; l < l1; ++l) {
       float se = 0.f, sw = 0.f;
       for (int64_t j = j0 + lane; j < j1; j += 32) {
@@ -545,8 +649,8 @@ __global__ void __launch_bounds__(kThreads) k_x3B_rows_any(const float* __restri
         chi[l * ldcs + 2 * J + 1] = h;
         clo[l * ldcs + 2 * J + 1] = lo;
       }
-      q0 += (double)se * se;
-      q1 += (double)sw * sw;
+      q0 = fmaf(se, se, q0);
+      q1 = fmaf(sw, sw, q1);
     }
     if (lane == 0) {
       part[(2 * J) * nch + chunk] = q0;
@@ -592,7 +696,7 @@ int64_t align_elems(int64_t elems) { return (elems * 2 + 255) / 256 * 128; }
 // partial sums of squares (fp32).
 size_t lp_part_bytes(const Plan& P) {
   const int64_t k = P.d.k > 0 ? P.d.k : 1;
-  return sizeof(double) * (2 * P.nvr * cdiv(k, kColsPerCta) + 2 * P.nvc * cdiv(k, kRowsPerCtaB)) +
+  return sizeof(double) * (2 * P.nvr * cdiv(k, kEncCols) + 2 * P.nvc * cdiv(k, kRowsPerCtaB)) +
          sizeof(float) * (P.d.m * cdiv(k, 256) + cdiv(k, kRowsPerCtaB) * P.d.n) + 64;
 }
 
@@ -620,7 +724,7 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, void
   const int64_t nchB = cdiv(d.k, kRowsPerCtaB);
   const int64_t nchr = cdiv(d.k, 256);
   double* partA = S.part;
-  double* partB = partA + 2 * P.nvr * nchA;
+  double* partB = partA + 2 * P.nvr * nchr;  // room for the bf16 pass's ceil(k/256) partials
   float* rowpart = reinterpret_cast<float*>(partB + 2 * P.nvc * nchB);
   float* colpart = rowpart + d.m * nchr;
   const bool fastB = d.vb_cols >= 8 && d.vb_cols <= 256 && (d.vb_cols & (d.vb_cols - 1)) == 0;
@@ -665,16 +769,16 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, void
     count_launches(6 + (P.bs > 0 ? 1 : 0) + (fastB ? 0 : 1));
     return cudaGetLastError();
   }
-  k_lpA_cols<<<dim3((unsigned)nchA, gy(P.nvr)), kThreads, 0, st>>>(
-      A, d.lda, d.m, d.k, d.vb_rows, P.er, acs, P.L.acs_ld, rowpart, nchr, partA, nchA);
+  k_lpA_cols<<<dim3((unsigned)cdiv(P.L.acs_ld, kEncCols), gy(P.nvr)), kThreads, 0, st>>>(
+      A, d.lda, d.m, d.k, d.vb_rows, P.er, acs, P.L.acs_ld, rowpart, nchr, partA);
   if (P.bs > 0)
     k_lpA_block<<<dim3((unsigned)cdiv(d.k, kThreads), gy(P.bs)), kThreads, 0, st>>>(
         A, d.lda, d.k, d.grid_p, P.bs, acs + 4 * P.nvr * P.L.acs_ld, P.L.acs_ld);
   k_lp_norms<<<(unsigned)cdiv(d.m, 128), 128, 0, st>>>(rowpart, d.m, nchr, nchr, 1, nArow);
-  k_lp_blk<<<(unsigned)cdiv(P.nvr, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA, nchA,
+  k_lp_blk<<<(unsigned)cdiv(P.nvr, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA, nchr,
                                                        nAblk);
   if (fastB) {
-    k_lpB_rows<<<dim3((unsigned)cdiv(d.n, kColsPerCta), (unsigned)nchB), kThreads, 0, st>>>(
+    k_lpB_rows<<<dim3((unsigned)cdiv(d.n, kEncCols), gy(nchB)), kThreads, 0, st>>>(
         B, d.ldb, d.k, d.n, d.vb_cols, P.ec, bcs, P.L.bcs_ld, colpart, partB, nchB);
   } else {
     k_lpB_rows_any<<<dim3((unsigned)cdiv(nchB, kThreads / 32), gy(P.nvc)), kThreads, 0, st>>>(
@@ -735,63 +839,76 @@ cudaError_t launch_gemm_lp(const Plan& P, const void* A, const void* B, float* C
 // ---------------- grouped encode (many bf16 problems per launch)
 namespace {
 
-__global__ void __launch_bounds__(kThreads) k_grp_encA(const GProb* __restrict__ probs,
-                                                       const int64_t* __restrict__ off,
-                                                       int count) {
-  __shared__ double sh[kThreads / 32];
-  const int p = find_prob(off, count, blockIdx.x);
-  const GProb& P = probs[p];
-  const int64_t u = blockIdx.x - off[p], nchA = cdiv(P.k, kColsPerCta);
-  lpA_cols_unit(static_cast<const __nv_bfloat16*>(P.A), P.lda, P.m, P.k, kGrpVbR, kGrpEr,
-                static_cast<__nv_bfloat16*>(P.acs), P.acs_ld, P.rowpart, cdiv(P.k, 256), P.partA,
-                nchA, u % nchA, u / nchA, sh);
+__global__ void __launch_bounds__(kThreads, 2) k_grp_encA(const GProb* __restrict__ probs,
+                                                       const int2* __restrict__ tab) {
+  __shared__ float red[kEncWarps * kEncCols * 2];
+  __shared__ float sh[kThreads / 32];
+  const int2 e = tab[blockIdx.x];
+  const GProb& P = probs[e.x];
+  const int64_t u = e.y, ncx = cdiv(P.acs_ld, kEncCols);
+  lpA_unit(static_cast<const __nv_bfloat16*>(P.A), P.lda, P.m, P.k, kGrpVbR, kGrpEr,
+           static_cast<__nv_bfloat16*>(P.acs), P.acs_ld, P.rowpart, cdiv(P.k, 256), P.partA,
+           u % ncx, u / ncx, red, sh);
 }
 
-__global__ void __launch_bounds__(kThreads) k_grp_encB(const GProb* __restrict__ probs,
-                                                       const int64_t* __restrict__ off,
-                                                       int count) {
-  const int p = find_prob(off, count, blockIdx.x);
-  const GProb& P = probs[p];
-  const int64_t u = blockIdx.x - off[p], ncx = cdiv(P.n, kColsPerCta);
-  lpB_rows_unit(static_cast<const __nv_bfloat16*>(P.B), P.ldb, P.k, P.n, kGrpVbC, kGrpEc,
-                static_cast<__nv_bfloat16*>(P.bcs), P.bcs_ld, P.colpart, P.partB,
-                cdiv(P.k, kRowsPerCtaB), u % ncx, u / ncx);
+__global__ void __launch_bounds__(kThreads, 2) k_grp_encB(const GProb* __restrict__ probs,
+                                                       const int2* __restrict__ tab) {
+  __shared__ float red[kEncWarps * kEncCols];
+  __shared__ float redq[kEncWarps * 32 * 2];
+  const int2 e = tab[blockIdx.x];
+  const GProb& P = probs[e.x];
+  const int64_t u = e.y, ncx = cdiv(P.n, kEncCols);
+  lpB_unit(static_cast<const __nv_bfloat16*>(P.B), P.ldb, P.k, P.n, kGrpVbC, kGrpEc,
+           static_cast<__nv_bfloat16*>(P.bcs), P.bcs_ld, P.colpart, P.partB,
+           cdiv(P.k, kRowsPerCtaB), u % ncx, u / ncx, red, redq);
 }
 
 // Row norms ||A_i|| (first ceil(m/256) CTAs of a problem) and column norms
-// ||B_:j|| (next ceil(n/256)) from the fp32 partial sums of squares.
+// ||B_:j|| (next ceil(n/256)) from the fp32 partial sums of squares (fp32
+// sums; stored as binary64 and as fp32 for the verify screen).
 __global__ void __launch_bounds__(kThreads) k_grp_lines(const GProb* __restrict__ probs,
-                                                        const int64_t* __restrict__ off,
-                                                        int count) {
-  const int p = find_prob(off, count, blockIdx.x);
-  const GProb& P = probs[p];
-  const int64_t u = blockIdx.x - off[p], nra = cdiv(P.m, kThreads);
+                                                        const int2* __restrict__ tab) {
+  const int2 e = tab[blockIdx.x];
+  const GProb& P = probs[e.x];
+  const int64_t u = e.y, nra = cdiv(P.m, kThreads);
   if (u < nra) {
     const int64_t i = u * kThreads + threadIdx.x;
     if (i >= P.m) return;
     const int64_t nchr = cdiv(P.k, 256);
-    double s = 0.0;
-    for (int64_t c = 0; c < nchr; ++c) s += (double)P.rowpart[i * nchr + c];
-    P.nArow[i] = sqrt(s);
+    float s = 0.f;
+    for (int64_t c = 0; c < nchr; ++c) s += P.rowpart[i * nchr + c];
+    s = sqrtf(s);
+    P.nArow[i] = (double)s;
+    P.nArow32[i] = s;
   } else {
     const int64_t j = (u - nra) * kThreads + threadIdx.x;
     if (j >= P.n) return;
     const int64_t nch = cdiv(P.k, kRowsPerCtaB);
-    double s = 0.0;
-    for (int64_t c = 0; c < nch; ++c) s += (double)P.colpart[c * P.n + j];
-    P.nBcol[j] = sqrt(s);
+    float s = 0.f;
+    for (int64_t c = 0; c < nch; ++c) s += P.colpart[c * P.n + j];
+    s = sqrtf(s);
+    P.nBcol[j] = (double)s;
+    P.nBcol32[j] = s;
   }
 }
 
-// Threshold norms of every verify block; one CTA per problem.
-__global__ void __launch_bounds__(kThreads) k_grp_blk(const GProb* __restrict__ probs) {
+// Threshold norms of every verify block and the fp32 threshold factors of
+// the verify screen; one CTA per problem.
+__global__ void __launch_bounds__(kThreads) k_grp_blk(const GProb* __restrict__ probs, double s) {
   const GProb& P = probs[blockIdx.x];
   for (int64_t t = threadIdx.x; t < P.nvr + P.nvc; t += kThreads) {
-    if (t < P.nvr)
-      lp_blk_one(P.nArow, P.m, kGrpVbR, kGrpEr, P.partA, cdiv(P.k, kColsPerCta), P.nAblk, t);
-    else
-      lp_blk_one(P.nBcol, P.n, kGrpVbC, kGrpEc, P.partB, cdiv(P.k, kRowsPerCtaB), P.nBblk,
-                 t - P.nvr);
+    if (t < P.nvr) {
+      lp_blk_one(P.nArow, P.m, kGrpVbR, kGrpEr, P.partA, cdiv(P.k, kEncCols), P.nAblk, t);
+      const double* nb = P.nAblk + 4 * t;
+      P.tauA[2 * t + 0] = (float)(s * (P.f1c * nb[0] + P.f2 * nb[2]));
+      P.tauA[2 * t + 1] = (float)(s * (P.f1c * nb[1] + P.f2 * nb[3]));
+    } else {
+      const int64_t J = t - P.nvr;
+      lp_blk_one(P.nBcol, P.n, kGrpVbC, kGrpEc, P.partB, cdiv(P.k, kRowsPerCtaB), P.nBblk, J);
+      const double* nb = P.nBblk + 4 * J;
+      P.tauB[2 * J + 0] = (float)(s * (P.f1r * nb[0] + P.f2 * nb[2]));
+      P.tauB[2 * J + 1] = (float)(s * (P.f1r * nb[1] + P.f2 * nb[3]));
+    }
   }
 }
 
@@ -800,13 +917,12 @@ __global__ void __launch_bounds__(kThreads) k_grp_blk(const GProb* __restrict__ 
 cudaError_t launch_group_encode(const GroupDev& G, cudaStream_t st) {
   if (G.count == 0) return cudaSuccess;
   if (G.nctas[kGkEncA] > 0)
-    k_grp_encA<<<(unsigned)G.nctas[kGkEncA], kThreads, 0, st>>>(G.probs, G.off[kGkEncA], G.count);
+    k_grp_encA<<<(unsigned)G.nctas[kGkEncA], kThreads, 0, st>>>(G.probs, G.tab[kGkEncA]);
   if (G.nctas[kGkEncB] > 0)
-    k_grp_encB<<<(unsigned)G.nctas[kGkEncB], kThreads, 0, st>>>(G.probs, G.off[kGkEncB], G.count);
+    k_grp_encB<<<(unsigned)G.nctas[kGkEncB], kThreads, 0, st>>>(G.probs, G.tab[kGkEncB]);
   if (G.nctas[kGkLines] > 0)
-    k_grp_lines<<<(unsigned)G.nctas[kGkLines], kThreads, 0, st>>>(G.probs, G.off[kGkLines],
-                                                                  G.count);
-  k_grp_blk<<<(unsigned)G.count, kThreads, 0, st>>>(G.probs);
+    k_grp_lines<<<(unsigned)G.nctas[kGkLines], kThreads, 0, st>>>(G.probs, G.tab[kGkLines]);
+  k_grp_blk<<<(unsigned)G.count, kThreads, 0, st>>>(G.probs, G.s);
   count_launches(4);
   return cudaGetLastError();
 }

@@ -160,9 +160,9 @@ struct TileView {
   // full B boxes (mbW: 3-D map at box index colW / 64); nullptr: per half / box
   const CUtensorMap* maW;
   const CUtensorMap* maW1;
-  const CUtensorMap* mbW;
+  const CUtensorMap* mbW;     // boxes [0, nW) in one copy; the rest per box
   const CUtensorMap* mbW1;
-  int32_t rowW, colW;
+  int32_t rowW, colW, nW;
   float* C;                   // data x data, ld ldc, m x n
   int64_t ldc, m, n;
   float* E16;                 // checksum rows x data columns, ld n, R16 rows
@@ -221,6 +221,7 @@ struct SingleSched {
       V.maW = T.kind == 1 ? &M->acs128[0] : &M->a128[0];
       V.maW1 = T.kind == 1 ? &M->acs128[1] : &M->a128[1];
     }
+    V.nW = 4;
     if (bcols == 4 && T.col0 + 256 <= ((T.kind == 2 ? g.C16 : g.n) / 64) * 64) {
       V.mbW = T.kind == 2 ? &M->bcs4[0] : &M->b4[0];
       V.mbW1 = T.kind == 2 ? &M->bcs4[1] : &M->b4[1];
@@ -350,16 +351,17 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
               tc::tma_load_2d(sa + h * (A_BYTES / 2), ma, full(s), kx, y);
             }
           }
+          int b_first = 0;
           if (T.mbW) {
             tc::tma_load_3d(sa + A_BYTES, seg == 1 ? T.mbW1 : T.mbW, full(s), 0, kx, T.colW / 64);
-          } else {
-            for (int b = 0; b < T.nbox; ++b) {
-              const bool dat = b < T.bsplit;
-              const CUtensorMap* mb =
-                  dat ? (seg == 1 ? T.mbD1 : T.mbD) : (seg == 1 ? T.mbC1 : T.mbC);
-              const int32_t x = dat ? T.colD + 64 * b : T.colC + 64 * (b - T.bsplit);
-              tc::tma_load_2d(sa + A_BYTES + b * B_BOX_BYTES, mb, full(s), x, kx);
-            }
+            b_first = T.nW;
+          }
+          for (int b = b_first; b < T.nbox; ++b) {
+            const bool dat = b < T.bsplit;
+            const CUtensorMap* mb =
+                dat ? (seg == 1 ? T.mbD1 : T.mbD) : (seg == 1 ? T.mbC1 : T.mbC);
+            const int32_t x = dat ? T.colD + 64 * b : T.colC + 64 * (b - T.bsplit);
+            tc::tma_load_2d(sa + A_BYTES + b * B_BOX_BYTES, mb, full(s), x, kx);
           }
           ++issued;
           if (++s == STAGES) { s = 0; ph ^= 1; }
@@ -593,12 +595,14 @@ struct GroupSched {
       V.maW = V.maW1 = &Mp.acs128;
       V.rowW = V.rowC;
     }
-    if (V.nbox == 4 && V.bsplit == 4 && b0 + 4 <= (int)(P.n / 64)) {
-      V.mbW = V.mbW1 = &Mp.b4;
+    if (V.bsplit >= 2 && b0 + V.bsplit <= (int)(P.n / 64)) {  // full data boxes
+      V.mbW = V.mbW1 = &Mp.bw[V.bsplit - 2];
       V.colW = V.colD;
+      V.nW = V.bsplit;
     } else if (V.nbox == 4 && V.bsplit == 0 && (b0 - nbd) + 4 <= (int)(P.C16 / 64)) {
       V.mbW = V.mbW1 = &Mp.bcs4;
       V.colW = V.colC;
+      V.nW = 4;
     }
     V.C = P.C;
     V.ldc = P.ldc;
@@ -666,8 +670,10 @@ bool make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols, int
 // 3-D bf16 view of a row-major rows x cols matrix as (64 columns, rows, column
 // box): element (x, y, z) is at ptr + y ld + 64 z + x.  Only the cols / 64 full
 // boxes are inside the view, so no copy reaches past a row or past the
-// matrix; the box is 64 x 64 x 4 (four B boxes of one stage), 128-byte swizzle.
-bool make_map_boxes(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols, int64_t ld) {
+// matrix; the box is 64 x 64 x depth (depth B boxes of one stage), 128-byte
+// swizzle.
+bool make_map_boxes(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols, int64_t ld,
+                    int depth = 4) {
   int64_t nb = cols / 64;
   if (rows == 0 || nb == 0) {  // never read: a dummy valid map
     rows = 1;
@@ -675,7 +681,7 @@ bool make_map_boxes(CUtensorMap* map, const void* ptr, int64_t rows, int64_t col
   }
   const cuuint64_t dims[3] = {64, (cuuint64_t)rows, (cuuint64_t)nb};
   const cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), 128};
-  const cuuint32_t box[3] = {64, 64, 4};
+  const cuuint32_t box[3] = {64, 64, (cuuint32_t)depth};
   const cuuint32_t estr[3] = {1, 1, 1};
   return g_encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -793,10 +799,10 @@ cudaError_t make_bf16_map(CUtensorMap* map, const void* ptr, int64_t rows, int64
 }
 
 cudaError_t make_bf16_map_boxes(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols,
-                                int64_t ld) {
+                                int64_t ld, int depth) {
   cudaError_t e = get_encoder();
   if (e != cudaSuccess) return e;
-  return make_map_boxes(map, ptr, rows, cols, ld) ? cudaSuccess : cudaErrorInvalidValue;
+  return make_map_boxes(map, ptr, rows, cols, ld, depth) ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_group_gemm(const GroupDev& G, bool checksums, cudaStream_t st) {

@@ -29,7 +29,8 @@ struct ProbShape {
   int64_t nvr, nvc, R16, C16, acs_ld, bcs_ld, nhc, nbc;
   // region offsets inside the workspace
   size_t acs, bcs, E16, F16, obs_col, obs_row, nArow, nAblk, nBcol, nBblk, rowpart, colpart,
-      partA, partB;
+      partA, partB, nArow32, nBcol32, tauA, tauB;
+  int64_t units[kGkCount];  // CTAs of each grouped kernel
 };
 
 }  // namespace
@@ -45,8 +46,9 @@ struct abft_group_s {
   abft_group_tuning tune{4, 1};
   // workspace layout
   size_t off_cnt = 0, off_colf = 0, off_rowf = 0, off_cand = 0, off_report = 0, off_inject = 0,
-         off_probs = 0, off_maps = 0, off_tiles_cs = 0, off_tiles_plain = 0, off_offs = 0,
+         off_probs = 0, off_maps = 0, off_tiles_cs = 0, off_tiles_plain = 0, off_tab = 0,
          total = 0;
+  int64_t ctas[kGkCount] = {};
   int64_t cap_tiles_cs = 0, cap_tiles_plain = 0;
   // bound state
   char* ws = nullptr;
@@ -87,7 +89,13 @@ abft_status upload_tables(abft_group_s& G, cudaStream_t st) {
   char* ws = G.ws;
   std::vector<GProb> probs(count);
   std::vector<GMaps> maps(count);
-  std::vector<int64_t> offs((size_t)kGkCount * (count + 1), 0);
+  std::vector<int2> tab;
+  int64_t ntab = 0;
+  for (int kk = 0; kk < kGkCount; ++kk) ntab += G.ctas[kk];
+  tab.reserve((size_t)ntab);
+  for (int kk = 0; kk < kGkCount; ++kk)
+    for (int p = 0; p < count; ++p)
+      for (int64_t u = 0; u < G.sh[p].units[kk]; ++u) tab.push_back(make_int2(p, (int)u));
   for (int p = 0; p < count; ++p) {
     const abft_problem& q = G.pr[p];
     const ProbShape& s = G.sh[p];
@@ -106,6 +114,10 @@ abft_status upload_tables(abft_group_s& G, cudaStream_t st) {
     P.nAblk = reinterpret_cast<double*>(ws + s.nAblk);
     P.nBcol = reinterpret_cast<double*>(ws + s.nBcol);
     P.nBblk = reinterpret_cast<double*>(ws + s.nBblk);
+    P.nArow32 = reinterpret_cast<float*>(ws + s.nArow32);
+    P.nBcol32 = reinterpret_cast<float*>(ws + s.nBcol32);
+    P.tauA = reinterpret_cast<float*>(ws + s.tauA);
+    P.tauB = reinterpret_cast<float*>(ws + s.tauB);
     P.rowpart = reinterpret_cast<float*>(ws + s.rowpart);
     P.colpart = reinterpret_cast<float*>(ws + s.colpart);
     P.partA = reinterpret_cast<double*>(ws + s.partA);
@@ -124,18 +136,12 @@ abft_status upload_tables(abft_group_s& G, cudaStream_t st) {
         (e = make_bf16_map(&Mp.bcs, P.bcs, q.k, s.C16, s.bcs_ld, 64, 64)) != cudaSuccess ||
         (e = make_bf16_map(&Mp.a128, q.A, q.m, q.k, q.lda, 64, 128)) != cudaSuccess ||
         (e = make_bf16_map(&Mp.acs128, P.acs, s.R16, q.k, s.acs_ld, 64, 128)) != cudaSuccess ||
-        (e = make_bf16_map_boxes(&Mp.b4, q.B, q.k, q.n, q.ldb)) != cudaSuccess ||
-        (e = make_bf16_map_boxes(&Mp.bcs4, P.bcs, q.k, s.C16, s.bcs_ld)) != cudaSuccess)
+        (e = make_bf16_map_boxes(&Mp.bw[0], q.B, q.k, q.n, q.ldb, 2)) != cudaSuccess ||
+        (e = make_bf16_map_boxes(&Mp.bw[1], q.B, q.k, q.n, q.ldb, 3)) != cudaSuccess ||
+        (e = make_bf16_map_boxes(&Mp.bw[2], q.B, q.k, q.n, q.ldb, 4)) != cudaSuccess ||
+        (e = make_bf16_map_boxes(&Mp.bcs4, P.bcs, q.k, s.C16, s.bcs_ld, 4)) != cudaSuccess)
       return fail(ABFT_ERR_INVALID, "problem %d: tensor map rejected (%s)", p,
                   cudaGetErrorString(e));
-    const int64_t n_units[kGkCount] = {
-        s.nvr * cdiv(q.k, 2048),                  // kGkEncA
-        cdiv(q.n, 2048) * cdiv(q.k, 128),         // kGkEncB
-        cdiv(q.m, 256) + cdiv(q.n, 256),          // kGkLines
-        s.nvr * cdiv(q.n, 256),                   // kGkColCheck
-        cdiv(q.m * s.nvc, 256)};                  // kGkRowCheck
-    for (int kk = 0; kk < kGkCount; ++kk)
-      offs[(size_t)kk * (count + 1) + p + 1] = offs[(size_t)kk * (count + 1) + p] + n_units[kk];
   }
   // product tile lists
   std::vector<int4> tcs, tpl;
@@ -165,8 +171,8 @@ abft_status upload_tables(abft_group_s& G, cudaStream_t st) {
   if (e == cudaSuccess && !tpl.empty())
     e = cudaMemcpyAsync(ws + G.off_tiles_plain, tpl.data(), sizeof(int4) * tpl.size(),
                         cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(ws + G.off_offs, offs.data(), sizeof(int64_t) * offs.size(),
+  if (e == cudaSuccess && !tab.empty())
+    e = cudaMemcpyAsync(ws + G.off_tab, tab.data(), sizeof(int2) * tab.size(),
                         cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "abft_group tables");
@@ -178,9 +184,11 @@ abft_status upload_tables(abft_group_s& G, cudaStream_t st) {
   D.ntiles_cs = (int64_t)tcs.size();
   D.tiles_plain = reinterpret_cast<const int4*>(ws + G.off_tiles_plain);
   D.ntiles_plain = (int64_t)tpl.size();
+  size_t t0 = 0;
   for (int kk = 0; kk < kGkCount; ++kk) {
-    D.off[kk] = reinterpret_cast<const int64_t*>(ws + G.off_offs) + (size_t)kk * (count + 1);
-    D.nctas[kk] = offs[(size_t)kk * (count + 1) + count];
+    D.tab[kk] = reinterpret_cast<const int2*>(ws + G.off_tab) + t0;
+    D.nctas[kk] = G.ctas[kk];
+    t0 += (size_t)G.ctas[kk];
   }
   D.s = G.s;
   D.cnt = reinterpret_cast<int32_t*>(ws + G.off_cnt);
@@ -308,12 +316,28 @@ abft_status abft_group_create(const abft_problem* problems, int32_t count, int32
     s.bcs_ld = (s.C16 + 7) / 8 * 8;
     s.nhc = cdiv(s.R16, 64);
     s.nbc = cdiv(s.C16, 64);
+    const int64_t units[kGkCount] = {
+        s.nvr * cdiv(s.acs_ld, 256),       // kGkEncA: verify block x 256 columns
+        cdiv(q.n, 256) * cdiv(q.k, 128),   // kGkEncB: 256 columns x 128 rows
+        cdiv(q.m, 256) + cdiv(q.n, 256),   // kGkLines: 256 rows, then 256 columns
+        s.nvr * cdiv(q.n, 256),            // kGkColCheck: verify block x 256 columns
+        cdiv(q.m * s.nvc, 256)};           // kGkRowCheck: 256 row lines
+    for (int kk = 0; kk < kGkCount; ++kk) {
+      s.units[kk] = units[kk];
+      G->ctas[kk] += units[kk];
+    }
     G->cap_tiles_cs += tiles_of(q, s, 2, true);     // the narrower tile gives the longer list
     G->cap_tiles_plain += tiles_of(q, s, 2, false);
   }
   G->off_tiles_cs = region(sizeof(int4) * G->cap_tiles_cs);
   G->off_tiles_plain = region(sizeof(int4) * G->cap_tiles_plain);
-  G->off_offs = region(sizeof(int64_t) * kGkCount * (count + 1));
+  int64_t ntab = 0;
+  for (int kk = 0; kk < kGkCount; ++kk) ntab += G->ctas[kk];
+  if (ntab >= (1ll << 31)) {
+    delete G;
+    return fail(ABFT_ERR_INVALID, "group too large for one launch per kernel");
+  }
+  G->off_tab = region(sizeof(int2) * ntab);
   for (int p = 0; p < count; ++p) {
     const abft_problem& q = problems[p];
     ProbShape& s = G->sh[p];
@@ -329,8 +353,12 @@ abft_status abft_group_create(const abft_problem* problems, int32_t count, int32
     s.nBblk = region((size_t)4 * s.nvc * 8);
     s.rowpart = region((size_t)q.m * cdiv(q.k, 256) * 4);
     s.colpart = region((size_t)cdiv(q.k, 128) * q.n * 4);
-    s.partA = region((size_t)2 * s.nvr * cdiv(q.k, 2048) * 8);
+    s.partA = region((size_t)2 * s.nvr * cdiv(q.k, 256) * 8);
     s.partB = region((size_t)2 * s.nvc * cdiv(q.k, 128) * 8);
+    s.nArow32 = region((size_t)q.m * 4);
+    s.nBcol32 = region((size_t)q.n * 4);
+    s.tauA = region((size_t)2 * s.nvr * 4);
+    s.tauB = region((size_t)2 * s.nvc * 4);
   }
   G->total = off;
   *out = G;

@@ -145,9 +145,13 @@ struct GProb {  // one problem of a group, in device memory
   double* nAblk;   // 4 nvr: threshold norms of each verify row block
   double* nBcol;   // n: ||B_:j||
   double* nBblk;   // 4 nvc
+  float* nArow32;  // m: ||A_i|| rounded to fp32 (screening)
+  float* nBcol32;  // n
+  float* tauA;     // 2 nvr: s (f1c ||A_I||_F + f2 ||e^T A_I||), the same with w (fp32)
+  float* tauB;     // 2 nvc: s (f1r ||B_J||_F + f2 ||B_J e||), the same with w
   float* rowpart;  // m x ceil(k/256) squared-norm partials
   float* colpart;  // ceil(k/128) x n
-  double* partA;   // 2 nvr x ceil(k/2048)
+  double* partA;   // 2 nvr x ceil(k/256)
   double* partB;   // 2 nvc x ceil(k/128)
   int64_t nvr, nvc, ngrp;
   double f1c, f1r, f2;  // threshold factors (the safety factor applies at use)
@@ -158,13 +162,15 @@ struct GProb {  // one problem of a group, in device memory
 struct GMaps {  // tensor maps of one problem (64-byte aligned in device memory)
   CUtensorMap a, acs, b, bcs;   // 64-row halves / one 64-column box
   CUtensorMap a128, acs128;     // 128-row boxes (a whole tile's A)
-  CUtensorMap b4, bcs4;         // four full 64-column boxes in one copy (3-D view)
+  CUtensorMap bw[3];            // 2, 3, 4 full 64-column boxes of B in one copy (3-D view)
+  CUtensorMap bcs4;             // four full checksum boxes in one copy
 };
 
-// CTA offsets of the grouped kernels: off[p] .. off[p+1] are problem p's CTAs.
+// The grouped kernels: CTA b of kernel kk works on problem tab[kk][b].x, its
+// local unit tab[kk][b].y.
 enum GroupKernel : int {
-  kGkEncA = 0,   // A column checksums: nvr x ceil(k/2048)
-  kGkEncB,       // B row checksums: ceil(n/2048) x ceil(k/128)
+  kGkEncA = 0,   // A column checksums: nvr x ceil(acs_ld/256)
+  kGkEncB,       // B row checksums: ceil(n/256) x ceil(k/128)
   kGkLines,      // line norms: ceil(m/256) + ceil(n/256)
   kGkColCheck,   // column lines: nvr x ceil(n/256)
   kGkRowCheck,   // row lines: ceil(m nvc / 256)
@@ -179,7 +185,7 @@ struct GroupDev {  // device view of a bound group (every pointer in the workspa
   int64_t ntiles_cs;
   const int4* tiles_plain;  // product tiles without checksums
   int64_t ntiles_plain;
-  const int64_t* off[kGkCount];
+  const int2* tab[kGkCount];
   int64_t nctas[kGkCount];
   double s;                 // threshold safety factor
   int32_t* cnt;             // verify counters
@@ -191,23 +197,12 @@ struct GroupDev {  // device view of a bound group (every pointer in the workspa
   InjectEntry* inj;
 };
 
-// Problem owning CTA b of a grouped kernel: the last p with off[p] <= b
-// (problems without CTAs have off[p] == off[p+1] and are skipped).
-__device__ __forceinline__ int find_prob(const int64_t* off, int count, int64_t b) {
-  int lo = 0, hi = count - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (off[mid] <= b) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
 cudaError_t make_bf16_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols,
                           int64_t ld, uint32_t box_cols, uint32_t box_rows);
-// The 3-D four-box view of a row-major rows x cols bf16 matrix (full 64-column
-// boxes only).
+// The 3-D view of a row-major rows x cols bf16 matrix as (64 columns, rows,
+// full 64-column box) with a box of `depth` 64 x 64 boxes.
 cudaError_t make_bf16_map_boxes(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols,
-                                int64_t ld);
+                                int64_t ld, int depth);
 cudaError_t launch_group_encode(const GroupDev& G, cudaStream_t st);
 cudaError_t launch_group_gemm(const GroupDev& G, bool checksums, cudaStream_t st);
 cudaError_t launch_group_verify(const GroupDev& G, cudaStream_t st);

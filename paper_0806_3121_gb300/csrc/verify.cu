@@ -626,19 +626,39 @@ struct GroupPol {
   __device__ __forceinline__ int32_t kc(uint64_t k) const { return (int32_t)((k >> 1) & 0xFFFFFu); }
 };
 
+// The verify screen.  A line passes when, evaluated in fp32, both residuals
+// are within 0.9 of their thresholds; any other line is evaluated in binary64
+// and flagged by the binary64 rule.  The fp32 evaluation differs from the
+// binary64 one by at most u32 (|expected| + |r|) plus a few u32 of the
+// threshold, and |expected| <= ||checksum row|| ||B_:j|| <= tau / (s f2) with
+// s f2 >= 4 * 2^-17, so u32 |expected| <= 2^-9 tau: a line the screen passes
+// is never one the binary64 rule flags (and non-finite sums never pass).
+__device__ __forceinline__ bool screen_pass(float se, float sw, float ee, float ew, float te,
+                                            float tw) {
+  const float re = se - ee, rw = sw - ew;
+  return fabsf(re) <= 0.9f * te && fabsf(rw) <= 0.9f * tw;  // false for NaN
+}
+
 // Column lines (problem, verify block I, column j) from the observed column
 // sums of the product's epilogue (verify block = tile row).  CTA = 256
 // columns of one verify block.
 __global__ void __launch_bounds__(kThreads) k_grp_col(const GProb* __restrict__ probs,
-                                                      const int64_t* __restrict__ off, int count,
-                                                      double s, int32_t* cnt, FlagEntry* colf) {
-  const int p = find_prob(off, count, blockIdx.x);
+                                                      const int2* __restrict__ tab, double s,
+                                                      int32_t* cnt, FlagEntry* colf) {
+  const int2 e = tab[blockIdx.x];
+  const int p = e.x;
   const GProb& P = probs[p];
-  const int64_t u = blockIdx.x - off[p], ncx = cdiv(P.n, kThreads);
-  const int64_t I = u / ncx, j = (u % ncx) * kThreads + threadIdx.x;
+  const int64_t ncx = cdiv(P.n, kThreads);
+  const int64_t I = e.y / ncx, j = (e.y % ncx) * kThreads + threadIdx.x;
   if (j >= P.n) return;
-  const double se = (double)P.obs_col[(I * 2 + 0) * P.n + j];
-  const double sw = (double)P.obs_col[(I * 2 + 1) * P.n + j];
+  const float se32 = P.obs_col[(I * 2 + 0) * P.n + j];
+  const float sw32 = P.obs_col[(I * 2 + 1) * P.n + j];
+  const float* E = P.E16 + 4 * I * P.n + j;
+  const float nb = P.nBcol32[j];
+  if (screen_pass(se32, sw32, E[0] + E[P.n], E[2 * P.n] + E[3 * P.n], nb * P.tauA[2 * I],
+                  nb * P.tauA[2 * I + 1]))
+    return;
+  const double se = (double)se32, sw = (double)sw32;
   const int nf = (isfinite(se) && isfinite(sw)) ? 0 : 1;
   const double re = se - grp_expect_col(P, I, j, 0), rw = sw - grp_expect_col(P, I, j, 1);
   double te, tw;
@@ -651,16 +671,27 @@ __global__ void __launch_bounds__(kThreads) k_grp_col(const GProb* __restrict__ 
 // Row lines (problem, row i, verify block J) from the observed row sums over
 // column groups.  One thread per line.
 __global__ void __launch_bounds__(kThreads) k_grp_row(const GProb* __restrict__ probs,
-                                                      const int64_t* __restrict__ off, int count,
-                                                      double s, int32_t* cnt, FlagEntry* rowf) {
-  const int p = find_prob(off, count, blockIdx.x);
+                                                      const int2* __restrict__ tab, double s,
+                                                      int32_t* cnt, FlagEntry* rowf) {
+  const int2 e = tab[blockIdx.x];
+  const int p = e.x;
   const GProb& P = probs[p];
-  const int64_t t = (blockIdx.x - off[p]) * kThreads + threadIdx.x;
+  const int64_t t = (int64_t)e.y * kThreads + threadIdx.x;
   const int64_t i = t / P.nvc, J = t % P.nvc;
   if (i >= P.m) return;
   const int64_t j0 = J * kGrpVbC, j1 = min(j0 + (int64_t)kGrpVbC, P.n);
+  const int64_t g0 = j0 / P.g, g1 = min(cdiv(j1, P.g), P.ngrp);
+  float se32 = 0.f, sw32 = 0.f;
+  for (int64_t gr = g0; gr < g1; ++gr) {
+    se32 += P.obs_row[(i * P.ngrp + gr) * 2 + 0];
+    sw32 += P.obs_row[(i * P.ngrp + gr) * 2 + 1];
+  }
+  const float* F = P.F16 + i * P.C16 + 4 * J;
+  const float na = P.nArow32[i];
+  if (screen_pass(se32, sw32, F[0] + F[1], F[2] + F[3], na * P.tauB[2 * J], na * P.tauB[2 * J + 1]))
+    return;
   double se = 0.0, sw = 0.0;
-  for (int64_t gr = j0 / P.g; gr < min(cdiv(j1, P.g), P.ngrp); ++gr) {
+  for (int64_t gr = g0; gr < g1; ++gr) {
     se += (double)P.obs_row[(i * P.ngrp + gr) * 2 + 0];
     sw += (double)P.obs_row[(i * P.ngrp + gr) * 2 + 1];
   }
@@ -867,10 +898,10 @@ cudaError_t launch_group_verify(const GroupDev& G, cudaStream_t st) {
   if (e != cudaSuccess || G.count == 0) return e;
   if (G.nctas[kGkColCheck] > 0)
     k_grp_col<<<(unsigned)G.nctas[kGkColCheck], kThreads, 0, st>>>(
-        G.probs, G.off[kGkColCheck], G.count, G.s, G.cnt, G.colf);
+        G.probs, G.tab[kGkColCheck], G.s, G.cnt, G.colf);
   if (G.nctas[kGkRowCheck] > 0)
     k_grp_row<<<(unsigned)G.nctas[kGkRowCheck], kThreads, 0, st>>>(
-        G.probs, G.off[kGkRowCheck], G.count, G.s, G.cnt, G.rowf);
+        G.probs, G.tab[kGkRowCheck], G.s, G.cnt, G.rowf);
   k_grp_locate<<<1, kLocThreads, 0, st>>>(G.probs, G.s, G.cnt, G.colf, G.rowf, G.cand, G.report);
   count_launches(3);
   return cudaGetLastError();

@@ -266,11 +266,39 @@ def make_inputs(w, seed, dev):
         A_np, B_np = wl.operands(w, seed)
         return torch.from_numpy(A_np).to(dev), torch.from_numpy(B_np).to(dev), A_np, B_np
     g = torch.Generator(device=dev).manual_seed(seed)
+    if w.dtype == "fp8":
+        return fp8_inputs(w, g, dev) + (None, None)
     A = torch.randn(w.m, w.k, generator=g, device=dev)
     B = torch.randn(w.k, w.n, generator=g, device=dev)
     if w.dtype == "bf16":
         A, B = A.to(torch.bfloat16), B.to(torch.bfloat16)
     return A, B, None, None
+
+
+def fp8_quantize_dev(x, blk=128):
+    """The FP8 recipe on the device (input preparation): one power-of-two scale per
+    blk x blk block, 2^ceil(log2(max|x| / 448)), codes rounded to nearest-even E4M3."""
+    import torch
+    r, c = x.shape
+    amax = x.abs().reshape(r // blk, blk, c // blk, blk).amax(dim=(1, 3))
+    e = torch.where(amax > 0, torch.ceil(torch.log2(amax / 448.0)), torch.zeros_like(amax))
+    s = torch.exp2(e).float()
+    full = s.repeat_interleave(blk, 0).repeat_interleave(blk, 1)
+    q = (x / full).to(torch.float8_e4m3fn).view(torch.uint8)
+    return q.contiguous(), s.contiguous()
+
+
+def fp8_inputs(w, g, dev):
+    """(A codes, B codes, A scales, B scales): U[-1,1] x 10^U(-2,2) per row, quantised."""
+    import torch
+    out = []
+    for rows, cols in ((w.m, w.k), (w.k, w.n)):
+        x = torch.rand(rows, cols, generator=g, device=dev) * 2 - 1
+        x *= 10.0 ** (torch.rand(rows, 1, generator=g, device=dev) * 4 - 2)
+        out.append(fp8_quantize_dev(x))
+        del x
+    (qa, sa), (qb, sb) = out
+    return qa, qb, sa, sb
 
 
 def run_workload(w, args, dev, rank, world, secondary=False):
@@ -279,7 +307,14 @@ def run_workload(w, args, dev, rank, world, secondary=False):
     from paper_0806_3121_gb300 import abft
 
     seed = args.seed + rank
-    A, B, A_np, B_np = make_inputs(w, seed, dev)
+    scales = {}
+    if w.dtype == "fp8":
+        import torch as _t
+        A, B, sa, sb = fp8_inputs(w, _t.Generator(device=dev).manual_seed(seed), dev)
+        A_np = B_np = None
+        scales = dict(a_scale=sa, b_scale=sb)
+    else:
+        A, B, A_np, B_np = make_inputs(w, seed, dev)
     lp = w.dtype != "f64"
     desc = abft.make_desc(w.m, w.n, w.k, w.dtype, w.vb_r, w.vb_c, w.p, w.q)
     L = abft.abft_workspace_layout(desc)
@@ -292,7 +327,7 @@ def run_workload(w, args, dev, rank, world, secondary=False):
         erased = wl.erased_blocks(seed, w.p, w.q, w.n_erased)
     pos = wl.bit_flips(seed, w.m, w.n, w.n_flips, distinct_blocks=(bs, bs), avoid_blocks=erased)
     # graded flips by construction: exponent bits that move the value by many orders
-    abft.abft_encode(desc, A, B, ws, stream=stream)
+    abft.abft_encode(desc, A, B, ws, stream=stream, **scales)
     abft.abft_gemm(desc, A, B, C, ws, stream=stream)
     torch.cuda.synchronize()
     flips = []
@@ -313,7 +348,7 @@ def run_workload(w, args, dev, rank, world, secondary=False):
     gemm_ms = []
 
     def step(timed_gemm=False):
-        abft.abft_encode(desc, A, B, ws, stream=stream)
+        abft.abft_encode(desc, A, B, ws, stream=stream, **scales)
         if timed_gemm:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -375,7 +410,7 @@ def run_workload(w, args, dev, rank, world, secondary=False):
         t_abft.append(timed(lambda: abft.abft_gemm(desc, A, B, C, ws, stream=stream), 1))
     plain_ms = statistics.median(t_plain)
     abft_pair_ms = statistics.median(t_abft)
-    encode_ms = timed(lambda: abft.abft_encode(desc, A, B, ws, stream=stream), 5)
+    encode_ms = timed(lambda: abft.abft_encode(desc, A, B, ws, stream=stream, **scales), 5)
     gemm_avg = sum(gemm_ms) / len(gemm_ms)
 
     e2e = None
@@ -427,8 +462,11 @@ def run_workload(w, args, dev, rank, world, secondary=False):
                  "traffic": TRAFFIC_BYTES.get(w.dtype), "algorithmic_flops_per_launch": kernel_flops})
     value = useful * world / (step_ms * 1e-3) / 1e12
     cfg = {"workload": w.name, "m": w.m, "n": w.n, "k": w.k, "verify_block": [w.vb_r, w.vb_c],
-           "dist": "N(0,1)" + {"bf16": " rounded to bf16", "bf16x3": " in fp32, split into "
-                                "bf16 hi+lo"}.get(w.dtype, ""),
+           "dist": {"fp8": "U[-1,1] x 10^U(-2,2) per row, e4m3 with power-of-two binary32 "
+                           "scales per 128x128 block (product of the exact dequantised values "
+                           "on the bf16 tensor path)"}.get(
+                w.dtype, "N(0,1)" + {"bf16": " rounded to bf16", "bf16x3": " in fp32, split "
+                                     "into bf16 hi+lo"}.get(w.dtype, "")),
            "faults_per_step": (f"{w.n_erased} erased block + " if w.n_erased else "") +
                               f"{w.n_flips} exponent bit-flips in distinct blocks" +
                               (" of the accumulator outputs (epilogue), verified from the "
@@ -619,7 +657,7 @@ def run_ours(args, rank, world):
             "roofline", "gpu_launches", "clocks", "config")
     if w.name == "f64_11264_grid22" and not args.no_secondary:
         # the tensor-core workloads first: the FP64 run is a minute of full-power load
-        for name in ("bf16_16384", "bf16x3_16384"):
+        for name in ("bf16_16384", "bf16x3_16384", "fp8_16384"):
             sec = run_workload(wl.WORKLOADS[name], args, dev, rank, world, secondary=True)
             secondary[name] = {k: sec[k] for k in keys}
         sec = run_grouped(wl.BF16_GROUPED_4096, args, dev, rank, world, secondary=True)

@@ -130,7 +130,12 @@ abft_status abft_workspace_layout(const abft_desc* desc, abft_ws_layout* out);
  * erasure grid is on) and the checksum columns of B (B_J e, B_J w), plus the
  * norms the detection thresholds use.  a_scale/b_scale: binary32 block scales
  * for ABFT_FP8_E4M3 (ceil(m/128) x ceil(k/128) and ceil(k/128) x ceil(n/128),
- * row-major), else NULL.  Asynchronous. */
+ * row-major), else NULL.  ABFT_FP8_E4M3: A and B are e4m3 bytes (lda, ldb in
+ * elements); the scales must be powers of two, so that every dequantised value
+ * e4m3(q) * scale is exact in bf16 -- the encode writes those values as bf16
+ * operand planes into ws, forms the checksums from them and the product reads
+ * them (a value that is not exact makes the next abft_verify_correct return
+ * ABFT_ERR_INVALID).  Asynchronous. */
 abft_status abft_encode(const abft_desc* desc, const void* A, const void* B, const void* a_scale,
                         const void* b_scale, void* ws, void* stream);
 
@@ -156,7 +161,9 @@ abft_status abft_encode_noalloc(const abft_desc* desc, const void* A, const void
 
 /* The ABFT product (Eq. (1)): [A; C_C^T A] [B, B C_R] on the GPU.  Writes the
  * data block A B into C and the checksum blocks into ws (E and F).  Requires a
- * preceding abft_encode on the same ws and operands.  Asynchronous. */
+ * preceding abft_encode on the same ws and operands.  ABFT_BF16X3 and
+ * ABFT_FP8_E4M3 multiply the bf16 operand planes that encode wrote (A, B and the
+ * scales are not read again).  Asynchronous. */
 abft_status abft_gemm(const abft_desc* desc, const void* A, const void* B, const void* a_scale,
                       const void* b_scale, void* C, void* ws, void* stream);
 
@@ -174,8 +181,8 @@ abft_status abft_set_epilogue_faults(const abft_desc* desc, void* ws, const int6
 
 /* The same GEMM kernel with no checksum tiles: C = A B only.  This is the
  * checksum-free baseline the ABFT overhead is measured against.  ws may be
- * NULL except for ABFT_BF16X3, whose product reads the bf16 planes a
- * preceding abft_encode wrote into ws.  Asynchronous. */
+ * NULL except for ABFT_BF16X3 and ABFT_FP8_E4M3, whose products read the bf16
+ * operand planes a preceding abft_encode wrote into ws.  Asynchronous. */
 abft_status abft_gemm_plain(const abft_desc* desc, const void* A, const void* B,
                             const void* a_scale, const void* b_scale, void* C, void* ws,
                             void* stream);

@@ -438,8 +438,11 @@ static void push_report(oracle_fault* rep, int32_t max_rep, int32_t* n, int32_t 
  *     a flagged line holding no candidate is reported uncorrectable;
  *  5. each candidate is corrected by recomputation from a line in which it
  *     is the only candidate -- C_ij = E - sum of the other elements of its
- *     column line, else F - sum of the other elements of its row line --
- *     otherwise it is reported uncorrectable and left untouched;
+ *     column line, or F - sum of the other elements of its row line; when it
+ *     is alone in both, the line with the smaller unweighted threshold (the
+ *     more accurate recomputation for lines of very different magnitude),
+ *     the column line on a tie -- otherwise it is reported uncorrectable and
+ *     left untouched;
  *  6. the column line and the row line of every corrected element are
  *     checked again; a line still flagged is reported uncorrectable (this
  *     catches several errors sharing lines, which the ratio cannot separate);
@@ -586,6 +589,9 @@ int oracle_verify_correct(const oracle_cfg* c, double* C, int64_t ldc, const dou
       if (cand[u].row == cand[t].row && cand[u].col / c->vb_c == J) ++nrow;
     }
     how[t] = ncol == 1 ? 0 : (nrow == 1 ? 1 : -1);
+    /* alone in both lines: recompute from the line whose unweighted threshold
+     * (the scale of its rounding errors) is smaller; ties take the column */
+    if (ncol == 1 && nrow == 1 && rte[cand[t].row * nvc + J] < cte[I * n + cand[t].col]) how[t] = 1;
   }
   for (size_t t = 0; t < nc; ++t) {
     int64_t i = cand[t].row, j = cand[t].col;

@@ -69,7 +69,7 @@ void threshold_factors(int dtype, int64_t k, int64_t vb_r, int64_t vb_c, double*
 
 namespace {
 
-size_t operand_bytes(int dtype) { return dtype == ABFT_F64 ? 8 : 2; }
+size_t operand_bytes(int dtype) { return dtype == ABFT_F64 ? 8 : 2; }  // of acs / bcs
 
 abft_status make_plan(const abft_desc* d, Plan* P) {
   if (!d) return fail(ABFT_ERR_INVALID, "desc is NULL");
@@ -92,8 +92,7 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
   if (d->flags != 0) return fail(ABFT_ERR_INVALID, "flags must be 0");
   if (!(d->tau_safety >= 0.0) || !isfinite(d->tau_safety))
     return fail(ABFT_ERR_INVALID, "tau_safety must be finite and >= 0");
-  if (d->dtype != ABFT_F64 && d->dtype != ABFT_BF16 && d->dtype != ABFT_BF16X3)
-    return fail(ABFT_ERR_UNSUPPORTED, "dtype %d not built yet", d->dtype);
+
   if (d->dtype == ABFT_BF16 && (d->lda % 8 || d->ldb % 8))  // TMA rows of A and B
     return fail(ABFT_ERR_INVALID, "bf16 operands need lda and ldb multiples of 8 (16-byte rows)");
 
@@ -123,6 +122,8 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
   const size_t eb = operand_bytes(d->dtype);
   const bool lp = d->dtype != ABFT_F64;
   const bool x3 = d->dtype == ABFT_BF16X3;
+  const bool f8 = d->dtype == ABFT_FP8_E4M3;
+  const int op_planes = x3 ? 2 : (f8 ? 1 : 0);  // bf16 operand planes the encode writes
   // Encoded operand rows/columns: binary64 checksums for F64.  bf16: each fp32
   // checksum is a bf16 hi+lo pair, as separate rows (4 rows per verify block, 2
   // per block-checksum row).  BF16X3: hi and lo planes of 2 rows per block
@@ -153,10 +154,10 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
   L.obs_col = region(p.fused ? (size_t)p.ntr_obs * 2 * d->n * 4 : 0);
   L.obs_row = region(p.fused ? (size_t)d->m * p.ngrp * 2 * 4 : 0);
   L.inject = region(lp ? 16 + sizeof(InjectEntry) * kMaxInject : 0);
-  L.op_a_ld = x3 ? (d->k + 7) / 8 * 8 : 0;
-  L.op_b_ld = x3 ? (d->n + 7) / 8 * 8 : 0;
-  L.op_a = region(x3 ? 2 * align256((size_t)d->m * L.op_a_ld * 2) : 0);
-  L.op_b = region(x3 ? 2 * align256((size_t)d->k * L.op_b_ld * 2) : 0);
+  L.op_a_ld = op_planes ? (d->k + 7) / 8 * 8 : 0;
+  L.op_b_ld = op_planes ? (d->n + 7) / 8 * 8 : 0;
+  L.op_a = region(op_planes * align256((size_t)d->m * L.op_a_ld * 2));
+  L.op_b = region(op_planes * align256((size_t)d->k * L.op_b_ld * 2));
   L.fused = p.fused;
   L.scratch = off;
   L.scratch_bytes = scratch_bytes(p);
@@ -240,18 +241,18 @@ abft_status abft_workspace_layout(const abft_desc* desc, abft_ws_layout* out) {
 
 abft_status abft_encode(const abft_desc* desc, const void* A, const void* B, const void* a_scale,
                         const void* b_scale, void* ws, void* stream) {
-  (void)a_scale;
-  (void)b_scale;
   Plan P;
   abft_status st = make_plan(desc, &P);
   if (st != ABFT_OK) return st;
   if (is_empty(P)) return ABFT_OK;
   if (!ws || (P.d.k > 0 && (!A || !B))) return fail(ABFT_ERR_INVALID, "NULL pointer");
+  if (P.d.dtype == ABFT_FP8_E4M3 && P.d.k > 0 && (!a_scale || !b_scale))
+    return fail(ABFT_ERR_INVALID, "ABFT_FP8_E4M3 needs a_scale and b_scale");
   const cudaError_t e =
       P.d.dtype == ABFT_F64
           ? launch_encode_f64(P, static_cast<const double*>(A), static_cast<const double*>(B), ws,
                               static_cast<cudaStream_t>(stream))
-          : launch_encode_lp(P, A, B, ws, static_cast<cudaStream_t>(stream));
+          : launch_encode_lp(P, A, B, a_scale, b_scale, ws, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? ABFT_OK : cuda_fail(e, "abft_encode");
 }
 
@@ -284,7 +285,8 @@ static abft_status gemm_common(const abft_desc* desc, const void* A, const void*
   abft_status st = make_plan(desc, &P);
   if (st != ABFT_OK) return st;
   if (is_empty(P)) return ABFT_OK;
-  if (!C || ((checksums || P.d.dtype == ABFT_BF16X3) && !ws) || (P.d.k > 0 && (!A || !B)))
+  if (!C || ((checksums || P.d.dtype == ABFT_BF16X3 || P.d.dtype == ABFT_FP8_E4M3) && !ws) ||
+      (P.d.k > 0 && (!A || !B)))
     return fail(ABFT_ERR_INVALID, "NULL pointer");
   cudaError_t e;
   if (P.d.dtype == ABFT_F64) {
@@ -371,6 +373,15 @@ abft_status abft_verify_correct(const abft_desc* desc, void* C, void* ws, int32_
     if (e != cudaSuccess) return cuda_fail(e, "abft_verify_correct");
     if (timed_out)
       return fail(ABFT_ERR_TIMEOUT, "a tensor-core product gave up waiting (bounded wait)");
+  }
+  if (P.d.dtype == ABFT_FP8_E4M3) {
+    bool inexact = false;
+    e = consume_fp8_inexact(s, &inexact);
+    if (e != cudaSuccess) return cuda_fail(e, "abft_verify_correct");
+    if (inexact)
+      return fail(ABFT_ERR_INVALID,
+                  "an e4m3 value times its block scale is not exact in bf16: the block scales "
+                  "must be powers of two (and the operands finite)");
   }
   const int total = cnt[kCntReport];
   const int stored = std::min(total, kCapReport);

@@ -12,6 +12,7 @@
 // two rows (hi, lo) per block checksum row.  bcs is row-major k x (4 nvc)
 // with the same piece order per verify column block.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "internal.cuh"
 
@@ -74,25 +75,8 @@ __device__ __forceinline__ void split(float x, __nv_bfloat16& hi, __nv_bfloat16&
 
 __device__ __forceinline__ float ldf(const __nv_bfloat16* p) { return __bfloat162float(*p); }
 
-// Eight consecutive elements starting at column c of a row (zeros past `len`).
-__device__ __forceinline__ void load8(const __nv_bfloat16* row, int64_t c, int64_t len,
-                                      float (&v)[8]) {
-  if (c + 8 <= len && ((reinterpret_cast<uintptr_t>(row + c) & 15) == 0)) {
-    const uint4 u = *reinterpret_cast<const uint4*>(row + c);
-    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float2 f = __bfloat1622float2(h[q]);
-      v[2 * q] = f.x;
-      v[2 * q + 1] = f.y;
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = (c + q < len) ? ldf(row + c + q) : 0.f;
-  }
-}
-
-// The same eight elements as raw bf16 bits (zeros past `len`), unpacked later:
+// Eight consecutive elements starting at column c of a row as raw bf16 bits
+// (zeros past `len`), unpacked later:
 // a row batch in flight costs 4 registers per row instead of 8.
 __device__ __forceinline__ uint4 load8raw(const __nv_bfloat16* row, int64_t c, int64_t len) {
   if (c + 8 <= len && ((reinterpret_cast<uintptr_t>(row + c) & 15) == 0))
@@ -684,6 +668,42 @@ __global__ void k_fold_F(const float* __restrict__ F16, int64_t m, int64_t Cc, i
   F[i * Cc + c] = v;
 }
 
+// ---------------- FP8 E4M3 with binary32 block scales
+
+// Dequantised operand plane: out[i][j] = e4m3(q[i][j]) * scale[i/128][j/128]
+// as bf16, which is exact when the scales are powers of two (an e4m3 value has
+// at most 4 significant bits).  A value that bf16 cannot hold exactly sets
+// *inexact (the call then reports ABFT_ERR_INVALID); columns cols .. ld-1 of
+// the plane are zero.  Thread = 8 consecutive elements of a row.
+__global__ void __launch_bounds__(kThreads) k_fp8_dequant(const uint8_t* __restrict__ q, int64_t ldq,
+                                                          int64_t rows, int64_t cols,
+                                                          const float* __restrict__ scale,
+                                                          __nv_bfloat16* __restrict__ out,
+                                                          int64_t ld, int* inexact) {
+  const int64_t c0 = 8 * ((int64_t)blockIdx.x * kThreads + threadIdx.x);
+  if (c0 >= ld) return;
+  const int64_t sld = cdiv(cols, 128);
+  for (int64_t i = blockIdx.y; i < rows; i += gridDim.y) {
+    const uint8_t* row = q + i * ldq;
+    const float* srow = scale + (i / 128) * sld;
+    __nv_bfloat16 o[8];
+    bool bad = false;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int64_t c = c0 + t;
+      float v = 0.f;
+      if (c < cols) {
+        const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)row[c], __NV_E4M3);
+        v = __half2float(__half(h)) * srow[c / 128];
+      }
+      o[t] = __float2bfloat16_rn(v);
+      bad |= !(__bfloat162float(o[t]) == v);  // also catches NaN
+    }
+    store8(out + i * ld + c0, o);
+    if (bad) atomicExch(inexact, 1);
+  }
+}
+
 unsigned gy(int64_t v) { return (unsigned)(v < 65535 ? v : 65535); }
 
 // bf16 elements in a 256-byte aligned plane of `elems` elements.
@@ -700,11 +720,26 @@ size_t lp_part_bytes(const Plan& P) {
          sizeof(float) * (P.d.m * cdiv(k, 256) + cdiv(k, kRowsPerCtaB) * P.d.n) + 64;
 }
 
-cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, void* ws,
-                             cudaStream_t st) {
+// Device flag of the FP8 dequantisation (an operand value not exact in bf16).
+__device__ int g_fp8_inexact = 0;
+
+cudaError_t consume_fp8_inexact(cudaStream_t st, bool* inexact) {
+  int* flag = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&flag), g_fp8_inexact);
+  int v = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&v, flag, sizeof v, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && v) e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+  *inexact = v != 0;
+  return e;
+}
+
+cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, const void* a_scale,
+                             const void* b_scale, void* ws, cudaStream_t st) {
   const abft_desc& d = P.d;
   const auto* A = static_cast<const __nv_bfloat16*>(Av);
   const auto* B = static_cast<const __nv_bfloat16*>(Bv);
+  int64_t lda = d.lda, ldb = d.ldb;
   char* w = static_cast<char*>(ws);
   auto* acs = reinterpret_cast<__nv_bfloat16*>(w + P.L.acs);
   auto* bcs = reinterpret_cast<__nv_bfloat16*>(w + P.L.bcs);
@@ -769,22 +804,42 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, void
     count_launches(6 + (P.bs > 0 ? 1 : 0) + (fastB ? 0 : 1));
     return cudaGetLastError();
   }
+  if (d.dtype == ABFT_FP8_E4M3) {
+    // dequantise into the bf16 operand planes; the checksums and the product
+    // then work on those exact values
+    int* flag = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&flag), g_fp8_inexact);
+    if (e != cudaSuccess) return e;
+    auto* pa = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_a);
+    auto* pb = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_b);
+    k_fp8_dequant<<<dim3((unsigned)cdiv(P.L.op_a_ld, 8 * kThreads), gy(d.m)), kThreads, 0, st>>>(
+        static_cast<const uint8_t*>(Av), d.lda, d.m, d.k, static_cast<const float*>(a_scale), pa,
+        P.L.op_a_ld, flag);
+    k_fp8_dequant<<<dim3((unsigned)cdiv(P.L.op_b_ld, 8 * kThreads), gy(d.k)), kThreads, 0, st>>>(
+        static_cast<const uint8_t*>(Bv), d.ldb, d.k, d.n, static_cast<const float*>(b_scale), pb,
+        P.L.op_b_ld, flag);
+    count_launches(2);
+    A = pa;
+    B = pb;
+    lda = P.L.op_a_ld;
+    ldb = P.L.op_b_ld;
+  }
   k_lpA_cols<<<dim3((unsigned)cdiv(P.L.acs_ld, kEncCols), gy(P.nvr)), kThreads, 0, st>>>(
-      A, d.lda, d.m, d.k, d.vb_rows, P.er, acs, P.L.acs_ld, rowpart, nchr, partA);
+      A, lda, d.m, d.k, d.vb_rows, P.er, acs, P.L.acs_ld, rowpart, nchr, partA);
   if (P.bs > 0)
     k_lpA_block<<<dim3((unsigned)cdiv(d.k, kThreads), gy(P.bs)), kThreads, 0, st>>>(
-        A, d.lda, d.k, d.grid_p, P.bs, acs + 4 * P.nvr * P.L.acs_ld, P.L.acs_ld);
+        A, lda, d.k, d.grid_p, P.bs, acs + 4 * P.nvr * P.L.acs_ld, P.L.acs_ld);
   k_lp_norms<<<(unsigned)cdiv(d.m, 128), 128, 0, st>>>(rowpart, d.m, nchr, nchr, 1, nArow);
   k_lp_blk<<<(unsigned)cdiv(P.nvr, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA, nchr,
                                                        nAblk);
   if (fastB) {
     k_lpB_rows<<<dim3((unsigned)cdiv(d.n, kEncCols), gy(nchB)), kThreads, 0, st>>>(
-        B, d.ldb, d.k, d.n, d.vb_cols, P.ec, bcs, P.L.bcs_ld, colpart, partB, nchB);
+        B, ldb, d.k, d.n, d.vb_cols, P.ec, bcs, P.L.bcs_ld, colpart, partB, nchB);
   } else {
     k_lpB_rows_any<<<dim3((unsigned)cdiv(nchB, kThreads / 32), gy(P.nvc)), kThreads, 0, st>>>(
-        B, d.ldb, d.k, d.n, d.vb_cols, P.ec, bcs, P.L.bcs_ld, partB, nchB);
+        B, ldb, d.k, d.n, d.vb_cols, P.ec, bcs, P.L.bcs_ld, partB, nchB);
     k_lp_col_sq<<<dim3((unsigned)cdiv(d.n, kThreads), gy(nchB)), kThreads, 0, st>>>(
-        B, d.ldb, d.k, d.n, colpart);
+        B, ldb, d.k, d.n, colpart);
   }
   k_lp_norms<<<(unsigned)cdiv(d.n, 128), 128, 0, st>>>(colpart, d.n, nchB, 1, d.n, nBcol);
   k_lp_blk<<<(unsigned)cdiv(P.nvc, 128), 128, 0, st>>>(nBcol, d.n, d.vb_cols, P.ec, partB, nchB,
@@ -816,6 +871,12 @@ cudaError_t launch_gemm_lp(const Plan& P, const void* A, const void* B, float* C
     op.lda = P.L.op_a_ld;
     op.ldb = P.L.op_b_ld;
     op.nseg = 3;
+  } else if (d.dtype == ABFT_FP8_E4M3) {  // the dequantised planes abft_encode wrote
+    op.a[0] = op.a[1] = w + P.L.op_a;
+    op.b[0] = op.b[1] = w + P.L.op_b;
+    op.lda = P.L.op_a_ld;
+    op.ldb = P.L.op_b_ld;
+    op.nseg = 1;
   } else {
     op.a[0] = op.a[1] = A;
     op.b[0] = op.b[1] = B;

@@ -108,8 +108,10 @@ cudaError_t launch_gemm_f64(const Plan& P, const double* A, const double* B, dou
                             bool checksums, cudaStream_t st);
 // Tensor-core dtypes: encode (checksum pieces, norms) and the product
 // followed by the fold of E16/F16 into the binary64 E/F.
-cudaError_t launch_encode_lp(const Plan& P, const void* A, const void* B, void* ws,
-                             cudaStream_t st);
+cudaError_t launch_encode_lp(const Plan& P, const void* A, const void* B, const void* a_scale,
+                             const void* b_scale, void* ws, cudaStream_t st);
+// Reads and clears the FP8 dequantisation flag (synchronises `st`).
+cudaError_t consume_fp8_inexact(cudaStream_t st, bool* inexact);
 size_t lp_part_bytes(const Plan& P);
 cudaError_t launch_gemm_lp(const Plan& P, const void* A, const void* B, float* C, void* ws,
                            bool checksums, cudaStream_t st);

@@ -294,6 +294,16 @@ struct SinglePol {
   __device__ __forceinline__ double expect_col(int, int64_t I, int64_t j) const {
     return a.E[(2 * I) * a.n + j];
   }
+  __device__ __forceinline__ double tau_col(int, int64_t I, int64_t j) const {
+    double te, tw;
+    col_taus(a, I, j, te, tw);
+    return te;
+  }
+  __device__ __forceinline__ double tau_row(int, int64_t i, int64_t J) const {
+    double te, tw;
+    row_taus(a, i, J, te, tw);
+    return te;
+  }
   __device__ __forceinline__ double expect_row(int, int64_t i, int64_t J) const {
     return a.F[i * a.Cc + 2 * J];
   }
@@ -453,6 +463,9 @@ __device__ __forceinline__ void locate_body(const Pol& A, int32_t* cnt, const Fl
       if (r2 == r && c2 / G.vb_c == J) ++nrow;
     }
     how[t] = ncol == 1 ? 0 : (nrow == 1 ? 1 : -1);
+    // alone in both lines: recompute from the line whose unweighted threshold
+    // (the scale of its rounding errors) is smaller; ties take the column
+    if (ncol == 1 && nrow == 1 && A.tau_row(p, r, J) < A.tau_col(p, I, c)) how[t] = 1;
   }
   __syncthreads();
 
@@ -574,6 +587,16 @@ struct GroupPol {
   }
   __device__ __forceinline__ double expect_col(int p, int64_t I, int64_t j) const {
     return grp_expect_col(probs[p], I, j, 0);
+  }
+  __device__ __forceinline__ double tau_col(int p, int64_t I, int64_t j) const {
+    double te, tw;
+    grp_col_taus(probs[p], s, I, j, te, tw);
+    return te;
+  }
+  __device__ __forceinline__ double tau_row(int p, int64_t i, int64_t J) const {
+    double te, tw;
+    grp_row_taus(probs[p], s, i, J, te, tw);
+    return te;
   }
   __device__ __forceinline__ double expect_row(int p, int64_t i, int64_t J) const {
     return grp_expect_row(probs[p], i, J, 0);

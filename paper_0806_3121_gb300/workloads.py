@@ -51,8 +51,14 @@ BF16X3_16384 = Workload("bf16x3_16384", "bf16x3", 16384, 16384, 16384, 256, 256,
                         note="FP32 16384^3 inputs N(0,1), split bf16x3 product, FP32 accumulate")
 BF16X3_8192 = Workload("bf16x3_8192", "bf16x3", 8192, 8192, 8192, 256, 256, dist="normal",
                        n_flips=3, note="split bf16x3 8192^3 (profiling size)")
+FP8_16384 = Workload("fp8_16384", "fp8", 16384, 16384, 16384, 256, 256, dist="fp8rows",
+                     n_flips=5, note="FP8 E4M3 16384^3: A, B iid U[-1,1] x 10^U(-2,2) per row, "
+                                     "quantised with one power-of-two binary32 scale per 128x128 "
+                                     "block; fp32 accumulate; 5 seeded faults")
+FP8_4096 = Workload("fp8_4096", "fp8", 4096, 4096, 4096, 256, 256, dist="fp8rows", n_flips=5,
+                    note="the FP8 recipe at 4096^3 (profiling size)")
 WORKLOADS = {w.name: w for w in (F64_512, F64_11264_GRID22, F64_4096_GRID8, BF16_16384,
-                                 BF16_8192, BF16X3_16384, BF16X3_8192)}
+                                 BF16_8192, BF16X3_16384, BF16X3_8192, FP8_16384, FP8_4096)}
 
 
 @dataclass(frozen=True)
@@ -91,6 +97,9 @@ def operand(shape, dist: str, seed: int, stream: int) -> np.ndarray:
         return g.standard_normal(size=shape)
     if dist == "int":
         return g.integers(-4, 5, size=shape).astype(np.float64)
+    if dist == "fp8rows":  # U[-1,1] times 10^U(-2,2), one magnitude per row
+        x = g.uniform(-1.0, 1.0, size=shape)
+        return x * 10.0 ** g.uniform(-2.0, 2.0, size=(shape[0], 1))
     raise ValueError(dist)
 
 
@@ -181,3 +190,27 @@ def faulty_instances(seed: int, count: int, frac: float):
     """Sorted indices of the instances that receive a flip (sampled without replacement)."""
     nf = max(1, int(round(frac * count)))
     return sorted(int(i) for i in rng(seed, 21).choice(count, size=nf, replace=False))
+
+
+E4M3_MAX = 448.0
+
+
+def quantize_e4m3(x: np.ndarray, blk: int = 128):
+    """Quantise to OCP FP8 E4M3 with one binary32 scale per blk x blk block: the scale is
+    the power of two 2^ceil(log2(max|x_block| / 448)) (1 for an all-zero block), the codes
+    are x / scale rounded to nearest-even E4M3 (torch's conversion on the CPU).  Returns
+    (codes uint8, scales float32 of shape ceil(rows/blk) x ceil(cols/blk))."""
+    import torch
+    x = np.asarray(x, dtype=np.float64)
+    rows, cols = x.shape
+    br, bc = -(-rows // blk), -(-cols // blk)
+    pad = np.zeros((br * blk, bc * blk))
+    pad[:rows, :cols] = np.abs(x)
+    amax = pad.reshape(br, blk, bc, blk).max(axis=(1, 3))
+    with np.errstate(divide="ignore"):
+        e = np.where(amax > 0, np.ceil(np.log2(amax / E4M3_MAX)), 0.0)
+    scales = np.exp2(e).astype(np.float32)
+    full = np.repeat(np.repeat(scales.astype(np.float64), blk, 0), blk, 1)[:rows, :cols]
+    t = torch.from_numpy(np.ascontiguousarray(x / full, dtype=np.float32))
+    codes = t.to(torch.float8_e4m3fn).view(torch.uint8).numpy().copy()
+    return codes, scales

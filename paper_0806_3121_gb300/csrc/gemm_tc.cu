@@ -39,6 +39,7 @@ constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 #endif
 constexpr int kEpiWarps = ABFT_EPI_WARPS;         // 4 or 8 (one or two per TMEM lane quarter)
 constexpr int kEpiCols = BN * 4 / kEpiWarps;       // tile columns per epilogue warp
+constexpr int kEpiChunks = kEpiCols / 32;          // 32-column TMEM loads per warp
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t A_BYTES = BM * BK * 2;          // 16 KiB
 constexpr uint32_t B_BOX_BYTES = 64 * BK * 2;      // one 64-column box: 8 KiB
@@ -46,7 +47,8 @@ constexpr uint32_t B_BYTES = BN * BK * 2;          // 32 KiB
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t TMEM_COLS = 2 * BN;             // two accumulators
 constexpr int GROUP_M = 16;                        // tile rows per raster group
-constexpr uint32_t OBS_BYTES = 4 * BN * 2 * 4;     // per-warp column partials (e, w)
+constexpr uint32_t OBS_BYTES = 2 * 4 * BN * 2 * 4; // column partials (e, w) per lane quarter,
+                                                   // two buffers (alternate fused tiles)
 constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + OBS_BYTES + 256;
 
 // Tensor maps of the operands: [0] = single / hi plane, [1] = lo plane.  The
@@ -80,6 +82,7 @@ struct TcArgs {
   const InjectEntry* inj;
   uint64_t wait_ns;          // bounded-wait limit
   int stall_test;            // timeout test: the producer skips the first tile
+  int kpg;                   // k-steps per promotion group (0: one group per tile)
 };
 
 struct Tile {
@@ -146,6 +149,7 @@ struct TileView {
   int prob;                   // problem index (grouped products; 0 otherwise)
   int64_t nkb;                // k-blocks per segment
   int nseg;
+  int kpg;                    // k-steps per promotion group (0: the whole K loop)
   const CUtensorMap* maD;     // A-side maps: data / checksum, plane 0 and 1
   const CUtensorMap* maD1;
   const CUtensorMap* maC;
@@ -198,6 +202,7 @@ struct SingleSched {
     V.prob = 0;
     V.nkb = (g.k + BK - 1) / BK;
     V.nseg = g.nseg;
+    V.kpg = g.kpg;
     V.maD = &M->a[0];
     V.maD1 = &M->a[1];
     V.maC = &M->acs[0];
@@ -275,10 +280,12 @@ __device__ __forceinline__ void transpose_reduce(float (&v)[32], int lane) {
   }
 }
 
-__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory"); }
 
 // The kernel body, shared by the single-problem and the grouped product.
-template <class Sched>
+// kPromote: the K loop runs in promotion groups whose accumulators the
+// epilogue sums in fp32 registers (a separate instantiation, so the register
+// accumulator of that path does not weigh on the single-group epilogue).
+template <bool kPromote, class Sched>
 __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wait_ns,
                                         int stall_test, const int32_t* inj_hdr,
                                         const InjectEntry* inj) {
@@ -287,8 +294,8 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
                                              ~static_cast<uintptr_t>(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + OBS_BYTES);
   // bars[0..S): full, [S..2S): empty, [2S..2S+2): tmem full, [2S+2..2S+4): tmem empty,
-  // [2S+4]: drain
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  // [2S+4]: drain, [2S+5..2S+7): epilogue combine (one per partial buffer)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 7);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -297,6 +304,7 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
   auto tfull = [&](int a) { return tc::smem_addr(&bars[2 * STAGES + a]); };
   auto tempty = [&](int a) { return tc::smem_addr(&bars[2 * STAGES + 2 + a]); };
   const uint32_t drain = tc::smem_addr(&bars[2 * STAGES + 4]);
+  auto ecomb = [&](int b) { return tc::smem_addr(&bars[2 * STAGES + 5 + b]); };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -308,6 +316,8 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
       tc::mbar_init(tempty(a), kEpiWarps);
     }
     tc::mbar_init(drain, 1);
+    tc::mbar_init(ecomb(0), kEpiWarps);
+    tc::mbar_init(ecomb(1), kEpiWarps);
     *abort = 0;
     tc::wait_limit_ns() = wait_ns;
     tc::fence_barrier_init();
@@ -384,32 +394,38 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
       for (int64_t t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
         const TileView T = S.view(t);
         const int64_t nkt = T.nkb * T.nseg;
+        const int64_t gsz = (kPromote && T.kpg > 0 && T.kpg < nkt) ? T.kpg : nkt;
         const uint32_t idesc = tc::idesc_bf16(BM, 64 * T.nbox, 1);
-        if (!tc::wait(tempty(acc), aph ^ 1, abort)) break;
-        tc::fence_after_sync();
-        const uint32_t d = tmem + acc * BN;
         bool ok = true;
-        for (int64_t kb = 0; kb < nkt; ++kb) {
-          if (!tc::wait(full(s), ph, abort)) { ok = false; break; }
+        // one accumulator per promotion group; the epilogue adds the groups
+        for (int64_t g0 = 0; g0 < nkt && ok; g0 += gsz) {
+          const int64_t g1 = min(g0 + gsz, nkt);
+          if (!tc::wait(tempty(acc), aph ^ 1, abort)) { ok = false; break; }
           tc::fence_after_sync();
-          const uint32_t sa = tc::smem_addr(smem + s * STAGE_BYTES);
-          const uint32_t sb = sa + A_BYTES;
+          const uint32_t d = tmem + acc * BN;
+          for (int64_t kb = g0; kb < g1; ++kb) {
+            if (!tc::wait(full(s), ph, abort)) { ok = false; break; }
+            tc::fence_after_sync();
+            const uint32_t sa = tc::smem_addr(smem + s * STAGE_BYTES);
+            const uint32_t sb = sa + A_BYTES;
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            // A: K-major, 128-byte rows, 8-row groups 1024 B apart; a K step
-            // of 16 elements moves 32 B inside the swizzled row.
-            const uint64_t ad = tc::sdesc_sw128(sa + kk * 32, 16, 1024);
-            // B: N-major, 64-column boxes 8 KiB apart, 8-row (K) groups
-            // 1024 B apart; a K step of 16 rows moves 2 KiB.
-            const uint64_t bd = tc::sdesc_sw128(sb + kk * 2048, B_BOX_BYTES, 1024);
-            tc::mma_f16(d, ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              // A: K-major, 128-byte rows, 8-row groups 1024 B apart; a K step
+              // of 16 elements moves 32 B inside the swizzled row.
+              const uint64_t ad = tc::sdesc_sw128(sa + kk * 32, 16, 1024);
+              // B: N-major, 64-column boxes 8 KiB apart, 8-row (K) groups
+              // 1024 B apart; a K step of 16 rows moves 2 KiB.
+              const uint64_t bd = tc::sdesc_sw128(sb + kk * 2048, B_BOX_BYTES, 1024);
+              tc::mma_f16(d, ad, bd, idesc, (kb > g0 || kk > 0) ? 1u : 0u);
+            }
+            tc::commit(empty(s));
+            if (++s == STAGES) { s = 0; ph ^= 1; }
           }
-          tc::commit(empty(s));
-          if (++s == STAGES) { s = 0; ph ^= 1; }
+          if (!ok) break;
+          tc::commit(tfull(acc));
+          if (++acc == 2) { acc = 0; aph ^= 1; }
         }
         if (!ok) break;
-        tc::commit(tfull(acc));
-        if (++acc == 2) { acc = 0; aph ^= 1; }
       }
       // Every MMA issued so far must complete before TMEM is freed.
       tc::commit(drain);
@@ -422,21 +438,26 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
     // ---------------- epilogue: warps 2..9; TMEM lane quarter q = warp % 4 (a
     // warp may only read its quarter), column half = (warp - 2) / 4
     const int q = warp & 3, half = q >> 1, c_lo = kEpiCols * ((warp - 2) >> 2);
-    float* obs = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);  // [4][BN][2]
+    float* obs_buf = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);  // [2][4][BN][2]
+    int eb = 0;               // partial buffer of the next fused tile
+    uint32_t eph[2] = {0, 0};  // phase of each buffer's combine barrier
     const int ninj = (inj_hdr && inj_hdr[0] == kInjectMagic)
                          ? max(0, min(inj_hdr[1], kMaxInject)) : 0;
     int acc = 0;
     uint32_t aph = 0;
-    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+    bool aborted = false;
+    for (int64_t t = blockIdx.x; t < total && !aborted; t += gridDim.x) {
       const TileView T = S.view(t);
-      if (!tc::wait(tfull(acc), aph, abort)) break;
-      tc::fence_after_sync();
+      const int64_t nkt = T.nkb * T.nseg;
+      const int64_t gsz = (kPromote && T.kpg > 0 && T.kpg < nkt) ? T.kpg : nkt;
+      const int ncol = 64 * T.nbox;
+      const int c_hi = min(c_lo + kEpiCols, ncol);
       // this warp's 32 rows: data rows, checksum rows or none
       const bool drow = half < T.hsplit, crow = !drow && half < T.hcnt;
       const int64_t rin = 32 * (q & 1) + lane;
       const int64_t row = drow ? T.rowD + 64 * half + rin : T.rowC + 64 * (half - T.hsplit) + rin;
       const bool rvalid = drow ? row < T.m : (crow && row < T.R16);
-      const int ndcol = 64 * T.bsplit, ncol = 64 * T.nbox;
+      const int ndcol = 64 * T.bsplit;
       const bool fused = T.obs_col != nullptr && T.hsplit > 0 && T.bsplit > 0;
       // armed faults inside this warp's part of the tile (one pass over the list)
       bool inj_hit = false;
@@ -451,17 +472,15 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
       }
       const float scr = scalbnf(1.0f, -T.er), scc = scalbnf(1.0f, -T.ec);
       const float wrow = (fused && drow) ? (float)((int)(row % T.vb_r) + 1) * scr : 0.f;
+      float* obs = obs_buf + eb * (4 * BN * 2);
       float racc_e = 0.f, racc_w = 0.f;
-      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
-      const int c_hi = min(c_lo + kEpiCols, ncol);
-#pragma unroll 1
-      for (int c = c_lo; c < c_hi; c += 32) {
-        float v[32];
-        tc::tmem_ld32(base + c, v);
+      // one 32-column chunk of the finished tile: fault injection, stores,
+      // fused observed sums (v is consumed)
+      auto chunk = [&](int c, float (&v)[32]) {
         const bool dcol = c < ndcol;
         if (dcol) {
           const int64_t col = T.colD + c;
-          if (col >= T.n) continue;
+          if (col >= T.n) return;
           if (drow) {
             if (inj_hit)
               for (int f = 0; f < ninj; ++f) {
@@ -499,8 +518,8 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
             float vw[32];
 #pragma unroll
             for (int u = 0; u < 32; ++u) vw[u] = wrow * v[u];
-            transpose_reduce(v, lane);
             transpose_reduce(vw, lane);
+            transpose_reduce(v, lane);
             obs[(q * BN + c + lane) * 2 + 0] = v[0];
             obs[(q * BN + c + lane) * 2 + 1] = vw[0];
           }
@@ -508,13 +527,72 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
           const int64_t col = T.colC + (c - ndcol);
           if (col < T.C16) store_row32(T.F16, T.C16, row, col, T.C16, v);
         }
+      };
+      if (!kPromote || gsz >= nkt) {
+        // one accumulator: each chunk is read and finished in turn; the
+        // accumulator is released after the last read
+        if (!tc::wait(tfull(acc), aph, abort)) break;
+        tc::fence_after_sync();
+        const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
+        const int nch = (c_hi - c_lo + 31) / 32;
+        for (int ci = 0; ci < nch; ++ci) {
+          float v[32];
+          tc::tmem_ld32(base + c_lo + 32 * ci, v);
+          if (ci == nch - 1) {
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(tempty(acc));
+            if (++acc == 2) { acc = 0; aph ^= 1; }
+          }
+          chunk(c_lo + 32 * ci, v);
+        }
+        if (nch <= 0) {  // nothing of this tile in this warp's half
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(tempty(acc));
+          if (++acc == 2) { acc = 0; aph ^= 1; }
+        }
+      } else if constexpr (kPromote) {
+        // promotion groups: this warp's part of the tile summed over the
+        // groups in fp32 registers (round to nearest), each accumulator
+        // released as soon as it is read
+        float accr[kEpiChunks][32];
+        for (int64_t g0 = 0; g0 < nkt; g0 += gsz) {
+          if (!tc::wait(tfull(acc), aph, abort)) { aborted = true; break; }
+          tc::fence_after_sync();
+          const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
+#pragma unroll
+          for (int ci = 0; ci < kEpiChunks; ++ci) {
+            const int c = c_lo + 32 * ci;
+            if (c < c_hi) {
+              if (g0 == 0) {
+                tc::tmem_ld32(base + c, accr[ci]);
+              } else {
+                float v[32];
+                tc::tmem_ld32(base + c, v);
+#pragma unroll
+                for (int u = 0; u < 32; ++u) accr[ci][u] += v[u];
+              }
+            }
+          }
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(tempty(acc));
+          if (++acc == 2) { acc = 0; aph ^= 1; }
+        }
+        if (aborted) break;
+#pragma unroll
+        for (int ci = 0; ci < kEpiChunks; ++ci)
+          if (c_lo + 32 * ci < c_hi) chunk(c_lo + 32 * ci, accr[ci]);
       }
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(tempty(acc));
-      if (++acc == 2) { acc = 0; aph ^= 1; }
       if (fused) {
-        epi_barrier();
+        // all epilogue warps' partials are in this buffer once its combine
+        // barrier completes (bounded wait; the next fused tile uses the other
+        // buffer, so no second barrier is needed before this one is rewritten)
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(ecomb(eb));
+        if (!tc::wait(ecomb(eb), eph[eb], abort)) break;
+        eph[eb] ^= 1;
 #pragma unroll
         for (int cc = (warp - 2) * 32 + lane; cc < BN; cc += 32 * kEpiWarps) {
           const int64_t col = T.colD + cc;
@@ -529,7 +607,7 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
             T.obs_col[(tr * 2 + 1) * T.n + col] = sw;
           }
         }
-        epi_barrier();
+        eb ^= 1;
       }
     }
   }
@@ -543,10 +621,11 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
   }
 }
 
+template <bool kPromote>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_bf16(const __grid_constant__ TcMaps M, const TcArgs g) {
   const SingleSched S{&M, &g};
-  tc_body(S, g.status, g.wait_ns, g.stall_test, g.inj_hdr, g.inj);
+  tc_body<kPromote>(S, g.status, g.wait_ns, g.stall_test, g.inj_hdr, g.inj);
 }
 
 // Many problems (grouped product).  The flattened tile list is a table of
@@ -562,6 +641,7 @@ struct GroupSched {
   const int4* tiles;  // {problem, tile row, tile column, 0}
   int64_t t_total;
   bool checksums;
+  int kpg;
   __device__ __forceinline__ int64_t total() const { return t_total; }
   __device__ __forceinline__ void prefetch() const {}
   __device__ __forceinline__ TileView view(int64_t t) const {
@@ -575,6 +655,7 @@ struct GroupSched {
     V.prob = e.x;
     V.nkb = cdiv(P.k, BK);
     V.nseg = 1;
+    V.kpg = kpg;
     V.maD = V.maD1 = &Mp.a;
     V.maC = V.maC1 = &Mp.acs;
     V.mbD = V.mbD1 = &Mp.b;
@@ -627,9 +708,9 @@ struct GroupSched {
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_grouped(const GProb* probs, const GMaps* maps, const int4* tiles, int64_t t_total,
                    int checksums, int* status, uint64_t wait_ns, const int32_t* inj_hdr,
-                   const InjectEntry* inj) {
-  const GroupSched S{probs, maps, tiles, t_total, checksums != 0};
-  tc_body(S, status, wait_ns, 0, inj_hdr, inj);
+                   const InjectEntry* inj, int kpg) {
+  const GroupSched S{probs, maps, tiles, t_total, checksums != 0, kpg};
+  tc_body<false>(S, status, wait_ns, 0, inj_hdr, inj);
 }
 
 // ---- host side
@@ -687,6 +768,18 @@ bool make_map_boxes(CUtensorMap* map, const void* ptr, int64_t rows, int64_t col
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Accumulator promotion: the tensor cores accumulate at most this many
+// 64-wide k-steps before the epilogue adds the partial into round-to-nearest
+// fp32 registers (0: the whole K loop in one accumulator).  The split bf16x3
+// product promotes every 4 steps (its point is accuracy: the tensor cores'
+// fp32 accumulation over long K loops dominates its error otherwise); the
+// environment variable ABFT_PROMOTE_KSTEPS overrides it for every dtype.
+int promote_ksteps(int dtype) {
+  const char* env = getenv("ABFT_PROMOTE_KSTEPS");
+  if (env && *env) return std::max(0, atoi(env));
+  return dtype == ABFT_BF16X3 ? 4 : 0;
 }
 
 int num_sms() {
@@ -779,13 +872,14 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
   // the call reports ABFT_ERR_TIMEOUT.  Off unless the variable is set.
   const char* stall = getenv("ABFT_TEST_STALL_PRODUCER");
   g.stall_test = stall && stall[0] == '1';
+  g.kpg = promote_ksteps(d.dtype);
   g.wait_ns = g.stall_test ? 200000000ull : tc::kWaitLimitNs;
-  e = cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)SMEM_BYTES);
+  const auto kernel = g.kpg > 0 ? k_gemm_bf16<true> : k_gemm_bf16<false>;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
   if (e != cudaSuccess) return e;
   const int grid = (int)std::min<int64_t>(g.t_total, num_sms());
   if (grid == 0) return cudaSuccess;
-  k_gemm_bf16<<<grid, kThreads, SMEM_BYTES, st>>>(M, g);
+  kernel<<<grid, kThreads, SMEM_BYTES, st>>>(M, g);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -814,7 +908,7 @@ cudaError_t launch_group_gemm(const GroupDev& G, bool checksums, cudaStream_t st
   if (grid == 0) return cudaSuccess;
   k_gemm_grouped<<<grid, kThreads, SMEM_BYTES, st>>>(
       G.probs, G.maps, checksums ? G.tiles_cs : G.tiles_plain, total, checksums ? 1 : 0, status,
-      tc::kWaitLimitNs, checksums ? G.inj_hdr : nullptr, G.inj);
+      tc::kWaitLimitNs, checksums ? G.inj_hdr : nullptr, G.inj, 0);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -4,11 +4,13 @@ oracle, through the C ABI.
 
 The oracle works in binary64 on the exact binary32 inputs.  Values: elementwise
 |C - C*| <= (2 k u32 + 2^-16)(|A||B|) -- fp32 accumulation plus the split's dropped A_lo B_lo
-term and the hi+lo representation of the inputs.  Accuracy: the relative Frobenius error
-against binary64 stays within 4 sqrt(3k) u32 + 2^-17 (the tensor cores' fp32 accumulation of
-3k products, at the scale measured for plain bf16, plus the split) and at least 50x below
-that of a plain bf16 product of the rounded inputs; the binary32 FMA GEMM (cuBLAS SGEMM,
-TF32 off) error is printed for comparison."""
+term and the hi+lo representation of the inputs.  Accuracy: the product promotes its tensor-core
+accumulator into round-to-nearest fp32 registers every 4 k-steps, so the accumulation error is
+small next to the split's own (inputs kept to ~16 significant bits, the A_lo B_lo term
+dropped): the relative Frobenius error against binary64 stays below 2^-17 and at least 500x
+below that of a plain bf16 product of the rounded inputs; the binary32 FMA GEMM (cuBLAS SGEMM,
+TF32 off) error is printed for comparison.  The looser 4 sqrt(3k) u32 + 2^-17 scale bounds
+the other cases."""
 import numpy as np
 import pytest
 
@@ -100,7 +102,7 @@ def test_x3_accuracy_fp32_level():
     e_bf = rel_fro(cb.astype(np.float64), ref)
     print(f"rel Frobenius error vs binary64: bf16x3 {e_x3:.2e}, fp32 SGEMM {e_32:.2e}, "
           f"bf16 {e_bf:.2e}")
-    assert e_x3 <= x3_tol(k) and e_x3 * 50 < e_bf
+    assert e_x3 <= 2.0 ** -17 and e_x3 * 500 < e_bf
 
 
 @pytest.mark.parametrize("seed", range(3))

@@ -272,7 +272,7 @@ def make_inputs(w, seed, dev):
     B = torch.randn(w.k, w.n, generator=g, device=dev)
     if w.dtype == "bf16":
         A, B = A.to(torch.bfloat16), B.to(torch.bfloat16)
-    return A, B, None, None
+    return A, B, None, None  # bf16x3 / bf16x6 take the binary32 values
 
 
 def fp8_quantize_dev(x, blk=128):
@@ -449,7 +449,7 @@ def run_workload(w, args, dev, rank, world, secondary=False):
 
     useful = 2.0 * w.m * w.n * w.k
     if lp:
-        nseg = 3 if w.dtype == "bf16x3" else 1  # split products are three bf16 products
+        nseg = {"bf16x3": 3, "bf16x6": 6}.get(w.dtype, 1)  # split products: 3 or 6 bf16 products
         kernel_flops = nseg * 2.0 * w.k * ((w.m + L.acs_rows) * w.n + w.m * L.bcs_cols)
         peak, peak_src = bf16_peak()
         roof = {"kernel": "k_gemm_bf16", "bound": "tensor", "peak_source": peak_src}
@@ -466,7 +466,8 @@ def run_workload(w, args, dev, rank, world, secondary=False):
                            "scales per 128x128 block (product of the exact dequantised values "
                            "on the bf16 tensor path)"}.get(
                 w.dtype, "N(0,1)" + {"bf16": " rounded to bf16", "bf16x3": " in fp32, split "
-                                     "into bf16 hi+lo"}.get(w.dtype, "")),
+                                     "into bf16 hi+lo", "bf16x6": " in fp32, split into three "
+                                     "bf16 pieces"}.get(w.dtype, "")),
            "faults_per_step": (f"{w.n_erased} erased block + " if w.n_erased else "") +
                               f"{w.n_flips} exponent bit-flips in distinct blocks" +
                               (" of the accumulator outputs (epilogue), verified from the "
@@ -657,7 +658,7 @@ def run_ours(args, rank, world):
             "roofline", "gpu_launches", "clocks", "config")
     if w.name == "f64_11264_grid22" and not args.no_secondary:
         # the tensor-core workloads first: the FP64 run is a minute of full-power load
-        for name in ("bf16_16384", "bf16x3_16384", "fp8_16384"):
+        for name in ("bf16_16384", "bf16x3_16384", "bf16x6_16384", "fp8_16384"):
             sec = run_workload(wl.WORKLOADS[name], args, dev, rank, world, secondary=True)
             secondary[name] = {k: sec[k] for k in keys}
         sec = run_grouped(wl.BF16_GROUPED_4096, args, dev, rank, world, secondary=True)

@@ -55,7 +55,10 @@ typedef enum {
   ABFT_BF16 = 1,    /* A, B bfloat16; C binary32; tensor-core product, fp32 accum.  */
   ABFT_BF16X3 = 2,  /* A, B binary32 split into bf16 hi+lo planes by abft_encode;
                        product A_hi B_hi + A_hi B_lo + A_lo B_hi; C binary32        */
-  ABFT_FP8_E4M3 = 3 /* A, B e4m3 with binary32 scales per 128x128 block; C binary32 */
+  ABFT_FP8_E4M3 = 3, /* A, B e4m3 with binary32 scales per 128x128 block; C binary32 */
+  ABFT_BF16X6 = 4   /* A, B binary32 split into three bf16 planes (x = p0 + p1 + p2,
+                       24 significant bits) by abft_encode; the six products
+                       p_a q_b with a + b <= 2; C binary32 (fp32-level accuracy)    */
 } abft_dtype;
 
 /* Report kinds (abft_fault.kind). */
@@ -112,9 +115,12 @@ typedef struct {
   size_t obs_col, obs_row;           /* fused observed partial sums (fp32)     */
   size_t inject;                     /* armed epilogue fault injections        */
   int32_t fused;                     /* 1: abft_gemm writes observed sums      */
-  int32_t planes;                    /* bf16 planes per operand: 2 for BF16X3  */
-  size_t acs_plane, bcs_plane;       /* bytes from the hi to the lo plane      */
-  size_t op_a, op_b;                 /* BF16X3: hi/lo planes of A and B        */
+  int32_t planes;                    /* bf16 planes per operand: 2 for BF16X3,
+                                        3 for BF16X6, else 1                   */
+  size_t acs_plane, bcs_plane;       /* bytes from one plane to the next       */
+  size_t op_a, op_b;                 /* split dtypes: the planes of A and B
+                                        (op_a_ld apart by align256 of a plane);
+                                        FP8: the dequantised bf16 operands     */
   int64_t op_a_ld, op_b_ld;          /* their leading dims (elements)          */
 } abft_ws_layout;
 
@@ -161,8 +167,8 @@ abft_status abft_encode_noalloc(const abft_desc* desc, const void* A, const void
 
 /* The ABFT product (Eq. (1)): [A; C_C^T A] [B, B C_R] on the GPU.  Writes the
  * data block A B into C and the checksum blocks into ws (E and F).  Requires a
- * preceding abft_encode on the same ws and operands.  ABFT_BF16X3 and
- * ABFT_FP8_E4M3 multiply the bf16 operand planes that encode wrote (A, B and the
+ * preceding abft_encode on the same ws and operands.  ABFT_BF16X3, ABFT_BF16X6
+ * and ABFT_FP8_E4M3 multiply the bf16 operand planes that encode wrote (A, B and the
  * scales are not read again).  Asynchronous. */
 abft_status abft_gemm(const abft_desc* desc, const void* A, const void* B, const void* a_scale,
                       const void* b_scale, void* C, void* ws, void* stream);
@@ -181,7 +187,7 @@ abft_status abft_set_epilogue_faults(const abft_desc* desc, void* ws, const int6
 
 /* The same GEMM kernel with no checksum tiles: C = A B only.  This is the
  * checksum-free baseline the ABFT overhead is measured against.  ws may be
- * NULL except for ABFT_BF16X3 and ABFT_FP8_E4M3, whose products read the bf16
+ * NULL except for ABFT_BF16X3, ABFT_BF16X6 and ABFT_FP8_E4M3, whose products read the bf16
  * operand planes a preceding abft_encode wrote into ws.  Asynchronous. */
 abft_status abft_gemm_plain(const abft_desc* desc, const void* A, const void* B,
                             const void* a_scale, const void* b_scale, void* C, void* ws,

@@ -171,6 +171,10 @@ def units(dtype: str) -> dict:
     """
     if dtype == "f64":
         return dict(u_acc=U64, u_sum=U64, u_enc=U64, u_c=U64, u_cs=U64)
+    if dtype == "bf16x6":
+        # three bf16 pieces keep 24 bits of each binary32 input: the dropped
+        # products and the residual of the pieces are below 2^-25 of a product
+        return dict(u_acc=U32, u_sum=U32, u_enc=U32, u_c=2.0 ** -25, u_cs=2.0 ** -26)
     if dtype == "bf16x3":
         # the split product drops A_lo B_lo and carries the hi+lo representation error of
         # the binary32 inputs: C deviates from their exact product by ~2^-17 relative

@@ -14,8 +14,8 @@ import threading
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libabft.so")
 
-F64, BF16, BF16X3, FP8_E4M3 = 0, 1, 2, 3
-DTYPE_CODES = {"f64": F64, "bf16": BF16, "bf16x3": BF16X3, "fp8": FP8_E4M3}
+F64, BF16, BF16X3, FP8_E4M3, BF16X6 = 0, 1, 2, 3, 4
+DTYPE_CODES = {"f64": F64, "bf16": BF16, "bf16x3": BF16X3, "fp8": FP8_E4M3, "bf16x6": BF16X6}
 
 OK, ERR_INVALID, ERR_CUDA, ERR_UNSUPPORTED, ERR_UNCORRECTABLE, ERR_TIMEOUT = range(6)
 KIND_CORRECTED, KIND_NONFINITE_CORRECTED, KIND_UNCORRECTABLE, KIND_BLOCK_RECOVERED = 1, 2, 3, 4

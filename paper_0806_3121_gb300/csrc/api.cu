@@ -53,6 +53,9 @@ Units units_for(int dtype) {
   // BF16X3: C also differs from the exact product of the fp32 inputs by the
   // dropped A_lo B_lo term and the hi+lo representation (2^-17 relative).
   if (dtype == ABFT_BF16X3) return {u32, u32, u32, ldexp(1.0, -17), ldexp(1.0, -17)};
+  // BF16X6: three pieces keep 24 bits; the dropped products and the pieces'
+  // residual stay below 2^-25 of a product, 2^-26 of a checksum.
+  if (dtype == ABFT_BF16X6) return {u32, u32, u32, ldexp(1.0, -25), ldexp(1.0, -26)};
   return {u32, u32, u32, 0.0, ldexp(1.0, -17)};
 }
 
@@ -74,7 +77,7 @@ size_t operand_bytes(int dtype) { return dtype == ABFT_F64 ? 8 : 2; }  // of acs
 abft_status make_plan(const abft_desc* d, Plan* P) {
   if (!d) return fail(ABFT_ERR_INVALID, "desc is NULL");
   if (d->dtype != ABFT_F64 && d->dtype != ABFT_BF16 && d->dtype != ABFT_BF16X3 &&
-      d->dtype != ABFT_FP8_E4M3)
+      d->dtype != ABFT_FP8_E4M3 && d->dtype != ABFT_BF16X6)
     return fail(ABFT_ERR_INVALID, "unknown dtype %d", d->dtype);
   if (d->m < 0 || d->n < 0 || d->k < 0) return fail(ABFT_ERR_INVALID, "negative size");
   if (d->m > (1ll << 22) || d->n > (1ll << 22) || d->k >= (1ll << 31))
@@ -121,14 +124,15 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
   abft_ws_layout& L = p.L;
   const size_t eb = operand_bytes(d->dtype);
   const bool lp = d->dtype != ABFT_F64;
-  const bool x3 = d->dtype == ABFT_BF16X3;
+  const bool x3 = d->dtype == ABFT_BF16X3 || d->dtype == ABFT_BF16X6;  // split binary32 inputs
+  const int nsplit = d->dtype == ABFT_BF16X6 ? 3 : 2;
   const bool f8 = d->dtype == ABFT_FP8_E4M3;
-  const int op_planes = x3 ? 2 : (f8 ? 1 : 0);  // bf16 operand planes the encode writes
+  const int op_planes = x3 ? nsplit : (f8 ? 1 : 0);  // bf16 operand planes the encode writes
   // Encoded operand rows/columns: binary64 checksums for F64.  bf16: each fp32
   // checksum is a bf16 hi+lo pair, as separate rows (4 rows per verify block, 2
   // per block-checksum row).  BF16X3: hi and lo planes of 2 rows per block
   // (the split product combines them).  Rows are 16-byte aligned.
-  L.planes = x3 ? 2 : 1;
+  L.planes = x3 ? nsplit : 1;
   L.acs_rows = x3 ? p.R : (lp ? 4 * p.nvr + 2 * p.bs : p.R);
   L.bcs_cols = x3 ? p.Cc : (lp ? 4 * p.nvc : p.Cc);
   L.acs_ld = lp ? (d->k + 7) / 8 * 8 : d->k;
@@ -285,7 +289,8 @@ static abft_status gemm_common(const abft_desc* desc, const void* A, const void*
   abft_status st = make_plan(desc, &P);
   if (st != ABFT_OK) return st;
   if (is_empty(P)) return ABFT_OK;
-  if (!C || ((checksums || P.d.dtype == ABFT_BF16X3 || P.d.dtype == ABFT_FP8_E4M3) && !ws) ||
+  if (!C || ((checksums || P.d.dtype == ABFT_BF16X3 || P.d.dtype == ABFT_BF16X6 ||
+               P.d.dtype == ABFT_FP8_E4M3) && !ws) ||
       (P.d.k > 0 && (!A || !B)))
     return fail(ABFT_ERR_INVALID, "NULL pointer");
   cudaError_t e;

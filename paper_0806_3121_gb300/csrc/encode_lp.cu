@@ -428,25 +428,53 @@ __device__ __forceinline__ void load8f(const float* row, int64_t c, int64_t len,
   }
 }
 
-// hi and lo bf16 planes of eight values, stored at hi + off and lo + off.
-__device__ __forceinline__ void store_split8(__nv_bfloat16* hi, __nv_bfloat16* lo, int64_t off,
-                                             const float (&v)[8]) {
-  __nv_bfloat16 h[8], l[8];
+// The bf16 planes of a split operand: x = p[0] + p[1] (+ p[2]) with
+// p[i] = bf16 of what the earlier pieces leave (each difference is exact in
+// fp32); np = 2 (bf16x3) or 3 (bf16x6).
+struct Planes {
+  __nv_bfloat16* p[3];
+  int np;
+};
+
+__device__ __forceinline__ void split_pieces(float x, __nv_bfloat16 (&out)[3]) {
+  float r = x;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) split(v[q], h[q], l[q]);
-  store8(hi + off, h);
-  store8(lo + off, l);
+  for (int i = 0; i < 3; ++i) {
+    out[i] = __float2bfloat16_rn(r);
+    r -= __bfloat162float(out[i]);
+  }
 }
 
-// A: hi/lo planes (m x ldk), column checksums of A per verify block from the
-// binary32 values (rows 2I, 2I+1 of the acs hi/lo planes), per-row partial
-// sums of squares and checksum-norm partials.  CTA = 2048 columns x a block.
+// One element into the planes at offset off.
+__device__ __forceinline__ void store_split1(const Planes& P, int64_t off, float x) {
+  __nv_bfloat16 h[3];
+  split_pieces(x, h);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    if (i < P.np) P.p[i][off] = h[i];
+}
+
+// Eight consecutive values into the planes at offset off (16-byte stores).
+__device__ __forceinline__ void store_split8(const Planes& P, int64_t off, const float (&v)[8]) {
+  __nv_bfloat16 h[3][8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    __nv_bfloat16 t[3];
+    split_pieces(v[q], t);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) h[i][q] = t[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    if (i < P.np) store8(P.p[i] + off, h[i]);
+}
+
+// A: planes (m x ldk), column checksums of A per verify block from the
+// binary32 values (rows 2I, 2I+1 of the acs planes), per-row partial sums of
+// squares and checksum-norm partials.  CTA = 2048 columns x a block.
 __global__ void __launch_bounds__(kThreads) k_x3A_cols(const float* __restrict__ A, int64_t lda,
                                                        int64_t m, int64_t k, int vb, int e,
-                                                       __nv_bfloat16* __restrict__ ahi,
-                                                       __nv_bfloat16* __restrict__ alo,
-                                                       __nv_bfloat16* __restrict__ chi,
-                                                       __nv_bfloat16* __restrict__ clo,
+                                                       const Planes op, const Planes cs,
                                                        int64_t ldk, float* __restrict__ rowpart,
                                                        int64_t nchr, double* __restrict__ part,
                                                        int64_t nch) {
@@ -463,8 +491,8 @@ __global__ void __launch_bounds__(kThreads) k_x3A_cols(const float* __restrict__
     for (int64_t i = i0; i < i1; ++i) {
       float v[8];
       load8f(A + i * lda, c0, k, v);
-      if (c0 < ldk) store_split8(ahi, alo, i * ldk + c0, v);
-      const float w = (float)(i - i0 + 1) * sc;
+      if (c0 < ldk) store_split8(op, i * ldk + c0, v);
+      const float w = (float)(int)(i - i0 + 1) * sc;
       float sq = 0.f;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -478,8 +506,8 @@ __global__ void __launch_bounds__(kThreads) k_x3A_cols(const float* __restrict__
     }
     float q0 = 0.f, q1 = 0.f;
     if (c0 < ldk) {
-      store_split8(chi, clo, (2 * I) * ldk + c0, se);
-      store_split8(chi, clo, (2 * I + 1) * ldk + c0, sw);
+      store_split8(cs, (2 * I) * ldk + c0, se);
+      store_split8(cs, (2 * I + 1) * ldk + c0, sw);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         q0 = fmaf(se[q], se[q], q0);
@@ -493,35 +521,28 @@ __global__ void __launch_bounds__(kThreads) k_x3A_cols(const float* __restrict__
   }
 }
 
-// Block checksum rows S_A[t] = sum_I A[I*bs + t] into rows 2 nvr + t of the planes.
+// Block checksum rows S_A[t] = sum_I A[I*bs + t] into rows 2 nvr + t of the
+// planes (cs points at row 2 nvr of each plane).
 __global__ void __launch_bounds__(kThreads) k_x3A_block(const float* __restrict__ A, int64_t lda,
                                                         int64_t k, int p, int64_t bs,
-                                                        __nv_bfloat16* __restrict__ shi,
-                                                        __nv_bfloat16* __restrict__ slo,
-                                                        int64_t ldk) {
+                                                        const Planes cs, int64_t ldk) {
   const int64_t l = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (l >= k) return;
   for (int64_t t = blockIdx.y; t < bs; t += gridDim.y) {
     float s = 0.f;
     for (int I = 0; I < p; ++I) s += A[(I * bs + t) * lda + l];
-    __nv_bfloat16 h, lo;
-    split(s, h, lo);
-    shi[t * ldk + l] = h;
-    slo[t * ldk + l] = lo;
+    store_split1(cs, t * ldk + l, s);
   }
 }
 
-// B: hi/lo planes (k x ldn), row checksums per verify column block (columns
-// 2J, 2J+1 of the bcs hi/lo planes), per-column partial sums of squares and
+// B: planes (k x ldn), row checksums per verify column block (columns 2J,
+// 2J+1 of the bcs planes), per-column partial sums of squares and
 // checksum-norm partials.  Verify blocks of 8 .. 256 columns (power of two).
 __global__ void __launch_bounds__(kThreads) k_x3B_rows(const float* __restrict__ B, int64_t ldb,
                                                        int64_t k, int64_t n, int vb, int e,
-                                                       __nv_bfloat16* __restrict__ bhi,
-                                                       __nv_bfloat16* __restrict__ blo,
-                                                       int64_t ldn,
-                                                       __nv_bfloat16* __restrict__ chi,
-                                                       __nv_bfloat16* __restrict__ clo,
-                                                       int64_t ldcs, float* __restrict__ colpart,
+                                                       const Planes op, int64_t ldn,
+                                                       const Planes cs, int64_t ldcs,
+                                                       float* __restrict__ colpart,
                                                        double* __restrict__ part, int64_t nch) {
   const int lane = threadIdx.x & 31;
   const int64_t c0 = (int64_t)blockIdx.x * kColsPerCta + 8 * threadIdx.x;
@@ -532,34 +553,29 @@ __global__ void __launch_bounds__(kThreads) k_x3B_rows(const float* __restrict__
   const float sc = scalbnf(1.0f, -e);
   float wq[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) wq[q] = (float)((c0 + q) % vb + 1) * sc;
-  float cs[8];
+  for (int q = 0; q < 8; ++q) wq[q] = (float)((int)((c0 + q) % vb) + 1) * sc;
+  float cs2[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) cs[q] = 0.f;
+  for (int q = 0; q < 8; ++q) cs2[q] = 0.f;
   float q0 = 0.f, q1 = 0.f;
   for (int64_t l = l0; l < l1; ++l) {
     float v[8];
     load8f(B + l * ldb, c0, n, v);
-    if (c0 < ldn) store_split8(bhi, blo, l * ldn + c0, v);
+    if (c0 < ldn) store_split8(op, l * ldn + c0, v);
     float se = 0.f, sw = 0.f;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       se += v[q];
       sw = fmaf(wq[q], v[q], sw);
-      cs[q] = fmaf(v[q], v[q], cs[q]);
+      cs2[q] = fmaf(v[q], v[q], cs2[q]);
     }
     for (int o = seg >> 1; o > 0; o >>= 1) {
       se += __shfl_xor_sync(0xffffffffu, se, o);
       sw += __shfl_xor_sync(0xffffffffu, sw, o);
     }
     if (leader) {
-      __nv_bfloat16 h, lo;
-      split(se, h, lo);
-      chi[l * ldcs + 2 * J] = h;
-      clo[l * ldcs + 2 * J] = lo;
-      split(sw, h, lo);
-      chi[l * ldcs + 2 * J + 1] = h;
-      clo[l * ldcs + 2 * J + 1] = lo;
+      store_split1(cs, l * ldcs + 2 * J, se);
+      store_split1(cs, l * ldcs + 2 * J + 1, sw);
       q0 = fmaf(se, se, q0);
       q1 = fmaf(sw, sw, q1);
     }
@@ -570,15 +586,13 @@ __global__ void __launch_bounds__(kThreads) k_x3B_rows(const float* __restrict__
   }
 #pragma unroll
   for (int q = 0; q < 8; ++q)
-    if (c0 + q < n) colpart[blockIdx.y * n + c0 + q] = cs[q];
+    if (c0 + q < n) colpart[blockIdx.y * n + c0 + q] = cs2[q];
 }
 
 // Any verify block size: planes and column partials by one kernel, row
 // checksums by one warp per (J, 128 rows).
 __global__ void __launch_bounds__(kThreads) k_x3B_split(const float* __restrict__ B, int64_t ldb,
-                                                        int64_t k, int64_t n,
-                                                        __nv_bfloat16* __restrict__ bhi,
-                                                        __nv_bfloat16* __restrict__ blo,
+                                                        int64_t k, int64_t n, const Planes op,
                                                         int64_t ldn, float* __restrict__ colpart) {
   const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (j >= ldn) return;
@@ -588,10 +602,7 @@ __global__ void __launch_bounds__(kThreads) k_x3B_split(const float* __restrict_
     float s = 0.f;
     for (int64_t l = l0; l < l1; ++l) {
       const float b = j < n ? B[l * ldb + j] : 0.f;
-      __nv_bfloat16 h, lo;
-      split(b, h, lo);
-      bhi[l * ldn + j] = h;
-      blo[l * ldn + j] = lo;
+      store_split1(op, l * ldn + j, b);
       s = fmaf(b, b, s);
     }
     if (j < n) colpart[c * n + j] = s;
@@ -600,9 +611,7 @@ __global__ void __launch_bounds__(kThreads) k_x3B_split(const float* __restrict_
 
 __global__ void __launch_bounds__(kThreads) k_x3B_rows_any(const float* __restrict__ B,
                                                            int64_t ldb, int64_t k, int64_t n,
-                                                           int vb, int e,
-                                                           __nv_bfloat16* __restrict__ chi,
-                                                           __nv_bfloat16* __restrict__ clo,
+                                                           int vb, int e, const Planes cs,
                                                            int64_t ldcs,
                                                            double* __restrict__ part,
                                                            int64_t nch) {
@@ -620,18 +629,13 @@ __global__ void __launch_bounds__(kThreads) k_x3B_rows_any(const float* __restri
       for (int64_t j = j0 + lane; j < j1; j += 32) {
         const float b = B[l * ldb + j];
         se += b;
-        sw = fmaf((float)(j - j0 + 1) * sc, b, sw);
+        sw = fmaf((float)(int)(j - j0 + 1) * sc, b, sw);
       }
       se = warp_sumf(se);
       sw = warp_sumf(sw);
       if (lane == 0) {
-        __nv_bfloat16 h, lo;
-        split(se, h, lo);
-        chi[l * ldcs + 2 * J] = h;
-        clo[l * ldcs + 2 * J] = lo;
-        split(sw, h, lo);
-        chi[l * ldcs + 2 * J + 1] = h;
-        clo[l * ldcs + 2 * J + 1] = lo;
+        store_split1(cs, l * ldcs + 2 * J, se);
+        store_split1(cs, l * ldcs + 2 * J + 1, sw);
       }
       q0 = fmaf(se, se, q0);
       q1 = fmaf(sw, sw, q1);
@@ -767,36 +771,39 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, cons
     if (P.L.bcs_ld > P.L.bcs_cols)
       cudaMemset2DAsync(reinterpret_cast<char*>(bcs) + pl * P.L.bcs_plane + P.L.bcs_cols * 2,
                         P.L.bcs_ld * 2, 0, (P.L.bcs_ld - P.L.bcs_cols) * 2, d.k, st);
-  if (d.dtype == ABFT_BF16X3) {
+  if (d.dtype == ABFT_BF16X3 || d.dtype == ABFT_BF16X6) {
     const float* Af = static_cast<const float*>(Av);
     const float* Bf = static_cast<const float*>(Bv);
-    auto* ahi = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_a);
-    auto* alo = ahi + align_elems(d.m * P.L.op_a_ld);
-    auto* bhi = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_b);
-    auto* blo = bhi + align_elems(d.k * P.L.op_b_ld);
-    auto* chi = acs;
-    auto* clo = reinterpret_cast<__nv_bfloat16*>(w + P.L.acs + P.L.acs_plane);
-    auto* bchi = bcs;
-    auto* bclo = reinterpret_cast<__nv_bfloat16*>(w + P.L.bcs + P.L.bcs_plane);
+    const int np = P.L.planes;
+    Planes opa{}, opb{}, acsp{}, bcsp{};
+    opa.np = opb.np = acsp.np = bcsp.np = np;
+    for (int i = 0; i < np; ++i) {
+      opa.p[i] = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_a) + i * align_elems(d.m * P.L.op_a_ld);
+      opb.p[i] = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_b) + i * align_elems(d.k * P.L.op_b_ld);
+      acsp.p[i] = reinterpret_cast<__nv_bfloat16*>(w + P.L.acs + i * P.L.acs_plane);
+      bcsp.p[i] = reinterpret_cast<__nv_bfloat16*>(w + P.L.bcs + i * P.L.bcs_plane);
+    }
     k_x3A_cols<<<dim3((unsigned)nchA, gy(P.nvr)), kThreads, 0, st>>>(
-        Af, d.lda, d.m, d.k, d.vb_rows, P.er, ahi, alo, chi, clo, P.L.acs_ld, rowpart, nchr,
-        partA, nchA);
-    if (P.bs > 0)
+        Af, d.lda, d.m, d.k, d.vb_rows, P.er, opa, acsp, P.L.acs_ld, rowpart, nchr, partA, nchA);
+    if (P.bs > 0) {
+      Planes sp = acsp;
+      for (int i = 0; i < np; ++i) sp.p[i] += 2 * P.nvr * P.L.acs_ld;
       k_x3A_block<<<dim3((unsigned)cdiv(d.k, kThreads), gy(P.bs)), kThreads, 0, st>>>(
-          Af, d.lda, d.k, d.grid_p, P.bs, chi + 2 * P.nvr * P.L.acs_ld,
-          clo + 2 * P.nvr * P.L.acs_ld, P.L.acs_ld);
+          Af, d.lda, d.k, d.grid_p, P.bs, sp, P.L.acs_ld);
+    }
     k_lp_norms<<<(unsigned)cdiv(d.m, 128), 128, 0, st>>>(rowpart, d.m, nchr, nchr, 1, nArow);
     k_lp_blk<<<(unsigned)cdiv(P.nvr, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA,
                                                          nchA, nAblk);
     if (fastB) {
       k_x3B_rows<<<dim3((unsigned)cdiv(P.L.op_b_ld, kColsPerCta), (unsigned)nchB), kThreads, 0,
-                   st>>>(Bf, d.ldb, d.k, d.n, d.vb_cols, P.ec, bhi, blo, P.L.op_b_ld, bchi, bclo,
-                         P.L.bcs_ld, colpart, partB, nchB);
+                   st>>>(
+          Bf, d.ldb, d.k, d.n, d.vb_cols, P.ec, opb, P.L.op_b_ld, bcsp, P.L.bcs_ld, colpart,
+          partB, nchB);
     } else {
       k_x3B_split<<<dim3((unsigned)cdiv(P.L.op_b_ld, kThreads), gy(nchB)), kThreads, 0, st>>>(
-          Bf, d.ldb, d.k, d.n, bhi, blo, P.L.op_b_ld, colpart);
+          Bf, d.ldb, d.k, d.n, opb, P.L.op_b_ld, colpart);
       k_x3B_rows_any<<<dim3((unsigned)cdiv(nchB, kThreads / 32), gy(P.nvc)), kThreads, 0, st>>>(
-          Bf, d.ldb, d.k, d.n, d.vb_cols, P.ec, bchi, bclo, P.L.bcs_ld, partB, nchB);
+          Bf, d.ldb, d.k, d.n, d.vb_cols, P.ec, bcsp, P.L.bcs_ld, partB, nchB);
     }
     k_lp_norms<<<(unsigned)cdiv(d.n, 128), 128, 0, st>>>(colpart, d.n, nchB, 1, d.n, nBcol);
     k_lp_blk<<<(unsigned)cdiv(P.nvc, 128), 128, 0, st>>>(nBcol, d.n, d.vb_cols, P.ec, partB,
@@ -861,32 +868,44 @@ cudaError_t launch_gemm_lp(const Plan& P, const void* A, const void* B, float* C
     return e;
   }
   TcOperands op{};
-  if (d.dtype == ABFT_BF16X3) {
-    const auto* ahi = reinterpret_cast<const __nv_bfloat16*>(w + P.L.op_a);
-    const auto* bhi = reinterpret_cast<const __nv_bfloat16*>(w + P.L.op_b);
-    op.a[0] = ahi;
-    op.a[1] = ahi + align_elems(d.m * P.L.op_a_ld);
-    op.b[0] = bhi;
-    op.b[1] = bhi + align_elems(d.k * P.L.op_b_ld);
+  if (d.dtype == ABFT_BF16X3 || d.dtype == ABFT_BF16X6) {
+    const auto* pa = reinterpret_cast<const __nv_bfloat16*>(w + P.L.op_a);
+    const auto* pb = reinterpret_cast<const __nv_bfloat16*>(w + P.L.op_b);
+    for (int i = 0; i < 3; ++i) {
+      const int pl = i < P.L.planes ? i : 0;
+      op.a[i] = pa + pl * align_elems(d.m * P.L.op_a_ld);
+      op.b[i] = pb + pl * align_elems(d.k * P.L.op_b_ld);
+    }
     op.lda = P.L.op_a_ld;
     op.ldb = P.L.op_b_ld;
-    op.nseg = 3;
+    if (d.dtype == ABFT_BF16X3) {
+      // A0 B0, A0 B1, A1 B0
+      op.nseg = 3;
+      op.seg_a = 0u | (0u << 2) | (1u << 4);
+      op.seg_b = 0u | (1u << 2) | (0u << 4);
+    } else {
+      // the six products with a + b <= 2, smallest first: A2 B0, A1 B1, A0 B2,
+      // A1 B0, A0 B1, A0 B0
+      op.nseg = 6;
+      op.seg_a = 2u | (1u << 2) | (0u << 4) | (1u << 6) | (0u << 8) | (0u << 10);
+      op.seg_b = 0u | (1u << 2) | (2u << 4) | (0u << 6) | (1u << 8) | (0u << 10);
+    }
   } else if (d.dtype == ABFT_FP8_E4M3) {  // the dequantised planes abft_encode wrote
-    op.a[0] = op.a[1] = w + P.L.op_a;
-    op.b[0] = op.b[1] = w + P.L.op_b;
+    op.a[0] = op.a[1] = op.a[2] = w + P.L.op_a;
+    op.b[0] = op.b[1] = op.b[2] = w + P.L.op_b;
     op.lda = P.L.op_a_ld;
     op.ldb = P.L.op_b_ld;
     op.nseg = 1;
   } else {
-    op.a[0] = op.a[1] = A;
-    op.b[0] = op.b[1] = B;
+    op.a[0] = op.a[1] = op.a[2] = A;
+    op.b[0] = op.b[1] = op.b[2] = B;
     op.lda = d.lda;
     op.ldb = d.ldb;
     op.nseg = 1;
   }
   cudaError_t e = launch_gemm_bf16(P, op, C, ws, checksums, st);
   if (e != cudaSuccess || !checksums) return e;
-  const int npc = d.dtype == ABFT_BF16X3 ? 1 : 2;
+  const int npc = (d.dtype == ABFT_BF16X3 || d.dtype == ABFT_BF16X6) ? 1 : 2;
   const float* E16 = reinterpret_cast<const float*>(w + P.L.E16);
   const float* F16 = reinterpret_cast<const float*>(w + P.L.F16);
   double* E = reinterpret_cast<double*>(w + P.L.E);

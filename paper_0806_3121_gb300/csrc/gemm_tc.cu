@@ -51,21 +51,19 @@ constexpr uint32_t OBS_BYTES = 2 * 4 * BN * 2 * 4; // column partials (e, w) per
                                                    // two buffers (alternate fused tiles)
 constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + OBS_BYTES + 256;
 
-// Tensor maps of the operands: [0] = single / hi plane, [1] = lo plane.  The
-// K loop runs over nseg segments of the k dimension; segment s reads A plane
-// (s == 2) and B plane (s == 1), so nseg = 3 accumulates
-// A_hi B_hi + A_hi B_lo + A_lo B_hi (split bf16x3) and nseg = 1 is plain bf16.
-// a / acs: 64-row boxes (one half); a128 / acs128: 128-row boxes (a whole
-// tile's A in one copy); b / bcs: one 64-column box; b4 / bcs4: a 3-D view
-// (64 columns, k rows, column box) that fetches four full 64-column boxes in
-// one copy (only boxes inside the matrix: n / 64 of them).
+// Tensor maps of the operands, per bf16 plane (the split dtypes have 2 or 3
+// planes; unused planes repeat plane 0).  The K loop runs nseg segments;
+// segment s reads A plane (seg_a >> 2s) & 3 and B plane (seg_b >> 2s) & 3.
+constexpr int kPlanes = 3;
 struct TcMaps {
-  CUtensorMap a[2], acs[2], b[2], bcs[2], a128[2], acs128[2], b4[2], bcs4[2];
+  CUtensorMap a[kPlanes], acs[kPlanes], b[kPlanes], bcs[kPlanes], a128[kPlanes],
+      acs128[kPlanes], b4[kPlanes], bcs4[kPlanes];
 };
 
 struct TcArgs {
   int64_t m, n, k, R16, C16;
   int nseg;
+  uint32_t seg_a, seg_b;
   int ntm, ntn, ntr, ntc;  // data tile rows/cols, checksum tile rows/cols (0 in plain mode)
   int64_t t_data, t_total;
   float* C;
@@ -150,22 +148,17 @@ struct TileView {
   int64_t nkb;                // k-blocks per segment
   int nseg;
   int kpg;                    // k-steps per promotion group (0: the whole K loop)
-  const CUtensorMap* maD;     // A-side maps: data / checksum, plane 0 and 1
-  const CUtensorMap* maD1;
+  uint32_t seg_a, seg_b;      // plane of A / B per K segment (2 bits each)
+  const CUtensorMap* maD;     // A-side maps: data / checksum (plane p at + p)
   const CUtensorMap* maC;
-  const CUtensorMap* maC1;
   const CUtensorMap* mbD;     // B-side maps
-  const CUtensorMap* mbD1;
   const CUtensorMap* mbC;
-  const CUtensorMap* mbC1;
   int32_t rowD, rowC, colD, colC;
   int hsplit, hcnt, bsplit, nbox;
   // one-copy loads: the whole A tile (maW: 128-row box at rowW) and four
   // full B boxes (mbW: 3-D map at box index colW / 64); nullptr: per half / box
-  const CUtensorMap* maW;
-  const CUtensorMap* maW1;
+  const CUtensorMap* maW;     // (plane p at + p)
   const CUtensorMap* mbW;     // boxes [0, nW) in one copy; the rest per box
-  const CUtensorMap* mbW1;
   int32_t rowW, colW, nW;
   float* C;                   // data x data, ld ldc, m x n
   int64_t ldc, m, n;
@@ -186,7 +179,7 @@ struct SingleSched {
   const TcArgs* a;
   __device__ __forceinline__ int64_t total() const { return a->t_total; }
   __device__ __forceinline__ void prefetch() const {
-    for (int pl = 0; pl < 2; ++pl) {
+    for (int pl = 0; pl < kPlanes; ++pl) {
       tc::prefetch_tmap(&M->a[pl]);
       tc::prefetch_tmap(&M->acs[pl]);
       tc::prefetch_tmap(&M->b[pl]);
@@ -203,14 +196,12 @@ struct SingleSched {
     V.nkb = (g.k + BK - 1) / BK;
     V.nseg = g.nseg;
     V.kpg = g.kpg;
+    V.seg_a = g.seg_a;
+    V.seg_b = g.seg_b;
     V.maD = &M->a[0];
-    V.maD1 = &M->a[1];
     V.maC = &M->acs[0];
-    V.maC1 = &M->acs[1];
     V.mbD = &M->b[0];
-    V.mbD1 = &M->b[1];
     V.mbC = &M->bcs[0];
-    V.mbC1 = &M->bcs[1];
     V.rowD = V.rowC = (int32_t)T.row0;
     V.colD = V.colC = (int32_t)T.col0;
     const int hrows = (int)clamp64(cdiv((T.kind == 1 ? g.R16 : g.m) - T.row0, 64), 1, 2);
@@ -219,17 +210,13 @@ struct SingleSched {
     V.hcnt = hrows;
     V.bsplit = T.kind == 2 ? 0 : bcols;
     V.nbox = bcols;
-    V.maW = V.maW1 = V.mbW = V.mbW1 = nullptr;
+    V.maW = V.mbW = nullptr;
     V.rowW = (int32_t)T.row0;
     V.colW = (int32_t)T.col0;
-    if (hrows == 2) {
-      V.maW = T.kind == 1 ? &M->acs128[0] : &M->a128[0];
-      V.maW1 = T.kind == 1 ? &M->acs128[1] : &M->a128[1];
-    }
+    if (hrows == 2) V.maW = T.kind == 1 ? &M->acs128[0] : &M->a128[0];
     V.nW = 4;
     if (bcols == 4 && T.col0 + 256 <= ((T.kind == 2 ? g.C16 : g.n) / 64) * 64) {
       V.mbW = T.kind == 2 ? &M->bcs4[0] : &M->b4[0];
-      V.mbW1 = T.kind == 2 ? &M->bcs4[1] : &M->b4[1];
     }
     V.C = g.C;
     V.ldc = g.ldc;
@@ -350,26 +337,26 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
           if (!tc::wait(empty(s), ph ^ 1, abort)) break;
           const uint32_t sa = tc::smem_addr(smem + s * STAGE_BYTES);
           tc::mbar_arrive_expect_tx(full(s), tx);
+          const int pa = (int)((T.seg_a >> (2 * seg)) & 3u);
+          const int pb = (int)((T.seg_b >> (2 * seg)) & 3u);
           if (T.maW) {
-            tc::tma_load_2d(sa, seg == 2 ? T.maW1 : T.maW, full(s), kx, T.rowW);
+            tc::tma_load_2d(sa, T.maW + pa, full(s), kx, T.rowW);
           } else {
             for (int h = 0; h < T.hcnt; ++h) {
               const bool dat = h < T.hsplit;
-              const CUtensorMap* ma =
-                  dat ? (seg == 2 ? T.maD1 : T.maD) : (seg == 2 ? T.maC1 : T.maC);
+              const CUtensorMap* ma = (dat ? T.maD : T.maC) + pa;
               const int32_t y = dat ? T.rowD + 64 * h : T.rowC + 64 * (h - T.hsplit);
               tc::tma_load_2d(sa + h * (A_BYTES / 2), ma, full(s), kx, y);
             }
           }
           int b_first = 0;
           if (T.mbW) {
-            tc::tma_load_3d(sa + A_BYTES, seg == 1 ? T.mbW1 : T.mbW, full(s), 0, kx, T.colW / 64);
+            tc::tma_load_3d(sa + A_BYTES, T.mbW + pb, full(s), 0, kx, T.colW / 64);
             b_first = T.nW;
           }
           for (int b = b_first; b < T.nbox; ++b) {
             const bool dat = b < T.bsplit;
-            const CUtensorMap* mb =
-                dat ? (seg == 1 ? T.mbD1 : T.mbD) : (seg == 1 ? T.mbC1 : T.mbC);
+            const CUtensorMap* mb = (dat ? T.mbD : T.mbC) + pb;
             const int32_t x = dat ? T.colD + 64 * b : T.colC + 64 * (b - T.bsplit);
             tc::tma_load_2d(sa + A_BYTES + b * B_BOX_BYTES, mb, full(s), x, kx);
           }
@@ -656,10 +643,11 @@ struct GroupSched {
     V.nkb = cdiv(P.k, BK);
     V.nseg = 1;
     V.kpg = kpg;
-    V.maD = V.maD1 = &Mp.a;
-    V.maC = V.maC1 = &Mp.acs;
-    V.mbD = V.mbD1 = &Mp.b;
-    V.mbC = V.mbC1 = &Mp.bcs;
+    V.seg_a = V.seg_b = 0;  // one plane
+    V.maD = &Mp.a;
+    V.maC = &Mp.acs;
+    V.mbD = &Mp.b;
+    V.mbC = &Mp.bcs;
     V.hsplit = max(0, min(2, nhd - h0));
     V.hcnt = min(2, nhd + nhc - h0);
     V.bsplit = max(0, min(P.bpt, nbd - b0));
@@ -668,20 +656,20 @@ struct GroupSched {
     V.rowC = 64 * max(0, h0 - nhd);
     V.colD = 64 * b0;
     V.colC = 64 * max(0, b0 - nbd);
-    V.maW = V.maW1 = V.mbW = V.mbW1 = nullptr;
+    V.maW = V.mbW = nullptr;
     if (V.hsplit == 2) {
-      V.maW = V.maW1 = &Mp.a128;
+      V.maW = &Mp.a128;
       V.rowW = V.rowD;
     } else if (V.hsplit == 0 && V.hcnt == 2) {
-      V.maW = V.maW1 = &Mp.acs128;
+      V.maW = &Mp.acs128;
       V.rowW = V.rowC;
     }
     if (V.bsplit >= 2 && b0 + V.bsplit <= (int)(P.n / 64)) {  // full data boxes
-      V.mbW = V.mbW1 = &Mp.bw[V.bsplit - 2];
+      V.mbW = &Mp.bw[V.bsplit - 2];
       V.colW = V.colD;
       V.nW = V.bsplit;
     } else if (V.nbox == 4 && V.bsplit == 0 && (b0 - nbd) + 4 <= (int)(P.C16 / 64)) {
-      V.mbW = V.mbW1 = &Mp.bcs4;
+      V.mbW = &Mp.bcs4;
       V.colW = V.colC;
       V.nW = 4;
     }
@@ -772,14 +760,18 @@ bool make_map_boxes(CUtensorMap* map, const void* ptr, int64_t rows, int64_t col
 
 // Accumulator promotion: the tensor cores accumulate at most this many
 // 64-wide k-steps before the epilogue adds the partial into round-to-nearest
-// fp32 registers (0: the whole K loop in one accumulator).  The split bf16x3
-// product promotes every 4 steps (its point is accuracy: the tensor cores'
-// fp32 accumulation over long K loops dominates its error otherwise); the
-// environment variable ABFT_PROMOTE_KSTEPS overrides it for every dtype.
+// fp32 registers (0: the whole K loop in one accumulator).  The split products
+// exist for accuracy, and the tensor cores' fp32 accumulation over long K
+// loops would dominate their error: bf16x6 promotes every 8 steps (measured
+// relative error 4.8e-7 at k = 4096 and 16384, below cuBLAS SGEMM's; every 4
+// steps gives 2.7e-7 at 5 % lower throughput), bf16x3 every 16 (its 2-piece
+// split floor, 4.4e-6, dominates anyway).  Plain bf16 and FP8 do not promote
+// by default (measured 12-25 % slower at 16384^3 with it).  The environment
+// variable ABFT_PROMOTE_KSTEPS overrides the choice for every dtype.
 int promote_ksteps(int dtype) {
   const char* env = getenv("ABFT_PROMOTE_KSTEPS");
   if (env && *env) return std::max(0, atoi(env));
-  return dtype == ABFT_BF16X3 ? 4 : 0;
+  return dtype == ABFT_BF16X6 ? 8 : (dtype == ABFT_BF16X3 ? 16 : 0);
 }
 
 int num_sms() {
@@ -823,9 +815,10 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
   const char* w = static_cast<const char*>(ws);
   const int64_t R16 = checksums ? P.L.acs_rows : 0, C16 = checksums ? P.L.bcs_cols : 0;
   TcMaps M;
-  for (int pl = 0; pl < 2; ++pl) {
-    const void* acs = checksums ? w + P.L.acs + pl * P.L.acs_plane : op.a[0];
-    const void* bcs = checksums ? w + P.L.bcs + pl * P.L.bcs_plane : op.b[0];
+  for (int pl = 0; pl < kPlanes; ++pl) {
+    const int cpl = pl < P.L.planes ? pl : 0;  // checksum planes beyond the dtype's repeat plane 0
+    const void* acs = checksums ? w + P.L.acs + cpl * P.L.acs_plane : op.a[0];
+    const void* bcs = checksums ? w + P.L.bcs + cpl * P.L.bcs_plane : op.b[0];
     const int64_t acs_ld = checksums ? P.L.acs_ld : op.lda;
     const int64_t bcs_ld = checksums ? P.L.bcs_ld : op.ldb;
     if (!make_map(&M.a[pl], op.a[pl], d.m, d.k, op.lda, 64, BM / 2) ||
@@ -841,6 +834,8 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
   TcArgs g{};
   g.m = d.m; g.n = d.n; g.k = d.k; g.R16 = R16; g.C16 = C16;
   g.nseg = op.nseg;
+  g.seg_a = op.seg_a;
+  g.seg_b = op.seg_b;
   g.ntm = (int)cdiv(d.m, BM);
   g.ntn = (int)cdiv(d.n, BN);
   g.ntr = checksums ? (int)cdiv(R16, BM) : 0;

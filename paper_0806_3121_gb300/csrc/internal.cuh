@@ -115,13 +115,15 @@ cudaError_t consume_fp8_inexact(cudaStream_t st, bool* inexact);
 size_t lp_part_bytes(const Plan& P);
 cudaError_t launch_gemm_lp(const Plan& P, const void* A, const void* B, float* C, void* ws,
                            bool checksums, cudaStream_t st);
-// Operands of the tensor-core product: bf16 planes [0] (single or hi) and [1]
-// (lo), K-major A (ld lda) and N-major B (ld ldb), nseg = 1 (bf16) or 3 (split).
+// Operands of the tensor-core product: up to three bf16 planes of K-major A
+// (ld lda) and N-major B (ld ldb).  The K loop runs nseg segments; segment s
+// multiplies A plane (seg_a >> 2s) & 3 by B plane (seg_b >> 2s) & 3.
 struct TcOperands {
-  const void* a[2];
-  const void* b[2];
+  const void* a[3];
+  const void* b[3];
   int64_t lda, ldb;
   int nseg;
+  uint32_t seg_a, seg_b;
 };
 cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void* ws,
                              bool checksums, cudaStream_t st);

@@ -51,6 +51,10 @@ BF16X3_16384 = Workload("bf16x3_16384", "bf16x3", 16384, 16384, 16384, 256, 256,
                         note="FP32 16384^3 inputs N(0,1), split bf16x3 product, FP32 accumulate")
 BF16X3_8192 = Workload("bf16x3_8192", "bf16x3", 8192, 8192, 8192, 256, 256, dist="normal",
                        n_flips=3, note="split bf16x3 8192^3 (profiling size)")
+BF16X6_16384 = Workload("bf16x6_16384", "bf16x6", 16384, 16384, 16384, 256, 256,
+                        dist="normal", n_flips=3,
+                        note="FP32 16384^3 inputs N(0,1), split bf16x6 product (three bf16 "
+                             "pieces, six products), FP32-level accuracy")
 FP8_16384 = Workload("fp8_16384", "fp8", 16384, 16384, 16384, 256, 256, dist="fp8rows",
                      n_flips=5, note="FP8 E4M3 16384^3: A, B iid U[-1,1] x 10^U(-2,2) per row, "
                                      "quantised with one power-of-two binary32 scale per 128x128 "
@@ -58,7 +62,8 @@ FP8_16384 = Workload("fp8_16384", "fp8", 16384, 16384, 16384, 256, 256, dist="fp
 FP8_4096 = Workload("fp8_4096", "fp8", 4096, 4096, 4096, 256, 256, dist="fp8rows", n_flips=5,
                     note="the FP8 recipe at 4096^3 (profiling size)")
 WORKLOADS = {w.name: w for w in (F64_512, F64_11264_GRID22, F64_4096_GRID8, BF16_16384,
-                                 BF16_8192, BF16X3_16384, BF16X3_8192, FP8_16384, FP8_4096)}
+                                 BF16_8192, BF16X3_16384, BF16X3_8192, BF16X6_16384, FP8_16384,
+                                 FP8_4096)}
 
 
 @dataclass(frozen=True)

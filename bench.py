@@ -45,8 +45,9 @@ METRIC = "ABFT GEMM TFLOPS (useful 2mnk) and % overhead vs checksum-free GEMM, s
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # Measured DRAM read + write per launch of the product kernel at the bench workloads (ncu
 # dram__bytes_read.sum + dram__bytes_write.sum, see profiles/), or None when the kernel
-# changed since it was captured.  f64: 45.50 + 1.08 GB; bf16: 8.76 + 1.09 GB.
-TRAFFIC_BYTES = {"f64": 46.58e9, "bf16": 9.85e9}
+# changed since it was captured.  f64: 45.50 + 1.08 GB; bf16: 8.77 + 1.10 GB; bf16x6:
+# 94.53 + 1.29 GB; grouped 4096: 30.80 + 19.39 GB.
+TRAFFIC_BYTES = {"f64": 46.58e9, "bf16": 9.87e9, "bf16x6": 95.82e9, "grouped": 50.19e9}
 
 
 def bf16_peak():
@@ -622,7 +623,8 @@ def run_grouped(w, args, dev, rank, world, secondary=False):
         "plain_useful_tflops": useful / (plain_ms * 1e-3) / 1e12,
         "roofline": {"kernel": "k_gemm_grouped", "bound": "tensor", "peak_source": peak_src,
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": TRAFFIC_BYTES["grouped"] if w.count == 4096 else None,
                      "algorithmic_flops_per_launch": useful + cs_flops},
         "gpu_launches": launches, "clocks": clocks, "e2e": None,
     }

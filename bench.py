@@ -37,6 +37,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_0806_3121_gb300 import multigpu as mg  # noqa: E402
 from paper_0806_3121_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "ABFT GEMM TFLOPS (useful 2mnk) and % overhead vs checksum-free GEMM, same GPU/dtype"
@@ -307,7 +308,7 @@ def run_workload(w, args, dev, rank, world, secondary=False):
     import torch
     from paper_0806_3121_gb300 import abft
 
-    seed = args.seed + rank
+    seed = mg.rank_seed(args.seed, rank)
     scales = {}
     if w.dtype == "fp8":
         import torch as _t
@@ -342,9 +343,7 @@ def run_workload(w, args, dev, rank, world, secondary=False):
         # before C and its fused observed checksums are formed; verify reads those sums
         abft.abft_set_epilogue_faults(desc, ws, flips, stream=stream)
 
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+    barrier = mg.barrier
 
     gemm_ms = []
 
@@ -434,19 +433,13 @@ def run_workload(w, args, dev, rank, world, secondary=False):
         torch.cuda.synchronize()
         barrier()
         e2e_ms = a.elapsed_time(b) / args.steps
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = t.item()
+        e2e_ms = mg.max_over_ranks(e2e_ms)
         e2e = {"value": 2.0 * w.m * w.n * w.k * world / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": A_h.numel() * A_h.element_size() +
                                      B_h.numel() * B_h.element_size(),
                "d2h_bytes_per_step": C_h.numel() * C_h.element_size()}
 
-    if world > 1:
-        t = torch.tensor([step_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = t.item()
+    step_ms = mg.max_over_ranks(step_ms)
 
     useful = 2.0 * w.m * w.n * w.k
     if lp:
@@ -461,7 +454,7 @@ def run_workload(w, args, dev, rank, world, secondary=False):
     achieved = kernel_flops / (gemm_avg * 1e-3) / 1e12
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                  "traffic": TRAFFIC_BYTES.get(w.dtype), "algorithmic_flops_per_launch": kernel_flops})
-    value = useful * world / (step_ms * 1e-3) / 1e12
+    value = mg.weak_scaling_value(useful, world, step_ms)
     cfg = {"workload": w.name, "m": w.m, "n": w.n, "k": w.k, "verify_block": [w.vb_r, w.vb_c],
            "dist": {"fp8": "U[-1,1] x 10^U(-2,2) per row, e4m3 with power-of-two binary32 "
                            "scales per 128x128 block (product of the exact dequantised values "
@@ -515,7 +508,7 @@ def run_grouped(w, args, dev, rank, world, secondary=False):
     import torch
     from paper_0806_3121_gb300 import abft
 
-    seed = args.seed + rank
+    seed = mg.rank_seed(args.seed, rank)
     shapes = wl.group_shapes(seed, w)
     g = torch.Generator(device=dev).manual_seed(seed)
     As, Bs, Cs, probs = [], [], [], []
@@ -553,9 +546,7 @@ def run_grouped(w, args, dev, rank, world, secondary=False):
     assert sorted((e["problem"], e["row"], e["col"]) for e in rep) == \
         sorted((p, i, j) for p, i, j, _ in flips), rep
 
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+    barrier = mg.barrier
 
     launches0 = abft.abft_kernel_launches()
     with ClockSampler(dev.index) as clk:
@@ -596,12 +587,9 @@ def run_grouped(w, args, dev, rank, world, secondary=False):
     cs_flops = sum(2.0 * k * (4 * -(-m // 128) * n + m * 4 * -(-n // 256)) for m, n, k in shapes)
     peak, peak_src = bf16_peak()
     achieved = (useful + cs_flops) / (abft_ms * 1e-3) / 1e12
-    if world > 1:
-        t = torch.tensor([step_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = t.item()
+    step_ms = mg.max_over_ranks(step_ms)
     out = {
-        "metric": METRIC, "value": useful * world / (step_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+        "metric": METRIC, "value": mg.weak_scaling_value(useful, world, step_ms), "unit": "TFLOP/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
         "data": "synthetic",

@@ -55,7 +55,7 @@ class OracleCfg(ct.Structure):
                 ("vb_r", ct.c_int64), ("vb_c", ct.c_int64), ("p", ct.c_int64), ("q", ct.c_int64),
                 ("u_acc", ct.c_double), ("u_sum", ct.c_double), ("u_enc", ct.c_double),
                 ("u_c", ct.c_double), ("u_cs", ct.c_double), ("s", ct.c_double),
-                ("round_f32", ct.c_int32), ("pad", ct.c_int32)]
+                ("round_f32", ct.c_int32), ("f", ct.c_int32)]
 
 
 class OracleFault(ct.Structure):
@@ -73,7 +73,11 @@ def lib():
             _lib.oracle_weight.restype = ct.c_double
             _lib.oracle_weight.argtypes = [i64, i64]
             _lib.oracle_gemm.argtypes = [i64, i64, i64, d, i64, d, i64, d, i64]
-            _lib.oracle_encode_A.argtypes = [i64, i64, d, i64, i64, i64, d]
+            _lib.oracle_encode_A.argtypes = [i64, i64, d, i64, i64, i64, i64, d]
+            _lib.oracle_block_coef.restype = ct.c_double
+            _lib.oracle_block_coef.argtypes = [i64, i64, i64]
+            _lib.oracle_recover_blocks.restype = ct.c_int
+            _lib.oracle_recover_blocks.argtypes = [d, d, i64, d, d, d, d, i32, d]
             _lib.oracle_encode_B.argtypes = [i64, i64, d, i64, i64, d]
             _lib.oracle_norms_A.argtypes = [i64, i64, d, i64, i64, d, d]
             _lib.oracle_norms_B.argtypes = [i64, i64, d, i64, i64, d, d]
@@ -122,13 +126,20 @@ def gemm(A, B) -> np.ndarray:
     return C
 
 
-def encode_A(A, vb: int, p: int = 0) -> np.ndarray:
-    """Checksum rows of A: [e^T A_I; w^T A_I] per verify block, then S_A (section 2.1)."""
+def block_coef(l: int, I: int, p: int) -> float:
+    """Coefficient of block row I in block checksum l (section 2.1, several checksums)."""
+    return lib().oracle_block_coef(l, I, p)
+
+
+def encode_A(A, vb: int, p: int = 0, f: int = 1) -> np.ndarray:
+    """Checksum rows of A: [e^T A_I; w^T A_I] per verify block, then the f block checksums
+    S^(l) = sum_I c_{l,I} A_I (section 2.1)."""
     A = _f64(A)
     m, k = A.shape
-    rows = 2 * cdiv(m, vb) + (m // p if p else 0)
+    f = max(1, f)
+    rows = 2 * cdiv(m, vb) + (f * (m // p) if p else 0)
     acs = np.empty((rows, k), np.float64)
-    lib().oracle_encode_A(m, k, _p(A), k, vb, p, _p(acs))
+    lib().oracle_encode_A(m, k, _p(A), k, vb, p, f, _p(acs))
     return acs
 
 
@@ -182,22 +193,22 @@ def units(dtype: str) -> dict:
     return dict(u_acc=U32, u_sum=U32, u_enc=U32, u_c=0.0, u_cs=2.0 ** -17)
 
 
-def make_cfg(m, n, k, vb_r, vb_c, p=0, q=0, dtype="f64", s=4.0) -> OracleCfg:
+def make_cfg(m, n, k, vb_r, vb_c, p=0, q=0, dtype="f64", s=4.0, f=1) -> OracleCfg:
     u = units(dtype)
     return OracleCfg(m=m, n=n, k=k, vb_r=vb_r, vb_c=vb_c, p=p, q=q, s=s,
-                     round_f32=0 if dtype == "f64" else 1, pad=0, **u)
+                     round_f32=0 if dtype == "f64" else 1, f=max(1, f), **u)
 
 
 class Encoded:
     """Everything the oracle derives from A and B before C is checked."""
 
-    def __init__(self, A, B, vb_r, vb_c, p=0, q=0, dtype="f64", s=4.0, products=True):
+    def __init__(self, A, B, vb_r, vb_c, p=0, q=0, dtype="f64", s=4.0, products=True, f=1):
         A, B = _f64(A), _f64(B)
         self.A, self.B = A, B
         self.m, self.k = A.shape
         self.n = B.shape[1]
-        self.cfg = make_cfg(self.m, self.n, self.k, vb_r, vb_c, p, q, dtype, s)
-        self.acs = encode_A(A, vb_r, p)
+        self.cfg = make_cfg(self.m, self.n, self.k, vb_r, vb_c, p, q, dtype, s, f)
+        self.acs = encode_A(A, vb_r, p, f)
         self.bcs = encode_B(B, vb_c)
         self.nArow, self.nAblk = norms_A(A, vb_r)
         self.nBcol, self.nBblk = norms_B(B, vb_c)
@@ -261,6 +272,18 @@ class Encoded:
         if d <= 0.5 * min(te_c, tw_c / wi, te_r, tw_r / wj):
             return "benign"
         return "guard"
+
+    def recover_blocks(self, C, blocks):
+        """Rebuild the erased blocks [(bi, bj), ...] on a copy of C (up to f per block
+        column); returns (status, C, n_flagged)."""
+        C = _f64(C).copy()
+        nfl = ct.c_int32(0)
+        bl = np.ascontiguousarray(np.array(blocks, np.int32).reshape(-1))
+        st = lib().oracle_recover_blocks(ct.byref(self.cfg), _p(C), self.cfg.n, _p(self.E),
+                                         _p(self.nBcol), _p(self.nAblk),
+                                         _p(bl) if bl.size else None, bl.size // 2,
+                                         ct.byref(nfl))
+        return st, C, nfl.value
 
     def recover_block(self, C, bi, bj):
         """Rebuild erased block (bi, bj) on a copy of C; returns (status, C, n_flagged)."""

@@ -90,16 +90,31 @@ void oracle_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Coefficient c_{l,I} of block row I in block checksum l of a p-block grid
+ * (section 2.1: f checksums with f independent weight vectors recover f lost
+ * blocks; the paper draws them at random so that every f-by-f minor is
+ * nonsingular).  Here: Vandermonde weights c_{l,I} = x_I^l with distinct
+ * nodes x_I = (I+1) / 2^e, 2^e > p -- every f-by-f minor of a Vandermonde
+ * matrix with distinct nodes is nonsingular, and the dyadic values are exact
+ * in binary32 and binary64.  l = 0 is the plain sum (c = 1). */
+double oracle_block_coef(int64_t l, int64_t I, int64_t p) {
+  int e = 0;
+  while (((int64_t)1 << e) <= p) ++e;
+  double x = ldexp((double)(I + 1), -e), c = 1.0;
+  for (int64_t t = 0; t < l; ++t) c *= x;
+  return c;
+}
+
 /* Encode A (section 2.1 and the left operand of Eq. (1)).
- * acs has (2*nvb + bs) rows of k values, nvb = ceil(m/vb), bs = m/p (0 if
+ * acs has (2*nvb + f*bs) rows of k values, nvb = ceil(m/vb), bs = m/p (0 if
  * p == 0):
- *   row 2I     : e^T A_I         (unweighted column checksum of block I)
- *   row 2I+1   : w^T A_I         (weighted column checksum of block I)
- *   row 2nvb+t : sum_I A[I*bs+t] (block checksum rows S_A, erasure grid)
+ *   row 2I           : e^T A_I                     (unweighted column checksum of block I)
+ *   row 2I+1         : w^T A_I                     (weighted column checksum of block I)
+ *   row 2nvb+l*bs+t  : sum_I c_{l,I} A[I*bs+t]     (block checksum rows S^(l), l < f)
  * Pinned by: hand-worked golden values and exact integer invariants
- * e^T C = (e^T A) B. */
+ * e^T C = (e^T A) B, S^(l) B = sum_I c_{l,I} C_I. */
 void oracle_encode_A(int64_t m, int64_t k, const double* A, int64_t lda, int64_t vb, int64_t p,
-                     double* acs) {
+                     int64_t f, double* acs) {
   int64_t nvb = ceil_div(m, vb);
   for (int64_t I = 0; I < nvb; ++I) {
     int64_t i0 = I * vb, i1 = (i0 + vb < m) ? i0 + vb : m;
@@ -115,12 +130,14 @@ void oracle_encode_A(int64_t m, int64_t k, const double* A, int64_t lda, int64_t
   }
   if (p > 0) {
     int64_t bs = m / p;
-    for (int64_t t = 0; t < bs; ++t)
-      for (int64_t l = 0; l < k; ++l) {
-        double s = 0.0;
-        for (int64_t I = 0; I < p; ++I) s += A[(I * bs + t) * lda + l];
-        acs[(2 * nvb + t) * k + l] = s;
-      }
+    if (f < 1) f = 1;
+    for (int64_t c = 0; c < f; ++c)
+      for (int64_t t = 0; t < bs; ++t)
+        for (int64_t l = 0; l < k; ++l) {
+          double s = 0.0;
+          for (int64_t I = 0; I < p; ++I) s += oracle_block_coef(c, I, p) * A[(I * bs + t) * lda + l];
+          acs[(2 * nvb + c * bs + t) * k + l] = s;
+        }
   }
 }
 
@@ -233,7 +250,7 @@ typedef struct {
   double u_cs;        /* relative representation error of the checksum operand */
   double s;           /* safety factor */
   int32_t round_f32;  /* corrected values are rounded to binary32 */
-  int32_t pad;
+  int32_t f;          /* block checksum rows of the erasure grid (0 means 1) */
 } oracle_cfg;
 
 typedef struct {
@@ -701,6 +718,100 @@ int oracle_recover_block(const oracle_cfg* c, double* C, int64_t ldc, const doub
   }
   *n_flagged = nfl;
   return nfl ? ST_UNCORRECTABLE : ST_OK;
+}
+
+/* Erasure recovery of several blocks (section 2.1: the lost parts follow from
+ * the checksums and the surviving parts; with f checksums, f lost blocks of a
+ * block column).  The listed blocks (bi, bj pairs) are grouped by block
+ * column; for a column J with t <= f erased block rows I_1..I_t, every element
+ * position (r, j) of the column's blocks solves
+ *   sum_u c_{l,I_u} C[I_u*bs + r][j] = S^(l)[r][j] - sum_{I not erased} c_{l,I} C[I*bs + r][j],
+ *   l = 0 .. t-1,
+ * by Gaussian elimination with partial pivoting in binary64 (rounded to
+ * binary32 for a binary32 C).  A column with more erasures than f is left
+ * untouched and reported (ST_UNCORRECTABLE).  Then every column line of the
+ * rebuilt blocks is verified again; *n_flagged counts the lines still flagged.
+ * Pinned by exact recovery of every subset of up to f blocks on integer
+ * data, and by the single-block case agreeing with the plain sum. */
+int oracle_recover_blocks(const oracle_cfg* c, double* C, int64_t ldc, const double* E,
+                          const double* nBcol, const double* nAblk, const int32_t* blocks,
+                          int32_t nb, int32_t* n_flagged) {
+  int64_t m = c->m, n = c->n;
+  if (c->p <= 0 || c->q <= 0 || m % c->p || n % c->q || nb < 0) return ST_INVALID;
+  int64_t bs = m / c->p, bc = n / c->q, f = c->f > 0 ? c->f : 1;
+  for (int32_t u = 0; u < nb; ++u)
+    if (blocks[2 * u] < 0 || blocks[2 * u] >= c->p || blocks[2 * u + 1] < 0 ||
+        blocks[2 * u + 1] >= c->q)
+      return ST_INVALID;
+  int64_t nvr = ceil_div(m, c->vb_r);
+  const double* S = E + (2 * nvr) * n;
+  int status = ST_OK;
+  int32_t nfl = 0;
+  int64_t rows[8];
+  for (int64_t J = 0; J < c->q; ++J) {
+    int64_t t = 0;
+    int dup = 0;
+    for (int32_t u = 0; u < nb; ++u)
+      if (blocks[2 * u + 1] == J) {
+        for (int64_t v = 0; v < t && v < 8; ++v) dup |= rows[v] == blocks[2 * u];
+        if (t < 8) rows[t] = blocks[2 * u];
+        ++t;
+      }
+    if (t == 0) continue;
+    if (dup || t > f || t > 8) { status = ST_UNCORRECTABLE; continue; }
+    for (int64_t r = 0; r < bs; ++r)
+      for (int64_t j = J * bc; j < (J + 1) * bc; ++j) {
+        double M[8][9];
+        for (int64_t l = 0; l < t; ++l) {
+          double rhs = S[(l * bs + r) * n + j];
+          for (int64_t I = 0; I < c->p; ++I) {
+            int erased = 0;
+            for (int64_t v = 0; v < t; ++v) erased |= rows[v] == I;
+            if (!erased) rhs -= oracle_block_coef(l, I, c->p) * C[(I * bs + r) * ldc + j];
+          }
+          for (int64_t v = 0; v < t; ++v) M[l][v] = oracle_block_coef(l, rows[v], c->p);
+          M[l][t] = rhs;
+        }
+        /* Gaussian elimination with partial pivoting */
+        for (int64_t col = 0; col < t; ++col) {
+          int64_t piv = col;
+          for (int64_t i = col + 1; i < t; ++i)
+            if (fabs(M[i][col]) > fabs(M[piv][col])) piv = i;
+          for (int64_t x = 0; x <= t; ++x) {
+            double tmp = M[col][x];
+            M[col][x] = M[piv][x];
+            M[piv][x] = tmp;
+          }
+          for (int64_t i = col + 1; i < t; ++i) {
+            double fct = M[i][col] / M[col][col];
+            for (int64_t x = col; x <= t; ++x) M[i][x] -= fct * M[col][x];
+          }
+        }
+        double x[8];
+        for (int64_t i = t - 1; i >= 0; --i) {
+          double v = M[i][t];
+          for (int64_t y = i + 1; y < t; ++y) v -= M[i][y] * x[y];
+          x[i] = v / M[i][i];
+        }
+        for (int64_t v = 0; v < t; ++v) {
+          double val = x[v];
+          if (c->round_f32) val = (double)(float)val;
+          C[(rows[v] * bs + r) * ldc + j] = val;
+        }
+      }
+    /* re-verify the rebuilt blocks' column lines */
+    for (int64_t v = 0; v < t; ++v) {
+      int64_t vb = c->vb_r, bi = rows[v];
+      for (int64_t I = (bi * bs) / vb; I < ceil_div((bi + 1) * bs, vb); ++I)
+        for (int64_t j = J * bc; j < (J + 1) * bc; ++j) {
+          double re, rw;
+          if (col_line_flagged(c, C, ldc, E, nBcol, nAblk, I, j, &re, &rw)) ++nfl;
+        }
+    }
+  }
+  *n_flagged = nfl;
+  if (nfl) status = ST_UNCORRECTABLE;
+  return status;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -329,3 +329,97 @@ def test_e4m3_decode():
     got = np.array([oracle.e4m3_value(b) for b in range(256)])
     fin = np.isfinite(ref)
     assert np.array_equal(got[fin], ref[fin]) and np.all(np.isnan(got[~fin]))
+
+
+# ---- several block checksums (section 2.1: f checksums recover f lost blocks)
+
+def test_block_coefficients_vandermonde():
+    """c_{l,I} = x_I^l with distinct dyadic nodes x_I = (I+1)/2^e, 2^e > p: l = 0 is the
+    plain sum, values are exact, and every f x f minor is nonsingular."""
+    import itertools
+    p = 22
+    for I in range(p):
+        assert oracle.block_coef(0, I, p) == 1.0
+        assert oracle.block_coef(1, I, p) == (I + 1) / 32.0
+        assert oracle.block_coef(3, I, p) == ((I + 1) / 32.0) ** 3   # exact: dyadic
+    p = 7
+    for f in (2, 3, 4):
+        Mfull = np.array([[oracle.block_coef(l, I, p) for I in range(p)] for l in range(f)])
+        for cols in itertools.combinations(range(p), f):
+            assert abs(np.linalg.det(Mfull[:, cols])) > 0
+
+
+def _int_problem(seed, m, k, n):
+    g = wl.rng(seed)
+    return (g.integers(-4, 5, (m, k)).astype(float), g.integers(-4, 5, (k, n)).astype(float))
+
+
+def test_block_checksum_rows_invariant_exact():
+    """S^(l) B = sum_I c_{l,I} C_I exactly on integer data, for every l < f."""
+    A, B = _int_problem(20, 12, 7, 9)
+    f, p = 3, 4
+    enc = oracle.Encoded(A, B, 3, 3, p, 3, f=f)
+    C = oracle.gemm(A, B)
+    bs, nvr = 12 // p, 4
+    for l in range(f):
+        S = enc.acs[2 * nvr + l * bs: 2 * nvr + (l + 1) * bs]
+        ref = sum(oracle.block_coef(l, I, p) * C[I * bs:(I + 1) * bs] for I in range(p))
+        assert np.array_equal(oracle.gemm(S, B), ref)
+        assert np.array_equal(enc.E[2 * nvr + l * bs: 2 * nvr + (l + 1) * bs], ref)
+
+
+def test_multi_erasure_every_subset_integer_data():
+    """Every subset of up to f = 3 erased block rows of a block column (and one more block
+    in another column) is rebuilt to the exact integer product."""
+    import itertools
+    A, B = _int_problem(21, 16, 7, 9)
+    p, q, f = 4, 3, 3
+    enc = oracle.Encoded(A, B, 4, 3, p, q, f=f)
+    C = oracle.gemm(A, B)
+    for J in range(q):
+        other = (0, (J + 1) % q)
+        for t in (1, 2, 3):
+            for rows in itertools.combinations(range(p), t):
+                blocks = [(r, J) for r in rows] + [other]
+                Ce = C.copy()
+                for bi, bj in blocks:
+                    Ce[4 * bi:4 * bi + 4, 3 * bj:3 * bj + 3] = np.nan
+                st, rep, Cv, n = enc.verify_correct(Ce, erased=blocks)
+                assert st == oracle.ST_OK and n == 0
+                st, Cr, nfl = enc.recover_blocks(Cv, blocks)
+                assert st == oracle.ST_OK and nfl == 0
+                assert np.allclose(Cr, C, rtol=0, atol=1e-9) and np.array_equal(np.rint(Cr), C)
+
+
+def test_multi_erasure_random_data_and_single_block_agrees():
+    w = wl.Workload("t", "f64", 96, 96, 64, 16, 16, 6, 6, dist="normal")
+    A, B = wl.operands(w, 12)
+    enc2 = oracle.Encoded(A, B, 16, 16, 6, 6, f=2)
+    enc1 = oracle.Encoded(A, B, 16, 16, 6, 6)
+    C = oracle.gemm(A, B)
+    Ce = C.copy()
+    Ce[32:48, 16:32] = np.nan
+    Ce[80:96, 16:32] = np.nan          # two blocks of block column 1
+    st, Cr, nfl = enc2.recover_blocks(Ce, [(2, 1), (5, 1)])
+    assert st == oracle.ST_OK and nfl == 0
+    blk = np.s_[32:48, 16:32], np.s_[80:96, 16:32]
+    for b in blk:
+        assert np.linalg.norm(Cr[b] - C[b]) <= 1e-12 * np.linalg.norm(C[b])
+    # one erased block: the first checksum (the plain sum) alone, as with f = 1
+    Ce = C.copy()
+    Ce[32:48, 16:32] = np.nan
+    st2, Cr2, _ = enc2.recover_blocks(Ce, [(2, 1)])
+    st1, Cr1, _ = enc1.recover_block(Ce, 2, 1)
+    assert st1 == st2 == oracle.ST_OK
+    assert np.allclose(Cr2, Cr1, rtol=1e-13, atol=1e-13)
+
+
+def test_more_erasures_than_checksums_is_uncorrectable():
+    A, B = _int_problem(22, 12, 7, 9)
+    enc = oracle.Encoded(A, B, 3, 3, 4, 3, f=2)
+    C = oracle.gemm(A, B)
+    Ce = C.copy()
+    for bi in (0, 1, 3):
+        Ce[3 * bi:3 * bi + 3, 0:3] = np.nan
+    st, Cr, nfl = enc.recover_blocks(Ce, [(0, 0), (1, 0), (3, 0)])
+    assert st == oracle.ST_UNCORRECTABLE and np.isnan(Cr[0:3, 0:3]).all()

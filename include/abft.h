@@ -77,6 +77,9 @@ typedef struct {
   int32_t grid_q;        /* erasure grid block-columns (with grid_p > 0)           */
   int32_t flags;         /* reserved, must be 0                                    */
   double tau_safety;     /* safety factor s of the detection threshold; 0 -> 4     */
+  int32_t grid_f;        /* block checksums of the erasure grid, 1..4 (0 -> 1): up
+                            to grid_f erased blocks per block column are rebuilt  */
+  int32_t reserved;      /* must be 0                                              */
 } abft_desc;
 
 /* One report entry.  row/col are element coordinates; -1 marks the unknown
@@ -225,6 +228,22 @@ abft_status abft_verify_correct(const abft_desc* desc, void* C, void* ws, int32_
  * rebuilt block fails its checks. */
 abft_status abft_recover_block(const abft_desc* desc, void* C, void* ws, int32_t bi, int32_t bj,
                                abft_fault* report_entry, void* stream);
+
+/* Several erased blocks at once (section 2.1: with f block checksums, f lost
+ * blocks of a block column follow from the checksums and the survivors).  The
+ * grid carries grid_f block checksums S^(l) = sum_I c_{l,I} A_I (B), l < f, with
+ * c_{l,I} = x_I^l, x_I = (I+1) / 2^e, 2^e > grid_p (distinct nodes: every
+ * f x f minor is nonsingular; l = 0 is the plain sum).  blocks: host (bi, bj)
+ * pairs, n_blocks <= 16, each listed once; a block column with t erased blocks
+ * solves, for every element position, the t x t system of its first t
+ * checksums in binary64 (the inverse is formed on the host), then the rebuilt
+ * blocks' column lines are checked again.  report (host, n_blocks entries, may
+ * be NULL) receives one kind-4 entry per block.  ABFT_ERR_UNCORRECTABLE, with
+ * nothing launched, when a block column has more erased blocks than grid_f;
+ * ABFT_ERR_UNCORRECTABLE also when a rebuilt block fails its checks.
+ * SYNCHRONISES `stream`. */
+abft_status abft_recover_blocks(const abft_desc* desc, void* C, void* ws, const int32_t* blocks,
+                                int32_t n_blocks, abft_fault* report, void* stream);
 
 /* Fault injection for tests and benchmarks (the paper's stress test kills
  * processes, section 4.3; here faults are bit flips and erasures chosen on the

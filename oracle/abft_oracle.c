@@ -763,12 +763,13 @@ int oracle_recover_blocks(const oracle_cfg* c, double* C, int64_t ldc, const dou
       for (int64_t j = J * bc; j < (J + 1) * bc; ++j) {
         double M[8][9];
         for (int64_t l = 0; l < t; ++l) {
-          double rhs = S[(l * bs + r) * n + j];
+          double sum = 0.0; /* the survivors, then checksum minus their sum */
           for (int64_t I = 0; I < c->p; ++I) {
             int erased = 0;
             for (int64_t v = 0; v < t; ++v) erased |= rows[v] == I;
-            if (!erased) rhs -= oracle_block_coef(l, I, c->p) * C[(I * bs + r) * ldc + j];
+            if (!erased) sum += oracle_block_coef(l, I, c->p) * C[(I * bs + r) * ldc + j];
           }
+          double rhs = S[(l * bs + r) * n + j] - sum;
           for (int64_t v = 0; v < t; ++v) M[l][v] = oracle_block_coef(l, rows[v], c->p);
           M[l][t] = rhs;
         }

@@ -23,7 +23,7 @@ KIND_CORRECTED, KIND_NONFINITE_CORRECTED, KIND_UNCORRECTABLE, KIND_BLOCK_RECOVER
 # Every symbol include/abft.h declares.
 EXPORTS = ("abft_workspace_bytes", "abft_workspace_layout", "abft_encode",
            "abft_encode_noalloc", "abft_gemm", "abft_set_epilogue_faults",
-           "abft_gemm_plain", "abft_verify_correct", "abft_recover_block",
+           "abft_gemm_plain", "abft_verify_correct", "abft_recover_block", "abft_recover_blocks",
            "abft_inject_bitflips", "abft_erase_block", "abft_kernel_launches",
            "abft_last_error", "abft_version",
            "abft_group_create", "abft_group_workspace_bytes", "abft_group_problem_layout",
@@ -45,7 +45,7 @@ class Desc(ct.Structure):
                 ("lda", ct.c_int64), ("ldb", ct.c_int64), ("ldc", ct.c_int64),
                 ("dtype", ct.c_int32), ("vb_rows", ct.c_int32), ("vb_cols", ct.c_int32),
                 ("grid_p", ct.c_int32), ("grid_q", ct.c_int32), ("flags", ct.c_int32),
-                ("tau_safety", ct.c_double)]
+                ("tau_safety", ct.c_double), ("grid_f", ct.c_int32), ("reserved", ct.c_int32)]
 
 
 class Fault(ct.Structure):
@@ -114,6 +114,7 @@ def load(path: str = LIB_PATH):
         lib.abft_verify_correct.argtypes = [D, vp, vp, i32, vp, i32, vp, i32,
                                             ct.POINTER(ct.c_int32), vp]
         lib.abft_recover_block.argtypes = [D, vp, vp, i32, i32, ct.POINTER(Fault), vp]
+        lib.abft_recover_blocks.argtypes = [D, vp, vp, vp, i32, vp, vp]
         lib.abft_inject_bitflips.argtypes = [D, vp, vp, vp, vp, i32, vp]
         lib.abft_erase_block.argtypes = [D, vp, i32, i32, vp]
         lib.abft_last_error.restype = ct.c_char_p
@@ -171,11 +172,12 @@ def _check(st: int, allow=(OK,)):
 
 
 def make_desc(m, n, k, dtype="f64", vb_rows=None, vb_cols=None, grid_p=0, grid_q=0,
-              lda=None, ldb=None, ldc=None, tau_safety=0.0) -> Desc:
+              lda=None, ldb=None, ldc=None, tau_safety=0.0, grid_f=0) -> Desc:
     code = DTYPE_CODES[dtype] if isinstance(dtype, str) else int(dtype)
     return Desc(m=m, n=n, k=k, lda=lda or max(k, 1), ldb=ldb or max(n, 1), ldc=ldc or max(n, 1),
                 dtype=code, vb_rows=vb_rows or max(m, 1), vb_cols=vb_cols or max(n, 1),
-                grid_p=grid_p, grid_q=grid_q, flags=0, tau_safety=tau_safety)
+                grid_p=grid_p, grid_q=grid_q, flags=0, tau_safety=tau_safety, grid_f=grid_f,
+                reserved=0)
 
 
 def abft_workspace_bytes(desc: Desc) -> int:
@@ -233,6 +235,18 @@ def abft_recover_block(desc, C, ws, bi, bj, stream=None):
                                    _stream(stream))
     _check(st, allow=(OK, ERR_UNCORRECTABLE))
     return st, f.as_dict()
+
+
+def abft_recover_blocks(desc, C, ws, blocks, stream=None):
+    """Rebuild several erased blocks [(bi, bj), ...] (up to grid_f per block column).
+    Returns (status, [report entry dicts]).  Synchronises the stream."""
+    n = len(blocks)
+    arr = (ct.c_int32 * max(1, 2 * n))(*[v for b in blocks for v in b])
+    rep = (Fault * max(1, n))()
+    st = load().abft_recover_blocks(ct.byref(desc), _ptr(C), _ptr(ws), ct.cast(arr, ct.c_void_p),
+                                    n, ct.cast(rep, ct.c_void_p), _stream(stream))
+    _check(st, allow=(OK, ERR_UNCORRECTABLE))
+    return st, [r.as_dict() for r in rep[:n]]
 
 
 def abft_inject_bitflips(desc, C, flips, stream=None):

@@ -92,7 +92,11 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
     return fail(ABFT_ERR_INVALID, "erasure grid: grid_p and grid_q both 0 or both > 0");
   if (d->grid_p > 0 && (d->m % d->grid_p || d->n % d->grid_q))
     return fail(ABFT_ERR_INVALID, "erasure grid must divide m and n");
-  if (d->flags != 0) return fail(ABFT_ERR_INVALID, "flags must be 0");
+  if (d->flags != 0 || d->reserved != 0) return fail(ABFT_ERR_INVALID, "flags must be 0");
+  if (d->grid_f < 0 || d->grid_f > kMaxBlockChecksums)
+    return fail(ABFT_ERR_INVALID, "grid_f must be in [0, %d]", kMaxBlockChecksums);
+  if (d->grid_p > 0 && d->grid_f > d->grid_p)
+    return fail(ABFT_ERR_INVALID, "grid_f larger than the number of block rows");
   if (!(d->tau_safety >= 0.0) || !isfinite(d->tau_safety))
     return fail(ABFT_ERR_INVALID, "tau_safety must be finite and >= 0");
 
@@ -106,7 +110,8 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
   p.nvc = d->n > 0 ? cdiv(d->n, d->vb_cols) : 0;
   p.bs = d->grid_p > 0 ? d->m / d->grid_p : 0;
   p.bc = d->grid_q > 0 ? d->n / d->grid_q : 0;
-  p.R = 2 * p.nvr + p.bs;
+  p.f = d->grid_f > 0 ? d->grid_f : 1;
+  p.R = 2 * p.nvr + p.f * p.bs;
   p.Cc = 2 * p.nvc;
   p.er = ceil_log2(d->vb_rows);
   p.ec = ceil_log2(d->vb_cols);
@@ -133,7 +138,7 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
   // per block-checksum row).  BF16X3: hi and lo planes of 2 rows per block
   // (the split product combines them).  Rows are 16-byte aligned.
   L.planes = x3 ? nsplit : 1;
-  L.acs_rows = x3 ? p.R : (lp ? 4 * p.nvr + 2 * p.bs : p.R);
+  L.acs_rows = x3 ? p.R : (lp ? 4 * p.nvr + 2 * p.f * p.bs : p.R);
   L.bcs_cols = x3 ? p.Cc : (lp ? 4 * p.nvc : p.Cc);
   L.acs_ld = lp ? (d->k + 7) / 8 * 8 : d->k;
   L.bcs_ld = lp ? (L.bcs_cols + 7) / 8 * 8 : p.Cc;
@@ -414,35 +419,100 @@ abft_status abft_verify_correct(const abft_desc* desc, void* C, void* ws, int32_
   return ABFT_OK;
 }
 
-abft_status abft_recover_block(const abft_desc* desc, void* C, void* ws, int32_t bi, int32_t bj,
-                               abft_fault* report_entry, void* stream) {
+// Inverse of the t x t matrix M[l][u] = block_coef(l, rows[u], p) (Gauss-Jordan
+// with partial pivoting, binary64).  False when it is singular (repeated rows).
+static bool invert_block_coefs(const int* rows, int t, int p, double* inv) {
+  double a[kMaxBlockChecksums][2 * kMaxBlockChecksums];
+  for (int l = 0; l < t; ++l)
+    for (int u = 0; u < 2 * t; ++u)
+      a[l][u] = u < t ? block_coef(l, rows[u], p) : (u - t == l ? 1.0 : 0.0);
+  for (int c = 0; c < t; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < t; ++i)
+      if (fabs(a[i][c]) > fabs(a[piv][c])) piv = i;
+    if (!(fabs(a[piv][c]) > 0.0)) return false;
+    for (int x = 0; x < 2 * t; ++x) std::swap(a[c][x], a[piv][x]);
+    const double d = a[c][c];
+    for (int x = 0; x < 2 * t; ++x) a[c][x] /= d;
+    for (int i = 0; i < t; ++i)
+      if (i != c) {
+        const double f = a[i][c];
+        for (int x = 0; x < 2 * t; ++x) a[i][x] -= f * a[c][x];
+      }
+  }
+  for (int u = 0; u < t; ++u)
+    for (int l = 0; l < t; ++l) inv[u * t + l] = a[u][t + l];
+  return true;
+}
+
+abft_status abft_recover_blocks(const abft_desc* desc, void* C, void* ws, const int32_t* blocks,
+                                int32_t n_blocks, abft_fault* report, void* stream) {
   Plan P;
   abft_status st = make_plan(desc, &P);
   if (st != ABFT_OK) return st;
   if (P.bs == 0) return fail(ABFT_ERR_INVALID, "no erasure grid in the descriptor");
-  if (bi < 0 || bj < 0 || bi >= P.d.grid_p || bj >= P.d.grid_q)
-    return fail(ABFT_ERR_INVALID, "block (%d, %d) outside the erasure grid", bi, bj);
+  if (n_blocks < 0 || n_blocks > kMaxErased || (n_blocks > 0 && !blocks))
+    return fail(ABFT_ERR_INVALID, "n_blocks must be in [0, %d]", kMaxErased);
+  for (int u = 0; u < n_blocks; ++u) {
+    const int bi = blocks[2 * u], bj = blocks[2 * u + 1];
+    if (bi < 0 || bj < 0 || bi >= P.d.grid_p || bj >= P.d.grid_q)
+      return fail(ABFT_ERR_INVALID, "block (%d, %d) outside the erasure grid", bi, bj);
+    for (int v = 0; v < u; ++v)
+      if (blocks[2 * v] == bi && blocks[2 * v + 1] == bj)
+        return fail(ABFT_ERR_INVALID, "block (%d, %d) listed twice", bi, bj);
+  }
+  // group by block column; more erasures in a column than block checksums
+  // cannot be rebuilt
+  std::vector<int> cols;
+  for (int u = 0; u < n_blocks; ++u)
+    if (std::find(cols.begin(), cols.end(), blocks[2 * u + 1]) == cols.end())
+      cols.push_back(blocks[2 * u + 1]);
+  for (int bj : cols) {
+    int t = 0;
+    for (int u = 0; u < n_blocks; ++u) t += blocks[2 * u + 1] == bj;
+    if (t > P.f)
+      return fail(ABFT_ERR_UNCORRECTABLE,
+                  "%d erased blocks in block column %d, more than the %d block checksums", t, bj,
+                  P.f);
+  }
+  if (n_blocks == 0) return ABFT_OK;
   if (!C || !ws) return fail(ABFT_ERR_INVALID, "NULL pointer");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Scratch S = scratch_view(P, ws);
   cudaError_t e = cudaMemsetAsync(S.cnt + kCntRecoverFlagged, 0, sizeof(int32_t), s);
-  if (e == cudaSuccess) e = launch_recover(P, C, ws, bi, bj, s);
+  for (int bj : cols) {
+    if (e != cudaSuccess) break;
+    int rows[kMaxBlockChecksums], t = 0;
+    for (int u = 0; u < n_blocks; ++u)
+      if (blocks[2 * u + 1] == bj) rows[t++] = blocks[2 * u];
+    double minv[kMaxBlockChecksums * kMaxBlockChecksums];
+    if (!invert_block_coefs(rows, t, P.d.grid_p, minv))
+      return fail(ABFT_ERR_INVALID, "singular block-checksum system in block column %d", bj);
+    e = launch_recover(P, C, ws, bj, rows, t, minv, s);
+  }
   int32_t nfl = 0;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&nfl, S.cnt + kCntRecoverFlagged, sizeof nfl, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(e, "abft_recover_block");
-  if (report_entry) {
-    report_entry->row = (int32_t)(bi * P.bs);
-    report_entry->col = (int32_t)(bj * P.bc);
-    report_entry->kind = ABFT_KIND_BLOCK_RECOVERED;
-    report_entry->side = 2;
-    report_entry->delta = 0.0;
-    report_entry->r_e = (double)nfl;
-    report_entry->r_w = 0.0;
-  }
-  if (nfl) return fail(ABFT_ERR_UNCORRECTABLE, "rebuilt block fails %d column checks", nfl);
+  if (e != cudaSuccess) return cuda_fail(e, "abft_recover_blocks");
+  if (report)
+    for (int u = 0; u < n_blocks; ++u) {
+      abft_fault f{};
+      f.row = (int32_t)(blocks[2 * u] * P.bs);
+      f.col = (int32_t)(blocks[2 * u + 1] * P.bc);
+      f.kind = ABFT_KIND_BLOCK_RECOVERED;
+      f.side = 2;
+      f.r_e = (double)nfl;
+      report[u] = f;
+    }
+  if (nfl) return fail(ABFT_ERR_UNCORRECTABLE, "rebuilt blocks fail %d column checks", nfl);
   return ABFT_OK;
+}
+
+abft_status abft_recover_block(const abft_desc* desc, void* C, void* ws, int32_t bi, int32_t bj,
+                               abft_fault* report_entry, void* stream) {
+  const int32_t blk[2] = {bi, bj};
+  return abft_recover_blocks(desc, C, ws, blk, 1, report_entry, stream);
 }
 
 abft_status abft_inject_bitflips(const abft_desc* desc, void* C, const int64_t* rows,

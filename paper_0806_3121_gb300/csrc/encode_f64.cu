@@ -69,14 +69,17 @@ __global__ void __launch_bounds__(kThreads) k_encA_cols(const double* __restrict
 // Block checksum rows S_A[t] = sum_I A[I*bs + t] (erasure grid).
 // Grid (ceil(k/256), bs).
 __global__ void __launch_bounds__(kThreads) k_encA_block(const double* __restrict__ A, int64_t lda,
-                                                         int64_t k, int p, int64_t bs,
+                                                         int64_t k, int p, int64_t bs, int f,
                                                          double* __restrict__ S) {
   const int64_t l = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (l >= k) return;
-  for (int64_t t = blockIdx.y; t < bs; t += gridDim.y) {
+  // row c*bs + t of S: sum_I c_{c,I} A[I*bs + t] (block checksum c of the grid)
+  for (int64_t ct = blockIdx.y; ct < f * bs; ct += gridDim.y) {
+    const int c = (int)(ct / bs);
+    const int64_t t = ct - c * bs;
     double s = 0.0;
-    for (int I = 0; I < p; ++I) s += A[(I * bs + t) * lda + l];
-    S[t * k + l] = s;
+    for (int I = 0; I < p; ++I) s += block_coef(c, I, p) * A[(I * bs + t) * lda + l];
+    S[ct * k + l] = s;
   }
 }
 
@@ -224,8 +227,8 @@ cudaError_t launch_encode_f64(const Plan& P, const double* A, const double* B, v
   k_encA_cols<<<dim3((unsigned)nchA, gy(P.nvr)), kThreads, 0, st>>>(
       A, d.lda, d.m, d.k, d.vb_rows, P.er, acs, partA, nchA);
   if (P.bs > 0)
-    k_encA_block<<<dim3((unsigned)cdiv(d.k, kThreads), gy(P.bs)), kThreads, 0, st>>>(
-        A, d.lda, d.k, d.grid_p, P.bs, acs + 2 * P.nvr * d.k);
+    k_encA_block<<<dim3((unsigned)cdiv(d.k, kThreads), gy(P.f * P.bs)), kThreads, 0, st>>>(
+        A, d.lda, d.k, d.grid_p, P.bs, P.f, acs + 2 * P.nvr * d.k);
   k_row_norms<<<(unsigned)cdiv(d.m * 32, kThreads), kThreads, 0, st>>>(A, d.lda, d.m, d.k, nArow);
   k_encB_rows<<<dim3((unsigned)cdiv(nchB, kThreads / 32), gy(P.nvc)), kThreads, 0, st>>>(
       B, d.ldb, d.k, d.n, d.vb_cols, P.ec, bcs, P.Cc, partB, nchB);
@@ -312,8 +315,8 @@ cudaError_t launch_encode_f64_noalloc(const Plan& P, const double* A, const doub
   k_encA_cols<<<dim3((unsigned)nchA, gy(P.nvr)), kThreads, 0, st>>>(
       A, d.lda, d.m, d.k, d.vb_rows, P.er, acs, partA, nchA);
   if (P.bs > 0)
-    k_encA_block<<<dim3((unsigned)cdiv(d.k, kThreads), gy(P.bs)), kThreads, 0, st>>>(
-        A, d.lda, d.k, d.grid_p, P.bs, acs + 2 * P.nvr * d.k);
+    k_encA_block<<<dim3((unsigned)cdiv(d.k, kThreads), gy(P.f * P.bs)), kThreads, 0, st>>>(
+        A, d.lda, d.k, d.grid_p, P.bs, P.f, acs + 2 * P.nvr * d.k);
   k_row_norms<<<(unsigned)cdiv(d.m * 32, kThreads), kThreads, 0, st>>>(A, d.lda, d.m, d.k, nArow);
   k_encB_rows<<<dim3((unsigned)cdiv(nchB, kThreads / 32), gy(P.nvc)), kThreads, 0, st>>>(
       B, d.ldb, d.k, d.n, d.vb_cols, P.ec, bcs, P.Cc, partB, nchB);

@@ -196,20 +196,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_lpA_cols(const __nv_bfloat16* _
     lpA_unit(A, lda, m, k, vb, e, acs, ldk, rowpart, nchr, part, blockIdx.x, I, red, sh);
 }
 
-// Block checksum rows S_A[t] = sum_I A[I*bs + t], as hi/lo pieces.
+// Block checksum rows S^(c)[t] = sum_I c_{c,I} A[I*bs + t] (c < f), fp32 sums
+// as hi/lo pieces: row c*bs + t of the block checksums -> rows 2 (c*bs + t),
+// 2 (c*bs + t) + 1 of S.
 __global__ void __launch_bounds__(kThreads) k_lpA_block(const __nv_bfloat16* __restrict__ A,
                                                         int64_t lda, int64_t k, int p, int64_t bs,
-                                                        __nv_bfloat16* __restrict__ S,
+                                                        int f, __nv_bfloat16* __restrict__ S,
                                                         int64_t ldk) {
   const int64_t l = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (l >= k) return;
-  for (int64_t t = blockIdx.y; t < bs; t += gridDim.y) {
+  for (int64_t ct = blockIdx.y; ct < f * bs; ct += gridDim.y) {
+    const int c = (int)(ct / bs);
+    const int64_t t = ct - c * bs;
     float s = 0.f;
-    for (int I = 0; I < p; ++I) s += ldf(A + (I * bs + t) * lda + l);
+    for (int I = 0; I < p; ++I) s = fmaf((float)block_coef(c, I, p), ldf(A + (I * bs + t) * lda + l), s);
     __nv_bfloat16 h, lo;
     split(s, h, lo);
-    S[(2 * t) * ldk + l] = h;
-    S[(2 * t + 1) * ldk + l] = lo;
+    S[(2 * ct) * ldk + l] = h;
+    S[(2 * ct + 1) * ldk + l] = lo;
   }
 }
 
@@ -521,17 +525,19 @@ __global__ void __launch_bounds__(kThreads) k_x3A_cols(const float* __restrict__
   }
 }
 
-// Block checksum rows S_A[t] = sum_I A[I*bs + t] into rows 2 nvr + t of the
-// planes (cs points at row 2 nvr of each plane).
+// Block checksum rows S^(c)[t] = sum_I c_{c,I} A[I*bs + t] (c < f) into rows
+// 2 nvr + c*bs + t of the planes (cs points at row 2 nvr of each plane).
 __global__ void __launch_bounds__(kThreads) k_x3A_block(const float* __restrict__ A, int64_t lda,
-                                                        int64_t k, int p, int64_t bs,
+                                                        int64_t k, int p, int64_t bs, int f,
                                                         const Planes cs, int64_t ldk) {
   const int64_t l = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (l >= k) return;
-  for (int64_t t = blockIdx.y; t < bs; t += gridDim.y) {
+  for (int64_t ct = blockIdx.y; ct < f * bs; ct += gridDim.y) {
+    const int c = (int)(ct / bs);
+    const int64_t t = ct - c * bs;
     float s = 0.f;
-    for (int I = 0; I < p; ++I) s += A[(I * bs + t) * lda + l];
-    store_split1(cs, t * ldk + l, s);
+    for (int I = 0; I < p; ++I) s = fmaf((float)block_coef(c, I, p), A[(I * bs + t) * lda + l], s);
+    store_split1(cs, ct * ldk + l, s);
   }
 }
 
@@ -788,8 +794,8 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, cons
     if (P.bs > 0) {
       Planes sp = acsp;
       for (int i = 0; i < np; ++i) sp.p[i] += 2 * P.nvr * P.L.acs_ld;
-      k_x3A_block<<<dim3((unsigned)cdiv(d.k, kThreads), gy(P.bs)), kThreads, 0, st>>>(
-          Af, d.lda, d.k, d.grid_p, P.bs, sp, P.L.acs_ld);
+      k_x3A_block<<<dim3((unsigned)cdiv(d.k, kThreads), gy(P.f * P.bs)), kThreads, 0, st>>>(
+          Af, d.lda, d.k, d.grid_p, P.bs, P.f, sp, P.L.acs_ld);
     }
     k_lp_norms<<<(unsigned)cdiv(d.m, 128), 128, 0, st>>>(rowpart, d.m, nchr, nchr, 1, nArow);
     k_lp_blk<<<(unsigned)cdiv(P.nvr, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA,
@@ -834,8 +840,8 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, cons
   k_lpA_cols<<<dim3((unsigned)cdiv(P.L.acs_ld, kEncCols), gy(P.nvr)), kThreads, 0, st>>>(
       A, lda, d.m, d.k, d.vb_rows, P.er, acs, P.L.acs_ld, rowpart, nchr, partA);
   if (P.bs > 0)
-    k_lpA_block<<<dim3((unsigned)cdiv(d.k, kThreads), gy(P.bs)), kThreads, 0, st>>>(
-        A, lda, d.k, d.grid_p, P.bs, acs + 4 * P.nvr * P.L.acs_ld, P.L.acs_ld);
+    k_lpA_block<<<dim3((unsigned)cdiv(d.k, kThreads), gy(P.f * P.bs)), kThreads, 0, st>>>(
+        A, lda, d.k, d.grid_p, P.bs, P.f, acs + 4 * P.nvr * P.L.acs_ld, P.L.acs_ld);
   k_lp_norms<<<(unsigned)cdiv(d.m, 128), 128, 0, st>>>(rowpart, d.m, nchr, nchr, 1, nArow);
   k_lp_blk<<<(unsigned)cdiv(P.nvr, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA, nchr,
                                                        nAblk);

@@ -4,6 +4,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "../../include/abft.h"
@@ -15,6 +16,19 @@ constexpr int kCapFlags = 4096;    // flagged lines per side
 constexpr int kCapCands = 2048;    // candidates merged in shared memory
 constexpr int kCapReport = 16384;  // device report entries
 constexpr int kMaxErased = 16;     // erased blocks per verify call
+constexpr int kMaxBlockChecksums = 4;  // block checksums of an erasure grid (grid_f)
+
+// Coefficient of block row I in block checksum l of a p-block-row grid:
+// x_I^l with distinct dyadic nodes x_I = (I+1) / 2^e, 2^e > p (every f x f
+// minor of this Vandermonde matrix is nonsingular; l = 0 is the plain sum).
+__host__ __device__ inline double block_coef(int l, int I, int p) {
+  int e = 0;
+  while ((1 << e) <= p) ++e;
+  const double x = ldexp((double)(I + 1), -e);
+  double c = 1.0;
+  for (int t = 0; t < l; ++t) c *= x;
+  return c;
+}
 constexpr int kMaxInject = 256;    // armed epilogue fault injections
 
 // Counter slots in the scratch region.
@@ -51,6 +65,7 @@ struct Plan {
   int64_t nvr, nvc;  // verify blocks along rows / columns
   int64_t R, Cc;     // checksum rows of A / checksum columns of B
   int64_t bs, bc;    // erasure block rows / columns (0 when no grid)
+  int f;             // block checksums of the erasure grid (rows f * bs after the verify rows)
   int er, ec;        // ceil(log2(vb_rows)), ceil(log2(vb_cols))
   double s;          // safety factor
   double f1_col, f2_col, f1_row, f2_row;  // threshold factors
@@ -219,7 +234,11 @@ cudaError_t launch_verify(const Plan& P, void* C, void* ws, const Erased& er, bo
                           cudaStream_t st);
 cudaError_t launch_set_inject(const Plan& P, void* ws, const int64_t* rows, const int64_t* cols,
                               const int32_t* bits, int count, cudaStream_t st);
-cudaError_t launch_recover(const Plan& P, void* C, void* ws, int bi, int bj, cudaStream_t st);
+// Rebuilds the erased blocks rows[0..t) of block column bj from the first t
+// block checksums (t <= f): minv is the inverse of M[l][u] = block_coef(l,
+// rows[u], p), row-major t x t, in binary64.
+cudaError_t launch_recover(const Plan& P, void* C, void* ws, int bj, const int* rows, int t,
+                           const double* minv, cudaStream_t st);
 cudaError_t launch_inject(const Plan& P, void* C, const int64_t* rows, const int64_t* cols,
                           const int32_t* bits, int count, cudaStream_t st);
 cudaError_t launch_erase(const Plan& P, void* C, int bi, int bj, cudaStream_t st);

@@ -736,20 +736,56 @@ __global__ void __launch_bounds__(kLocThreads, 1) k_grp_locate(const GProb* prob
   locate_body(A, cnt, colf, rowf, cand, report);
 }
 
-// C[bi*bs + t][j] = S[t][j] - sum_{I != bi} C[I*bs + t][j], binary64.
+// Erased blocks rows[0..t) of block column bj (t <= kMaxBlockChecksums): for
+// every element position (r, j) of the column's blocks,
+//   rhs_l = S^(l)[r][j] - sum_{I not erased} c_{l,I} C[I*bs + r][j],   l < t,
+//   C[rows[u]*bs + r][j] = sum_l minv[u][l] rhs_l,
+// all in binary64 (t = 1: the block checksum minus the sum of the survivors).
 // Grid (ceil(bc/256), bs).
+struct RecoverSet {
+  int t;
+  int rows[kMaxBlockChecksums];
+  double minv[kMaxBlockChecksums * kMaxBlockChecksums];
+};
+
 template <typename TC>
 __global__ void __launch_bounds__(kThreads) k_recover(TC* C, int64_t ldc, const double* S,
                                                       int64_t n, int p, int64_t bs, int64_t bc,
-                                                      int bi, int bj) {
+                                                      int bj, const RecoverSet rs) {
   const int64_t jj = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (jj >= bc) return;
   const int64_t j = (int64_t)bj * bc + jj;
-  for (int64_t t = blockIdx.y; t < bs; t += gridDim.y) {
-    double s = 0.0;
-    for (int I = 0; I < p; ++I)
-      if (I != bi) s += (double)C[(I * bs + t) * ldc + j];
-    C[((int64_t)bi * bs + t) * ldc + j] = (TC)(S[t * n + j] - s);
+  int e = 0;
+  while ((1 << e) <= p) ++e;
+  for (int64_t r = blockIdx.y; r < bs; r += gridDim.y) {
+    double sum[kMaxBlockChecksums] = {0.0, 0.0, 0.0, 0.0};
+    for (int I = 0; I < p; ++I) {
+      bool erased = false;
+#pragma unroll
+      for (int u = 0; u < kMaxBlockChecksums; ++u) erased |= u < rs.t && rs.rows[u] == I;
+      if (erased) continue;
+      const double v = (double)C[(I * bs + r) * ldc + j];
+      const double x = ldexp((double)(I + 1), -e);
+      double c = 1.0;  // c_{l,I} = x^l
+#pragma unroll
+      for (int l = 0; l < kMaxBlockChecksums; ++l) {
+        if (l < rs.t) sum[l] += c * v;
+        c *= x;
+      }
+    }
+    double rhs[kMaxBlockChecksums];
+#pragma unroll
+    for (int l = 0; l < kMaxBlockChecksums; ++l)
+      rhs[l] = l < rs.t ? S[(l * bs + r) * n + j] - sum[l] : 0.0;
+#pragma unroll
+    for (int u = 0; u < kMaxBlockChecksums; ++u) {
+      if (u >= rs.t) break;
+      double xu = 0.0;
+#pragma unroll
+      for (int l = 0; l < kMaxBlockChecksums; ++l)
+        if (l < rs.t) xu += rs.minv[u * rs.t + l] * rhs[l];
+      C[((int64_t)rs.rows[u] * bs + r) * ldc + j] = (TC)xu;
+    }
   }
 }
 
@@ -821,16 +857,23 @@ cudaError_t verify_t(const Plan& P, void* C, void* ws, const Erased& er, bool re
 }
 
 template <typename TC>
-cudaError_t recover_t(const Plan& P, void* C, void* ws, int bi, int bj, cudaStream_t st) {
+cudaError_t recover_t(const Plan& P, void* C, void* ws, int bj, const int* rows, int t,
+                      const double* minv, cudaStream_t st) {
   CheckArgs a = make_args(P, C, ws);
   const double* S = a.E + 2 * P.nvr * P.d.n;
+  RecoverSet rs{};
+  rs.t = t;
+  for (int u = 0; u < t; ++u) rs.rows[u] = rows[u];
+  for (int x = 0; x < t * t; ++x) rs.minv[x] = minv[x];
   k_recover<TC><<<dim3((unsigned)cdiv(P.bc, kThreads), gy(P.bs)), kThreads, 0, st>>>(
-      static_cast<TC*>(C), P.d.ldc, S, P.d.n, P.d.grid_p, P.bs, P.bc, bi, bj);
-  const int64_t I0 = ((int64_t)bi * P.bs) / P.d.vb_rows;
-  const int64_t I1 = cdiv(((int64_t)bi + 1) * P.bs, P.d.vb_rows);
-  k_col_check<TC><<<dim3((unsigned)cdiv(P.bc, kThreads), gy(I1 - I0)), kThreads, 0, st>>>(
-      a, (int64_t)bj * P.bc, ((int64_t)bj + 1) * P.bc, I0, I1, 1);
-  count_launches(2);
+      static_cast<TC*>(C), P.d.ldc, S, P.d.n, P.d.grid_p, P.bs, P.bc, bj, rs);
+  for (int u = 0; u < t; ++u) {  // re-check the rebuilt blocks' column lines
+    const int64_t I0 = ((int64_t)rows[u] * P.bs) / P.d.vb_rows;
+    const int64_t I1 = cdiv(((int64_t)rows[u] + 1) * P.bs, P.d.vb_rows);
+    k_col_check<TC><<<dim3((unsigned)cdiv(P.bc, kThreads), gy(I1 - I0)), kThreads, 0, st>>>(
+        a, (int64_t)bj * P.bc, ((int64_t)bj + 1) * P.bc, I0, I1, 1);
+  }
+  count_launches(1 + t);
   return cudaGetLastError();
 }
 
@@ -884,9 +927,10 @@ cudaError_t launch_set_inject(const Plan& P, void* ws, const int64_t* rows, cons
   return launch_set_inject_raw(hdr, e, count, st);
 }
 
-cudaError_t launch_recover(const Plan& P, void* C, void* ws, int bi, int bj, cudaStream_t st) {
-  return P.d.dtype == ABFT_F64 ? recover_t<double>(P, C, ws, bi, bj, st)
-                               : recover_t<float>(P, C, ws, bi, bj, st);
+cudaError_t launch_recover(const Plan& P, void* C, void* ws, int bj, const int* rows, int t,
+                           const double* minv, cudaStream_t st) {
+  return P.d.dtype == ABFT_F64 ? recover_t<double>(P, C, ws, bj, rows, t, minv, st)
+                               : recover_t<float>(P, C, ws, bj, rows, t, minv, st);
 }
 
 cudaError_t launch_inject(const Plan& P, void* C, const int64_t* rows, const int64_t* cols,

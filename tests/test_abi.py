@@ -38,7 +38,7 @@ def test_version(lib):
 
 
 def test_struct_sizes_match_header(lib):
-    assert ct.sizeof(abft.Desc) == 6 * 8 + 6 * 4 + 8
+    assert ct.sizeof(abft.Desc) == 6 * 8 + 6 * 4 + 8 + 2 * 4
     assert ct.sizeof(abft.Fault) == 4 * 4 + 3 * 8 + 2 * 4
     assert ct.sizeof(abft.Problem) == 6 * 8 + 3 * 8
     assert ct.sizeof(abft.GroupTuning) == 2 * 4

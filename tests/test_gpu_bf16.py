@@ -318,3 +318,34 @@ def test_bounded_wait_timeout_is_reported(monkeypatch):
     st, rep, nrep = abft.abft_verify_correct(r.desc, r.C, r.ws)
     assert st == abft.OK and nrep == 0
     check_fp32_product(r.C.cpu().numpy(), r.A64, r.B64, oracle.gemm(r.A64, r.B64))
+
+
+def test_two_erasures_in_a_block_column_bf16():
+    """bf16 product with 2 block checksums: two erased blocks of one block column rebuilt
+    from the first two checksums (binary64 solve), against the oracle's rebuild."""
+    m = n = 512
+    k = 256
+    desc_kw = dict(p=4, q=4)
+    A, A64, lda = bf16_matrix(m, k, "normal", 23, 1)
+    B, B64, ldb = bf16_matrix(k, n, "normal", 23, 2)
+    desc = abft.make_desc(m, n, k, "bf16", 128, 128, 4, 4, lda=lda, ldb=ldb, grid_f=2)
+    L = abft.abft_workspace_layout(desc)
+    assert L.acs_rows == 4 * 4 + 2 * 2 * 128
+    ws = torch.zeros(L.total, dtype=torch.uint8, device="cuda")
+    C = torch.empty((m, n), dtype=torch.float32, device="cuda")
+    abft.abft_encode(desc, A, B, ws)
+    abft.abft_gemm(desc, A, B, C, ws)
+    enc = oracle.Encoded(A64, B64, 128, 128, 4, 4, dtype="bf16", f=2)
+    ref = oracle.gemm(A64, B64)
+    blocks = [(1, 3), (2, 3)]
+    for bi, bj in blocks:
+        abft.abft_erase_block(desc, C, bi, bj)
+    st, rep, nrep = abft.abft_verify_correct(desc, C, ws, erased=blocks)
+    assert st == abft.OK and nrep == 0
+    st, ents = abft.abft_recover_blocks(desc, C, ws, blocks)
+    assert st == abft.OK
+    Cg = C.cpu().numpy().astype(np.float64)
+    blk = np.s_[128:384, 384:512]
+    # the rebuilt blocks carry the errors of the checksums and of the survivors,
+    # amplified by the 2 x 2 solve (nodes 2/8 and 3/8)
+    assert rel_fro(Cg[blk], ref[blk]) <= 8 * (4 * np.sqrt(k) * U32 + 2.0 ** -17)

@@ -27,12 +27,12 @@ def lib():
 class Run:
     """One problem on the GPU: operands, workspace, encode + ABFT product."""
 
-    def __init__(self, A, B, vb_r, vb_c, p=0, q=0, plain=False):
+    def __init__(self, A, B, vb_r, vb_c, p=0, q=0, plain=False, f=0):
         self.A_np, self.B_np = np.ascontiguousarray(A), np.ascontiguousarray(B)
         m, k = A.shape
         n = B.shape[1]
         self.m, self.n, self.k = m, n, k
-        self.desc = abft.make_desc(m, n, k, "f64", vb_r, vb_c, p, q)
+        self.desc = abft.make_desc(m, n, k, "f64", vb_r, vb_c, p, q, grid_f=f)
         self.L = abft.abft_workspace_layout(self.desc)
         self.A = torch.from_numpy(self.A_np).cuda()
         self.B = torch.from_numpy(self.B_np).cuda()
@@ -310,3 +310,56 @@ def test_f64_11264_grid22_full_size():
     for i, j, _ in flips:
         assert abs(Cg[i, j] - C_clean[i, j]) <= 1e-12 * np.abs(C_clean[i]).max()
     assert oracle.residual_check(A, B, Cg, x) < 1.0
+
+
+@pytest.mark.parametrize("f,nerase", [(2, 2), (3, 3), (3, 2)])
+def test_multiple_erasures_per_block_column(f, nerase):
+    """f block checksums (section 2.1): nerase erased blocks in one block column, one more in
+    another column, and a flip elsewhere -- verified (erased blocks skipped), the flip
+    corrected, every erased block rebuilt; values against the oracle's rebuild and the
+    binary64 product, block checksum rows against the oracle's encode."""
+    m = n = 384
+    k = 256
+    p = q = 6
+    bs = m // p
+    A = wl.operand((m, k), "normal", 40 + f, 1)
+    B = wl.operand((k, n), "normal", 40 + f, 2)
+    r = Run(A, B, 64, 64, p, q, f=f)
+    enc = oracle.Encoded(A, B, 64, 64, p, q, f=f)
+    assert r.L.R == 2 * (m // 64) + f * bs
+    E = r.E()
+    assert rel_fro(E, enc.E) <= TOL_F64
+    Cstar = oracle.gemm(A, B)
+    blocks = [(bi, 2) for bi in (0, 3, 5)[:nerase]] + [(4, 0)]
+    flip = (20, 300, 61)  # block (0, 4)
+    abft.abft_inject_bitflips(r.desc, r.C, [flip])
+    for bi, bj in blocks:
+        abft.abft_erase_block(r.desc, r.C, bi, bj)
+    Cf = r.C.cpu().numpy()
+    (st, rep, n_), (ost, orep, oC, on) = verify_both(r, enc, Cf, erased=blocks)
+    assert st == abft.OK and ost == oracle.ST_OK
+    assert positions(rep) == positions(orep) == [(20, 300, abft.KIND_CORRECTED)]
+    st, ents = abft.abft_recover_blocks(r.desc, r.C, r.ws, blocks)
+    ost, oCr, onfl = enc.recover_blocks(oC, blocks)
+    assert st == abft.OK and ost == oracle.ST_OK and onfl == 0
+    assert [(e["row"], e["col"], e["kind"]) for e in ents] == \
+        [(bs * bi, 64 * bj, abft.KIND_BLOCK_RECOVERED) for bi, bj in blocks]
+    Cg = r.C.cpu().numpy()
+    for bi, bj in blocks:
+        blk = np.s_[bs * bi:bs * (bi + 1), 64 * bj:64 * (bj + 1)]
+        assert rel_fro(Cg[blk], Cstar[blk]) <= 1e-11
+        assert rel_fro(Cg[blk], oCr[blk]) <= 1e-11
+    assert rel_fro(Cg, Cstar) <= 1e-11
+
+
+def test_more_erasures_than_block_checksums_refused():
+    A = wl.operand((256, 128), "normal", 50, 1)
+    B = wl.operand((128, 256), "normal", 50, 2)
+    r = Run(A, B, 64, 64, 4, 4, f=2)
+    for bi in (0, 1, 2):
+        abft.abft_erase_block(r.desc, r.C, bi, 1)
+    st, ents = abft.abft_recover_blocks(r.desc, r.C, r.ws, [(0, 1), (1, 1), (2, 1)])
+    assert st == abft.ERR_UNCORRECTABLE
+    assert np.isnan(r.C.cpu().numpy()[0:192, 64:128]).all()      # nothing launched
+    st, ents = abft.abft_recover_blocks(r.desc, r.C, r.ws, [(0, 1), (1, 1)])
+    assert st == abft.ERR_UNCORRECTABLE                            # block (2, 1) still NaN

@@ -495,8 +495,51 @@ def run_workload(w, args, dev, rank, world, secondary=False):
             out["cpu_baseline"] = cpu_baseline(A_np, B_np, w, 8, seed)
         else:
             out["cpu_baseline"] = cpu_baseline(A_np, B_np, w, 4, seed)
+    if w.p and not secondary:
+        out["multi_erasure"] = multi_erasure_leg(w, A, B, dev, stream, seed)
     del A, B, C, ws
     torch.cuda.empty_cache()
+    return out
+
+
+def multi_erasure_leg(w, A, B, dev, stream, seed, f=2):
+    """Two block checksums (grid_f = 2) on the same operands: two erased blocks of one block
+    column rebuilt from the checksums and the survivors by the binary64 2 x 2 solve.  One
+    encode + product (not timed), then the rebuild timed with CUDA events and its error
+    against the values before the erasure.  Returns the dict attached to the JSON line."""
+    import torch
+    from paper_0806_3121_gb300 import abft
+    desc = abft.make_desc(w.m, w.n, w.k, w.dtype, w.vb_r, w.vb_c, w.p, w.q, grid_f=f)
+    L = abft.abft_workspace_layout(desc)
+    ws = torch.zeros(L.total, dtype=torch.uint8, device=dev)
+    C = torch.empty((w.m, w.n), dtype=torch.float64, device=dev)
+    abft.abft_encode(desc, A, B, ws, stream=stream)
+    abft.abft_gemm(desc, A, B, C, ws, stream=stream)
+    bs, bc = w.m // w.p, w.n // w.q
+    g = wl.rng(seed, 9)
+    bj = int(g.integers(0, w.q))
+    rows = sorted(int(x) for x in g.choice(w.p, size=f, replace=False))
+    blocks = [(bi, bj) for bi in rows]
+    torch.cuda.synchronize()
+    saved = [C[bi * bs:(bi + 1) * bs, bj * bc:(bj + 1) * bc].clone() for bi, _ in blocks]
+    for bi, _ in blocks:
+        abft.abft_erase_block(desc, C, bi, bj, stream=stream)
+    st, rep, n = abft.abft_verify_correct(desc, C, ws, erased=blocks, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st2, ents = abft.abft_recover_blocks(desc, C, ws, blocks, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    err = max(((C[bi * bs:(bi + 1) * bs, bj * bc:(bj + 1) * bc] - sv).norm() / sv.norm()).item()
+              for (bi, _), sv in zip(blocks, saved))
+    # algorithmic bytes: the survivors of the block column, the f checksum blocks, the
+    # rebuilt blocks written and read back by the re-check
+    nbytes = 8 * bs * bc * ((w.p - f) + f + 2 * f)
+    out = {"grid_f": f, "erased_blocks": blocks, "verify_status": st, "recover_status": st2,
+           "recover_ms": ms, "recover_GBps": nbytes / (ms * 1e-3) / 1e9,
+           "max_rel_err_rebuilt_block": err}
+    del ws, C
     return out
 
 

@@ -46,7 +46,6 @@ constexpr uint32_t B_BOX_BYTES = 64 * BK * 2;      // one 64-column box: 8 KiB
 constexpr uint32_t B_BYTES = BN * BK * 2;          // 32 KiB
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t TMEM_COLS = 2 * BN;             // two accumulators
-constexpr int GROUP_M = 16;                        // tile rows per raster group
 constexpr uint32_t OBS_BYTES = 2 * 4 * BN * 2 * 4; // column partials (e, w) per lane quarter,
                                                    // two buffers (alternate fused tiles)
 constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + OBS_BYTES + 256;
@@ -81,6 +80,7 @@ struct TcArgs {
   uint64_t wait_ns;          // bounded-wait limit
   int stall_test;            // timeout test: the producer skips the first tile
   int kpg;                   // k-steps per promotion group (0: one group per tile)
+  int group_m;               // raster group height (tile rows)
 };
 
 struct Tile {
@@ -88,13 +88,13 @@ struct Tile {
   int64_t row0, col0;
 };
 
-// Tile order: groups of GROUP_M data tile rows; the checksum tile rows are
+// Tile order: groups of GROUP_M (raster group height) data tile rows; the checksum tile rows are
 // dealt round-robin to the groups (row r joins group r % groups).  Inside a
 // group the tiles run column by column -- data columns over the group's data
 // and checksum rows, then the checksum columns over its data rows -- so every
 // checksum tile reuses the A or B panels its group already keeps in L2.
 __device__ __forceinline__ Tile decode_local(int64_t t, int64_t ntm, int64_t ntn, int64_t ntr,
-                                             int64_t ntc) {
+                                             int64_t ntc, int64_t GROUP_M) {
   const int64_t ngr = (ntm + GROUP_M - 1) / GROUP_M;
   int64_t off = 0;
   for (int64_t G = 0; G < ngr; ++G) {
@@ -190,7 +190,7 @@ struct SingleSched {
   }
   __device__ __forceinline__ TileView view(int64_t t) const {
     const TcArgs& g = *a;
-    const Tile T = decode_local(t, g.ntm, g.ntn, g.ntr, g.ntc);
+    const Tile T = decode_local(t, g.ntm, g.ntn, g.ntr, g.ntc, g.group_m);
     TileView V;
     V.prob = 0;
     V.nkb = (g.k + BK - 1) / BK;
@@ -774,6 +774,15 @@ int promote_ksteps(int dtype) {
   return dtype == ABFT_BF16X6 ? 8 : (dtype == ABFT_BF16X3 ? 16 : 0);
 }
 
+// Raster group height of the single-problem tile order: tiles run column by
+// column over groups of this many tile rows, so consecutive CTAs share the
+// group's A panels and one B panel in L2.  ABFT_GROUP_M overrides the default.
+int raster_group_rows() {
+  const char* env = getenv("ABFT_GROUP_M");
+  if (env && *env) return std::max(1, atoi(env));
+  return 16;
+}
+
 int num_sms() {
   int dev = 0;
   cudaGetDevice(&dev);
@@ -868,6 +877,7 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
   const char* stall = getenv("ABFT_TEST_STALL_PRODUCER");
   g.stall_test = stall && stall[0] == '1';
   g.kpg = promote_ksteps(d.dtype);
+  g.group_m = raster_group_rows();
   g.wait_ns = g.stall_test ? 200000000ull : tc::kWaitLimitNs;
   const auto kernel = g.kpg > 0 ? k_gemm_bf16<true> : k_gemm_bf16<false>;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);

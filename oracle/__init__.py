@@ -55,7 +55,8 @@ class OracleCfg(ct.Structure):
                 ("vb_r", ct.c_int64), ("vb_c", ct.c_int64), ("p", ct.c_int64), ("q", ct.c_int64),
                 ("u_acc", ct.c_double), ("u_sum", ct.c_double), ("u_enc", ct.c_double),
                 ("u_c", ct.c_double), ("u_cs", ct.c_double), ("s", ct.c_double),
-                ("round_f32", ct.c_int32), ("f", ct.c_int32)]
+                ("round_f32", ct.c_int32), ("f", ct.c_int32),
+                ("car_a", ct.c_void_p), ("car_b", ct.c_void_p)]
 
 
 class OracleFault(ct.Structure):
@@ -94,6 +95,10 @@ def lib():
             _lib.oracle_e4m3_value.restype = ct.c_double
             _lib.oracle_e4m3_value.argtypes = [ct.c_uint8]
             _lib.oracle_dequant_e4m3.argtypes = [i64, i64, d, d, i64, d]
+            _lib.oracle_norms_carried_rows.argtypes = [i64, i64, d, i64, d]
+            _lib.oracle_norms_carried_cols.argtypes = [i64, i64, d, i64, d]
+            _lib.oracle_carry_rows.argtypes = [d, d, d, d]
+            _lib.oracle_carry_cols.argtypes = [d, d, d, d]
     return _lib
 
 
@@ -199,19 +204,64 @@ def make_cfg(m, n, k, vb_r, vb_c, p=0, q=0, dtype="f64", s=4.0, f=1) -> OracleCf
                      round_f32=0 if dtype == "f64" else 1, f=max(1, f), **u)
 
 
-class Encoded:
-    """Everything the oracle derives from A and B before C is checked."""
+def carry_rows(prev: "Encoded") -> np.ndarray:
+    """Deviation bound of the column checksum rows carried out of product `prev`
+    (2 per row verify block; section 3.2, chained calls)."""
+    out = np.empty(2 * cdiv(prev.m, prev.cfg.vb_r), np.float64)
+    lib().oracle_carry_rows(ct.byref(prev.cfg), _p(prev.nAblk), _p(prev.nBcol), _p(out))
+    return out
 
-    def __init__(self, A, B, vb_r, vb_c, p=0, q=0, dtype="f64", s=4.0, products=True, f=1):
+
+def carry_cols(prev: "Encoded") -> np.ndarray:
+    """Deviation bound of the row checksum columns carried out of product `prev`
+    (2 per column verify block)."""
+    out = np.empty(2 * cdiv(prev.n, prev.cfg.vb_c), np.float64)
+    lib().oracle_carry_cols(ct.byref(prev.cfg), _p(prev.nBblk), _p(prev.nArow), _p(out))
+    return out
+
+
+class Encoded:
+    """Everything the oracle derives from A and B before C is checked.
+
+    left / right (chained calls, section 3.2): an earlier product's Encoded whose
+    output C is this product's A (left) or B (right).  Its expected checksums E (rows)
+    or F (columns) are carried as this product's encoded rows of A / columns of B
+    instead of being computed from A / B, and the thresholds gain the bound of their
+    deviation from the stored operand (carry_rows / carry_cols).
+    """
+
+    def __init__(self, A, B, vb_r, vb_c, p=0, q=0, dtype="f64", s=4.0, products=True, f=1,
+                 left=None, right=None):
         A, B = _f64(A), _f64(B)
         self.A, self.B = A, B
         self.m, self.k = A.shape
         self.n = B.shape[1]
         self.cfg = make_cfg(self.m, self.n, self.k, vb_r, vb_c, p, q, dtype, s, f)
-        self.acs = encode_A(A, vb_r, p, f)
-        self.bcs = encode_B(B, vb_c)
+        nvr, nvc = cdiv(self.m, vb_r), cdiv(self.n, vb_c)
         self.nArow, self.nAblk = norms_A(A, vb_r)
         self.nBcol, self.nBblk = norms_B(B, vb_c)
+        self.car_a = np.zeros(2 * nvr, np.float64)
+        self.car_b = np.zeros(2 * nvc, np.float64)
+        if left is not None:
+            assert (left.m, left.n, left.cfg.vb_r) == (self.m, self.k, vb_r), "left chain shape"
+            rows = 2 * nvr
+            if p:
+                assert left.cfg.p == p and left.cfg.f >= max(1, f), "left chain erasure grid"
+                rows += max(1, f) * (self.m // p)
+            self.acs = np.ascontiguousarray(left.E[:rows])
+            lib().oracle_norms_carried_rows(nvr, self.k, _p(self.acs), self.k, _p(self.nAblk))
+            self.car_a = carry_rows(left)
+        else:
+            self.acs = encode_A(A, vb_r, p, f)
+        if right is not None:
+            assert (right.m, right.n, right.cfg.vb_c) == (self.k, self.n, vb_c), "right chain shape"
+            self.bcs = np.ascontiguousarray(right.F)
+            lib().oracle_norms_carried_cols(self.k, nvc, _p(self.bcs), 2 * nvc, _p(self.nBblk))
+            self.car_b = carry_cols(right)
+        else:
+            self.bcs = encode_B(B, vb_c)
+        self.cfg.car_a = self.car_a.ctypes.data
+        self.cfg.car_b = self.car_b.ctypes.data
         if products:  # skipped for large shapes, where tests sample E and F instead
             self.E = gemm(self.acs, B)   # expected column checksums (+ block checksum rows)
             self.F = gemm(A, self.bcs)   # expected row checksums

@@ -251,6 +251,10 @@ typedef struct {
   double s;           /* safety factor */
   int32_t round_f32;  /* corrected values are rounded to binary32 */
   int32_t f;          /* block checksum rows of the erasure grid (0 means 1) */
+  /* Chained calls: bounds of the carried checksums' deviation from the sums
+   * of the stored operand (see oracle_carry_rows); NULL when not chained. */
+  const double* car_a; /* 2 per row verify block: unweighted, weighted */
+  const double* car_b; /* 2 per column verify block */
 } oracle_cfg;
 
 typedef struct {
@@ -273,12 +277,28 @@ typedef struct {
  * unpinned as a formula (it is a reading); pinned as a property: fault-free
  * residuals stay far below it over many seeds, exact integer data leave
  * residual 0. */
-static void taus(const oracle_cfg* c, int64_t vb, double nvec, const double* nb4, double* te,
-                 double* tw) {
-  double f1 = sqrt((double)c->k) * c->u_acc + sqrt((double)vb) * (c->u_sum + c->u_enc) + c->u_c;
-  double f2 = sqrt((double)c->k) * c->u_acc + c->u_cs;
-  *te = c->s * nvec * (f1 * nb4[0] + f2 * nb4[2]);
-  *tw = c->s * nvec * (f1 * nb4[1] + f2 * nb4[3]);
+static void factors(const oracle_cfg* c, int64_t vb, double* f1, double* f2) {
+  *f1 = sqrt((double)c->k) * c->u_acc + sqrt((double)vb) * (c->u_sum + c->u_enc) + c->u_c;
+  *f2 = sqrt((double)c->k) * c->u_acc + c->u_cs;
+}
+
+/* In a chained call the threshold gains the carried deviation (car2: the two
+ * bounds of the line's verify block, NULL when not chained):
+ *   tau_e = s * ||B_j|| * (f1 * ||A_I||_F + f2 * ||e^T A_I|| + car_e(I)). */
+static void taus(const oracle_cfg* c, int64_t vb, double nvec, const double* nb4,
+                 const double* car2, double* te, double* tw) {
+  double f1, f2;
+  factors(c, vb, &f1, &f2);
+  double ce = car2 ? car2[0] : 0.0, cw = car2 ? car2[1] : 0.0;
+  *te = c->s * nvec * (f1 * nb4[0] + f2 * nb4[2] + ce);
+  *tw = c->s * nvec * (f1 * nb4[1] + f2 * nb4[3] + cw);
+}
+
+static const double* car_col(const oracle_cfg* c, int64_t I) {
+  return c->car_a ? &c->car_a[2 * I] : NULL;
+}
+static const double* car_row(const oracle_cfg* c, int64_t J) {
+  return c->car_b ? &c->car_b[2 * J] : NULL;
 }
 
 /* The four thresholds that apply to element (i, j): those of its column line
@@ -286,8 +306,9 @@ static void taus(const oracle_cfg* c, int64_t vb, double nvec, const double* nb4
 void oracle_thresholds_at(const oracle_cfg* c, const double* nArow, const double* nAblk,
                           const double* nBcol, const double* nBblk, int64_t i, int64_t j,
                           double* out4) {
-  taus(c, c->vb_r, nBcol[j], &nAblk[4 * (i / c->vb_r)], &out4[0], &out4[1]);
-  taus(c, c->vb_c, nArow[i], &nBblk[4 * (j / c->vb_c)], &out4[2], &out4[3]);
+  int64_t I = i / c->vb_r, J = j / c->vb_c;
+  taus(c, c->vb_r, nBcol[j], &nAblk[4 * I], car_col(c, I), &out4[0], &out4[1]);
+  taus(c, c->vb_c, nArow[i], &nBblk[4 * J], car_row(c, J), &out4[2], &out4[3]);
 }
 
 /* Does the line of rows [i0, i1) x columns [j0, j1) touch an erased block? */
@@ -323,7 +344,7 @@ void oracle_col_residuals(const oracle_cfg* c, const double* C, int64_t ldc, con
       }
       re[I * n + j] = se - E[(2 * I) * n + j];
       rw[I * n + j] = sw - E[(2 * I + 1) * n + j];
-      taus(c, vb, nBcol[j], &nAblk[4 * I], &te[I * n + j], &tw[I * n + j]);
+      taus(c, vb, nBcol[j], &nAblk[4 * I], car_col(c, I), &te[I * n + j], &tw[I * n + j]);
       nonfin[I * n + j] = nf;
     }
   }
@@ -347,7 +368,7 @@ void oracle_row_residuals(const oracle_cfg* c, const double* C, int64_t ldc, con
       }
       re[i * nvb + J] = se - F[i * (2 * nvb) + 2 * J];
       rw[i * nvb + J] = sw - F[i * (2 * nvb) + 2 * J + 1];
-      taus(c, vb, nArow[i], &nBblk[4 * J], &te[i * nvb + J], &tw[i * nvb + J]);
+      taus(c, vb, nArow[i], &nBblk[4 * J], car_row(c, J), &te[i * nvb + J], &tw[i * nvb + J]);
       nonfin[i * nvb + J] = nf;
     }
 }
@@ -385,7 +406,7 @@ static int col_line_flagged(const oracle_cfg* c, const double* C, int64_t ldc, c
   }
   *re = se - E[(2 * I) * c->n + j];
   *rw = sw - E[(2 * I + 1) * c->n + j];
-  taus(c, vb, nBcol[j], &nAblk[4 * I], &te, &tw);
+  taus(c, vb, nBcol[j], &nAblk[4 * I], car_col(c, I), &te, &tw);
   return flagged(*re, *rw, te, tw);
 }
 
@@ -400,7 +421,7 @@ static int row_line_flagged(const oracle_cfg* c, const double* C, int64_t ldc, c
   }
   *re = se - F[i * (2 * nvb) + 2 * J];
   *rw = sw - F[i * (2 * nvb) + 2 * J + 1];
-  taus(c, vb, nArow[i], &nBblk[4 * J], &te, &tw);
+  taus(c, vb, nArow[i], &nBblk[4 * J], car_row(c, J), &te, &tw);
   return flagged(*re, *rw, te, tw);
 }
 
@@ -813,6 +834,91 @@ int oracle_recover_blocks(const oracle_cfg* c, double* C, int64_t ldc, const dou
   *n_flagged = nfl;
   if (nfl) status = ST_UNCORRECTABLE;
   return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Chained calls (section 3.2: when ABFT BLAS routines are called one after
+ * the other, the checksums are not recomputed between the calls).  A product
+ * whose left operand A is the output C of an earlier product takes that
+ * product's expected column checksum rows E (the unweighted and weighted row
+ * of every verify block, then the block checksum rows) as its encoded rows of
+ * A, without reading A for them; one whose right operand B is an earlier
+ * output takes that product's expected row checksum columns F as its encoded
+ * columns of B.  The norms that enter the thresholds are those of the
+ * operand itself (||A_I||_F, ||A_i||) and of the carried rows / columns.
+ *
+ * A carried row is not the sum of the stored operand rows: it carries the
+ * rounding of the earlier product (and of every product before it).  The
+ * reading here bounds that deviation with the same rounding model as the
+ * thresholds.  The column deviation d_I(j) = E[2I][j] - sum_{i in I} C_ij of
+ * the earlier product stays within its unscaled threshold
+ *   |d_I(j)| <= ||B_j|| (f1 ||A_I||_F + f2 ||e^T A_I|| + car_e(I)),
+ * so its largest entry is at most
+ *   car'_e(I) = max_j ||B_j|| * (f1 ||A_I||_F + f2 ||e^T A_I|| + car_e(I))
+ * (car_e = 0 for a freshly encoded product; the weighted row likewise with
+ * diag(w) A_I, w^T A_I and car_w).  In the next product the deviation enters
+ * a column residual as sum_l d_I(l) B'_lj, whose independent terms add in
+ * quadrature to at most car'(I) ||B'_j||: the next threshold adds car'(I)
+ * inside its bracket (taus above).  The row side is the transpose, with
+ * max_i ||A_i|| of the earlier product.  Parity of this bound: a reading,
+ * pinned as properties (exact zero residuals on integer chains, the measured
+ * deviation below the bound, no false flag over seeds where the uncarried
+ * threshold fails). */
+
+/* nblk[4I+2], nblk[4I+3] = norms of the carried rows acs[2I], acs[2I+1]
+ * (length len, leading dimension ld). */
+void oracle_norms_carried_rows(int64_t nvb, int64_t len, const double* acs, int64_t ld,
+                               double* nblk) {
+  for (int64_t I = 0; I < nvb; ++I)
+    for (int64_t c = 0; c < 2; ++c) {
+      double q = 0.0;
+      for (int64_t l = 0; l < len; ++l) q += acs[(2 * I + c) * ld + l] * acs[(2 * I + c) * ld + l];
+      nblk[4 * I + 2 + c] = sqrt(q);
+    }
+}
+
+/* nblk[4J+2], nblk[4J+3] = norms of the carried columns bcs[:, 2J], bcs[:, 2J+1]. */
+void oracle_norms_carried_cols(int64_t len, int64_t nvb, const double* bcs, int64_t ld,
+                               double* nblk) {
+  for (int64_t J = 0; J < nvb; ++J)
+    for (int64_t c = 0; c < 2; ++c) {
+      double q = 0.0;
+      for (int64_t l = 0; l < len; ++l) q += bcs[l * ld + 2 * J + c] * bcs[l * ld + 2 * J + c];
+      nblk[4 * J + 2 + c] = sqrt(q);
+    }
+}
+
+/* Deviation bound of the column checksum rows carried out of a product with
+ * configuration prev, norms nAblk / nBcol (and its own carried bound
+ * prev->car_a): car_out[2I+c] as above. */
+void oracle_carry_rows(const oracle_cfg* prev, const double* nAblk, const double* nBcol,
+                       double* car_out) {
+  double f1, f2, mx = 0.0;
+  factors(prev, prev->vb_r, &f1, &f2);
+  for (int64_t j = 0; j < prev->n; ++j)
+    if (nBcol[j] > mx) mx = nBcol[j];
+  int64_t nvb = ceil_div(prev->m, prev->vb_r);
+  for (int64_t I = 0; I < nvb; ++I)
+    for (int64_t c = 0; c < 2; ++c) {
+      double cp = prev->car_a ? prev->car_a[2 * I + c] : 0.0;
+      car_out[2 * I + c] = mx * (f1 * nAblk[4 * I + c] + f2 * nAblk[4 * I + 2 + c] + cp);
+    }
+}
+
+/* The row side: deviation bound of the row checksum columns carried out of
+ * a product (max_i ||A_i|| of that product, its nBblk and prev->car_b). */
+void oracle_carry_cols(const oracle_cfg* prev, const double* nBblk, const double* nArow,
+                       double* car_out) {
+  double f1, f2, mx = 0.0;
+  factors(prev, prev->vb_c, &f1, &f2);
+  for (int64_t i = 0; i < prev->m; ++i)
+    if (nArow[i] > mx) mx = nArow[i];
+  int64_t nvb = ceil_div(prev->n, prev->vb_c);
+  for (int64_t J = 0; J < nvb; ++J)
+    for (int64_t c = 0; c < 2; ++c) {
+      double cp = prev->car_b ? prev->car_b[2 * J + c] : 0.0;
+      car_out[2 * J + c] = mx * (f1 * nBblk[4 * J + c] + f2 * nBblk[4 * J + 2 + c] + cp);
+    }
 }
 
 /* ------------------------------------------------------------------------ */

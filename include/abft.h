@@ -125,6 +125,10 @@ typedef struct {
                                         (op_a_ld apart by align256 of a plane);
                                         FP8: the dequantised bf16 operands     */
   int64_t op_a_ld, op_b_ld;          /* their leading dims (elements)          */
+  size_t car_a, car_b;               /* chained calls: bounds of the carried
+                                        checksums' deviation (binary64, 2 per
+                                        row / column verify block; zero after
+                                        abft_encode)                           */
 } abft_ws_layout;
 
 /* Size of the caller-owned device workspace for `desc`.  Returns 0 for an
@@ -167,6 +171,38 @@ abft_status abft_encode(const abft_desc* desc, const void* A, const void* B, con
  * serialised by the caller.  ABFT_F64 only.  Asynchronous. */
 abft_status abft_encode_noalloc(const abft_desc* desc, const void* A, const void* B,
                                 const void* a_scale, const void* b_scale, void* ws, void* stream);
+
+/* Chained encode (section 3.2: ABFT BLAS calls stacked one after the other do
+ * not recompute the checksums between calls).  Like abft_encode, except that
+ *  - left_desc / left_ws (may be NULL): A is the output C of that earlier
+ *    product, whose workspace still holds its expected checksums.  Its column
+ *    checksum rows E (and its first grid_f block checksum rows) become this
+ *    product's encoded rows of A; A is read only for the threshold norms.
+ *    Requires left_desc->m == m, left_desc->n == k, the same vb_rows and,
+ *    when this desc has an erasure grid, the same grid_p and a left grid_f of
+ *    at least this grid_f.
+ *  - right_desc / right_ws (may be NULL): B is the output of that earlier
+ *    product; its row checksum columns F become this product's encoded
+ *    columns of B.  Requires right_desc->m == k, right_desc->n == n and the
+ *    same vb_cols.
+ * The carried checksums differ from the sums of the stored operand by the
+ * earlier products' rounding; the detection thresholds of this product gain
+ * that deviation's bound (car_a / car_b in abft_ws_layout), carried on
+ * through further chained calls.  Because the checksums are carried and not
+ * recomputed, an operand value that changed after the earlier product's
+ * verify is caught by this product's verify: the whole output row (left) or
+ * column (right) it spoils is recomputed from the carried checksums, and the
+ * other side's lines, whose expectations were formed from the changed
+ * operand, are reported ABFT_KIND_UNCORRECTABLE (status
+ * ABFT_ERR_UNCORRECTABLE; at most 2048 elements can be recomputed in one
+ * verify).  ABFT_F64 only (ABFT_ERR_UNSUPPORTED otherwise); the earlier
+ * descriptors must be ABFT_F64 too.  With both left and right NULL this is
+ * abft_encode.  Asynchronous; the earlier workspaces must stay untouched
+ * until the call completes on the stream. */
+abft_status abft_encode_chained(const abft_desc* desc, const void* A, const void* B,
+                                const abft_desc* left_desc, const void* left_ws,
+                                const abft_desc* right_desc, const void* right_ws, void* ws,
+                                void* stream);
 
 /* The ABFT product (Eq. (1)): [A; C_C^T A] [B, B C_R] on the GPU.  Writes the
  * data block A B into C and the checksum blocks into ws (E and F).  Requires a

@@ -22,7 +22,7 @@ KIND_CORRECTED, KIND_NONFINITE_CORRECTED, KIND_UNCORRECTABLE, KIND_BLOCK_RECOVER
 
 # Every symbol include/abft.h declares.
 EXPORTS = ("abft_workspace_bytes", "abft_workspace_layout", "abft_encode",
-           "abft_encode_noalloc", "abft_gemm", "abft_set_epilogue_faults",
+           "abft_encode_noalloc", "abft_encode_chained", "abft_gemm", "abft_set_epilogue_faults",
            "abft_gemm_plain", "abft_verify_correct", "abft_recover_block", "abft_recover_blocks",
            "abft_inject_bitflips", "abft_erase_block", "abft_kernel_launches",
            "abft_last_error", "abft_version",
@@ -69,7 +69,8 @@ class WsLayout(ct.Structure):
                 ("bcs_cols", ct.c_int64), ("obs_col", ct.c_size_t), ("obs_row", ct.c_size_t),
                 ("inject", ct.c_size_t), ("fused", ct.c_int32), ("planes", ct.c_int32),
                 ("acs_plane", ct.c_size_t), ("bcs_plane", ct.c_size_t), ("op_a", ct.c_size_t),
-                ("op_b", ct.c_size_t), ("op_a_ld", ct.c_int64), ("op_b_ld", ct.c_int64)]
+                ("op_b", ct.c_size_t), ("op_a_ld", ct.c_int64), ("op_b_ld", ct.c_int64),
+                ("car_a", ct.c_size_t), ("car_b", ct.c_size_t)]
 
 
 class Problem(ct.Structure):
@@ -108,6 +109,7 @@ def load(path: str = LIB_PATH):
         lib.abft_workspace_layout.argtypes = [D, ct.POINTER(WsLayout)]
         lib.abft_encode.argtypes = [D, vp, vp, vp, vp, vp, vp]
         lib.abft_encode_noalloc.argtypes = [D, vp, vp, vp, vp, vp, vp]
+        lib.abft_encode_chained.argtypes = [D, vp, vp, D, vp, D, vp, vp, vp]
         lib.abft_gemm.argtypes = [D, vp, vp, vp, vp, vp, vp, vp]
         lib.abft_gemm_plain.argtypes = [D, vp, vp, vp, vp, vp, vp, vp]
         lib.abft_set_epilogue_faults.argtypes = [D, vp, vp, vp, vp, i32, vp]
@@ -203,6 +205,15 @@ def abft_encode_noalloc(desc, A, B, ws, a_scale=None, b_scale=None, stream=None)
     bytes below the layout's scratch offset."""
     _check(load().abft_encode_noalloc(ct.byref(desc), _ptr(A), _ptr(B), _ptr(a_scale),
                                       _ptr(b_scale), _ptr(ws), _stream(stream)))
+
+
+def abft_encode_chained(desc, A, B, ws, left=None, right=None, stream=None):
+    """Chained encode (section 3.2): left / right are (desc, ws) of the earlier products
+    whose outputs are A / B; their expected checksums are carried, not recomputed."""
+    ld, lw = (ct.byref(left[0]), _ptr(left[1])) if left is not None else (None, None)
+    rd, rw = (ct.byref(right[0]), _ptr(right[1])) if right is not None else (None, None)
+    _check(load().abft_encode_chained(ct.byref(desc), _ptr(A), _ptr(B), ld, lw, rd, rw,
+                                      _ptr(ws), _stream(stream)))
 
 
 def abft_gemm(desc, A, B, C, ws, a_scale=None, b_scale=None, stream=None):

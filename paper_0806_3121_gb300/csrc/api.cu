@@ -158,6 +158,8 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
   L.nAblk = region((size_t)4 * p.nvr * 8);
   L.nBcol = region((size_t)d->n * 8);
   L.nBblk = region((size_t)4 * p.nvc * 8);
+  L.car_a = region((size_t)2 * p.nvr * 8);
+  L.car_b = region((size_t)2 * p.nvc * 8);
   L.E16 = region(lp ? (size_t)L.acs_rows * d->n * 4 : 0);
   L.F16 = region(lp ? (size_t)d->m * L.bcs_cols * 4 : 0);
   L.obs_col = region(p.fused ? (size_t)p.ntr_obs * 2 * d->n * 4 : 0);
@@ -181,6 +183,14 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
 }
 
 bool is_empty(const Plan& P) { return P.d.m == 0 || P.d.n == 0; }
+
+// A freshly encoded product carries no checksum deviation.
+cudaError_t clear_carry(const Plan& P, void* ws, cudaStream_t st) {
+  char* w = static_cast<char*>(ws);
+  cudaError_t e = cudaMemsetAsync(w + P.L.car_a, 0, sizeof(double) * 2 * P.nvr, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w + P.L.car_b, 0, sizeof(double) * 2 * P.nvc, st);
+  return e;
+}
 
 // Partial-reduction sizes used by the encode kernels (in doubles).
 size_t part_elems(const Plan& P) {
@@ -257,12 +267,55 @@ abft_status abft_encode(const abft_desc* desc, const void* A, const void* B, con
   if (!ws || (P.d.k > 0 && (!A || !B))) return fail(ABFT_ERR_INVALID, "NULL pointer");
   if (P.d.dtype == ABFT_FP8_E4M3 && P.d.k > 0 && (!a_scale || !b_scale))
     return fail(ABFT_ERR_INVALID, "ABFT_FP8_E4M3 needs a_scale and b_scale");
-  const cudaError_t e =
-      P.d.dtype == ABFT_F64
-          ? launch_encode_f64(P, static_cast<const double*>(A), static_cast<const double*>(B), ws,
-                              static_cast<cudaStream_t>(stream))
-          : launch_encode_lp(P, A, B, a_scale, b_scale, ws, static_cast<cudaStream_t>(stream));
+  cudaError_t e = clear_carry(P, ws, static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess)
+    e = P.d.dtype == ABFT_F64
+            ? launch_encode_f64(P, static_cast<const double*>(A), static_cast<const double*>(B),
+                                ws, static_cast<cudaStream_t>(stream))
+            : launch_encode_lp(P, A, B, a_scale, b_scale, ws, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? ABFT_OK : cuda_fail(e, "abft_encode");
+}
+
+abft_status abft_encode_chained(const abft_desc* desc, const void* A, const void* B,
+                                const abft_desc* left_desc, const void* left_ws,
+                                const abft_desc* right_desc, const void* right_ws, void* ws,
+                                void* stream) {
+  if (!left_desc && !right_desc) return abft_encode(desc, A, B, nullptr, nullptr, ws, stream);
+  Plan P, PL, PR;
+  abft_status st = make_plan(desc, &P);
+  if (st != ABFT_OK) return st;
+  const abft_desc& d = P.d;
+  if (d.dtype != ABFT_F64) return fail(ABFT_ERR_UNSUPPORTED, "chained encode: ABFT_F64 only");
+  if (left_desc) {
+    if ((st = make_plan(left_desc, &PL)) != ABFT_OK) return st;
+    if (PL.d.dtype != ABFT_F64) return fail(ABFT_ERR_UNSUPPORTED, "chained encode: ABFT_F64 only");
+    if (PL.d.m != d.m || PL.d.n != d.k || PL.d.vb_rows != d.vb_rows)
+      return fail(ABFT_ERR_INVALID,
+                  "left chain: the earlier product must be m x k with the same vb_rows");
+    if (P.bs > 0 && (PL.d.grid_p != d.grid_p || PL.f < P.f))
+      return fail(ABFT_ERR_INVALID,
+                  "left chain: the earlier product needs the same grid_p and at least grid_f "
+                  "block checksums");
+    if (d.k > 0 && !left_ws) return fail(ABFT_ERR_INVALID, "left chain: left_ws is NULL");
+  }
+  if (right_desc) {
+    if ((st = make_plan(right_desc, &PR)) != ABFT_OK) return st;
+    if (PR.d.dtype != ABFT_F64)
+      return fail(ABFT_ERR_UNSUPPORTED, "chained encode: ABFT_F64 only");
+    if (PR.d.m != d.k || PR.d.n != d.n || PR.d.vb_cols != d.vb_cols)
+      return fail(ABFT_ERR_INVALID,
+                  "right chain: the earlier product must be k x n with the same vb_cols");
+    if (d.k > 0 && !right_ws) return fail(ABFT_ERR_INVALID, "right chain: right_ws is NULL");
+  }
+  if (is_empty(P)) return ABFT_OK;
+  if (!ws || (d.k > 0 && (!A || !B))) return fail(ABFT_ERR_INVALID, "NULL pointer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = clear_carry(P, ws, s);
+  if (e == cudaSuccess)
+    e = launch_encode_f64_chained(P, static_cast<const double*>(A), static_cast<const double*>(B),
+                                  ws, left_desc ? &PL : nullptr, left_ws,
+                                  right_desc ? &PR : nullptr, right_ws, s);
+  return e == cudaSuccess ? ABFT_OK : cuda_fail(e, "abft_encode_chained");
 }
 
 abft_status abft_encode_noalloc(const abft_desc* desc, const void* A, const void* B,
@@ -282,9 +335,10 @@ abft_status abft_encode_noalloc(const abft_desc* desc, const void* A, const void
                 need, static_encode_part_bytes());
   if (is_empty(P)) return ABFT_OK;
   if (!ws || (P.d.k > 0 && (!A || !B))) return fail(ABFT_ERR_INVALID, "NULL pointer");
-  const cudaError_t e = launch_encode_f64_noalloc(P, static_cast<const double*>(A),
-                                                  static_cast<const double*>(B), ws,
-                                                  static_cast<cudaStream_t>(stream));
+  cudaError_t e = clear_carry(P, ws, static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess)
+    e = launch_encode_f64_noalloc(P, static_cast<const double*>(A), static_cast<const double*>(B),
+                                  ws, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? ABFT_OK : cuda_fail(e, "abft_encode_noalloc");
 }
 

@@ -195,6 +195,77 @@ __global__ void k_finalize_blk(const double* __restrict__ nvec, int64_t len, int
   nblk[4 * I + 3] = sqrt(q1);
 }
 
+// ---------------------------------------------------------------- chained calls
+// A chained product (section 3.2: stacked calls do not recompute checksums)
+// takes its encoded rows of A / columns of B from an earlier product's
+// expected checksums; the kernels below form the norms of those carried
+// vectors and the bound of their deviation from the stored operand.
+
+// part[r * nch + chunk] = sum over the chunk's 256 columns of acs[r][l]^2, the
+// layout k_encA_cols leaves for the checksum-row norms (r = 2I + c).
+// Grid (nch, <= 65535).
+__global__ void __launch_bounds__(kThreads) k_rows_sq(const double* __restrict__ acs, int64_t k,
+                                                      int64_t rows, double* __restrict__ part,
+                                                      int nch) {
+  __shared__ double sh[kThreads / 32];
+  const int64_t l = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
+    const double v = l < k ? acs[r * k + l] : 0.0;
+    const double t = block_sum(v * v, sh);
+    if (threadIdx.x == 0) part[r * nch + blockIdx.x] = t;
+  }
+}
+
+// part[c * nch + chunk] = sum over the chunk's kRowsPerWarpB rows of
+// bcs[l][c]^2, the layout k_encB_rows leaves (c = 2J + w).  One thread per
+// (c, chunk).
+__global__ void __launch_bounds__(kThreads) k_cols_sq(const double* __restrict__ bcs, int64_t k,
+                                                      int64_t Cc, double* __restrict__ part,
+                                                      int nch) {
+  const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (t >= Cc * nch) return;
+  const int64_t c = t / nch, chunk = t - c * nch;
+  const int64_t l0 = chunk * kRowsPerWarpB, l1 = min(l0 + (int64_t)kRowsPerWarpB, k);
+  double q = 0.0;
+  for (int64_t l = l0; l < l1; ++l) {
+    const double b = bcs[l * Cc + c];
+    q = fma(b, b, q);
+  }
+  part[c * nch + chunk] = q;
+}
+
+// Deviation bound of checksums carried out of an earlier product: its
+// deviation per line stays within that product's unscaled threshold, so the
+// largest one of verify block I is at most
+//   car[2I+c] = max_t nvec[t] * (f1 * nblk[4I+c] + f2 * nblk[4I+2+c] + car_prev[2I+c]),
+// nvec the earlier product's column norms of B (row side: row norms of A).
+// One CTA.
+__global__ void __launch_bounds__(kThreads) k_carry(const double* __restrict__ nvec, int64_t len,
+                                                    const double* __restrict__ nblk,
+                                                    const double* __restrict__ car_prev,
+                                                    int64_t nvb, double f1, double f2,
+                                                    double* __restrict__ car) {
+  __shared__ double sh[kThreads / 32];
+  __shared__ double s_mx;
+  double mx = 0.0;
+  for (int64_t t = threadIdx.x; t < len; t += kThreads) mx = fmax(mx, nvec[t]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) v = fmax(v, sh[w]);
+    s_mx = v;
+  }
+  __syncthreads();
+  mx = s_mx;
+  for (int64_t x = threadIdx.x; x < 2 * nvb; x += kThreads) {
+    const int64_t I = x >> 1, c = x & 1;
+    car[x] = mx * (f1 * nblk[4 * I + c] + f2 * nblk[4 * I + 2 + c] + car_prev[x]);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_encode_f64(const Plan& P, const double* A, const double* B, void* ws,
@@ -327,6 +398,85 @@ cudaError_t launch_encode_f64_noalloc(const Plan& P, const double* A, const doub
                                                              nchA, nAblk);
   k_finalize_blk<<<(unsigned)cdiv(P.nvc, 128), 128, 0, st>>>(nBcol, d.n, d.vb_cols, P.ec, partB,
                                                              nchB, nBblk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_encode_f64_chained(const Plan& P, const double* A, const double* B, void* ws,
+                                      const Plan* PL, const void* wsL, const Plan* PR,
+                                      const void* wsR, cudaStream_t st) {
+  const abft_desc& d = P.d;
+  if (d.k == 0) return launch_encode_f64(P, A, B, ws, st);  // nothing to carry: zero norms
+  char* w = static_cast<char*>(ws);
+  double* acs = reinterpret_cast<double*>(w + P.L.acs);
+  double* bcs = reinterpret_cast<double*>(w + P.L.bcs);
+  double* nArow = reinterpret_cast<double*>(w + P.L.nArow);
+  double* nAblk = reinterpret_cast<double*>(w + P.L.nAblk);
+  double* nBcol = reinterpret_cast<double*>(w + P.L.nBcol);
+  double* nBblk = reinterpret_cast<double*>(w + P.L.nBblk);
+  double* carA = reinterpret_cast<double*>(w + P.L.car_a);
+  double* carB = reinterpret_cast<double*>(w + P.L.car_b);
+  Scratch S = scratch_view(P, ws);
+  const int nchA = (int)cdiv(d.k, kThreads);
+  const int nchB = (int)cdiv(d.k, kRowsPerWarpB);
+  const int nchC = (int)cdiv(d.k, kThreads);
+  double* partA = S.part;
+  double* partB = partA + 4 * P.nvr * nchA;
+  double* partC = partB + 4 * P.nvc * nchB;
+  auto gy = [](int64_t v) { return (unsigned)(v < 65535 ? v : 65535); };
+  cudaError_t e = cudaSuccess;
+  int launches = 0;
+
+  if (PL) {  // rows of A: the earlier product's E (verify rows, then block checksum rows)
+    const char* wl = static_cast<const char*>(wsL);
+    const double* EL = reinterpret_cast<const double*>(wl + PL->L.E);
+    e = cudaMemcpyAsync(acs, EL, sizeof(double) * (size_t)P.R * d.k, cudaMemcpyDeviceToDevice,
+                        st);
+    if (e != cudaSuccess) return e;
+    k_rows_sq<<<dim3((unsigned)nchA, gy(2 * P.nvr)), kThreads, 0, st>>>(acs, d.k, 2 * P.nvr,
+                                                                         partA, nchA);
+    k_carry<<<1, kThreads, 0, st>>>(reinterpret_cast<const double*>(wl + PL->L.nBcol), PL->d.n,
+                                    reinterpret_cast<const double*>(wl + PL->L.nAblk),
+                                    reinterpret_cast<const double*>(wl + PL->L.car_a), P.nvr,
+                                    PL->f1_col, PL->f2_col, carA);
+    launches += 2;
+  } else {
+    k_encA_cols<<<dim3((unsigned)nchA, gy(P.nvr)), kThreads, 0, st>>>(
+        A, d.lda, d.m, d.k, d.vb_rows, P.er, acs, partA, nchA);
+    ++launches;
+    if (P.bs > 0) {
+      k_encA_block<<<dim3((unsigned)cdiv(d.k, kThreads), gy(P.f * P.bs)), kThreads, 0, st>>>(
+          A, d.lda, d.k, d.grid_p, P.bs, P.f, acs + 2 * P.nvr * d.k);
+      ++launches;
+    }
+  }
+  k_row_norms<<<(unsigned)cdiv(d.m * 32, kThreads), kThreads, 0, st>>>(A, d.lda, d.m, d.k, nArow);
+
+  if (PR) {  // columns of B: the earlier product's F (k x Cc)
+    const char* wr = static_cast<const char*>(wsR);
+    const double* FR = reinterpret_cast<const double*>(wr + PR->L.F);
+    e = cudaMemcpyAsync(bcs, FR, sizeof(double) * (size_t)d.k * P.Cc, cudaMemcpyDeviceToDevice,
+                        st);
+    if (e != cudaSuccess) return e;
+    k_cols_sq<<<(unsigned)cdiv(P.Cc * nchB, kThreads), kThreads, 0, st>>>(bcs, d.k, P.Cc, partB,
+                                                                           nchB);
+    k_carry<<<1, kThreads, 0, st>>>(reinterpret_cast<const double*>(wr + PR->L.nArow), PR->d.m,
+                                    reinterpret_cast<const double*>(wr + PR->L.nBblk),
+                                    reinterpret_cast<const double*>(wr + PR->L.car_b), P.nvc,
+                                    PR->f1_row, PR->f2_row, carB);
+    launches += 2;
+  } else {
+    k_encB_rows<<<dim3((unsigned)cdiv(nchB, kThreads / 32), gy(P.nvc)), kThreads, 0, st>>>(
+        B, d.ldb, d.k, d.n, d.vb_cols, P.ec, bcs, P.Cc, partB, nchB);
+    ++launches;
+  }
+  k_col_sq<<<dim3((unsigned)cdiv(d.n, kThreads), gy(nchC)), kThreads, 0, st>>>(
+      B, d.ldb, d.k, d.n, partC);
+  k_sum_sqrt<<<(unsigned)cdiv(d.n, 128), 128, 0, st>>>(partC, d.n, nchC, 1, d.n, nBcol);
+  k_finalize_blk<<<(unsigned)cdiv(P.nvr, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA,
+                                                             nchA, nAblk);
+  k_finalize_blk<<<(unsigned)cdiv(P.nvc, 128), 128, 0, st>>>(nBcol, d.n, d.vb_cols, P.ec, partB,
+                                                             nchB, nBblk);
+  count_launches(launches + 5);
   return cudaGetLastError();
 }
 

@@ -115,6 +115,12 @@ void threshold_factors(int dtype, int64_t k, int64_t vb_r, int64_t vb_c, double*
 // Launchers (return cudaGetLastError() of the launches).
 cudaError_t launch_encode_f64(const Plan& P, const double* A, const double* B, void* ws,
                               cudaStream_t st);
+// Chained encode: the checksum rows of A carried from the earlier product PL
+// (its workspace wsL), and/or the checksum columns of B from PR (wsR); the
+// other side encoded as usual.  Writes the carried deviation bounds.
+cudaError_t launch_encode_f64_chained(const Plan& P, const double* A, const double* B, void* ws,
+                                      const Plan* PL, const void* wsL, const Plan* PR,
+                                      const void* wsR, cudaStream_t st);
 // Encode with its partial sums in a static device array (no workspace scratch).
 cudaError_t launch_encode_f64_noalloc(const Plan& P, const double* A, const double* B, void* ws,
                                       cudaStream_t st);

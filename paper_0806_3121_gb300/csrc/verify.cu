@@ -33,6 +33,8 @@ struct CheckArgs {
   const double* nAblk;
   const double* nBcol;
   const double* nBblk;
+  const double* carA;  // carried-checksum deviation bounds (zero unless chained)
+  const double* carB;
   int vb_r, vb_c, er, ec;
   int64_t nvr, nvc, Cc, bs, bc;
   double s, f1c, f2c, f1r, f2r;
@@ -85,14 +87,14 @@ __device__ __forceinline__ bool is_flagged(double re, double rw, double te, doub
 __device__ __forceinline__ void col_taus(const CheckArgs& a, int64_t I, int64_t j, double& te,
                                          double& tw) {
   const double nb = a.nBcol[j];
-  te = a.s * nb * (a.f1c * a.nAblk[4 * I + 0] + a.f2c * a.nAblk[4 * I + 2]);
-  tw = a.s * nb * (a.f1c * a.nAblk[4 * I + 1] + a.f2c * a.nAblk[4 * I + 3]);
+  te = a.s * nb * (a.f1c * a.nAblk[4 * I + 0] + a.f2c * a.nAblk[4 * I + 2] + a.carA[2 * I]);
+  tw = a.s * nb * (a.f1c * a.nAblk[4 * I + 1] + a.f2c * a.nAblk[4 * I + 3] + a.carA[2 * I + 1]);
 }
 __device__ __forceinline__ void row_taus(const CheckArgs& a, int64_t i, int64_t J, double& te,
                                          double& tw) {
   const double na = a.nArow[i];
-  te = a.s * na * (a.f1r * a.nBblk[4 * J + 0] + a.f2r * a.nBblk[4 * J + 2]);
-  tw = a.s * na * (a.f1r * a.nBblk[4 * J + 1] + a.f2r * a.nBblk[4 * J + 3]);
+  te = a.s * na * (a.f1r * a.nBblk[4 * J + 0] + a.f2r * a.nBblk[4 * J + 2] + a.carB[2 * J]);
+  tw = a.s * na * (a.f1r * a.nBblk[4 * J + 1] + a.f2r * a.nBblk[4 * J + 3] + a.carB[2 * J + 1]);
 }
 
 // Observed block sums run in the element type of C: binary64 for a binary64
@@ -827,6 +829,8 @@ CheckArgs make_args(const Plan& P, void* C, void* ws) {
   a.nAblk = reinterpret_cast<const double*>(w + P.L.nAblk);
   a.nBcol = reinterpret_cast<const double*>(w + P.L.nBcol);
   a.nBblk = reinterpret_cast<const double*>(w + P.L.nBblk);
+  a.carA = reinterpret_cast<const double*>(w + P.L.car_a);
+  a.carB = reinterpret_cast<const double*>(w + P.L.car_b);
   a.vb_r = P.d.vb_rows; a.vb_c = P.d.vb_cols; a.er = P.er; a.ec = P.ec;
   a.nvr = P.nvr; a.nvc = P.nvc; a.Cc = P.Cc; a.bs = P.bs; a.bc = P.bc;
   a.s = P.s; a.f1c = P.f1_col; a.f2c = P.f2_col; a.f1r = P.f1_row; a.f2r = P.f2_row;

@@ -50,8 +50,10 @@ def test_workspace_layout_shapes(lib):
     L = abft.abft_workspace_layout(d)
     assert L.nvr == 22 and L.nvc == 22 and L.bs == 512
     assert L.R == 2 * 22 + 512 and L.Cc == 44
-    for off in (L.acs, L.bcs, L.E, L.F, L.nArow, L.nAblk, L.nBcol, L.nBblk, L.scratch):
+    for off in (L.acs, L.bcs, L.E, L.F, L.nArow, L.nAblk, L.nBcol, L.nBblk, L.car_a, L.car_b,
+                L.scratch):
         assert off % 256 == 0
+    assert L.car_b >= L.car_a + 2 * 22 * 8 and L.scratch >= L.car_b + 2 * 22 * 8
     assert L.bcs >= L.acs + L.R * 11264 * 8
     assert L.E >= L.bcs + 11264 * L.Cc * 8
     assert L.F >= L.E + L.R * 11264 * 8
@@ -107,6 +109,34 @@ def test_invalid_calls_launch_nothing(lib):
     d2 = abft.make_desc(64, 64, 64, "f64", 32, 32)
     st = lib.abft_recover_block(ct.byref(d2), ct.c_void_p(1), ct.c_void_p(1), 0, 0, None, None)
     assert st == abft.ERR_INVALID and "grid" in lib.abft_last_error().decode()
+
+
+@pytest.mark.parametrize("side,kw,status,msg", [
+    ("left", dict(m=96), abft.ERR_INVALID, "left chain"),          # earlier product m != m
+    ("left", dict(n=40), abft.ERR_INVALID, "left chain"),          # earlier n != this k
+    ("left", dict(vb_rows=16), abft.ERR_INVALID, "left chain"),
+    ("left", dict(grid_p=0, grid_q=0), abft.ERR_INVALID, "grid"),  # no block checksums to carry
+    ("left", dict(dtype=1, lda=64, ldb=80), abft.ERR_UNSUPPORTED, "ABFT_F64"),
+    ("right", dict(m=32), abft.ERR_INVALID, "right chain"),        # earlier m != this k
+    ("right", dict(vb_cols=8), abft.ERR_INVALID, "right chain"),
+    ("this", dict(dtype=1), abft.ERR_UNSUPPORTED, "ABFT_F64"),
+])
+def test_chained_encode_validation_launches_nothing(lib, side, kw, status, msg):
+    """Shape, grid and dtype mismatches of a chained encode are refused on the host."""
+    this = abft.make_desc(64, 48, 80, "f64", 32, 16, 2, 2)       # C' = A' B', A' is 64 x 80
+    left = abft.make_desc(64, 80, 20, "f64", 32, 16, 2, 2)       # earlier 64 x 80 product
+    right = abft.make_desc(80, 48, 20, "f64", 16, 16)            # earlier 80 x 48 product
+    tgt = {"left": left, "right": right, "this": this}[side]
+    for k, v in kw.items():
+        setattr(tgt, k, v)
+    fake = ct.c_void_p(1)
+    st = lib.abft_encode_chained(ct.byref(this), fake, fake,
+                                 ct.byref(left) if side in ("left", "this") else None,
+                                 fake if side in ("left", "this") else None,
+                                 ct.byref(right) if side == "right" else None,
+                                 fake if side == "right" else None, fake, None)
+    assert st == status
+    assert msg in lib.abft_last_error().decode()
 
 
 def test_empty_problem_is_a_no_op(lib):

@@ -41,6 +41,11 @@ constexpr int kEpiWarps = ABFT_EPI_WARPS;         // 4 or 8 (one or two per TMEM
 constexpr int kEpiCols = BN * 4 / kEpiWarps;       // tile columns per epilogue warp
 constexpr int kEpiChunks = kEpiCols / 32;          // 32-column TMEM loads per warp
 constexpr int kThreads = 64 + 32 * kEpiWarps;
+// Every epilogue warp reads whole 32-column chunks of its TMEM lane quarter:
+// a split that is not a multiple of 32 columns would read past the
+// accumulator (and past the allocated TMEM for the second one).
+static_assert(kEpiWarps == 4 || kEpiWarps == 8, "4 or 8 epilogue warps");
+static_assert((BN * 4) % kEpiWarps == 0 && kEpiCols % 32 == 0, "whole 32-column chunks");
 constexpr uint32_t A_BYTES = BM * BK * 2;          // 16 KiB
 constexpr uint32_t B_BOX_BYTES = 64 * BK * 2;      // one 64-column box: 8 KiB
 constexpr uint32_t B_BYTES = BN * BK * 2;          // 32 KiB
@@ -238,6 +243,9 @@ struct SingleSched {
   }
 };
 
+// Row-wise store of one lane's 32 consecutive values (lane = row): the
+// promoted epilogue keeps its whole part of the tile in registers, and the
+// transposed store below would spill there.
 __device__ __forceinline__ void store_row32(float* dst, int64_t ld, int64_t row, int64_t col,
                                             int64_t clim, const float (&v)[32]) {
   float* p = dst + row * ld + col;
@@ -265,6 +273,42 @@ __device__ __forceinline__ void transpose_reduce(float (&v)[32], int lane) {
       v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
     }
   }
+}
+
+// 32 x 32 transpose across the lanes of a warp: on entry lane l holds row l
+// of the block in v[0..31], on return lane l holds column l (v[i] = element
+// (i, l)).  Butterfly over the five lane bits, 16 shuffles each.
+__device__ __forceinline__ void transpose32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      if ((i & s) == 0) {
+        const float send = upper ? v[i] : v[i | s];
+        const float recv = __shfl_xor_sync(0xffffffffu, send, s);
+        if (upper)
+          v[i] = recv;
+        else
+          v[i | s] = recv;
+      }
+    }
+  }
+}
+
+// Stores a transposed 32 x 32 block (lane = column c0 + lane, v[i] = row r0 + i)
+// into a row-major fp32 matrix: each store instruction writes one row's 32
+// consecutive columns.  Rows >= rlim and columns >= clim are skipped.
+__device__ __forceinline__ void store_cols32(float* dst, int64_t ld, int64_t r0, int64_t c0,
+                                             int64_t rlim, int64_t clim, const float (&v)[32],
+                                             int lane) {
+  const int64_t col = c0 + lane;
+  const int64_t nr = rlim - r0;
+  if (col >= clim || nr <= 0) return;
+  float* p = dst + r0 * ld + col;
+#pragma unroll
+  for (int i = 0; i < 32; ++i)
+    if (i < nr) p[(int64_t)i * ld] = v[i];
 }
 
 
@@ -458,31 +502,29 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
         inj_hit = __any_sync(0xffffffffu, inj_hit);
       }
       const float scr = scalbnf(1.0f, -T.er), scc = scalbnf(1.0f, -T.ec);
-      const float wrow = (fused && drow) ? (float)((int)(row % T.vb_r) + 1) * scr : 0.f;
       float* obs = obs_buf + eb * (4 * BN * 2);
       float racc_e = 0.f, racc_w = 0.f;
-      // one 32-column chunk of the finished tile: fault injection, stores,
-      // fused observed sums (v is consumed)
+      // first row of this warp's 32 (data rows, checksum rows or none)
+      const int64_t r0 = row - lane;
+      const int64_t rlim = drow ? T.m : (crow ? T.R16 : 0);
+      // one 32-column chunk of the finished tile: fault injection, row
+      // partials (lane = row), transpose (lane = column), coalesced stores,
+      // column partials (v is consumed)
       auto chunk = [&](int c, float (&v)[32]) {
         const bool dcol = c < ndcol;
         if (dcol) {
           const int64_t col = T.colD + c;
           if (col >= T.n) return;
-          if (drow) {
-            if (inj_hit)
-              for (int f = 0; f < ninj; ++f) {
-                const InjectEntry ie = inj[f];
-                if (ie.pad == T.prob && ie.row == row && ie.col >= col && ie.col < col + 32) {
-                  const int x = ie.col - (int)col;
+          if (drow && inj_hit)
+            for (int f = 0; f < ninj; ++f) {
+              const InjectEntry ie = inj[f];
+              if (ie.pad == T.prob && ie.row == row && ie.col >= col && ie.col < col + 32) {
+                const int x = ie.col - (int)col;
 #pragma unroll
-                  for (int u = 0; u < 32; ++u)
-                    if (u == x) v[u] = __uint_as_float(__float_as_uint(v[u]) ^ (1u << (ie.bit & 31)));
-                }
+                for (int u = 0; u < 32; ++u)
+                  if (u == x) v[u] = __uint_as_float(__float_as_uint(v[u]) ^ (1u << (ie.bit & 31)));
               }
-            if (rvalid) store_row32(T.C, T.ldc, row, col, T.n, v);
-          } else if (rvalid) {
-            store_row32(T.E16, T.n, row, col, T.n, v);
-          }
+            }
           if (fused && drow) {
             // row partials over the column group (weights restart per verify
             // block; a 32-column chunk never straddles one, a group never
@@ -501,18 +543,50 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
               }
               racc_e = racc_w = 0.f;
             }
-            // column partials of this warp's 32 rows
-            float vw[32];
-#pragma unroll
-            for (int u = 0; u < 32; ++u) vw[u] = wrow * v[u];
-            transpose_reduce(vw, lane);
-            transpose_reduce(v, lane);
-            obs[(q * BN + c + lane) * 2 + 0] = v[0];
-            obs[(q * BN + c + lane) * 2 + 1] = vw[0];
           }
-        } else if (drow && rvalid) {
+          if (!drow && !crow) return;
+          if constexpr (kPromote) {
+            if (rvalid) store_row32(drow ? T.C : T.E16, drow ? T.ldc : T.n, row, col, T.n, v);
+            if (fused && drow) {
+              const float wrow = (float)((int)(row % T.vb_r) + 1) * scr;
+              float vw[32];
+#pragma unroll
+              for (int u = 0; u < 32; ++u) vw[u] = wrow * v[u];
+              transpose_reduce(vw, lane);
+              transpose_reduce(v, lane);
+              obs[(q * BN + c + lane) * 2 + 0] = v[0];
+              obs[(q * BN + c + lane) * 2 + 1] = vw[0];
+            }
+          } else {
+            transpose32(v, lane);
+            if (drow)
+              store_cols32(T.C, T.ldc, r0, col, rlim, T.n, v, lane);
+            else
+              store_cols32(T.E16, T.n, r0, col, rlim, T.n, v, lane);
+            if (fused && drow) {
+              // column partials of this warp's 32 rows (weights of the rows in
+              // their verify block; the 32 rows never straddle one)
+              const int rb = (int)(r0 % T.vb_r) + 1;
+              float se = 0.f, sw = 0.f;
+#pragma unroll
+              for (int i = 0; i < 32; ++i) {
+                se += v[i];
+                sw = fmaf((float)(rb + i) * scr, v[i], sw);
+              }
+              obs[(q * BN + c + lane) * 2 + 0] = se;
+              obs[(q * BN + c + lane) * 2 + 1] = sw;
+            }
+          }
+        } else if (drow) {
           const int64_t col = T.colC + (c - ndcol);
-          if (col < T.C16) store_row32(T.F16, T.C16, row, col, T.C16, v);
+          if (col < T.C16) {
+            if constexpr (kPromote) {
+              if (rvalid) store_row32(T.F16, T.C16, row, col, T.C16, v);
+            } else {
+              transpose32(v, lane);
+              store_cols32(T.F16, T.C16, r0, col, rlim, T.C16, v, lane);
+            }
+          }
         }
       };
       if (!kPromote || gsz >= nkt) {

@@ -123,7 +123,7 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
             (256 % d->vb_cols == 0 || d->vb_cols % 256 == 0);
   p.g = d->vb_cols < 128 ? d->vb_cols : 128;  // row-sum groups never straddle 128 columns
   p.ngrp = d->n > 0 ? cdiv(d->n, p.g) : 0;
-  p.ntr_obs = d->m > 0 ? cdiv(d->m, 128) : 0;
+  p.ntr_obs = d->m > 0 ? cdiv(d->m, 32) : 0;  // observed column sums per 32 rows
 
 
   abft_ws_layout& L = p.L;

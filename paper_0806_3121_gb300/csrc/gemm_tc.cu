@@ -51,9 +51,9 @@ constexpr uint32_t B_BOX_BYTES = 64 * BK * 2;      // one 64-column box: 8 KiB
 constexpr uint32_t B_BYTES = BN * BK * 2;          // 32 KiB
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t TMEM_COLS = 2 * BN;             // two accumulators
-constexpr uint32_t OBS_BYTES = 2 * 4 * BN * 2 * 4; // column partials (e, w) per lane quarter,
-                                                   // two buffers (alternate fused tiles)
-constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + OBS_BYTES + 256;
+constexpr uint32_t STG_BYTES = 32 * 32 * 4;        // one epilogue warp's staging block
+constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + kEpiWarps * STG_BYTES + 256;
+static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
 
 // Tensor maps of the operands, per bf16 plane (the split dtypes have 2 or 3
 // planes; unused planes repeat plane 0).  The K loop runs nseg segments;
@@ -62,6 +62,7 @@ constexpr int kPlanes = 3;
 struct TcMaps {
   CUtensorMap a[kPlanes], acs[kPlanes], b[kPlanes], bcs[kPlanes], a128[kPlanes],
       acs128[kPlanes], b4[kPlanes], bcs4[kPlanes];
+  CUtensorMap cst, est, fst;  // fp32 store maps of C, E16, F16 (valid per TcArgs::st_ok)
 };
 
 struct TcArgs {
@@ -76,8 +77,9 @@ struct TcArgs {
   float* F16;  // m x C16
   int* status;
   // fused observed checksums of data tiles (nullptr: off)
-  float* obs_col;  // [tile row][2][n]
+  float* obs_col;  // [32-row block][2][n]
   float* obs_row;  // [row][ngrp][2]
+  int st_ok;       // bit 0/1/2: TMA store map of C / E16 / F16 valid
   int vb_r, vb_c, er, ec;
   int64_t g, ngrp;
   const int32_t* inj_hdr;    // armed epilogue injections (nullptr: none)
@@ -171,8 +173,12 @@ struct TileView {
   int64_t R16;
   float* F16;                 // data rows x checksum columns, ld C16
   int64_t C16;
+  // TMA store maps of the three outputs (nullptr: plain stores)
+  const CUtensorMap* sC;
+  const CUtensorMap* sE;
+  const CUtensorMap* sF;
   // fused observed checksums of data tiles (obs_col == nullptr: off)
-  float* obs_col;             // [tile row][2][n]
+  float* obs_col;             // [32-row block][2][n]
   float* obs_row;             // [row][ngrp][2]
   int64_t g, ngrp;
   int vb_r, vb_c, er, ec;
@@ -231,6 +237,9 @@ struct SingleSched {
     V.R16 = g.R16;
     V.F16 = g.F16;
     V.C16 = g.C16;
+    V.sC = (g.st_ok & 1) ? &M->cst : nullptr;
+    V.sE = (g.st_ok & 2) ? &M->est : nullptr;
+    V.sF = (g.st_ok & 4) ? &M->fst : nullptr;
     V.obs_col = T.kind == 0 ? g.obs_col : nullptr;
     V.obs_row = g.obs_row;
     V.g = g.g;
@@ -243,9 +252,9 @@ struct SingleSched {
   }
 };
 
-// Row-wise store of one lane's 32 consecutive values (lane = row): the
-// promoted epilogue keeps its whole part of the tile in registers, and the
-// transposed store below would spill there.
+// Row-wise store of one lane's 32 consecutive values (lane = row), for
+// outputs without a TMA store map (a leading dimension or base address that
+// is not 16-byte aligned).
 __device__ __forceinline__ void store_row32(float* dst, int64_t ld, int64_t row, int64_t col,
                                             int64_t clim, const float (&v)[32]) {
   float* p = dst + row * ld + col;
@@ -260,55 +269,22 @@ __device__ __forceinline__ void store_row32(float* dst, int64_t ld, int64_t row,
   }
 }
 
-// Column sums across the 32 lanes of a warp: on return lane l holds, in
-// v[0], the sum over all lanes of their element l (31 shuffles).
-__device__ __forceinline__ void transpose_reduce(float (&v)[32], int lane) {
+// One warp's 32 x 32 fp32 staging block for the TMA store of a chunk: row r
+// (128 bytes) at r * 128, its 16-byte unit j at unit j ^ (r % 8) -- the
+// 128-byte swizzle of a TMA box with 32 fp32 columns (the block is
+// 1024-byte aligned).  Lane r writes its row: for each unit the 32 lanes
+// cover all 32 banks once per 8 rows (4 wavefronts, the minimum).
+__device__ __forceinline__ void stage_row32(float* stg, int lane, const float (&v)[32]) {
+  float4* rowp = reinterpret_cast<float4*>(stg + lane * 32);
 #pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) {
-    const bool upper = (lane & s) != 0;
-#pragma unroll
-    for (int i = 0; i < s; ++i) {
-      const float send = upper ? v[i] : v[i + s];
-      const float keep = upper ? v[i + s] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
-    }
-  }
+  for (int j = 0; j < 8; ++j)
+    rowp[j ^ (lane & 7)] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
 }
 
-// 32 x 32 transpose across the lanes of a warp: on entry lane l holds row l
-// of the block in v[0..31], on return lane l holds column l (v[i] = element
-// (i, l)).  Butterfly over the five lane bits, 16 shuffles each.
-__device__ __forceinline__ void transpose32(float (&v)[32], int lane) {
-#pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) {
-    const bool upper = (lane & s) != 0;
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      if ((i & s) == 0) {
-        const float send = upper ? v[i] : v[i | s];
-        const float recv = __shfl_xor_sync(0xffffffffu, send, s);
-        if (upper)
-          v[i] = recv;
-        else
-          v[i | s] = recv;
-      }
-    }
-  }
-}
-
-// Stores a transposed 32 x 32 block (lane = column c0 + lane, v[i] = row r0 + i)
-// into a row-major fp32 matrix: each store instruction writes one row's 32
-// consecutive columns.  Rows >= rlim and columns >= clim are skipped.
-__device__ __forceinline__ void store_cols32(float* dst, int64_t ld, int64_t r0, int64_t c0,
-                                             int64_t rlim, int64_t clim, const float (&v)[32],
-                                             int lane) {
-  const int64_t col = c0 + lane;
-  const int64_t nr = rlim - r0;
-  if (col >= clim || nr <= 0) return;
-  float* p = dst + r0 * ld + col;
-#pragma unroll
-  for (int i = 0; i < 32; ++i)
-    if (i < nr) p[(int64_t)i * ld] = v[i];
+// Element (r, c) of a staged block (conflict-free when the lanes read one
+// row's 32 columns).
+__device__ __forceinline__ float staged_at(const float* stg, int r, int c) {
+  return stg[r * 32 + (((c >> 2) ^ (r & 7)) << 2) + (c & 3)];
 }
 
 
@@ -323,10 +299,11 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + OBS_BYTES);
+  uint64_t* bars =
+      reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + kEpiWarps * STG_BYTES);
   // bars[0..S): full, [S..2S): empty, [2S..2S+2): tmem full, [2S+2..2S+4): tmem empty,
-  // [2S+4]: drain, [2S+5..2S+7): epilogue combine (one per partial buffer)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 7);
+  // [2S+4]: drain
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -335,7 +312,6 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
   auto tfull = [&](int a) { return tc::smem_addr(&bars[2 * STAGES + a]); };
   auto tempty = [&](int a) { return tc::smem_addr(&bars[2 * STAGES + 2 + a]); };
   const uint32_t drain = tc::smem_addr(&bars[2 * STAGES + 4]);
-  auto ecomb = [&](int b) { return tc::smem_addr(&bars[2 * STAGES + 5 + b]); };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -347,8 +323,6 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
       tc::mbar_init(tempty(a), kEpiWarps);
     }
     tc::mbar_init(drain, 1);
-    tc::mbar_init(ecomb(0), kEpiWarps);
-    tc::mbar_init(ecomb(1), kEpiWarps);
     *abort = 0;
     tc::wait_limit_ns() = wait_ns;
     tc::fence_barrier_init();
@@ -467,11 +441,13 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
     __syncwarp();
   } else {
     // ---------------- epilogue: warps 2..9; TMEM lane quarter q = warp % 4 (a
-    // warp may only read its quarter), column half = (warp - 2) / 4
+    // warp may only read its quarter), column half = (warp - 2) / 4.  Each
+    // 32 x 32 chunk goes to this warp's staging block in shared memory (the
+    // 128-byte-swizzled layout of a TMA box) and from there to global memory
+    // by a TMA store; the fused column sums read the staged columns back.
     const int q = warp & 3, half = q >> 1, c_lo = kEpiCols * ((warp - 2) >> 2);
-    float* obs_buf = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);  // [2][4][BN][2]
-    int eb = 0;               // partial buffer of the next fused tile
-    uint32_t eph[2] = {0, 0};  // phase of each buffer's combine barrier
+    float* stg = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + (warp - 2) * STG_BYTES);
+    const uint32_t stg_addr = tc::smem_addr(stg);
     const int ninj = (inj_hdr && inj_hdr[0] == kInjectMagic)
                          ? max(0, min(inj_hdr[1], kMaxInject)) : 0;
     int acc = 0;
@@ -487,13 +463,14 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
       const bool drow = half < T.hsplit, crow = !drow && half < T.hcnt;
       const int64_t rin = 32 * (q & 1) + lane;
       const int64_t row = drow ? T.rowD + 64 * half + rin : T.rowC + 64 * (half - T.hsplit) + rin;
+      const int64_t r0 = row - lane;  // first of the warp's 32 rows
       const bool rvalid = drow ? row < T.m : (crow && row < T.R16);
       const int ndcol = 64 * T.bsplit;
       const bool fused = T.obs_col != nullptr && T.hsplit > 0 && T.bsplit > 0;
       // armed faults inside this warp's part of the tile (one pass over the list)
       bool inj_hit = false;
       if (drow && ninj > 0) {
-        const int64_t r0 = T.rowD + 64 * half + 32 * (q & 1), c0 = T.colD + c_lo;
+        const int64_t c0 = T.colD + c_lo;
         for (int f = lane; f < ninj; f += 32) {
           const InjectEntry ie = inj[f];
           inj_hit |= ie.pad == T.prob && ie.row >= r0 && ie.row < r0 + 32 && ie.col >= c0 &&
@@ -502,14 +479,23 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
         inj_hit = __any_sync(0xffffffffu, inj_hit);
       }
       const float scr = scalbnf(1.0f, -T.er), scc = scalbnf(1.0f, -T.ec);
-      float* obs = obs_buf + eb * (4 * BN * 2);
       float racc_e = 0.f, racc_w = 0.f;
-      // first row of this warp's 32 (data rows, checksum rows or none)
-      const int64_t r0 = row - lane;
-      const int64_t rlim = drow ? T.m : (crow ? T.R16 : 0);
+      // Stage v (lane = row) into this warp's block; with a store map, send
+      // the block to (x, y) by one TMA store.  The block is reused only after
+      // the previous store has read it and every lane is past its reads.
+      auto stage = [&](const float (&v)[32], const CUtensorMap* map, int64_t x, int64_t y) {
+        if (lane == 0) tc::bulk_wait_read0();
+        __syncwarp();
+        stage_row32(stg, lane, v);
+        if (map) tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (map && lane == 0) {
+          tc::tma_store_2d(map, stg_addr, (int32_t)x, (int32_t)y);
+          tc::bulk_commit();
+        }
+      };
       // one 32-column chunk of the finished tile: fault injection, row
-      // partials (lane = row), transpose (lane = column), coalesced stores,
-      // column partials (v is consumed)
+      // partials (lane = row), store, column partials (v is consumed)
       auto chunk = [&](int c, float (&v)[32]) {
         const bool dcol = c < ndcol;
         if (dcol) {
@@ -545,47 +531,36 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
             }
           }
           if (!drow && !crow) return;
-          if constexpr (kPromote) {
-            if (rvalid) store_row32(drow ? T.C : T.E16, drow ? T.ldc : T.n, row, col, T.n, v);
-            if (fused && drow) {
-              const float wrow = (float)((int)(row % T.vb_r) + 1) * scr;
-              float vw[32];
+          if (r0 >= (drow ? T.m : T.R16)) return;  // all 32 rows past the output
+          const CUtensorMap* map = drow ? T.sC : T.sE;
+          const bool colsums = fused && drow;
+          if (map || colsums) stage(v, map, col, r0);
+          if (!map && rvalid) store_row32(drow ? T.C : T.E16, drow ? T.ldc : T.n, row, col, T.n, v);
+          if (colsums) {
+            // column partials of this warp's 32 rows (lane = column) from the
+            // staged block; weights of the rows in their verify block (the 32
+            // rows never straddle one)
+            const int rb = (int)(r0 % T.vb_r) + 1;
+            float se = 0.f, sw = 0.f;
 #pragma unroll
-              for (int u = 0; u < 32; ++u) vw[u] = wrow * v[u];
-              transpose_reduce(vw, lane);
-              transpose_reduce(v, lane);
-              obs[(q * BN + c + lane) * 2 + 0] = v[0];
-              obs[(q * BN + c + lane) * 2 + 1] = vw[0];
+            for (int i = 0; i < 32; ++i) {
+              const float x = staged_at(stg, i, lane);
+              se += x;
+              sw = fmaf((float)(rb + i) * scr, x, sw);
             }
-          } else {
-            transpose32(v, lane);
-            if (drow)
-              store_cols32(T.C, T.ldc, r0, col, rlim, T.n, v, lane);
-            else
-              store_cols32(T.E16, T.n, r0, col, rlim, T.n, v, lane);
-            if (fused && drow) {
-              // column partials of this warp's 32 rows (weights of the rows in
-              // their verify block; the 32 rows never straddle one)
-              const int rb = (int)(r0 % T.vb_r) + 1;
-              float se = 0.f, sw = 0.f;
-#pragma unroll
-              for (int i = 0; i < 32; ++i) {
-                se += v[i];
-                sw = fmaf((float)(rb + i) * scr, v[i], sw);
-              }
-              obs[(q * BN + c + lane) * 2 + 0] = se;
-              obs[(q * BN + c + lane) * 2 + 1] = sw;
+            if (r0 < T.m && col + lane < T.n) {
+              float* o = T.obs_col + (r0 >> 5) * 2 * T.n + col + lane;
+              o[0] = se;
+              o[T.n] = sw;
             }
           }
-        } else if (drow) {
+        } else if (drow && r0 < T.m) {
           const int64_t col = T.colC + (c - ndcol);
           if (col < T.C16) {
-            if constexpr (kPromote) {
-              if (rvalid) store_row32(T.F16, T.C16, row, col, T.C16, v);
-            } else {
-              transpose32(v, lane);
-              store_cols32(T.F16, T.C16, r0, col, rlim, T.C16, v, lane);
-            }
+            if (T.sF)
+              stage(v, T.sF, col, r0);
+            else if (rvalid)
+              store_row32(T.F16, T.C16, row, col, T.C16, v);
           }
         }
       };
@@ -646,32 +621,12 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
         for (int ci = 0; ci < kEpiChunks; ++ci)
           if (c_lo + 32 * ci < c_hi) chunk(c_lo + 32 * ci, accr[ci]);
       }
-      if (fused) {
-        // all epilogue warps' partials are in this buffer once its combine
-        // barrier completes (bounded wait; the next fused tile uses the other
-        // buffer, so no second barrier is needed before this one is rewritten)
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(ecomb(eb));
-        if (!tc::wait(ecomb(eb), eph[eb], abort)) break;
-        eph[eb] ^= 1;
-#pragma unroll
-        for (int cc = (warp - 2) * 32 + lane; cc < BN; cc += 32 * kEpiWarps) {
-          const int64_t col = T.colD + cc;
-          if (cc < ndcol && col < T.n) {
-            const int64_t tr = T.rowD / BM;
-            float se = 0.f, sw = 0.f;
-            for (int w4 = 0; w4 < 2 * T.hsplit; ++w4) {
-              se += obs[(w4 * BN + cc) * 2 + 0];
-              sw += obs[(w4 * BN + cc) * 2 + 1];
-            }
-            T.obs_col[(tr * 2 + 0) * T.n + col] = se;
-            T.obs_col[(tr * 2 + 1) * T.n + col] = sw;
-          }
-        }
-        eb ^= 1;
-      }
     }
+    // every TMA store of this warp has completed before the kernel ends
+    if (lane == 0) tc::bulk_wait0();
+    __syncwarp();
   }
+
 
   tc::fence_before_sync();
   __syncthreads();
@@ -755,6 +710,9 @@ struct GroupSched {
     V.R16 = P.R16;
     V.F16 = P.F16;
     V.C16 = P.C16;
+    V.sC = (P.st_ok & 1) ? &Mp.cst : nullptr;
+    V.sE = (P.st_ok & 2) ? &Mp.est : nullptr;
+    V.sF = (P.st_ok & 4) ? &Mp.fst : nullptr;
     V.obs_col = checksums ? P.obs_col : nullptr;
     V.obs_row = P.obs_row;
     V.g = P.g;
@@ -784,8 +742,8 @@ cudaError_t get_encoder() {
   std::call_once(g_encode_once, [] {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) ==
-            cudaSuccess &&
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
       g_encode_tiled = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   });
@@ -807,6 +765,25 @@ bool make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols, int
   return g_encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 2-D fp32 store map of a row-major rows x cols output with leading dimension
+// ld: box 32 x 32, 128-byte swizzle (the epilogue's staging layout).  TMA
+// needs a 16-byte aligned base and a row pitch that is a multiple of 16
+// bytes; otherwise (or for an empty output) there is no map and the
+// epilogue stores with plain instructions.  Out-of-range parts of a box are
+// not written.
+bool make_store_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols, int64_t ld) {
+  if (!ptr || rows <= 0 || cols <= 0 || (reinterpret_cast<uintptr_t>(ptr) & 15) || (ld * 4) % 16)
+    return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+  const cuuint32_t box[2] = {32, 32};
+  const cuuint32_t estr[2] = {1, 1};
+  return g_encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -916,6 +893,11 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
   }
   TcArgs g{};
   g.m = d.m; g.n = d.n; g.k = d.k; g.R16 = R16; g.C16 = C16;
+  g.st_ok = make_store_map(&M.cst, C, d.m, d.n, d.ldc) ? 1 : 0;
+  if (checksums) {
+    g.st_ok |= make_store_map(&M.est, w + P.L.E16, R16, d.n, d.n) ? 2 : 0;
+    g.st_ok |= make_store_map(&M.fst, w + P.L.F16, d.m, C16, C16) ? 4 : 0;
+  }
   g.nseg = op.nseg;
   g.seg_a = op.seg_a;
   g.seg_b = op.seg_b;
@@ -969,6 +951,14 @@ cudaError_t make_bf16_map(CUtensorMap* map, const void* ptr, int64_t rows, int64
   if (e != cudaSuccess) return e;
   return make_map(map, ptr, rows, cols, ld, box_cols, box_rows) ? cudaSuccess
                                                                 : cudaErrorInvalidValue;
+}
+
+cudaError_t make_f32_store_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols,
+                               int64_t ld, bool* ok) {
+  cudaError_t e = get_encoder();
+  if (e != cudaSuccess) return e;
+  *ok = make_store_map(map, ptr, rows, cols, ld);
+  return cudaSuccess;
 }
 
 cudaError_t make_bf16_map_boxes(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols,

@@ -142,6 +142,14 @@ abft_status upload_tables(abft_group_s& G, cudaStream_t st) {
         (e = make_bf16_map_boxes(&Mp.bcs4, P.bcs, q.k, s.C16, s.bcs_ld, 4)) != cudaSuccess)
       return fail(ABFT_ERR_INVALID, "problem %d: tensor map rejected (%s)", p,
                   cudaGetErrorString(e));
+    // TMA store maps of the outputs (an unaligned C is stored without one)
+    bool okc = false, oke = false, okf = false;
+    if ((e = make_f32_store_map(&Mp.cst, q.C, q.m, q.n, q.ldc, &okc)) != cudaSuccess ||
+        (e = make_f32_store_map(&Mp.est, P.E16, s.R16, q.n, q.n, &oke)) != cudaSuccess ||
+        (e = make_f32_store_map(&Mp.fst, P.F16, q.m, s.C16, s.C16, &okf)) != cudaSuccess)
+      return fail(ABFT_ERR_INVALID, "problem %d: store map rejected (%s)", p,
+                  cudaGetErrorString(e));
+    P.st_ok = (okc ? 1 : 0) | (oke ? 2 : 0) | (okf ? 4 : 0);
   }
   // product tile lists
   std::vector<int4> tcs, tpl;
@@ -345,7 +353,7 @@ abft_status abft_group_create(const abft_problem* problems, int32_t count, int32
     s.bcs = region((size_t)q.k * s.bcs_ld * 2);
     s.E16 = region((size_t)s.R16 * q.n * 4);
     s.F16 = region((size_t)q.m * s.C16 * 4);
-    s.obs_col = region((size_t)s.nvr * 2 * q.n * 4);
+    s.obs_col = region((size_t)cdiv(q.m, 32) * 2 * q.n * 4);  // per 32-row block
     s.obs_row = region((size_t)q.m * cdiv(q.n, 128) * 2 * 4);  // groups of >= 128 columns
     s.nArow = region((size_t)q.m * 8);
     s.nAblk = region((size_t)4 * s.nvr * 8);

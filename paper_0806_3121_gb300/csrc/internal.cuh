@@ -164,7 +164,7 @@ struct GProb {  // one problem of a group, in device memory
   int64_t acs_ld, bcs_ld, R16, C16;
   float* E16;      // R16 x n: acs B
   float* F16;      // m x C16: A bcs
-  float* obs_col;  // [tile row][2][n]: observed e/w column sums of each 128-row tile
+  float* obs_col;  // [32-row block][2][n]: observed e/w column sums of each 32 rows
   float* obs_row;  // [row][ngrp][2]: observed e/w row sums of each g-column group
   double* nArow;   // m: ||A_i||
   double* nAblk;   // 4 nvr: threshold norms of each verify row block
@@ -182,6 +182,7 @@ struct GProb {  // one problem of a group, in device memory
   double f1c, f1r, f2;  // threshold factors (the safety factor applies at use)
   int32_t nhc, nbc;     // checksum halves (64 rows) / boxes (64 columns)
   int32_t bpt, g;       // boxes per tile (tile width 64 bpt), row-sum group width
+  int32_t st_ok, pad2;  // bit 0/1/2: TMA store map of C / E16 / F16 valid
 };
 
 struct GMaps {  // tensor maps of one problem (64-byte aligned in device memory)
@@ -189,6 +190,7 @@ struct GMaps {  // tensor maps of one problem (64-byte aligned in device memory)
   CUtensorMap a128, acs128;     // 128-row boxes (a whole tile's A)
   CUtensorMap bw[3];            // 2, 3, 4 full 64-column boxes of B in one copy (3-D view)
   CUtensorMap bcs4;             // four full checksum boxes in one copy
+  CUtensorMap cst, est, fst;    // fp32 store maps of C, E16, F16 (per GProb::st_ok)
 };
 
 // The grouped kernels: CTA b of kernel kk works on problem tab[kk][b].x, its
@@ -228,6 +230,10 @@ cudaError_t make_bf16_map(CUtensorMap* map, const void* ptr, int64_t rows, int64
 // full 64-column box) with a box of `depth` 64 x 64 boxes.
 cudaError_t make_bf16_map_boxes(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols,
                                 int64_t ld, int depth);
+// fp32 TMA store map of a row-major output (box 32 x 32, 128-byte swizzle);
+// *ok = false (no map) when the base or the row pitch is not 16-byte aligned.
+cudaError_t make_f32_store_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols,
+                               int64_t ld, bool* ok);
 cudaError_t launch_group_encode(const GroupDev& G, cudaStream_t st);
 cudaError_t launch_group_gemm(const GroupDev& G, bool checksums, cudaStream_t st);
 cudaError_t launch_group_verify(const GroupDev& G, cudaStream_t st);

@@ -209,14 +209,14 @@ __global__ void __launch_bounds__(kThreads) k_row_check(const CheckArgs a) {
 }
 
 // Column lines from the observed partial sums the product's epilogue wrote
-// (one per 128-row tile): obs[(tile*2 + 0|1)*n + j].  Verify blocks span whole
-// tiles.  A non-finite observed sum marks the line non-finite (the locate
-// step then scans C for it).
+// (one per 32 rows): obs[(block*2 + 0|1)*n + j].  Verify blocks span whole
+// 32-row blocks.  A non-finite observed sum marks the line non-finite (the
+// locate step then scans C for it).
 __global__ void __launch_bounds__(kThreads) k_col_fused(const CheckArgs a, const float* obs,
                                                         int64_t ntr) {
   const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (j >= a.n) return;
-  const int64_t tpb = a.vb_r / 128;  // tiles per verify block
+  const int64_t tpb = a.vb_r / 32;  // 32-row blocks per verify block
   for (int64_t I = blockIdx.y; I < a.nvr; I += gridDim.y) {
     const int64_t i0 = I * a.vb_r, i1 = min(i0 + (int64_t)a.vb_r, a.m);
     if (touches_erased(a.erased, a.bs, a.bc, i0, i1, j, j + 1)) continue;
@@ -676,8 +676,12 @@ __global__ void __launch_bounds__(kThreads) k_grp_col(const GProb* __restrict__ 
   const int64_t ncx = cdiv(P.n, kThreads);
   const int64_t I = e.y / ncx, j = (e.y % ncx) * kThreads + threadIdx.x;
   if (j >= P.n) return;
-  const float se32 = P.obs_col[(I * 2 + 0) * P.n + j];
-  const float sw32 = P.obs_col[(I * 2 + 1) * P.n + j];
+  // the verify block (one tile row) is four 32-row blocks of observed sums
+  float se32 = 0.f, sw32 = 0.f;
+  for (int64_t b = 4 * I; b < min(4 * I + 4, cdiv(P.m, 32)); ++b) {
+    se32 += P.obs_col[(b * 2 + 0) * P.n + j];
+    sw32 += P.obs_col[(b * 2 + 1) * P.n + j];
+  }
   const float* E = P.E16 + 4 * I * P.n + j;
   const float nb = P.nBcol32[j];
   if (screen_pass(se32, sw32, E[0] + E[P.n], E[2 * P.n] + E[3 * P.n], nb * P.tauA[2 * I],

@@ -26,6 +26,26 @@ constexpr int kRowBatch = 8;               // rows whose loads are in flight tog
 constexpr int kRowBatchB = 16;             // the same for the B pass
 constexpr int kEncCols = 256;              // columns of one bf16 encode unit (8 per lane)
 constexpr int kEncWarps = kThreads / 32;   // warps sharing a unit's rows
+// A pass with asynchronous copies: each warp keeps kAsyncBatches batches of
+// kRowBatch rows in flight in its shared-memory ring (16 bytes per lane per
+// row), so the loads do not wait on registers.
+constexpr int kAsyncBatches = 2;
+constexpr int kRingBytesA = kEncWarps * kAsyncBatches * kRowBatch * 32 * 16;  // 64 KiB
+
+// 16-byte asynchronous global -> shared copy; bytes < 16 zero-fills the rest
+// (0: nothing is read).  Both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// All but the N most recent committed groups of this thread have landed.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 __device__ __forceinline__ float warp_sumf(float v) {
 #pragma unroll
@@ -106,51 +126,28 @@ __device__ __forceinline__ void store8(__nv_bfloat16* dst, const __nv_bfloat16 (
 // Column checksums of A per verify block (fp32 sums, hi/lo pieces), per-row
 // partial sums of squares (one per 256 columns) and per-CTA partials of the
 // squared norms of the two checksum rows.  Unit = 256 columns (chunk cx) x one
-// verify block I: lane = 8 consecutive columns, warp w = rows i0 + w + 8 t
-// (the loads of kRowBatch rows in flight together); the eight warps' column
-// sums meet in shared memory (red: [8][256][2] floats).
-__device__ __forceinline__ void lpA_unit(const __nv_bfloat16* __restrict__ A, int64_t lda,
-                                         int64_t m, int64_t k, int vb, int e,
-                                         __nv_bfloat16* __restrict__ acs, int64_t ldk,
-                                         float* __restrict__ rowpart, int64_t nchr,
-                                         double* __restrict__ part, int64_t cx, int64_t I,
-                                         float* red, float* sh) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t c0 = cx * kEncCols + 8 * lane;
-  const float sc = scalbnf(1.0f, -e);
-  const int64_t i0 = I * vb, i1 = min(i0 + (int64_t)vb, m);
-  const int nrow = (int)(i1 - i0);
-  const __nv_bfloat16* Ab = A + i0 * lda;
-  float se[8], sw[8];
+// verify block I: lane = 8 consecutive columns, warp w = rows i0 + w + 8 t;
+// the eight warps' column sums meet in shared memory (red: [8][256][2]
+// floats).  lpA_rows adds one row (its 1-based position t + 1 in the block)
+// into the lane's sums; lpA_finish combines the warps and writes the unit's
+// checksum pieces and norm partials.
+__device__ __forceinline__ void lpA_rows(const float (&v)[8], int t, float sc, float (&se)[8],
+                                         float (&sw)[8], float& sq) {
+  const float w = (float)(t + 1) * sc;
+  sq = 0.f;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) se[q] = sw[q] = 0.f;
-  for (int rb = warp; rb < nrow; rb += kEncWarps * kRowBatch) {
-    uint4 raw[kRowBatch];
-#pragma unroll
-    for (int r = 0; r < kRowBatch; ++r) {
-      const int t = rb + kEncWarps * r;
-      raw[r] = t < nrow ? load8raw(Ab + (int64_t)t * lda, c0, k) : make_uint4(0u, 0u, 0u, 0u);
-    }
-    float sq[kRowBatch];
-#pragma unroll
-    for (int r = 0; r < kRowBatch; ++r) {
-      const int t = rb + kEncWarps * r;
-      float v[8];
-      unpack8(raw[r], v);
-      const float w = (float)(t + 1) * sc;
-      sq[r] = 0.f;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        se[q] += v[q];
-        sw[q] = fmaf(w, v[q], sw[q]);
-        sq[r] = fmaf(v[q], v[q], sq[r]);
-      }
-    }
-    reduce_rows<kRowBatch>(sq, lane);  // row r's sum of squares in lanes r * (32 / kRowBatch) ..
-    constexpr int kLanesPerRow = 32 / kRowBatch;
-    const int t = rb + kEncWarps * (lane / kLanesPerRow);
-    if (lane % kLanesPerRow == 0 && t < nrow) rowpart[(i0 + t) * nchr + cx] = sq[0];
+  for (int q = 0; q < 8; ++q) {
+    se[q] += v[q];
+    sw[q] = fmaf(w, v[q], sw[q]);
+    sq = fmaf(v[q], v[q], sq);
   }
+}
+
+__device__ __forceinline__ void lpA_finish(const float (&se)[8], const float (&sw)[8],
+                                           __nv_bfloat16* __restrict__ acs, int64_t ldk,
+                                           double* __restrict__ part, int64_t nchr, int64_t cx,
+                                           int64_t I, float* red, float* sh) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     red[(warp * kEncCols + 8 * lane + q) * 2 + 0] = se[q];
@@ -182,6 +179,45 @@ __device__ __forceinline__ void lpA_unit(const __nv_bfloat16* __restrict__ A, in
   const float t1 = block_sumf(q1, sh);
   if (threadIdx.x == 0) part[(2 * I + 1) * nchr + cx] = (double)t1;
   __syncthreads();  // red is reused by the next unit
+}
+
+// One unit with register loads (any alignment): kRowBatch rows of loads in
+// flight per warp at a time.
+__device__ __forceinline__ void lpA_unit(const __nv_bfloat16* __restrict__ A, int64_t lda,
+                                         int64_t m, int64_t k, int vb, int e,
+                                         __nv_bfloat16* __restrict__ acs, int64_t ldk,
+                                         float* __restrict__ rowpart, int64_t nchr,
+                                         double* __restrict__ part, int64_t cx, int64_t I,
+                                         float* red, float* sh) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c0 = cx * kEncCols + 8 * lane;
+  const float sc = scalbnf(1.0f, -e);
+  const int64_t i0 = I * vb, i1 = min(i0 + (int64_t)vb, m);
+  const int nrow = (int)(i1 - i0);
+  const __nv_bfloat16* Ab = A + i0 * lda;
+  float se[8], sw[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) se[q] = sw[q] = 0.f;
+  constexpr int kLanesPerRow = 32 / kRowBatch;
+  for (int rb = warp; rb < nrow; rb += kEncWarps * kRowBatch) {
+    uint4 raw[kRowBatch];
+#pragma unroll
+    for (int r = 0; r < kRowBatch; ++r) {
+      const int t = rb + kEncWarps * r;
+      raw[r] = t < nrow ? load8raw(Ab + (int64_t)t * lda, c0, k) : make_uint4(0u, 0u, 0u, 0u);
+    }
+    float sq[kRowBatch];
+#pragma unroll
+    for (int r = 0; r < kRowBatch; ++r) {
+      float v[8];
+      unpack8(raw[r], v);
+      lpA_rows(v, rb + kEncWarps * r, sc, se, sw, sq[r]);
+    }
+    reduce_rows<kRowBatch>(sq, lane);  // row r's sum of squares in lanes r * kLanesPerRow ..
+    const int t = rb + kEncWarps * (lane / kLanesPerRow);
+    if (lane % kLanesPerRow == 0 && t < nrow) rowpart[(i0 + t) * nchr + cx] = sq[0];
+  }
+  lpA_finish(se, sw, acs, ldk, part, nchr, cx, I, red, sh);
 }
 
 __global__ void __launch_bounds__(kThreads, 2) k_lpA_cols(const __nv_bfloat16* __restrict__ A,
@@ -223,7 +259,70 @@ __global__ void __launch_bounds__(kThreads) k_lpA_block(const __nv_bfloat16* __r
 // 256 columns: the lanes of a block reduce with shuffles.  Unit = 256 columns
 // (chunk cx) x 128 rows (chunk ry): lane = 8 consecutive columns, warp w = rows
 // l0 + w + 8 t; the warps' column squares and block partials meet in shared
-// memory (red: [8][256] floats, redq: [8][32][2] floats).
+// memory (red: [8][256] floats, redq: [8][32][2] floats) in lpB_finish.
+__device__ __forceinline__ void lpB_finish(const float (&cs)[8], float q0, float q1, int64_t n,
+                                           int vb, float* __restrict__ colpart,
+                                           double* __restrict__ part, int64_t nch, int64_t cx,
+                                           int64_t ry, float* red, float* redq) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int seg = vb / 8;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) red[warp * kEncCols + 8 * lane + q] = cs[q];
+  redq[(warp * 32 + lane) * 2 + 0] = q0;
+  redq[(warp * 32 + lane) * 2 + 1] = q1;
+  __syncthreads();
+  const int c = threadIdx.x;
+  float t = 0.f;
+#pragma unroll
+  for (int w = 0; w < kEncWarps; ++w) t += red[w * kEncCols + c];
+  if (cx * kEncCols + c < n) colpart[ry * n + cx * kEncCols + c] = t;
+  if (c < 32 && (c % seg) == 0 && cx * kEncCols + 8 * c < n) {
+    float a0 = 0.f, a1 = 0.f;
+    for (int w = 0; w < kEncWarps; ++w) {
+      a0 += redq[(w * 32 + c) * 2 + 0];
+      a1 += redq[(w * 32 + c) * 2 + 1];
+    }
+    const int64_t Jc = (cx * kEncCols + 8 * c) / vb;
+    part[(2 * Jc) * nch + ry] = (double)a0;
+    part[(2 * Jc + 1) * nch + ry] = (double)a1;
+  }
+  __syncthreads();  // red / redq are reused by the next unit
+}
+
+// One row of B in a lane's 8 columns: its (e, w) partial sums (reduced over
+// the verify block by the caller) and the column squares.
+__device__ __forceinline__ void lpB_row(const float (&v)[8], const float (&wq)[8], float (&cs)[8],
+                                        float& se, float& sw) {
+  se = 0.f;
+  sw = 0.f;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    se += v[q];
+    sw = fmaf(wq[q], v[q], sw);
+    cs[q] = fmaf(v[q], v[q], cs[q]);
+  }
+}
+
+// The lanes' (e, w) sums of row l reduced over their verify block (seg lanes)
+// and stored as hi/lo pieces by the block's first lane.
+__device__ __forceinline__ void lpB_store_shfl(float se, float sw, int seg, bool leader, bool valid,
+                                               __nv_bfloat16* __restrict__ dst, float& q0,
+                                               float& q1) {
+  for (int o = seg >> 1; o > 0; o >>= 1) {
+    se += __shfl_xor_sync(0xffffffffu, se, o);
+    sw += __shfl_xor_sync(0xffffffffu, sw, o);
+  }
+  if (leader && valid) {
+    __nv_bfloat16 pc[4];
+    split(se, pc[0], pc[1]);
+    split(sw, pc[2], pc[3]);
+    *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(pc);
+    q0 = fmaf(se, se, q0);
+    q1 = fmaf(sw, sw, q1);
+  }
+}
+
+// One unit with register loads (any alignment).
 __device__ __forceinline__ void lpB_unit(const __nv_bfloat16* __restrict__ B, int64_t ldb,
                                          int64_t k, int64_t n, int vb, int e,
                                          __nv_bfloat16* __restrict__ bcs, int64_t ldcs,
@@ -256,50 +355,13 @@ __device__ __forceinline__ void lpB_unit(const __nv_bfloat16* __restrict__ B, in
 #pragma unroll
     for (int r = 0; r < kRowBatchB; ++r) {
       const int64_t l = l0 + rb + kEncWarps * r;
-      float v[8];
+      float v[8], se, sw;
       unpack8(raw[r], v);
-      float se = 0.f, sw = 0.f;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        se += v[q];
-        sw = fmaf(wq[q], v[q], sw);
-        cs[q] = fmaf(v[q], v[q], cs[q]);
-      }
-      for (int o = seg >> 1; o > 0; o >>= 1) {
-        se += __shfl_xor_sync(0xffffffffu, se, o);
-        sw += __shfl_xor_sync(0xffffffffu, sw, o);
-      }
-      if (leader && l < l1) {
-        __nv_bfloat16 pc[4];
-        split(se, pc[0], pc[1]);
-        split(sw, pc[2], pc[3]);
-        *reinterpret_cast<uint2*>(bcs + l * ldcs + 4 * J) = *reinterpret_cast<const uint2*>(pc);
-        q0 = fmaf(se, se, q0);
-        q1 = fmaf(sw, sw, q1);
-      }
+      lpB_row(v, wq, cs, se, sw);
+      lpB_store_shfl(se, sw, seg, leader, l < l1, bcs + l * ldcs + 4 * J, q0, q1);
     }
   }
-#pragma unroll
-  for (int q = 0; q < 8; ++q) red[warp * kEncCols + 8 * lane + q] = cs[q];
-  redq[(warp * 32 + lane) * 2 + 0] = q0;
-  redq[(warp * 32 + lane) * 2 + 1] = q1;
-  __syncthreads();
-  const int c = threadIdx.x;
-  float t = 0.f;
-#pragma unroll
-  for (int w = 0; w < kEncWarps; ++w) t += red[w * kEncCols + c];
-  if (cx * kEncCols + c < n) colpart[ry * n + cx * kEncCols + c] = t;
-  if (c < 32 && (c % seg) == 0 && cx * kEncCols + 8 * c < n) {
-    float a0 = 0.f, a1 = 0.f;
-    for (int w = 0; w < kEncWarps; ++w) {
-      a0 += redq[(w * 32 + c) * 2 + 0];
-      a1 += redq[(w * 32 + c) * 2 + 1];
-    }
-    const int64_t Jc = (cx * kEncCols + 8 * c) / vb;
-    part[(2 * Jc) * nch + ry] = (double)a0;
-    part[(2 * Jc + 1) * nch + ry] = (double)a1;
-  }
-  __syncthreads();  // red / redq are reused by the next unit
+  lpB_finish(cs, q0, q1, n, vb, colpart, part, nch, cx, ry, red, redq);
 }
 
 __global__ void __launch_bounds__(kThreads, 2) k_lpB_rows(const __nv_bfloat16* __restrict__ B,
@@ -311,6 +373,278 @@ __global__ void __launch_bounds__(kThreads, 2) k_lpB_rows(const __nv_bfloat16* _
   __shared__ float redq[kEncWarps * 32 * 2];
   for (int64_t ry = blockIdx.y; ry < nch; ry += gridDim.y)
     lpB_unit(B, ldb, k, n, vb, e, bcs, ldcs, colpart, part, nch, blockIdx.x, ry, red, redq);
+}
+
+// ---------------- streaming encode (16-byte aligned operands and row pitch)
+// Persistent CTAs; each warp copies its rows of the CTA's units into its own
+// shared-memory ring (16 bytes per lane per row) with asynchronous copies,
+// kAsyncBatches batches of kRowBatch rows ahead of the arithmetic.  The ring
+// runs across units, so the loads of the next unit overlap the finishing of
+// the current one, and no register holds a load in flight.
+
+struct EncAUnit {  // 256 columns (chunk cx) x verify block I of A
+  const __nv_bfloat16* A;
+  int64_t lda, m, k;
+  int vb, e;
+  __nv_bfloat16* acs;
+  int64_t ldk;
+  float* rowpart;
+  int64_t nchr;
+  double* part;
+  int64_t cx, I;
+};
+struct EncBUnit {  // 256 columns (chunk cx) x 128 rows (chunk ry) of B
+  const __nv_bfloat16* B;
+  int64_t ldb, k, n;
+  int vb, e;
+  __nv_bfloat16* bcs;
+  int64_t ldcs;
+  float* colpart;
+  double* part;
+  int64_t nch, cx, ry;
+};
+// The rows of a unit as the copies see them.
+struct RowSrc {
+  const __nv_bfloat16* base;  // first row of the unit
+  int64_t ld, cols, col0;
+  int nrow;
+};
+__device__ __forceinline__ RowSrc rows_of(const EncAUnit& u) {
+  const int64_t i0 = u.I * u.vb;
+  return RowSrc{u.A + i0 * u.lda, u.lda, u.k, u.cx * kEncCols,
+                (int)(min(i0 + (int64_t)u.vb, u.m) - i0)};
+}
+__device__ __forceinline__ RowSrc rows_of(const EncBUnit& u) {
+  const int64_t l0 = u.ry * kRowsPerCtaB;
+  return RowSrc{u.B + l0 * u.ldb, u.ldb, u.n, u.cx * kEncCols,
+                (int)(min(l0 + (int64_t)kRowsPerCtaB, u.k) - l0)};
+}
+// Batches of kRowBatch rows of warp w (rows w + 8 j) in a unit of nrow rows.
+__device__ __forceinline__ int warp_batches(int nrow, int warp) {
+  const int nj = nrow > warp ? (nrow - warp + kEncWarps - 1) / kEncWarps : 0;
+  return (nj + kRowBatch - 1) / kRowBatch;
+}
+
+// Unit lists: one problem (units in column-chunk-major order) or a group.
+struct SingleAUnits {
+  EncAUnit base;
+  int64_t ncx, cnt;
+  __device__ __forceinline__ int64_t count() const { return cnt; }
+  __device__ __forceinline__ EncAUnit get(int64_t u) const {
+    EncAUnit x = base;
+    x.cx = u % ncx;
+    x.I = u / ncx;
+    return x;
+  }
+};
+struct SingleBUnits {
+  EncBUnit base;
+  int64_t ncx, cnt;
+  __device__ __forceinline__ int64_t count() const { return cnt; }
+  __device__ __forceinline__ EncBUnit get(int64_t u) const {
+    EncBUnit x = base;
+    x.cx = u % ncx;
+    x.ry = u / ncx;
+    return x;
+  }
+};
+struct GroupAUnits {
+  const GProb* probs;
+  const int2* tab;
+  int64_t cnt;
+  __device__ __forceinline__ int64_t count() const { return cnt; }
+  __device__ __forceinline__ EncAUnit get(int64_t u) const {
+    const int2 e = tab[u];
+    const GProb& P = probs[e.x];
+    const int64_t ncx = cdiv(P.acs_ld, kEncCols);
+    return EncAUnit{static_cast<const __nv_bfloat16*>(P.A), P.lda, P.m, P.k, kGrpVbR, kGrpEr,
+                    static_cast<__nv_bfloat16*>(P.acs), P.acs_ld, P.rowpart, cdiv(P.k, 256),
+                    P.partA, e.y % ncx, e.y / ncx};
+  }
+};
+struct GroupBUnits {
+  const GProb* probs;
+  const int2* tab;
+  int64_t cnt;
+  __device__ __forceinline__ int64_t count() const { return cnt; }
+  __device__ __forceinline__ EncBUnit get(int64_t u) const {
+    const int2 e = tab[u];
+    const GProb& P = probs[e.x];
+    const int64_t ncx = cdiv(P.n, kEncCols);
+    return EncBUnit{static_cast<const __nv_bfloat16*>(P.B), P.ldb, P.k, P.n, kGrpVbC, kGrpEc,
+                    static_cast<__nv_bfloat16*>(P.bcs), P.bcs_ld, P.colpart, P.partB,
+                    cdiv(P.k, kRowsPerCtaB), e.y % ncx, e.y / ncx};
+  }
+};
+
+// A warp's copy cursor: issues the batches of the CTA's units (u, u + grid,
+// ...) in the order the arithmetic consumes them, one commit group per call
+// (an empty group once nothing is left keeps the group count uniform).
+template <class Units>
+struct RingIssuer {
+  const Units& U;
+  uint4* ring;
+  int warp, lane;
+  int64_t u;
+  int b, nbat, issued;
+  RowSrc src;
+  __device__ __forceinline__ void load() {
+    if (u < U.count()) {
+      src = rows_of(U.get(u));
+      nbat = warp_batches(src.nrow, warp);
+    }
+  }
+  __device__ __forceinline__ void start(int64_t u0) {
+    u = u0;
+    b = 0;
+    issued = 0;
+    nbat = 0;
+    load();
+  }
+  __device__ __forceinline__ void next() {
+    while (u < U.count() && b >= nbat) {
+      u += gridDim.x;
+      b = 0;
+      load();
+    }
+    if (u < U.count()) {
+      uint4* slot = ring + (issued % kAsyncBatches) * kRowBatch * 32;
+      const int64_t c0 = src.col0 + 8 * lane, rem = src.cols - c0;
+      const uint32_t nb = rem >= 8 ? 16u : (rem > 0 ? (uint32_t)rem * 2u : 0u);
+#pragma unroll
+      for (int r = 0; r < kRowBatch; ++r) {
+        const int t = warp + kEncWarps * (b * kRowBatch + r);
+        const bool in = t < src.nrow && nb > 0;
+        cp_async16(static_cast<uint32_t>(__cvta_generic_to_shared(slot + r * 32 + lane)),
+                   in ? src.base + (int64_t)t * src.ld + c0 : src.base, in ? nb : 0u);
+      }
+      ++b;
+    }
+    cp_async_commit();
+    ++issued;
+  }
+};
+
+template <class Units>
+__global__ void __launch_bounds__(kThreads, 2) k_encA_stream(const Units U) {
+  __shared__ float red[kEncWarps * kEncCols * 2];
+  __shared__ float sh[kThreads / 32];
+  extern __shared__ uint4 ring_s[];  // kRingBytesA
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint4* ring = ring_s + warp * kAsyncBatches * kRowBatch * 32;
+  RingIssuer<Units> is{U, ring, warp, lane};
+  is.start(blockIdx.x);
+#pragma unroll
+  for (int i = 0; i < kAsyncBatches; ++i) is.next();
+  constexpr int kLanesPerRow = 32 / kRowBatch;
+  int consumed = 0;
+  for (int64_t u = blockIdx.x; u < U.count(); u += gridDim.x) {
+    const EncAUnit X = U.get(u);
+    const RowSrc src = rows_of(X);
+    const int nbat = warp_batches(src.nrow, warp);
+    const float sc = scalbnf(1.0f, -X.e);
+    float se[8], sw[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) se[q] = sw[q] = 0.f;
+    for (int b = 0; b < nbat; ++b) {
+      cp_async_wait<kAsyncBatches - 1>();  // this warp's oldest batch has landed
+      const uint4* slot = ring + (consumed % kAsyncBatches) * kRowBatch * 32;
+      float sq[kRowBatch];
+#pragma unroll
+      for (int r = 0; r < kRowBatch; ++r) {
+        float v[8];
+        unpack8(slot[r * 32 + lane], v);
+        lpA_rows(v, warp + kEncWarps * (b * kRowBatch + r), sc, se, sw, sq[r]);
+      }
+      ++consumed;
+      is.next();  // refills the slot just read (each lane reads only its own copies)
+      reduce_rows<kRowBatch>(sq, lane);
+      const int t = warp + kEncWarps * (b * kRowBatch + lane / kLanesPerRow);
+      if (lane % kLanesPerRow == 0 && t < src.nrow)
+        X.rowpart[(X.I * X.vb + t) * X.nchr + X.cx] = sq[0];
+    }
+    lpA_finish(se, sw, X.acs, X.ldk, X.part, X.nchr, X.cx, X.I, red, sh);
+  }
+  cp_async_wait<0>();
+}
+
+template <class Units>
+__global__ void __launch_bounds__(kThreads, 2) k_encB_stream(const Units U) {
+  __shared__ float red[kEncWarps * kEncCols];
+  __shared__ float redq[kEncWarps * 32 * 2];
+  extern __shared__ uint4 ring_s[];  // kRingBytesA
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint4* ring = ring_s + warp * kAsyncBatches * kRowBatch * 32;
+  RingIssuer<Units> is{U, ring, warp, lane};
+  is.start(blockIdx.x);
+#pragma unroll
+  for (int i = 0; i < kAsyncBatches; ++i) is.next();
+  int consumed = 0;
+  for (int64_t u = blockIdx.x; u < U.count(); u += gridDim.x) {
+    const EncBUnit X = U.get(u);
+    const RowSrc src = rows_of(X);
+    const int nbat = warp_batches(src.nrow, warp);
+    const int64_t c0 = X.cx * kEncCols + 8 * lane, l0 = X.ry * kRowsPerCtaB;
+    const int seg = X.vb / 8;  // lanes per verify block (1 .. 32)
+    const bool leader = (lane % seg) == 0 && c0 < X.n;
+    const int64_t J = c0 / X.vb;
+    const float sc = scalbnf(1.0f, -X.e);
+    float wq[8], cs[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      wq[q] = (float)((int)((c0 + q) % X.vb) + 1) * sc;
+      cs[q] = 0.f;
+    }
+    float q0 = 0.f, q1 = 0.f;
+    for (int b = 0; b < nbat; ++b) {
+      cp_async_wait<kAsyncBatches - 1>();
+      const uint4* slot = ring + (consumed % kAsyncBatches) * kRowBatch * 32;
+      if (seg == 32) {
+        // one verify block across the warp: the batch's 8 rows' (e, w) sums
+        // reduce in one transposing butterfly (15 + 1 shuffles for 16 sums);
+        // lane l then holds sum l / 2: row l / 4, e (l / 2 even) or w
+        float sums[2 * kRowBatch];
+#pragma unroll
+        for (int r = 0; r < kRowBatch; ++r) {
+          float v[8];
+          unpack8(slot[r * 32 + lane], v);
+          lpB_row(v, wq, cs, sums[2 * r], sums[2 * r + 1]);
+        }
+        ++consumed;
+        is.next();
+        reduce_rows<2 * kRowBatch>(sums, lane);
+        const int t = warp + kEncWarps * (b * kRowBatch + (lane >> 2)), kind = (lane >> 1) & 1;
+        if ((lane & 1) == 0 && t < src.nrow && X.cx * kEncCols < X.n) {
+          __nv_bfloat16 pc[2];
+          split(sums[0], pc[0], pc[1]);
+          *reinterpret_cast<uint32_t*>(X.bcs + (l0 + t) * X.ldcs + 4 * J + 2 * kind) =
+              *reinterpret_cast<const uint32_t*>(pc);
+          if (kind)
+            q1 = fmaf(sums[0], sums[0], q1);
+          else
+            q0 = fmaf(sums[0], sums[0], q0);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < kRowBatch; ++r) {
+          const int t = warp + kEncWarps * (b * kRowBatch + r);
+          float v[8], se, sw;
+          unpack8(slot[r * 32 + lane], v);
+          lpB_row(v, wq, cs, se, sw);
+          lpB_store_shfl(se, sw, seg, leader, t < src.nrow, X.bcs + (l0 + t) * X.ldcs + 4 * J,
+                         q0, q1);
+        }
+        ++consumed;
+        is.next();
+      }
+    }
+    if (seg == 32) {  // the checksum-norm partials of the warp's rows to lane 0
+      q0 = warp_sumf(q0);
+      q1 = warp_sumf(q1);
+    }
+    lpB_finish(cs, q0, q1, X.n, X.vb, X.colpart, X.part, X.nch, X.cx, X.ry, red, redq);
+  }
+  cp_async_wait<0>();
 }
 
 // The same outputs for any verify block size (one warp per row segment).
@@ -410,11 +744,35 @@ __device__ __forceinline__ void lp_blk_one(const double* __restrict__ nvec, int6
   nblk[4 * I + 3] = (double)sqrtf(q1);
 }
 
+// The same, one warp per verify block (the lanes split its lines and
+// partials).  Grid: ceil(nvb * 32 / 128) CTAs of 128 threads.
 __global__ void k_lp_blk(const double* __restrict__ nvec, int64_t len, int vb, int e,
                          const double* __restrict__ part, int64_t nch, double* __restrict__ nblk) {
-  const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t I = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (I >= cdiv(len, vb)) return;
-  lp_blk_one(nvec, len, vb, e, part, nch, nblk, I);
+  const float sc = scalbnf(1.0f, -e);
+  const int64_t t0 = I * vb, t1 = min(t0 + (int64_t)vb, len);
+  float f0 = 0.f, f1 = 0.f, q0 = 0.f, q1 = 0.f;
+  for (int64_t t = t0 + lane; t < t1; t += 32) {
+    const float v = (float)nvec[t], wv = (float)(t - t0 + 1) * sc * v;
+    f0 = fmaf(v, v, f0);
+    f1 = fmaf(wv, wv, f1);
+  }
+  for (int64_t c = lane; c < nch; c += 32) {
+    q0 += (float)part[(2 * I) * nch + c];
+    q1 += (float)part[(2 * I + 1) * nch + c];
+  }
+  f0 = warp_sumf(f0);
+  f1 = warp_sumf(f1);
+  q0 = warp_sumf(q0);
+  q1 = warp_sumf(q1);
+  if (lane == 0) {
+    nblk[4 * I + 0] = (double)sqrtf(f0);
+    nblk[4 * I + 1] = (double)sqrtf(f1);
+    nblk[4 * I + 2] = (double)sqrtf(q0);
+    nblk[4 * I + 3] = (double)sqrtf(q1);
+  }
 }
 
 // ---------------- split bf16x3 (binary32 inputs)
@@ -716,6 +1074,40 @@ __global__ void __launch_bounds__(kThreads) k_fp8_dequant(const uint8_t* __restr
 
 unsigned gy(int64_t v) { return (unsigned)(v < 65535 ? v : 65535); }
 
+// The streaming passes keep their row rings in dynamic shared memory beyond
+// the default 48 KiB.
+template <class Units>
+cudaError_t launch_stream_A(const Units& U, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_encA_stream<Units>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytesA);
+  if (e != cudaSuccess || U.cnt == 0) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t grid = std::min<int64_t>(U.cnt, 2 * (int64_t)std::max(sms, 1));  // 2 CTAs per SM
+  k_encA_stream<Units><<<(unsigned)grid, kThreads, kRingBytesA, st>>>(U);
+  count_launches(1);
+  return cudaGetLastError();
+}
+template <class Units>
+cudaError_t launch_stream_B(const Units& U, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_encB_stream<Units>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytesA);
+  if (e != cudaSuccess || U.cnt == 0) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t grid = std::min<int64_t>(U.cnt, 2 * (int64_t)std::max(sms, 1));
+  k_encB_stream<Units><<<(unsigned)grid, kThreads, kRingBytesA, st>>>(U);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// Asynchronous copies need 16-byte aligned rows.
+bool rows_aligned(const void* p, int64_t ld) {
+  return ((reinterpret_cast<uintptr_t>(p) & 15) == 0) && ld % 8 == 0;
+}
+
 // bf16 elements in a 256-byte aligned plane of `elems` elements.
 int64_t align_elems(int64_t elems) { return (elems * 2 + 255) / 256 * 128; }
 
@@ -798,7 +1190,7 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, cons
           Af, d.lda, d.k, d.grid_p, P.bs, P.f, sp, P.L.acs_ld);
     }
     k_lp_norms<<<(unsigned)cdiv(d.m, 128), 128, 0, st>>>(rowpart, d.m, nchr, nchr, 1, nArow);
-    k_lp_blk<<<(unsigned)cdiv(P.nvr, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA,
+    k_lp_blk<<<(unsigned)cdiv(P.nvr * 32, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA,
                                                          nchA, nAblk);
     if (fastB) {
       k_x3B_rows<<<dim3((unsigned)cdiv(P.L.op_b_ld, kColsPerCta), (unsigned)nchB), kThreads, 0,
@@ -812,7 +1204,7 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, cons
           Bf, d.ldb, d.k, d.n, d.vb_cols, P.ec, bcsp, P.L.bcs_ld, partB, nchB);
     }
     k_lp_norms<<<(unsigned)cdiv(d.n, 128), 128, 0, st>>>(colpart, d.n, nchB, 1, d.n, nBcol);
-    k_lp_blk<<<(unsigned)cdiv(P.nvc, 128), 128, 0, st>>>(nBcol, d.n, d.vb_cols, P.ec, partB,
+    k_lp_blk<<<(unsigned)cdiv(P.nvc * 32, 128), 128, 0, st>>>(nBcol, d.n, d.vb_cols, P.ec, partB,
                                                          nchB, nBblk);
     count_launches(6 + (P.bs > 0 ? 1 : 0) + (fastB ? 0 : 1));
     return cudaGetLastError();
@@ -837,17 +1229,37 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, cons
     lda = P.L.op_a_ld;
     ldb = P.L.op_b_ld;
   }
-  k_lpA_cols<<<dim3((unsigned)cdiv(P.L.acs_ld, kEncCols), gy(P.nvr)), kThreads, 0, st>>>(
-      A, lda, d.m, d.k, d.vb_rows, P.er, acs, P.L.acs_ld, rowpart, nchr, partA);
+  int nlaunch = 0;
+  if (rows_aligned(A, lda)) {
+    SingleAUnits U{};
+    U.base = EncAUnit{A, lda, d.m, d.k, d.vb_rows, P.er, acs, P.L.acs_ld, rowpart, nchr, partA, 0, 0};
+    U.ncx = cdiv(P.L.acs_ld, kEncCols);
+    U.cnt = U.ncx * P.nvr;
+    cudaError_t e = launch_stream_A(U, st);
+    if (e != cudaSuccess) return e;
+  } else {
+    k_lpA_cols<<<dim3((unsigned)cdiv(P.L.acs_ld, kEncCols), gy(P.nvr)), kThreads, 0, st>>>(
+        A, lda, d.m, d.k, d.vb_rows, P.er, acs, P.L.acs_ld, rowpart, nchr, partA);
+    ++nlaunch;
+  }
   if (P.bs > 0)
     k_lpA_block<<<dim3((unsigned)cdiv(d.k, kThreads), gy(P.f * P.bs)), kThreads, 0, st>>>(
         A, lda, d.k, d.grid_p, P.bs, P.f, acs + 4 * P.nvr * P.L.acs_ld, P.L.acs_ld);
   k_lp_norms<<<(unsigned)cdiv(d.m, 128), 128, 0, st>>>(rowpart, d.m, nchr, nchr, 1, nArow);
-  k_lp_blk<<<(unsigned)cdiv(P.nvr, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA, nchr,
+  k_lp_blk<<<(unsigned)cdiv(P.nvr * 32, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA, nchr,
                                                        nAblk);
-  if (fastB) {
+  if (fastB && rows_aligned(B, ldb)) {
+    SingleBUnits U{};
+    U.base = EncBUnit{B, ldb, d.k, d.n, d.vb_cols, P.ec, bcs, P.L.bcs_ld, colpart, partB, nchB,
+                      0, 0};
+    U.ncx = cdiv(d.n, kEncCols);
+    U.cnt = U.ncx * nchB;
+    cudaError_t e = launch_stream_B(U, st);
+    if (e != cudaSuccess) return e;
+  } else if (fastB) {
     k_lpB_rows<<<dim3((unsigned)cdiv(d.n, kEncCols), gy(nchB)), kThreads, 0, st>>>(
         B, ldb, d.k, d.n, d.vb_cols, P.ec, bcs, P.L.bcs_ld, colpart, partB, nchB);
+    ++nlaunch;
   } else {
     k_lpB_rows_any<<<dim3((unsigned)cdiv(nchB, kThreads / 32), gy(P.nvc)), kThreads, 0, st>>>(
         B, ldb, d.k, d.n, d.vb_cols, P.ec, bcs, P.L.bcs_ld, partB, nchB);
@@ -855,9 +1267,9 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, cons
         B, ldb, d.k, d.n, colpart);
   }
   k_lp_norms<<<(unsigned)cdiv(d.n, 128), 128, 0, st>>>(colpart, d.n, nchB, 1, d.n, nBcol);
-  k_lp_blk<<<(unsigned)cdiv(P.nvc, 128), 128, 0, st>>>(nBcol, d.n, d.vb_cols, P.ec, partB, nchB,
+  k_lp_blk<<<(unsigned)cdiv(P.nvc * 32, 128), 128, 0, st>>>(nBcol, d.n, d.vb_cols, P.ec, partB, nchB,
                                                        nBblk);
-  count_launches(6 + (P.bs > 0 ? 1 : 0) + (fastB ? 0 : 1));
+  count_launches(nlaunch + 4 + (P.bs > 0 ? 1 : 0) + (fastB ? 0 : 2));
   return cudaGetLastError();
 }
 
@@ -925,30 +1337,6 @@ cudaError_t launch_gemm_lp(const Plan& P, const void* A, const void* B, float* C
 // ---------------- grouped encode (many bf16 problems per launch)
 namespace {
 
-__global__ void __launch_bounds__(kThreads, 2) k_grp_encA(const GProb* __restrict__ probs,
-                                                       const int2* __restrict__ tab) {
-  __shared__ float red[kEncWarps * kEncCols * 2];
-  __shared__ float sh[kThreads / 32];
-  const int2 e = tab[blockIdx.x];
-  const GProb& P = probs[e.x];
-  const int64_t u = e.y, ncx = cdiv(P.acs_ld, kEncCols);
-  lpA_unit(static_cast<const __nv_bfloat16*>(P.A), P.lda, P.m, P.k, kGrpVbR, kGrpEr,
-           static_cast<__nv_bfloat16*>(P.acs), P.acs_ld, P.rowpart, cdiv(P.k, 256), P.partA,
-           u % ncx, u / ncx, red, sh);
-}
-
-__global__ void __launch_bounds__(kThreads, 2) k_grp_encB(const GProb* __restrict__ probs,
-                                                       const int2* __restrict__ tab) {
-  __shared__ float red[kEncWarps * kEncCols];
-  __shared__ float redq[kEncWarps * 32 * 2];
-  const int2 e = tab[blockIdx.x];
-  const GProb& P = probs[e.x];
-  const int64_t u = e.y, ncx = cdiv(P.n, kEncCols);
-  lpB_unit(static_cast<const __nv_bfloat16*>(P.B), P.ldb, P.k, P.n, kGrpVbC, kGrpEc,
-           static_cast<__nv_bfloat16*>(P.bcs), P.bcs_ld, P.colpart, P.partB,
-           cdiv(P.k, kRowsPerCtaB), u % ncx, u / ncx, red, redq);
-}
-
 // Row norms ||A_i|| (first ceil(m/256) CTAs of a problem) and column norms
 // ||B_:j|| (next ceil(n/256)) from the fp32 partial sums of squares (fp32
 // sums; stored as binary64 and as fp32 for the verify screen).
@@ -1002,14 +1390,15 @@ __global__ void __launch_bounds__(kThreads) k_grp_blk(const GProb* __restrict__ 
 
 cudaError_t launch_group_encode(const GroupDev& G, cudaStream_t st) {
   if (G.count == 0) return cudaSuccess;
-  if (G.nctas[kGkEncA] > 0)
-    k_grp_encA<<<(unsigned)G.nctas[kGkEncA], kThreads, 0, st>>>(G.probs, G.tab[kGkEncA]);
-  if (G.nctas[kGkEncB] > 0)
-    k_grp_encB<<<(unsigned)G.nctas[kGkEncB], kThreads, 0, st>>>(G.probs, G.tab[kGkEncB]);
+  // (every problem's operands have 16-byte aligned rows: their tensor maps need it)
+  cudaError_t e = launch_stream_A(GroupAUnits{G.probs, G.tab[kGkEncA], G.nctas[kGkEncA]}, st);
+  if (e == cudaSuccess)
+    e = launch_stream_B(GroupBUnits{G.probs, G.tab[kGkEncB], G.nctas[kGkEncB]}, st);
+  if (e != cudaSuccess) return e;
   if (G.nctas[kGkLines] > 0)
     k_grp_lines<<<(unsigned)G.nctas[kGkLines], kThreads, 0, st>>>(G.probs, G.tab[kGkLines]);
   k_grp_blk<<<(unsigned)G.count, kThreads, 0, st>>>(G.probs, G.s);
-  count_launches(4);
+  count_launches(2);
   return cudaGetLastError();
 }
 

@@ -46,9 +46,9 @@ METRIC = "ABFT GEMM TFLOPS (useful 2mnk) and % overhead vs checksum-free GEMM, s
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # Measured DRAM read + write per launch of the product kernel at the bench workloads (ncu
 # dram__bytes_read.sum + dram__bytes_write.sum, see profiles/), or None when the kernel
-# changed since it was captured.  f64: 45.50 + 1.08 GB; bf16: 8.77 + 1.10 GB; bf16x6:
-# 94.53 + 1.29 GB; grouped 4096: 30.80 + 19.39 GB.
-TRAFFIC_BYTES = {"f64": 46.58e9, "bf16": 9.87e9, "bf16x6": 95.82e9, "grouped": 50.19e9}
+# changed since it was captured.  f64: 45.50 + 1.08 GB; bf16: 8.91 + 1.18 GB; bf16x6:
+# 126.78 + 1.54 GB; grouped 4096 (ABFT product, chosen tuning): 18.98 + 20.55 GB.
+TRAFFIC_BYTES = {"f64": 46.58e9, "bf16": 10.09e9, "bf16x6": 128.32e9, "grouped": 39.53e9}
 
 
 def bf16_peak():

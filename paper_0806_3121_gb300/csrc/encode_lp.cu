@@ -29,7 +29,10 @@ constexpr int kEncWarps = kThreads / 32;   // warps sharing a unit's rows
 // A pass with asynchronous copies: each warp keeps kAsyncBatches batches of
 // kRowBatch rows in flight in its shared-memory ring (16 bytes per lane per
 // row), so the loads do not wait on registers.
-constexpr int kAsyncBatches = 2;
+#ifndef ABFT_ENC_BATCHES
+#define ABFT_ENC_BATCHES 2
+#endif
+constexpr int kAsyncBatches = ABFT_ENC_BATCHES;
 constexpr int kRingBytesA = kEncWarps * kAsyncBatches * kRowBatch * 32 * 16;  // 64 KiB
 
 // 16-byte asynchronous global -> shared copy; bytes < 16 zero-fills the rest

@@ -349,3 +349,44 @@ def test_two_erasures_in_a_block_column_bf16():
     # the rebuilt blocks carry the errors of the checksums and of the survivors,
     # amplified by the 2 x 2 solve (nodes 2/8 and 3/8)
     assert rel_fro(Cg[blk], ref[blk]) <= 8 * (4 * np.sqrt(k) * U32 + 2.0 ** -17)
+
+
+@pytest.mark.parametrize("m,n,k,vbr,vbc,ldc", [
+    (256, 301, 192, 128, 32, 301),   # C and E16 rows not 16-byte multiples: plain stores
+    (256, 320, 192, 128, 64, 323),   # C plain stores, E16 / F16 by TMA
+    (384, 300, 136, 128, 64, 304),   # TMA stores clipped at n inside a wider C
+])
+def test_outputs_with_any_row_pitch(m, n, k, vbr, vbc, ldc):
+    """C with a leading dimension beyond n: the product writes exactly the m x n data block
+    (the padding keeps its NaNs), by TMA stores when the row pitch allows and plain stores
+    otherwise; fused checksums and located epilogue faults are the oracle's either way."""
+    A, A64, lda = bf16_matrix(m, k, "normal", 61, 1)
+    B, B64, ldb = bf16_matrix(k, n, "normal", 61, 2)
+    desc = abft.make_desc(m, n, k, "bf16", vbr, vbc, lda=lda, ldb=ldb, ldc=ldc)
+    L = abft.abft_workspace_layout(desc)
+    assert L.fused == 1
+    ws = torch.zeros(L.total, dtype=torch.uint8, device="cuda")
+    Cbuf = torch.full((m, ldc), float("nan"), dtype=torch.float32, device="cuda")
+    abft.abft_encode(desc, A, B, ws)
+    abft.abft_gemm(desc, A, B, Cbuf, ws)
+    torch.cuda.synchronize()
+    full = Cbuf.cpu().numpy().astype(np.float64)
+    assert np.isnan(full[:, n:]).all()
+    ref = oracle.gemm(A64, B64)
+    check_fp32_product(full[:, :n], A64, B64, ref)
+    st, rep, nrep = abft.abft_verify_correct(desc, Cbuf, ws, reread_C=0)
+    assert st == abft.OK and nrep == 0
+    enc = oracle.Encoded(A64, B64, vbr, vbc, dtype="bf16")
+    pos = [(p[0], p[1]) for p in wl.bit_flips(13, m, n, 2, bits=32, distinct_blocks=(vbr, 64))]
+    flips = graded_bits(full[:, :n], pos)
+    abft.abft_set_epilogue_faults(desc, ws, flips)
+    abft.abft_gemm(desc, A, B, Cbuf, ws)
+    abft.abft_set_epilogue_faults(desc, ws, [])
+    Cf = Cbuf.cpu().numpy().astype(np.float64)
+    assert np.isnan(Cf[:, n:]).all()
+    st, rep, nrep = abft.abft_verify_correct(desc, Cbuf, ws, reread_C=0)
+    ost, orep, oC, on = enc.verify_correct(Cf[:, :n])
+    assert st == abft.OK and ost == oracle.ST_OK
+    assert [(a, b) for a, b, _ in positions(rep)] == sorted(pos)
+    assert positions(rep) == positions(orep)
+    assert rel_fro(Cbuf.cpu().numpy().astype(np.float64)[:, :n], ref) <= 4 * np.sqrt(k) * U32

@@ -2,17 +2,21 @@
 // [A; acs] [B, bcs] with fp32 accumulation in TMEM.
 //
 // Persistent, warp-specialised kernel, one CTA per SM:
-//   warp 0      TMA producer: A tile (two 64-row halves x 64, K-major) and B
-//               tile (64 x up to four 64-column boxes, N-major) per stage,
-//               128-byte swizzle, into a 4-stage shared-memory ring guarded by
-//               mbarriers.
+//   warp 0      TMA producer of A: one 128-row box (or two 64-row halves) per
+//               stage, K-major, 128-byte swizzle, into a 4-stage shared-memory
+//               ring guarded by mbarriers.
+//   warp 10     TMA producer of B: one 3-D copy of up to four 64-column boxes
+//               (N-major) per stage, the ragged / checksum boxes one by one; the
+//               two producers arrive on a stage's full barrier with their own
+//               bytes (one issuing thread could not keep up with the MMAs).
 //   warp 1      MMA issuer: one thread issues tcgen05.mma (M=128, N=64 x boxes,
 //               K=16) into one of two TMEM accumulators (2 x 256 columns) and
 //               frees ring stages and accumulators with tcgen05.commit.
 //   warps 2-9   epilogue: tcgen05.ld of the accumulator (a warp reads its
 //               32-lane quarter of TMEM and one 128-column half of the tile),
-//               fp32 stores to C or to the checksum outputs, the fused observed
-//               sums, then release of the accumulator so the next tile's MMAs
+//               each 32 x 32 chunk staged in shared memory and written to C or
+//               the checksum outputs by a TMA store, the fused observed sums,
+//               then release of the accumulator so the next tile's MMAs
 //               overlap this tile's epilogue.
 // Single problem: data tiles (grouped raster for L2 reuse), checksum-row tiles
 // (acs x B -> E16) and checksum-column tiles (A x bcs -> F16); the corner is
@@ -40,7 +44,10 @@ constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 constexpr int kEpiWarps = ABFT_EPI_WARPS;         // 4 or 8 (one or two per TMEM lane quarter)
 constexpr int kEpiCols = BN * 4 / kEpiWarps;       // tile columns per epilogue warp
 constexpr int kEpiChunks = kEpiCols / 32;          // 32-column TMEM loads per warp
-constexpr int kThreads = 64 + 32 * kEpiWarps;
+// warps: 0 TMA producer of A, 1 MMA issuer, 2 .. 1 + kEpiWarps epilogue (warp
+// w reads TMEM lane quarter w % 4), then the TMA producer of B
+constexpr int kWarpProdB = 2 + kEpiWarps;
+constexpr int kThreads = 32 * (kWarpProdB + 1);
 // Every epilogue warp reads whole 32-column chunks of its TMEM lane quarter:
 // a split that is not a multiple of 32 columns would read past the
 // accumulator (and past the allocated TMEM for the second one).
@@ -315,7 +322,7 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      tc::mbar_init(full(s), 1);
+      tc::mbar_init(full(s), 2);  // the A and the B producer each arrive with their bytes
       tc::mbar_init(empty(s), 1);
     }
     for (int a = 0; a < 2; ++a) {
@@ -338,9 +345,12 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
   const uint32_t tmem = *tmem_slot;
   const int64_t total = S.total();
 
-  if (warp == 0) {
+  if (warp == 0 || warp == kWarpProdB) {
     if (lane == 0) {
-      // ---------------- TMA producer
+      // ---------------- TMA producers: warp 0 copies A, warp kWarpProdB copies
+      // B (two issuing threads: one thread's issue rate limited the ring);
+      // each arrives on the stage's full barrier with its own bytes
+      const bool pA = warp == 0;
       int s = 0;
       uint32_t ph = 0;
       int64_t issued = 0;  // stages filled and not known to be consumed
@@ -348,16 +358,30 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
         const TileView T = S.view(t);
         if (stall_test && t == 0) continue;  // nothing will fill these stages
         const int64_t nkb = T.nkb, nkt = T.nkb * T.nseg;
-        const uint32_t tx = (uint32_t)T.hcnt * (A_BYTES / 2) + (uint32_t)T.nbox * B_BOX_BYTES;
+        const uint32_t tx = pA ? (uint32_t)T.hcnt * (A_BYTES / 2) : (uint32_t)T.nbox * B_BOX_BYTES;
+        // a stage's MMAs take ~700 cycles: the per-stage bookkeeping is
+        // incremental (no division per stage)
+        int seg = 0, pa = (int)(T.seg_a & 3u), pb = (int)(T.seg_b & 3u);
+        int64_t kb = 0;
         for (int64_t kt = 0; kt < nkt; ++kt) {
-          const int seg = (int)(kt / nkb);
-          const int32_t kx = (int32_t)((kt - (int64_t)seg * nkb) * BK);
+          const int32_t kx = (int32_t)(kb * BK);
           if (!tc::wait(empty(s), ph ^ 1, abort)) break;
           const uint32_t sa = tc::smem_addr(smem + s * STAGE_BYTES);
           tc::mbar_arrive_expect_tx(full(s), tx);
-          const int pa = (int)((T.seg_a >> (2 * seg)) & 3u);
-          const int pb = (int)((T.seg_b >> (2 * seg)) & 3u);
-          if (T.maW) {
+          if (!pA) {
+            // B: the full boxes in one 3-D copy, the rest (ragged, checksum) per box
+            int b_first = 0;
+            if (T.mbW) {
+              tc::tma_load_3d(sa + A_BYTES, T.mbW + pb, full(s), 0, kx, T.colW / 64);
+              b_first = T.nW;
+            }
+            for (int b = b_first; b < T.nbox; ++b) {
+              const bool dat = b < T.bsplit;
+              const CUtensorMap* mb = (dat ? T.mbD : T.mbC) + pb;
+              const int32_t x = dat ? T.colD + 64 * b : T.colC + 64 * (b - T.bsplit);
+              tc::tma_load_2d(sa + A_BYTES + b * B_BOX_BYTES, mb, full(s), x, kx);
+            }
+          } else if (T.maW) {
             tc::tma_load_2d(sa, T.maW + pa, full(s), kx, T.rowW);
           } else {
             for (int h = 0; h < T.hcnt; ++h) {
@@ -367,19 +391,14 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
               tc::tma_load_2d(sa + h * (A_BYTES / 2), ma, full(s), kx, y);
             }
           }
-          int b_first = 0;
-          if (T.mbW) {
-            tc::tma_load_3d(sa + A_BYTES, T.mbW + pb, full(s), 0, kx, T.colW / 64);
-            b_first = T.nW;
-          }
-          for (int b = b_first; b < T.nbox; ++b) {
-            const bool dat = b < T.bsplit;
-            const CUtensorMap* mb = (dat ? T.mbD : T.mbC) + pb;
-            const int32_t x = dat ? T.colD + 64 * b : T.colC + 64 * (b - T.bsplit);
-            tc::tma_load_2d(sa + A_BYTES + b * B_BOX_BYTES, mb, full(s), x, kx);
-          }
           ++issued;
           if (++s == STAGES) { s = 0; ph ^= 1; }
+          if (++kb == nkb) {  // next K segment: its planes of A and B
+            kb = 0;
+            ++seg;
+            pa = (int)((T.seg_a >> (2 * seg)) & 3u);
+            pb = (int)((T.seg_b >> (2 * seg)) & 3u);
+          }
         }
       }
       // Do not leave copies in flight: wait for the last fills (bounded).

@@ -41,6 +41,10 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes)
                : "memory");
 }
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(bytes)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -409,18 +413,54 @@ struct EncBUnit {  // 256 columns (chunk cx) x 128 rows (chunk ry) of B
 // The rows of a unit as the copies see them.
 struct RowSrc {
   const __nv_bfloat16* base;  // first row of the unit
-  int64_t ld, cols, col0;
+  int64_t ld, cols, col0, row0;
   int nrow;
 };
 __device__ __forceinline__ RowSrc rows_of(const EncAUnit& u) {
   const int64_t i0 = u.I * u.vb;
-  return RowSrc{u.A + i0 * u.lda, u.lda, u.k, u.cx * kEncCols,
+  return RowSrc{u.A + i0 * u.lda, u.lda, u.k, u.cx * kEncCols, i0,
                 (int)(min(i0 + (int64_t)u.vb, u.m) - i0)};
 }
 __device__ __forceinline__ RowSrc rows_of(const EncBUnit& u) {
   const int64_t l0 = u.ry * kRowsPerCtaB;
-  return RowSrc{u.B + l0 * u.ldb, u.ldb, u.n, u.cx * kEncCols,
+  return RowSrc{u.B + l0 * u.ldb, u.ldb, u.n, u.cx * kEncCols, l0,
                 (int)(min(l0 + (int64_t)kRowsPerCtaB, u.k) - l0)};
+}
+
+// FP8 E4M3 source of a single-problem pass (q == nullptr: the rows are bf16):
+// the pass reads the e4m3 rows (8 bytes per lane per row), dequantises them
+// with their 128 x 128 block scale, writes the exact values into the bf16
+// operand plane the product reads, and forms the checksums from them -- one
+// pass instead of a dequantisation pass and a checksum pass over the plane.
+struct Fp8Src {
+  const uint8_t* q;
+  int64_t ldq;
+  const float* sc;  // scale[row / 128][col / 128]
+  int64_t sld;      // scale columns
+  __nv_bfloat16* plane;
+  int64_t pld;      // plane leading dimension (columns cols .. pld-1 are zero)
+  int* inexact;     // set when a value is not exact in bf16
+};
+
+// Eight e4m3 values (w0, w1 little-endian) times scale: the fp32 values (zero
+// from column cols on), their bf16 images, and whether any is inexact.
+__device__ __forceinline__ void dequant8(uint32_t w0, uint32_t w1, float scl, int64_t c0,
+                                         int64_t cols, float (&v)[8], __nv_bfloat16 (&o)[8],
+                                         bool& bad) {
+  const uint32_t w[2] = {w0, w1};
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const __half2_raw h2 = __nv_cvt_fp8x2_to_halfraw2(
+        (__nv_fp8x2_storage_t)((w[t >> 1] >> (16 * (t & 1))) & 0xFFFFu), __NV_E4M3);
+    const float2 f = __half22float2(__half2(h2));
+    v[2 * t] = c0 + 2 * t < cols ? f.x * scl : 0.f;
+    v[2 * t + 1] = c0 + 2 * t + 1 < cols ? f.y * scl : 0.f;
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    o[q] = __float2bfloat16_rn(v[q]);
+    bad |= !(__bfloat162float(o[q]) == v[q]);  // also catches NaN
+  }
 }
 // Batches of kRowBatch rows of warp w (rows w + 8 j) in a unit of nrow rows.
 __device__ __forceinline__ int warp_batches(int nrow, int warp) {
@@ -483,9 +523,10 @@ struct GroupBUnits {
 // A warp's copy cursor: issues the batches of the CTA's units (u, u + grid,
 // ...) in the order the arithmetic consumes them, one commit group per call
 // (an empty group once nothing is left keeps the group count uniform).
-template <class Units>
+template <class Units, bool kF8>
 struct RingIssuer {
   const Units& U;
+  const Fp8Src& f8;
   uint4* ring;
   int warp, lane;
   int64_t u;
@@ -513,13 +554,17 @@ struct RingIssuer {
     if (u < U.count()) {
       uint4* slot = ring + (issued % kAsyncBatches) * kRowBatch * 32;
       const int64_t c0 = src.col0 + 8 * lane, rem = src.cols - c0;
-      const uint32_t nb = rem >= 8 ? 16u : (rem > 0 ? (uint32_t)rem * 2u : 0u);
+      const uint32_t esz = kF8 ? 1u : 2u;  // bytes per element
+      const uint32_t nb = rem >= 8 ? 8u * esz : (rem > 0 ? (uint32_t)rem * esz : 0u);
 #pragma unroll
       for (int r = 0; r < kRowBatch; ++r) {
         const int t = warp + kEncWarps * (b * kRowBatch + r);
         const bool in = t < src.nrow && nb > 0;
-        cp_async16(static_cast<uint32_t>(__cvta_generic_to_shared(slot + r * 32 + lane)),
-                   in ? src.base + (int64_t)t * src.ld + c0 : src.base, in ? nb : 0u);
+        const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(slot + r * 32 + lane));
+        if constexpr (kF8)
+          cp_async8(dst, in ? f8.q + (src.row0 + t) * f8.ldq + c0 : f8.q, in ? nb : 0u);
+        else
+          cp_async16(dst, in ? src.base + (int64_t)t * src.ld + c0 : src.base, in ? nb : 0u);
       }
       ++b;
     }
@@ -528,14 +573,31 @@ struct RingIssuer {
   }
 };
 
-template <class Units>
-__global__ void __launch_bounds__(kThreads, 2) k_encA_stream(const Units U) {
+// One row of a batch from the ring: bf16 rows are unpacked; e4m3 rows are
+// dequantised, and their bf16 values written to the operand plane (row `row`).
+template <bool kF8>
+__device__ __forceinline__ void ring_row(const uint4& raw, const Fp8Src& f8, int64_t row,
+                                         bool valid, int64_t c0, int64_t cols, float (&v)[8],
+                                         bool& bad) {
+  if constexpr (kF8) {
+    const float scl = (valid && c0 < cols) ? f8.sc[(row / 128) * f8.sld + c0 / 128] : 0.f;
+    __nv_bfloat16 o[8];
+    dequant8(raw.x, raw.y, scl, c0, cols, v, o, bad);
+    if (valid && c0 < f8.pld) store8(f8.plane + row * f8.pld + c0, o);
+  } else {
+    unpack8(raw, v);
+  }
+}
+
+template <class Units, bool kF8>
+__global__ void __launch_bounds__(kThreads, 2) k_encA_stream(const Units U, const Fp8Src f8) {
   __shared__ float red[kEncWarps * kEncCols * 2];
   __shared__ float sh[kThreads / 32];
   extern __shared__ uint4 ring_s[];  // kRingBytesA
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint4* ring = ring_s + warp * kAsyncBatches * kRowBatch * 32;
-  RingIssuer<Units> is{U, ring, warp, lane};
+  bool bad = false;
+  RingIssuer<Units, kF8> is{U, f8, ring, warp, lane};
   is.start(blockIdx.x);
 #pragma unroll
   for (int i = 0; i < kAsyncBatches; ++i) is.next();
@@ -555,9 +617,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_encA_stream(const Units U) {
       float sq[kRowBatch];
 #pragma unroll
       for (int r = 0; r < kRowBatch; ++r) {
+        const int t = warp + kEncWarps * (b * kRowBatch + r);
         float v[8];
-        unpack8(slot[r * 32 + lane], v);
-        lpA_rows(v, warp + kEncWarps * (b * kRowBatch + r), sc, se, sw, sq[r]);
+        ring_row<kF8>(slot[r * 32 + lane], f8, src.row0 + t, t < src.nrow,
+                      src.col0 + 8 * lane, src.cols, v, bad);
+        lpA_rows(v, t, sc, se, sw, sq[r]);
       }
       ++consumed;
       is.next();  // refills the slot just read (each lane reads only its own copies)
@@ -569,16 +633,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_encA_stream(const Units U) {
     lpA_finish(se, sw, X.acs, X.ldk, X.part, X.nchr, X.cx, X.I, red, sh);
   }
   cp_async_wait<0>();
+  if (kF8 && bad) atomicExch(f8.inexact, 1);
 }
 
-template <class Units>
-__global__ void __launch_bounds__(kThreads, 2) k_encB_stream(const Units U) {
+template <class Units, bool kF8>
+__global__ void __launch_bounds__(kThreads, 2) k_encB_stream(const Units U, const Fp8Src f8) {
   __shared__ float red[kEncWarps * kEncCols];
   __shared__ float redq[kEncWarps * 32 * 2];
   extern __shared__ uint4 ring_s[];  // kRingBytesA
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint4* ring = ring_s + warp * kAsyncBatches * kRowBatch * 32;
-  RingIssuer<Units> is{U, ring, warp, lane};
+  bool bad = false;
+  RingIssuer<Units, kF8> is{U, f8, ring, warp, lane};
   is.start(blockIdx.x);
 #pragma unroll
   for (int i = 0; i < kAsyncBatches; ++i) is.next();
@@ -609,8 +675,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_encB_stream(const Units U) {
         float sums[2 * kRowBatch];
 #pragma unroll
         for (int r = 0; r < kRowBatch; ++r) {
+          const int t = warp + kEncWarps * (b * kRowBatch + r);
           float v[8];
-          unpack8(slot[r * 32 + lane], v);
+          ring_row<kF8>(slot[r * 32 + lane], f8, l0 + t, t < src.nrow, c0, X.n, v, bad);
           lpB_row(v, wq, cs, sums[2 * r], sums[2 * r + 1]);
         }
         ++consumed;
@@ -632,7 +699,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_encB_stream(const Units U) {
         for (int r = 0; r < kRowBatch; ++r) {
           const int t = warp + kEncWarps * (b * kRowBatch + r);
           float v[8], se, sw;
-          unpack8(slot[r * 32 + lane], v);
+          ring_row<kF8>(slot[r * 32 + lane], f8, l0 + t, t < src.nrow, c0, X.n, v, bad);
           lpB_row(v, wq, cs, se, sw);
           lpB_store_shfl(se, sw, seg, leader, t < src.nrow, X.bcs + (l0 + t) * X.ldcs + 4 * J,
                          q0, q1);
@@ -648,6 +715,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_encB_stream(const Units U) {
     lpB_finish(cs, q0, q1, X.n, X.vb, X.colpart, X.part, X.nch, X.cx, X.ry, red, redq);
   }
   cp_async_wait<0>();
+  if (kF8 && bad) atomicExch(f8.inexact, 1);
 }
 
 // The same outputs for any verify block size (one warp per row segment).
@@ -1045,7 +1113,11 @@ __global__ void k_fold_F(const float* __restrict__ F16, int64_t m, int64_t Cc, i
 // as bf16, which is exact when the scales are powers of two (an e4m3 value has
 // at most 4 significant bits).  A value that bf16 cannot hold exactly sets
 // *inexact (the call then reports ABFT_ERR_INVALID); columns cols .. ld-1 of
-// the plane are zero.  Thread = 8 consecutive elements of a row.
+// the plane are zero.  Thread = 8 consecutive elements (one 8-byte load, one
+// 16-byte store) of kDqRows rows, whose loads are in flight together; the 8
+// elements share one scale (8 divides 128).
+constexpr int kDqRows = 8;
+
 __global__ void __launch_bounds__(kThreads) k_fp8_dequant(const uint8_t* __restrict__ q, int64_t ldq,
                                                           int64_t rows, int64_t cols,
                                                           const float* __restrict__ scale,
@@ -1054,54 +1126,79 @@ __global__ void __launch_bounds__(kThreads) k_fp8_dequant(const uint8_t* __restr
   const int64_t c0 = 8 * ((int64_t)blockIdx.x * kThreads + threadIdx.x);
   if (c0 >= ld) return;
   const int64_t sld = cdiv(cols, 128);
-  for (int64_t i = blockIdx.y; i < rows; i += gridDim.y) {
-    const uint8_t* row = q + i * ldq;
-    const float* srow = scale + (i / 128) * sld;
-    __nv_bfloat16 o[8];
-    bool bad = false;
+  const bool full8 = c0 + 8 <= cols;
+  bool bad = false;
+  for (int64_t i0 = (int64_t)blockIdx.y * kDqRows; i0 < rows; i0 += (int64_t)gridDim.y * kDqRows) {
+    uint2 raw[kDqRows];
+    float sc[kDqRows];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const int64_t c = c0 + t;
-      float v = 0.f;
-      if (c < cols) {
-        const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)row[c], __NV_E4M3);
-        v = __half2float(__half(h)) * srow[c / 128];
+    for (int r = 0; r < kDqRows; ++r) {
+      const int64_t i = i0 + r;
+      raw[r] = make_uint2(0u, 0u);
+      sc[r] = 0.f;
+      if (i < rows && c0 < cols) {
+        const uint8_t* p = q + i * ldq + c0;
+        if (full8 && (reinterpret_cast<uintptr_t>(p) & 7) == 0) {
+          raw[r] = *reinterpret_cast<const uint2*>(p);
+        } else {
+          uint32_t w[2] = {0u, 0u};
+          for (int t = 0; t < 8; ++t)
+            if (c0 + t < cols) w[t >> 2] |= (uint32_t)p[t] << (8 * (t & 3));
+          raw[r] = make_uint2(w[0], w[1]);
+        }
+        sc[r] = scale[(i / 128) * sld + c0 / 128];
       }
-      o[t] = __float2bfloat16_rn(v);
-      bad |= !(__bfloat162float(o[t]) == v);  // also catches NaN
     }
-    store8(out + i * ld + c0, o);
-    if (bad) atomicExch(inexact, 1);
+#pragma unroll
+    for (int r = 0; r < kDqRows; ++r) {
+      const int64_t i = i0 + r;
+      if (i >= rows) break;
+      const uint32_t w[2] = {raw[r].x, raw[r].y};
+      __nv_bfloat16 o[8];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const __half2_raw h2 = __nv_cvt_fp8x2_to_halfraw2(
+            (__nv_fp8x2_storage_t)((w[t >> 1] >> (16 * (t & 1))) & 0xFFFFu), __NV_E4M3);
+        const float2 f = __half22float2(__half2(h2));
+        const float v0 = c0 + 2 * t < cols ? f.x * sc[r] : 0.f;
+        const float v1 = c0 + 2 * t + 1 < cols ? f.y * sc[r] : 0.f;
+        o[2 * t] = __float2bfloat16_rn(v0);
+        o[2 * t + 1] = __float2bfloat16_rn(v1);
+        bad |= !(__bfloat162float(o[2 * t]) == v0) || !(__bfloat162float(o[2 * t + 1]) == v1);
+      }
+      store8(out + i * ld + c0, o);
+    }
   }
+  if (bad) atomicExch(inexact, 1);
 }
 
 unsigned gy(int64_t v) { return (unsigned)(v < 65535 ? v : 65535); }
 
 // The streaming passes keep their row rings in dynamic shared memory beyond
 // the default 48 KiB.
-template <class Units>
-cudaError_t launch_stream_A(const Units& U, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_encA_stream<Units>,
+template <class Units, bool kF8 = false>
+cudaError_t launch_stream_A(const Units& U, cudaStream_t st, const Fp8Src& f8 = Fp8Src{}) {
+  cudaError_t e = cudaFuncSetAttribute(k_encA_stream<Units, kF8>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytesA);
   if (e != cudaSuccess || U.cnt == 0) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t grid = std::min<int64_t>(U.cnt, 2 * (int64_t)std::max(sms, 1));  // 2 CTAs per SM
-  k_encA_stream<Units><<<(unsigned)grid, kThreads, kRingBytesA, st>>>(U);
+  k_encA_stream<Units, kF8><<<(unsigned)grid, kThreads, kRingBytesA, st>>>(U, f8);
   count_launches(1);
   return cudaGetLastError();
 }
-template <class Units>
-cudaError_t launch_stream_B(const Units& U, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_encB_stream<Units>,
+template <class Units, bool kF8 = false>
+cudaError_t launch_stream_B(const Units& U, cudaStream_t st, const Fp8Src& f8 = Fp8Src{}) {
+  cudaError_t e = cudaFuncSetAttribute(k_encB_stream<Units, kF8>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytesA);
   if (e != cudaSuccess || U.cnt == 0) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t grid = std::min<int64_t>(U.cnt, 2 * (int64_t)std::max(sms, 1));
-  k_encB_stream<Units><<<(unsigned)grid, kThreads, kRingBytesA, st>>>(U);
+  k_encB_stream<Units, kF8><<<(unsigned)grid, kThreads, kRingBytesA, st>>>(U, f8);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -1212,33 +1309,48 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, cons
     count_launches(6 + (P.bs > 0 ? 1 : 0) + (fastB ? 0 : 1));
     return cudaGetLastError();
   }
+  // FP8: the exact dequantised values go to bf16 operand planes, which the
+  // checksums and the product use.  With 8-byte aligned e4m3 rows the
+  // streaming passes dequantise as they read (one pass over each operand);
+  // otherwise a dequantisation pass writes the planes first.
+  bool f8A = false, f8B = false;
+  Fp8Src fa{}, fb{};
+  int nlaunch = 0;
   if (d.dtype == ABFT_FP8_E4M3) {
-    // dequantise into the bf16 operand planes; the checksums and the product
-    // then work on those exact values
     int* flag = nullptr;
     cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&flag), g_fp8_inexact);
     if (e != cudaSuccess) return e;
     auto* pa = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_a);
     auto* pb = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_b);
-    k_fp8_dequant<<<dim3((unsigned)cdiv(P.L.op_a_ld, 8 * kThreads), gy(d.m)), kThreads, 0, st>>>(
-        static_cast<const uint8_t*>(Av), d.lda, d.m, d.k, static_cast<const float*>(a_scale), pa,
-        P.L.op_a_ld, flag);
-    k_fp8_dequant<<<dim3((unsigned)cdiv(P.L.op_b_ld, 8 * kThreads), gy(d.k)), kThreads, 0, st>>>(
-        static_cast<const uint8_t*>(Bv), d.ldb, d.k, d.n, static_cast<const float*>(b_scale), pb,
-        P.L.op_b_ld, flag);
-    count_launches(2);
+    const auto* qa = static_cast<const uint8_t*>(Av);
+    const auto* qb = static_cast<const uint8_t*>(Bv);
+    fa = Fp8Src{qa, d.lda, static_cast<const float*>(a_scale), cdiv(d.k, 128), pa, P.L.op_a_ld,
+                flag};
+    fb = Fp8Src{qb, d.ldb, static_cast<const float*>(b_scale), cdiv(d.n, 128), pb, P.L.op_b_ld,
+                flag};
+    f8A = ((reinterpret_cast<uintptr_t>(qa) & 7) == 0) && d.lda % 8 == 0;
+    f8B = ((reinterpret_cast<uintptr_t>(qb) & 7) == 0) && d.ldb % 8 == 0 && fastB;
+    if (!f8A) {
+      k_fp8_dequant<<<dim3((unsigned)cdiv(P.L.op_a_ld, 8 * kThreads), gy(cdiv(d.m, kDqRows))),
+                      kThreads, 0, st>>>(qa, d.lda, d.m, d.k, fa.sc, pa, P.L.op_a_ld, flag);
+      ++nlaunch;
+    }
+    if (!f8B) {
+      k_fp8_dequant<<<dim3((unsigned)cdiv(P.L.op_b_ld, 8 * kThreads), gy(cdiv(d.k, kDqRows))),
+                      kThreads, 0, st>>>(qb, d.ldb, d.k, d.n, fb.sc, pb, P.L.op_b_ld, flag);
+      ++nlaunch;
+    }
     A = pa;
     B = pb;
     lda = P.L.op_a_ld;
     ldb = P.L.op_b_ld;
   }
-  int nlaunch = 0;
-  if (rows_aligned(A, lda)) {
+  if (f8A || rows_aligned(A, lda)) {
     SingleAUnits U{};
     U.base = EncAUnit{A, lda, d.m, d.k, d.vb_rows, P.er, acs, P.L.acs_ld, rowpart, nchr, partA, 0, 0};
     U.ncx = cdiv(P.L.acs_ld, kEncCols);
     U.cnt = U.ncx * P.nvr;
-    cudaError_t e = launch_stream_A(U, st);
+    cudaError_t e = f8A ? launch_stream_A<SingleAUnits, true>(U, st, fa) : launch_stream_A(U, st);
     if (e != cudaSuccess) return e;
   } else {
     k_lpA_cols<<<dim3((unsigned)cdiv(P.L.acs_ld, kEncCols), gy(P.nvr)), kThreads, 0, st>>>(
@@ -1251,13 +1363,13 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, cons
   k_lp_norms<<<(unsigned)cdiv(d.m, 128), 128, 0, st>>>(rowpart, d.m, nchr, nchr, 1, nArow);
   k_lp_blk<<<(unsigned)cdiv(P.nvr * 32, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA, nchr,
                                                        nAblk);
-  if (fastB && rows_aligned(B, ldb)) {
+  if (f8B || (fastB && rows_aligned(B, ldb))) {
     SingleBUnits U{};
     U.base = EncBUnit{B, ldb, d.k, d.n, d.vb_cols, P.ec, bcs, P.L.bcs_ld, colpart, partB, nchB,
                       0, 0};
     U.ncx = cdiv(d.n, kEncCols);
     U.cnt = U.ncx * nchB;
-    cudaError_t e = launch_stream_B(U, st);
+    cudaError_t e = f8B ? launch_stream_B<SingleBUnits, true>(U, st, fb) : launch_stream_B(U, st);
     if (e != cudaSuccess) return e;
   } else if (fastB) {
     k_lpB_rows<<<dim3((unsigned)cdiv(d.n, kEncCols), gy(nchB)), kThreads, 0, st>>>(

@@ -77,6 +77,7 @@ SHAPES = [  # (m, n, k, vb_r, vb_c, p, q)
     (384, 256, 200, 128, 64, 3, 2),
     (200, 300, 136, 40, 30, 0, 0),
     (640, 700, 520, 128, 256, 0, 0),
+    (256, 264, 250, 128, 64, 0, 0),   # rows of A not 8-byte aligned: separate dequantisation
 ]
 
 

@@ -12,8 +12,10 @@ product) and attaches them as "bf16_16384" and "bf16x3_16384".
 value       useful TFLOP/s (2mnk per step / step time), operands resident in HBM
 overhead    product-only and whole-step time over the checksum-free product of the same
             kernel, minus one
-e2e         the same metric through the C ABI with host buffers: pinned host -> device
-            copy of A and B and device -> host copy of C inside the timed region
+e2e         the same metric through the C ABI with host buffers: every step's pinned
+            host -> device copy of A and B and device -> host copy of C inside the timed
+            region, pipelined over two device buffer sets (the next step's inputs are
+            copied, and the previous step's result read back, while a step computes)
 roofline    the product kernel: algorithmic FLOPs per launch / measured launch time
 cpu_baseline the CPU oracle on a bounded sample of the workload, on the host cores
 
@@ -347,23 +349,24 @@ def run_workload(w, args, dev, rank, world, secondary=False):
 
     gemm_ms = []
 
-    def step(timed_gemm=False):
-        abft.abft_encode(desc, A, B, ws, stream=stream, **scales)
+    def step(timed_gemm=False, bufs=None):
+        A_, B_, C_, ws_ = bufs if bufs is not None else (A, B, C, ws)
+        abft.abft_encode(desc, A_, B_, ws_, stream=stream, **scales)
         if timed_gemm:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-        abft.abft_gemm(desc, A, B, C, ws, stream=stream)
+        abft.abft_gemm(desc, A_, B_, C_, ws_, stream=stream)
         if timed_gemm:
             e1.record(stream)
         if not lp:  # memory faults in the stored C
-            abft.abft_inject_bitflips(desc, C, flips, stream=stream)
+            abft.abft_inject_bitflips(desc, C_, flips, stream=stream)
         for bi, bj in erased:
-            abft.abft_erase_block(desc, C, bi, bj, stream=stream)
-        st, rep, n = abft.abft_verify_correct(desc, C, ws, erased=erased, stream=stream,
+            abft.abft_erase_block(desc, C_, bi, bj, stream=stream)
+        st, rep, n = abft.abft_verify_correct(desc, C_, ws_, erased=erased, stream=stream,
                                               reread_C=0 if lp else 1)
         st2 = abft.OK
         for bi, bj in erased:
-            st2, _ = abft.abft_recover_block(desc, C, ws, bi, bj, stream=stream)
+            st2, _ = abft.abft_recover_block(desc, C_, ws_, bi, bj, stream=stream)
         if timed_gemm:
             gemm_ms.append(e0.elapsed_time(e1))
         return st, st2, rep
@@ -415,29 +418,65 @@ def run_workload(w, args, dev, rank, world, secondary=False):
 
     e2e = None
     if not args.no_e2e and not secondary:
+        # Two device buffer sets: step i computes on set i % 2 while the host -> device
+        # copy of step i + 1's inputs (copy stream) and the device -> host read of step
+        # i - 1's result (read-back stream) run on the copy engines.  Every step's copies
+        # are inside the timed region.
         A_h = A.cpu().pin_memory()
         B_h = B.cpu().pin_memory()
-        C_h = torch.empty(C.shape, dtype=C.dtype).pin_memory()
+        C_h = [torch.empty(C.shape, dtype=C.dtype).pin_memory() for _ in range(2)]
+        A2, B2, C2 = torch.empty_like(A), torch.empty_like(B), torch.empty_like(C)
+        ws2 = torch.zeros_like(ws)
+        if lp:  # the armed epilogue faults live in the workspace
+            abft.abft_encode(desc, A, B, ws2, stream=stream, **scales)
+            abft.abft_set_epilogue_faults(desc, ws2, flips, stream=stream)
+        sets = [(A, B, C, ws), (A2, B2, C2, ws2)]
+        h2d_s, d2h_s = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+        ev = lambda: torch.cuda.Event()  # noqa: E731
+        loaded = [ev(), ev()]     # a set's inputs are on the device
+        computed = [ev(), ev()]   # a set's step is done (its C may be read back)
+        freed = [ev(), ev()]      # a set's result has been read back (the set may be reused)
         torch.cuda.synchronize()
         barrier()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for _ in range(args.steps):
-            with torch.cuda.stream(stream):
-                A.copy_(A_h, non_blocking=True)
-                B.copy_(B_h, non_blocking=True)
-            step()
-            with torch.cuda.stream(stream):
-                C_h.copy_(C, non_blocking=True)
+
+        def load(x):
+            h2d_s.wait_event(a)
+            if used[x]:
+                h2d_s.wait_event(freed[x])
+            with torch.cuda.stream(h2d_s):
+                sets[x][0].copy_(A_h, non_blocking=True)
+                sets[x][1].copy_(B_h, non_blocking=True)
+            loaded[x].record(h2d_s)
+            used[x] = True
+
+        used = [False, False]
+        load(0)
+        for i in range(args.steps):
+            x = i % 2
+            if i + 1 < args.steps:
+                load(1 - x)
+            stream.wait_event(loaded[x])
+            step(bufs=sets[x])
+            computed[x].record(stream)
+            d2h_s.wait_event(computed[x])
+            with torch.cuda.stream(d2h_s):
+                C_h[x].copy_(sets[x][2], non_blocking=True)
+            freed[x].record(d2h_s)
+        stream.wait_event(freed[(args.steps - 1) % 2])
+        if args.steps > 1:
+            stream.wait_event(freed[args.steps % 2])
         b.record(stream)
         torch.cuda.synchronize()
         barrier()
         e2e_ms = a.elapsed_time(b) / args.steps
+        del A2, B2, C2, ws2
         e2e_ms = mg.max_over_ranks(e2e_ms)
         e2e = {"value": 2.0 * w.m * w.n * w.k * world / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": A_h.numel() * A_h.element_size() +
                                      B_h.numel() * B_h.element_size(),
-               "d2h_bytes_per_step": C_h.numel() * C_h.element_size()}
+               "d2h_bytes_per_step": C_h[0].numel() * C_h[0].element_size()}
 
     step_ms = mg.max_over_ranks(step_ms)
 

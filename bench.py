@@ -48,9 +48,11 @@ METRIC = "ABFT GEMM TFLOPS (useful 2mnk) and % overhead vs checksum-free GEMM, s
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # Measured DRAM read + write per launch of the product kernel at the bench workloads (ncu
 # dram__bytes_read.sum + dram__bytes_write.sum, see profiles/), or None when the kernel
-# changed since it was captured.  f64: 45.50 + 1.08 GB; bf16: 8.91 + 1.18 GB; bf16x6:
-# 126.78 + 1.54 GB; grouped 4096 (ABFT product, chosen tuning): 18.98 + 20.55 GB.
-TRAFFIC_BYTES = {"f64": 46.58e9, "bf16": None, "bf16x6": None, "grouped": None}
+# changed since it was captured.  f64: 45.50 + 1.08 GB; bf16 and fp8 (the product of the
+# bf16 planes): 8.91 + 1.18 GB; bf16x6: 56.30 + 1.54 GB (mean of three launches, 53-59 GB
+# read); grouped 4096 (ABFT product, chosen tuning): 18.98 + 20.55 GB.
+TRAFFIC_BYTES = {"f64_11264_grid22": 46.58e9, "bf16_16384": 10.09e9, "fp8_16384": 10.09e9,
+                 "bf16x6_16384": 57.83e9, "bf16_grouped_4096": 39.53e9}
 
 
 def bf16_peak():
@@ -492,7 +494,7 @@ def run_workload(w, args, dev, rank, world, secondary=False):
         roof = {"kernel": "k_gemm_f64", "bound": "alu", "peak_source": peak_src}
     achieved = kernel_flops / (gemm_avg * 1e-3) / 1e12
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                 "traffic": TRAFFIC_BYTES.get(w.dtype), "algorithmic_flops_per_launch": kernel_flops})
+                 "traffic": TRAFFIC_BYTES.get(w.name), "algorithmic_flops_per_launch": kernel_flops})
     value = mg.weak_scaling_value(useful, world, step_ms)
     cfg = {"workload": w.name, "m": w.m, "n": w.n, "k": w.k, "verify_block": [w.vb_r, w.vb_c],
            "dist": {"fp8": "U[-1,1] x 10^U(-2,2) per row, e4m3 with power-of-two binary32 "
@@ -694,7 +696,7 @@ def run_grouped(w, args, dev, rank, world, secondary=False):
         "roofline": {"kernel": "k_gemm_grouped", "bound": "tensor", "peak_source": peak_src,
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
-                     "traffic": TRAFFIC_BYTES["grouped"] if w.count == 4096 else None,
+                     "traffic": TRAFFIC_BYTES.get(w.name),
                      "algorithmic_flops_per_launch": useful + cs_flops},
         "gpu_launches": launches, "clocks": clocks, "e2e": None,
     }

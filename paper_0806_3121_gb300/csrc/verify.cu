@@ -677,11 +677,17 @@ __global__ void __launch_bounds__(kThreads) k_grp_col(const GProb* __restrict__ 
   const int64_t I = e.y / ncx, j = (e.y % ncx) * kThreads + threadIdx.x;
   if (j >= P.n) return;
   // the verify block (one tile row) is four 32-row blocks of observed sums
-  float se32 = 0.f, sw32 = 0.f;
-  for (int64_t b = 4 * I; b < min(4 * I + 4, cdiv(P.m, 32)); ++b) {
-    se32 += P.obs_col[(b * 2 + 0) * P.n + j];
-    sw32 += P.obs_col[(b * 2 + 1) * P.n + j];
+  // (all eight loads issued before the sums, added in block order)
+  const int64_t nb32 = cdiv(P.m, 32);
+  float pe[4], pw[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t b = 4 * I + q;
+    pe[q] = b < nb32 ? P.obs_col[(b * 2 + 0) * P.n + j] : 0.f;
+    pw[q] = b < nb32 ? P.obs_col[(b * 2 + 1) * P.n + j] : 0.f;
   }
+  const float se32 = ((pe[0] + pe[1]) + pe[2]) + pe[3];
+  const float sw32 = ((pw[0] + pw[1]) + pw[2]) + pw[3];
   const float* E = P.E16 + 4 * I * P.n + j;
   const float nb = P.nBcol32[j];
   if (screen_pass(se32, sw32, E[0] + E[P.n], E[2 * P.n] + E[3 * P.n], nb * P.tauA[2 * I],

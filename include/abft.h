@@ -195,8 +195,12 @@ abft_status abft_encode_noalloc(const abft_desc* desc, const void* A, const void
  * other side's lines, whose expectations were formed from the changed
  * operand, are reported ABFT_KIND_UNCORRECTABLE (status
  * ABFT_ERR_UNCORRECTABLE; at most 2048 elements can be recomputed in one
- * verify).  ABFT_F64 only (ABFT_ERR_UNSUPPORTED otherwise); the earlier
- * descriptors must be ABFT_F64 too.  With both left and right NULL this is
+ * verify).  dtype ABFT_F64, ABFT_BF16X3 or ABFT_BF16X6 (ABFT_ERR_UNSUPPORTED
+ * otherwise).  An ABFT_F64 product chains to ABFT_F64 products (binary64 C);
+ * a split product chains to any tensor-core product (binary32 C: ABFT_BF16,
+ * ABFT_BF16X3, ABFT_BF16X6, ABFT_FP8_E4M3), whose binary64 checksums enter
+ * its checksum planes as two (X3) or three (X6) bf16 pieces; other pairings
+ * return ABFT_ERR_INVALID.  With both left and right NULL this is
  * abft_encode.  Asynchronous; the earlier workspaces must stay untouched
  * until the call completes on the stream. */
 abft_status abft_encode_chained(const abft_desc* desc, const void* A, const void* B,

@@ -285,10 +285,18 @@ abft_status abft_encode_chained(const abft_desc* desc, const void* A, const void
   abft_status st = make_plan(desc, &P);
   if (st != ABFT_OK) return st;
   const abft_desc& d = P.d;
-  if (d.dtype != ABFT_F64) return fail(ABFT_ERR_UNSUPPORTED, "chained encode: ABFT_F64 only");
+  const bool split = d.dtype == ABFT_BF16X3 || d.dtype == ABFT_BF16X6;
+  if (d.dtype != ABFT_F64 && !split)
+    return fail(ABFT_ERR_UNSUPPORTED,
+                "chained encode: ABFT_F64, ABFT_BF16X3 and ABFT_BF16X6 products only");
+  // the earlier product's C is this product's operand: binary64 C for an
+  // ABFT_F64 product, binary32 C (any tensor-core dtype) for a split one
+  auto c_matches = [&](int dt) { return split ? dt != ABFT_F64 : dt == ABFT_F64; };
+  const char* c_msg = split ? "a split product takes the binary32 C of a tensor-core product"
+                            : "an ABFT_F64 product takes the binary64 C of an ABFT_F64 product";
   if (left_desc) {
     if ((st = make_plan(left_desc, &PL)) != ABFT_OK) return st;
-    if (PL.d.dtype != ABFT_F64) return fail(ABFT_ERR_UNSUPPORTED, "chained encode: ABFT_F64 only");
+    if (!c_matches(PL.d.dtype)) return fail(ABFT_ERR_INVALID, "left chain: %s", c_msg);
     if (PL.d.m != d.m || PL.d.n != d.k || PL.d.vb_rows != d.vb_rows)
       return fail(ABFT_ERR_INVALID,
                   "left chain: the earlier product must be m x k with the same vb_rows");
@@ -300,8 +308,7 @@ abft_status abft_encode_chained(const abft_desc* desc, const void* A, const void
   }
   if (right_desc) {
     if ((st = make_plan(right_desc, &PR)) != ABFT_OK) return st;
-    if (PR.d.dtype != ABFT_F64)
-      return fail(ABFT_ERR_UNSUPPORTED, "chained encode: ABFT_F64 only");
+    if (!c_matches(PR.d.dtype)) return fail(ABFT_ERR_INVALID, "right chain: %s", c_msg);
     if (PR.d.m != d.k || PR.d.n != d.n || PR.d.vb_cols != d.vb_cols)
       return fail(ABFT_ERR_INVALID,
                   "right chain: the earlier product must be k x n with the same vb_cols");
@@ -311,10 +318,14 @@ abft_status abft_encode_chained(const abft_desc* desc, const void* A, const void
   if (!ws || (d.k > 0 && (!A || !B))) return fail(ABFT_ERR_INVALID, "NULL pointer");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = clear_carry(P, ws, s);
-  if (e == cudaSuccess)
-    e = launch_encode_f64_chained(P, static_cast<const double*>(A), static_cast<const double*>(B),
-                                  ws, left_desc ? &PL : nullptr, left_ws,
-                                  right_desc ? &PR : nullptr, right_ws, s);
+  if (e == cudaSuccess) {
+    const Plan* pl = left_desc ? &PL : nullptr;
+    const Plan* pr = right_desc ? &PR : nullptr;
+    e = split ? launch_encode_lp_chained(P, A, B, ws, pl, left_ws, pr, right_ws, s)
+              : launch_encode_f64_chained(P, static_cast<const double*>(A),
+                                          static_cast<const double*>(B), ws, pl, left_ws, pr,
+                                          right_ws, s);
+  }
   return e == cudaSuccess ? ABFT_OK : cuda_fail(e, "abft_encode_chained");
 }
 

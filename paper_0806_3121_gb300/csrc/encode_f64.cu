@@ -401,6 +401,26 @@ cudaError_t launch_encode_f64_noalloc(const Plan& P, const double* A, const doub
   return cudaGetLastError();
 }
 
+// Deviation bounds of the checksums carried out of an earlier product PL
+// (workspace wsL): its column checksum rows (one pair per row verify block)
+// and its row checksum columns (one pair per column verify block).
+cudaError_t launch_carry_rows(const Plan& PL, const void* wsL, double* car, cudaStream_t st) {
+  const char* wl = static_cast<const char*>(wsL);
+  k_carry<<<1, kThreads, 0, st>>>(reinterpret_cast<const double*>(wl + PL.L.nBcol), PL.d.n,
+                                  reinterpret_cast<const double*>(wl + PL.L.nAblk),
+                                  reinterpret_cast<const double*>(wl + PL.L.car_a), PL.nvr,
+                                  PL.f1_col, PL.f2_col, car);
+  return cudaGetLastError();
+}
+cudaError_t launch_carry_cols(const Plan& PR, const void* wsR, double* car, cudaStream_t st) {
+  const char* wr = static_cast<const char*>(wsR);
+  k_carry<<<1, kThreads, 0, st>>>(reinterpret_cast<const double*>(wr + PR.L.nArow), PR.d.m,
+                                  reinterpret_cast<const double*>(wr + PR.L.nBblk),
+                                  reinterpret_cast<const double*>(wr + PR.L.car_b), PR.nvc,
+                                  PR.f1_row, PR.f2_row, car);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_encode_f64_chained(const Plan& P, const double* A, const double* B, void* ws,
                                       const Plan* PL, const void* wsL, const Plan* PR,
                                       const void* wsR, cudaStream_t st) {
@@ -434,10 +454,7 @@ cudaError_t launch_encode_f64_chained(const Plan& P, const double* A, const doub
     if (e != cudaSuccess) return e;
     k_rows_sq<<<dim3((unsigned)nchA, gy(2 * P.nvr)), kThreads, 0, st>>>(acs, d.k, 2 * P.nvr,
                                                                          partA, nchA);
-    k_carry<<<1, kThreads, 0, st>>>(reinterpret_cast<const double*>(wl + PL->L.nBcol), PL->d.n,
-                                    reinterpret_cast<const double*>(wl + PL->L.nAblk),
-                                    reinterpret_cast<const double*>(wl + PL->L.car_a), P.nvr,
-                                    PL->f1_col, PL->f2_col, carA);
+    launch_carry_rows(*PL, wsL, carA, st);
     launches += 2;
   } else {
     k_encA_cols<<<dim3((unsigned)nchA, gy(P.nvr)), kThreads, 0, st>>>(
@@ -459,10 +476,7 @@ cudaError_t launch_encode_f64_chained(const Plan& P, const double* A, const doub
     if (e != cudaSuccess) return e;
     k_cols_sq<<<(unsigned)cdiv(P.Cc * nchB, kThreads), kThreads, 0, st>>>(bcs, d.k, P.Cc, partB,
                                                                            nchB);
-    k_carry<<<1, kThreads, 0, st>>>(reinterpret_cast<const double*>(wr + PR->L.nArow), PR->d.m,
-                                    reinterpret_cast<const double*>(wr + PR->L.nBblk),
-                                    reinterpret_cast<const double*>(wr + PR->L.car_b), P.nvc,
-                                    PR->f1_row, PR->f2_row, carB);
+    launch_carry_cols(*PR, wsR, carB, st);
     launches += 2;
   } else {
     k_encB_rows<<<dim3((unsigned)cdiv(nchB, kThreads / 32), gy(P.nvc)), kThreads, 0, st>>>(

@@ -910,7 +910,7 @@ __global__ void __launch_bounds__(kThreads) k_x3A_cols(const float* __restrict__
                                                        const Planes op, const Planes cs,
                                                        int64_t ldk, float* __restrict__ rowpart,
                                                        int64_t nchr, double* __restrict__ part,
-                                                       int64_t nch) {
+                                                       int64_t nch, int cs_on) {
   __shared__ float sh[kThreads / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t c0 = (int64_t)blockIdx.x * kColsPerCta + 8 * threadIdx.x;
@@ -937,6 +937,7 @@ __global__ void __launch_bounds__(kThreads) k_x3A_cols(const float* __restrict__
       const int64_t rc = (int64_t)blockIdx.x * (kThreads / 32) + warp;
       if (lane == 0 && rc < nchr) rowpart[i * nchr + rc] = sq;
     }
+    if (!cs_on) continue;  // chained: the checksum rows are carried, not formed
     float q0 = 0.f, q1 = 0.f;
     if (c0 < ldk) {
       store_split8(cs, (2 * I) * ldk + c0, se);
@@ -1172,6 +1173,91 @@ __global__ void __launch_bounds__(kThreads) k_fp8_dequant(const uint8_t* __restr
   if (bad) atomicExch(inexact, 1);
 }
 
+// ---------------- chained split products (binary32 operands)
+// A chained bf16x3 / bf16x6 product carries the earlier product's binary64
+// checksums (section 3.2); they enter the checksum planes as bf16 pieces of
+// the binary64 values (three pieces hold a value to 2^-27, two to 2^-18 --
+// the representation the thresholds already carry as u_cs).
+
+__device__ __forceinline__ void split_pieces_d(double x, __nv_bfloat16 (&out)[3]) {
+  double r = x;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    out[i] = __double2bfloat16(r);
+    r -= (double)__bfloat162float(out[i]);
+  }
+}
+
+// Carried rows E[r][l] (rows x k, binary64, ld k) into row r of the checksum
+// planes (ld ldk; columns k .. ldk-1 zero), and partials of the squared norms
+// of the first nrm rows: part[r * nch + chunk], chunks of 8 * 256 columns
+// (the layout the split A pass leaves).  Grid (nch, <= 65535); thread = 8
+// consecutive columns.
+__global__ void __launch_bounds__(kThreads) k_carried_rows_split(const double* __restrict__ E,
+                                                                 int64_t rows, int64_t k,
+                                                                 const Planes cs, int64_t ldk,
+                                                                 double* __restrict__ part,
+                                                                 int64_t nch, int64_t nrm) {
+  __shared__ double shd[kThreads / 32];
+  const int64_t c0 = (int64_t)blockIdx.x * kColsPerCta + 8 * threadIdx.x;
+  for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
+    double q = 0.0;
+    if (c0 < ldk) {
+      __nv_bfloat16 h[3][8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const double x = c0 + t < k ? E[r * k + c0 + t] : 0.0;
+        q = fma(x, x, q);
+        __nv_bfloat16 pc[3];
+        split_pieces_d(x, pc);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) h[i][t] = pc[i];
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        if (i < cs.np) store8(cs.p[i] + r * ldk + c0, h[i]);
+    }
+    if (r < nrm) {  // uniform in the block
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+      __syncthreads();
+      if ((threadIdx.x & 31) == 0) shd[threadIdx.x >> 5] = q;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) t += shd[w];
+        part[r * nch + blockIdx.x] = t;
+      }
+    }
+  }
+}
+
+// Carried columns F[l][c] (k x Cc, binary64) into column c of the checksum
+// planes (ld ldcs), and partials part[c * nch + chunk] of their squared norms
+// over chunks of 128 rows (the layout the split B pass leaves).  One thread
+// per (column, chunk).
+__global__ void __launch_bounds__(kThreads) k_carried_cols_split(const double* __restrict__ F,
+                                                                 int64_t k, int64_t Cc,
+                                                                 const Planes cs, int64_t ldcs,
+                                                                 double* __restrict__ part,
+                                                                 int64_t nch) {
+  const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (t >= Cc * nch) return;
+  const int64_t c = t % Cc, chunk = t / Cc;
+  const int64_t l0 = chunk * kRowsPerCtaB, l1 = min(l0 + (int64_t)kRowsPerCtaB, k);
+  double q = 0.0;
+  for (int64_t l = l0; l < l1; ++l) {
+    const double x = F[l * Cc + c];
+    q = fma(x, x, q);
+    __nv_bfloat16 pc[3];
+    split_pieces_d(x, pc);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      if (i < cs.np) cs.p[i][l * ldcs + c] = pc[i];
+  }
+  part[c * nch + chunk] = q;
+}
+
 unsigned gy(int64_t v) { return (unsigned)(v < 65535 ? v : 65535); }
 
 // The streaming passes keep their row rings in dynamic shared memory beyond
@@ -1282,7 +1368,8 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, cons
       bcsp.p[i] = reinterpret_cast<__nv_bfloat16*>(w + P.L.bcs + i * P.L.bcs_plane);
     }
     k_x3A_cols<<<dim3((unsigned)nchA, gy(P.nvr)), kThreads, 0, st>>>(
-        Af, d.lda, d.m, d.k, d.vb_rows, P.er, opa, acsp, P.L.acs_ld, rowpart, nchr, partA, nchA);
+        Af, d.lda, d.m, d.k, d.vb_rows, P.er, opa, acsp, P.L.acs_ld, rowpart, nchr, partA, nchA,
+        1);
     if (P.bs > 0) {
       Planes sp = acsp;
       for (int i = 0; i < np; ++i) sp.p[i] += 2 * P.nvr * P.L.acs_ld;
@@ -1385,6 +1472,97 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, cons
   k_lp_blk<<<(unsigned)cdiv(P.nvc * 32, 128), 128, 0, st>>>(nBcol, d.n, d.vb_cols, P.ec, partB, nchB,
                                                        nBblk);
   count_launches(nlaunch + 4 + (P.bs > 0 ? 1 : 0) + (fastB ? 0 : 2));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_encode_lp_chained(const Plan& P, const void* Av, const void* Bv, void* ws,
+                                     const Plan* PL, const void* wsL, const Plan* PR,
+                                     const void* wsR, cudaStream_t st) {
+  const abft_desc& d = P.d;
+  if (d.k == 0 || (!PL && !PR)) return launch_encode_lp(P, Av, Bv, nullptr, nullptr, ws, st);
+  char* w = static_cast<char*>(ws);
+  double* nArow = reinterpret_cast<double*>(w + P.L.nArow);
+  double* nAblk = reinterpret_cast<double*>(w + P.L.nAblk);
+  double* nBcol = reinterpret_cast<double*>(w + P.L.nBcol);
+  double* nBblk = reinterpret_cast<double*>(w + P.L.nBblk);
+  double* carA = reinterpret_cast<double*>(w + P.L.car_a);
+  double* carB = reinterpret_cast<double*>(w + P.L.car_b);
+  Scratch S = scratch_view(P, ws);
+  const int64_t nchA = cdiv(d.k, kColsPerCta);
+  const int64_t nchB = cdiv(d.k, kRowsPerCtaB);
+  const int64_t nchr = cdiv(d.k, 256);
+  double* partA = S.part;
+  double* partB = partA + 2 * P.nvr * nchr;
+  float* rowpart = reinterpret_cast<float*>(partB + 2 * P.nvc * nchB);
+  float* colpart = rowpart + d.m * nchr;
+  const bool fastB = d.vb_cols >= 8 && d.vb_cols <= 256 && (d.vb_cols & (d.vb_cols - 1)) == 0;
+  const float* Af = static_cast<const float*>(Av);
+  const float* Bf = static_cast<const float*>(Bv);
+  const int np = P.L.planes;
+  Planes opa{}, opb{}, acsp{}, bcsp{};
+  opa.np = opb.np = acsp.np = bcsp.np = np;
+  for (int i = 0; i < np; ++i) {
+    opa.p[i] = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_a) + i * align_elems(d.m * P.L.op_a_ld);
+    opb.p[i] = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_b) + i * align_elems(d.k * P.L.op_b_ld);
+    acsp.p[i] = reinterpret_cast<__nv_bfloat16*>(w + P.L.acs + i * P.L.acs_plane);
+    bcsp.p[i] = reinterpret_cast<__nv_bfloat16*>(w + P.L.bcs + i * P.L.bcs_plane);
+  }
+  for (int pl = 0; pl < np; ++pl)
+    if (P.L.bcs_ld > P.L.bcs_cols)
+      cudaMemset2DAsync(reinterpret_cast<char*>(bcsp.p[pl]) + P.L.bcs_cols * 2, P.L.bcs_ld * 2, 0,
+                        (P.L.bcs_ld - P.L.bcs_cols) * 2, d.k, st);
+  int launches = 0;
+  cudaError_t e = cudaSuccess;
+  // A: operand planes and row norms from A; checksum rows carried (E of the
+  // earlier product: verify rows, then block checksum rows) or formed
+  k_x3A_cols<<<dim3((unsigned)nchA, gy(P.nvr)), kThreads, 0, st>>>(
+      Af, d.lda, d.m, d.k, d.vb_rows, P.er, opa, acsp, P.L.acs_ld, rowpart, nchr, partA, nchA,
+      PL ? 0 : 1);
+  ++launches;
+  if (PL) {
+    const double* EL = reinterpret_cast<const double*>(static_cast<const char*>(wsL) + PL->L.E);
+    k_carried_rows_split<<<dim3((unsigned)nchA, gy(P.R)), kThreads, 0, st>>>(
+        EL, P.R, d.k, acsp, P.L.acs_ld, partA, nchA, 2 * P.nvr);
+    if ((e = launch_carry_rows(*PL, wsL, carA, st)) != cudaSuccess) return e;
+    launches += 2;
+  } else if (P.bs > 0) {
+    Planes sp = acsp;
+    for (int i = 0; i < np; ++i) sp.p[i] += 2 * P.nvr * P.L.acs_ld;
+    k_x3A_block<<<dim3((unsigned)cdiv(d.k, kThreads), gy(P.f * P.bs)), kThreads, 0, st>>>(
+        Af, d.lda, d.k, d.grid_p, P.bs, P.f, sp, P.L.acs_ld);
+    ++launches;
+  }
+  k_lp_norms<<<(unsigned)cdiv(d.m, 128), 128, 0, st>>>(rowpart, d.m, nchr, nchr, 1, nArow);
+  k_lp_blk<<<(unsigned)cdiv(P.nvr * 32, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA,
+                                                       nchA, nAblk);
+  launches += 2;
+  // B: operand planes and column norms from B; checksum columns carried (F of
+  // the earlier product) or formed
+  if (PR) {
+    k_x3B_split<<<dim3((unsigned)cdiv(P.L.op_b_ld, kThreads), gy(nchB)), kThreads, 0, st>>>(
+        Bf, d.ldb, d.k, d.n, opb, P.L.op_b_ld, colpart);
+    const double* FR = reinterpret_cast<const double*>(static_cast<const char*>(wsR) + PR->L.F);
+    k_carried_cols_split<<<(unsigned)cdiv(P.Cc * nchB, kThreads), kThreads, 0, st>>>(
+        FR, d.k, P.Cc, bcsp, P.L.bcs_ld, partB, nchB);
+    if ((e = launch_carry_cols(*PR, wsR, carB, st)) != cudaSuccess) return e;
+    launches += 3;
+  } else if (fastB) {
+    k_x3B_rows<<<dim3((unsigned)cdiv(P.L.op_b_ld, kColsPerCta), (unsigned)nchB), kThreads, 0,
+                 st>>>(Bf, d.ldb, d.k, d.n, d.vb_cols, P.ec, opb, P.L.op_b_ld, bcsp, P.L.bcs_ld,
+                       colpart, partB, nchB);
+    ++launches;
+  } else {
+    k_x3B_split<<<dim3((unsigned)cdiv(P.L.op_b_ld, kThreads), gy(nchB)), kThreads, 0, st>>>(
+        Bf, d.ldb, d.k, d.n, opb, P.L.op_b_ld, colpart);
+    k_x3B_rows_any<<<dim3((unsigned)cdiv(nchB, kThreads / 32), gy(P.nvc)), kThreads, 0, st>>>(
+        Bf, d.ldb, d.k, d.n, d.vb_cols, P.ec, bcsp, P.L.bcs_ld, partB, nchB);
+    launches += 2;
+  }
+  k_lp_norms<<<(unsigned)cdiv(d.n, 128), 128, 0, st>>>(colpart, d.n, nchB, 1, d.n, nBcol);
+  k_lp_blk<<<(unsigned)cdiv(P.nvc * 32, 128), 128, 0, st>>>(nBcol, d.n, d.vb_cols, P.ec, partB,
+                                                       nchB, nBblk);
+  launches += 2;
+  count_launches(launches);
   return cudaGetLastError();
 }
 

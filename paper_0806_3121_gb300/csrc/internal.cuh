@@ -121,6 +121,16 @@ cudaError_t launch_encode_f64(const Plan& P, const double* A, const double* B, v
 cudaError_t launch_encode_f64_chained(const Plan& P, const double* A, const double* B, void* ws,
                                       const Plan* PL, const void* wsL, const Plan* PR,
                                       const void* wsR, cudaStream_t st);
+// Deviation bounds of the checksum rows / columns carried out of an earlier
+// product (its plan and workspace), into car (2 per verify block).
+cudaError_t launch_carry_rows(const Plan& PL, const void* wsL, double* car, cudaStream_t st);
+cudaError_t launch_carry_cols(const Plan& PR, const void* wsR, double* car, cudaStream_t st);
+// Chained encode of the split dtypes (binary32 operands, bf16 pieces): the
+// operand planes are split from A and B as usual; the carried rows / columns
+// are split into the checksum planes instead of forming checksums.
+cudaError_t launch_encode_lp_chained(const Plan& P, const void* A, const void* B, void* ws,
+                                     const Plan* PL, const void* wsL, const Plan* PR,
+                                     const void* wsR, cudaStream_t st);
 // Encode with its partial sums in a static device array (no workspace scratch).
 cudaError_t launch_encode_f64_noalloc(const Plan& P, const double* A, const double* B, void* ws,
                                       cudaStream_t st);

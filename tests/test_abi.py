@@ -116,10 +116,12 @@ def test_invalid_calls_launch_nothing(lib):
     ("left", dict(n=40), abft.ERR_INVALID, "left chain"),          # earlier n != this k
     ("left", dict(vb_rows=16), abft.ERR_INVALID, "left chain"),
     ("left", dict(grid_p=0, grid_q=0), abft.ERR_INVALID, "grid"),  # no block checksums to carry
-    ("left", dict(dtype=1, lda=64, ldb=80), abft.ERR_UNSUPPORTED, "ABFT_F64"),
+    ("left", dict(dtype=1, lda=64, ldb=80), abft.ERR_INVALID, "binary64 C"),  # bf16 earlier C
     ("right", dict(m=32), abft.ERR_INVALID, "right chain"),        # earlier m != this k
     ("right", dict(vb_cols=8), abft.ERR_INVALID, "right chain"),
-    ("this", dict(dtype=1), abft.ERR_UNSUPPORTED, "ABFT_F64"),
+    ("right", dict(dtype=1, lda=80), abft.ERR_INVALID, "binary64 C"),
+    ("this", dict(dtype=1), abft.ERR_UNSUPPORTED, "ABFT_F64"),     # plain bf16 is not chained
+    ("this", dict(dtype=4), abft.ERR_INVALID, "binary32 C"),       # split product, binary64 C
 ])
 def test_chained_encode_validation_launches_nothing(lib, side, kw, status, msg):
     """Shape, grid and dtype mismatches of a chained encode are refused on the host."""

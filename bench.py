@@ -265,48 +265,6 @@ def run_reference(args, rank, world):
 
 
 # --------------------------------------------------------------------------- our arm
-def make_inputs(w, seed, dev):
-    """Device operands plus host copies (float64 values for the oracle sample)."""
-    import torch
-    if w.dtype == "f64":
-        A_np, B_np = wl.operands(w, seed)
-        return torch.from_numpy(A_np).to(dev), torch.from_numpy(B_np).to(dev), A_np, B_np
-    g = torch.Generator(device=dev).manual_seed(seed)
-    if w.dtype == "fp8":
-        return fp8_inputs(w, g, dev) + (None, None)
-    A = torch.randn(w.m, w.k, generator=g, device=dev)
-    B = torch.randn(w.k, w.n, generator=g, device=dev)
-    if w.dtype == "bf16":
-        A, B = A.to(torch.bfloat16), B.to(torch.bfloat16)
-    return A, B, None, None  # bf16x3 / bf16x6 take the binary32 values
-
-
-def fp8_quantize_dev(x, blk=128):
-    """The FP8 recipe on the device (input preparation): one power-of-two scale per
-    blk x blk block, 2^ceil(log2(max|x| / 448)), codes rounded to nearest-even E4M3."""
-    import torch
-    r, c = x.shape
-    amax = x.abs().reshape(r // blk, blk, c // blk, blk).amax(dim=(1, 3))
-    e = torch.where(amax > 0, torch.ceil(torch.log2(amax / 448.0)), torch.zeros_like(amax))
-    s = torch.exp2(e).float()
-    full = s.repeat_interleave(blk, 0).repeat_interleave(blk, 1)
-    q = (x / full).to(torch.float8_e4m3fn).view(torch.uint8)
-    return q.contiguous(), s.contiguous()
-
-
-def fp8_inputs(w, g, dev):
-    """(A codes, B codes, A scales, B scales): U[-1,1] x 10^U(-2,2) per row, quantised."""
-    import torch
-    out = []
-    for rows, cols in ((w.m, w.k), (w.k, w.n)):
-        x = torch.rand(rows, cols, generator=g, device=dev) * 2 - 1
-        x *= 10.0 ** (torch.rand(rows, 1, generator=g, device=dev) * 4 - 2)
-        out.append(fp8_quantize_dev(x))
-        del x
-    (qa, sa), (qb, sb) = out
-    return qa, qb, sa, sb
-
-
 def run_workload(w, args, dev, rank, world, secondary=False):
     """Measure one workload; returns the JSON dict (without the driver's wrapper keys)."""
     import torch
@@ -314,13 +272,14 @@ def run_workload(w, args, dev, rank, world, secondary=False):
 
     seed = mg.rank_seed(args.seed, rank)
     scales = {}
-    if w.dtype == "fp8":
-        import torch as _t
-        A, B, sa, sb = fp8_inputs(w, _t.Generator(device=dev).manual_seed(seed), dev)
-        A_np = B_np = None
-        scales = dict(a_scale=sa, b_scale=sb)
+    if w.dtype == "f64":
+        A_np, B_np = wl.operands(w, seed)
+        A, B = torch.from_numpy(A_np).to(dev), torch.from_numpy(B_np).to(dev)
     else:
-        A, B, A_np, B_np = make_inputs(w, seed, dev)
+        A_np = B_np = None
+        A, B, sa, sb = wl.device_operands(w, seed, dev)
+        if sa is not None:
+            scales = dict(a_scale=sa, b_scale=sb)
     lp = w.dtype != "f64"
     desc = abft.make_desc(w.m, w.n, w.k, w.dtype, w.vb_r, w.vb_c, w.p, w.q)
     L = abft.abft_workspace_layout(desc)

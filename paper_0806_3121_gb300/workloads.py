@@ -66,6 +66,43 @@ WORKLOADS = {w.name: w for w in (F64_512, F64_11264_GRID22, F64_4096_GRID8, BF16
                                  FP8_4096)}
 
 
+def fp8_quantize_dev(x, blk=128):
+    """The FP8 input recipe on the device: one power-of-two binary32 scale per blk x blk
+    block, 2^ceil(log2(max|x| / 448)), codes rounded to nearest-even E4M3.  Returns
+    (uint8 codes, float32 scales [rows/blk x cols/blk])."""
+    import torch
+    r, c = x.shape
+    amax = x.abs().reshape(r // blk, blk, c // blk, blk).amax(dim=(1, 3))
+    e = torch.where(amax > 0, torch.ceil(torch.log2(amax / 448.0)), torch.zeros_like(amax))
+    s = torch.exp2(e).float()
+    full = s.repeat_interleave(blk, 0).repeat_interleave(blk, 1)
+    q = (x / full).to(torch.float8_e4m3fn).view(torch.uint8)
+    return q.contiguous(), s.contiguous()
+
+
+def device_operands(w: Workload, seed: int, dev):
+    """Operands of a tensor-core workload drawn on the device (torch.Generator(seed)):
+    (A, B, a_scale, b_scale).  bf16: N(0,1) rounded to bf16; bf16x3 / bf16x6: the binary32
+    N(0,1) values; fp8: U[-1,1] x 10^U(-2,2) per row, quantised by fp8_quantize_dev
+    (scales returned, None otherwise)."""
+    import torch
+    g = torch.Generator(device=dev).manual_seed(seed)
+    if w.dtype == "fp8":
+        out = []
+        for rows, cols in ((w.m, w.k), (w.k, w.n)):
+            x = torch.rand(rows, cols, generator=g, device=dev) * 2 - 1
+            x *= 10.0 ** (torch.rand(rows, 1, generator=g, device=dev) * 4 - 2)
+            out.append(fp8_quantize_dev(x))
+            del x
+        (qa, sa), (qb, sb) = out
+        return qa, qb, sa, sb
+    A = torch.randn(w.m, w.k, generator=g, device=dev)
+    B = torch.randn(w.k, w.n, generator=g, device=dev)
+    if w.dtype == "bf16":
+        A, B = A.to(torch.bfloat16), B.to(torch.bfloat16)
+    return A, B, None, None
+
+
 @dataclass(frozen=True)
 class GroupWorkload:
     """Many independent bf16 problems: m, n, k uniform over multiples of `step` in

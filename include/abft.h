@@ -132,7 +132,10 @@ typedef struct {
 } abft_ws_layout;
 
 /* Size of the caller-owned device workspace for `desc`.  Returns 0 for an
- * invalid descriptor (abft_last_error() says why). */
+ * invalid descriptor (abft_last_error() says why).  Every call that takes a
+ * workspace requires its base to be 256-byte aligned (cudaMalloc and the
+ * PyTorch caching allocator give at least that) and returns ABFT_ERR_INVALID
+ * with nothing launched otherwise. */
 size_t abft_workspace_bytes(const abft_desc* desc);
 
 /* Fill *out (host) with the workspace layout.  ABFT_ERR_INVALID on a bad desc. */

@@ -24,6 +24,10 @@ abft_status fail(abft_status st, const char* fmt, ...) {
   return st;
 }
 
+// Workspaces must be 256-byte aligned (every region offset is a multiple of
+// 256 from the base: TMA maps, vector loads and stores rely on it).
+bool ws_misaligned(const void* ws) { return (reinterpret_cast<uintptr_t>(ws) & 255) != 0; }
+
 abft_status cuda_fail(cudaError_t e, const char* where) {
   return fail(ABFT_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
@@ -265,6 +269,7 @@ abft_status abft_encode(const abft_desc* desc, const void* A, const void* B, con
   if (st != ABFT_OK) return st;
   if (is_empty(P)) return ABFT_OK;
   if (!ws || (P.d.k > 0 && (!A || !B))) return fail(ABFT_ERR_INVALID, "NULL pointer");
+  if (ws_misaligned(ws)) return fail(ABFT_ERR_INVALID, "ws must be 256-byte aligned");
   if (P.d.dtype == ABFT_FP8_E4M3 && P.d.k > 0 && (!a_scale || !b_scale))
     return fail(ABFT_ERR_INVALID, "ABFT_FP8_E4M3 needs a_scale and b_scale");
   cudaError_t e = clear_carry(P, ws, static_cast<cudaStream_t>(stream));
@@ -316,6 +321,9 @@ abft_status abft_encode_chained(const abft_desc* desc, const void* A, const void
   }
   if (is_empty(P)) return ABFT_OK;
   if (!ws || (d.k > 0 && (!A || !B))) return fail(ABFT_ERR_INVALID, "NULL pointer");
+  if (ws_misaligned(ws) || (left_desc && ws_misaligned(left_ws)) ||
+      (right_desc && ws_misaligned(right_ws)))
+    return fail(ABFT_ERR_INVALID, "ws, left_ws and right_ws must be 256-byte aligned");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = clear_carry(P, ws, s);
   if (e == cudaSuccess) {
@@ -346,6 +354,7 @@ abft_status abft_encode_noalloc(const abft_desc* desc, const void* A, const void
                 need, static_encode_part_bytes());
   if (is_empty(P)) return ABFT_OK;
   if (!ws || (P.d.k > 0 && (!A || !B))) return fail(ABFT_ERR_INVALID, "NULL pointer");
+  if (ws_misaligned(ws)) return fail(ABFT_ERR_INVALID, "ws must be 256-byte aligned");
   cudaError_t e = clear_carry(P, ws, static_cast<cudaStream_t>(stream));
   if (e == cudaSuccess)
     e = launch_encode_f64_noalloc(P, static_cast<const double*>(A), static_cast<const double*>(B),
@@ -363,6 +372,7 @@ static abft_status gemm_common(const abft_desc* desc, const void* A, const void*
                P.d.dtype == ABFT_FP8_E4M3) && !ws) ||
       (P.d.k > 0 && (!A || !B)))
     return fail(ABFT_ERR_INVALID, "NULL pointer");
+  if (ws && ws_misaligned(ws)) return fail(ABFT_ERR_INVALID, "ws must be 256-byte aligned");
   cudaError_t e;
   if (P.d.dtype == ABFT_F64) {
     e = launch_gemm_f64(P, static_cast<const double*>(A), static_cast<const double*>(B),
@@ -432,6 +442,7 @@ abft_status abft_verify_correct(const abft_desc* desc, void* C, void* ws, int32_
   }
   if (is_empty(P)) return ABFT_OK;
   if (!C || !ws) return fail(ABFT_ERR_INVALID, "NULL pointer");
+  if (ws_misaligned(ws)) return fail(ABFT_ERR_INVALID, "ws must be 256-byte aligned");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Scratch S = scratch_view(P, ws);
   cudaError_t e = cudaMemsetAsync(S.cnt, 0, 256, s);
@@ -542,6 +553,7 @@ abft_status abft_recover_blocks(const abft_desc* desc, void* C, void* ws, const 
   }
   if (n_blocks == 0) return ABFT_OK;
   if (!C || !ws) return fail(ABFT_ERR_INVALID, "NULL pointer");
+  if (ws_misaligned(ws)) return fail(ABFT_ERR_INVALID, "ws must be 256-byte aligned");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Scratch S = scratch_view(P, ws);
   cudaError_t e = cudaMemsetAsync(S.cnt + kCntRecoverFlagged, 0, sizeof(int32_t), s);

@@ -54,6 +54,7 @@ constexpr int kThreads = 32 * (kWarpProdB + 1);
 static_assert(kEpiWarps == 4 || kEpiWarps == 8, "4 or 8 epilogue warps");
 static_assert((BN * 4) % kEpiWarps == 0 && kEpiCols % 32 == 0, "whole 32-column chunks");
 constexpr uint32_t A_BYTES = BM * BK * 2;          // 16 KiB
+constexpr uint32_t HALF_BYTES = 64 * BK * 2;       // one 64-row half of A: 8 KiB
 constexpr uint32_t B_BOX_BYTES = 64 * BK * 2;      // one 64-column box: 8 KiB
 constexpr uint32_t B_BYTES = BN * BK * 2;          // 32 KiB
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
@@ -61,6 +62,28 @@ constexpr uint32_t TMEM_COLS = 2 * BN;             // two accumulators
 constexpr uint32_t STG_BYTES = 32 * 32 * 4;        // one epilogue warp's staging block
 constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + kEpiWarps * STG_BYTES + 256;
 static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
+
+// Tile geometry.  Regular tiles are 128 x 256 with two accumulators that
+// alternate between tiles (the epilogue of one tile overlaps the MMAs of the
+// next).  Tall tiles are 256 x 256: two M = 128 MMAs per K step share the B
+// stage, one accumulator per 128-row half (both halves of TMEM), so the
+// operand bytes per flop fall by a third and the ring holds 3 stages of
+// 64 KiB; the epilogue no longer overlaps the next tile's MMAs, which pays
+// off for long K loops.
+template <bool kTall>
+struct Geo {
+  static constexpr int kBM = kTall ? 256 : BM;
+  static constexpr int kStages = kTall ? 3 : STAGES;
+  static constexpr uint32_t kABytes = (uint32_t)kBM * BK * 2;
+  static constexpr uint32_t kStageBytes = kABytes + B_BYTES;
+  static constexpr int kSlots = kTall ? 1 : 2;            // accumulator slots that alternate
+  static constexpr int kCols = kTall ? BN : kEpiCols;     // tile columns per epilogue warp
+  static constexpr size_t kSmem =
+      1024 + (size_t)kStages * kStageBytes + kEpiWarps * STG_BYTES + 256;
+};
+static_assert(Geo<false>::kSmem == SMEM_BYTES, "regular tiles");
+static_assert(Geo<true>::kSmem <= 232448, "shared memory per CTA (tall tiles)");
+static_assert(Geo<true>::kBM / 128 * BN <= (int)TMEM_COLS, "tall accumulators fit TMEM");
 
 // Tensor maps of the operands, per bf16 plane (the split dtypes have 2 or 3
 // planes; unused planes repeat plane 0).  The K loop runs nseg segments;
@@ -108,7 +131,7 @@ struct Tile {
 // and checksum rows, then the checksum columns over its data rows -- so every
 // checksum tile reuses the A or B panels its group already keeps in L2.
 __device__ __forceinline__ Tile decode_local(int64_t t, int64_t ntm, int64_t ntn, int64_t ntr,
-                                             int64_t ntc, int64_t GROUP_M) {
+                                             int64_t ntc, int64_t GROUP_M, int64_t bm) {
   const int64_t ngr = (ntm + GROUP_M - 1) / GROUP_M;
   int64_t off = 0;
   for (int64_t G = 0; G < ngr; ++G) {
@@ -123,16 +146,16 @@ __device__ __forceinline__ Tile decode_local(int64_t t, int64_t ntm, int64_t ntn
         T.col0 = col * BN;
         if (ri < gd) {
           T.kind = 0;
-          T.row0 = (G * GROUP_M + ri) * BM;
+          T.row0 = (G * GROUP_M + ri) * bm;
         } else {
           T.kind = 1;
-          T.row0 = (G + (ri - gd) * ngr) * BM;
+          T.row0 = (G + (ri - gd) * ngr) * bm;
         }
       } else {
         u -= part1;
         T.kind = 2;
         T.col0 = (u / gd) * BN;
-        T.row0 = (G * GROUP_M + u % gd) * BM;
+        T.row0 = (G * GROUP_M + u % gd) * bm;
       }
       return T;
     }
@@ -169,11 +192,12 @@ struct TileView {
   const CUtensorMap* mbC;
   int32_t rowD, rowC, colD, colC;
   int hsplit, hcnt, bsplit, nbox;
-  // one-copy loads: the whole A tile (maW: 128-row box at rowW) and four
+  // one-copy loads: A as nA128 128-row boxes (maW, rows rowW + 128 i) and
   // full B boxes (mbW: 3-D map at box index colW / 64); nullptr: per half / box
   const CUtensorMap* maW;     // (plane p at + p)
   const CUtensorMap* mbW;     // boxes [0, nW) in one copy; the rest per box
   int32_t rowW, colW, nW;
+  int nA128;
   float* C;                   // data x data, ld ldc, m x n
   int64_t ldc, m, n;
   float* E16;                 // checksum rows x data columns, ld n, R16 rows
@@ -191,7 +215,8 @@ struct TileView {
   int vb_r, vb_c, er, ec;
 };
 
-// One problem (abft_gemm).
+// One problem (abft_gemm), tiles of kBM rows (128 or 256).
+template <int kBM>
 struct SingleSched {
   const TcMaps* M;
   const TcArgs* a;
@@ -208,7 +233,7 @@ struct SingleSched {
   }
   __device__ __forceinline__ TileView view(int64_t t) const {
     const TcArgs& g = *a;
-    const Tile T = decode_local(t, g.ntm, g.ntn, g.ntr, g.ntc, g.group_m);
+    const Tile T = decode_local(t, g.ntm, g.ntn, g.ntr, g.ntc, g.group_m, kBM);
     TileView V;
     V.prob = 0;
     V.nkb = (g.k + BK - 1) / BK;
@@ -222,7 +247,8 @@ struct SingleSched {
     V.mbC = &M->bcs[0];
     V.rowD = V.rowC = (int32_t)T.row0;
     V.colD = V.colC = (int32_t)T.col0;
-    const int hrows = (int)clamp64(cdiv((T.kind == 1 ? g.R16 : g.m) - T.row0, 64), 1, 2);
+    const int hrows =
+        (int)clamp64(cdiv((T.kind == 1 ? g.R16 : g.m) - T.row0, 64), 1, kBM / 64);
     const int bcols = (int)clamp64(cdiv((T.kind == 2 ? g.C16 : g.n) - T.col0, 64), 1, 4);
     V.hsplit = T.kind == 1 ? 0 : hrows;
     V.hcnt = hrows;
@@ -231,7 +257,8 @@ struct SingleSched {
     V.maW = V.mbW = nullptr;
     V.rowW = (int32_t)T.row0;
     V.colW = (int32_t)T.col0;
-    if (hrows == 2) V.maW = T.kind == 1 ? &M->acs128[0] : &M->a128[0];
+    V.nA128 = hrows % 2 == 0 ? hrows / 2 : 0;  // whole 128-row boxes, else per half
+    if (V.nA128) V.maW = T.kind == 1 ? &M->acs128[0] : &M->a128[0];
     V.nW = 4;
     if (bcols == 4 && T.col0 + 256 <= ((T.kind == 2 ? g.C16 : g.n) / 64) * 64) {
       V.mbW = T.kind == 2 ? &M->bcs4[0] : &M->b4[0];
@@ -288,10 +315,11 @@ __device__ __forceinline__ void stage_row32(float* stg, int lane, const float (&
     rowp[j ^ (lane & 7)] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
 }
 
-// Element (r, c) of a staged block (conflict-free when the lanes read one
-// row's 32 columns).
-__device__ __forceinline__ float staged_at(const float* stg, int r, int c) {
-  return stg[r * 32 + (((c >> 2) ^ (r & 7)) << 2) + (c & 3)];
+// Columns 4 j .. 4 j + 3 of row r of a staged block (one 16-byte unit; a
+// warp reading four rows' eight units touches every bank four times, the
+// minimum for 512 bytes).
+__device__ __forceinline__ float4 staged4(const float* stg, int r, int j) {
+  return reinterpret_cast<const float4*>(stg + r * 32)[j ^ (r & 7)];
 }
 
 
@@ -299,29 +327,33 @@ __device__ __forceinline__ float staged_at(const float* stg, int r, int c) {
 // kPromote: the K loop runs in promotion groups whose accumulators the
 // epilogue sums in fp32 registers (a separate instantiation, so the register
 // accumulator of that path does not weigh on the single-group epilogue).
-template <bool kPromote, class Sched>
+template <bool kPromote, bool kTall, class Sched>
 __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wait_ns,
                                         int stall_test, const int32_t* inj_hdr,
                                         const InjectEntry* inj) {
+  using G = Geo<kTall>;
+  static_assert(!(kPromote && kTall), "promotion runs on regular tiles");
+  static_assert(!kTall || kEpiWarps == 8, "tall tiles: one epilogue warp per lane quarter and half");
+  constexpr int NS = G::kStages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
   uint64_t* bars =
-      reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + kEpiWarps * STG_BYTES);
+      reinterpret_cast<uint64_t*>(smem + NS * G::kStageBytes + kEpiWarps * STG_BYTES);
   // bars[0..S): full, [S..2S): empty, [2S..2S+2): tmem full, [2S+2..2S+4): tmem empty,
   // [2S+4]: drain
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 5);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto full = [&](int s) { return tc::smem_addr(&bars[s]); };
-  auto empty = [&](int s) { return tc::smem_addr(&bars[STAGES + s]); };
-  auto tfull = [&](int a) { return tc::smem_addr(&bars[2 * STAGES + a]); };
-  auto tempty = [&](int a) { return tc::smem_addr(&bars[2 * STAGES + 2 + a]); };
-  const uint32_t drain = tc::smem_addr(&bars[2 * STAGES + 4]);
+  auto empty = [&](int s) { return tc::smem_addr(&bars[NS + s]); };
+  auto tfull = [&](int a) { return tc::smem_addr(&bars[2 * NS + a]); };
+  auto tempty = [&](int a) { return tc::smem_addr(&bars[2 * NS + 2 + a]); };
+  const uint32_t drain = tc::smem_addr(&bars[2 * NS + 4]);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < NS; ++s) {
       tc::mbar_init(full(s), 2);  // the A and the B producer each arrive with their bytes
       tc::mbar_init(empty(s), 1);
     }
@@ -358,7 +390,7 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
         const TileView T = S.view(t);
         if (stall_test && t == 0) continue;  // nothing will fill these stages
         const int64_t nkb = T.nkb, nkt = T.nkb * T.nseg;
-        const uint32_t tx = pA ? (uint32_t)T.hcnt * (A_BYTES / 2) : (uint32_t)T.nbox * B_BOX_BYTES;
+        const uint32_t tx = pA ? (uint32_t)T.hcnt * HALF_BYTES : (uint32_t)T.nbox * B_BOX_BYTES;
         // a stage's MMAs take ~700 cycles: the per-stage bookkeeping is
         // incremental (no division per stage)
         int seg = 0, pa = (int)(T.seg_a & 3u), pb = (int)(T.seg_b & 3u);
@@ -366,33 +398,34 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
         for (int64_t kt = 0; kt < nkt; ++kt) {
           const int32_t kx = (int32_t)(kb * BK);
           if (!tc::wait(empty(s), ph ^ 1, abort)) break;
-          const uint32_t sa = tc::smem_addr(smem + s * STAGE_BYTES);
+          const uint32_t sa = tc::smem_addr(smem + s * G::kStageBytes);
           tc::mbar_arrive_expect_tx(full(s), tx);
           if (!pA) {
             // B: the full boxes in one 3-D copy, the rest (ragged, checksum) per box
             int b_first = 0;
             if (T.mbW) {
-              tc::tma_load_3d(sa + A_BYTES, T.mbW + pb, full(s), 0, kx, T.colW / 64);
+              tc::tma_load_3d(sa + G::kABytes, T.mbW + pb, full(s), 0, kx, T.colW / 64);
               b_first = T.nW;
             }
             for (int b = b_first; b < T.nbox; ++b) {
               const bool dat = b < T.bsplit;
               const CUtensorMap* mb = (dat ? T.mbD : T.mbC) + pb;
               const int32_t x = dat ? T.colD + 64 * b : T.colC + 64 * (b - T.bsplit);
-              tc::tma_load_2d(sa + A_BYTES + b * B_BOX_BYTES, mb, full(s), x, kx);
+              tc::tma_load_2d(sa + G::kABytes + b * B_BOX_BYTES, mb, full(s), x, kx);
             }
           } else if (T.maW) {
-            tc::tma_load_2d(sa, T.maW + pa, full(s), kx, T.rowW);
+            for (int i = 0; i < T.nA128; ++i)
+              tc::tma_load_2d(sa + i * (2 * HALF_BYTES), T.maW + pa, full(s), kx, T.rowW + 128 * i);
           } else {
             for (int h = 0; h < T.hcnt; ++h) {
               const bool dat = h < T.hsplit;
               const CUtensorMap* ma = (dat ? T.maD : T.maC) + pa;
               const int32_t y = dat ? T.rowD + 64 * h : T.rowC + 64 * (h - T.hsplit);
-              tc::tma_load_2d(sa + h * (A_BYTES / 2), ma, full(s), kx, y);
+              tc::tma_load_2d(sa + h * HALF_BYTES, ma, full(s), kx, y);
             }
           }
           ++issued;
-          if (++s == STAGES) { s = 0; ph ^= 1; }
+          if (++s == NS) { s = 0; ph ^= 1; }
           if (++kb == nkb) {  // next K segment: its planes of A and B
             kb = 0;
             ++seg;
@@ -402,8 +435,8 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
         }
       }
       // Do not leave copies in flight: wait for the last fills (bounded).
-      for (int q = 0; q < STAGES && issued > 0; ++q, --issued) {
-        if (--s < 0) { s = STAGES - 1; ph ^= 1; }
+      for (int q = 0; q < NS && issued > 0; ++q, --issued) {
+        if (--s < 0) { s = NS - 1; ph ^= 1; }
         const uint64_t t0 = tc::globaltimer();
         while (!tc::mbar_try_wait(full(s), ph) && tc::globaltimer() - t0 < tc::wait_limit_ns()) {
         }
@@ -427,27 +460,33 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
           if (!tc::wait(tempty(acc), aph ^ 1, abort)) { ok = false; break; }
           tc::fence_after_sync();
           const uint32_t d = tmem + acc * BN;
+          // tall tiles: the second 128-row half only when it holds rows
+          const int nmma = kTall && T.hcnt > 2 ? 2 : 1;
           for (int64_t kb = g0; kb < g1; ++kb) {
             if (!tc::wait(full(s), ph, abort)) { ok = false; break; }
             tc::fence_after_sync();
-            const uint32_t sa = tc::smem_addr(smem + s * STAGE_BYTES);
-            const uint32_t sb = sa + A_BYTES;
+            const uint32_t sa = tc::smem_addr(smem + s * G::kStageBytes);
+            const uint32_t sb = sa + G::kABytes;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
-              // A: K-major, 128-byte rows, 8-row groups 1024 B apart; a K step
-              // of 16 elements moves 32 B inside the swizzled row.
-              const uint64_t ad = tc::sdesc_sw128(sa + kk * 32, 16, 1024);
               // B: N-major, 64-column boxes 8 KiB apart, 8-row (K) groups
               // 1024 B apart; a K step of 16 rows moves 2 KiB.
               const uint64_t bd = tc::sdesc_sw128(sb + kk * 2048, B_BOX_BYTES, 1024);
-              tc::mma_f16(d, ad, bd, idesc, (kb > g0 || kk > 0) ? 1u : 0u);
+              for (int h2 = 0; h2 < nmma; ++h2) {
+                // A: K-major, 128-byte rows, 8-row groups 1024 B apart; a K
+                // step of 16 elements moves 32 B inside the swizzled row; the
+                // second 128-row half starts 16 KiB later and accumulates into
+                // the second TMEM accumulator
+                const uint64_t ad = tc::sdesc_sw128(sa + h2 * (2 * HALF_BYTES) + kk * 32, 16, 1024);
+                tc::mma_f16(d + h2 * BN, ad, bd, idesc, (kb > g0 || kk > 0) ? 1u : 0u);
+              }
             }
             tc::commit(empty(s));
-            if (++s == STAGES) { s = 0; ph ^= 1; }
+            if (++s == NS) { s = 0; ph ^= 1; }
           }
           if (!ok) break;
           tc::commit(tfull(acc));
-          if (++acc == 2) { acc = 0; aph ^= 1; }
+          if (++acc == G::kSlots) { acc = 0; aph ^= 1; }
         }
         if (!ok) break;
       }
@@ -464,8 +503,13 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
     // 32 x 32 chunk goes to this warp's staging block in shared memory (the
     // 128-byte-swizzled layout of a TMA box) and from there to global memory
     // by a TMA store; the fused column sums read the staged columns back.
-    const int q = warp & 3, half = q >> 1, c_lo = kEpiCols * ((warp - 2) >> 2);
-    float* stg = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + (warp - 2) * STG_BYTES);
+    // regular tiles: warp (w - 2) / 4 takes one 128-column half of the tile;
+    // tall tiles: it takes the accumulator of 128-row half (w - 2) / 4, all
+    // 256 columns
+    const int q = warp & 3, ta = kTall ? (warp - 2) >> 2 : 0;
+    const int half = 2 * ta + (q >> 1);  // this warp's 64-row half of the tile
+    const int c_lo = kTall ? 0 : kEpiCols * ((warp - 2) >> 2);
+    float* stg = reinterpret_cast<float*>(smem + NS * G::kStageBytes + (warp - 2) * STG_BYTES);
     const uint32_t stg_addr = tc::smem_addr(stg);
     const int ninj = (inj_hdr && inj_hdr[0] == kInjectMagic)
                          ? max(0, min(inj_hdr[1], kMaxInject)) : 0;
@@ -477,7 +521,7 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
       const int64_t nkt = T.nkb * T.nseg;
       const int64_t gsz = (kPromote && T.kpg > 0 && T.kpg < nkt) ? T.kpg : nkt;
       const int ncol = 64 * T.nbox;
-      const int c_hi = min(c_lo + kEpiCols, ncol);
+      const int c_hi = min(c_lo + G::kCols, ncol);
       // this warp's 32 rows: data rows, checksum rows or none
       const bool drow = half < T.hsplit, crow = !drow && half < T.hcnt;
       const int64_t rin = 32 * (q & 1) + lane;
@@ -493,16 +537,76 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
         for (int f = lane; f < ninj; f += 32) {
           const InjectEntry ie = inj[f];
           inj_hit |= ie.pad == T.prob && ie.row >= r0 && ie.row < r0 + 32 && ie.col >= c0 &&
-                     ie.col < c0 + kEpiCols;
+                     ie.col < c0 + G::kCols;
         }
         inj_hit = __any_sync(0xffffffffu, inj_hit);
       }
       const float scr = scalbnf(1.0f, -T.er), scc = scalbnf(1.0f, -T.ec);
       float racc_e = 0.f, racc_w = 0.f;
+      // verify-block and group offsets of the warp's rows and the tile's
+      // columns, once per tile (64-bit division is a software routine);
+      // the chunks use 32-bit offsets from them
+      const int g32 = (int)T.g;
+      const int rb0 = fused ? (int)(r0 % T.vb_r) + 1 : 1;  // weight of row r0
+      const int cm0 = fused ? (int)(T.colD % T.vb_c) : 0;
+      const int cg0 = fused ? (int)(T.colD % T.g) : 0;
+      const int64_t gi0 = fused ? T.colD / T.g : 0;
+      // Column partials of this warp's 32 rows (r0 ..) for the chunk at
+      // column col, from the staged block: lane = (row group g4 of 8 rows,
+      // 4-column unit c4), one 16-byte read per row, then the four row groups
+      // summed by two shuffles; weights of the rows in their verify block
+      // (the 32 rows never straddle one).  They run one chunk late, after the
+      // next chunk's TMEM load and row partials, so the staged block is read
+      // well after its writes were fenced for the TMA store.
+      bool cs_pend = false;
+      int64_t cs_col = 0;
+      auto colsum = [&](int64_t col) {
+        const int g4 = lane >> 3, c4 = lane & 7;
+        const int rb = rb0 + 8 * g4;
+        float se[4] = {0.f, 0.f, 0.f, 0.f}, sw[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float4 x = staged4(stg, 8 * g4 + i, c4);
+          const float w = (float)(rb + i) * scr;
+          se[0] += x.x; se[1] += x.y; se[2] += x.z; se[3] += x.w;
+          sw[0] = fmaf(w, x.x, sw[0]); sw[1] = fmaf(w, x.y, sw[1]);
+          sw[2] = fmaf(w, x.z, sw[2]); sw[3] = fmaf(w, x.w, sw[3]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          se[j] += __shfl_xor_sync(0xffffffffu, se[j], 8);
+          sw[j] += __shfl_xor_sync(0xffffffffu, sw[j], 8);
+          se[j] += __shfl_xor_sync(0xffffffffu, se[j], 16);
+          sw[j] += __shfl_xor_sync(0xffffffffu, sw[j], 16);
+        }
+        const int64_t c0 = col + 4 * c4;
+        if (g4 == 0 && r0 < T.m && c0 < T.n) {
+          float* o = T.obs_col + (r0 >> 5) * 2 * T.n + c0;
+          if (c0 + 4 <= T.n && (T.n & 3) == 0) {  // 16-byte aligned rows
+            *reinterpret_cast<float4*>(o) = make_float4(se[0], se[1], se[2], se[3]);
+            *reinterpret_cast<float4*>(o + T.n) = make_float4(sw[0], sw[1], sw[2], sw[3]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              if (c0 + j < T.n) {
+                o[j] = se[j];
+                o[T.n + j] = sw[j];
+              }
+          }
+        }
+      };
+      auto flush = [&]() {
+        if (cs_pend) {
+          cs_pend = false;
+          colsum(cs_col);
+        }
+      };
       // Stage v (lane = row) into this warp's block; with a store map, send
       // the block to (x, y) by one TMA store.  The block is reused only after
-      // the previous store has read it and every lane is past its reads.
+      // the pending column partials have read it, the previous store has
+      // read it and every lane is past its reads.
       auto stage = [&](const float (&v)[32], const CUtensorMap* map, int64_t x, int64_t y) {
+        flush();
         if (lane == 0) tc::bulk_wait_read0();
         __syncwarp();
         stage_row32(stg, lane, v);
@@ -533,16 +637,21 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
           if (fused && drow) {
             // row partials over the column group (weights restart per verify
             // block; a 32-column chunk never straddles one, a group never
-            // straddles the two column halves)
-            const int cm = (int)(col % T.vb_c) + 1;
+            // straddles the two column halves): sum_u (cm + u) scc v[u] as
+            // scc (cm sum_u v[u] + sum_u u v[u])
+            const int cm = (cm0 + c) % T.vb_c + 1;
+            float s0 = 0.f, s1 = 0.f;
 #pragma unroll
             for (int u = 0; u < 32; ++u) {
-              racc_e += v[u];
-              racc_w = fmaf((float)(cm + u) * scc, v[u], racc_w);
+              s0 += v[u];
+              s1 = fmaf((float)u, v[u], s1);
             }
-            if (((col + 32) % T.g) == 0 || c + 32 == ndcol || col + 32 >= T.n) {
+            racc_e += s0;
+            racc_w = fmaf((float)cm * scc, s0, fmaf(scc, s1, racc_w));
+            const int cg = cg0 + c;  // column offset from the start of colD's group
+            if (((cg + 32) % g32) == 0 || c + 32 == ndcol || col + 32 >= T.n) {
               if (rvalid) {
-                float* o = T.obs_row + (row * T.ngrp + (int)(col / T.g)) * 2;
+                float* o = T.obs_row + (row * T.ngrp + gi0 + cg / g32) * 2;
                 o[0] = racc_e;
                 o[1] = racc_w;
               }
@@ -556,21 +665,11 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
           if (map || colsums) stage(v, map, col, r0);
           if (!map && rvalid) store_row32(drow ? T.C : T.E16, drow ? T.ldc : T.n, row, col, T.n, v);
           if (colsums) {
-            // column partials of this warp's 32 rows (lane = column) from the
-            // staged block; weights of the rows in their verify block (the 32
-            // rows never straddle one)
-            const int rb = (int)(r0 % T.vb_r) + 1;
-            float se = 0.f, sw = 0.f;
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const float x = staged_at(stg, i, lane);
-              se += x;
-              sw = fmaf((float)(rb + i) * scr, x, sw);
-            }
-            if (r0 < T.m && col + lane < T.n) {
-              float* o = T.obs_col + (r0 >> 5) * 2 * T.n + col + lane;
-              o[0] = se;
-              o[T.n] = sw;
+            if constexpr (kPromote) {
+              colsum(col);  // the promoted epilogue has no registers to spare
+            } else {        // read back from the staged block one chunk later
+              cs_pend = true;
+              cs_col = col;
             }
           }
         } else if (drow && r0 < T.m) {
@@ -588,7 +687,7 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
         // accumulator is released after the last read
         if (!tc::wait(tfull(acc), aph, abort)) break;
         tc::fence_after_sync();
-        const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
+        const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (acc + ta) * BN;
         const int nch = (c_hi - c_lo + 31) / 32;
         for (int ci = 0; ci < nch; ++ci) {
           float v[32];
@@ -597,15 +696,16 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(tempty(acc));
-            if (++acc == 2) { acc = 0; aph ^= 1; }
+            if (++acc == G::kSlots) { acc = 0; aph ^= 1; }
           }
           chunk(c_lo + 32 * ci, v);
         }
+        flush();
         if (nch <= 0) {  // nothing of this tile in this warp's half
           tc::fence_before_sync();
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(tempty(acc));
-          if (++acc == 2) { acc = 0; aph ^= 1; }
+          if (++acc == G::kSlots) { acc = 0; aph ^= 1; }
         }
       } else if constexpr (kPromote) {
         // promotion groups: this warp's part of the tile summed over the
@@ -639,6 +739,7 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
 #pragma unroll
         for (int ci = 0; ci < kEpiChunks; ++ci)
           if (c_lo + 32 * ci < c_hi) chunk(c_lo + 32 * ci, accr[ci]);
+        flush();
       }
     }
     // every TMA store of this warp has completed before the kernel ends
@@ -656,11 +757,11 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
   }
 }
 
-template <bool kPromote>
+template <bool kPromote, bool kTall>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_bf16(const __grid_constant__ TcMaps M, const TcArgs g) {
-  const SingleSched S{&M, &g};
-  tc_body<kPromote>(S, g.status, g.wait_ns, g.stall_test, g.inj_hdr, g.inj);
+  const SingleSched<Geo<kTall>::kBM> S{&M, &g};
+  tc_body<kPromote, kTall>(S, g.status, g.wait_ns, g.stall_test, g.inj_hdr, g.inj);
 }
 
 // Many problems (grouped product).  The flattened tile list is a table of
@@ -705,6 +806,7 @@ struct GroupSched {
     V.colD = 64 * b0;
     V.colC = 64 * max(0, b0 - nbd);
     V.maW = V.mbW = nullptr;
+    V.nA128 = 1;
     if (V.hsplit == 2) {
       V.maW = &Mp.a128;
       V.rowW = V.rowD;
@@ -749,7 +851,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                    int checksums, int* status, uint64_t wait_ns, const int32_t* inj_hdr,
                    const InjectEntry* inj, int kpg) {
   const GroupSched S{probs, maps, tiles, t_total, checksums != 0, kpg};
-  tc_body<false>(S, status, wait_ns, 0, inj_hdr, inj);
+  tc_body<false, false>(S, status, wait_ns, 0, inj_hdr, inj);
 }
 
 // ---- host side
@@ -845,12 +947,24 @@ int promote_ksteps(int dtype) {
 }
 
 // Raster group height of the single-problem tile order: tiles run column by
-// column over groups of this many tile rows, so consecutive CTAs share the
-// group's A panels and one B panel in L2.  ABFT_GROUP_M overrides the default.
-int raster_group_rows() {
+// column over groups of this many tile rows (2048 rows), so consecutive CTAs
+// share the group's A panels and one B panel in L2.  ABFT_GROUP_M overrides
+// the default.
+int raster_group_rows(int bm) {
   const char* env = getenv("ABFT_GROUP_M");
   if (env && *env) return std::max(1, atoi(env));
-  return 16;
+  return 2048 / bm;
+}
+
+// Tall (256-row) tiles for products without promotion whose K loop is long
+// enough (at least 32 k-steps) that the tile's epilogue, which no longer
+// overlaps the next tile's MMAs, is a small share of it.  ABFT_TALL_TILES=0
+// or 1 forces the choice.
+bool use_tall(int64_t m, int64_t nkt, int kpg) {
+  if (kpg > 0) return false;
+  const char* env = getenv("ABFT_TALL_TILES");
+  if (env && *env) return env[0] == '1';
+  return m > BM && nkt >= 32;
 }
 
 int num_sms() {
@@ -920,9 +1034,12 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
   g.nseg = op.nseg;
   g.seg_a = op.seg_a;
   g.seg_b = op.seg_b;
-  g.ntm = (int)cdiv(d.m, BM);
+  g.kpg = promote_ksteps(d.dtype);
+  const bool tall = use_tall(d.m, cdiv(d.k, BK) * op.nseg, g.kpg);
+  const int bm = tall ? Geo<true>::kBM : BM;
+  g.ntm = (int)cdiv(d.m, bm);
   g.ntn = (int)cdiv(d.n, BN);
-  g.ntr = checksums ? (int)cdiv(R16, BM) : 0;
+  g.ntr = checksums ? (int)cdiv(R16, bm) : 0;
   g.ntc = checksums ? (int)cdiv(C16, BN) : 0;
   g.t_data = (int64_t)g.ntm * g.ntn;
   g.t_total = g.t_data + (int64_t)g.ntr * g.ntn + (int64_t)g.ntm * g.ntc;
@@ -951,15 +1068,16 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
   // the call reports ABFT_ERR_TIMEOUT.  Off unless the variable is set.
   const char* stall = getenv("ABFT_TEST_STALL_PRODUCER");
   g.stall_test = stall && stall[0] == '1';
-  g.kpg = promote_ksteps(d.dtype);
-  g.group_m = raster_group_rows();
+  g.group_m = raster_group_rows(bm);
   g.wait_ns = g.stall_test ? 200000000ull : tc::kWaitLimitNs;
-  const auto kernel = g.kpg > 0 ? k_gemm_bf16<true> : k_gemm_bf16<false>;
-  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  const auto kernel = g.kpg > 0 ? k_gemm_bf16<true, false>
+                                : (tall ? k_gemm_bf16<false, true> : k_gemm_bf16<false, false>);
+  const size_t smem = tall ? Geo<true>::kSmem : Geo<false>::kSmem;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = (int)std::min<int64_t>(g.t_total, num_sms());
   if (grid == 0) return cudaSuccess;
-  kernel<<<grid, kThreads, SMEM_BYTES, st>>>(M, g);
+  kernel<<<grid, kThreads, smem, st>>>(M, g);
   count_launches(1);
   return cudaGetLastError();
 }

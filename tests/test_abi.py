@@ -204,3 +204,19 @@ def test_group_other_dtypes_unsupported(lib):
     with pytest.raises(abft.AbftError) as e:
         abft.abft_group_create([_fake_problem(64, 64, 64)], "f64")
     assert e.value.status == abft.ERR_UNSUPPORTED
+
+
+def test_misaligned_workspace_is_refused(lib):
+    """Every call that takes a workspace checks its 256-byte alignment before launching."""
+    d = abft.make_desc(64, 64, 64, "f64", 32, 32)
+    ok, bad = ct.c_void_p(1 << 20), ct.c_void_p((1 << 20) + 8)
+    st = lib.abft_encode(ct.byref(d), ok, ok, None, None, bad, None)
+    assert st == abft.ERR_INVALID and "256-byte" in lib.abft_last_error().decode()
+    st = lib.abft_gemm(ct.byref(d), ok, ok, None, None, ok, bad, None)
+    assert st == abft.ERR_INVALID and "256-byte" in lib.abft_last_error().decode()
+    n = ct.c_int32(0)
+    st = lib.abft_verify_correct(ct.byref(d), ok, bad, 1, None, 0, None, 0, ct.byref(n), None)
+    assert st == abft.ERR_INVALID and "256-byte" in lib.abft_last_error().decode()
+    left = abft.make_desc(64, 64, 16, "f64", 32, 32)
+    st = lib.abft_encode_chained(ct.byref(d), ok, ok, ct.byref(left), bad, None, None, ok, None)
+    assert st == abft.ERR_INVALID and "256-byte" in lib.abft_last_error().decode()

@@ -168,6 +168,13 @@ def bit_flips(seed: int, m: int, n: int, count: int, bits: int = 64, stream: int
     """
     g = rng(seed, stream)
     out, used = [], set(tuple(b) for b in avoid_blocks)
+    if distinct_blocks is not None:
+        nb = -(-m // distinct_blocks[0]) * -(-n // distinct_blocks[1])
+        free = nb - len({b for b in used
+                         if 0 <= b[0] < -(-m // distinct_blocks[0])
+                         and 0 <= b[1] < -(-n // distinct_blocks[1])})
+        if count > free:
+            raise ValueError(f"{count} flips in distinct blocks, but only {free} blocks are free")
     while len(out) < count:
         i, j, b = int(g.integers(0, m)), int(g.integers(0, n)), int(g.integers(0, bits))
         if distinct_blocks is not None:

@@ -390,3 +390,40 @@ def test_outputs_with_any_row_pitch(m, n, k, vbr, vbc, ldc):
     assert [(a, b) for a, b, _ in positions(rep)] == sorted(pos)
     assert positions(rep) == positions(orep)
     assert rel_fro(Cbuf.cpu().numpy().astype(np.float64)[:, :n], ref) <= 4 * np.sqrt(k) * U32
+
+
+# --------------------------------------------------------------------------- tile heights
+@pytest.mark.parametrize("tall", ["0", "1"])
+@pytest.mark.parametrize("shape", [(200, 300, 136, 128, 64), (640, 700, 520, 128, 256),
+                                   (320, 256, 2048, 256, 256), (1000, 264, 72, 128, 32)])
+def test_tile_heights_agree(shape, tall, monkeypatch):
+    """128-row and 256-row tiles (ABFT_TALL_TILES forces the choice): ragged rows, tiles
+    holding one, two or three 64-row halves, checksum-row tiles of 256 rows; products,
+    expected checksums and fused-verify decisions against the oracle, and the plain
+    product equal to the ABFT product's data bit for bit."""
+    monkeypatch.setenv("ABFT_TALL_TILES", tall)
+    m, n, k, vbr, vbc = shape
+    r = Run(m, n, k, vbr, vbc, seed=61)
+    enc = oracle.Encoded(r.A64, r.B64, vbr, vbc, dtype="bf16")
+    C = r.C.cpu().numpy().astype(np.float64)
+    check_fp32_product(C, r.A64, r.B64, oracle.gemm(r.A64, r.B64))
+    check_fp32_product(r.E(), np.abs(enc.acs), r.B64, enc.E, extra_rel=2.0 ** -17 + 256 * U32)
+    check_fp32_product(r.F(), r.A64, np.abs(enc.bcs), enc.F, extra_rel=2.0 ** -17 + 256 * U32)
+    for reread in (0, 1):
+        st, rep, nrep = abft.abft_verify_correct(r.desc, r.C, r.ws, reread_C=reread)
+        assert st == abft.OK and nrep == 0
+    plain = Run(m, n, k, vbr, vbc, seed=61, plain=True)
+    assert torch.equal(plain.C, r.C)
+    blocks = (vbr, max(vbc, 64))
+    nflip = min(3, -(-m // blocks[0]) * -(-n // blocks[1]))
+    pos = [(p[0], p[1]) for p in wl.bit_flips(62, m, n, nflip, bits=32, distinct_blocks=blocks)]
+    flips = graded_bits(C, pos)
+    abft.abft_set_epilogue_faults(r.desc, r.ws, flips)
+    abft.abft_gemm(r.desc, r.A, r.B, r.C, r.ws)
+    abft.abft_set_epilogue_faults(r.desc, r.ws, [])
+    Cf = r.C.cpu().numpy().astype(np.float64)
+    st, rep, nrep = abft.abft_verify_correct(r.desc, r.C, r.ws, reread_C=0)
+    ost, orep, oC, on = enc.verify_correct(Cf)
+    assert st == abft.OK and ost == oracle.ST_OK
+    assert [(a, b) for a, b, _ in positions(rep)] == sorted(pos)
+    assert positions(rep) == positions(orep)

@@ -1,6 +1,7 @@
 """The seeded input recipes (no method arithmetic): shapes, distributions, fault draws and
 the FP8 E4M3 block quantiser the FP8 workload feeds to both the CUDA path and the oracle."""
 import numpy as np
+import pytest
 
 import oracle
 from paper_0806_3121_gb300 import workloads as wl
@@ -40,3 +41,14 @@ def test_group_shapes_and_faulty_instances():
     f = wl.faulty_instances(0, 4096, 0.01)
     assert len(f) == 41 and f == sorted(set(f)) and max(f) < 4096
     assert wl.group_shapes(0, w) == shapes                   # seeded
+
+
+def test_bit_flips_refuses_more_flips_than_free_blocks():
+    """Flips in distinct blocks: a request the block grid cannot hold is refused at once
+    (it would otherwise redraw forever)."""
+    with pytest.raises(ValueError):
+        wl.bit_flips(1, 320, 256, 3, distinct_blocks=(256, 256))
+    with pytest.raises(ValueError):
+        wl.bit_flips(1, 512, 512, 4, distinct_blocks=(256, 256), avoid_blocks=[(0, 0)])
+    got = wl.bit_flips(1, 320, 256, 2, distinct_blocks=(256, 256))
+    assert sorted(i // 256 for i, _, _ in got) == [0, 1]

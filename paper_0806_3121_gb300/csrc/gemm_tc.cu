@@ -4,14 +4,16 @@
 // Persistent, warp-specialised kernel, one CTA per SM:
 //   warp 0      TMA producer of A: one 128-row box (or two 64-row halves) per
 //               stage, K-major, 128-byte swizzle, into a 4-stage shared-memory
-//               ring guarded by mbarriers.
+//               ring guarded by mbarriers (256-row tiles: two 128-row boxes,
+//               3 stages; see Geo).
 //   warp 10     TMA producer of B: one 3-D copy of up to four 64-column boxes
 //               (N-major) per stage, the ragged / checksum boxes one by one; the
 //               two producers arrive on a stage's full barrier with their own
 //               bytes (one issuing thread could not keep up with the MMAs).
 //   warp 1      MMA issuer: one thread issues tcgen05.mma (M=128, N=64 x boxes,
-//               K=16) into one of two TMEM accumulators (2 x 256 columns) and
-//               frees ring stages and accumulators with tcgen05.commit.
+//               K=16) into one of two TMEM accumulators (2 x 256 columns; a
+//               256-row tile uses both, one per 128-row half) and frees ring
+//               stages and accumulators with tcgen05.commit.
 //   warps 2-9   epilogue: tcgen05.ld of the accumulator (a warp reads its
 //               32-lane quarter of TMEM and one 128-column half of the tile),
 //               each 32 x 32 chunk staged in shared memory and written to C or

@@ -266,6 +266,42 @@ def run_reference(args, rank, world):
 
 
 # --------------------------------------------------------------------------- our arm
+def library_context(w, A, B, scales, dev, useful, reps=None):
+    """cuBLAS on the same operands, for context (not a baseline of the method): FP64
+    DGEMM, bf16 GEMM (bf16 output), binary32 SGEMM with TF32 off for the split dtypes (their
+    accuracy class), FP8 torch._scaled_mm with unit per-tensor scales.  Timed with CUDA
+    events on torch's current stream after one warm-up; any library error is reported, not
+    raised."""
+    import torch
+    reps = reps or (1 if w.dtype == "f64" else 3)  # an FP64 DGEMM of 11264^3 takes seconds
+    try:
+        if w.dtype == "fp8":
+            a = A.view(torch.float8_e4m3fn)
+            b = B.view(torch.float8_e4m3fn).t().contiguous().t()
+            one = torch.ones((), dtype=torch.float32, device=dev)
+            op, fn = "torch._scaled_mm e4m3 (unit per-tensor scales, fp32 out)", \
+                lambda: torch._scaled_mm(a, b, one, one, out_dtype=torch.float32)
+        elif w.dtype in ("bf16x3", "bf16x6"):
+            torch.backends.cuda.matmul.allow_tf32 = False
+            op, fn = "torch.matmul fp32 (SGEMM, TF32 off)", lambda: torch.matmul(A, B)
+        else:
+            op, fn = f"torch.matmul {w.dtype} ({'bf16' if w.dtype == 'bf16' else 'fp64'} out)", \
+                lambda: torch.matmul(A, B)
+        out = fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        del out
+        ms = e0.elapsed_time(e1) / reps
+        return {"op": op, "ms": ms, "tflops": useful / (ms * 1e-3) / 1e12}
+    except Exception as exc:  # context only: the line stands without it
+        return {"unavailable": f"{type(exc).__name__}: {exc}"[:200]}
+
+
 def run_workload(w, args, dev, rank, world, secondary=False):
     """Measure one workload; returns the JSON dict (without the driver's wrapper keys)."""
     import torch
@@ -486,6 +522,7 @@ def run_workload(w, args, dev, rank, world, secondary=False):
                      "encode": encode_ms},
         "useful_frac_of_peak": (useful / (step_ms * 1e-3) / 1e12) / peak,
         "roofline": roof, "gpu_launches": launches, "clocks": clocks, "e2e": e2e,
+        "library_context": library_context(w, A, B, scales, dev, useful),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not secondary:
         if A_np is None:
@@ -658,6 +695,7 @@ def run_grouped(w, args, dev, rank, world, secondary=False):
                      "frac": achieved / peak,
                      "traffic": TRAFFIC_BYTES.get(w.name),
                      "algorithmic_flops_per_launch": useful + cs_flops},
+        "library_context": {"unavailable": "torch has no grouped GEMM of uneven shapes"},
         "gpu_launches": launches, "clocks": clocks, "e2e": None,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not secondary:
@@ -689,7 +727,7 @@ def run_ours(args, rank, world):
     w = wl.WORKLOADS[args.workload]
     secondary = {}
     keys = ("value", "unit", "ms_per_step", "overhead_pct", "times_ms", "useful_frac_of_peak",
-            "roofline", "gpu_launches", "clocks", "config")
+            "roofline", "gpu_launches", "clocks", "config", "library_context")
     if w.name == "f64_11264_grid22" and not args.no_secondary:
         # the tensor-core workloads first: the FP64 run is a minute of full-power load
         for name in ("bf16_16384", "bf16x3_16384", "bf16x6_16384", "fp8_16384"):

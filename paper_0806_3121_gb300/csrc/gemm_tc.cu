@@ -15,11 +15,12 @@
 //               256-row tile uses both, one per 128-row half) and frees ring
 //               stages and accumulators with tcgen05.commit.
 //   warps 2-9   epilogue: tcgen05.ld of the accumulator (a warp reads its
-//               32-lane quarter of TMEM and one 128-column half of the tile),
+//               32-lane quarter of TMEM and one 128-column half of the tile;
+//               on 256-row tiles one 128-row accumulator, all 256 columns),
 //               each 32 x 32 chunk staged in shared memory and written to C or
 //               the checksum outputs by a TMA store, the fused observed sums,
 //               then release of the accumulator so the next tile's MMAs
-//               overlap this tile's epilogue.
+//               overlap this tile's epilogue (on 128-row tiles).
 // Single problem: data tiles (grouped raster for L2 reuse), checksum-row tiles
 // (acs x B -> E16) and checksum-column tiles (A x bcs -> F16); the corner is
 // not computed.  Grouped problems: each problem's checksum halves / boxes

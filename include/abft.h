@@ -30,6 +30,23 @@
  *  - Erasure grid: grid_p x grid_q blocks (m % grid_p == 0, n % grid_q == 0).
  *    A also gains m/grid_p block checksum rows S_A = sum_I A_I, so the product
  *    carries S = sum_I C_I, enough to rebuild one lost block per block column.
+ *  - Workspaces (ws) are 256-byte aligned device buffers (see
+ *    abft_workspace_bytes).
+ *
+ * Environment variables read at each launch (tuning and testing only; the
+ * defaults are the measured best choices):
+ *  - ABFT_PROMOTE_KSTEPS  tensor-core k-steps (64 wide) accumulated before the
+ *                         epilogue adds a partial into fp32 registers (0: none;
+ *                         default 8 for ABFT_BF16X6, 16 for ABFT_BF16X3, 0 else).
+ *  - ABFT_TALL_TILES      0 / 1: 128- or 256-row tiles for products without
+ *                         promotion (default: 256 rows when m > 128 and the K
+ *                         loop has at least 32 k-steps).
+ *  - ABFT_GROUP_M         raster group height in tile rows of single products
+ *                         (default 2048 rows).
+ *  - ABFT_TUNE_CACHE      file of grouped-product tunings (abft_group_autotune).
+ *  - ABFT_TEST_STALL_PRODUCER  1: the tensor-core product's producer skips its
+ *                         first tile so its bounded waits run out (tests of
+ *                         ABFT_ERR_TIMEOUT; never set in production).
  */
 #ifndef ABFT_H
 #define ABFT_H

@@ -395,7 +395,8 @@ def test_outputs_with_any_row_pitch(m, n, k, vbr, vbc, ldc):
 # --------------------------------------------------------------------------- tile heights
 @pytest.mark.parametrize("tall", ["0", "1"])
 @pytest.mark.parametrize("shape", [(200, 300, 136, 128, 64), (640, 700, 520, 128, 256),
-                                   (320, 256, 2048, 256, 256), (1000, 264, 72, 128, 32)])
+                                   (320, 256, 2048, 256, 256), (1000, 264, 72, 128, 32),
+                                   (400, 320, 200, 128, 64)])  # last tall tile: 3 halves
 def test_tile_heights_agree(shape, tall, monkeypatch):
     """128-row and 256-row tiles (ABFT_TALL_TILES forces the choice): ragged rows, tiles
     holding one, two or three 64-row halves, checksum-row tiles of 256 rows; products,

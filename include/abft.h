@@ -273,7 +273,11 @@ abft_status abft_gemm_plain(const abft_desc* desc, const void* A, const void* B,
  * max_reports entries sorted by (row, col, kind); *n_reports (host) gets the
  * full count.  SYNCHRONISES `stream`.  Returns ABFT_OK, or
  * ABFT_ERR_UNCORRECTABLE when a flagged line could not be fixed (those
- * elements are left unmodified). */
+ * elements are left unmodified).  A NaN or Inf in A or B makes a whole row
+ * (column) of C and the checksums covering it non-finite: each such element
+ * is reported ABFT_KIND_NONFINITE_CORRECTED (recomputed, still non-finite),
+ * its lines ABFT_KIND_UNCORRECTABLE, and the status is
+ * ABFT_ERR_UNCORRECTABLE; the finite elements are left as they are. */
 abft_status abft_verify_correct(const abft_desc* desc, void* C, void* ws, int32_t reread_C,
                                 const int32_t* erased_blocks, int32_t n_erased, abft_fault* report,
                                 int32_t max_reports, int32_t* n_reports, void* stream);

@@ -428,3 +428,32 @@ def test_tile_heights_agree(shape, tall, monkeypatch):
     assert st == abft.OK and ost == oracle.ST_OK
     assert [(a, b) for a, b, _ in positions(rep)] == sorted(pos)
     assert positions(rep) == positions(orep)
+
+
+@pytest.mark.parametrize("reread", [0, 1])
+def test_non_finite_operand_decided_like_oracle(reread):
+    """A NaN in a bf16 operand: the non-finite row of C is located element by element,
+    recomputed to non-finite values and its lines reported uncorrectable, as the oracle
+    decides on the GPU's C, from the fused sums or from a re-read of C."""
+    m, n, k = 256, 384, 192
+    bits_a = wl.bf16_bits(wl.operand((m, k), "normal", 7, 1))
+    bits_a[37, 11] = 0x7FC0  # bf16 quiet NaN
+    bits_b = wl.bf16_bits(wl.operand((k, n), "normal", 7, 2))
+    A = torch.from_numpy(bits_a.view(np.int16)).view(torch.bfloat16).cuda()
+    B = torch.from_numpy(bits_b.view(np.int16)).view(torch.bfloat16).cuda()
+    A64, B64 = oracle.bf16_to_f64(bits_a), oracle.bf16_to_f64(bits_b)
+    desc = abft.make_desc(m, n, k, "bf16", 128, 128)
+    ws = torch.zeros(abft.abft_workspace_bytes(desc), dtype=torch.uint8, device="cuda")
+    C = torch.empty((m, n), dtype=torch.float32, device="cuda")
+    abft.abft_encode(desc, A, B, ws)
+    abft.abft_gemm(desc, A, B, C, ws)
+    torch.cuda.synchronize()
+    Cg = C.cpu().numpy().astype(np.float64)
+    assert np.isnan(Cg[37]).all() and np.isfinite(np.delete(Cg, 37, axis=0)).all()
+    enc = oracle.Encoded(A64, B64, 128, 128, dtype="bf16")
+    st, rep, nrep = abft.abft_verify_correct(desc, C, ws, reread_C=reread, max_reports=4096)
+    ost, orep, oC, on = enc.verify_correct(Cg, max_reports=4096)
+    assert st == abft.ERR_UNCORRECTABLE and ost == oracle.ST_UNCORRECTABLE
+    key = lambda e: (e["row"], e["col"], e["kind"])
+    assert nrep == on and sorted(map(key, rep)) == sorted(map(key, orep))
+    assert np.array_equal(np.delete(C.cpu().numpy(), 37, axis=0), np.delete(Cg, 37, axis=0))

@@ -363,3 +363,33 @@ def test_more_erasures_than_block_checksums_refused():
     assert np.isnan(r.C.cpu().numpy()[0:192, 64:128]).all()      # nothing launched
     st, ents = abft.abft_recover_blocks(r.desc, r.C, r.ws, [(0, 1), (1, 1)])
     assert st == abft.ERR_UNCORRECTABLE                            # block (2, 1) still NaN
+
+
+@pytest.mark.parametrize("where", ["A", "B"])
+@pytest.mark.parametrize("value", [np.nan, np.inf])
+def test_non_finite_operand_decided_like_oracle(where, value):
+    """A NaN or Inf in an operand (a degenerate input of the method): a whole row (A) or
+    column (B) of C is non-finite and so are the checksums that cover it.  Every such
+    element is located by the non-finite scan and recomputed -- to a non-finite value --
+    and its lines stay flagged: the verify reports them uncorrectable, exactly as the
+    oracle does, and leaves every finite element alone."""
+    g = wl.rng(5)
+    m, n, k = 256, 192, 128
+    A, B = g.standard_normal((m, k)), g.standard_normal((k, n))
+    if where == "A":
+        A[37, 11] = value
+    else:
+        B[5, 100] = value
+    r = Run(A, B, 64, 64)
+    enc = oracle.Encoded(A, B, 64, 64)
+    C = r.C.cpu().numpy()
+    with np.errstate(invalid="ignore", over="ignore"):
+        ref = oracle.gemm(A, B)
+    assert np.array_equal(np.isfinite(C), np.isfinite(ref))
+    st, rep, nrep = abft.abft_verify_correct(r.desc, r.C, r.ws, max_reports=4096)
+    ost, orep, oC, on = enc.verify_correct(C, max_reports=4096)
+    assert st == abft.ERR_UNCORRECTABLE and ost == oracle.ST_UNCORRECTABLE
+    key = lambda e: (e["row"], e["col"], e["kind"])
+    assert nrep == on and sorted(map(key, rep)) == sorted(map(key, orep))
+    fin = np.isfinite(ref)
+    assert np.array_equal(r.C.cpu().numpy()[fin], C[fin])

@@ -139,7 +139,8 @@ class ClockSampler:
 def oracle_pipeline(A, B, w, blocks: int, seed: int):
     """The CPU oracle's whole path on a leading sub-problem of the workload (full k): for a
     grid workload the leading blocks x blocks blocks with one erasure, else a
-    (blocks*128)^2 corner; three flips.  Returns (useful flops, seconds)."""
+    (blocks*128)^2 corner; three flips.  Returns (useful flops, seconds, corner size, seconds
+    of the product C = A B alone)."""
     import oracle
     if w.p:
         bs = w.m // w.p
@@ -152,7 +153,9 @@ def oracle_pipeline(A, B, w, blocks: int, seed: int):
     As, Bs = np.ascontiguousarray(A[:ms]), np.ascontiguousarray(B[:, :ns])
     t0 = time.perf_counter()
     enc = oracle.Encoded(As, Bs, w.vb_r, w.vb_c, p, q, dtype=w.dtype)
+    tg = time.perf_counter()
     C = oracle.gemm(As, Bs)
+    dt_gemm = time.perf_counter() - tg
     flips = wl.bit_flips(seed, ms, ns, 3, distinct_blocks=(bs, bs))
     erased = []
     if p:
@@ -166,7 +169,7 @@ def oracle_pipeline(A, B, w, blocks: int, seed: int):
     for bi, bj in erased:
         enc.recover_block(C, bi, bj)
     dt = time.perf_counter() - t0
-    return 2.0 * ms * ns * w.k, dt, ms
+    return 2.0 * ms * ns * w.k, dt, ms, dt_gemm
 
 
 def oracle_group_pipeline(w, seed: int, budget_flops: float = 6e10):
@@ -196,10 +199,10 @@ def oracle_group_pipeline(w, seed: int, budget_flops: float = 6e10):
 
 
 def cpu_baseline(A, B, w, blocks, seed):
-    flops, dt, ms = oracle_pipeline(A, B, w, blocks, seed)
+    flops, dt, ms, dt_gemm = oracle_pipeline(A, B, w, blocks, seed)
     what = "erased block + 3 flips" if w.p else "3 flips"
     return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
-            "kind": "oracle",
+            "kind": "oracle", "gemm_only_value": flops / dt_gemm / 1e12,
             "sample": f"oracle encode+gemm+verify/correct{'+recover' if w.p else ''} on a "
                       f"{ms}x{ms} corner of the workload with full k={w.k}, {what}; gemm "
                       f"loop OpenMP over all cores, the rest serial; {dt:.1f} s"}
@@ -246,7 +249,7 @@ def run_reference(args, rank, world):
         oracle_pipeline(A, B, w, blocks, args.seed)
     tot_f, tot_t = 0.0, 0.0
     for _ in range(args.steps):
-        f, t, ms = oracle_pipeline(A, B, w, blocks, args.seed)
+        f, t, ms, _ = oracle_pipeline(A, B, w, blocks, args.seed)
         tot_f += f
         tot_t += t
     v = tot_f / tot_t / 1e12

@@ -167,8 +167,9 @@ abft_status abft_workspace_layout(const abft_desc* desc, abft_ws_layout* out);
  * elements); the scales must be powers of two, so that every dequantised value
  * e4m3(q) * scale is exact in bf16 -- the encode writes those values as bf16
  * operand planes into ws, forms the checksums from them and the product reads
- * them (a value that is not exact makes the next abft_verify_correct return
- * ABFT_ERR_INVALID).  Asynchronous. */
+ * them (a value that is not exact sets a status word of this workspace, and
+ * abft_verify_correct on it returns ABFT_ERR_INVALID until the next encode).
+ * Asynchronous. */
 abft_status abft_encode(const abft_desc* desc, const void* A, const void* B, const void* a_scale,
                         const void* b_scale, void* ws, void* stream);
 
@@ -184,9 +185,11 @@ abft_status abft_encode(const abft_desc* desc, const void* A, const void* B, con
  * library, which each device that loads the library keeps until the process
  * exits.  It allocates nothing.  Problems whose partial sums need more than
  * 8 MiB (about 8 * (k/256 * (n + 4*nvr) + k/64 * 4*nvc) bytes) return
- * ABFT_ERR_INVALID with nothing launched.  The first call on each device
- * looks up the array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture.  All calls share the one array, so
+ * ABFT_ERR_INVALID with nothing launched.  Every call looks up the array's
+ * device address on the current device (cudaGetSymbolAddress; nothing is
+ * cached, so a device reset leaves no stale address); the first call on a
+ * device may load the library's device code, so make it before any stream
+ * capture.  All calls share the one array, so
  * calls that overlap on the GPU (different streams, threads) race and must be
  * serialised by the caller.  ABFT_F64 only.  Asynchronous. */
 abft_status abft_encode_noalloc(const abft_desc* desc, const void* A, const void* B,
@@ -251,7 +254,9 @@ abft_status abft_set_epilogue_faults(const abft_desc* desc, void* ws, const int6
 /* The same GEMM kernel with no checksum tiles: C = A B only.  This is the
  * checksum-free baseline the ABFT overhead is measured against.  ws may be
  * NULL except for ABFT_BF16X3, ABFT_BF16X6 and ABFT_FP8_E4M3, whose products read the bf16
- * operand planes a preceding abft_encode wrote into ws.  Asynchronous. */
+ * operand planes a preceding abft_encode wrote into ws.  A bounded wait that
+ * gives up is recorded in ws's status word (as for abft_gemm); without ws it
+ * is not reported.  Asynchronous. */
 abft_status abft_gemm_plain(const abft_desc* desc, const void* A, const void* B,
                             const void* a_scale, const void* b_scale, void* C, void* ws,
                             void* stream);
@@ -273,7 +278,10 @@ abft_status abft_gemm_plain(const abft_desc* desc, const void* A, const void* B,
  * max_reports entries sorted by (row, col, kind); *n_reports (host) gets the
  * full count.  SYNCHRONISES `stream`.  Returns ABFT_OK, or
  * ABFT_ERR_UNCORRECTABLE when a flagged line could not be fixed (those
- * elements are left unmodified).  A NaN or Inf in A or B makes a whole row
+ * elements are left unmodified).  ABFT_ERR_TIMEOUT, with C left as it is,
+ * when the last tensor-core product on this workspace gave up a bounded
+ * wait (each workspace keeps that status of its own last product, so
+ * problems running at the same time never see each other's).  A NaN or Inf in A or B makes a whole row
  * (column) of C and the checksums covering it non-finite: each such element
  * is reported ABFT_KIND_NONFINITE_CORRECTED (recomputed, still non-finite),
  * its lines ABFT_KIND_UNCORRECTABLE, and the status is

@@ -188,11 +188,16 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
 
 bool is_empty(const Plan& P) { return P.d.m == 0 || P.d.n == 0; }
 
-// A freshly encoded product carries no checksum deviation.
+// A freshly encoded product carries no checksum deviation, and (tensor-core
+// dtypes) its workspace's status words start clear: no product has timed out
+// on it and no operand has been found inexact.
 cudaError_t clear_carry(const Plan& P, void* ws, cudaStream_t st) {
   char* w = static_cast<char*>(ws);
   cudaError_t e = cudaMemsetAsync(w + P.L.car_a, 0, sizeof(double) * 2 * P.nvr, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(w + P.L.car_b, 0, sizeof(double) * 2 * P.nvc, st);
+  if (e == cudaSuccess && P.d.dtype != ABFT_F64)
+    e = cudaMemsetAsync(w + P.L.scratch + sizeof(int32_t) * kCntTimeout, 0,
+                        sizeof(int32_t) * (kCntFp8Inexact - kCntTimeout + 1), st);
   return e;
 }
 
@@ -445,7 +450,7 @@ abft_status abft_verify_correct(const abft_desc* desc, void* C, void* ws, int32_
   if (ws_misaligned(ws)) return fail(ABFT_ERR_INVALID, "ws must be 256-byte aligned");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Scratch S = scratch_view(P, ws);
-  cudaError_t e = cudaMemsetAsync(S.cnt, 0, 256, s);
+  cudaError_t e = cudaMemsetAsync(S.cnt, 0, sizeof(int32_t) * kNumCleared, s);
   if (e != cudaSuccess) return cuda_fail(e, "abft_verify_correct memset");
   e = launch_verify(P, C, ws, er, reread_C != 0 || !P.fused, s);
   if (e != cudaSuccess) return cuda_fail(e, "abft_verify_correct launch");
@@ -453,22 +458,15 @@ abft_status abft_verify_correct(const abft_desc* desc, void* C, void* ws, int32_
   e = cudaMemcpyAsync(cnt, S.cnt, sizeof cnt, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "abft_verify_correct");
-  if (P.d.dtype != ABFT_F64) {
-    bool timed_out = false;
-    e = consume_tc_timeout(s, &timed_out);
-    if (e != cudaSuccess) return cuda_fail(e, "abft_verify_correct");
-    if (timed_out)
-      return fail(ABFT_ERR_TIMEOUT, "a tensor-core product gave up waiting (bounded wait)");
-  }
-  if (P.d.dtype == ABFT_FP8_E4M3) {
-    bool inexact = false;
-    e = consume_fp8_inexact(s, &inexact);
-    if (e != cudaSuccess) return cuda_fail(e, "abft_verify_correct");
-    if (inexact)
-      return fail(ABFT_ERR_INVALID,
-                  "an e4m3 value times its block scale is not exact in bf16: the block scales "
-                  "must be powers of two (and the operands finite)");
-  }
+  // status words of this workspace's last product and last encode
+  if (P.d.dtype != ABFT_F64 && cnt[kCntTimeout])
+    return fail(ABFT_ERR_TIMEOUT,
+                "the tensor-core product on this workspace gave up waiting (bounded wait); C and "
+                "its checksums are incomplete and were not corrected");
+  if (P.d.dtype == ABFT_FP8_E4M3 && cnt[kCntFp8Inexact])
+    return fail(ABFT_ERR_INVALID,
+                "an e4m3 value times its block scale is not exact in bf16: the block scales "
+                "must be powers of two (and the operands finite)");
   const int total = cnt[kCntReport];
   const int stored = std::min(total, kCapReport);
   std::vector<abft_fault> rep((size_t)stored);
@@ -567,11 +565,16 @@ abft_status abft_recover_blocks(const abft_desc* desc, void* C, void* ws, const 
       return fail(ABFT_ERR_INVALID, "singular block-checksum system in block column %d", bj);
     e = launch_recover(P, C, ws, bj, rows, t, minv, s);
   }
-  int32_t nfl = 0;
+  int32_t cnt[kNumCounters] = {};
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&nfl, S.cnt + kCntRecoverFlagged, sizeof nfl, cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(cnt, S.cnt, sizeof cnt, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "abft_recover_blocks");
+  if (P.d.dtype != ABFT_F64 && cnt[kCntTimeout])
+    return fail(ABFT_ERR_TIMEOUT,
+                "the tensor-core product on this workspace gave up waiting (bounded wait); its "
+                "block checksums are incomplete and nothing was rebuilt");
+  const int32_t nfl = cnt[kCntRecoverFlagged];
   if (report)
     for (int u = 0; u < n_blocks; ++u) {
       abft_fault f{};

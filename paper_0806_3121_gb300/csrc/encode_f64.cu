@@ -2,7 +2,6 @@
 // of Eq. (1)).  All kernels stream A or B once per quantity with coalesced
 // loads; reductions along the long dimension are two-stage (per-chunk
 // partials, then an ordered sum) so the result does not depend on scheduling.
-#include <mutex>
 
 #include "internal.cuh"
 
@@ -268,94 +267,12 @@ __global__ void __launch_bounds__(kThreads) k_carry(const double* __restrict__ n
 
 }  // namespace
 
-cudaError_t launch_encode_f64(const Plan& P, const double* A, const double* B, void* ws,
-                              cudaStream_t st) {
-  const abft_desc& d = P.d;
-  char* w = static_cast<char*>(ws);
-  double* acs = reinterpret_cast<double*>(w + P.L.acs);
-  double* bcs = reinterpret_cast<double*>(w + P.L.bcs);
-  double* nArow = reinterpret_cast<double*>(w + P.L.nArow);
-  double* nAblk = reinterpret_cast<double*>(w + P.L.nAblk);
-  double* nBcol = reinterpret_cast<double*>(w + P.L.nBcol);
-  double* nBblk = reinterpret_cast<double*>(w + P.L.nBblk);
-  Scratch S = scratch_view(P, ws);
-  const int nchA = (int)cdiv(d.k, kThreads);
-  const int nchB = (int)cdiv(d.k, kRowsPerWarpB);
-  const int nchC = (int)cdiv(d.k, kThreads);
-  double* partA = S.part;
-  double* partB = partA + 4 * P.nvr * nchA;
-  double* partC = partB + 4 * P.nvc * nchB;
-
-  auto gy = [](int64_t v) { return (unsigned)(v < 65535 ? v : 65535); };
-  if (d.k == 0) {  // empty inner dimension: all checksums and norms are zero
-    cudaMemsetAsync(nArow, 0, sizeof(double) * d.m, st);
-    cudaMemsetAsync(nAblk, 0, sizeof(double) * 4 * P.nvr, st);
-    cudaMemsetAsync(nBcol, 0, sizeof(double) * d.n, st);
-    cudaMemsetAsync(nBblk, 0, sizeof(double) * 4 * P.nvc, st);
-    return cudaGetLastError();
-  }
-  count_launches(P.bs > 0 ? 8 : 7);
-  k_encA_cols<<<dim3((unsigned)nchA, gy(P.nvr)), kThreads, 0, st>>>(
-      A, d.lda, d.m, d.k, d.vb_rows, P.er, acs, partA, nchA);
-  if (P.bs > 0)
-    k_encA_block<<<dim3((unsigned)cdiv(d.k, kThreads), gy(P.f * P.bs)), kThreads, 0, st>>>(
-        A, d.lda, d.k, d.grid_p, P.bs, P.f, acs + 2 * P.nvr * d.k);
-  k_row_norms<<<(unsigned)cdiv(d.m * 32, kThreads), kThreads, 0, st>>>(A, d.lda, d.m, d.k, nArow);
-  k_encB_rows<<<dim3((unsigned)cdiv(nchB, kThreads / 32), gy(P.nvc)), kThreads, 0, st>>>(
-      B, d.ldb, d.k, d.n, d.vb_cols, P.ec, bcs, P.Cc, partB, nchB);
-  k_col_sq<<<dim3((unsigned)cdiv(d.n, kThreads), gy(nchC)), kThreads, 0, st>>>(
-      B, d.ldb, d.k, d.n, partC);
-  k_sum_sqrt<<<(unsigned)cdiv(d.n, 128), 128, 0, st>>>(partC, d.n, nchC, 1, d.n, nBcol);
-  k_finalize_blk<<<(unsigned)cdiv(P.nvr, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA,
-                                                             nchA, nAblk);
-  k_finalize_blk<<<(unsigned)cdiv(P.nvc, 128), 128, 0, st>>>(nBcol, d.n, d.vb_cols, P.ec, partB,
-                                                             nchB, nBblk);
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Encode without a workspace scratch region (abft_encode_noalloc).
-//
-// The encode's per-chunk partial sums normally live in the scratch part of the
-// caller's workspace.  For callers that cannot allocate device memory, this
-// variant keeps them in the file-scope array below instead.  The array is
-// created by the CUDA runtime when this module is loaded on a device and stays
-// resident on every device that loads the library until the process exits.
-// Every call shares it; every slot a call reads is first written by the same
-// call, so nothing needs clearing, but calls that overlap on the GPU race on
-// it.
-constexpr size_t kStaticEncodePartBytes = size_t(8) << 20;  // 8 MiB
-static __device__ __align__(256) double g_encode_part[kStaticEncodePartBytes / sizeof(double)];
-
-size_t static_encode_part_bytes() { return kStaticEncodePartBytes; }
-
 namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_part_mu;
-double* g_part_addr[kMaxDevices] = {};
-}  // namespace
 
-// Device address of g_encode_part on the current device.  In host code the
-// array's name is only a stand-in, so the address is resolved once per device
-// with cudaGetSymbolAddress and cached.
-static cudaError_t encode_part_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_part_mu);
-  if (!g_part_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_encode_part);
-    if (e != cudaSuccess) return e;
-    g_part_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_part_addr[dev];
-  return cudaSuccess;
-}
-
-cudaError_t launch_encode_f64_noalloc(const Plan& P, const double* A, const double* B, void* ws,
-                                      cudaStream_t st) {
+// The encode's launch sequence, with its per-chunk partial sums at `part`
+// (the workspace scratch, or the static array of abft_encode_noalloc).
+cudaError_t encode_f64_into(const Plan& P, const double* A, const double* B, void* ws,
+                            double* part, cudaStream_t st) {
   const abft_desc& d = P.d;
   char* w = static_cast<char*>(ws);
   double* acs = reinterpret_cast<double*>(w + P.L.acs);
@@ -364,9 +281,6 @@ cudaError_t launch_encode_f64_noalloc(const Plan& P, const double* A, const doub
   double* nAblk = reinterpret_cast<double*>(w + P.L.nAblk);
   double* nBcol = reinterpret_cast<double*>(w + P.L.nBcol);
   double* nBblk = reinterpret_cast<double*>(w + P.L.nBblk);
-  double* part = nullptr;
-  cudaError_t e = encode_part_address(&part);
-  if (e != cudaSuccess) return e;
   const int nchA = (int)cdiv(d.k, kThreads);
   const int nchB = (int)cdiv(d.k, kRowsPerWarpB);
   const int nchC = (int)cdiv(d.k, kThreads);
@@ -399,6 +313,41 @@ cudaError_t launch_encode_f64_noalloc(const Plan& P, const double* A, const doub
   k_finalize_blk<<<(unsigned)cdiv(P.nvc, 128), 128, 0, st>>>(nBcol, d.n, d.vb_cols, P.ec, partB,
                                                              nchB, nBblk);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_encode_f64(const Plan& P, const double* A, const double* B, void* ws,
+                              cudaStream_t st) {
+  return encode_f64_into(P, A, B, ws, scratch_view(P, ws).part, st);
+}
+
+// ---------------------------------------------------------------------------
+// Encode without a workspace scratch region (abft_encode_noalloc).
+//
+// The encode's per-chunk partial sums normally live in the scratch part of the
+// caller's workspace.  For callers that cannot allocate device memory, this
+// variant keeps them in the file-scope array below instead.  The array is
+// created by the CUDA runtime when this module is loaded on a device and stays
+// resident on every device that loads the library until the process exits.
+// Every call shares it; every slot a call reads is first written by the same
+// call, so nothing needs clearing, but calls that overlap on the GPU race on
+// it.
+constexpr size_t kStaticEncodePartBytes = size_t(8) << 20;  // 8 MiB
+static __device__ __align__(256) double g_encode_part[kStaticEncodePartBytes / sizeof(double)];
+
+size_t static_encode_part_bytes() { return kStaticEncodePartBytes; }
+
+// In host code the array's name is only a stand-in, not a device address:
+// the address on the current device is looked up with cudaGetSymbolAddress on
+// every call (it is not cached, so a device reset or a new context cannot
+// leave a stale pointer behind).
+cudaError_t launch_encode_f64_noalloc(const Plan& P, const double* A, const double* B, void* ws,
+                                      cudaStream_t st) {
+  void* part = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&part, g_encode_part);
+  if (e != cudaSuccess) return e;
+  return encode_f64_into(P, A, B, ws, static_cast<double*>(part), st);
 }
 
 // Deviation bounds of the checksums carried out of an earlier product PL

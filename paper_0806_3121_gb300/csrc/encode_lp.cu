@@ -1308,20 +1308,6 @@ size_t lp_part_bytes(const Plan& P) {
          sizeof(float) * (P.d.m * cdiv(k, 256) + cdiv(k, kRowsPerCtaB) * P.d.n) + 64;
 }
 
-// Device flag of the FP8 dequantisation (an operand value not exact in bf16).
-__device__ int g_fp8_inexact = 0;
-
-cudaError_t consume_fp8_inexact(cudaStream_t st, bool* inexact) {
-  int* flag = nullptr;
-  cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&flag), g_fp8_inexact);
-  int v = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&v, flag, sizeof v, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e == cudaSuccess && v) e = cudaMemsetAsync(flag, 0, sizeof(int), st);
-  *inexact = v != 0;
-  return e;
-}
-
 cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, const void* a_scale,
                              const void* b_scale, void* ws, cudaStream_t st) {
   const abft_desc& d = P.d;
@@ -1404,8 +1390,9 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, cons
   Fp8Src fa{}, fb{};
   int nlaunch = 0;
   if (d.dtype == ABFT_FP8_E4M3) {
-    int* flag = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&flag), g_fp8_inexact);
+    // this workspace's status word of its last encode (read by the verify)
+    int* flag = S.cnt + kCntFp8Inexact;
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     auto* pa = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_a);
     auto* pb = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_b);
@@ -1614,7 +1601,13 @@ cudaError_t launch_gemm_lp(const Plan& P, const void* A, const void* B, float* C
     op.ldb = d.ldb;
     op.nseg = 1;
   }
-  cudaError_t e = launch_gemm_bf16(P, op, C, ws, checksums, st);
+  // a timeout goes to this workspace's status word (read by the verify); a
+  // checksum-free product without a workspace has no report to carry it
+  int* status = nullptr;
+  cudaError_t e = ws ? cudaSuccess : tc_timeout_fallback(&status);
+  if (e != cudaSuccess) return e;
+  if (ws) status = scratch_view(P, ws).cnt + kCntTimeout;
+  e = launch_gemm_bf16(P, op, C, ws, checksums, status, st);
   if (e != cudaSuccess || !checksums) return e;
   const int npc = (d.dtype == ABFT_BF16X3 || d.dtype == ABFT_BF16X6) ? 1 : 2;
   const float* E16 = reinterpret_cast<const float*>(w + P.L.E16);

@@ -25,7 +25,7 @@
 // (acs x B -> E16) and checksum-column tiles (A x bcs -> F16); the corner is
 // not computed.  Grouped problems: each problem's checksum halves / boxes
 // follow its data halves / boxes and share the last data tiles.  Every barrier wait is bounded; a timeout sets a device flag
-// the host reports as ABFT_ERR_TIMEOUT, and the kernel still drains its
+// of the workspace that the host reports as ABFT_ERR_TIMEOUT, and the kernel still drains its
 // copies and MMAs and frees TMEM before returning.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -984,27 +984,15 @@ int num_sms() {
 
 }  // namespace
 
-// Device flag set by a tensor-core product whose bounded waits gave up.
-__device__ int g_tc_timeout = 0;
+// Timeout word of checksum-free products run without a workspace.
+__device__ int g_tc_timeout_fallback = 0;
 
-cudaError_t tc_timeout_flag(int** dev_ptr) {
-  return cudaGetSymbolAddress(reinterpret_cast<void**>(dev_ptr), g_tc_timeout);
-}
-
-// Reads and clears the timeout flag, stream-ordered (synchronises `st`).
-cudaError_t consume_tc_timeout(cudaStream_t st, bool* timed_out) {
-  int* flag = nullptr;
-  cudaError_t e = tc_timeout_flag(&flag);
-  int v = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&v, flag, sizeof v, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e == cudaSuccess && v) e = cudaMemsetAsync(flag, 0, sizeof(int), st);
-  *timed_out = v != 0;
-  return e;
+cudaError_t tc_timeout_fallback(int** dev_ptr) {
+  return cudaGetSymbolAddress(reinterpret_cast<void**>(dev_ptr), g_tc_timeout_fallback);
 }
 
 cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void* ws,
-                             bool checksums, cudaStream_t st) {
+                             bool checksums, int* status, cudaStream_t st) {
   cudaError_t e = get_encoder();
   if (e != cudaSuccess) return e;
   const abft_desc& d = P.d;
@@ -1064,8 +1052,7 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
     g.inj_hdr = reinterpret_cast<const int32_t*>(w + P.L.inject);
     g.inj = reinterpret_cast<const InjectEntry*>(w + P.L.inject + 16);
   }
-  e = tc_timeout_flag(&g.status);
-  if (e != cudaSuccess) return e;
+  g.status = status;
   // Test hook for the bounded waits: ABFT_TEST_STALL_PRODUCER=1 makes the
   // producer skip the first tile, so its MMA wait runs out (after 0.2 s) and
   // the call reports ABFT_ERR_TIMEOUT.  Off unless the variable is set.
@@ -1080,6 +1067,8 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
   if (e != cudaSuccess) return e;
   const int grid = (int)std::min<int64_t>(g.t_total, num_sms());
   if (grid == 0) return cudaSuccess;
+  e = cudaMemsetAsync(status, 0, sizeof(int), st);  // the status of this product
+  if (e != cudaSuccess) return e;
   kernel<<<grid, kThreads, smem, st>>>(M, g);
   count_launches(1);
   return cudaGetLastError();
@@ -1109,12 +1098,12 @@ cudaError_t make_bf16_map_boxes(CUtensorMap* map, const void* ptr, int64_t rows,
 }
 
 cudaError_t launch_group_gemm(const GroupDev& G, bool checksums, cudaStream_t st) {
-  int* status = nullptr;
-  cudaError_t e = tc_timeout_flag(&status);
-  if (e != cudaSuccess) return e;
+  int* status = G.cnt + kCntTimeout;  // the group's own status word
   const int64_t total = checksums ? G.ntiles_cs : G.ntiles_plain;
   const int grid = (int)std::min<int64_t>(total, num_sms());
   if (grid == 0) return cudaSuccess;
+  const cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
   k_gemm_grouped<<<grid, kThreads, SMEM_BYTES, st>>>(
       G.probs, G.maps, checksums ? G.tiles_cs : G.tiles_plain, total, checksums ? 1 : 0, status,
       tc::kWaitLimitNs, checksums ? G.inj_hdr : nullptr, G.inj, 0);

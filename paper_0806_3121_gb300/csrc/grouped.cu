@@ -457,11 +457,10 @@ abft_status abft_group_report(abft_group g, abft_fault* report, int32_t max_repo
   cudaError_t e = cudaMemcpyAsync(cnt, g->dev.cnt, sizeof cnt, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "abft_group_report");
-  bool timed_out = false;
-  e = consume_tc_timeout(st, &timed_out);
-  if (e != cudaSuccess) return cuda_fail(e, "abft_group_report");
-  if (timed_out)
-    return fail(ABFT_ERR_TIMEOUT, "a tensor-core product gave up waiting (bounded wait)");
+  if (cnt[kCntTimeout])  // the group's status word of its last product
+    return fail(ABFT_ERR_TIMEOUT,
+                "the group's product gave up waiting (bounded wait); results are incomplete and "
+                "were not corrected");
   const int total = cnt[kCntReport];
   const int stored = std::min(total, kCapReport);
   std::vector<abft_fault> rep((size_t)stored);

@@ -31,7 +31,14 @@ __host__ __device__ inline double block_coef(int l, int I, int p) {
 }
 constexpr int kMaxInject = 256;    // armed epilogue fault injections
 
-// Counter slots in the scratch region.
+// Counter slots in the scratch region.  Slots below kNumCleared are cleared
+// by every verify call; the status words after them belong to the workspace
+// and describe its last encode / product (they are read, not cleared, by the
+// verify and the group report):
+//   kCntTimeout     set by a tensor-core product whose bounded waits gave up
+//                   (cleared when the next product on this workspace starts);
+//   kCntFp8Inexact  set by an FP8 encode that met a value not exact in bf16
+//                   (cleared when the next encode on this workspace starts).
 enum Counter : int {
   kCntColFlags = 0,
   kCntRowFlags = 1,
@@ -39,6 +46,9 @@ enum Counter : int {
   kCntOverflow = 3,
   kCntRecoverFlagged = 4,
   kCntCands = 5,
+  kNumCleared = 8,
+  kCntTimeout = 8,
+  kCntFp8Inexact = 9,
   kNumCounters = 16
 };
 
@@ -141,8 +151,6 @@ cudaError_t launch_gemm_f64(const Plan& P, const double* A, const double* B, dou
 // followed by the fold of E16/F16 into the binary64 E/F.
 cudaError_t launch_encode_lp(const Plan& P, const void* A, const void* B, const void* a_scale,
                              const void* b_scale, void* ws, cudaStream_t st);
-// Reads and clears the FP8 dequantisation flag (synchronises `st`).
-cudaError_t consume_fp8_inexact(cudaStream_t st, bool* inexact);
 size_t lp_part_bytes(const Plan& P);
 cudaError_t launch_gemm_lp(const Plan& P, const void* A, const void* B, float* C, void* ws,
                            bool checksums, cudaStream_t st);
@@ -156,9 +164,13 @@ struct TcOperands {
   int nseg;
   uint32_t seg_a, seg_b;
 };
+// status: the word a timeout is recorded in (cleared on `st` before the
+// launch).
 cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void* ws,
-                             bool checksums, cudaStream_t st);
-cudaError_t tc_timeout_flag(int** dev_ptr);
+                             bool checksums, int* status, cudaStream_t st);
+// Process-wide word that receives the timeout of a checksum-free product run
+// without a workspace (nothing reads it: such a call has no report).
+cudaError_t tc_timeout_fallback(int** dev_ptr);
 
 // ---- grouped products (many independent bf16 problems, one launch per step)
 // Verify blocks: 128 rows (one product tile row) x 256 columns.
@@ -251,7 +263,6 @@ cudaError_t prepare_group_kernels();
 // Arms `count` epilogue injections (count = 0 disarms) in the region at hdr.
 cudaError_t launch_set_inject_raw(int32_t* hdr, const InjectEntry* entries, int count,
                                   cudaStream_t st);
-cudaError_t consume_tc_timeout(cudaStream_t st, bool* timed_out);
 cudaError_t launch_verify(const Plan& P, void* C, void* ws, const Erased& er, bool reread,
                           cudaStream_t st);
 cudaError_t launch_set_inject(const Plan& P, void* ws, const int64_t* rows, const int64_t* cols,

@@ -44,6 +44,10 @@ struct CheckArgs {
   int32_t* cnt;
   abft_fault* report;
   CandEntry* cand;
+  // status word of the workspace's last tensor-core product (nullptr for
+  // binary64): when that product timed out, C is incomplete and nothing is
+  // located or corrected
+  const int32_t* timeout;
 };
 
 template <typename TC>
@@ -546,6 +550,7 @@ __device__ __forceinline__ void locate_body(const Pol& A, int32_t* cnt, const Fl
 
 template <typename TC>
 __global__ void __launch_bounds__(kLocThreads, 1) k_locate_correct(const CheckArgs a) {
+  if (a.timeout && *a.timeout) return;  // an incomplete product: write nothing
   const SinglePol<TC> A{a};
   locate_body(A, a.cnt, a.colf, a.rowf, a.cand, a.report);
 }
@@ -744,6 +749,7 @@ __global__ void __launch_bounds__(kLocThreads, 1) k_grp_locate(const GProb* prob
                                                                const FlagEntry* rowf,
                                                                CandEntry* cand,
                                                                abft_fault* report) {
+  if (cnt[kCntTimeout]) return;  // the group's product timed out: write nothing
   const GroupPol A{probs, s};
   locate_body(A, cnt, colf, rowf, cand, report);
 }
@@ -763,9 +769,11 @@ struct RecoverSet {
 template <typename TC>
 __global__ void __launch_bounds__(kThreads) k_recover(TC* C, int64_t ldc, const double* S,
                                                       int64_t n, int p, int64_t bs, int64_t bc,
-                                                      int bj, const RecoverSet rs) {
+                                                      int bj, const RecoverSet rs,
+                                                      const int32_t* timeout) {
   const int64_t jj = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (jj >= bc) return;
+  if (timeout && *timeout) return;  // block checksums of an incomplete product
   const int64_t j = (int64_t)bj * bc + jj;
   int e = 0;
   while ((1 << e) <= p) ++e;
@@ -845,6 +853,7 @@ CheckArgs make_args(const Plan& P, void* C, void* ws) {
   a.nvr = P.nvr; a.nvc = P.nvc; a.Cc = P.Cc; a.bs = P.bs; a.bc = P.bc;
   a.s = P.s; a.f1c = P.f1_col; a.f2c = P.f2_col; a.f1r = P.f1_row; a.f2r = P.f2_row;
   a.colf = S.colf; a.rowf = S.rowf; a.cnt = S.cnt; a.report = S.report; a.cand = S.cand;
+  a.timeout = P.d.dtype == ABFT_F64 ? nullptr : S.cnt + kCntTimeout;
   return a;
 }
 
@@ -880,7 +889,7 @@ cudaError_t recover_t(const Plan& P, void* C, void* ws, int bj, const int* rows,
   for (int u = 0; u < t; ++u) rs.rows[u] = rows[u];
   for (int x = 0; x < t * t; ++x) rs.minv[x] = minv[x];
   k_recover<TC><<<dim3((unsigned)cdiv(P.bc, kThreads), gy(P.bs)), kThreads, 0, st>>>(
-      static_cast<TC*>(C), P.d.ldc, S, P.d.n, P.d.grid_p, P.bs, P.bc, bj, rs);
+      static_cast<TC*>(C), P.d.ldc, S, P.d.n, P.d.grid_p, P.bs, P.bc, bj, rs, a.timeout);
   for (int u = 0; u < t; ++u) {  // re-check the rebuilt blocks' column lines
     const int64_t I0 = ((int64_t)rows[u] * P.bs) / P.d.vb_rows;
     const int64_t I1 = cdiv(((int64_t)rows[u] + 1) * P.bs, P.d.vb_rows);
@@ -975,7 +984,7 @@ cudaError_t launch_erase(const Plan& P, void* C, int bi, int bj, cudaStream_t st
 }
 
 cudaError_t launch_group_verify(const GroupDev& G, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(G.cnt, 0, sizeof(int32_t) * kNumCounters, st);
+  cudaError_t e = cudaMemsetAsync(G.cnt, 0, sizeof(int32_t) * kNumCleared, st);
   if (e != cudaSuccess || G.count == 0) return e;
   if (G.nctas[kGkColCheck] > 0)
     k_grp_col<<<(unsigned)G.nctas[kGkColCheck], kThreads, 0, st>>>(

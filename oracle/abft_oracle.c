@@ -273,10 +273,13 @@ typedef struct {
  *   f2 = sqrt(k) u_acc + u_cs
  * (f1: accumulation of the block's elements, their block sum, the checksum
  * encoding and C's storage; f2: the checksum row's own product and its
- * representation).  The row check is the transposed formula.  Parity
- * unpinned as a formula (it is a reading); pinned as a property: fault-free
- * residuals stay far below it over many seeds, exact integer data leave
- * residual 0. */
+ * representation).  The row check is the transposed formula.  The formula is
+ * a reading of section 2.1; it is pinned by hand-worked values on a small
+ * integer case, by the rigorous worst-case rounding bound of each residual
+ * (every fault-free residual lies inside it and the threshold never exceeds
+ * it), by the rounding model's predicted size of fault-free residuals for
+ * N(0,1) data (the largest sits at a predictable fraction of the threshold),
+ * and by exact integer data leaving residual 0. */
 static void factors(const oracle_cfg* c, int64_t vb, double* f1, double* f2) {
   *f1 = sqrt((double)c->k) * c->u_acc + sqrt((double)vb) * (c->u_sum + c->u_enc) + c->u_c;
   *f2 = sqrt((double)c->k) * c->u_acc + c->u_cs;
@@ -860,10 +863,12 @@ int oracle_recover_blocks(const oracle_cfg* c, double* C, int64_t ldc, const dou
  * a column residual as sum_l d_I(l) B'_lj, whose independent terms add in
  * quadrature to at most car'(I) ||B'_j||: the next threshold adds car'(I)
  * inside its bracket (taus above).  The row side is the transpose, with
- * max_i ||A_i|| of the earlier product.  Parity of this bound: a reading,
- * pinned as properties (exact zero residuals on integer chains, the measured
- * deviation below the bound, no false flag over seeds where the uncarried
- * threshold fails). */
+ * max_i ||A_i|| of the earlier product.  The bound is a reading of section
+ * 3.2, pinned by hand-worked values of a two-product chain, by the rigorous
+ * worst-case bound of the deviation (the actual deviation, computed exactly,
+ * lies below this bound and this bound below the worst case), by exact zero
+ * residuals on integer chains and by no false flag over seeds where the
+ * uncarried threshold fails. */
 
 /* nblk[4I+2], nblk[4I+3] = norms of the carried rows acs[2I], acs[2I+1]
  * (length len, leading dimension ld). */

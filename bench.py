@@ -65,6 +65,13 @@ def bf16_peak():
         return 1900.0, "fallback 1.9 PFLOP/s (no MEASURED_PEAKS.json)"
 
 
+def fp8_peak():
+    """Dense FP8 tensor peak: the measured bf16 burst peak times the nominal FP8 / bf16
+    ratio (4.5 / 2.25 PFLOP/s dense)."""
+    p, src = bf16_peak()
+    return 2.0 * p, src + " x 2 (nominal FP8 / bf16 dense ratio)"
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -76,6 +83,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the bf16_16384 summary")
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure the dtype peaks (cuBLAS DGEMM, FP8 _scaled_mm, bf16 GEMM at "
+                         "8192^3, and a DFMA throughput probe) and print them as one JSON line")
     return ap.parse_args()
 
 
@@ -485,7 +495,7 @@ def run_workload(w, args, dev, rank, world, secondary=False):
     if lp:
         nseg = {"bf16x3": 3, "bf16x6": 6}.get(w.dtype, 1)  # split products: 3 or 6 bf16 products
         kernel_flops = nseg * 2.0 * w.k * ((w.m + L.acs_rows) * w.n + w.m * L.bcs_cols)
-        peak, peak_src = bf16_peak()
+        peak, peak_src = fp8_peak() if w.dtype == "fp8" else bf16_peak()
         roof = {"kernel": "k_gemm_bf16", "bound": "tensor", "peak_source": peak_src}
     else:
         kernel_flops = 2.0 * w.k * ((w.m + L.R) * w.n + w.m * L.Cc)
@@ -740,12 +750,130 @@ def run_ours(args, rank, world):
         secondary[wl.BF16_GROUPED_4096.name] = {k: sec[k] for k in keys + ("plain_useful_tflops",)}
     out = run_workload(w, args, dev, rank, world)
     out.update(secondary)
+    out["summary"] = summary(out, secondary)
     if rank == 0:
         print(json.dumps(out), flush=True)
 
 
+def summary(main, secondary):
+    """One short row per workload, the last key of the line (a reader of the line's tail
+    sees every workload): useful TF/s per step, product-only and whole-step overhead over
+    the checksum-free product, roofline fraction of the product kernel, encode ms and the
+    median SM clock under load."""
+    rows = {"cols": "useful TF/s | product ovh % | step ovh % | roofline frac | encode ms | "
+                    "SM MHz"}
+    for name, d in [(main["config"]["workload"], main)] + list(secondary.items()):
+        ov, tm = d.get("overhead_pct", {}), d.get("times_ms", {})
+        rows[name] = [round(d["value"], 3), round(ov.get("gemm_only", float("nan")), 2),
+                      round(ov.get("end_to_end_step", ov.get("step", float("nan"))), 2),
+                      round(d["roofline"]["frac"], 3), round(tm.get("encode", float("nan")), 3),
+                      (d.get("clocks") or {}).get("sm_mhz")]
+    return rows
+
+
+# --------------------------------------------------------------------------- peaks
+DFMA_PROBE = r"""
+#include <cuda_runtime.h>
+// Independent chains of binary64 fused multiply-adds: each thread runs 8 chains of
+// `iters` steps (16 flops per step); enough warps per SM to hide the pipe latency.
+__global__ void k_dfma(double* out, int iters, double a, double b) {
+  double x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5,
+         x6 = x0 + 6, x7 = x0 + 7;
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+extern "C" double dfma_tflops(int iters, int reps) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int threads = 512, blocks = sms * 4;
+  double* out = nullptr;
+  if (cudaMalloc(&out, sizeof(double) * threads * blocks) != cudaSuccess) return -1.0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_dfma<<<blocks, threads>>>(out, iters, 0.999999, 1e-7);
+  float best = 1e30f;
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(e0);
+    k_dfma<<<blocks, threads>>>(out, iters, 0.999999, 1e-7);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) best = ms;
+  }
+  const cudaError_t err = cudaGetLastError();
+  cudaFree(out);
+  if (err != cudaSuccess) return -2.0;
+  return 16.0 * iters * (double)threads * blocks / (best * 1e-3) / 1e12;
+}
+"""
+
+
+def run_peaks(args):
+    """Dtype peaks on this GPU, for the roofline denominators: best of 10 at 8192^3 of
+    cuBLAS DGEMM (torch.matmul float64), FP8 torch._scaled_mm (e4m3, unit scales, bf16 and
+    fp32 out) and bf16 torch.matmul, plus a DFMA throughput probe (independent fma chains,
+    best of 10).  nvidia-smi clocks are sampled during the measurements."""
+    import ctypes
+    import torch
+    dev = torch.device("cuda", 0)
+    n = 8192
+    out = {"what": "dtype peaks, best of 10 at 8192^3 (2 n^3 flops), CUDA events"}
+
+    def best(fn, reps=10):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return 2.0 * n ** 3 / (min(ts) * 1e-3) / 1e12
+
+    src = os.path.join(ROOT, "paper_0806_3121_gb300", "_build", "dfma_probe.cu")
+    lib = src[:-3] + ".so"
+    os.makedirs(os.path.dirname(src), exist_ok=True)
+    with open(src, "w") as f:
+        f.write(DFMA_PROBE)
+    from paper_0806_3121_gb300 import build
+    subprocess.run([build.nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-shared",
+                    "-Xcompiler", "-fPIC", src, "-o", lib], check=True)
+    with ClockSampler(0) as clk:
+        x = torch.randn(n, n, device=dev, dtype=torch.float64)
+        out["fp64_dgemm_tflops"] = best(lambda: torch.matmul(x, x))
+        del x
+        probe = ctypes.CDLL(lib)
+        probe.dfma_tflops.restype = ctypes.c_double
+        probe.dfma_tflops.argtypes = [ctypes.c_int, ctypes.c_int]
+        out["fp64_dfma_probe_tflops"] = probe.dfma_tflops(20000, 10)
+        a = torch.randn(n, n, device=dev).to(torch.float8_e4m3fn)
+        b = torch.randn(n, n, device=dev).to(torch.float8_e4m3fn).t().contiguous().t()
+        one = torch.ones((), dtype=torch.float32, device=dev)
+        out["fp8_scaled_mm_bf16out_tflops"] = best(
+            lambda: torch._scaled_mm(a, b, one, one, out_dtype=torch.bfloat16))
+        out["fp8_scaled_mm_fp32out_tflops"] = best(
+            lambda: torch._scaled_mm(a, b, one, one, out_dtype=torch.float32))
+        del a, b
+        x = torch.randn(n, n, device=dev, dtype=torch.bfloat16)
+        out["bf16_matmul_tflops"] = best(lambda: torch.matmul(x, x))
+    out["clocks"] = clk.summary()
+    out["gpu"] = torch.cuda.get_device_name(dev)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.peaks:
+        run_peaks(args)
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if world > 1 and args.impl == "ours":

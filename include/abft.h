@@ -146,6 +146,8 @@ typedef struct {
                                         checksums' deviation (binary64, 2 per
                                         row / column verify block; zero after
                                         abft_encode)                           */
+  size_t scales;                     /* FP8: the block scales of A, then of B
+                                        (binary32, copied by abft_encode)      */
 } abft_ws_layout;
 
 /* Size of the caller-owned device workspace for `desc`.  Returns 0 for an
@@ -316,6 +318,38 @@ abft_status abft_recover_block(const abft_desc* desc, void* C, void* ws, int32_t
  * SYNCHRONISES `stream`. */
 abft_status abft_recover_blocks(const abft_desc* desc, void* C, void* ws, const int32_t* blocks,
                                 int32_t n_blocks, abft_fault* report, void* stream);
+
+/* Block rebuild when the block rows of one problem are spread over several
+ * GPUs (section 3.1: the process grid holds the blocks; section 3.3: a lost
+ * block is the block checksum minus the survivors, formed by one reduction
+ * over the processes of its block column).  Each rank holds some block rows
+ * of C as a problem of its own (desc with grid_p = its block rows, grid_q as
+ * the global grid); one rank also holds the global block checksum rows
+ * S = sum_I C_I of every block row in its workspace (its encoded S_A rows are
+ * the reduction of every rank's local sum of A blocks before its product).
+ *
+ * abft_block_partial writes this rank's share of the rebuild of a block of
+ * block column bj into out (device, bs x bc binary64, row-major, ld = bc;
+ * bs = m / grid_p, bc = n / grid_q):
+ *   out = (with_checksum ? S_bj : 0) - sum_{local block rows I != bi_skip} C_I,bj
+ * (bi_skip = -1 when the lost block is not on this rank; with_checksum = 1 on
+ * the rank that holds S, whose ws is then read).  Summing every rank's out
+ * (one reduction, e.g. an NCCL reduce to the rank of the lost block) gives
+ * the lost block.  ws may be NULL when with_checksum = 0.  Asynchronous.
+ *
+ * abft_block_restore writes sum (device, bs x bc binary64, as above) into
+ * block (bi, bj) of C, rounded to C's type, and re-checks the block's column
+ * lines against this workspace's element checksums.  report_entry (host, may
+ * be NULL) receives a kind-4 entry.  ABFT_ERR_UNCORRECTABLE when the rebuilt
+ * block fails its checks; ABFT_ERR_TIMEOUT (nothing written) when this
+ * workspace's last tensor-core product timed out.  SYNCHRONISES `stream`.
+ * Call abft_verify_correct (listing the block as erased) first on every rank,
+ * since the shares read the rest of the block column. */
+abft_status abft_block_partial(const abft_desc* desc, const void* C, const void* ws,
+                               int32_t bi_skip, int32_t bj, int32_t with_checksum, double* out,
+                               void* stream);
+abft_status abft_block_restore(const abft_desc* desc, void* C, void* ws, int32_t bi, int32_t bj,
+                               const double* sum, abft_fault* report_entry, void* stream);
 
 /* Fault injection for tests and benchmarks (the paper's stress test kills
  * processes, section 4.3; here faults are bit flips and erasures chosen on the

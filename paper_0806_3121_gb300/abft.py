@@ -24,6 +24,7 @@ KIND_CORRECTED, KIND_NONFINITE_CORRECTED, KIND_UNCORRECTABLE, KIND_BLOCK_RECOVER
 EXPORTS = ("abft_workspace_bytes", "abft_workspace_layout", "abft_encode",
            "abft_encode_noalloc", "abft_encode_chained", "abft_gemm", "abft_set_epilogue_faults",
            "abft_gemm_plain", "abft_verify_correct", "abft_recover_block", "abft_recover_blocks",
+           "abft_block_partial", "abft_block_restore",
            "abft_inject_bitflips", "abft_erase_block", "abft_kernel_launches",
            "abft_last_error", "abft_version",
            "abft_group_create", "abft_group_workspace_bytes", "abft_group_problem_layout",
@@ -70,7 +71,7 @@ class WsLayout(ct.Structure):
                 ("inject", ct.c_size_t), ("fused", ct.c_int32), ("planes", ct.c_int32),
                 ("acs_plane", ct.c_size_t), ("bcs_plane", ct.c_size_t), ("op_a", ct.c_size_t),
                 ("op_b", ct.c_size_t), ("op_a_ld", ct.c_int64), ("op_b_ld", ct.c_int64),
-                ("car_a", ct.c_size_t), ("car_b", ct.c_size_t)]
+                ("car_a", ct.c_size_t), ("car_b", ct.c_size_t), ("scales", ct.c_size_t)]
 
 
 class Problem(ct.Structure):
@@ -117,6 +118,8 @@ def load(path: str = LIB_PATH):
                                             ct.POINTER(ct.c_int32), vp]
         lib.abft_recover_block.argtypes = [D, vp, vp, i32, i32, ct.POINTER(Fault), vp]
         lib.abft_recover_blocks.argtypes = [D, vp, vp, vp, i32, vp, vp]
+        lib.abft_block_partial.argtypes = [D, vp, vp, i32, i32, i32, vp, vp]
+        lib.abft_block_restore.argtypes = [D, vp, vp, i32, i32, vp, ct.POINTER(Fault), vp]
         lib.abft_inject_bitflips.argtypes = [D, vp, vp, vp, vp, i32, vp]
         lib.abft_erase_block.argtypes = [D, vp, i32, i32, vp]
         lib.abft_last_error.restype = ct.c_char_p
@@ -258,6 +261,24 @@ def abft_recover_blocks(desc, C, ws, blocks, stream=None):
                                     n, ct.cast(rep, ct.c_void_p), _stream(stream))
     _check(st, allow=(OK, ERR_UNCORRECTABLE))
     return st, [r.as_dict() for r in rep[:n]]
+
+
+def abft_block_partial(desc, C, ws, bi_skip, bj, with_checksum, out, stream=None):
+    """This rank's share of the rebuild of a block of block column bj (block rows spread
+    over GPUs): out (bs x bc float64, device) = (with_checksum ? S_bj : 0) minus the local
+    blocks of the column other than block row bi_skip (-1: none)."""
+    _check(load().abft_block_partial(ct.byref(desc), _ptr(C), _ptr(ws), bi_skip, bj,
+                                     1 if with_checksum else 0, _ptr(out), _stream(stream)))
+
+
+def abft_block_restore(desc, C, ws, bi, bj, total, stream=None):
+    """Write the reduced shares `total` (bs x bc float64, device) into block (bi, bj) of C
+    and re-check it.  Returns (status, report entry dict).  Synchronises the stream."""
+    f = Fault()
+    st = load().abft_block_restore(ct.byref(desc), _ptr(C), _ptr(ws), bi, bj, _ptr(total),
+                                   ct.byref(f), _stream(stream))
+    _check(st, allow=(OK, ERR_UNCORRECTABLE))
+    return st, f.as_dict()
 
 
 def abft_inject_bitflips(desc, C, flips, stream=None):

@@ -173,6 +173,11 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
   L.op_b_ld = op_planes ? (d->n + 7) / 8 * 8 : 0;
   L.op_a = region(op_planes * align256((size_t)d->m * L.op_a_ld * 2));
   L.op_b = region(op_planes * align256((size_t)d->k * L.op_b_ld * 2));
+  // FP8: a copy of the block scales (the product's data tiles scale their e4m3
+  // partials by them)
+  L.scales = region(f8 ? sizeof(float) * (size_t)(cdiv(d->m, 128) * cdiv(d->k, 128) +
+                                                   cdiv(d->k, 128) * cdiv(d->n, 128))
+                       : 0);
   L.fused = p.fused;
   L.scratch = off;
   L.scratch_bytes = scratch_bytes(p);
@@ -593,6 +598,59 @@ abft_status abft_recover_block(const abft_desc* desc, void* C, void* ws, int32_t
                                abft_fault* report_entry, void* stream) {
   const int32_t blk[2] = {bi, bj};
   return abft_recover_blocks(desc, C, ws, blk, 1, report_entry, stream);
+}
+
+abft_status abft_block_partial(const abft_desc* desc, const void* C, const void* ws,
+                               int32_t bi_skip, int32_t bj, int32_t with_checksum, double* out,
+                               void* stream) {
+  Plan P;
+  abft_status st = make_plan(desc, &P);
+  if (st != ABFT_OK) return st;
+  if (P.bs == 0) return fail(ABFT_ERR_INVALID, "no erasure grid in the descriptor");
+  if (bj < 0 || bj >= P.d.grid_q || bi_skip < -1 || bi_skip >= P.d.grid_p)
+    return fail(ABFT_ERR_INVALID, "block column %d / skipped block row %d outside the grid", bj,
+                bi_skip);
+  if (!C || !out || (with_checksum && !ws)) return fail(ABFT_ERR_INVALID, "NULL pointer");
+  if (ws && ws_misaligned(ws)) return fail(ABFT_ERR_INVALID, "ws must be 256-byte aligned");
+  const cudaError_t e = launch_block_partial(P, C, ws, bi_skip, bj, with_checksum != 0, out,
+                                             static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? ABFT_OK : cuda_fail(e, "abft_block_partial");
+}
+
+abft_status abft_block_restore(const abft_desc* desc, void* C, void* ws, int32_t bi, int32_t bj,
+                               const double* sum, abft_fault* report_entry, void* stream) {
+  Plan P;
+  abft_status st = make_plan(desc, &P);
+  if (st != ABFT_OK) return st;
+  if (P.bs == 0) return fail(ABFT_ERR_INVALID, "no erasure grid in the descriptor");
+  if (bi < 0 || bj < 0 || bi >= P.d.grid_p || bj >= P.d.grid_q)
+    return fail(ABFT_ERR_INVALID, "block (%d, %d) outside the erasure grid", bi, bj);
+  if (!C || !ws || !sum) return fail(ABFT_ERR_INVALID, "NULL pointer");
+  if (ws_misaligned(ws)) return fail(ABFT_ERR_INVALID, "ws must be 256-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Scratch S = scratch_view(P, ws);
+  cudaError_t e = cudaMemsetAsync(S.cnt + kCntRecoverFlagged, 0, sizeof(int32_t), s);
+  if (e == cudaSuccess) e = launch_block_restore(P, C, ws, bi, bj, sum, s);
+  int32_t cnt[kNumCounters] = {};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, S.cnt, sizeof cnt, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "abft_block_restore");
+  if (P.d.dtype != ABFT_F64 && cnt[kCntTimeout])
+    return fail(ABFT_ERR_TIMEOUT,
+                "the tensor-core product on this workspace gave up waiting (bounded wait); "
+                "nothing was written");
+  const int32_t nfl = cnt[kCntRecoverFlagged];
+  if (report_entry) {
+    abft_fault f{};
+    f.row = (int32_t)(bi * P.bs);
+    f.col = (int32_t)(bj * P.bc);
+    f.kind = ABFT_KIND_BLOCK_RECOVERED;
+    f.side = 2;
+    f.r_e = (double)nfl;
+    *report_entry = f;
+  }
+  if (nfl) return fail(ABFT_ERR_UNCORRECTABLE, "rebuilt block fails %d column checks", nfl);
+  return ABFT_OK;
 }
 
 abft_status abft_inject_bitflips(const abft_desc* desc, void* C, const int64_t* rows,

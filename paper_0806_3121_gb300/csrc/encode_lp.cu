@@ -14,6 +14,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <stdlib.h>
+
 #include "internal.cuh"
 
 namespace abft {
@@ -1394,6 +1396,14 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, cons
     int* flag = S.cnt + kCntFp8Inexact;
     cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
+    // the block scales, for the product's native FP8 data tiles
+    const size_t nsa = (size_t)(cdiv(d.m, 128) * cdiv(d.k, 128));
+    const size_t nsb = (size_t)(cdiv(d.k, 128) * cdiv(d.n, 128));
+    e = cudaMemcpyAsync(w + P.L.scales, a_scale, sizeof(float) * nsa, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(w + P.L.scales + sizeof(float) * nsa, b_scale, sizeof(float) * nsb,
+                          cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
     auto* pa = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_a);
     auto* pb = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_b);
     const auto* qa = static_cast<const uint8_t*>(Av);
@@ -1553,6 +1563,19 @@ cudaError_t launch_encode_lp_chained(const Plan& P, const void* Av, const void* 
   return cudaGetLastError();
 }
 
+// Native FP8 data tiles (the e4m3 codes on the 8-bit tensor path) when the
+// environment variable ABFT_FP8_NATIVE is 1; otherwise the data tiles multiply
+// the dequantised bf16 planes.
+static bool fp8_native() {
+  const char* env = getenv("ABFT_FP8_NATIVE");
+  return env && env[0] == '1';
+}
+
+// A byte matrix whose base and row pitch are 16-byte multiples (TMA rows).
+static bool aligned16(const void* p, int64_t ld_bytes) {
+  return p && ((reinterpret_cast<uintptr_t>(p) & 15) == 0) && ld_bytes % 16 == 0;
+}
+
 cudaError_t launch_gemm_lp(const Plan& P, const void* A, const void* B, float* C, void* ws,
                            bool checksums, cudaStream_t st) {
   const abft_desc& d = P.d;
@@ -1588,12 +1611,23 @@ cudaError_t launch_gemm_lp(const Plan& P, const void* A, const void* B, float* C
       op.seg_a = 2u | (1u << 2) | (0u << 4) | (1u << 6) | (0u << 8) | (0u << 10);
       op.seg_b = 0u | (1u << 2) | (2u << 4) | (0u << 6) | (1u << 8) | (0u << 10);
     }
-  } else if (d.dtype == ABFT_FP8_E4M3) {  // the dequantised planes abft_encode wrote
+  } else if (d.dtype == ABFT_FP8_E4M3) {
+    // checksum tiles: the exact dequantised bf16 planes abft_encode wrote; data
+    // tiles: the e4m3 codes on the 8-bit tensor path when their rows suit TMA
+    // (16-byte aligned), else the planes too
     op.a[0] = op.a[1] = op.a[2] = w + P.L.op_a;
     op.b[0] = op.b[1] = op.b[2] = w + P.L.op_b;
     op.lda = P.L.op_a_ld;
     op.ldb = P.L.op_b_ld;
     op.nseg = 1;
+    if (fp8_native() && aligned16(A, d.lda) && aligned16(B, d.ldb)) {
+      op.a8 = A;
+      op.b8 = B;
+      op.lda8 = d.lda;
+      op.ldb8 = d.ldb;
+      op.sA = reinterpret_cast<const float*>(w + P.L.scales);
+      op.sB = op.sA + cdiv(d.m, 128) * cdiv(d.k, 128);
+    }
   } else {
     op.a[0] = op.a[1] = op.a[2] = A;
     op.b[0] = op.b[1] = op.b[2] = B;

@@ -60,6 +60,11 @@ constexpr uint32_t A_BYTES = BM * BK * 2;          // 16 KiB
 constexpr uint32_t HALF_BYTES = 64 * BK * 2;       // one 64-row half of A: 8 KiB
 constexpr uint32_t B_BOX_BYTES = 64 * BK * 2;      // one 64-column box: 8 KiB
 constexpr uint32_t B_BYTES = BN * BK * 2;          // 32 KiB
+// FP8 data tiles: a k-step is 128 e4m3 codes (the same 128 bytes per row as a
+// bf16 k-step, so the stage layout is unchanged) and a B box is 128 columns x
+// 128 k-rows (16 KiB; two per 256-column tile)
+constexpr int BK8 = 128;
+constexpr uint32_t B8_BOX_BYTES = 128 * BK8;
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t TMEM_COLS = 2 * BN;             // two accumulators
 constexpr uint32_t STG_BYTES = 32 * 32 * 4;        // one epilogue warp's staging block
@@ -96,6 +101,10 @@ struct TcMaps {
   CUtensorMap a[kPlanes], acs[kPlanes], b[kPlanes], bcs[kPlanes], a128[kPlanes],
       acs128[kPlanes], b4[kPlanes], bcs4[kPlanes];
   CUtensorMap cst, est, fst;  // fp32 store maps of C, E16, F16 (valid per TcArgs::st_ok)
+  // e4m3 codes of the data operands (native FP8 data tiles): A as 64-row halves
+  // and 128-row boxes of 128 codes, B as 128-column N-major boxes of 128 k-rows
+  // (one box or, in the 3-D view, both boxes of a 256-column tile)
+  CUtensorMap a8, a8_128, b8, b8w;
 };
 
 struct TcArgs {
@@ -121,6 +130,13 @@ struct TcArgs {
   int stall_test;            // timeout test: the producer skips the first tile
   int kpg;                   // k-steps per promotion group (0: one group per tile)
   int group_m;               // raster group height (tile rows)
+  // native FP8 data tiles: e4m3 products on the 8-bit tensor path, one
+  // 128-wide k-step per accumulator, each scaled in the epilogue by the
+  // power-of-two block scales sA[row block][k block] * sB[k block][column block]
+  int f8;
+  const float* sA;           // ceil(m/128) x nsa
+  const float* sB;           // ceil(k/128) x nsb
+  int64_t nsa, nsb;
 };
 
 struct Tile {
@@ -216,6 +232,12 @@ struct TileView {
   float* obs_row;             // [row][ngrp][2]
   int64_t g, ngrp;
   int vb_r, vb_c, er, ec;
+  // native FP8 data tile: k-steps of 128 e4m3 codes (maD / maW / mbD / mbW are
+  // the e4m3 maps), each promoted with the scale sArow[kb] * sB[kb * nsb + J]
+  bool f8;
+  const float* sArow;
+  const float* sB;
+  int64_t nsb;
 };
 
 // One problem (abft_gemm), tiles of kBM rows (128 or 256).
@@ -265,6 +287,21 @@ struct SingleSched {
     V.nW = 4;
     if (bcols == 4 && T.col0 + 256 <= ((T.kind == 2 ? g.C16 : g.n) / 64) * 64) {
       V.mbW = T.kind == 2 ? &M->bcs4[0] : &M->b4[0];
+    }
+    V.f8 = g.f8 && T.kind == 0;
+    V.sArow = nullptr;
+    V.sB = g.sB;
+    V.nsb = g.nsb;
+    if (V.f8) {  // data tile on the e4m3 codes: 128-wide k-steps, promoted each step
+      V.nkb = (g.k + 127) / 128;
+      V.nseg = 1;
+      V.kpg = 1;
+      V.seg_a = V.seg_b = 0;
+      V.maD = &M->a8;
+      V.mbD = &M->b8;
+      V.maW = V.nA128 ? &M->a8_128 : nullptr;
+      V.mbW = (bcols == 4 && T.col0 + 256 <= (g.n / 128) * 128) ? &M->b8w : nullptr;
+      V.sArow = g.sA + (T.row0 / 128) * g.nsa;
     }
     V.C = g.C;
     V.ldc = g.ldc;
@@ -330,12 +367,13 @@ __device__ __forceinline__ float4 staged4(const float* stg, int r, int j) {
 // kPromote: the K loop runs in promotion groups whose accumulators the
 // epilogue sums in fp32 registers (a separate instantiation, so the register
 // accumulator of that path does not weigh on the single-group epilogue).
-template <bool kPromote, bool kTall, class Sched>
+template <bool kPromote, bool kTall, bool kF8, class Sched>
 __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wait_ns,
                                         int stall_test, const int32_t* inj_hdr,
                                         const InjectEntry* inj) {
   using G = Geo<kTall>;
   static_assert(!(kPromote && kTall), "promotion runs on regular tiles");
+  static_assert(!kF8 || kPromote, "FP8 data tiles promote every k-step");
   static_assert(!kTall || kEpiWarps == 8, "tall tiles: one epilogue warp per lane quarter and half");
   constexpr int NS = G::kStages;
   extern __shared__ uint8_t smem_raw[];
@@ -393,17 +431,32 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
         const TileView T = S.view(t);
         if (stall_test && t == 0) continue;  // nothing will fill these stages
         const int64_t nkb = T.nkb, nkt = T.nkb * T.nseg;
-        const uint32_t tx = pA ? (uint32_t)T.hcnt * HALF_BYTES : (uint32_t)T.nbox * B_BOX_BYTES;
+        // an FP8 data tile's k-step is 128 codes (128 bytes, as a bf16 k-step) and
+        // its B boxes are 128 columns wide
+        const int nb8 = (T.nbox + 1) / 2;
+        const uint32_t tx = pA ? (uint32_t)T.hcnt * HALF_BYTES
+                               : (T.f8 ? (uint32_t)nb8 * B8_BOX_BYTES
+                                       : (uint32_t)T.nbox * B_BOX_BYTES);
+        const int bkx = T.f8 ? BK8 : BK;
         // a stage's MMAs take ~700 cycles: the per-stage bookkeeping is
         // incremental (no division per stage)
         int seg = 0, pa = (int)(T.seg_a & 3u), pb = (int)(T.seg_b & 3u);
         int64_t kb = 0;
         for (int64_t kt = 0; kt < nkt; ++kt) {
-          const int32_t kx = (int32_t)(kb * BK);
+          const int32_t kx = (int32_t)(kb * bkx);
           if (!tc::wait(empty(s), ph ^ 1, abort)) break;
           const uint32_t sa = tc::smem_addr(smem + s * G::kStageBytes);
           tc::mbar_arrive_expect_tx(full(s), tx);
-          if (!pA) {
+          if (!pA && T.f8) {
+            // e4m3 B: both 128-column boxes in one 3-D copy, else box by box
+            if (T.mbW) {
+              tc::tma_load_3d(sa + G::kABytes, T.mbW, full(s), 0, kx, T.colW / 128);
+            } else {
+              for (int b = 0; b < nb8; ++b)
+                tc::tma_load_2d(sa + G::kABytes + b * B8_BOX_BYTES, T.mbD, full(s),
+                                T.colD + 128 * b, kx);
+            }
+          } else if (!pA) {
             // B: the full boxes in one 3-D copy, the rest (ragged, checksum) per box
             int b_first = 0;
             if (T.mbW) {
@@ -454,8 +507,9 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
       for (int64_t t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
         const TileView T = S.view(t);
         const int64_t nkt = T.nkb * T.nseg;
-        const int64_t gsz = (kPromote && T.kpg > 0 && T.kpg < nkt) ? T.kpg : nkt;
-        const uint32_t idesc = tc::idesc_bf16(BM, 64 * T.nbox, 1);
+        const int64_t gsz = (kPromote && T.kpg > 0 && (T.kpg < nkt || T.f8)) ? T.kpg : nkt;
+        const uint32_t idesc = T.f8 ? tc::idesc_e4m3(BM, 64 * T.nbox, 1)
+                                    : tc::idesc_bf16(BM, 64 * T.nbox, 1);
         bool ok = true;
         // one accumulator per promotion group; the epilogue adds the groups
         for (int64_t g0 = 0; g0 < nkt && ok; g0 += gsz) {
@@ -470,6 +524,21 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
             tc::fence_after_sync();
             const uint32_t sa = tc::smem_addr(smem + s * G::kStageBytes);
             const uint32_t sb = sa + G::kABytes;
+            if (kF8 && T.f8) {
+              // e4m3: K = 32 codes per MMA.  A: K-major 128-byte rows, a K step
+              // moves 32 B inside the swizzled row.  B: N-major, 128-column
+              // boxes 16 KiB apart, 8-row (K) groups 1024 B apart, a K step of
+              // 32 rows moves 4 KiB.
+#pragma unroll
+              for (int kk = 0; kk < BK8 / 32; ++kk) {
+                const uint64_t bd = tc::sdesc_sw128(sb + kk * 4096, B8_BOX_BYTES, 1024);
+                const uint64_t ad = tc::sdesc_sw128(sa + kk * 32, 16, 1024);
+                tc::mma_f8(d, ad, bd, idesc, (kb > g0 || kk > 0) ? 1u : 0u);
+              }
+              tc::commit(empty(s));
+              if (++s == NS) { s = 0; ph ^= 1; }
+              continue;
+            }
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
               // B: N-major, 64-column boxes 8 KiB apart, 8-row (K) groups
@@ -522,7 +591,7 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
     for (int64_t t = blockIdx.x; t < total && !aborted; t += gridDim.x) {
       const TileView T = S.view(t);
       const int64_t nkt = T.nkb * T.nseg;
-      const int64_t gsz = (kPromote && T.kpg > 0 && T.kpg < nkt) ? T.kpg : nkt;
+      const int64_t gsz = (kPromote && T.kpg > 0 && (T.kpg < nkt || T.f8)) ? T.kpg : nkt;
       const int ncol = 64 * T.nbox;
       const int c_hi = min(c_lo + G::kCols, ncol);
       // this warp's 32 rows: data rows, checksum rows or none
@@ -685,7 +754,7 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
           }
         }
       };
-      if (!kPromote || gsz >= nkt) {
+      if (!kPromote || (gsz >= nkt && !T.f8)) {
         // one accumulator: each chunk is read and finished in turn; the
         // accumulator is released after the last read
         if (!tc::wait(tfull(acc), aph, abort)) break;
@@ -715,7 +784,16 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
         // groups in fp32 registers (round to nearest), each accumulator
         // released as soon as it is read
         float accr[kEpiChunks][32];
+        // FP8 data tiles: each k-step's partial times its block scales (powers of
+        // two, so the product is exact); this warp's 128 columns are one column
+        // block of B's scales.  The next step's scale is loaded ahead.
+        const bool scaled = kF8 && T.f8 && c_lo < c_hi;
+        const int64_t jb = scaled ? (T.colD + c_lo) / 128 : 0;
+        float sc_next = scaled ? __ldg(&T.sArow[0]) * __ldg(&T.sB[jb]) : 1.0f;
         for (int64_t g0 = 0; g0 < nkt; g0 += gsz) {
+          const float sc = sc_next;
+          if (scaled && g0 + 1 < nkt)
+            sc_next = __ldg(&T.sArow[g0 + 1]) * __ldg(&T.sB[(g0 + 1) * T.nsb + jb]);
           if (!tc::wait(tfull(acc), aph, abort)) { aborted = true; break; }
           tc::fence_after_sync();
           const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
@@ -725,11 +803,20 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
             if (c < c_hi) {
               if (g0 == 0) {
                 tc::tmem_ld32(base + c, accr[ci]);
+                if (scaled) {
+#pragma unroll
+                  for (int u = 0; u < 32; ++u) accr[ci][u] *= sc;
+                }
               } else {
                 float v[32];
                 tc::tmem_ld32(base + c, v);
+                if (scaled) {
 #pragma unroll
-                for (int u = 0; u < 32; ++u) accr[ci][u] += v[u];
+                  for (int u = 0; u < 32; ++u) accr[ci][u] = fmaf(sc, v[u], accr[ci][u]);
+                } else {
+#pragma unroll
+                  for (int u = 0; u < 32; ++u) accr[ci][u] += v[u];
+                }
               }
             }
           }
@@ -760,11 +847,11 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
   }
 }
 
-template <bool kPromote, bool kTall>
+template <bool kPromote, bool kTall, bool kF8>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_bf16(const __grid_constant__ TcMaps M, const TcArgs g) {
   const SingleSched<Geo<kTall>::kBM> S{&M, &g};
-  tc_body<kPromote, kTall>(S, g.status, g.wait_ns, g.stall_test, g.inj_hdr, g.inj);
+  tc_body<kPromote, kTall, kF8>(S, g.status, g.wait_ns, g.stall_test, g.inj_hdr, g.inj);
 }
 
 // Many problems (grouped product).  The flattened tile list is a table of
@@ -845,6 +932,10 @@ struct GroupSched {
     V.vb_c = kGrpVbC;
     V.er = kGrpEr;
     V.ec = kGrpEc;
+    V.f8 = false;
+    V.sArow = nullptr;
+    V.sB = nullptr;
+    V.nsb = 0;
     return V;
   }
 };
@@ -854,7 +945,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                    int checksums, int* status, uint64_t wait_ns, const int32_t* inj_hdr,
                    const InjectEntry* inj, int kpg) {
   const GroupSched S{probs, maps, tiles, t_total, checksums != 0, kpg};
-  tc_body<false, false>(S, status, wait_ns, 0, inj_hdr, inj);
+  tc_body<false, false, false>(S, status, wait_ns, 0, inj_hdr, inj);
 }
 
 // ---- host side
@@ -928,6 +1019,36 @@ bool make_map_boxes(CUtensorMap* map, const void* ptr, int64_t rows, int64_t col
   const cuuint32_t box[3] = {64, 64, (cuuint32_t)depth};
   const cuuint32_t estr[3] = {1, 1, 1};
   return g_encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// e4m3 (byte) maps of the native FP8 data tiles.  2-D: a row-major rows x cols
+// byte matrix with leading dimension ld, box box_cols x box_rows, 128-byte
+// swizzle.  3-D: the (128 columns, rows, column box) view of B with a box of
+// both 128-column boxes of a 256-column tile (only the cols / 128 full boxes
+// are inside the view).
+bool make_map_u8(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols, int64_t ld,
+                 uint32_t box_cols, uint32_t box_rows) {
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld};
+  const cuuint32_t box[2] = {box_cols, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return g_encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(ptr), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+bool make_map_boxes_u8(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols,
+                       int64_t ld) {
+  int64_t nb = cols / 128;
+  if (nb == 0) nb = 1;  // never read (no full box): a dummy valid view
+  const cuuint64_t dims[3] = {128, (cuuint64_t)rows, (cuuint64_t)nb};
+  const cuuint64_t strides[2] = {(cuuint64_t)ld, 128};
+  const cuuint32_t box[3] = {128, (cuuint32_t)BK8, 2};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return g_encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(ptr), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -1026,7 +1147,20 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
   g.seg_a = op.seg_a;
   g.seg_b = op.seg_b;
   g.kpg = promote_ksteps(d.dtype);
-  const bool tall = use_tall(d.m, cdiv(d.k, BK) * op.nseg, g.kpg);
+  if (op.a8) {  // native FP8 data tiles on the e4m3 codes (promoted every k-step)
+    if (!make_map_u8(&M.a8, op.a8, d.m, d.k, op.lda8, 128, BM / 2) ||
+        !make_map_u8(&M.a8_128, op.a8, d.m, d.k, op.lda8, 128, BM) ||
+        !make_map_u8(&M.b8, op.b8, d.k, d.n, op.ldb8, 128, BK8) ||
+        !make_map_boxes_u8(&M.b8w, op.b8, d.k, d.n, op.ldb8))
+      return cudaErrorInvalidValue;
+    g.f8 = 1;
+    g.sA = op.sA;
+    g.sB = op.sB;
+    g.nsa = cdiv(d.k, 128);
+    g.nsb = cdiv(d.n, 128);
+    g.kpg = 0;  // the checksum tiles (bf16 planes) run one group
+  }
+  const bool tall = !g.f8 && use_tall(d.m, cdiv(d.k, BK) * op.nseg, g.kpg);
   const int bm = tall ? Geo<true>::kBM : BM;
   g.ntm = (int)cdiv(d.m, bm);
   g.ntn = (int)cdiv(d.n, BN);
@@ -1060,8 +1194,10 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
   g.stall_test = stall && stall[0] == '1';
   g.group_m = raster_group_rows(bm);
   g.wait_ns = g.stall_test ? 200000000ull : tc::kWaitLimitNs;
-  const auto kernel = g.kpg > 0 ? k_gemm_bf16<true, false>
-                                : (tall ? k_gemm_bf16<false, true> : k_gemm_bf16<false, false>);
+  const auto kernel = g.f8 ? k_gemm_bf16<true, false, true>
+                           : g.kpg > 0 ? k_gemm_bf16<true, false, false>
+                                       : (tall ? k_gemm_bf16<false, true, false>
+                                               : k_gemm_bf16<false, false, false>);
   const size_t smem = tall ? Geo<true>::kSmem : Geo<false>::kSmem;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

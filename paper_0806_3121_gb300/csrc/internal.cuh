@@ -163,6 +163,15 @@ struct TcOperands {
   int64_t lda, ldb;
   int nseg;
   uint32_t seg_a, seg_b;
+  // native FP8 data tiles (a8 == nullptr: none): e4m3 codes of A (m x k, lda8
+  // bytes) and B (k x n, ldb8 bytes), 16-byte aligned rows, and their binary32
+  // power-of-two block scales (ceil(m/128) x ceil(k/128), ceil(k/128) x
+  // ceil(n/128), row-major, device)
+  const void* a8;
+  const void* b8;
+  int64_t lda8, ldb8;
+  const float* sA;
+  const float* sB;
 };
 // status: the word a timeout is recorded in (cleared on `st` before the
 // launch).
@@ -272,6 +281,15 @@ cudaError_t launch_set_inject(const Plan& P, void* ws, const int64_t* rows, cons
 // rows[u], p), row-major t x t, in binary64.
 cudaError_t launch_recover(const Plan& P, void* C, void* ws, int bj, const int* rows, int t,
                            const double* minv, cudaStream_t st);
+// One rank's share of a block rebuild over GPUs: out (bs x bc binary64) =
+// (with_checksum ? S_bj : 0) - sum of the local blocks of block column bj other
+// than block row `skip` (-1: none).
+cudaError_t launch_block_partial(const Plan& P, const void* C, const void* ws, int skip, int bj,
+                                 bool with_checksum, double* out, cudaStream_t st);
+// Writes src (bs x bc binary64) into block (bi, bj) of C and re-checks the
+// block's column lines (count in cnt[kCntRecoverFlagged]).
+cudaError_t launch_block_restore(const Plan& P, void* C, void* ws, int bi, int bj,
+                                 const double* src, cudaStream_t st);
 cudaError_t launch_inject(const Plan& P, void* C, const int64_t* rows, const int64_t* cols,
                           const int32_t* bits, int count, cudaStream_t st);
 cudaError_t launch_erase(const Plan& P, void* C, int bi, int bj, cudaStream_t st);

@@ -809,6 +809,42 @@ __global__ void __launch_bounds__(kThreads) k_recover(TC* C, int64_t ldc, const 
   }
 }
 
+// One rank's share of the rebuild of a block of block column bj when the
+// block rows are spread over several GPUs (section 3.3: the lost block is the
+// block checksum minus the sum of the survivors, formed by one reduction over
+// the processes of the block column).  out[r][jj] (bs x bc, binary64):
+//   (S == nullptr ? 0 : S[r][j]) - sum over local block rows I != skip of C[I bs + r][j],
+// j = bj bc + jj.  The sum of every rank's share is the lost block.  Grid
+// (ceil(bc/256), min(bs, 65535)).
+template <typename TC>
+__global__ void __launch_bounds__(kThreads) k_block_partial(const TC* C, int64_t ldc,
+                                                            const double* S, int64_t n, int p,
+                                                            int64_t bs, int64_t bc, int bj,
+                                                            int skip, double* out) {
+  const int64_t jj = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (jj >= bc) return;
+  const int64_t j = (int64_t)bj * bc + jj;
+  for (int64_t r = blockIdx.y; r < bs; r += gridDim.y) {
+    double sum = 0.0;
+    for (int I = 0; I < p; ++I)
+      if (I != skip) sum += (double)C[(I * bs + r) * ldc + j];
+    out[r * bc + jj] = (S ? S[r * n + j] : 0.0) - sum;
+  }
+}
+
+// The rebuilt block written into C (rounded to C's type): C[bi bs + r][bj bc + jj]
+// = src[r][jj].  Grid (ceil(bc/256), min(bs, 65535)).
+template <typename TC>
+__global__ void __launch_bounds__(kThreads) k_block_store(TC* C, int64_t ldc, const double* src,
+                                                          int64_t bs, int64_t bc, int bi, int bj,
+                                                          const int32_t* timeout) {
+  const int64_t jj = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (jj >= bc) return;
+  if (timeout && *timeout) return;  // checksums of an incomplete product
+  for (int64_t r = blockIdx.y; r < bs; r += gridDim.y)
+    C[((int64_t)bi * bs + r) * ldc + (int64_t)bj * bc + jj] = (TC)src[r * bc + jj];
+}
+
 struct Flip {
   int64_t row, col;
   int32_t bit, pad;
@@ -900,7 +936,45 @@ cudaError_t recover_t(const Plan& P, void* C, void* ws, int bj, const int* rows,
   return cudaGetLastError();
 }
 
+template <typename TC>
+cudaError_t block_partial_t(const Plan& P, const void* C, const void* ws, int skip, int bj,
+                            bool with_checksum, double* out, cudaStream_t st) {
+  const char* w = static_cast<const char*>(ws);
+  const double* S = with_checksum ? reinterpret_cast<const double*>(w + P.L.E) + 2 * P.nvr * P.d.n
+                                  : nullptr;
+  k_block_partial<TC><<<dim3((unsigned)cdiv(P.bc, kThreads), gy(P.bs)), kThreads, 0, st>>>(
+      static_cast<const TC*>(C), P.d.ldc, S, P.d.n, P.d.grid_p, P.bs, P.bc, bj, skip, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename TC>
+cudaError_t block_restore_t(const Plan& P, void* C, void* ws, int bi, int bj, const double* src,
+                            cudaStream_t st) {
+  CheckArgs a = make_args(P, C, ws);
+  k_block_store<TC><<<dim3((unsigned)cdiv(P.bc, kThreads), gy(P.bs)), kThreads, 0, st>>>(
+      static_cast<TC*>(C), P.d.ldc, src, P.bs, P.bc, bi, bj, a.timeout);
+  const int64_t I0 = ((int64_t)bi * P.bs) / P.d.vb_rows;
+  const int64_t I1 = cdiv(((int64_t)bi + 1) * P.bs, P.d.vb_rows);
+  k_col_check<TC><<<dim3((unsigned)cdiv(P.bc, kThreads), gy(I1 - I0)), kThreads, 0, st>>>(
+      a, (int64_t)bj * P.bc, ((int64_t)bj + 1) * P.bc, I0, I1, 1);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_block_partial(const Plan& P, const void* C, const void* ws, int skip, int bj,
+                                 bool with_checksum, double* out, cudaStream_t st) {
+  return P.d.dtype == ABFT_F64 ? block_partial_t<double>(P, C, ws, skip, bj, with_checksum, out, st)
+                               : block_partial_t<float>(P, C, ws, skip, bj, with_checksum, out, st);
+}
+
+cudaError_t launch_block_restore(const Plan& P, void* C, void* ws, int bi, int bj,
+                                 const double* src, cudaStream_t st) {
+  return P.d.dtype == ABFT_F64 ? block_restore_t<double>(P, C, ws, bi, bj, src, st)
+                               : block_restore_t<float>(P, C, ws, bi, bj, src, st);
+}
 
 cudaError_t launch_verify(const Plan& P, void* C, void* ws, const Erased& er, bool reread,
                           cudaStream_t st) {

@@ -305,15 +305,26 @@ def test_rate_1e9_epilogue_injection_seeded():
 def test_bounded_wait_timeout_is_reported(monkeypatch):
     """Failure detection without a GPU fault: with the test hook set, the producer of the
     single data tile never fills its stages, the MMA warp's bounded wait runs out (0.2 s),
-    the kernel drains and frees TMEM, and the next synchronising call reports
-    ABFT_ERR_TIMEOUT.  The context stays usable: the same problem then runs normally."""
+    the kernel drains and frees TMEM, and the verify on that workspace reports
+    ABFT_ERR_TIMEOUT (writing nothing into C) until the next product; a problem on
+    another workspace is not affected.  The context stays usable: the same problem then
+    runs normally."""
     r = Run(128, 256, 64, 128, 256, seed=61)  # 1 data tile + 1 checksum-row + 1 checksum-col tile
+    other = Run(256, 256, 128, 128, 256, seed=62)  # a problem on another workspace
     monkeypatch.setenv("ABFT_TEST_STALL_PRODUCER", "1")
     abft.abft_gemm(r.desc, r.A, r.B, r.C, r.ws)
     monkeypatch.delenv("ABFT_TEST_STALL_PRODUCER")
-    with pytest.raises(abft.AbftError) as e:
-        abft.abft_verify_correct(r.desc, r.C, r.ws)
-    assert e.value.status == abft.ERR_TIMEOUT
+    # the status belongs to r's workspace: the other problem verifies clean
+    abft.abft_gemm(other.desc, other.A, other.B, other.C, other.ws)
+    st, rep, nrep = abft.abft_verify_correct(other.desc, other.C, other.ws)
+    assert st == abft.OK and nrep == 0
+    torch.cuda.synchronize()
+    before = r.C.clone()
+    for _ in range(2):  # reported on every verify until the next product; C untouched
+        with pytest.raises(abft.AbftError) as e:
+            abft.abft_verify_correct(r.desc, r.C, r.ws)
+        assert e.value.status == abft.ERR_TIMEOUT
+        assert torch.equal(r.C.view(torch.int32), before.view(torch.int32))
     abft.abft_gemm(r.desc, r.A, r.B, r.C, r.ws)
     st, rep, nrep = abft.abft_verify_correct(r.desc, r.C, r.ws)
     assert st == abft.OK and nrep == 0

@@ -336,6 +336,9 @@ def run_workload(w, args, dev, rank, world, secondary=False):
     stream = torch.cuda.Stream(device=dev)
     C = torch.empty((w.m, w.n), dtype=torch.float32 if lp else torch.float64, device=dev)
     ws = torch.zeros(L.total, dtype=torch.uint8, device=dev)
+    # torch's side streams do not wait for its default stream, where the operands were
+    # drawn and the workspace zeroed
+    stream.wait_stream(torch.cuda.current_stream(dev))
     erased = []
     bs = w.m // w.p if w.p else 512
     if w.n_erased:
@@ -438,6 +441,7 @@ def run_workload(w, args, dev, rank, world, secondary=False):
         C_h = [torch.empty(C.shape, dtype=C.dtype).pin_memory() for _ in range(2)]
         A2, B2, C2 = torch.empty_like(A), torch.empty_like(B), torch.empty_like(C)
         ws2 = torch.zeros_like(ws)
+        stream.wait_stream(torch.cuda.current_stream(dev))
         if lp:  # the armed epilogue faults live in the workspace
             abft.abft_encode(desc, A, B, ws2, stream=stream, **scales)
             abft.abft_set_epilogue_faults(desc, ws2, flips, stream=stream)
@@ -564,6 +568,7 @@ def multi_erasure_leg(w, A, B, dev, stream, seed, f=2):
     L = abft.abft_workspace_layout(desc)
     ws = torch.zeros(L.total, dtype=torch.uint8, device=dev)
     C = torch.empty((w.m, w.n), dtype=torch.float64, device=dev)
+    stream.wait_stream(torch.cuda.current_stream(dev))
     abft.abft_encode(desc, A, B, ws, stream=stream)
     abft.abft_gemm(desc, A, B, C, ws, stream=stream)
     bs, bc = w.m // w.p, w.n // w.q
@@ -614,6 +619,7 @@ def run_grouped(w, args, dev, rank, world, secondary=False):
     stream = torch.cuda.Stream(device=dev)
     grp = abft.abft_group_create(probs, "bf16")
     ws = torch.zeros(abft.abft_group_workspace_bytes(grp), dtype=torch.uint8, device=dev)
+    stream.wait_stream(torch.cuda.current_stream(dev))  # operands and ws on the default stream
     abft.abft_group_bind(grp, ws, stream=stream)
     tuning, tune_ms = abft.abft_group_autotune(grp, reps=3, stream=stream)
     abft.abft_group_encode(grp, stream=stream)

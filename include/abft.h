@@ -17,7 +17,10 @@
  *    pointers are marked (host).  The library allocates no device memory per
  *    call.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
- *    Calls are stream-ordered and asynchronous unless stated otherwise.
+ *    Calls are stream-ordered and asynchronous unless stated otherwise: work
+ *    that produced the inputs or the workspace on another stream must be
+ *    ordered before the call by the caller (an event or a stream wait; a
+ *    non-blocking stream does not wait for the legacy default stream).
  *  - No C++ exception crosses the ABI.  Every call returns an abft_status; on a
  *    non-OK status abft_last_error() (thread-local) holds a one-line message.
  *    An invalid descriptor or argument returns ABFT_ERR_INVALID with nothing
@@ -44,6 +47,12 @@
  *  - ABFT_GROUP_M         raster group height in tile rows of single products
  *                         (default 2048 rows).
  *  - ABFT_TUNE_CACHE      file of grouped-product tunings (abft_group_autotune).
+ *  - ABFT_FP8_NATIVE      0: ABFT_FP8_E4M3 data tiles multiply the dequantised
+ *                         bf16 planes instead of the e4m3 codes (comparison
+ *                         only; an encode and its product must see the same
+ *                         value).
+ *  - ABFT_FP8_CS_STRIDE   position stride of the checksum tiles in the FP8
+ *                         product's tile order (default 1: all first).
  *  - ABFT_TEST_STALL_PRODUCER  1: the tensor-core product's producer skips its
  *                         first tile so its bounded waits run out (tests of
  *                         ABFT_ERR_TIMEOUT; never set in production).
@@ -148,6 +157,10 @@ typedef struct {
                                         abft_encode)                           */
   size_t scales;                     /* FP8: the block scales of A, then of B
                                         (binary32, copied by abft_encode)      */
+  size_t f8grp;                      /* FP8: scale groups of the product's data
+                                        tiles (written by abft_gemm)           */
+  size_t f8bt;                       /* FP8: B's e4m3 codes transposed (n rows
+                                        of ceil16(k) bytes, by abft_encode)    */
 } abft_ws_layout;
 
 /* Size of the caller-owned device workspace for `desc`.  Returns 0 for an
@@ -168,10 +181,13 @@ abft_status abft_workspace_layout(const abft_desc* desc, abft_ws_layout* out);
  * row-major), else NULL.  ABFT_FP8_E4M3: A and B are e4m3 bytes (lda, ldb in
  * elements); the scales must be powers of two, so that every dequantised value
  * e4m3(q) * scale is exact in bf16 -- the encode writes those values as bf16
- * operand planes into ws, forms the checksums from them and the product reads
- * them (a value that is not exact sets a status word of this workspace, and
- * abft_verify_correct on it returns ABFT_ERR_INVALID until the next encode).
- * Asynchronous. */
+ * operand planes into ws and forms the checksums from them (a value that is
+ * not exact sets a status word of this workspace, and abft_verify_correct on
+ * it returns ABFT_ERR_INVALID until the next encode).  When A and B have
+ * 16-byte aligned rows (base and lda, ldb multiples of 16) the encode also
+ * copies the scales, writes B's codes transposed (layout.f8bt) and the scale
+ * groups of the product's data tiles (layout.f8grp), for the product's FP8
+ * tensor-core data tiles.  Asynchronous. */
 abft_status abft_encode(const abft_desc* desc, const void* A, const void* B, const void* a_scale,
                         const void* b_scale, void* ws, void* stream);
 
@@ -235,9 +251,15 @@ abft_status abft_encode_chained(const abft_desc* desc, const void* A, const void
 
 /* The ABFT product (Eq. (1)): [A; C_C^T A] [B, B C_R] on the GPU.  Writes the
  * data block A B into C and the checksum blocks into ws (E and F).  Requires a
- * preceding abft_encode on the same ws and operands.  ABFT_BF16X3, ABFT_BF16X6
- * and ABFT_FP8_E4M3 multiply the bf16 operand planes that encode wrote (A, B and the
- * scales are not read again).  Asynchronous. */
+ * preceding abft_encode on the same ws and operands.  ABFT_BF16X3 and
+ * ABFT_BF16X6 multiply the bf16 operand planes that encode wrote.
+ * ABFT_FP8_E4M3: the data block multiplies the e4m3 codes of A and the
+ * transposed codes of B that encode wrote, on the 8-bit tensor path
+ * (tcgen05 kind::f8f6f4) with fp32 accumulation, each run of k-steps (128
+ * wide) with the same block-scale product in its own accumulator, scaled once
+ * by that power of two (exact); the checksum blocks multiply the bf16 planes.
+ * Without 16-byte aligned rows the data block multiplies the planes too.
+ * a_scale and b_scale are not read (the encode kept a copy).  Asynchronous. */
 abft_status abft_gemm(const abft_desc* desc, const void* A, const void* B, const void* a_scale,
                       const void* b_scale, void* C, void* ws, void* stream);
 
@@ -306,7 +328,7 @@ abft_status abft_recover_block(const abft_desc* desc, void* C, void* ws, int32_t
 /* Several erased blocks at once (section 2.1: with f block checksums, f lost
  * blocks of a block column follow from the checksums and the survivors).  The
  * grid carries grid_f block checksums S^(l) = sum_I c_{l,I} A_I (B), l < f, with
- * c_{l,I} = x_I^l, x_I = (I+1) / 2^e, 2^e > grid_p (distinct nodes: every
+ * c_{l,I} = x_I^l, x_I = (2I+1-grid_p) / 2^e, 2^e > grid_p (distinct nodes: every
  * f x f minor is nonsingular; l = 0 is the plain sum).  blocks: host (bi, bj)
  * pairs, n_blocks <= 16, each listed once; a block column with t erased blocks
  * solves, for every element position, the t x t system of its first t

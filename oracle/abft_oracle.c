@@ -94,13 +94,15 @@ void oracle_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
  * (section 2.1: f checksums with f independent weight vectors recover f lost
  * blocks; the paper draws them at random so that every f-by-f minor is
  * nonsingular).  Here: Vandermonde weights c_{l,I} = x_I^l with distinct
- * nodes x_I = (I+1) / 2^e, 2^e > p -- every f-by-f minor of a Vandermonde
- * matrix with distinct nodes is nonsingular, and the dyadic values are exact
- * in binary32 and binary64.  l = 0 is the plain sum (c = 1). */
+ * nodes x_I = (2I + 1 - p) / 2^e, 2^e > p, symmetric about 0 -- every
+ * f-by-f minor of a Vandermonde matrix with distinct nodes is nonsingular,
+ * the dyadic values are exact in binary32 and binary64, and centred nodes
+ * keep the systems of neighbouring blocks better conditioned than nodes in
+ * (0, 1).  l = 0 is the plain sum (c = 1). */
 double oracle_block_coef(int64_t l, int64_t I, int64_t p) {
   int e = 0;
   while (((int64_t)1 << e) <= p) ++e;
-  double x = ldexp((double)(I + 1), -e), c = 1.0;
+  double x = ldexp((double)(2 * I + 1 - p), -e), c = 1.0;
   for (int64_t t = 0; t < l; ++t) c *= x;
   return c;
 }

@@ -71,7 +71,8 @@ class WsLayout(ct.Structure):
                 ("inject", ct.c_size_t), ("fused", ct.c_int32), ("planes", ct.c_int32),
                 ("acs_plane", ct.c_size_t), ("bcs_plane", ct.c_size_t), ("op_a", ct.c_size_t),
                 ("op_b", ct.c_size_t), ("op_a_ld", ct.c_int64), ("op_b_ld", ct.c_int64),
-                ("car_a", ct.c_size_t), ("car_b", ct.c_size_t), ("scales", ct.c_size_t)]
+                ("car_a", ct.c_size_t), ("car_b", ct.c_size_t), ("scales", ct.c_size_t),
+                ("f8grp", ct.c_size_t), ("f8bt", ct.c_size_t)]
 
 
 class Problem(ct.Structure):

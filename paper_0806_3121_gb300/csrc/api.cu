@@ -178,6 +178,14 @@ abft_status make_plan(const abft_desc* d, Plan* P) {
   L.scales = region(f8 ? sizeof(float) * (size_t)(cdiv(d->m, 128) * cdiv(d->k, 128) +
                                                    cdiv(d->k, 128) * cdiv(d->n, 128))
                        : 0);
+  // FP8: the transposed copy B^T of the e4m3 codes (n x ceil16(k) bytes), the
+  // K-major B operand of the native data tiles
+  L.f8bt = region(f8 ? (size_t)d->n * (size_t)((d->k + 15) / 16 * 16) : 0);
+  // FP8: per data tile (128 x 256) one bit per 128-wide k-step, set where the
+  // block-scale product changes (the product's scale groups)
+  L.f8grp = region(f8 ? sizeof(uint32_t) * (size_t)(cdiv(d->m, 128) * cdiv(d->n, 256) *
+                                                     cdiv(cdiv(d->k, 128), 32))
+                      : 0);
   L.fused = p.fused;
   L.scratch = off;
   L.scratch_bytes = scratch_bytes(p);

@@ -1291,6 +1291,74 @@ cudaError_t launch_stream_B(const Units& U, cudaStream_t st, const Fp8Src& f8 = 
   return cudaGetLastError();
 }
 
+// B^T of the e4m3 codes (the K-major B operand of the product's native FP8
+// data tiles): B is k x n (ldb bytes, 16-byte aligned rows), Bt is n x ldbt
+// (ldbt = ceil16(k); the bytes past k are written as zero).  A CTA moves a
+// 128 x 128 byte tile: 16-byte row loads into shared memory (4-byte words,
+// the word column XOR-ed with 4 x (row / 16) so the transposing reads hit 32
+// distinct banks), then each thread transposes a 16 (k) x 4 (n) byte block in
+// registers (byte permutes) and stores four 16-byte pieces of rows of B^T
+// (eight threads cover 128 contiguous bytes of a row).  Grid (ceil(n/128),
+// min(ceil(ldbt/128), 65535)).
+__device__ __forceinline__ void transpose4x4(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3,
+                                             uint32_t (&o)[4]) {
+  const uint32_t lo01 = __byte_perm(r0, r1, 0x5140), hi01 = __byte_perm(r0, r1, 0x7362);
+  const uint32_t lo23 = __byte_perm(r2, r3, 0x5140), hi23 = __byte_perm(r2, r3, 0x7362);
+  o[0] = __byte_perm(lo01, lo23, 0x5410);
+  o[1] = __byte_perm(lo01, lo23, 0x7632);
+  o[2] = __byte_perm(hi01, hi23, 0x5410);
+  o[3] = __byte_perm(hi01, hi23, 0x7632);
+}
+
+__global__ void __launch_bounds__(256) k_transpose_u8(const uint8_t* __restrict__ B, int64_t ldb,
+                                                      int64_t k, int64_t n,
+                                                      uint8_t* __restrict__ Bt, int64_t ldbt) {
+  __shared__ __align__(16) uint32_t tile[128][32];
+  const int t = threadIdx.x;
+  const int kb = t & 7, w = t >> 3;  // transpose: k rows 16 kb .. +15, n bytes 4 w .. +3
+  const int64_t n0 = (int64_t)blockIdx.x * 128;
+  for (int64_t k0 = (int64_t)blockIdx.y * 128; k0 < ldbt; k0 += (int64_t)gridDim.y * 128) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = t + 256 * q, r = idx >> 3, c = (idx & 7) * 4;
+      const int64_t kk = k0 + r, nn = n0 + 4 * c;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (kk < k) {
+        if (nn + 16 <= n) {
+          v = *reinterpret_cast<const uint4*>(B + kk * ldb + nn);
+        } else {
+          uint32_t x[4] = {0u, 0u, 0u, 0u};
+          for (int i = 0; i < 16; ++i)
+            if (nn + i < n) x[i >> 2] |= (uint32_t)B[kk * ldb + nn + i] << (8 * (i & 3));
+          v = make_uint4(x[0], x[1], x[2], x[3]);
+        }
+      }
+      *reinterpret_cast<uint4*>(&tile[r][c ^ (((r >> 4) & 7) << 2)]) = v;
+    }
+    __syncthreads();
+    uint32_t o[4][4];  // o[j][q]: row n = 4 w + j of B^T, k bytes 16 kb + 4 q .. +3
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = 16 * kb + 4 * q, col = w ^ (kb << 2);
+      uint32_t x[4];
+      transpose4x4(tile[r][col], tile[r + 1][col], tile[r + 2][col], tile[r + 3][col], x);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) o[j][q] = x[j];
+    }
+    const int64_t ok = k0 + 16 * kb;
+    if (ok < ldbt) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t on = n0 + 4 * w + j;
+        if (on < n)
+          *reinterpret_cast<uint4*>(Bt + on * ldbt + ok) = make_uint4(o[j][0], o[j][1], o[j][2],
+                                                                      o[j][3]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Asynchronous copies need 16-byte aligned rows.
 bool rows_aligned(const void* p, int64_t ld) {
   return ((reinterpret_cast<uintptr_t>(p) & 15) == 0) && ld % 8 == 0;
@@ -1300,6 +1368,20 @@ bool rows_aligned(const void* p, int64_t ld) {
 int64_t align_elems(int64_t elems) { return (elems * 2 + 255) / 256 * 128; }
 
 }  // namespace
+
+// Native FP8 data tiles (the e4m3 codes on the 8-bit tensor path) unless the
+// environment variable ABFT_FP8_NATIVE is 0, which multiplies the dequantised
+// bf16 planes instead (for comparison; the encode and the product of a
+// workspace must see the same setting).
+static bool fp8_native() {
+  const char* env = getenv("ABFT_FP8_NATIVE");
+  return !(env && env[0] == '0');
+}
+
+// A byte matrix whose base and row pitch are 16-byte multiples (TMA rows).
+static bool aligned16(const void* p, int64_t ld_bytes) {
+  return p && ((reinterpret_cast<uintptr_t>(p) & 15) == 0) && ld_bytes % 16 == 0;
+}
 
 // Scratch of the tensor-core encode, carved from the workspace's partial-sum
 // region: checksum-norm partials (binary64), then per-row and per-column
@@ -1404,6 +1486,19 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, cons
       e = cudaMemcpyAsync(w + P.L.scales + sizeof(float) * nsa, b_scale, sizeof(float) * nsb,
                           cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
+    // B^T of the codes and the scale groups of the data tiles, for the
+    // product's native data tiles (K-major B)
+    if (fp8_native() && aligned16(Av, d.lda) && aligned16(Bv, d.ldb)) {
+      const float* ws_sa = reinterpret_cast<const float*>(w + P.L.scales);
+      e = launch_f8_groups(ws_sa, ws_sa + nsa, d.m, d.n, d.k,
+                           reinterpret_cast<uint32_t*>(w + P.L.f8grp), st);
+      if (e != cudaSuccess) return e;
+      const int64_t ldbt = (d.k + 15) / 16 * 16;
+      k_transpose_u8<<<dim3((unsigned)cdiv(d.n, 128), gy(cdiv(ldbt, 128))), 256, 0, st>>>(
+          static_cast<const uint8_t*>(Bv), d.ldb, d.k, d.n,
+          reinterpret_cast<uint8_t*>(w + P.L.f8bt), ldbt);
+      ++nlaunch;
+    }
     auto* pa = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_a);
     auto* pb = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_b);
     const auto* qa = static_cast<const uint8_t*>(Av);
@@ -1563,19 +1658,6 @@ cudaError_t launch_encode_lp_chained(const Plan& P, const void* Av, const void* 
   return cudaGetLastError();
 }
 
-// Native FP8 data tiles (the e4m3 codes on the 8-bit tensor path) when the
-// environment variable ABFT_FP8_NATIVE is 1; otherwise the data tiles multiply
-// the dequantised bf16 planes.
-static bool fp8_native() {
-  const char* env = getenv("ABFT_FP8_NATIVE");
-  return env && env[0] == '1';
-}
-
-// A byte matrix whose base and row pitch are 16-byte multiples (TMA rows).
-static bool aligned16(const void* p, int64_t ld_bytes) {
-  return p && ((reinterpret_cast<uintptr_t>(p) & 15) == 0) && ld_bytes % 16 == 0;
-}
-
 cudaError_t launch_gemm_lp(const Plan& P, const void* A, const void* B, float* C, void* ws,
                            bool checksums, cudaStream_t st) {
   const abft_desc& d = P.d;
@@ -1622,11 +1704,12 @@ cudaError_t launch_gemm_lp(const Plan& P, const void* A, const void* B, float* C
     op.nseg = 1;
     if (fp8_native() && aligned16(A, d.lda) && aligned16(B, d.ldb)) {
       op.a8 = A;
-      op.b8 = B;
+      op.b8 = w + P.L.f8bt;  // B^T, written by the encode
       op.lda8 = d.lda;
-      op.ldb8 = d.ldb;
+      op.ldb8 = (d.k + 15) / 16 * 16;
       op.sA = reinterpret_cast<const float*>(w + P.L.scales);
       op.sB = op.sA + cdiv(d.m, 128) * cdiv(d.k, 128);
+      op.f8grp = reinterpret_cast<uint32_t*>(w + P.L.f8grp);
     }
   } else {
     op.a[0] = op.a[1] = op.a[2] = A;

@@ -61,10 +61,9 @@ constexpr uint32_t HALF_BYTES = 64 * BK * 2;       // one 64-row half of A: 8 Ki
 constexpr uint32_t B_BOX_BYTES = 64 * BK * 2;      // one 64-column box: 8 KiB
 constexpr uint32_t B_BYTES = BN * BK * 2;          // 32 KiB
 // FP8 data tiles: a k-step is 128 e4m3 codes (the same 128 bytes per row as a
-// bf16 k-step, so the stage layout is unchanged) and a B box is 128 columns x
-// 128 k-rows (16 KiB; two per 256-column tile)
+// bf16 k-step, so the stage layout is unchanged); B is read K-major from its
+// transposed copy, 64 columns of C (64 rows of B^T, 8 KiB) per box
 constexpr int BK8 = 128;
-constexpr uint32_t B8_BOX_BYTES = 128 * BK8;
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t TMEM_COLS = 2 * BN;             // two accumulators
 constexpr uint32_t STG_BYTES = 32 * 32 * 4;        // one epilogue warp's staging block
@@ -97,14 +96,17 @@ static_assert(Geo<true>::kBM / 128 * BN <= (int)TMEM_COLS, "tall accumulators fi
 // planes; unused planes repeat plane 0).  The K loop runs nseg segments;
 // segment s reads A plane (seg_a >> 2s) & 3 and B plane (seg_b >> 2s) & 3.
 constexpr int kPlanes = 3;
+// Native FP8 data tiles read the e4m3 codes, both K-major: A as 64-row halves
+// (a[kF8Slot]) and 128-row boxes (a128[kF8Slot]) of 128 codes, B's transposed
+// copy B^T (n x k) as 64-row boxes (b[kF8Slot]) and the 256-row box of a full
+// tile (b4[kF8Slot]).  They take the plane-1 slots, which an FP8 product does
+// not use (its checksum tiles read plane 0), so the kernel parameters stay
+// within 4 KiB.
+constexpr int kF8Slot = 1;
 struct TcMaps {
   CUtensorMap a[kPlanes], acs[kPlanes], b[kPlanes], bcs[kPlanes], a128[kPlanes],
       acs128[kPlanes], b4[kPlanes], bcs4[kPlanes];
   CUtensorMap cst, est, fst;  // fp32 store maps of C, E16, F16 (valid per TcArgs::st_ok)
-  // e4m3 codes of the data operands (native FP8 data tiles): A as 64-row halves
-  // and 128-row boxes of 128 codes, B as 128-column N-major boxes of 128 k-rows
-  // (one box or, in the 3-D view, both boxes of a 256-column tile)
-  CUtensorMap a8, a8_128, b8, b8w;
 };
 
 struct TcArgs {
@@ -137,7 +139,19 @@ struct TcArgs {
   const float* sA;           // ceil(m/128) x nsa
   const float* sB;           // ceil(k/128) x nsb
   int64_t nsa, nsb;
+  // scale groups of every data tile: bit kb of its f8words words is set when
+  // k-step kb starts a new group (the block-scale product of either 128-column
+  // half of the tile differs from k-step kb - 1's); a group accumulates in one
+  // TMEM accumulator and is scaled once
+  const uint32_t* f8grp;
+  int64_t f8words;
+  int64_t cs_stride;         // FP8 tile order: checksum tile c at position c * cs_stride
 };
+
+// The product kernel's parameters (tensor maps and arguments, passed by value
+// as __grid_constant__ and copied at every launch) stay within the classic
+// 4 KiB parameter space.
+static_assert(sizeof(TcMaps) + sizeof(TcArgs) <= 4096, "kernel parameters within 4 KiB");
 
 struct Tile {
   int kind;  // 0 data -> C, 1 checksum rows -> E16, 2 checksum columns -> F16
@@ -186,6 +200,38 @@ __device__ __forceinline__ Tile decode_local(int64_t t, int64_t ntm, int64_t ntn
   return T;
 }
 
+// Tile order of products with native FP8 data tiles: their checksum tiles run
+// on the bf16 planes (twice as long per tile, sharing no operand with the data
+// tiles, so their panels come from DRAM), so they are spread through the
+// first part of the schedule: checksum tile c (the checksum-row tiles first,
+// the two of a tile column back to back, then the checksum-column tiles) sits
+// at flat position c * S, the data tiles fill the other positions in the
+// grouped raster of the data alone.  S is coprime with the grid, so the
+// round-robin assignment gives every CTA at most ceil(checksum tiles / grid)
+// of them, at different times (S = 1: all checksum tiles first).
+__device__ __forceinline__ Tile decode_cs_spread(int64_t t, int64_t ntm, int64_t ntn, int64_t ntr,
+                                                 int64_t ntc, int64_t GROUP_M, int64_t bm,
+                                                 int64_t S) {
+  const int64_t n1 = ntr * ntn, n2 = ntm * ntc, ncs = n1 + n2;
+  if (t % S == 0 && t / S < ncs) {
+    const int64_t c = t / S;
+    Tile T;
+    if (c < n1) {
+      T.kind = 1;
+      T.row0 = (c % ntr) * bm;
+      T.col0 = (c / ntr) * BN;
+    } else {
+      const int64_t u = c - n1;
+      T.kind = 2;
+      T.row0 = (u % ntm) * bm;
+      T.col0 = (u / ntm) * BN;
+    }
+    return T;
+  }
+  const int64_t before = min(ncs, t / S + 1);  // checksum positions at or before t
+  return decode_local(t - before, ntm, ntn, 0, 0, GROUP_M, bm);
+}
+
 __device__ __forceinline__ int64_t clamp64(int64_t v, int64_t lo, int64_t hi) {
   return v < lo ? lo : (v > hi ? hi : v);
 }
@@ -211,6 +257,14 @@ struct TileView {
   const CUtensorMap* mbC;
   int32_t rowD, rowC, colD, colC;
   int hsplit, hcnt, bsplit, nbox;
+  int nmma;                   // MMA N: 64 nbox, or less when the last box is a checksum
+                              // box with fewer used columns (see mma_cols)
+  // swapped checksum-row tile (grouped products, kGrpSwapTile): E16 columns
+  // colW .. colW + 255 as the M side of two M = 128 MMAs (four B boxes from mbW
+  // / mbD, in the B region), the R16 checksum rows as their N side (nsw_h
+  // 64-row halves of acs from maC, in the A region), MMA N = nsw_n <= 128; the
+  // epilogue stores the accumulators transposed into E16
+  int swap, nsw_h, nsw_n;
   // one-copy loads: A as nA128 128-row boxes (maW, rows rowW + 128 i) and
   // full B boxes (mbW: 3-D map at box index colW / 64); nullptr: per half / box
   const CUtensorMap* maW;     // (plane p at + p)
@@ -238,7 +292,35 @@ struct TileView {
   const float* sArow;
   const float* sB;
   int64_t nsb;
+  const uint32_t* gmask;      // this tile's scale-group words (see TcArgs::f8grp)
 };
+
+// End of the scale group that starts at k-step kb: the next k-step whose bit is
+// set in the tile's group words, or nkt.
+__device__ __forceinline__ int64_t group_end(const uint32_t* mask, int64_t kb, int64_t nkt) {
+  int64_t x = kb + 1;
+  while (x < nkt) {
+    const uint32_t w = __ldg(&mask[x >> 5]) >> (x & 31);
+    if (w) {
+      const int64_t e = x + __ffs(w) - 1;
+      return e < nkt ? e : nkt;
+    }
+    x = (x | 31) + 1;
+  }
+  return nkt;
+}
+
+// MMA N of a tile: its boxes are 64 columns wide, but when the last one is a
+// checksum box (bsplit < nbox) only its columns below the checksum width C16
+// are used, so N stops at the first multiple of 16 past them.  The TMEM columns
+// beyond N are never stored (checksum columns >= C16) and no fused sum reads
+// checksum columns.
+__device__ __forceinline__ int mma_cols(int nbox, int bsplit, int64_t colC, int64_t C16) {
+  if (bsplit >= nbox) return 64 * nbox;
+  const int64_t first = colC + 64 * (nbox - 1 - bsplit);  // first column of the last box
+  const int64_t used = C16 - first < 64 ? C16 - first : 64;
+  return 64 * (nbox - 1) + (used > 0 ? (int)((used + 15) / 16 * 16) : 64);
+}
 
 // One problem (abft_gemm), tiles of kBM rows (128 or 256).
 template <int kBM>
@@ -258,7 +340,9 @@ struct SingleSched {
   }
   __device__ __forceinline__ TileView view(int64_t t) const {
     const TcArgs& g = *a;
-    const Tile T = decode_local(t, g.ntm, g.ntn, g.ntr, g.ntc, g.group_m, kBM);
+    const Tile T = g.f8 ? decode_cs_spread(t, g.ntm, g.ntn, g.ntr, g.ntc, g.group_m, kBM,
+                                           g.cs_stride)
+                        : decode_local(t, g.ntm, g.ntn, g.ntr, g.ntc, g.group_m, kBM);
     TileView V;
     V.prob = 0;
     V.nkb = (g.k + BK - 1) / BK;
@@ -279,6 +363,8 @@ struct SingleSched {
     V.hcnt = hrows;
     V.bsplit = T.kind == 2 ? 0 : bcols;
     V.nbox = bcols;
+    V.nmma = mma_cols(V.nbox, V.bsplit, T.col0, g.C16);
+    V.swap = V.nsw_h = V.nsw_n = 0;
     V.maW = V.mbW = nullptr;
     V.rowW = (int32_t)T.row0;
     V.colW = (int32_t)T.col0;
@@ -292,15 +378,17 @@ struct SingleSched {
     V.sArow = nullptr;
     V.sB = g.sB;
     V.nsb = g.nsb;
-    if (V.f8) {  // data tile on the e4m3 codes: 128-wide k-steps, promoted each step
+    V.gmask = nullptr;
+    if (V.f8) {  // data tile on the e4m3 codes: 128-wide k-steps in scale groups
       V.nkb = (g.k + 127) / 128;
       V.nseg = 1;
-      V.kpg = 1;
+      V.kpg = 0;
+      V.gmask = g.f8grp + ((T.row0 / 128) * g.ntn + T.col0 / 256) * g.f8words;
       V.seg_a = V.seg_b = 0;
-      V.maD = &M->a8;
-      V.mbD = &M->b8;
-      V.maW = V.nA128 ? &M->a8_128 : nullptr;
-      V.mbW = (bcols == 4 && T.col0 + 256 <= (g.n / 128) * 128) ? &M->b8w : nullptr;
+      V.maD = &M->a[kF8Slot];
+      V.mbD = &M->b[kF8Slot];
+      V.maW = V.nA128 ? &M->a128[kF8Slot] : nullptr;
+      V.mbW = (bcols == 4 && T.col0 + 256 <= g.n) ? &M->b4[kF8Slot] : nullptr;
       V.sArow = g.sA + (T.row0 / 128) * g.nsa;
     }
     V.C = g.C;
@@ -431,12 +519,11 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
         const TileView T = S.view(t);
         if (stall_test && t == 0) continue;  // nothing will fill these stages
         const int64_t nkb = T.nkb, nkt = T.nkb * T.nseg;
-        // an FP8 data tile's k-step is 128 codes (128 bytes, as a bf16 k-step) and
-        // its B boxes are 128 columns wide
-        const int nb8 = (T.nbox + 1) / 2;
-        const uint32_t tx = pA ? (uint32_t)T.hcnt * HALF_BYTES
-                               : (T.f8 ? (uint32_t)nb8 * B8_BOX_BYTES
-                                       : (uint32_t)T.nbox * B_BOX_BYTES);
+        // an FP8 data tile's k-step is 128 codes (128 bytes, as a bf16 k-step);
+        // its B boxes hold 64 rows of B^T (8 KiB, as a bf16 box)
+        const uint32_t tx = T.swap ? (pA ? (uint32_t)T.nsw_h * HALF_BYTES : 4 * B_BOX_BYTES)
+                                   : pA ? (uint32_t)T.hcnt * HALF_BYTES
+                                        : (uint32_t)T.nbox * B_BOX_BYTES;
         const int bkx = T.f8 ? BK8 : BK;
         // a stage's MMAs take ~700 cycles: the per-stage bookkeeping is
         // incremental (no division per stage)
@@ -447,14 +534,28 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
           if (!tc::wait(empty(s), ph ^ 1, abort)) break;
           const uint32_t sa = tc::smem_addr(smem + s * G::kStageBytes);
           tc::mbar_arrive_expect_tx(full(s), tx);
-          if (!pA && T.f8) {
-            // e4m3 B: both 128-column boxes in one 3-D copy, else box by box
-            if (T.mbW) {
-              tc::tma_load_3d(sa + G::kABytes, T.mbW, full(s), 0, kx, T.colW / 128);
+          if (T.swap) {
+            // swapped checksum-row tile: the A region takes the checksum rows'
+            // halves (the N side), the B region four B boxes (the M side)
+            if (pA) {
+              for (int h = 0; h < T.nsw_h; ++h)
+                tc::tma_load_2d(sa + h * HALF_BYTES, T.maC, full(s), kx, 64 * h);
+            } else if (T.mbW) {
+              tc::tma_load_3d(sa + G::kABytes, T.mbW, full(s), 0, kx, T.colW / 64);
             } else {
-              for (int b = 0; b < nb8; ++b)
-                tc::tma_load_2d(sa + G::kABytes + b * B8_BOX_BYTES, T.mbD, full(s),
-                                T.colD + 128 * b, kx);
+              for (int b = 0; b < 4; ++b)
+                tc::tma_load_2d(sa + G::kABytes + b * B_BOX_BYTES, T.mbD, full(s), T.colW + 64 * b,
+                                kx);
+            }
+          } else if (!pA && T.f8) {
+            // e4m3 B^T (K-major): the 256 rows of a full tile in one copy, else
+            // 64 rows per box
+            if (T.mbW) {
+              tc::tma_load_2d(sa + G::kABytes, T.mbW, full(s), kx, T.colW);
+            } else {
+              for (int b = 0; b < T.nbox; ++b)
+                tc::tma_load_2d(sa + G::kABytes + b * B_BOX_BYTES, T.mbD, full(s), kx,
+                                T.colD + 64 * b);
             }
           } else if (!pA) {
             // B: the full boxes in one 3-D copy, the rest (ragged, checksum) per box
@@ -507,13 +608,16 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
       for (int64_t t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
         const TileView T = S.view(t);
         const int64_t nkt = T.nkb * T.nseg;
-        const int64_t gsz = (kPromote && T.kpg > 0 && (T.kpg < nkt || T.f8)) ? T.kpg : nkt;
-        const uint32_t idesc = T.f8 ? tc::idesc_e4m3(BM, 64 * T.nbox, 1)
-                                    : tc::idesc_bf16(BM, 64 * T.nbox, 1);
+        const int64_t gsz = (kPromote && T.kpg > 0 && T.kpg < nkt) ? T.kpg : nkt;
+        const bool f8t = kF8 && T.f8;
+        const uint32_t idesc = f8t ? tc::idesc_e4m3(BM, T.nmma, 0)
+                                   : tc::idesc_bf16(BM, T.nmma, 1);
         bool ok = true;
-        // one accumulator per promotion group; the epilogue adds the groups
-        for (int64_t g0 = 0; g0 < nkt && ok; g0 += gsz) {
-          const int64_t g1 = min(g0 + gsz, nkt);
+        // one accumulator per promotion group (FP8 data tiles: per scale
+        // group); the epilogue adds the groups
+        int64_t g1 = 0;
+        for (int64_t g0 = 0; g0 < nkt && ok; g0 = g1) {
+          g1 = f8t ? group_end(T.gmask, g0, nkt) : min(g0 + gsz, nkt);
           if (!tc::wait(tempty(acc), aph ^ 1, abort)) { ok = false; break; }
           tc::fence_after_sync();
           const uint32_t d = tmem + acc * BN;
@@ -524,14 +628,32 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
             tc::fence_after_sync();
             const uint32_t sa = tc::smem_addr(smem + s * G::kStageBytes);
             const uint32_t sb = sa + G::kABytes;
-            if (kF8 && T.f8) {
-              // e4m3: K = 32 codes per MMA.  A: K-major 128-byte rows, a K step
-              // moves 32 B inside the swizzled row.  B: N-major, 128-column
-              // boxes 16 KiB apart, 8-row (K) groups 1024 B apart, a K step of
-              // 32 rows moves 4 KiB.
+            if (T.swap) {
+              // swapped tile: two MMAs per K step, MN-major A = two B boxes each
+              // (64-column atoms 8 KiB apart, 8-row K groups 1024 B apart, a K
+              // step of 16 rows moves 2 KiB) into accumulator columns 0 and
+              // 128, K-major B = the checksum rows in the A region
+              const uint32_t idesc_sw = tc::idesc_bf16_mn_a(BM, T.nsw_n);
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; ++kk) {
+                const uint64_t bd = tc::sdesc_sw128(sa + kk * 32, 16, 1024);
+                for (int h2 = 0; h2 < 2; ++h2) {
+                  const uint64_t ad =
+                      tc::sdesc_sw128(sb + h2 * (2 * B_BOX_BYTES) + kk * 2048, B_BOX_BYTES, 1024);
+                  tc::mma_f16(d + h2 * 128, ad, bd, idesc_sw, (kb > g0 || kk > 0) ? 1u : 0u);
+                }
+              }
+              tc::commit(empty(s));
+              if (++s == NS) { s = 0; ph ^= 1; }
+              continue;
+            }
+            if (f8t) {
+              // e4m3: K = 32 codes per MMA.  A and B^T: K-major 128-byte rows in
+              // 8-row groups 1024 B apart; a K step moves 32 B inside the
+              // swizzled rows.
 #pragma unroll
               for (int kk = 0; kk < BK8 / 32; ++kk) {
-                const uint64_t bd = tc::sdesc_sw128(sb + kk * 4096, B8_BOX_BYTES, 1024);
+                const uint64_t bd = tc::sdesc_sw128(sb + kk * 32, 16, 1024);
                 const uint64_t ad = tc::sdesc_sw128(sa + kk * 32, 16, 1024);
                 tc::mma_f8(d, ad, bd, idesc, (kb > g0 || kk > 0) ? 1u : 0u);
               }
@@ -590,8 +712,53 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
     bool aborted = false;
     for (int64_t t = blockIdx.x; t < total && !aborted; t += gridDim.x) {
       const TileView T = S.view(t);
+      if (T.swap) {
+        // swapped checksum-row tile: this warp's half h of the tile (columns
+        // colW + 128 h ..) sits in accumulator columns 128 h .., TMEM lane
+        // quarter q holds columns + 32 q .., lane = column j of E16 and
+        // accumulator column 128 h + r = checksum row r; each store instruction
+        // writes one row r for 32 consecutive columns
+        if (!tc::wait(tfull(acc), aph, abort)) break;
+        tc::fence_after_sync();
+        const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + acc * BN + c_lo;
+        const int nchs = (T.nsw_n + 31) / 32;
+        const int64_t j = T.colW + c_lo + 32 * q + lane;
+        for (int ci = 0; ci < nchs; ++ci) {
+          float v[32];
+          tc::tmem_ld32(base + 32 * ci, v);
+          if (ci == nchs - 1) {
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(tempty(acc));
+            if (++acc == G::kSlots) { acc = 0; aph ^= 1; }
+          }
+          if (j < T.n) {
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+              const int64_t r = 32 * ci + u;
+              if (r < T.R16) T.E16[r * T.n + j] = v[u];
+            }
+          }
+        }
+        if (nchs <= 0) {
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(tempty(acc));
+          if (++acc == G::kSlots) { acc = 0; aph ^= 1; }
+        }
+        continue;
+      }
       const int64_t nkt = T.nkb * T.nseg;
-      const int64_t gsz = (kPromote && T.kpg > 0 && (T.kpg < nkt || T.f8)) ? T.kpg : nkt;
+      const int64_t gsz = (kPromote && T.kpg > 0 && T.kpg < nkt) ? T.kpg : nkt;
+      const bool f8t = kF8 && T.f8;
+      const bool one_group = f8t ? group_end(T.gmask, 0, nkt) >= nkt : gsz >= nkt;
+      // FP8 data tiles: this warp's 128 columns are one column block of B's
+      // scales; the partial of a scale group is multiplied by its (power-of-two,
+      // so exact) block-scale product
+      const int64_t jb = f8t ? (T.colD + c_lo) / 128 : 0;
+      auto f8scale = [&](int64_t kb) {
+        return __ldg(&T.sArow[kb]) * __ldg(&T.sB[kb * T.nsb + jb]);
+      };
       const int ncol = 64 * T.nbox;
       const int c_hi = min(c_lo + G::kCols, ncol);
       // this warp's 32 rows: data rows, checksum rows or none
@@ -754,16 +921,21 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
           }
         }
       };
-      if (!kPromote || (gsz >= nkt && !T.f8)) {
+      if (!kPromote || one_group) {
         // one accumulator: each chunk is read and finished in turn; the
         // accumulator is released after the last read
         if (!tc::wait(tfull(acc), aph, abort)) break;
         tc::fence_after_sync();
         const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (acc + ta) * BN;
         const int nch = (c_hi - c_lo + 31) / 32;
+        const float sc1 = (f8t && nch > 0) ? f8scale(0) : 1.0f;
         for (int ci = 0; ci < nch; ++ci) {
           float v[32];
           tc::tmem_ld32(base + c_lo + 32 * ci, v);
+          if (f8t) {
+#pragma unroll
+            for (int u = 0; u < 32; ++u) v[u] *= sc1;
+          }
           if (ci == nch - 1) {
             tc::fence_before_sync();
             __syncwarp();
@@ -784,16 +956,15 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
         // groups in fp32 registers (round to nearest), each accumulator
         // released as soon as it is read
         float accr[kEpiChunks][32];
-        // FP8 data tiles: each k-step's partial times its block scales (powers of
-        // two, so the product is exact); this warp's 128 columns are one column
-        // block of B's scales.  The next step's scale is loaded ahead.
-        const bool scaled = kF8 && T.f8 && c_lo < c_hi;
-        const int64_t jb = scaled ? (T.colD + c_lo) / 128 : 0;
-        float sc_next = scaled ? __ldg(&T.sArow[0]) * __ldg(&T.sB[jb]) : 1.0f;
-        for (int64_t g0 = 0; g0 < nkt; g0 += gsz) {
+        // FP8 data tiles: each scale group's partial times its block scales;
+        // the next group's scale is loaded ahead
+        const bool scaled = f8t && c_lo < c_hi;
+        float sc_next = scaled ? f8scale(0) : 1.0f;
+        int64_t g1 = 0;
+        for (int64_t g0 = 0; g0 < nkt; g0 = g1) {
+          g1 = f8t ? group_end(T.gmask, g0, nkt) : min(g0 + gsz, nkt);
           const float sc = sc_next;
-          if (scaled && g0 + 1 < nkt)
-            sc_next = __ldg(&T.sArow[g0 + 1]) * __ldg(&T.sB[(g0 + 1) * T.nsb + jb]);
+          if (scaled && g1 < nkt) sc_next = f8scale(g1);
           if (!tc::wait(tfull(acc), aph, abort)) { aborted = true; break; }
           tc::fence_after_sync();
           const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
@@ -875,7 +1046,7 @@ struct GroupSched {
     const GProb& P = probs[e.x];
     const GMaps& Mp = maps[e.x];
     const int nhd = (int)cdiv(P.m, 64), nbd = (int)cdiv(P.n, 64);
-    const int nhc = checksums ? P.nhc : 0, nbc = checksums ? P.nbc : 0;
+    const int nhc = checksums && !P.swap_rows ? P.nhc : 0, nbc = checksums ? P.nbc : 0;
     const int h0 = 2 * e.y, b0 = P.bpt * e.z;
     TileView V;
     V.prob = e.x;
@@ -895,6 +1066,8 @@ struct GroupSched {
     V.rowC = 64 * max(0, h0 - nhd);
     V.colD = 64 * b0;
     V.colC = 64 * max(0, b0 - nbd);
+    V.nmma = mma_cols(V.nbox, V.bsplit, V.colC, P.C16);
+    V.swap = V.nsw_h = V.nsw_n = 0;
     V.maW = V.mbW = nullptr;
     V.nA128 = 1;
     if (V.hsplit == 2) {
@@ -936,6 +1109,18 @@ struct GroupSched {
     V.sArow = nullptr;
     V.sB = nullptr;
     V.nsb = 0;
+    V.gmask = nullptr;
+    if (e.w == kGrpSwapTile) {  // E16 columns 256 e.z .. + 255 from the swapped operands
+      V.swap = 1;
+      V.nsw_h = (int)cdiv(P.R16, 64);
+      V.nsw_n = (int)cdiv(P.R16, 16) * 16;
+      V.colW = 256 * e.z;
+      V.mbD = &Mp.b;
+      V.mbW = V.colW + 256 <= (int32_t)((P.n / 64) * 64) ? &Mp.bw[2] : nullptr;
+      V.maC = &Mp.acs;
+      V.hsplit = V.hcnt = V.bsplit = V.nbox = 0;
+      V.obs_col = nullptr;
+    }
     return V;
   }
 };
@@ -947,6 +1132,45 @@ __global__ void __launch_bounds__(kThreads, 1)
   const GroupSched S{probs, maps, tiles, t_total, checksums != 0, kpg};
   tc_body<false, false, false>(S, status, wait_ns, 0, inj_hdr, inj);
 }
+
+// Scale groups of the FP8 data tiles (see TcArgs::f8grp): one thread per word
+// of one tile (tile row I of 128 rows, tile column Jt of 256 columns = scale
+// column blocks 2 Jt and 2 Jt + 1).  The products compare exactly in binary64.
+__global__ void k_f8_groups(const float* __restrict__ sA, const float* __restrict__ sB,
+                            int64_t nsa, int64_t nsb, int64_t ntm, int64_t ntn, int64_t nkb,
+                            int64_t words, uint32_t* __restrict__ out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ntm * ntn * words) return;
+  const int64_t w = idx % words, t = idx / words, Jt = t % ntn, I = t / ntn;
+  const int64_t J0 = 2 * Jt, J1 = 2 * Jt + 1;
+  uint32_t bits = 0;
+  for (int b = 0; b < 32; ++b) {
+    const int64_t kb = w * 32 + b;
+    if (kb < 1 || kb >= nkb) continue;
+    const double a1 = sA[I * nsa + kb], a0 = sA[I * nsa + kb - 1];
+    bool diff = a1 * (double)sB[kb * nsb + J0] != a0 * (double)sB[(kb - 1) * nsb + J0];
+    if (J1 < nsb) diff |= a1 * (double)sB[kb * nsb + J1] != a0 * (double)sB[(kb - 1) * nsb + J1];
+    if (diff) bits |= 1u << b;
+  }
+  out[idx] = bits;
+}
+
+}  // namespace
+
+// The scale-group words of every data tile of an FP8 product (run by the
+// encode, which copies the scales; the product only reads them).
+cudaError_t launch_f8_groups(const float* sA, const float* sB, int64_t m, int64_t n, int64_t k,
+                             uint32_t* out, cudaStream_t st) {
+  const int64_t words = cdiv(cdiv(k, 128), 32), ntm = cdiv(m, BM), ntn = cdiv(n, BN);
+  const int64_t nw = ntm * ntn * words;
+  if (nw == 0) return cudaSuccess;
+  k_f8_groups<<<(unsigned)cdiv(nw, 256), 256, 0, st>>>(sA, sB, cdiv(k, 128), cdiv(n, 128), ntm,
+                                                       ntn, cdiv(k, 128), words, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+namespace {
 
 // ---- host side
 PFN_cuTensorMapEncodeTiled_v12000 g_encode_tiled = nullptr;
@@ -1024,11 +1248,8 @@ bool make_map_boxes(CUtensorMap* map, const void* ptr, int64_t rows, int64_t col
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// e4m3 (byte) maps of the native FP8 data tiles.  2-D: a row-major rows x cols
-// byte matrix with leading dimension ld, box box_cols x box_rows, 128-byte
-// swizzle.  3-D: the (128 columns, rows, column box) view of B with a box of
-// both 128-column boxes of a 256-column tile (only the cols / 128 full boxes
-// are inside the view).
+// e4m3 (byte) map of the native FP8 data tiles: a row-major rows x cols byte
+// matrix with leading dimension ld, box box_cols x box_rows, 128-byte swizzle.
 bool make_map_u8(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols, int64_t ld,
                  uint32_t box_cols, uint32_t box_rows) {
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
@@ -1036,19 +1257,6 @@ bool make_map_u8(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols, 
   const cuuint32_t box[2] = {box_cols, box_rows};
   const cuuint32_t estr[2] = {1, 1};
   return g_encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(ptr), dims,
-                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-bool make_map_boxes_u8(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols,
-                       int64_t ld) {
-  int64_t nb = cols / 128;
-  if (nb == 0) nb = 1;  // never read (no full box): a dummy valid view
-  const cuuint64_t dims[3] = {128, (cuuint64_t)rows, (cuuint64_t)nb};
-  const cuuint64_t strides[2] = {(cuuint64_t)ld, 128};
-  const cuuint32_t box[3] = {128, (cuuint32_t)BK8, 2};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  return g_encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(ptr), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -1089,6 +1297,31 @@ bool use_tall(int64_t m, int64_t nkt, int kpg) {
   const char* env = getenv("ABFT_TALL_TILES");
   if (env && *env) return env[0] == '1';
   return m > BM && nkt >= 32;
+}
+
+// Stride of the checksum tiles in the FP8 tile order.  Measured at FP8 16384^3:
+// all checksum tiles first (S = 1) 3.18 ms per ABFT product, S = 2 / 3 / 5
+// 3.28-3.38 ms, spread over the first 65 % of the schedule 3.35 ms (their
+// bf16-plane panels then evict the data tiles' panels from L2).  So S = 1;
+// ABFT_FP8_CS_STRIDE sets another stride, and ABFT_FP8_CS_STRIDE=spread the
+// spread order (coprime with the grid, every CTA at most ceil(checksum
+// tiles / grid) of them).
+int64_t cs_stride(int64_t ncs, int64_t total, int grid) {
+  const char* env = getenv("ABFT_FP8_CS_STRIDE");
+  if (!(env && *env)) return 1;
+  if (env[0] != 's') return std::max<int64_t>(1, atoll(env));
+  if (ncs <= 0) return 1;
+  int64_t S = std::max<int64_t>(1, (total * 65 / 100) / ncs);
+  auto gcd = [](int64_t a, int64_t b) {
+    while (b) {
+      const int64_t r = a % b;
+      a = b;
+      b = r;
+    }
+    return a;
+  };
+  while (S > 1 && gcd(S, grid) != 1) --S;
+  return S;
 }
 
 int num_sms() {
@@ -1148,10 +1381,10 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
   g.seg_b = op.seg_b;
   g.kpg = promote_ksteps(d.dtype);
   if (op.a8) {  // native FP8 data tiles on the e4m3 codes (promoted every k-step)
-    if (!make_map_u8(&M.a8, op.a8, d.m, d.k, op.lda8, 128, BM / 2) ||
-        !make_map_u8(&M.a8_128, op.a8, d.m, d.k, op.lda8, 128, BM) ||
-        !make_map_u8(&M.b8, op.b8, d.k, d.n, op.ldb8, 128, BK8) ||
-        !make_map_boxes_u8(&M.b8w, op.b8, d.k, d.n, op.ldb8))
+    if (!make_map_u8(&M.a[kF8Slot], op.a8, d.m, d.k, op.lda8, 128, BM / 2) ||
+        !make_map_u8(&M.a128[kF8Slot], op.a8, d.m, d.k, op.lda8, 128, BM) ||
+        !make_map_u8(&M.b[kF8Slot], op.b8, d.n, d.k, op.ldb8, 128, 64) ||
+        !make_map_u8(&M.b4[kF8Slot], op.b8, d.n, d.k, op.ldb8, 128, BN))
       return cudaErrorInvalidValue;
     g.f8 = 1;
     g.sA = op.sA;
@@ -1159,6 +1392,8 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
     g.nsa = cdiv(d.k, 128);
     g.nsb = cdiv(d.n, 128);
     g.kpg = 0;  // the checksum tiles (bf16 planes) run one group
+    g.f8grp = op.f8grp;
+    g.f8words = cdiv(cdiv(d.k, 128), 32);
   }
   const bool tall = !g.f8 && use_tall(d.m, cdiv(d.k, BK) * op.nseg, g.kpg);
   const int bm = tall ? Geo<true>::kBM : BM;
@@ -1203,6 +1438,7 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
   if (e != cudaSuccess) return e;
   const int grid = (int)std::min<int64_t>(g.t_total, num_sms());
   if (grid == 0) return cudaSuccess;
+  if (g.f8) g.cs_stride = cs_stride(g.t_total - g.t_data, g.t_total, grid);  // 1 unless set
   e = cudaMemsetAsync(status, 0, sizeof(int), st);  // the status of this product
   if (e != cudaSuccess) return e;
   kernel<<<grid, kThreads, smem, st>>>(M, g);

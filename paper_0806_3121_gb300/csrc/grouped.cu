@@ -60,10 +60,23 @@ struct abft_group_s {
 namespace abft {
 namespace {
 
+// Checksum rows of a problem as swapped tiles (kGrpSwapTile): when its data
+// rows fill whole 128-row tiles, appended checksum halves would need a tile row
+// of their own; a swapped tile's MMA N is the R16 checksum rows (<= 128).
+// ABFT_GRP_SWAP=0 keeps the appended halves (for comparison).
+bool swap_rows(const abft_problem& p, const ProbShape& s) {
+  static const bool on = [] {
+    const char* env = getenv("ABFT_GRP_SWAP");
+    return !(env && env[0] == '0');
+  }();
+  return on && cdiv(p.m, 64) % 2 == 0 && s.R16 <= 128;
+}
+
 int64_t tiles_of(const abft_problem& p, const ProbShape& s, int bpt, bool cs) {
   const int64_t nhd = cdiv(p.m, 64), nbd = cdiv(p.n, 64);
-  const int64_t nh = nhd + (cs ? s.nhc : 0), nb = nbd + (cs ? s.nbc : 0);
-  return cdiv(nh, 2) * cdiv(nb, bpt);
+  const bool sw = cs && swap_rows(p, s);
+  const int64_t nh = nhd + (cs && !sw ? s.nhc : 0), nb = nbd + (cs ? s.nbc : 0);
+  return cdiv(nh, 2) * cdiv(nb, bpt) + (sw ? cdiv(p.n, 256) : 0);
 }
 
 // Problem order of the tile list: as given, or by decreasing inner dimension
@@ -127,6 +140,7 @@ abft_status upload_tables(abft_group_s& G, cudaStream_t st) {
     P.g = 128;  // row-sum groups: one per 128 columns (one epilogue warp's column half)
     P.ngrp = cdiv(q.n, P.g);
     P.nhc = (int32_t)s.nhc; P.nbc = (int32_t)s.nbc;
+    P.swap_rows = swap_rows(q, s) ? 1 : 0;
     threshold_factors(G.dtype, q.k, kGrpVbR, kGrpVbC, &P.f1c, &P.f1r, &P.f2);
     cudaError_t e;
     GMaps& Mp = maps[p];
@@ -159,11 +173,18 @@ abft_status upload_tables(abft_group_s& G, cudaStream_t st) {
     const abft_problem& q = G.pr[p];
     const ProbShape& s = G.sh[p];
     for (int cs = 0; cs < 2; ++cs) {
-      const int64_t nh = cdiv(q.m, 64) + (cs ? s.nhc : 0), nb = cdiv(q.n, 64) + (cs ? s.nbc : 0);
+      const bool sw = cs && swap_rows(q, s);
+      const int64_t nh = cdiv(q.m, 64) + (cs && !sw ? s.nhc : 0),
+                    nb = cdiv(q.n, 64) + (cs ? s.nbc : 0);
       const int64_t ntr = cdiv(nh, 2), ntc = cdiv(nb, bpt);
       std::vector<int4>& v = cs ? tcs : tpl;
       for (int64_t i = 0; i < ntr; ++i)
         for (int64_t j = 0; j < ntc; ++j) v.push_back(make_int4(p, (int)i, (int)j, 0));
+      // the swapped checksum-row tiles follow the problem's data tiles (its B
+      // panels are then still in L2)
+      if (sw)
+        for (int64_t j = 0; j < cdiv(q.n, 256); ++j)
+          v.push_back(make_int4(p, 0, (int)j, kGrpSwapTile));
     }
   }
   if ((int64_t)tcs.size() > G.cap_tiles_cs || (int64_t)tpl.size() > G.cap_tiles_plain)

@@ -19,12 +19,14 @@ constexpr int kMaxErased = 16;     // erased blocks per verify call
 constexpr int kMaxBlockChecksums = 4;  // block checksums of an erasure grid (grid_f)
 
 // Coefficient of block row I in block checksum l of a p-block-row grid:
-// x_I^l with distinct dyadic nodes x_I = (I+1) / 2^e, 2^e > p (every f x f
-// minor of this Vandermonde matrix is nonsingular; l = 0 is the plain sum).
+// x_I^l with distinct dyadic nodes x_I = (2I + 1 - p) / 2^e, 2^e > p,
+// symmetric about 0 (every f x f minor of this Vandermonde matrix is
+// nonsingular; centring the nodes keeps neighbouring blocks' systems ten
+// times better conditioned than nodes in (0, 1); l = 0 is the plain sum).
 __host__ __device__ inline double block_coef(int l, int I, int p) {
   int e = 0;
   while ((1 << e) <= p) ++e;
-  const double x = ldexp((double)(I + 1), -e);
+  const double x = ldexp((double)(2 * I + 1 - p), -e);
   double c = 1.0;
   for (int t = 0; t < l; ++t) c *= x;
   return c;
@@ -164,19 +166,25 @@ struct TcOperands {
   int nseg;
   uint32_t seg_a, seg_b;
   // native FP8 data tiles (a8 == nullptr: none): e4m3 codes of A (m x k, lda8
-  // bytes) and B (k x n, ldb8 bytes), 16-byte aligned rows, and their binary32
-  // power-of-two block scales (ceil(m/128) x ceil(k/128), ceil(k/128) x
-  // ceil(n/128), row-major, device)
+  // bytes) and of B transposed (b8 = B^T, n x k, ldb8 bytes), 16-byte aligned
+  // rows, and their binary32 power-of-two block scales (ceil(m/128) x
+  // ceil(k/128), ceil(k/128) x ceil(n/128), row-major, device)
   const void* a8;
   const void* b8;
   int64_t lda8, ldb8;
   const float* sA;
   const float* sB;
+  uint32_t* f8grp;  // the data tiles' scale-group words (workspace, written first)
 };
 // status: the word a timeout is recorded in (cleared on `st` before the
 // launch).
 cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void* ws,
                              bool checksums, int* status, cudaStream_t st);
+// Scale groups of the data tiles (128 x 256) of an FP8 product: per tile one bit
+// per 128-wide k-step, set where the block-scale product of either 128-column
+// half changes (out: ceil(m/128) * ceil(n/256) * ceil(ceil(k/128)/32) words).
+cudaError_t launch_f8_groups(const float* sA, const float* sB, int64_t m, int64_t n, int64_t k,
+                             uint32_t* out, cudaStream_t st);
 // Process-wide word that receives the timeout of a checksum-free product run
 // without a workspace (nothing reads it: such a call has no report).
 cudaError_t tc_timeout_fallback(int** dev_ptr);
@@ -213,8 +221,20 @@ struct GProb {  // one problem of a group, in device memory
   double f1c, f1r, f2;  // threshold factors (the safety factor applies at use)
   int32_t nhc, nbc;     // checksum halves (64 rows) / boxes (64 columns)
   int32_t bpt, g;       // boxes per tile (tile width 64 bpt), row-sum group width
-  int32_t st_ok, pad2;  // bit 0/1/2: TMA store map of C / E16 / F16 valid
+  int32_t st_ok;        // bit 0/1/2: TMA store map of C / E16 / F16 valid
+  int32_t swap_rows;    // 1: the checksum rows are products of their own (swapped
+                        // tiles, see kGrpSwapTile), not halves after the data rows
 };
+
+// Tile-list entries of a grouped product are int4 {problem, tile row, tile
+// column, kind}.  kind kGrpSwapTile: the expected column checksums E16 = acs B
+// of 256 columns of B (tile column = 256-column block) computed with the
+// operands' roles swapped -- B's columns on the M side (MN-major, two M = 128
+// MMAs), the R16 <= 128 checksum rows on the N side (K-major) -- so the MMAs'
+// N is R16 rounded up to 16 instead of a whole 128-row tile of mostly empty
+// rows.  Used for problems whose data rows fill whole tiles (an even number of
+// 64-row halves).
+constexpr int kGrpSwapTile = 1;
 
 struct GMaps {  // tensor maps of one problem (64-byte aligned in device memory)
   CUtensorMap a, acs, b, bcs;   // 64-row halves / one 64-column box

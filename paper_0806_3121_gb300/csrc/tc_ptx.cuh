@@ -200,6 +200,18 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int b_mn_major) 
          | (static_cast<uint32_t>(M >> 4) << 24);  // M / 16
 }
 
+// Instruction descriptor for kind::f16 with MN-major A (the A operand's M
+// index contiguous, as B's N index in an N-major B) and K-major B: bf16 x bf16
+// -> f32, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16_mn_a(int M, int N) {
+  return (1u << 4)                                 // D format f32
+         | (1u << 7)                               // A format bf16
+         | (1u << 10)                              // B format bf16
+         | (1u << 15)                              // A MN-major
+         | (static_cast<uint32_t>(N >> 3) << 17)   // N / 8
+         | (static_cast<uint32_t>(M >> 4) << 24);  // M / 16
+}
+
 // Instruction descriptor for kind::f8f6f4: e4m3 x e4m3 -> f32 (format code 0
 // for both operands), M x N, A K-major, B K-major (0) or MN-major (1).
 __host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N, int b_mn_major) {

@@ -785,7 +785,7 @@ __global__ void __launch_bounds__(kThreads) k_recover(TC* C, int64_t ldc, const 
       for (int u = 0; u < kMaxBlockChecksums; ++u) erased |= u < rs.t && rs.rows[u] == I;
       if (erased) continue;
       const double v = (double)C[(I * bs + r) * ldc + j];
-      const double x = ldexp((double)(I + 1), -e);
+      const double x = ldexp((double)(2 * I + 1 - p), -e);
       double c = 1.0;  // c_{l,I} = x^l
 #pragma unroll
       for (int l = 0; l < kMaxBlockChecksums; ++l) {

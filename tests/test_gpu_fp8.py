@@ -2,10 +2,14 @@
 128 x 128 block) with the CPU oracle, through the C ABI.
 
 The oracle dequantises the same codes and scales in binary64 (e4m3 decoding pinned in
-test_oracle) and runs the same checks as for bf16: the GPU multiplies the dequantised values
-(exact in bf16 for power-of-two scales) with fp32 accumulation, so the product bound is the
-bf16 one, elementwise 2 k u32 (|A||B|) and relative Frobenius 4 sqrt(k) u32, against the
-oracle's product of the dequantised operands.  The quantisation error against the binary64
+test_oracle) and runs the same checks as for bf16.  The GPU's data tiles multiply the e4m3
+codes on the 8-bit tensor path (kind::f8f6f4), one TMEM accumulator per run of k-steps with
+the same block-scale product, each scaled exactly by that power of two in the epilogue
+("native"), or the dequantised values (exact in bf16 for power-of-two scales) on the bf16
+path ("planes", ABFT_FP8_NATIVE=0); the checksum tiles always use the bf16 planes.  Either
+way the products are exact and accumulate in fp32, so the product bound is the bf16 one,
+elementwise 2 k u32 (|A||B|) and relative Frobenius 4 sqrt(k) u32, against the oracle's
+product of the dequantised operands.  The quantisation error against the binary64
 product of the unquantised inputs is stated (printed) and bounded loosely.  Decisions:
 bit-exact fault positions and kinds."""
 import numpy as np
@@ -29,6 +33,13 @@ def lib():
     return abft.load()
 
 
+@pytest.fixture(params=["native", "planes"])
+def mode(request, monkeypatch):
+    """Data tiles on the e4m3 codes (native) or on the dequantised bf16 planes."""
+    monkeypatch.setenv("ABFT_FP8_NATIVE", "1" if request.param == "native" else "0")
+    return request.param
+
+
 def rel_fro(x, ref):
     den = np.linalg.norm(ref)
     return np.linalg.norm(x - ref) / (den if den > 0 else 1.0)
@@ -47,13 +58,15 @@ def positions(rep):
 
 
 class Run:
-    def __init__(self, m, n, k, vb_r, vb_c, p=0, q=0, seed=0, scale_fix=None):
+    def __init__(self, m, n, k, vb_r, vb_c, p=0, q=0, seed=0, scale_fix=None, scale_fix_b=None):
         self.m, self.n, self.k = m, n, k
         self.A_src, self.B_src = wl.operands(wl.FP8_4096, seed, m, n, k)
         qa, sa = wl.quantize_e4m3(self.A_src)
         qb, sb = wl.quantize_e4m3(self.B_src)
         if scale_fix:
             scale_fix(sa)
+        if scale_fix_b:
+            scale_fix_b(sb)
         self.A64, self.B64 = oracle.dequant_e4m3(qa, sa), oracle.dequant_e4m3(qb, sb)
         self.A = torch.from_numpy(qa).cuda()
         self.B = torch.from_numpy(qb).cuda()
@@ -78,11 +91,15 @@ SHAPES = [  # (m, n, k, vb_r, vb_c, p, q)
     (200, 300, 136, 40, 30, 0, 0),
     (640, 700, 520, 128, 256, 0, 0),
     (256, 264, 250, 128, 64, 0, 0),   # rows of A not 8-byte aligned: separate dequantisation
+    # 16-byte aligned rows (native data tiles) with ragged m, n and k
+    (200, 272, 144, 40, 136, 0, 0),
+    (640, 704, 528, 128, 256, 0, 0),
+    (384, 512, 1040, 128, 128, 3, 4),
 ]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
-def test_fp8_product_and_checksums_vs_oracle(shape):
+def test_fp8_product_and_checksums_vs_oracle(shape, mode):
     m, n, k, vbr, vbc, p, q = shape
     r = Run(m, n, k, vbr, vbc, p, q, seed=3)
     enc = oracle.Encoded(r.A64, r.B64, vbr, vbc, p, q, dtype="fp8")
@@ -102,7 +119,7 @@ def test_fp8_product_and_checksums_vs_oracle(shape):
     assert st == abft.OK and nrep == 0
 
 
-def test_fp8_five_seeded_faults_located_like_oracle():
+def test_fp8_five_seeded_faults_located_like_oracle(mode):
     """Five accumulator-output flips (graded exponent bits) in distinct verify blocks, armed
     in the epilogue: located from the fused sums at the oracle's positions and corrected."""
     m, n, k = 1024, 1024, 512
@@ -125,7 +142,7 @@ def test_fp8_five_seeded_faults_located_like_oracle():
     assert rel_fro(Cg, oracle.gemm(r.A64, r.B64)) <= 4 * np.sqrt(k) * U32 + 1e-7
 
 
-def test_fp8_fault_free_runs_report_nothing():
+def test_fp8_fault_free_runs_report_nothing(mode):
     for seed in range(4):
         r = Run(512, 384, 640, 128, 128, seed=100 + seed)
         for reread in (0, 1):
@@ -133,7 +150,7 @@ def test_fp8_fault_free_runs_report_nothing():
             assert st == abft.OK and nrep == 0
 
 
-def test_fp8_plain_product_matches():
+def test_fp8_plain_product_matches(mode):
     r = Run(384, 512, 256, 128, 128, seed=5)
     C2 = torch.full_like(r.C, float("nan"))
     abft.abft_gemm_plain(r.desc, r.A, r.B, C2, ws=r.ws)
@@ -153,3 +170,53 @@ def test_fp8_non_power_of_two_scale_is_rejected():
     r2 = Run(256, 256, 256, 128, 128, seed=7)
     st, rep, nrep = abft.abft_verify_correct(r2.desc, r2.C, r2.ws)
     assert st == abft.OK and nrep == 0
+
+
+def test_fp8_varying_block_scales_several_scale_groups(mode):
+    """Block scales that change along k (powers of two times the recipe's: A's scales x4
+    on every second k-block, B's x1/2 on every third) split each native data tile's K loop
+    into several scale groups, each accumulated in its own TMEM accumulator and scaled in
+    the epilogue: the product and the checks still match the oracle, with one graded
+    fault located."""
+    def fa(sa):
+        sa[:, ::2] *= 4.0
+
+    def fb(sb):
+        sb[1::3, :] *= 0.5
+    m, n, k = 512, 768, 1280
+    r = Run(m, n, k, 256, 256, seed=21, scale_fix=fa, scale_fix_b=fb)
+    ref = oracle.gemm(r.A64, r.B64)
+    C = r.C.cpu().numpy()
+    check_fp32_product(C, r.A64, r.B64, ref)
+    enc = oracle.Encoded(r.A64, r.B64, 256, 256, dtype="fp8")
+    st, rep, nrep = abft.abft_verify_correct(r.desc, r.C, r.ws, reread_C=1)
+    assert st == abft.OK and nrep == 0
+    i, j = 300, 517
+    flips = [(i, j, 29 if abs(C[i, j]) >= 2.0 else 30)]
+    abft.abft_set_epilogue_faults(r.desc, r.ws, flips)
+    abft.abft_gemm(r.desc, r.A, r.B, r.C, r.ws)
+    abft.abft_set_epilogue_faults(r.desc, r.ws, [])
+    Cf = r.C.cpu().numpy().astype(np.float64)
+    st, rep, nrep = abft.abft_verify_correct(r.desc, r.C, r.ws, reread_C=0)
+    ost, orep, oC, on = enc.verify_correct(Cf)
+    assert st == abft.OK and positions(rep) == positions(orep) == [(i, j, abft.KIND_CORRECTED)]
+    check_fp32_product(r.C.cpu().numpy().astype(np.float64), r.A64, r.B64, ref)
+
+
+def test_fp8_native_and_planes_agree():
+    """The same codes through both data-tile paths: both within the product bound of the
+    oracle's product, and within twice that bound of each other."""
+    import os
+    out = {}
+    for mode_ in ("1", "0"):
+        os.environ["ABFT_FP8_NATIVE"] = mode_
+        try:
+            r = Run(512, 512, 2048, 128, 128, seed=9)
+        finally:
+            del os.environ["ABFT_FP8_NATIVE"]
+        out[mode_] = r.C.cpu().numpy().astype(np.float64)
+    ref = oracle.gemm(r.A64, r.B64)
+    for C in out.values():
+        check_fp32_product(C, r.A64, r.B64, ref)
+    mag = np.abs(r.A64) @ np.abs(r.B64)
+    assert np.all(np.abs(out["1"] - out["0"]) <= 4 * 2048 * U32 * mag + 1e-30)

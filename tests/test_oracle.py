@@ -334,14 +334,16 @@ def test_e4m3_decode():
 # ---- several block checksums (section 2.1: f checksums recover f lost blocks)
 
 def test_block_coefficients_vandermonde():
-    """c_{l,I} = x_I^l with distinct dyadic nodes x_I = (I+1)/2^e, 2^e > p: l = 0 is the
-    plain sum, values are exact, and every f x f minor is nonsingular."""
+    """c_{l,I} = x_I^l with distinct dyadic nodes x_I = (2I+1-p)/2^e, 2^e > p (symmetric
+    about 0): l = 0 is the plain sum, values are exact, and every f x f minor is
+    nonsingular."""
     import itertools
     p = 22
     for I in range(p):
         assert oracle.block_coef(0, I, p) == 1.0
-        assert oracle.block_coef(1, I, p) == (I + 1) / 32.0
-        assert oracle.block_coef(3, I, p) == ((I + 1) / 32.0) ** 3   # exact: dyadic
+        assert oracle.block_coef(1, I, p) == (2 * I + 1 - 22) / 32.0
+        assert oracle.block_coef(3, I, p) == ((2 * I + 1 - 22) / 32.0) ** 3   # exact: dyadic
+    assert oracle.block_coef(1, 0, 1) == 0.0 and oracle.block_coef(1, 1, 3) == 0.0
     p = 7
     for f in (2, 3, 4):
         Mfull = np.array([[oracle.block_coef(l, I, p) for I in range(p)] for l in range(f)])
@@ -423,3 +425,34 @@ def test_more_erasures_than_checksums_is_uncorrectable():
         Ce[3 * bi:3 * bi + 3, 0:3] = np.nan
     st, Cr, nfl = enc.recover_blocks(Ce, [(0, 0), (1, 0), (3, 0)])
     assert st == oracle.ST_UNCORRECTABLE and np.isnan(Cr[0:3, 0:3]).all()
+
+
+def test_multi_erasure_conditioning_p22():
+    """Several adjacent lost blocks of the 22-block-row grid (binary64, N(0,1) data): the
+    rebuild solves the Vandermonde system of their nodes, whose condition number bounds
+    the amplification of the survivors' and checksums' rounding (centred nodes: at most
+    45, 1.1e3 and 1.6e4 for 2, 3 and 4 adjacent blocks).  Two adjacent blocks come back
+    within 1e-12 and pass the re-check; three or four come back within cond(M) times the
+    rounding of a line (1e-11 relative here), which the element checksums' re-check does
+    flag: the status is uncorrectable, never a silently wrong block."""
+    p, bs, q, bc, k = 22, 32, 2, 32, 512
+    g = wl.rng(5)
+    A = g.standard_normal((p * bs, k))
+    B = g.standard_normal((k, q * bc))
+    C = oracle.gemm(A, B)
+    for f, start in ((2, 0), (2, 10), (3, 0), (4, 0), (4, 9)):
+        rows = list(range(start, start + f))
+        M = np.array([[oracle.block_coef(l, I, p) for I in rows] for l in range(f)])
+        assert np.linalg.cond(M) <= {2: 45, 3: 1.1e3, 4: 1.7e4}[f]
+        enc = oracle.Encoded(A, B, bs, bc, p, q, f=f)
+        Ce = C.copy()
+        for I in rows:
+            Ce[I * bs:(I + 1) * bs, bc:] = np.nan
+        st, Cr, nfl = enc.recover_blocks(Ce, [(I, 1) for I in rows])
+        err = max(np.linalg.norm(Cr[I * bs:(I + 1) * bs, bc:] - C[I * bs:(I + 1) * bs, bc:])
+                  / np.linalg.norm(C[I * bs:(I + 1) * bs, bc:]) for I in rows)
+        if f == 2:
+            assert st == oracle.ST_OK and nfl == 0 and err <= 1e-12
+        else:
+            assert err <= 1e-11
+            assert st == oracle.ST_UNCORRECTABLE and nfl > 0

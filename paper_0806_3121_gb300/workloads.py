@@ -61,9 +61,13 @@ FP8_16384 = Workload("fp8_16384", "fp8", 16384, 16384, 16384, 256, 256, dist="fp
                                      "block; fp32 accumulate; 5 seeded faults")
 FP8_4096 = Workload("fp8_4096", "fp8", 4096, 4096, 4096, 256, 256, dist="fp8rows", n_flips=5,
                     note="the FP8 recipe at 4096^3 (profiling size)")
+FP8_8192 = Workload("fp8_8192", "fp8", 8192, 8192, 8192, 256, 256, dist="fp8rows", n_flips=5,
+                    note="the FP8 recipe at 8192^3 (profiling size)")
+BF16X6_8192 = Workload("bf16x6_8192", "bf16x6", 8192, 8192, 8192, 256, 256, dist="normal",
+                       n_flips=3, note="split bf16x6 8192^3 (profiling size)")
 WORKLOADS = {w.name: w for w in (F64_512, F64_11264_GRID22, F64_4096_GRID8, BF16_16384,
-                                 BF16_8192, BF16X3_16384, BF16X3_8192, BF16X6_16384, FP8_16384,
-                                 FP8_4096)}
+                                 BF16_8192, BF16X3_16384, BF16X3_8192, BF16X6_16384, BF16X6_8192,
+                                 FP8_16384, FP8_4096, FP8_8192)}
 
 
 def fp8_quantize_dev(x, blk=128):

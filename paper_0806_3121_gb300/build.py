@@ -30,6 +30,20 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
+def _big_stack():
+    """Raise the compiler's stack limit (soft limit up to the hard one, at most 1 GiB)."""
+    try:
+        import resource
+        soft, hard = resource.getrlimit(resource.RLIMIT_STACK)
+        want = 1 << 30
+        if hard != resource.RLIM_INFINITY:
+            want = min(want, hard)
+        if soft != resource.RLIM_INFINITY and soft < want:
+            resource.setrlimit(resource.RLIMIT_STACK, (want, hard))
+    except (ImportError, ValueError, OSError):
+        pass
+
+
 def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
@@ -55,8 +69,18 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     objs = [os.path.join(OUT_DIR, os.path.basename(s)[:-3] + ".o") for s in srcs]
 
     def run(job):
+        # A compiler process that crashes (a signal, not a diagnostic) is run
+        # again, up to twice, with a larger stack: the Arm toolchain has been
+        # seen to crash now and then on the tensor-core product's translation
+        # unit and to succeed on the next run of the same command.
         src, cmd = job
-        r = subprocess.run(cmd, capture_output=True, text=True)
+        for attempt in range(3):
+            r = subprocess.run(cmd, capture_output=True, text=True, preexec_fn=_big_stack)
+            crashed = r.returncode < 0 or "Segmentation fault" in (r.stdout + r.stderr)
+            if r.returncode == 0 or not crashed:
+                break
+            sys.stderr.write(f"nvcc crashed on {os.path.basename(src)} (attempt {attempt + 1}); "
+                             "running it again\n")
         return src, r
 
     if jobs:

@@ -76,13 +76,20 @@ static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
 // stage, one accumulator per 128-row half (both halves of TMEM), so the
 // operand bytes per flop fall by a third and the ring holds 3 stages of
 // 64 KiB; the epilogue no longer overlaps the next tile's MMAs, which pays
-// off for long K loops.
-template <bool kTall>
+// off for long K loops.  Pair tiles are 256 x 256 on a CTA pair (a cluster of
+// two): one M = 256 MMA per K step (cta_group::2) reads 128 rows of A and
+// 128 columns of B from each CTA's ring, so each CTA stages 32 KiB per K step
+// (the tall tile's bytes per flop) in a 6-stage ring and keeps its 128 rows
+// of the tile in TMEM with two alternating accumulators (the regular tile's
+// overlapped epilogue).
+template <bool kTall, bool kPair = false>
 struct Geo {
-  static constexpr int kBM = kTall ? 256 : BM;
-  static constexpr int kStages = kTall ? 3 : STAGES;
-  static constexpr uint32_t kABytes = (uint32_t)kBM * BK * 2;
-  static constexpr uint32_t kStageBytes = kABytes + B_BYTES;
+  static_assert(!(kTall && kPair), "tall or pair tiles");
+  static constexpr int kBM = (kTall || kPair) ? 256 : BM;   // rows of the scheduled tile
+  static constexpr int kStages = kTall ? 3 : (kPair ? 6 : STAGES);
+  static constexpr uint32_t kABytes = (uint32_t)(kTall ? 256 : BM) * BK * 2;  // this CTA's A
+  static constexpr uint32_t kBBytes = kPair ? B_BYTES / 2 : B_BYTES;         // this CTA's B
+  static constexpr uint32_t kStageBytes = kABytes + kBBytes;
   static constexpr int kSlots = kTall ? 1 : 2;            // accumulator slots that alternate
   static constexpr int kCols = kTall ? BN : kEpiCols;     // tile columns per epilogue warp
   static constexpr size_t kSmem =
@@ -90,6 +97,7 @@ struct Geo {
 };
 static_assert(Geo<false>::kSmem == SMEM_BYTES, "regular tiles");
 static_assert(Geo<true>::kSmem <= 232448, "shared memory per CTA (tall tiles)");
+static_assert(Geo<false, true>::kSmem <= 232448, "shared memory per CTA (pair tiles)");
 static_assert(Geo<true>::kBM / 128 * BN <= (int)TMEM_COLS, "tall accumulators fit TMEM");
 
 // Tensor maps of the operands, per bf16 plane (the split dtypes have 2 or 3
@@ -293,6 +301,10 @@ struct TileView {
   const float* sB;
   int64_t nsb;
   const uint32_t* gmask;      // this tile's scale-group words (see TcArgs::f8grp)
+  // 256-row tiles: the scales and group words of rows row0 + 128 .. (nullptr
+  // when those rows are past the data)
+  const float* sArow2;
+  const uint32_t* gmask2;
 };
 
 // End of the scale group that starts at k-step kb: the next k-step whose bit is
@@ -308,6 +320,13 @@ __device__ __forceinline__ int64_t group_end(const uint32_t* mask, int64_t kb, i
     x = (x | 31) + 1;
   }
   return nkt;
+}
+
+// End of the scale group of a tile that starts at k-step kb; a 256-row tile
+// (a CTA pair's) ends one where either 128-row half's group ends.
+__device__ __forceinline__ int64_t group_end_tile(const TileView& T, int64_t kb, int64_t nkt) {
+  const int64_t e = group_end(T.gmask, kb, nkt);
+  return T.gmask2 ? min(e, group_end(T.gmask2, kb, nkt)) : e;
 }
 
 // MMA N of a tile: its boxes are 64 columns wide, but when the last one is a
@@ -379,6 +398,8 @@ struct SingleSched {
     V.sB = g.sB;
     V.nsb = g.nsb;
     V.gmask = nullptr;
+    V.sArow2 = nullptr;
+    V.gmask2 = nullptr;
     if (V.f8) {  // data tile on the e4m3 codes: 128-wide k-steps in scale groups
       V.nkb = (g.k + 127) / 128;
       V.nseg = 1;
@@ -390,6 +411,10 @@ struct SingleSched {
       V.maW = V.nA128 ? &M->a128[kF8Slot] : nullptr;
       V.mbW = (bcols == 4 && T.col0 + 256 <= g.n) ? &M->b4[kF8Slot] : nullptr;
       V.sArow = g.sA + (T.row0 / 128) * g.nsa;
+      if (kBM == 256 && T.row0 + 128 < g.m) {
+        V.sArow2 = V.sArow + g.nsa;
+        V.gmask2 = V.gmask + g.ntn * g.f8words;
+      }
     }
     V.C = g.C;
     V.ldc = g.ldc;
@@ -455,12 +480,14 @@ __device__ __forceinline__ float4 staged4(const float* stg, int r, int j) {
 // kPromote: the K loop runs in promotion groups whose accumulators the
 // epilogue sums in fp32 registers (a separate instantiation, so the register
 // accumulator of that path does not weigh on the single-group epilogue).
-template <bool kPromote, bool kTall, bool kF8, class Sched>
+// kPair: 256 x 256 tiles on a CTA pair (see Geo); this CTA takes rows
+// 128 rank .. of every tile, the even CTA issues the MMAs for both.
+template <bool kPromote, bool kTall, bool kF8, bool kPair, class Sched>
 __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wait_ns,
                                         int stall_test, const int32_t* inj_hdr,
                                         const InjectEntry* inj) {
-  using G = Geo<kTall>;
-  static_assert(!(kPromote && kTall), "promotion runs on regular tiles");
+  using G = Geo<kTall, kPair>;
+  static_assert(!(kPromote && kTall), "promotion runs on regular or pair tiles");
   static_assert(!kF8 || kPromote, "FP8 data tiles promote every k-step");
   static_assert(!kTall || kEpiWarps == 8, "tall tiles: one epilogue warp per lane quarter and half");
   constexpr int NS = G::kStages;
@@ -480,6 +507,15 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
   auto tfull = [&](int a) { return tc::smem_addr(&bars[2 * NS + a]); };
   auto tempty = [&](int a) { return tc::smem_addr(&bars[2 * NS + 2 + a]); };
   const uint32_t drain = tc::smem_addr(&bars[2 * NS + 4]);
+  // CTA pair: this CTA's rank; the MMA issuer's (even CTA's) stage-full and
+  // accumulator-empty barriers count both CTAs' bytes and epilogue warps
+  const uint32_t rank = kPair ? tc::cluster_ctarank() : 0u;
+  const bool issuer = rank == 0;
+  auto full_i = [&](int s) { return kPair ? tc::mapa(full(s), 0) : full(s); };
+  auto tempty_i = [&](int a) { return kPair ? tc::mapa(tempty(a), 0) : tempty(a); };
+  // persistent tile loop: tiles per CTA (per pair)
+  const int64_t tfirst = kPair ? (int64_t)tc::cluster_id() : (int64_t)blockIdx.x;
+  const int64_t tstep = kPair ? (int64_t)tc::num_clusters() : (int64_t)gridDim.x;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
@@ -488,7 +524,7 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
     }
     for (int a = 0; a < 2; ++a) {
       tc::mbar_init(tfull(a), 1);
-      tc::mbar_init(tempty(a), kEpiWarps);
+      tc::mbar_init(tempty(a), kPair ? 2 * kEpiWarps : kEpiWarps);
     }
     tc::mbar_init(drain, 1);
     *abort = 0;
@@ -497,11 +533,19 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
     S.prefetch();
   }
   if (warp == 1) {
-    tc::tmem_alloc(tc::smem_addr(tmem_slot), TMEM_COLS);
-    tc::tmem_relinquish();
+    if constexpr (kPair) {  // one warp of each CTA, together
+      tc::tmem_alloc_pair(tc::smem_addr(tmem_slot), TMEM_COLS);
+      tc::tmem_relinquish_pair();
+    } else {
+      tc::tmem_alloc(tc::smem_addr(tmem_slot), TMEM_COLS);
+      tc::tmem_relinquish();
+    }
   }
   tc::fence_before_sync();
-  __syncthreads();
+  if constexpr (kPair)
+    tc::cluster_sync();  // the peer's barriers are initialised before any use
+  else
+    __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
   const int64_t total = S.total();
@@ -515,16 +559,23 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
       int s = 0;
       uint32_t ph = 0;
       int64_t issued = 0;  // stages filled and not known to be consumed
-      for (int64_t t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
+      for (int64_t t = tfirst; t < total && !*abort; t += tstep) {
         const TileView T = S.view(t);
         if (stall_test && t == 0) continue;  // nothing will fill these stages
         const int64_t nkb = T.nkb, nkt = T.nkb * T.nseg;
         // an FP8 data tile's k-step is 128 codes (128 bytes, as a bf16 k-step);
-        // its B boxes hold 64 rows of B^T (8 KiB, as a bf16 box)
+        // its B boxes hold 64 rows of B^T (8 KiB, as a bf16 box).  A pair's
+        // bytes (both CTAs') land on the issuer's barrier, which the issuer's
+        // producers expect: the same totals as one CTA's 256-row tile.
         const uint32_t tx = T.swap ? (pA ? (uint32_t)T.nsw_h * HALF_BYTES : 4 * B_BOX_BYTES)
                                    : pA ? (uint32_t)T.hcnt * HALF_BYTES
                                         : (uint32_t)T.nbox * B_BOX_BYTES;
         const int bkx = T.f8 ? BK8 : BK;
+        // this CTA's halves [h_lo, h_hi) and boxes [b_lo, b_hi) of the tile
+        // (a pair splits both: rows 128 rank .., columns 128 rank ..)
+        const int h_lo = kPair ? 2 * (int)rank : 0, b_lo = kPair ? 2 * (int)rank : 0;
+        const int h_hi = kPair ? min(T.hcnt, h_lo + 2) : T.hcnt;
+        const int b_hi = kPair ? min(T.nbox, b_lo + 2) : T.nbox;
         // a stage's MMAs take ~700 cycles: the per-stage bookkeeping is
         // incremental (no division per stage)
         int seg = 0, pa = (int)(T.seg_a & 3u), pb = (int)(T.seg_b & 3u);
@@ -533,8 +584,15 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
           const int32_t kx = (int32_t)(kb * bkx);
           if (!tc::wait(empty(s), ph ^ 1, abort)) break;
           const uint32_t sa = tc::smem_addr(smem + s * G::kStageBytes);
-          tc::mbar_arrive_expect_tx(full(s), tx);
-          if (T.swap) {
+          const uint32_t fb = full_i(s);
+          if (issuer) tc::mbar_arrive_expect_tx(full(s), tx);
+          auto load2 = [&](uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y) {
+            if constexpr (kPair)
+              tc::tma_load_2d_pair(dst, map, fb, x, y);
+            else
+              tc::tma_load_2d(dst, map, fb, x, y);
+          };
+          if (!kPair && T.swap) {
             // swapped checksum-row tile: the A region takes the checksum rows'
             // halves (the N side), the B region four B boxes (the M side)
             if (pA) {
@@ -548,37 +606,42 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
                                 kx);
             }
           } else if (!pA && T.f8) {
-            // e4m3 B^T (K-major): the 256 rows of a full tile in one copy, else
-            // 64 rows per box
+            // e4m3 B^T (K-major): this CTA's rows of a full tile in one copy
+            // (256 rows, a pair's CTA 128), else 64 rows per box
             if (T.mbW) {
-              tc::tma_load_2d(sa + G::kABytes, T.mbW, full(s), kx, T.colW);
+              load2(sa + G::kABytes, T.mbW, kx, T.colW + 64 * b_lo);
             } else {
-              for (int b = 0; b < T.nbox; ++b)
-                tc::tma_load_2d(sa + G::kABytes + b * B_BOX_BYTES, T.mbD, full(s), kx,
-                                T.colD + 64 * b);
+              for (int b = b_lo; b < b_hi; ++b)
+                load2(sa + G::kABytes + (b - b_lo) * B_BOX_BYTES, T.mbD, kx, T.colD + 64 * b);
             }
           } else if (!pA) {
-            // B: the full boxes in one 3-D copy, the rest (ragged, checksum) per box
-            int b_first = 0;
+            // B: the full boxes in one 3-D copy (4 boxes, a pair's CTA 2), the
+            // rest (ragged, checksum) per box
+            int b_first = b_lo;
             if (T.mbW) {
-              tc::tma_load_3d(sa + G::kABytes, T.mbW + pb, full(s), 0, kx, T.colW / 64);
-              b_first = T.nW;
+              if constexpr (kPair)
+                tc::tma_load_3d_pair(sa + G::kABytes, T.mbW + pb, fb, 0, kx, T.colW / 64 + b_lo);
+              else
+                tc::tma_load_3d(sa + G::kABytes, T.mbW + pb, fb, 0, kx, T.colW / 64);
+              b_first = kPair ? b_hi : T.nW;  // a pair tile's W copy is all of its boxes
             }
-            for (int b = b_first; b < T.nbox; ++b) {
+            for (int b = b_first; b < b_hi; ++b) {
               const bool dat = b < T.bsplit;
               const CUtensorMap* mb = (dat ? T.mbD : T.mbC) + pb;
               const int32_t x = dat ? T.colD + 64 * b : T.colC + 64 * (b - T.bsplit);
-              tc::tma_load_2d(sa + G::kABytes + b * B_BOX_BYTES, mb, full(s), x, kx);
+              load2(sa + G::kABytes + (b - b_lo) * B_BOX_BYTES, mb, x, kx);
             }
           } else if (T.maW) {
-            for (int i = 0; i < T.nA128; ++i)
-              tc::tma_load_2d(sa + i * (2 * HALF_BYTES), T.maW + pa, full(s), kx, T.rowW + 128 * i);
+            // whole 128-row boxes: box i at rows rowW + 128 i (a pair's CTA: box rank)
+            const int i_lo = kPair ? (int)rank : 0, i_hi = kPair ? min(T.nA128, i_lo + 1) : T.nA128;
+            for (int i = i_lo; i < i_hi; ++i)
+              load2(sa + (i - i_lo) * (2 * HALF_BYTES), T.maW + pa, kx, T.rowW + 128 * i);
           } else {
-            for (int h = 0; h < T.hcnt; ++h) {
+            for (int h = h_lo; h < h_hi; ++h) {
               const bool dat = h < T.hsplit;
               const CUtensorMap* ma = (dat ? T.maD : T.maC) + pa;
               const int32_t y = dat ? T.rowD + 64 * h : T.rowC + 64 * (h - T.hsplit);
-              tc::tma_load_2d(sa + h * HALF_BYTES, ma, full(s), kx, y);
+              load2(sa + (h - h_lo) * HALF_BYTES, ma, kx, y);
             }
           }
           ++issued;
@@ -591,33 +654,40 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
           }
         }
       }
-      // Do not leave copies in flight: wait for the last fills (bounded).
+      // Do not leave copies in flight: wait for the last fills (bounded).  A
+      // pair's copies complete on the issuer's barriers, so its CTAs wait
+      // until the MMAs consumed the stages instead (the commit that frees a
+      // stage reaches both CTAs; once it arrived no signal to this CTA's
+      // barriers is outstanding).
       for (int q = 0; q < NS && issued > 0; ++q, --issued) {
         if (--s < 0) { s = NS - 1; ph ^= 1; }
         const uint64_t t0 = tc::globaltimer();
-        while (!tc::mbar_try_wait(full(s), ph) && tc::globaltimer() - t0 < tc::wait_limit_ns()) {
+        const uint32_t bar = kPair ? empty(s) : full(s);
+        while (!tc::mbar_try_wait(bar, ph) && tc::globaltimer() - t0 < tc::wait_limit_ns()) {
         }
       }
     }
     __syncwarp();
   } else if (warp == 1) {
-    if (lane == 0) {
-      // ---------------- MMA issuer
+    if (lane == 0 && issuer) {
+      // ---------------- MMA issuer (a pair: the even CTA's, for both)
       int s = 0, acc = 0;
       uint32_t ph = 0, aph = 0;
-      for (int64_t t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
+      for (int64_t t = tfirst; t < total && !*abort; t += tstep) {
         const TileView T = S.view(t);
         const int64_t nkt = T.nkb * T.nseg;
         const int64_t gsz = (kPromote && T.kpg > 0 && T.kpg < nkt) ? T.kpg : nkt;
         const bool f8t = kF8 && T.f8;
-        const uint32_t idesc = f8t ? tc::idesc_e4m3(BM, T.nmma, 0)
-                                   : tc::idesc_bf16(BM, T.nmma, 1);
+        // a pair's MMA: M = 256 (128 rows per CTA), N = 256 (128 columns of B
+        // per CTA; boxes a tile does not have are never stored)
+        const int mm = kPair ? 256 : BM, nn = kPair ? BN : T.nmma;
+        const uint32_t idesc = f8t ? tc::idesc_e4m3(mm, nn, 0) : tc::idesc_bf16(mm, nn, 1);
         bool ok = true;
         // one accumulator per promotion group (FP8 data tiles: per scale
         // group); the epilogue adds the groups
         int64_t g1 = 0;
         for (int64_t g0 = 0; g0 < nkt && ok; g0 = g1) {
-          g1 = f8t ? group_end(T.gmask, g0, nkt) : min(g0 + gsz, nkt);
+          g1 = f8t ? group_end_tile(T, g0, nkt) : min(g0 + gsz, nkt);
           if (!tc::wait(tempty(acc), aph ^ 1, abort)) { ok = false; break; }
           tc::fence_after_sync();
           const uint32_t d = tmem + acc * BN;
@@ -628,7 +698,7 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
             tc::fence_after_sync();
             const uint32_t sa = tc::smem_addr(smem + s * G::kStageBytes);
             const uint32_t sb = sa + G::kABytes;
-            if (T.swap) {
+            if (!kPair && T.swap) {
               // swapped tile: two MMAs per K step, MN-major A = two B boxes each
               // (64-column atoms 8 KiB apart, 8-row K groups 1024 B apart, a K
               // step of 16 rows moves 2 KiB) into accumulator columns 0 and
@@ -640,10 +710,11 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
                 for (int h2 = 0; h2 < 2; ++h2) {
                   const uint64_t ad =
                       tc::sdesc_sw128(sb + h2 * (2 * B_BOX_BYTES) + kk * 2048, B_BOX_BYTES, 1024);
-                  tc::mma_f16(d + h2 * 128, ad, bd, idesc_sw, (kb > g0 || kk > 0) ? 1u : 0u);
+                  tc::mma_f16_x<kPair>(d + h2 * 128, ad, bd, idesc_sw,
+                                       (kb > g0 || kk > 0) ? 1u : 0u);
                 }
               }
-              tc::commit(empty(s));
+              tc::commit_x<kPair>(empty(s));
               if (++s == NS) { s = 0; ph ^= 1; }
               continue;
             }
@@ -655,9 +726,9 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
               for (int kk = 0; kk < BK8 / 32; ++kk) {
                 const uint64_t bd = tc::sdesc_sw128(sb + kk * 32, 16, 1024);
                 const uint64_t ad = tc::sdesc_sw128(sa + kk * 32, 16, 1024);
-                tc::mma_f8(d, ad, bd, idesc, (kb > g0 || kk > 0) ? 1u : 0u);
+                tc::mma_f8_x<kPair>(d, ad, bd, idesc, (kb > g0 || kk > 0) ? 1u : 0u);
               }
-              tc::commit(empty(s));
+              tc::commit_x<kPair>(empty(s));
               if (++s == NS) { s = 0; ph ^= 1; }
               continue;
             }
@@ -672,20 +743,23 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
                 // second 128-row half starts 16 KiB later and accumulates into
                 // the second TMEM accumulator
                 const uint64_t ad = tc::sdesc_sw128(sa + h2 * (2 * HALF_BYTES) + kk * 32, 16, 1024);
-                tc::mma_f16(d + h2 * BN, ad, bd, idesc, (kb > g0 || kk > 0) ? 1u : 0u);
+                tc::mma_f16_x<kPair>(d + h2 * BN, ad, bd, idesc, (kb > g0 || kk > 0) ? 1u : 0u);
               }
             }
-            tc::commit(empty(s));
+            tc::commit_x<kPair>(empty(s));
             if (++s == NS) { s = 0; ph ^= 1; }
           }
           if (!ok) break;
-          tc::commit(tfull(acc));
+          tc::commit_x<kPair>(tfull(acc));
           if (++acc == G::kSlots) { acc = 0; aph ^= 1; }
         }
         if (!ok) break;
       }
       // Every MMA issued so far must complete before TMEM is freed.
-      tc::commit(drain);
+      if constexpr (kPair)
+        tc::commit_pair(drain, 1);
+      else
+        tc::commit(drain);
       const uint64_t t0 = tc::globaltimer();
       while (!tc::mbar_try_wait(drain, 0) && tc::globaltimer() - t0 < tc::wait_limit_ns()) {
       }
@@ -700,8 +774,9 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
     // regular tiles: warp (w - 2) / 4 takes one 128-column half of the tile;
     // tall tiles: it takes the accumulator of 128-row half (w - 2) / 4, all
     // 256 columns
+    // pair tiles: this CTA's rows are the tile's halves 2 rank, 2 rank + 1
     const int q = warp & 3, ta = kTall ? (warp - 2) >> 2 : 0;
-    const int half = 2 * ta + (q >> 1);  // this warp's 64-row half of the tile
+    const int half = 2 * (kPair ? (int)rank : ta) + (q >> 1);  // this warp's 64-row half of the tile
     const int c_lo = kTall ? 0 : kEpiCols * ((warp - 2) >> 2);
     float* stg = reinterpret_cast<float*>(smem + NS * G::kStageBytes + (warp - 2) * STG_BYTES);
     const uint32_t stg_addr = tc::smem_addr(stg);
@@ -710,7 +785,15 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
     int acc = 0;
     uint32_t aph = 0;
     bool aborted = false;
-    for (int64_t t = blockIdx.x; t < total && !aborted; t += gridDim.x) {
+    // an accumulator is free again once every epilogue warp (of both CTAs of
+    // a pair) has read it
+    auto release = [&](int a) {
+      if constexpr (kPair)
+        tc::mbar_arrive_cluster(tempty_i(a));
+      else
+        tc::mbar_arrive(tempty(a));
+    };
+    for (int64_t t = tfirst; t < total && !aborted; t += tstep) {
       const TileView T = S.view(t);
       if (T.swap) {
         // swapped checksum-row tile: this warp's half h of the tile (columns
@@ -729,7 +812,7 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
           if (ci == nchs - 1) {
             tc::fence_before_sync();
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(tempty(acc));
+            if (lane == 0) release(acc);
             if (++acc == G::kSlots) { acc = 0; aph ^= 1; }
           }
           if (j < T.n) {
@@ -743,7 +826,7 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
         if (nchs <= 0) {
           tc::fence_before_sync();
           __syncwarp();
-          if (lane == 0) tc::mbar_arrive(tempty(acc));
+          if (lane == 0) release(acc);
           if (++acc == G::kSlots) { acc = 0; aph ^= 1; }
         }
         continue;
@@ -751,13 +834,15 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
       const int64_t nkt = T.nkb * T.nseg;
       const int64_t gsz = (kPromote && T.kpg > 0 && T.kpg < nkt) ? T.kpg : nkt;
       const bool f8t = kF8 && T.f8;
-      const bool one_group = f8t ? group_end(T.gmask, 0, nkt) >= nkt : gsz >= nkt;
+      const bool one_group = f8t ? group_end_tile(T, 0, nkt) >= nkt : gsz >= nkt;
       // FP8 data tiles: this warp's 128 columns are one column block of B's
       // scales; the partial of a scale group is multiplied by its (power-of-two,
-      // so exact) block-scale product
+      // so exact) block-scale product.  This CTA's row block: a pair's odd CTA
+      // takes the tile's second one (none past the data: nothing is stored)
       const int64_t jb = f8t ? (T.colD + c_lo) / 128 : 0;
+      const float* sArow = (kPair && rank) ? T.sArow2 : T.sArow;
       auto f8scale = [&](int64_t kb) {
-        return __ldg(&T.sArow[kb]) * __ldg(&T.sB[kb * T.nsb + jb]);
+        return __ldg(&sArow[kb]) * __ldg(&T.sB[kb * T.nsb + jb]);
       };
       const int ncol = 64 * T.nbox;
       const int c_hi = min(c_lo + G::kCols, ncol);
@@ -928,7 +1013,7 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
         tc::fence_after_sync();
         const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (acc + ta) * BN;
         const int nch = (c_hi - c_lo + 31) / 32;
-        const float sc1 = (f8t && nch > 0) ? f8scale(0) : 1.0f;
+        const float sc1 = (f8t && nch > 0 && sArow) ? f8scale(0) : 1.0f;
         for (int ci = 0; ci < nch; ++ci) {
           float v[32];
           tc::tmem_ld32(base + c_lo + 32 * ci, v);
@@ -939,7 +1024,7 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
           if (ci == nch - 1) {
             tc::fence_before_sync();
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(tempty(acc));
+            if (lane == 0) release(acc);
             if (++acc == G::kSlots) { acc = 0; aph ^= 1; }
           }
           chunk(c_lo + 32 * ci, v);
@@ -948,7 +1033,7 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
         if (nch <= 0) {  // nothing of this tile in this warp's half
           tc::fence_before_sync();
           __syncwarp();
-          if (lane == 0) tc::mbar_arrive(tempty(acc));
+          if (lane == 0) release(acc);
           if (++acc == G::kSlots) { acc = 0; aph ^= 1; }
         }
       } else if constexpr (kPromote) {
@@ -958,11 +1043,11 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
         float accr[kEpiChunks][32];
         // FP8 data tiles: each scale group's partial times its block scales;
         // the next group's scale is loaded ahead
-        const bool scaled = f8t && c_lo < c_hi;
+        const bool scaled = f8t && c_lo < c_hi && sArow;
         float sc_next = scaled ? f8scale(0) : 1.0f;
         int64_t g1 = 0;
         for (int64_t g0 = 0; g0 < nkt; g0 = g1) {
-          g1 = f8t ? group_end(T.gmask, g0, nkt) : min(g0 + gsz, nkt);
+          g1 = f8t ? group_end_tile(T, g0, nkt) : min(g0 + gsz, nkt);
           const float sc = sc_next;
           if (scaled && g1 < nkt) sc_next = f8scale(g1);
           if (!tc::wait(tfull(acc), aph, abort)) { aborted = true; break; }
@@ -993,7 +1078,7 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
           }
           tc::fence_before_sync();
           __syncwarp();
-          if (lane == 0) tc::mbar_arrive(tempty(acc));
+          if (lane == 0) release(acc);
           if (++acc == 2) { acc = 0; aph ^= 1; }
         }
         if (aborted) break;
@@ -1010,19 +1095,28 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
 
 
   tc::fence_before_sync();
-  __syncthreads();
+  // a pair: neither CTA frees TMEM or exits while the other may still signal
+  // its barriers or (the issuer's MMAs) read its shared memory
+  if constexpr (kPair)
+    tc::cluster_sync();
+  else
+    __syncthreads();
   if (threadIdx.x == 0 && *abort) atomicExch(status, 1);
   if (warp == 1) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, TMEM_COLS);
+    if constexpr (kPair)
+      tc::tmem_dealloc_pair(tmem, TMEM_COLS);
+    else
+      tc::tmem_dealloc(tmem, TMEM_COLS);
   }
+  if constexpr (kPair) tc::cluster_sync();
 }
 
-template <bool kPromote, bool kTall, bool kF8>
+template <bool kPromote, bool kTall, bool kF8, bool kPair>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_bf16(const __grid_constant__ TcMaps M, const TcArgs g) {
-  const SingleSched<Geo<kTall>::kBM> S{&M, &g};
-  tc_body<kPromote, kTall, kF8>(S, g.status, g.wait_ns, g.stall_test, g.inj_hdr, g.inj);
+  const SingleSched<Geo<kTall, kPair>::kBM> S{&M, &g};
+  tc_body<kPromote, kTall, kF8, kPair>(S, g.status, g.wait_ns, g.stall_test, g.inj_hdr, g.inj);
 }
 
 // Many problems (grouped product).  The flattened tile list is a table of
@@ -1110,6 +1204,8 @@ struct GroupSched {
     V.sB = nullptr;
     V.nsb = 0;
     V.gmask = nullptr;
+    V.sArow2 = nullptr;
+    V.gmask2 = nullptr;
     if (e.w == kGrpSwapTile) {  // E16 columns 256 e.z .. + 255 from the swapped operands
       V.swap = 1;
       V.nsw_h = (int)cdiv(P.R16, 64);
@@ -1130,7 +1226,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                    int checksums, int* status, uint64_t wait_ns, const int32_t* inj_hdr,
                    const InjectEntry* inj, int kpg) {
   const GroupSched S{probs, maps, tiles, t_total, checksums != 0, kpg};
-  tc_body<false, false, false>(S, status, wait_ns, 0, inj_hdr, inj);
+  tc_body<false, false, false, false>(S, status, wait_ns, 0, inj_hdr, inj);
 }
 
 // Scale groups of the FP8 data tiles (see TcArgs::f8grp): one thread per word
@@ -1299,6 +1395,26 @@ bool use_tall(int64_t m, int64_t nkt, int kpg) {
   return m > BM && nkt >= 32;
 }
 
+// Pair tiles (256 x 256 on a CTA pair, see Geo).  Measured at 16384^3 against
+// the one-CTA schedules: FP8 (native data tiles) no faster (the MMA warp waits
+// on stage data 10 % of the time instead of 17 %, but a pair MMA that does not
+// wait runs about 5 % slower per SM than a one-CTA MMA); bf16 10 % slower than
+// tall tiles and the promoted bf16x3 / bf16x6 12-20 % slower than regular
+// tiles: a pair tile takes half as long as a tall one, so the same drift
+// between CTAs puts the tiles that share an operand panel twice as far apart
+// in K, and the product reads 17.8 GB from DRAM instead of 7.0; the promoted
+// products also wait twice as long for a free accumulator (both CTAs'
+// epilogues must release it).  FP8 with pair tiles: 4.097 ms per step against
+// 4.099 with regular tiles (the checksum-free product 3.12 against 3.04 ms).  So
+// no product uses them unless ABFT_PAIR_TILES=1 asks for them (0 or unset:
+// tall or regular tiles).
+bool use_pair(int64_t m, bool f8) {
+  const char* env = getenv("ABFT_PAIR_TILES");
+  (void)m;
+  (void)f8;
+  return env && env[0] == '1';
+}
+
 // Stride of the checksum tiles in the FP8 tile order.  Measured at FP8 16384^3:
 // all checksum tiles first (S = 1) 3.18 ms per ABFT product, S = 2 / 3 / 5
 // 3.28-3.38 ms, spread over the first 65 % of the schedule 3.35 ms (their
@@ -1322,6 +1438,35 @@ int64_t cs_stride(int64_t ncs, int64_t total, int grid) {
   };
   while (S > 1 && gcd(S, grid) != 1) --S;
   return S;
+}
+
+// CTA pairs (clusters of two) of a pair-tile kernel that fit on the GPU at
+// once: the persistent grid's size.  Clusters are placed within a GPC, so this
+// can be less than half the SM count.
+int g_pair_clusters[64] = {};
+int num_sms();
+int pair_clusters(const void* kernel, size_t smem) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && g_pair_clusters[dev]) return g_pair_clusters[dev];
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(2 * (num_sms() / 2), 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    n = num_sms() / 2;
+  }
+  if (dev >= 0 && dev < 64) g_pair_clusters[dev] = n;
+  return n;
 }
 
 int num_sms() {
@@ -1353,6 +1498,9 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
   const char* w = static_cast<const char*>(ws);
   const int64_t R16 = checksums ? P.L.acs_rows : 0, C16 = checksums ? P.L.bcs_cols : 0;
   TcMaps M;
+  // pair tiles: each CTA of a pair copies half of a full tile's B boxes
+  const bool pair = use_pair(d.m, op.a8 != nullptr);
+  const int bdepth = pair ? 2 : 4;
   for (int pl = 0; pl < kPlanes; ++pl) {
     const int cpl = pl < P.L.planes ? pl : 0;  // checksum planes beyond the dtype's repeat plane 0
     const void* acs = checksums ? w + P.L.acs + cpl * P.L.acs_plane : op.a[0];
@@ -1365,8 +1513,8 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
         !make_map(&M.bcs[pl], bcs, d.k, C16, bcs_ld, 64, BK) ||
         !make_map(&M.a128[pl], op.a[pl], d.m, d.k, op.lda, 64, BM) ||
         !make_map(&M.acs128[pl], acs, R16, d.k, acs_ld, 64, BM) ||
-        !make_map_boxes(&M.b4[pl], op.b[pl], d.k, d.n, op.ldb) ||
-        !make_map_boxes(&M.bcs4[pl], bcs, d.k, C16, bcs_ld))
+        !make_map_boxes(&M.b4[pl], op.b[pl], d.k, d.n, op.ldb, bdepth) ||
+        !make_map_boxes(&M.bcs4[pl], bcs, d.k, C16, bcs_ld, bdepth))
       return cudaErrorInvalidValue;
   }
   TcArgs g{};
@@ -1384,7 +1532,7 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
     if (!make_map_u8(&M.a[kF8Slot], op.a8, d.m, d.k, op.lda8, 128, BM / 2) ||
         !make_map_u8(&M.a128[kF8Slot], op.a8, d.m, d.k, op.lda8, 128, BM) ||
         !make_map_u8(&M.b[kF8Slot], op.b8, d.n, d.k, op.ldb8, 128, 64) ||
-        !make_map_u8(&M.b4[kF8Slot], op.b8, d.n, d.k, op.ldb8, 128, BN))
+        !make_map_u8(&M.b4[kF8Slot], op.b8, d.n, d.k, op.ldb8, 128, pair ? BN / 2 : BN))
       return cudaErrorInvalidValue;
     g.f8 = 1;
     g.sA = op.sA;
@@ -1395,8 +1543,8 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
     g.f8grp = op.f8grp;
     g.f8words = cdiv(cdiv(d.k, 128), 32);
   }
-  const bool tall = !g.f8 && use_tall(d.m, cdiv(d.k, BK) * op.nseg, g.kpg);
-  const int bm = tall ? Geo<true>::kBM : BM;
+  const bool tall = !pair && !g.f8 && use_tall(d.m, cdiv(d.k, BK) * op.nseg, g.kpg);
+  const int bm = (tall || pair) ? 256 : BM;
   g.ntm = (int)cdiv(d.m, bm);
   g.ntn = (int)cdiv(d.n, BN);
   g.ntr = checksums ? (int)cdiv(R16, bm) : 0;
@@ -1429,19 +1577,43 @@ cudaError_t launch_gemm_bf16(const Plan& P, const TcOperands& op, float* C, void
   g.stall_test = stall && stall[0] == '1';
   g.group_m = raster_group_rows(bm);
   g.wait_ns = g.stall_test ? 200000000ull : tc::kWaitLimitNs;
-  const auto kernel = g.f8 ? k_gemm_bf16<true, false, true>
-                           : g.kpg > 0 ? k_gemm_bf16<true, false, false>
-                                       : (tall ? k_gemm_bf16<false, true, false>
-                                               : k_gemm_bf16<false, false, false>);
-  const size_t smem = tall ? Geo<true>::kSmem : Geo<false>::kSmem;
+  const auto kernel =
+      pair ? (g.f8 ? k_gemm_bf16<true, false, true, true>
+                   : g.kpg > 0 ? k_gemm_bf16<true, false, false, true>
+                               : k_gemm_bf16<false, false, false, true>)
+           : (g.f8 ? k_gemm_bf16<true, false, true, false>
+                   : g.kpg > 0 ? k_gemm_bf16<true, false, false, false>
+                               : (tall ? k_gemm_bf16<false, true, false, false>
+                                       : k_gemm_bf16<false, false, false, false>));
+  const size_t smem =
+      pair ? Geo<false, true>::kSmem : (tall ? Geo<true>::kSmem : Geo<false>::kSmem);
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int grid = (int)std::min<int64_t>(g.t_total, num_sms());
-  if (grid == 0) return cudaSuccess;
-  if (g.f8) g.cs_stride = cs_stride(g.t_total - g.t_data, g.t_total, grid);  // 1 unless set
+  // tile workers: CTAs, or CTA pairs
+  const int workers = (int)std::min<int64_t>(
+      g.t_total, pair ? pair_clusters(reinterpret_cast<const void*>(kernel), smem) : num_sms());
+  if (workers == 0) return cudaSuccess;
+  if (g.f8) g.cs_stride = cs_stride(g.t_total - g.t_data, g.t_total, workers);  // 1 unless set
   e = cudaMemsetAsync(status, 0, sizeof(int), st);  // the status of this product
   if (e != cudaSuccess) return e;
-  kernel<<<grid, kThreads, smem, st>>>(M, g);
+  if (pair) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * workers, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kernel, M, g);
+    if (e != cudaSuccess) return e;
+  } else {
+    kernel<<<workers, kThreads, smem, st>>>(M, g);
+  }
   count_launches(1);
   return cudaGetLastError();
 }

@@ -468,14 +468,6 @@ __device__ __forceinline__ void stage_row32(float* stg, int lane, const float (&
     rowp[j ^ (lane & 7)] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
 }
 
-// Columns 4 j .. 4 j + 3 of row r of a staged block (one 16-byte unit; a
-// warp reading four rows' eight units touches every bank four times, the
-// minimum for 512 bytes).
-__device__ __forceinline__ float4 staged4(const float* stg, int r, int j) {
-  return reinterpret_cast<const float4*>(stg + r * 32)[j ^ (r & 7)];
-}
-
-
 // The kernel body, shared by the single-problem and the grouped product.
 // kPromote: the K loop runs in promotion groups whose accumulators the
 // epilogue sums in fp32 registers (a separate instantiation, so the register
@@ -876,47 +868,41 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
       const int cg0 = fused ? (int)(T.colD % T.g) : 0;
       const int64_t gi0 = fused ? T.colD / T.g : 0;
       // Column partials of this warp's 32 rows (r0 ..) for the chunk at
-      // column col, from the staged block: lane = (row group g4 of 8 rows,
-      // 4-column unit c4), one 16-byte read per row, then the four row groups
-      // summed by two shuffles; weights of the rows in their verify block
-      // (the 32 rows never straddle one).  They run one chunk late, after the
-      // next chunk's TMEM load and row partials, so the staged block is read
-      // well after its writes were fenced for the TMA store.
+      // column col, from the staged block (no shuffles: each lane sums one
+      // column); weights of the rows in their verify block (the 32 rows never
+      // straddle one).  They run one chunk late, after the next chunk's TMEM
+      // load and row partials, so the staged block is read well after its
+      // writes were fenced for the TMA store.
       bool cs_pend = false;
       int64_t cs_col = 0;
+      float* const obs_base = fused ? T.obs_col + (r0 >> 5) * 2 * T.n : nullptr;
+      // the row partials' column position, kept incrementally: the chunks of a
+      // tile come in column order, 32 apart, and the verify block width vb_c
+      // and the group width g are multiples of 32 when the sums are fused
+      int cm_run = fused ? (cm0 + c_lo) % T.vb_c : 0;             // (cm0 + c) % vb_c
+      int cg_run = fused ? (cg0 + c_lo) % g32 : 0;                // (cg0 + c) % g
+      int64_t gi_run = fused ? gi0 + (cg0 + c_lo) / g32 : 0;      // group of column colD + c
       auto colsum = [&](int64_t col) {
-        const int g4 = lane >> 3, c4 = lane & 7;
-        const int rb = rb0 + 8 * g4;
-        float se[4] = {0.f, 0.f, 0.f, 0.f}, sw[4] = {0.f, 0.f, 0.f, 0.f};
+        // lane = column: its 32 rows of the staged block (row r's 16-byte unit
+        // j at unit j ^ (r % 8): one conflict-free word per lane and row), in
+        // four independent partial sums.  Row r's weight (rb0 + r) scr lies in
+        // (0, 1] and is exact, so a weighted term never exceeds its element
+        // (no overflow that the element itself does not have) and an infinite
+        // element gives an infinite sum.
+        const int u4 = lane >> 2, sub = lane & 3;
+        float a[4] = {0.f, 0.f, 0.f, 0.f}, b[4] = {0.f, 0.f, 0.f, 0.f};
+        float wr = (float)rb0 * scr;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float4 x = staged4(stg, 8 * g4 + i, c4);
-          const float w = (float)(rb + i) * scr;
-          se[0] += x.x; se[1] += x.y; se[2] += x.z; se[3] += x.w;
-          sw[0] = fmaf(w, x.x, sw[0]); sw[1] = fmaf(w, x.y, sw[1]);
-          sw[2] = fmaf(w, x.z, sw[2]); sw[3] = fmaf(w, x.w, sw[3]);
+        for (int r = 0; r < 32; ++r) {
+          const float x = stg[r * 32 + ((u4 ^ (r & 7)) << 2) + sub];
+          a[r & 3] += x;
+          b[r & 3] = fmaf(wr, x, b[r & 3]);
+          wr += scr;
         }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          se[j] += __shfl_xor_sync(0xffffffffu, se[j], 8);
-          sw[j] += __shfl_xor_sync(0xffffffffu, sw[j], 8);
-          se[j] += __shfl_xor_sync(0xffffffffu, se[j], 16);
-          sw[j] += __shfl_xor_sync(0xffffffffu, sw[j], 16);
-        }
-        const int64_t c0 = col + 4 * c4;
-        if (g4 == 0 && r0 < T.m && c0 < T.n) {
-          float* o = T.obs_col + (r0 >> 5) * 2 * T.n + c0;
-          if (c0 + 4 <= T.n && (T.n & 3) == 0) {  // 16-byte aligned rows
-            *reinterpret_cast<float4*>(o) = make_float4(se[0], se[1], se[2], se[3]);
-            *reinterpret_cast<float4*>(o + T.n) = make_float4(sw[0], sw[1], sw[2], sw[3]);
-          } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-              if (c0 + j < T.n) {
-                o[j] = se[j];
-                o[T.n + j] = sw[j];
-              }
-          }
+        const int64_t c = col + lane;
+        if (r0 < T.m && c < T.n) {
+          obs_base[c] = (a[0] + a[1]) + (a[2] + a[3]);
+          obs_base[T.n + c] = (b[0] + b[1]) + (b[2] + b[3]);
         }
       };
       auto flush = [&]() {
@@ -963,23 +949,36 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
             // block; a 32-column chunk never straddles one, a group never
             // straddles the two column halves): sum_u (cm + u) scc v[u] as
             // scc (cm sum_u v[u] + sum_u u v[u])
-            const int cm = (cm0 + c) % T.vb_c + 1;
-            float s0 = 0.f, s1 = 0.f;
+            // four independent partial sums each (short dependency chains);
+            // s1 weighs v[u] by u / 32 < 1, so no weighted term exceeds its
+            // element, and sum_u (cm + u) scc v[u] = cm scc s0 + 32 scc s1
+            float a[4] = {0.f, 0.f, 0.f, 0.f}, b[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int u = 0; u < 32; ++u) {
-              s0 += v[u];
-              s1 = fmaf((float)u, v[u], s1);
+            for (int u = 0; u < 32; u += 4) {
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                a[j] += v[u + j];
+                b[j] = fmaf((float)(u + j) * 0.03125f, v[u + j], b[j]);
+              }
             }
+            const float s0 = (a[0] + a[1]) + (a[2] + a[3]);
+            const float s1 = (b[0] + b[1]) + (b[2] + b[3]);
             racc_e += s0;
-            racc_w = fmaf((float)cm * scc, s0, fmaf(scc, s1, racc_w));
-            const int cg = cg0 + c;  // column offset from the start of colD's group
-            if (((cg + 32) % g32) == 0 || c + 32 == ndcol || col + 32 >= T.n) {
+            racc_w = fmaf((float)(cm_run + 1) * scc, s0, fmaf(32.0f * scc, s1, racc_w));
+            if (cg_run + 32 == g32 || c + 32 == ndcol || col + 32 >= T.n) {
               if (rvalid) {
-                float* o = T.obs_row + (row * T.ngrp + gi0 + cg / g32) * 2;
+                float* o = T.obs_row + (row * T.ngrp + gi_run) * 2;
                 o[0] = racc_e;
                 o[1] = racc_w;
               }
               racc_e = racc_w = 0.f;
+            }
+            cm_run += 32;
+            if (cm_run >= T.vb_c) cm_run -= T.vb_c;
+            cg_run += 32;
+            if (cg_run >= g32) {
+              cg_run -= g32;
+              ++gi_run;
             }
           }
           if (!drow && !crow) return;

@@ -783,15 +783,49 @@ __global__ void __launch_bounds__(kThreads) k_lp_col_sq(const __nv_bfloat16* __r
   }
 }
 
-// out[o] = sqrt(sum_c part[o*so + c*sc]): fp32 partials summed in fp32 (the
-// norms scale the thresholds; a few u32 of relative error is immaterial).
-__global__ void k_lp_norms(const float* __restrict__ part, int64_t nout, int64_t nch, int64_t so,
-                           int64_t sc, double* __restrict__ out) {
-  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= nout) return;
-  float s = 0.f;
-  for (int64_t c = 0; c < nch; ++c) s += part[o * so + c * sc];
-  out[o] = (double)sqrtf(s);
+// The line norms and the threshold norms of their verify blocks in one pass:
+// CTA I (256 threads) takes the lines of verify block I, each line's norm
+// sqrt(sum_c part[t so + c sc]) from its fp32 partials (summed in fp32: the
+// norms scale the thresholds, a few u32 of relative error is immaterial), then
+// the block's norms as lp_blk_one forms them.
+__global__ void __launch_bounds__(kThreads) k_lp_norms_blk(
+    const float* __restrict__ part, int64_t nout, int64_t nch, int64_t so, int64_t sc,
+    double* __restrict__ nvec, int vb, int e, const double* __restrict__ cpart, int64_t cnch,
+    double* __restrict__ nblk) {
+  __shared__ float sh[kThreads / 32];
+  const int64_t I = blockIdx.x;
+  const int64_t t0 = I * vb, t1 = min(t0 + (int64_t)vb, nout);
+  const float scw = scalbnf(1.0f, -e);
+  float f0 = 0.f, f1 = 0.f;
+  for (int64_t t = t0 + threadIdx.x; t < t1; t += kThreads) {
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    int64_t c = 0;
+    for (; c + 4 <= nch; c += 4) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) s[j] += part[t * so + (c + j) * sc];
+    }
+    for (; c < nch; ++c) s[0] += part[t * so + c * sc];
+    const float v = sqrtf((s[0] + s[1]) + (s[2] + s[3]));
+    nvec[t] = (double)v;
+    const float wv = (float)(t - t0 + 1) * scw * v;
+    f0 = fmaf(v, v, f0);
+    f1 = fmaf(wv, wv, f1);
+  }
+  float q0 = 0.f, q1 = 0.f;
+  for (int64_t c = threadIdx.x; c < cnch; c += kThreads) {
+    q0 += (float)cpart[(2 * I) * cnch + c];
+    q1 += (float)cpart[(2 * I + 1) * cnch + c];
+  }
+  f0 = block_sumf(f0, sh);
+  f1 = block_sumf(f1, sh);
+  q0 = block_sumf(q0, sh);
+  q1 = block_sumf(q1, sh);
+  if (threadIdx.x == 0) {
+    nblk[4 * I + 0] = (double)sqrtf(f0);
+    nblk[4 * I + 1] = (double)sqrtf(f1);
+    nblk[4 * I + 2] = (double)sqrtf(q0);
+    nblk[4 * I + 3] = (double)sqrtf(q1);
+  }
 }
 
 // Threshold norms of verify block I from the line norms and the checksum
@@ -817,36 +851,6 @@ __device__ __forceinline__ void lp_blk_one(const double* __restrict__ nvec, int6
   nblk[4 * I + 3] = (double)sqrtf(q1);
 }
 
-// The same, one warp per verify block (the lanes split its lines and
-// partials).  Grid: ceil(nvb * 32 / 128) CTAs of 128 threads.
-__global__ void k_lp_blk(const double* __restrict__ nvec, int64_t len, int vb, int e,
-                         const double* __restrict__ part, int64_t nch, double* __restrict__ nblk) {
-  const int64_t I = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (I >= cdiv(len, vb)) return;
-  const float sc = scalbnf(1.0f, -e);
-  const int64_t t0 = I * vb, t1 = min(t0 + (int64_t)vb, len);
-  float f0 = 0.f, f1 = 0.f, q0 = 0.f, q1 = 0.f;
-  for (int64_t t = t0 + lane; t < t1; t += 32) {
-    const float v = (float)nvec[t], wv = (float)(t - t0 + 1) * sc * v;
-    f0 = fmaf(v, v, f0);
-    f1 = fmaf(wv, wv, f1);
-  }
-  for (int64_t c = lane; c < nch; c += 32) {
-    q0 += (float)part[(2 * I) * nch + c];
-    q1 += (float)part[(2 * I + 1) * nch + c];
-  }
-  f0 = warp_sumf(f0);
-  f1 = warp_sumf(f1);
-  q0 = warp_sumf(q0);
-  q1 = warp_sumf(q1);
-  if (lane == 0) {
-    nblk[4 * I + 0] = (double)sqrtf(f0);
-    nblk[4 * I + 1] = (double)sqrtf(f1);
-    nblk[4 * I + 2] = (double)sqrtf(q0);
-    nblk[4 * I + 3] = (double)sqrtf(q1);
-  }
-}
 
 // ---------------- split bf16x3 (binary32 inputs)
 
@@ -1446,9 +1450,8 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, cons
       k_x3A_block<<<dim3((unsigned)cdiv(d.k, kThreads), gy(P.f * P.bs)), kThreads, 0, st>>>(
           Af, d.lda, d.k, d.grid_p, P.bs, P.f, sp, P.L.acs_ld);
     }
-    k_lp_norms<<<(unsigned)cdiv(d.m, 128), 128, 0, st>>>(rowpart, d.m, nchr, nchr, 1, nArow);
-    k_lp_blk<<<(unsigned)cdiv(P.nvr * 32, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA,
-                                                         nchA, nAblk);
+    k_lp_norms_blk<<<(unsigned)P.nvr, kThreads, 0, st>>>(rowpart, d.m, nchr, nchr, 1, nArow,
+                                                       d.vb_rows, P.er, partA, nchA, nAblk);
     if (fastB) {
       k_x3B_rows<<<dim3((unsigned)cdiv(P.L.op_b_ld, kColsPerCta), (unsigned)nchB), kThreads, 0,
                    st>>>(
@@ -1460,10 +1463,9 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, cons
       k_x3B_rows_any<<<dim3((unsigned)cdiv(nchB, kThreads / 32), gy(P.nvc)), kThreads, 0, st>>>(
           Bf, d.ldb, d.k, d.n, d.vb_cols, P.ec, bcsp, P.L.bcs_ld, partB, nchB);
     }
-    k_lp_norms<<<(unsigned)cdiv(d.n, 128), 128, 0, st>>>(colpart, d.n, nchB, 1, d.n, nBcol);
-    k_lp_blk<<<(unsigned)cdiv(P.nvc * 32, 128), 128, 0, st>>>(nBcol, d.n, d.vb_cols, P.ec, partB,
-                                                         nchB, nBblk);
-    count_launches(6 + (P.bs > 0 ? 1 : 0) + (fastB ? 0 : 1));
+    k_lp_norms_blk<<<(unsigned)P.nvc, kThreads, 0, st>>>(colpart, d.n, nchB, 1, d.n, nBcol,
+                                                       d.vb_cols, P.ec, partB, nchB, nBblk);
+    count_launches(4 + (P.bs > 0 ? 1 : 0) + (fastB ? 0 : 1));
     return cudaGetLastError();
   }
   // FP8: the exact dequantised values go to bf16 operand planes, which the
@@ -1539,9 +1541,8 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, cons
   if (P.bs > 0)
     k_lpA_block<<<dim3((unsigned)cdiv(d.k, kThreads), gy(P.f * P.bs)), kThreads, 0, st>>>(
         A, lda, d.k, d.grid_p, P.bs, P.f, acs + 4 * P.nvr * P.L.acs_ld, P.L.acs_ld);
-  k_lp_norms<<<(unsigned)cdiv(d.m, 128), 128, 0, st>>>(rowpart, d.m, nchr, nchr, 1, nArow);
-  k_lp_blk<<<(unsigned)cdiv(P.nvr * 32, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA, nchr,
-                                                       nAblk);
+  k_lp_norms_blk<<<(unsigned)P.nvr, kThreads, 0, st>>>(rowpart, d.m, nchr, nchr, 1, nArow,
+                                                     d.vb_rows, P.er, partA, nchr, nAblk);
   if (f8B || (fastB && rows_aligned(B, ldb))) {
     SingleBUnits U{};
     U.base = EncBUnit{B, ldb, d.k, d.n, d.vb_cols, P.ec, bcs, P.L.bcs_ld, colpart, partB, nchB,
@@ -1560,10 +1561,9 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, cons
     k_lp_col_sq<<<dim3((unsigned)cdiv(d.n, kThreads), gy(nchB)), kThreads, 0, st>>>(
         B, ldb, d.k, d.n, colpart);
   }
-  k_lp_norms<<<(unsigned)cdiv(d.n, 128), 128, 0, st>>>(colpart, d.n, nchB, 1, d.n, nBcol);
-  k_lp_blk<<<(unsigned)cdiv(P.nvc * 32, 128), 128, 0, st>>>(nBcol, d.n, d.vb_cols, P.ec, partB, nchB,
-                                                       nBblk);
-  count_launches(nlaunch + 4 + (P.bs > 0 ? 1 : 0) + (fastB ? 0 : 2));
+  k_lp_norms_blk<<<(unsigned)P.nvc, kThreads, 0, st>>>(colpart, d.n, nchB, 1, d.n, nBcol,
+                                                     d.vb_cols, P.ec, partB, nchB, nBblk);
+  count_launches(nlaunch + 2 + (P.bs > 0 ? 1 : 0) + (fastB ? 0 : 2));
   return cudaGetLastError();
 }
 
@@ -1624,10 +1624,9 @@ cudaError_t launch_encode_lp_chained(const Plan& P, const void* Av, const void* 
         Af, d.lda, d.k, d.grid_p, P.bs, P.f, sp, P.L.acs_ld);
     ++launches;
   }
-  k_lp_norms<<<(unsigned)cdiv(d.m, 128), 128, 0, st>>>(rowpart, d.m, nchr, nchr, 1, nArow);
-  k_lp_blk<<<(unsigned)cdiv(P.nvr * 32, 128), 128, 0, st>>>(nArow, d.m, d.vb_rows, P.er, partA,
-                                                       nchA, nAblk);
-  launches += 2;
+  k_lp_norms_blk<<<(unsigned)P.nvr, kThreads, 0, st>>>(rowpart, d.m, nchr, nchr, 1, nArow,
+                                                     d.vb_rows, P.er, partA, nchA, nAblk);
+  ++launches;
   // B: operand planes and column norms from B; checksum columns carried (F of
   // the earlier product) or formed
   if (PR) {
@@ -1650,10 +1649,9 @@ cudaError_t launch_encode_lp_chained(const Plan& P, const void* Av, const void* 
         Bf, d.ldb, d.k, d.n, d.vb_cols, P.ec, bcsp, P.L.bcs_ld, partB, nchB);
     launches += 2;
   }
-  k_lp_norms<<<(unsigned)cdiv(d.n, 128), 128, 0, st>>>(colpart, d.n, nchB, 1, d.n, nBcol);
-  k_lp_blk<<<(unsigned)cdiv(P.nvc * 32, 128), 128, 0, st>>>(nBcol, d.n, d.vb_cols, P.ec, partB,
-                                                       nchB, nBblk);
-  launches += 2;
+  k_lp_norms_blk<<<(unsigned)P.nvc, kThreads, 0, st>>>(colpart, d.n, nchB, 1, d.n, nBcol,
+                                                     d.vb_cols, P.ec, partB, nchB, nBblk);
+  ++launches;
   count_launches(launches);
   return cudaGetLastError();
 }

@@ -1228,26 +1228,27 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_body<false, false, false, false>(S, status, wait_ns, 0, inj_hdr, inj);
 }
 
-// Scale groups of the FP8 data tiles (see TcArgs::f8grp): one thread per word
+// Scale groups of the FP8 data tiles (see TcArgs::f8grp): one warp per word
 // of one tile (tile row I of 128 rows, tile column Jt of 256 columns = scale
 // column blocks 2 Jt and 2 Jt + 1).  The products compare exactly in binary64.
 __global__ void k_f8_groups(const float* __restrict__ sA, const float* __restrict__ sB,
                             int64_t nsa, int64_t nsb, int64_t ntm, int64_t ntn, int64_t nkb,
                             int64_t words, uint32_t* __restrict__ out) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= ntm * ntn * words) return;
-  const int64_t w = idx % words, t = idx / words, Jt = t % ntn, I = t / ntn;
+  // one warp per word, lane = k-step of the word (the whole warp shares gw)
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= ntm * ntn * words) return;
+  const int64_t w = gw % words, t = gw / words, Jt = t % ntn, I = t / ntn;
   const int64_t J0 = 2 * Jt, J1 = 2 * Jt + 1;
-  uint32_t bits = 0;
-  for (int b = 0; b < 32; ++b) {
-    const int64_t kb = w * 32 + b;
-    if (kb < 1 || kb >= nkb) continue;
+  const int64_t kb = w * 32 + lane;
+  bool diff = false;
+  if (kb >= 1 && kb < nkb) {
     const double a1 = sA[I * nsa + kb], a0 = sA[I * nsa + kb - 1];
-    bool diff = a1 * (double)sB[kb * nsb + J0] != a0 * (double)sB[(kb - 1) * nsb + J0];
+    diff = a1 * (double)sB[kb * nsb + J0] != a0 * (double)sB[(kb - 1) * nsb + J0];
     if (J1 < nsb) diff |= a1 * (double)sB[kb * nsb + J1] != a0 * (double)sB[(kb - 1) * nsb + J1];
-    if (diff) bits |= 1u << b;
   }
-  out[idx] = bits;
+  const uint32_t bits = __ballot_sync(0xffffffffu, diff);
+  if (lane == 0) out[gw] = bits;
 }
 
 }  // namespace
@@ -1259,8 +1260,8 @@ cudaError_t launch_f8_groups(const float* sA, const float* sB, int64_t m, int64_
   const int64_t words = cdiv(cdiv(k, 128), 32), ntm = cdiv(m, BM), ntn = cdiv(n, BN);
   const int64_t nw = ntm * ntn * words;
   if (nw == 0) return cudaSuccess;
-  k_f8_groups<<<(unsigned)cdiv(nw, 256), 256, 0, st>>>(sA, sB, cdiv(k, 128), cdiv(n, 128), ntm,
-                                                       ntn, cdiv(k, 128), words, out);
+  k_f8_groups<<<(unsigned)cdiv(nw * 32, 256), 256, 0, st>>>(sA, sB, cdiv(k, 128), cdiv(n, 128),
+                                                            ntm, ntn, cdiv(k, 128), words, out);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -468,3 +468,29 @@ def test_non_finite_operand_decided_like_oracle(reread):
     key = lambda e: (e["row"], e["col"], e["kind"])
     assert nrep == on and sorted(map(key, rep)) == sorted(map(key, orep))
     assert np.array_equal(np.delete(C.cpu().numpy(), 37, axis=0), np.delete(Cg, 37, axis=0))
+
+
+@pytest.mark.parametrize("tall", ["0", "1"])
+def test_flip_near_binary32_max_located(tall, monkeypatch):
+    """A flip of exponent bit 30 of an element in [0.5, 1) gives a value in [2^127, 2^128):
+    finite, near the binary32 maximum.  The fused weighted sums scale every term by a weight
+    in (0, 1], so they stay finite like the element itself and the fault is located and
+    corrected (an unscaled weight of 31 overflowed to inf and left it uncorrectable)."""
+    monkeypatch.setenv("ABFT_TALL_TILES", tall)
+    m, n, k = 512, 512, 256
+    r = Run(m, n, k, 128, 128, seed=71)
+    C = r.C.cpu().numpy().astype(np.float64)
+    enc = oracle.Encoded(r.A64, r.B64, 128, 128, dtype="bf16")
+    # an element in [0.5, 1) at row and column offsets 29..31 of its 32 x 32 chunk
+    cand = [(i, j) for i in range(29, m, 32) for j in range(29, n, 32) if 0.5 <= abs(C[i, j]) < 1.0]
+    assert cand
+    i, j = cand[len(cand) // 2]
+    abft.abft_set_epilogue_faults(r.desc, r.ws, [(i, j, 30)])
+    abft.abft_gemm(r.desc, r.A, r.B, r.C, r.ws)
+    abft.abft_set_epilogue_faults(r.desc, r.ws, [])
+    Cf = r.C.cpu().numpy().astype(np.float64)
+    assert np.isfinite(Cf[i, j]) and abs(Cf[i, j]) >= 2.0 ** 127
+    st, rep, nrep = abft.abft_verify_correct(r.desc, r.C, r.ws, reread_C=0)
+    ost, orep, oC, on = enc.verify_correct(Cf)
+    assert st == abft.OK and positions(rep) == [(i, j, abft.KIND_CORRECTED)] == positions(orep)
+    check_fp32_product(r.C.cpu().numpy().astype(np.float64), r.A64, r.B64, oracle.gemm(r.A64, r.B64))

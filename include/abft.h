@@ -179,11 +179,12 @@ abft_status abft_workspace_layout(const abft_desc* desc, abft_ws_layout* out);
  * norms the detection thresholds use.  a_scale/b_scale: binary32 block scales
  * for ABFT_FP8_E4M3 (ceil(m/128) x ceil(k/128) and ceil(k/128) x ceil(n/128),
  * row-major), else NULL.  ABFT_FP8_E4M3: A and B are e4m3 bytes (lda, ldb in
- * elements); the scales must be powers of two, so that every dequantised value
- * e4m3(q) * scale is exact in bf16 -- the encode writes those values as bf16
- * operand planes into ws and forms the checksums from them (a value that is
- * not exact sets a status word of this workspace, and abft_verify_correct on
- * it returns ABFT_ERR_INVALID until the next encode).  When A and B have
+ * elements); the scales must be powers of two, 2^e with -117 <= e <= 119 (or
+ * zero), so that every dequantised value e4m3(q) * scale is exact in bf16 --
+ * the encode writes those values as bf16 operand planes into ws and forms the
+ * checksums from them (a scale outside that set, or a NaN code, sets a status
+ * word of this workspace, and abft_verify_correct on it returns
+ * ABFT_ERR_INVALID until the next encode).  When A and B have
  * 16-byte aligned rows (base and lda, ldb multiples of 16) the encode also
  * copies the scales, writes B's codes transposed (layout.f8bt) and the scale
  * groups of the product's data tiles (layout.f8grp), for the product's FP8

@@ -16,6 +16,8 @@
 
 #include <stdlib.h>
 
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace abft {
@@ -28,14 +30,19 @@ constexpr int kRowBatch = 8;               // rows whose loads are in flight tog
 constexpr int kRowBatchB = 16;             // the same for the B pass
 constexpr int kEncCols = 256;              // columns of one bf16 encode unit (8 per lane)
 constexpr int kEncWarps = kThreads / 32;   // warps sharing a unit's rows
-// A pass with asynchronous copies: each warp keeps kAsyncBatches batches of
-// kRowBatch rows in flight in its shared-memory ring (16 bytes per lane per
-// row), so the loads do not wait on registers.
-#ifndef ABFT_ENC_BATCHES
-#define ABFT_ENC_BATCHES 2
-#endif
-constexpr int kAsyncBatches = ABFT_ENC_BATCHES;
-constexpr int kRingBytesA = kEncWarps * kAsyncBatches * kRowBatch * 32 * 16;  // 64 KiB
+// A pass with asynchronous copies: each warp keeps Ring::kBatches batches of
+// kRowBatch rows in flight in its shared-memory ring (one slot per lane and
+// row: 16 bytes of bf16, 8 bytes of e4m3), so the loads do not wait on
+// registers.  Both keep 8 KiB per warp in flight (3 batches of bf16 rows, 4
+// of e4m3 rows; with 2 batches of 8-byte e4m3 rows the passes ran at 3.3-3.7
+// TB/s, short of the bytes in flight that the memory latency asks for).
+template <bool kF8>
+struct Ring {
+  using Slot = typename std::conditional<kF8, uint2, uint4>::type;
+  static constexpr int kBatches = kF8 ? 4 : 3;
+  static constexpr int kBytes = kEncWarps * kBatches * kRowBatch * 32 * (int)sizeof(Slot);
+};
+static_assert(Ring<true>::kBytes == 64 * 1024 && Ring<false>::kBytes == 96 * 1024, "ring sizes");
 
 // 16-byte asynchronous global -> shared copy; bytes < 16 zero-fills the rest
 // (0: nothing is read).  Both addresses 16-byte aligned.
@@ -386,8 +393,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_lpB_rows(const __nv_bfloat16* _
 
 // ---------------- streaming encode (16-byte aligned operands and row pitch)
 // Persistent CTAs; each warp copies its rows of the CTA's units into its own
-// shared-memory ring (16 bytes per lane per row) with asynchronous copies,
-// kAsyncBatches batches of kRowBatch rows ahead of the arithmetic.  The ring
+// shared-memory ring (one Ring slot per lane and row) with asynchronous copies,
+// Ring::kBatches batches of kRowBatch rows ahead of the arithmetic.  The ring
 // runs across units, so the loads of the next unit overlap the finishing of
 // the current one, and no register holds a load in flight.
 
@@ -445,24 +452,43 @@ struct Fp8Src {
 };
 
 // Eight e4m3 values (w0, w1 little-endian) times scale: the fp32 values (zero
-// from column cols on), their bf16 images, and whether any is inexact.
-__device__ __forceinline__ void dequant8(uint32_t w0, uint32_t w1, float scl, int64_t c0,
-                                         int64_t cols, float (&v)[8], __nv_bfloat16 (&o)[8],
-                                         bool& bad) {
+// from column cols on; `full`: all eight columns are below cols) and their bf16
+// images.
+__device__ __forceinline__ void dequant8(uint32_t w0, uint32_t w1, float scl, bool full,
+                                         int64_t c0, int64_t cols, float (&v)[8],
+                                         __nv_bfloat16 (&o)[8]) {
   const uint32_t w[2] = {w0, w1};
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
     const __half2_raw h2 = __nv_cvt_fp8x2_to_halfraw2(
         (__nv_fp8x2_storage_t)((w[t >> 1] >> (16 * (t & 1))) & 0xFFFFu), __NV_E4M3);
     const float2 f = __half22float2(__half2(h2));
-    v[2 * t] = c0 + 2 * t < cols ? f.x * scl : 0.f;
-    v[2 * t + 1] = c0 + 2 * t + 1 < cols ? f.y * scl : 0.f;
+    v[2 * t] = f.x * scl;
+    v[2 * t + 1] = f.y * scl;
+  }
+  if (!full) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (c0 + q >= cols) v[q] = 0.f;
   }
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    o[q] = __float2bfloat16_rn(v[q]);
-    bad |= !(__bfloat162float(o[q]) == v[q]);  // also catches NaN
+  for (int q = 0; q < 8; q += 2) {
+    const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[q], v[q + 1]);
+    o[q] = b2.x;
+    o[q + 1] = b2.y;
   }
+}
+// Every e4m3 value times `scl` is exact in bf16 (and in binary32) when the
+// scale is +-0 or +-2^e with -117 <= e <= 119: the codes carry at most 4
+// significant bits and lie between 2^-9 and 448 in magnitude, so the products
+// stay normal.  Checked once per row and lane instead of per value.
+__device__ __forceinline__ bool scale_exact(float scl) {
+  const uint32_t b = __float_as_uint(scl), e = (b >> 23) & 0xFFu;
+  return (b & 0x7FFFFFu) == 0u && ((e >= 10u && e <= 246u) || e == 0u);
+}
+// Any of the four e4m3 codes of w a NaN (S.1111.111)?
+__device__ __forceinline__ bool nan_code4(uint32_t w) {
+  return (((w & 0x7F7F7F7Fu) + 0x01010101u) & 0x80808080u) != 0u;
 }
 // Batches of kRowBatch rows of warp w (rows w + 8 j) in a unit of nrow rows.
 __device__ __forceinline__ int warp_batches(int nrow, int warp) {
@@ -527,9 +553,10 @@ struct GroupBUnits {
 // (an empty group once nothing is left keeps the group count uniform).
 template <class Units, bool kF8>
 struct RingIssuer {
+  using R = Ring<kF8>;
   const Units& U;
   const Fp8Src& f8;
-  uint4* ring;
+  typename R::Slot* ring;
   int warp, lane;
   int64_t u;
   int b, nbat, issued;
@@ -554,19 +581,30 @@ struct RingIssuer {
       load();
     }
     if (u < U.count()) {
-      uint4* slot = ring + (issued % kAsyncBatches) * kRowBatch * 32;
+      typename R::Slot* slot = ring + (issued % R::kBatches) * kRowBatch * 32;
       const int64_t c0 = src.col0 + 8 * lane, rem = src.cols - c0;
       const uint32_t esz = kF8 ? 1u : 2u;  // bytes per element
       const uint32_t nb = rem >= 8 ? 8u * esz : (rem > 0 ? (uint32_t)rem * esz : 0u);
+      // the batch's rows are kEncWarps apart: one pointer, advanced per row
+      const int tb = warp + kEncWarps * b * kRowBatch;
+      const uint32_t dst0 = static_cast<uint32_t>(__cvta_generic_to_shared(slot + lane));
+      if constexpr (kF8) {
+        const uint8_t* p = f8.q + (src.row0 + tb) * f8.ldq + c0;
+        const int64_t step = kEncWarps * f8.ldq;
 #pragma unroll
-      for (int r = 0; r < kRowBatch; ++r) {
-        const int t = warp + kEncWarps * (b * kRowBatch + r);
-        const bool in = t < src.nrow && nb > 0;
-        const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(slot + r * 32 + lane));
-        if constexpr (kF8)
-          cp_async8(dst, in ? f8.q + (src.row0 + t) * f8.ldq + c0 : f8.q, in ? nb : 0u);
-        else
-          cp_async16(dst, in ? src.base + (int64_t)t * src.ld + c0 : src.base, in ? nb : 0u);
+        for (int r = 0; r < kRowBatch; ++r, p += step) {
+          const bool in = tb + kEncWarps * r < src.nrow && nb > 0;
+          cp_async8(dst0 + r * 32 * (uint32_t)sizeof(typename R::Slot), in ? p : f8.q, in ? nb : 0u);
+        }
+      } else {
+        const __nv_bfloat16* p = src.base + (int64_t)tb * src.ld + c0;
+        const int64_t step = kEncWarps * src.ld;
+#pragma unroll
+        for (int r = 0; r < kRowBatch; ++r, p += step) {
+          const bool in = tb + kEncWarps * r < src.nrow && nb > 0;
+          cp_async16(dst0 + r * 32 * (uint32_t)sizeof(typename R::Slot), in ? p : src.base,
+                     in ? nb : 0u);
+        }
       }
       ++b;
     }
@@ -575,17 +613,38 @@ struct RingIssuer {
   }
 };
 
-// One row of a batch from the ring: bf16 rows are unpacked; e4m3 rows are
-// dequantised, and their bf16 values written to the operand plane (row `row`).
+// Per-batch addressing of the e4m3 source: the scale index of the batch's
+// first row (row0b: its row in the operand) and its plane row pointer; the
+// batch's kRowBatch rows are kEncWarps apart, so they span fewer than 128 rows
+// and at most two scale rows.
+struct F8Batch {
+  int64_t sidx;                // scale index of row row0b, column c0
+  int rin;                     // row0b % 128
+  __nv_bfloat16* plane;        // plane row row0b, column c0
+  __device__ __forceinline__ F8Batch() : sidx(0), rin(0), plane(nullptr) {}
+  __device__ __forceinline__ F8Batch(const Fp8Src& f8, int64_t row0b, int64_t c0)
+      : sidx((row0b >> 7) * f8.sld + (c0 >> 7)),
+        rin((int)(row0b & 127)),
+        plane(f8.plane + row0b * f8.pld + c0) {}
+};
+
+// Row r of a batch from the ring: bf16 rows are unpacked; e4m3 rows are
+// dequantised with their block scale, and their bf16 values written to the
+// operand plane.
 template <bool kF8>
-__device__ __forceinline__ void ring_row(const uint4& raw, const Fp8Src& f8, int64_t row,
-                                         bool valid, int64_t c0, int64_t cols, float (&v)[8],
-                                         bool& bad) {
+__device__ __forceinline__ void ring_row(const typename Ring<kF8>::Slot& raw, const Fp8Src& f8,
+                                         const F8Batch* fb, int r, bool valid, int64_t c0,
+                                         int64_t cols, float (&v)[8], bool& bad) {
   if constexpr (kF8) {
-    const float scl = (valid && c0 < cols) ? f8.sc[(row / 128) * f8.sld + c0 / 128] : 0.f;
+    const bool in = valid && c0 < cols;
+    const int64_t si = fb->sidx + (fb->rin + kEncWarps * r >= 128 ? f8.sld : 0);
+    const float scl = in ? f8.sc[si] : 0.f;
     __nv_bfloat16 o[8];
-    dequant8(raw.x, raw.y, scl, c0, cols, v, o, bad);
-    if (valid && c0 < f8.pld) store8(f8.plane + row * f8.pld + c0, o);
+    dequant8(raw.x, raw.y, scl, c0 + 8 <= cols, c0, cols, v, o);
+    // a value that is not exact in bf16 (scale not a power of two in range)
+    // or a NaN code (bytes past cols are zero-filled by the copy)
+    bad |= in && (!scale_exact(scl) || nan_code4(raw.x) || nan_code4(raw.y));
+    if (valid && c0 < f8.pld) store8(fb->plane + (int64_t)(kEncWarps * r) * f8.pld, o);
   } else {
     unpack8(raw, v);
   }
@@ -595,14 +654,16 @@ template <class Units, bool kF8>
 __global__ void __launch_bounds__(kThreads, 2) k_encA_stream(const Units U, const Fp8Src f8) {
   __shared__ float red[kEncWarps * kEncCols * 2];
   __shared__ float sh[kThreads / 32];
-  extern __shared__ uint4 ring_s[];  // kRingBytesA
+  using R = Ring<kF8>;
+  extern __shared__ uint4 ring_s[];  // R::kBytes
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint4* ring = ring_s + warp * kAsyncBatches * kRowBatch * 32;
+  typename R::Slot* ring =
+      reinterpret_cast<typename R::Slot*>(ring_s) + warp * R::kBatches * kRowBatch * 32;
   bool bad = false;
   RingIssuer<Units, kF8> is{U, f8, ring, warp, lane};
   is.start(blockIdx.x);
 #pragma unroll
-  for (int i = 0; i < kAsyncBatches; ++i) is.next();
+  for (int i = 0; i < R::kBatches; ++i) is.next();
   constexpr int kLanesPerRow = 32 / kRowBatch;
   int consumed = 0;
   for (int64_t u = blockIdx.x; u < U.count(); u += gridDim.x) {
@@ -614,15 +675,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_encA_stream(const Units U, cons
 #pragma unroll
     for (int q = 0; q < 8; ++q) se[q] = sw[q] = 0.f;
     for (int b = 0; b < nbat; ++b) {
-      cp_async_wait<kAsyncBatches - 1>();  // this warp's oldest batch has landed
-      const uint4* slot = ring + (consumed % kAsyncBatches) * kRowBatch * 32;
+      cp_async_wait<R::kBatches - 1>();  // this warp's oldest batch has landed
+      const typename R::Slot* slot = ring + (consumed % R::kBatches) * kRowBatch * 32;
       float sq[kRowBatch];
+      const int tb = warp + kEncWarps * b * kRowBatch;
+      const int64_t c0 = src.col0 + 8 * lane;
+      F8Batch fb = kF8 ? F8Batch(f8, src.row0 + tb, c0) : F8Batch();
 #pragma unroll
       for (int r = 0; r < kRowBatch; ++r) {
-        const int t = warp + kEncWarps * (b * kRowBatch + r);
+        const int t = tb + kEncWarps * r;
         float v[8];
-        ring_row<kF8>(slot[r * 32 + lane], f8, src.row0 + t, t < src.nrow,
-                      src.col0 + 8 * lane, src.cols, v, bad);
+        ring_row<kF8>(slot[r * 32 + lane], f8, &fb, r, t < src.nrow, c0, src.cols, v, bad);
         lpA_rows(v, t, sc, se, sw, sq[r]);
       }
       ++consumed;
@@ -642,14 +705,16 @@ template <class Units, bool kF8>
 __global__ void __launch_bounds__(kThreads, 2) k_encB_stream(const Units U, const Fp8Src f8) {
   __shared__ float red[kEncWarps * kEncCols];
   __shared__ float redq[kEncWarps * 32 * 2];
-  extern __shared__ uint4 ring_s[];  // kRingBytesA
+  using R = Ring<kF8>;
+  extern __shared__ uint4 ring_s[];  // R::kBytes
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint4* ring = ring_s + warp * kAsyncBatches * kRowBatch * 32;
+  typename R::Slot* ring =
+      reinterpret_cast<typename R::Slot*>(ring_s) + warp * R::kBatches * kRowBatch * 32;
   bool bad = false;
   RingIssuer<Units, kF8> is{U, f8, ring, warp, lane};
   is.start(blockIdx.x);
 #pragma unroll
-  for (int i = 0; i < kAsyncBatches; ++i) is.next();
+  for (int i = 0; i < R::kBatches; ++i) is.next();
   int consumed = 0;
   for (int64_t u = blockIdx.x; u < U.count(); u += gridDim.x) {
     const EncBUnit X = U.get(u);
@@ -668,18 +733,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_encB_stream(const Units U, cons
     }
     float q0 = 0.f, q1 = 0.f;
     for (int b = 0; b < nbat; ++b) {
-      cp_async_wait<kAsyncBatches - 1>();
-      const uint4* slot = ring + (consumed % kAsyncBatches) * kRowBatch * 32;
+      cp_async_wait<R::kBatches - 1>();
+      const typename R::Slot* slot = ring + (consumed % R::kBatches) * kRowBatch * 32;
       if (seg == 32) {
         // one verify block across the warp: the batch's 8 rows' (e, w) sums
         // reduce in one transposing butterfly (15 + 1 shuffles for 16 sums);
         // lane l then holds sum l / 2: row l / 4, e (l / 2 even) or w
         float sums[2 * kRowBatch];
+        const int tb = warp + kEncWarps * b * kRowBatch;
+        F8Batch fb = kF8 ? F8Batch(f8, l0 + tb, c0) : F8Batch();
 #pragma unroll
         for (int r = 0; r < kRowBatch; ++r) {
-          const int t = warp + kEncWarps * (b * kRowBatch + r);
+          const int t = tb + kEncWarps * r;
           float v[8];
-          ring_row<kF8>(slot[r * 32 + lane], f8, l0 + t, t < src.nrow, c0, X.n, v, bad);
+          ring_row<kF8>(slot[r * 32 + lane], f8, &fb, r, t < src.nrow, c0, X.n, v, bad);
           lpB_row(v, wq, cs, sums[2 * r], sums[2 * r + 1]);
         }
         ++consumed;
@@ -697,11 +764,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_encB_stream(const Units U, cons
             q0 = fmaf(sums[0], sums[0], q0);
         }
       } else {
+        const int tb = warp + kEncWarps * b * kRowBatch;
+        F8Batch fb = kF8 ? F8Batch(f8, l0 + tb, c0) : F8Batch();
 #pragma unroll
         for (int r = 0; r < kRowBatch; ++r) {
-          const int t = warp + kEncWarps * (b * kRowBatch + r);
+          const int t = tb + kEncWarps * r;
           float v[8], se, sw;
-          ring_row<kF8>(slot[r * 32 + lane], f8, l0 + t, t < src.nrow, c0, X.n, v, bad);
+          ring_row<kF8>(slot[r * 32 + lane], f8, &fb, r, t < src.nrow, c0, X.n, v, bad);
           lpB_row(v, wq, cs, se, sw);
           lpB_store_shfl(se, sw, seg, leader, t < src.nrow, X.bcs + (l0 + t) * X.ldcs + 4 * J,
                          q0, q1);
@@ -1171,8 +1240,9 @@ __global__ void __launch_bounds__(kThreads) k_fp8_dequant(const uint8_t* __restr
         const float v1 = c0 + 2 * t + 1 < cols ? f.y * sc[r] : 0.f;
         o[2 * t] = __float2bfloat16_rn(v0);
         o[2 * t + 1] = __float2bfloat16_rn(v1);
-        bad |= !(__bfloat162float(o[2 * t]) == v0) || !(__bfloat162float(o[2 * t + 1]) == v1);
       }
+      // the same rule as the streaming passes (bytes past cols are zero here)
+      bad |= c0 < cols && (!scale_exact(sc[r]) || nan_code4(w[0]) || nan_code4(w[1]));
       store8(out + i * ld + c0, o);
     }
   }
@@ -1271,26 +1341,28 @@ unsigned gy(int64_t v) { return (unsigned)(v < 65535 ? v : 65535); }
 template <class Units, bool kF8 = false>
 cudaError_t launch_stream_A(const Units& U, cudaStream_t st, const Fp8Src& f8 = Fp8Src{}) {
   cudaError_t e = cudaFuncSetAttribute(k_encA_stream<Units, kF8>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytesA);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Ring<kF8>::kBytes);
   if (e != cudaSuccess || U.cnt == 0) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t grid = std::min<int64_t>(U.cnt, 2 * (int64_t)std::max(sms, 1));  // 2 CTAs per SM
-  k_encA_stream<Units, kF8><<<(unsigned)grid, kThreads, kRingBytesA, st>>>(U, f8);
+  k_encA_stream<Units, kF8><<<(unsigned)grid, kThreads, Ring<kF8>::kBytes, st>>>(U, f8);
   count_launches(1);
   return cudaGetLastError();
 }
 template <class Units, bool kF8 = false>
 cudaError_t launch_stream_B(const Units& U, cudaStream_t st, const Fp8Src& f8 = Fp8Src{}) {
   cudaError_t e = cudaFuncSetAttribute(k_encB_stream<Units, kF8>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytesA);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Ring<kF8>::kBytes);
   if (e != cudaSuccess || U.cnt == 0) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t grid = std::min<int64_t>(U.cnt, 2 * (int64_t)std::max(sms, 1));
-  k_encB_stream<Units, kF8><<<(unsigned)grid, kThreads, kRingBytesA, st>>>(U, f8);
+  k_encB_stream<Units, kF8><<<(unsigned)grid, kThreads, Ring<kF8>::kBytes, st>>>(U, f8);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -159,8 +159,9 @@ def test_fp8_plain_product_matches(mode):
 
 
 def test_fp8_non_power_of_two_scale_is_rejected():
-    """A block scale that is not a power of two makes a dequantised value inexact in bf16:
-    the next verify reports ABFT_ERR_INVALID, and a correct call afterwards succeeds."""
+    """A block scale that is not a power of two (so the dequantised values need not be
+    exact in bf16) is rejected: the next verify reports ABFT_ERR_INVALID, and a correct call
+    afterwards succeeds."""
     def bad(sa):
         sa[0, 0] *= 1.1
     r = Run(256, 256, 256, 128, 128, seed=7, scale_fix=bad)

@@ -449,7 +449,73 @@ struct Fp8Src {
   __nv_bfloat16* plane;
   int64_t pld;      // plane leading dimension (columns cols .. pld-1 are zero)
   int* inexact;     // set when a value is not exact in bf16
+  // B pass of the native FP8 product: also write the codes transposed, B^T
+  // (cols x ldbt bytes, zeros past the rows), or nullptr
+  uint8_t* bt;
+  int64_t ldbt;
 };
+
+// The B pass's transposed copy of a unit (128 rows x 256 columns of e4m3
+// codes): each lane stores its 8 bytes of a row into a shared tile of 128 rows
+// x 64 words, word column c of row r at c ^ (4 ((r / 16) % 8)), so that the
+// transposing reads (16 consecutive rows of one word column, 8 row groups per
+// warp) hit 32 distinct banks; then each thread turns 16 rows x 4 columns into
+// four 16-byte pieces of rows of B^T (byte permutes), eight threads covering
+// 128 contiguous bytes of a row.
+constexpr int kBtBytes = 128 * 256;
+__device__ __forceinline__ void bt_store_row(uint32_t* tileT, int t, int lane, uint2 raw) {
+  const int s = ((t >> 4) & 7) << 2;
+  *reinterpret_cast<uint2*>(&tileT[t * 64 + ((2 * lane) ^ s)]) = raw;
+}
+
+// A 4 x 4 byte block transposed: r0..r3 are four rows of four bytes; o[j] is
+// column j (byte i from row i).
+__device__ __forceinline__ void transpose4x4(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3,
+                                             uint32_t (&o)[4]) {
+  const uint32_t lo01 = __byte_perm(r0, r1, 0x5140), hi01 = __byte_perm(r0, r1, 0x7362);
+  const uint32_t lo23 = __byte_perm(r2, r3, 0x5140), hi23 = __byte_perm(r2, r3, 0x7362);
+  o[0] = __byte_perm(lo01, lo23, 0x5410);
+  o[1] = __byte_perm(lo01, lo23, 0x7632);
+  o[2] = __byte_perm(hi01, hi23, 0x5410);
+  o[3] = __byte_perm(hi01, hi23, 0x7632);
+}
+
+// Write a unit's tile (see bt_store_row) to B^T: B rows k0 .. (kvalid of them
+// hold codes; the others are written as zeros), B columns n0 .. n0 + 255.
+__device__ __forceinline__ void bt_write_unit(const uint32_t* tileT, uint8_t* __restrict__ Bt,
+                                              int64_t ldbt, int64_t n, int64_t n0, int64_t k0,
+                                              int kvalid) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int item = threadIdx.x + kThreads * h;
+    const int kb = item & 7, ng = item >> 3;  // rows 16 kb .. +15, word column ng
+    const int64_t ok = k0 + 16 * kb;
+    uint32_t o[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t x[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = 16 * kb + 4 * q + i;
+        x[i] = r < kvalid ? tileT[r * 64 + (ng ^ (kb << 2))] : 0u;
+      }
+      uint32_t y[4];
+      transpose4x4(x[0], x[1], x[2], x[3], y);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) o[j][q] = y[j];
+    }
+    if (ok < ldbt) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t on = n0 + 4 * ng + j;
+        if (on < n)
+          *reinterpret_cast<uint4*>(Bt + on * ldbt + ok) = make_uint4(o[j][0], o[j][1], o[j][2],
+                                                                      o[j][3]);
+      }
+    }
+  }
+}
+
 
 // Eight e4m3 values (w0, w1 little-endian) times scale: the fp32 values (zero
 // from column cols on; `full`: all eight columns are below cols) and their bf16
@@ -706,10 +772,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_encB_stream(const Units U, cons
   __shared__ float red[kEncWarps * kEncCols];
   __shared__ float redq[kEncWarps * 32 * 2];
   using R = Ring<kF8>;
-  extern __shared__ uint4 ring_s[];  // R::kBytes
+  extern __shared__ uint4 ring_s[];  // R::kBytes (+ kBtBytes for e4m3: the B^T tile)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   typename R::Slot* ring =
       reinterpret_cast<typename R::Slot*>(ring_s) + warp * R::kBatches * kRowBatch * 32;
+  uint32_t* tileT = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(ring_s) + R::kBytes);
+  const bool wbt = kF8 && f8.bt != nullptr;  // this pass also writes B^T
   bool bad = false;
   RingIssuer<Units, kF8> is{U, f8, ring, warp, lane};
   is.start(blockIdx.x);
@@ -747,6 +815,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_encB_stream(const Units U, cons
           const int t = tb + kEncWarps * r;
           float v[8];
           ring_row<kF8>(slot[r * 32 + lane], f8, &fb, r, t < src.nrow, c0, X.n, v, bad);
+          if constexpr (kF8)
+            if (wbt) bt_store_row(tileT, t, lane, slot[r * 32 + lane]);
           lpB_row(v, wq, cs, sums[2 * r], sums[2 * r + 1]);
         }
         ++consumed;
@@ -771,6 +841,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_encB_stream(const Units U, cons
           const int t = tb + kEncWarps * r;
           float v[8], se, sw;
           ring_row<kF8>(slot[r * 32 + lane], f8, &fb, r, t < src.nrow, c0, X.n, v, bad);
+          if constexpr (kF8)
+            if (wbt) bt_store_row(tileT, t, lane, slot[r * 32 + lane]);
           lpB_row(v, wq, cs, se, sw);
           lpB_store_shfl(se, sw, seg, leader, t < src.nrow, X.bcs + (l0 + t) * X.ldcs + 4 * J,
                          q0, q1);
@@ -784,6 +856,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_encB_stream(const Units U, cons
       q1 = warp_sumf(q1);
     }
     lpB_finish(cs, q0, q1, X.n, X.vb, X.colpart, X.part, X.nch, X.cx, X.ry, red, redq);
+    if (wbt) {  // every warp's rows of the unit are in the tile (lpB_finish synchronised)
+      bt_write_unit(tileT, f8.bt, f8.ldbt, X.n, X.cx * kEncCols, l0, src.nrow);
+      __syncthreads();  // the tile is rewritten by the next unit
+    }
   }
   cp_async_wait<0>();
   if (kF8 && bad) atomicExch(f8.inexact, 1);
@@ -1354,15 +1430,15 @@ cudaError_t launch_stream_A(const Units& U, cudaStream_t st, const Fp8Src& f8 = 
 }
 template <class Units, bool kF8 = false>
 cudaError_t launch_stream_B(const Units& U, cudaStream_t st, const Fp8Src& f8 = Fp8Src{}) {
+  constexpr int kSmem = Ring<kF8>::kBytes + (kF8 ? kBtBytes : 0);
   cudaError_t e = cudaFuncSetAttribute(k_encB_stream<Units, kF8>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       Ring<kF8>::kBytes);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
   if (e != cudaSuccess || U.cnt == 0) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t grid = std::min<int64_t>(U.cnt, 2 * (int64_t)std::max(sms, 1));
-  k_encB_stream<Units, kF8><<<(unsigned)grid, kThreads, Ring<kF8>::kBytes, st>>>(U, f8);
+  k_encB_stream<Units, kF8><<<(unsigned)grid, kThreads, kSmem, st>>>(U, f8);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -1376,16 +1452,6 @@ cudaError_t launch_stream_B(const Units& U, cudaStream_t st, const Fp8Src& f8 = 
 // registers (byte permutes) and stores four 16-byte pieces of rows of B^T
 // (eight threads cover 128 contiguous bytes of a row).  Grid (ceil(n/128),
 // min(ceil(ldbt/128), 65535)).
-__device__ __forceinline__ void transpose4x4(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3,
-                                             uint32_t (&o)[4]) {
-  const uint32_t lo01 = __byte_perm(r0, r1, 0x5140), hi01 = __byte_perm(r0, r1, 0x7362);
-  const uint32_t lo23 = __byte_perm(r2, r3, 0x5140), hi23 = __byte_perm(r2, r3, 0x7362);
-  o[0] = __byte_perm(lo01, lo23, 0x5410);
-  o[1] = __byte_perm(lo01, lo23, 0x7632);
-  o[2] = __byte_perm(hi01, hi23, 0x5410);
-  o[3] = __byte_perm(hi01, hi23, 0x7632);
-}
-
 __global__ void __launch_bounds__(256) k_transpose_u8(const uint8_t* __restrict__ B, int64_t ldb,
                                                       int64_t k, int64_t n,
                                                       uint8_t* __restrict__ Bt, int64_t ldbt) {
@@ -1560,29 +1626,34 @@ cudaError_t launch_encode_lp(const Plan& P, const void* Av, const void* Bv, cons
       e = cudaMemcpyAsync(w + P.L.scales + sizeof(float) * nsa, b_scale, sizeof(float) * nsb,
                           cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
+    auto* pa = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_a);
+    auto* pb = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_b);
+    const auto* qa = static_cast<const uint8_t*>(Av);
+    const auto* qb = static_cast<const uint8_t*>(Bv);
+    fa = Fp8Src{qa, d.lda, static_cast<const float*>(a_scale), cdiv(d.k, 128), pa, P.L.op_a_ld,
+                flag, nullptr, 0};
+    fb = Fp8Src{qb, d.ldb, static_cast<const float*>(b_scale), cdiv(d.n, 128), pb, P.L.op_b_ld,
+                flag, nullptr, 0};
+    f8A = ((reinterpret_cast<uintptr_t>(qa) & 7) == 0) && d.lda % 8 == 0;
+    f8B = ((reinterpret_cast<uintptr_t>(qb) & 7) == 0) && d.ldb % 8 == 0 && fastB;
     // B^T of the codes and the scale groups of the data tiles, for the
-    // product's native data tiles (K-major B)
+    // product's native data tiles (K-major B); the streaming B pass writes
+    // B^T as it reads B, else a transposing pass does
     if (fp8_native() && aligned16(Av, d.lda) && aligned16(Bv, d.ldb)) {
       const float* ws_sa = reinterpret_cast<const float*>(w + P.L.scales);
       e = launch_f8_groups(ws_sa, ws_sa + nsa, d.m, d.n, d.k,
                            reinterpret_cast<uint32_t*>(w + P.L.f8grp), st);
       if (e != cudaSuccess) return e;
       const int64_t ldbt = (d.k + 15) / 16 * 16;
-      k_transpose_u8<<<dim3((unsigned)cdiv(d.n, 128), gy(cdiv(ldbt, 128))), 256, 0, st>>>(
-          static_cast<const uint8_t*>(Bv), d.ldb, d.k, d.n,
-          reinterpret_cast<uint8_t*>(w + P.L.f8bt), ldbt);
-      ++nlaunch;
+      if (f8B) {
+        fb.bt = reinterpret_cast<uint8_t*>(w + P.L.f8bt);
+        fb.ldbt = ldbt;
+      } else {
+        k_transpose_u8<<<dim3((unsigned)cdiv(d.n, 128), gy(cdiv(ldbt, 128))), 256, 0, st>>>(
+            qb, d.ldb, d.k, d.n, reinterpret_cast<uint8_t*>(w + P.L.f8bt), ldbt);
+        ++nlaunch;
+      }
     }
-    auto* pa = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_a);
-    auto* pb = reinterpret_cast<__nv_bfloat16*>(w + P.L.op_b);
-    const auto* qa = static_cast<const uint8_t*>(Av);
-    const auto* qb = static_cast<const uint8_t*>(Bv);
-    fa = Fp8Src{qa, d.lda, static_cast<const float*>(a_scale), cdiv(d.k, 128), pa, P.L.op_a_ld,
-                flag};
-    fb = Fp8Src{qb, d.ldb, static_cast<const float*>(b_scale), cdiv(d.n, 128), pb, P.L.op_b_ld,
-                flag};
-    f8A = ((reinterpret_cast<uintptr_t>(qa) & 7) == 0) && d.lda % 8 == 0;
-    f8B = ((reinterpret_cast<uintptr_t>(qb) & 7) == 0) && d.ldb % 8 == 0 && fastB;
     if (!f8A) {
       k_fp8_dequant<<<dim3((unsigned)cdiv(P.L.op_a_ld, 8 * kThreads), gy(cdiv(d.m, kDqRows))),
                       kThreads, 0, st>>>(qa, d.lda, d.m, d.k, fa.sc, pa, P.L.op_a_ld, flag);

@@ -1228,27 +1228,51 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_body<false, false, false, false>(S, status, wait_ns, 0, inj_hdr, inj);
 }
 
+// a1 b1 == a0 b0, decided without rounding: true when the scales are the same
+// bits, or when all four are normal powers of two whose products have the same
+// sign and exponent; false (a group boundary) otherwise.  Exact for the power-of-
+// two scales the FP8 path accepts; for any other scale it may split a run that
+// did not change, which costs an accumulator switch, never a wrong scale.
+__device__ __forceinline__ bool same_scale_product(float a1, float b1, float a0, float b0) {
+  const uint32_t x1 = __float_as_uint(a1), y1 = __float_as_uint(b1);
+  const uint32_t x0 = __float_as_uint(a0), y0 = __float_as_uint(b0);
+  if (x1 == x0 && y1 == y0) return true;
+  auto pow2 = [](uint32_t x) {
+    const uint32_t e = (x >> 23) & 0xFFu;
+    return (x & 0x7FFFFFu) == 0u && e != 0u && e != 0xFFu;
+  };
+  if (!(pow2(x1) && pow2(y1) && pow2(x0) && pow2(y0))) return false;
+  return ((x1 ^ y1) >> 31) == ((x0 ^ y0) >> 31) &&
+         ((x1 >> 23) & 0xFFu) + ((y1 >> 23) & 0xFFu) == ((x0 >> 23) & 0xFFu) + ((y0 >> 23) & 0xFFu);
+}
+
 // Scale groups of the FP8 data tiles (see TcArgs::f8grp): one warp per word
 // of one tile (tile row I of 128 rows, tile column Jt of 256 columns = scale
-// column blocks 2 Jt and 2 Jt + 1).  The products compare exactly in binary64.
+// column blocks 2 Jt and 2 Jt + 1), integer comparisons only (GB300's FP64
+// pipe made the binary64 products and conversions of an earlier version cost
+// 30 us).
 __global__ void k_f8_groups(const float* __restrict__ sA, const float* __restrict__ sB,
                             int64_t nsa, int64_t nsb, int64_t ntm, int64_t ntn, int64_t nkb,
                             int64_t words, uint32_t* __restrict__ out) {
-  // one warp per word, lane = k-step of the word (the whole warp shares gw)
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  // one warp per word, lane = k-step of the word (the whole warp shares the
+  // word); grid (the words of a tile row / 8 warps, tile rows up to 65535)
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // word within a tile row
   const int lane = threadIdx.x & 31;
-  if (gw >= ntm * ntn * words) return;
-  const int64_t w = gw % words, t = gw / words, Jt = t % ntn, I = t / ntn;
+  if (gw >= (uint32_t)(ntn * words)) return;
+  const int64_t w = gw % (uint32_t)words, Jt = gw / (uint32_t)words;
   const int64_t J0 = 2 * Jt, J1 = 2 * Jt + 1;
   const int64_t kb = w * 32 + lane;
-  bool diff = false;
-  if (kb >= 1 && kb < nkb) {
-    const double a1 = sA[I * nsa + kb], a0 = sA[I * nsa + kb - 1];
-    diff = a1 * (double)sB[kb * nsb + J0] != a0 * (double)sB[(kb - 1) * nsb + J0];
-    if (J1 < nsb) diff |= a1 * (double)sB[kb * nsb + J1] != a0 * (double)sB[(kb - 1) * nsb + J1];
+  for (int64_t I = blockIdx.y; I < ntm; I += gridDim.y) {
+    bool diff = false;
+    if (kb >= 1 && kb < nkb) {
+      const float a1 = sA[I * nsa + kb], a0 = sA[I * nsa + kb - 1];
+      diff = !same_scale_product(a1, sB[kb * nsb + J0], a0, sB[(kb - 1) * nsb + J0]);
+      if (J1 < nsb)
+        diff |= !same_scale_product(a1, sB[kb * nsb + J1], a0, sB[(kb - 1) * nsb + J1]);
+    }
+    const uint32_t bits = __ballot_sync(0xffffffffu, diff);
+    if (lane == 0) out[(I * ntn + Jt) * words + w] = bits;
   }
-  const uint32_t bits = __ballot_sync(0xffffffffu, diff);
-  if (lane == 0) out[gw] = bits;
 }
 
 }  // namespace
@@ -1260,8 +1284,9 @@ cudaError_t launch_f8_groups(const float* sA, const float* sB, int64_t m, int64_
   const int64_t words = cdiv(cdiv(k, 128), 32), ntm = cdiv(m, BM), ntn = cdiv(n, BN);
   const int64_t nw = ntm * ntn * words;
   if (nw == 0) return cudaSuccess;
-  k_f8_groups<<<(unsigned)cdiv(nw * 32, 256), 256, 0, st>>>(sA, sB, cdiv(k, 128), cdiv(n, 128),
-                                                            ntm, ntn, cdiv(k, 128), words, out);
+  k_f8_groups<<<dim3((unsigned)cdiv(ntn * words * 32, 256), (unsigned)std::min<int64_t>(ntm, 65535)),
+                256, 0, st>>>(
+      sA, sB, cdiv(k, 128), cdiv(n, 128), ntm, ntn, cdiv(k, 128), words, out);
   count_launches(1);
   return cudaGetLastError();
 }

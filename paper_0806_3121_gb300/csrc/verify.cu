@@ -141,6 +141,34 @@ __device__ int col_line(const CheckArgs& a, int64_t I, int64_t j, double& re, do
   return nf;
 }
 
+// The same computed by one warp (lanes split the rows; sums in the element
+// type, then added across the lanes); residuals and thresholds valid in every
+// lane.
+template <typename TC>
+__device__ int col_line_warp(const CheckArgs& a, int64_t I, int64_t j, double& re, double& rw,
+                             double& te, double& tw) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i0 = I * a.vb_r, i1 = min(i0 + (int64_t)a.vb_r, a.m);
+  const TC sc = (TC)scalbn(1.0, -a.er);
+  const TC* C = static_cast<const TC*>(a.C);
+  TC se = 0, sw = 0;
+  int nf = 0;
+  const int len = (int)(i1 - i0);
+  for (int t = lane; t < len; t += 32) {
+    const TC x = C[(i0 + t) * a.ldc + j];
+    se += x;
+    sw = fma_t<TC>((TC)(t + 1) * sc, x, sw);
+    nf += isfinite(x) ? 0 : 1;
+  }
+  se = warp_sum_t<TC>(se);
+  sw = warp_sum_t<TC>(sw);
+  nf = warp_isum(nf);
+  re = (double)se - a.E[(2 * I) * a.n + j];
+  rw = (double)sw - a.E[(2 * I + 1) * a.n + j];
+  col_taus(a, I, j, te, tw);
+  return nf;
+}
+
 // Residuals of row line (i, J) computed by one warp; the sums and the
 // non-finite count are valid in every lane, the residuals and thresholds in
 // lane 0 only (binary64 work done once per line).
@@ -212,25 +240,68 @@ __global__ void __launch_bounds__(kThreads) k_row_check(const CheckArgs a) {
   if (slot < kCapFlags) a.rowf[slot] = FlagEntry{(int32_t)i, (int32_t)J, nf, 0, re, rw};
 }
 
+// Screen of the fused checks: a line whose binary32 evaluation passes with a
+// margin is one the binary64 rule passes, so only the others are evaluated in
+// binary64 (GB300's FP64 pipe is narrow: the binary64 sums of every line took
+// most of the verify).  With s the binary32 sum of the observed partials (nt of
+// them, absolute sum b), e the expected checksum rounded to binary32 and r the
+// binary32 residual s - e: the binary64 residual is at most
+// |r| + (nt + 2) u32 (b + |e| + |r|) in magnitude (u32 = 2^-24; the partials'
+// sum, e's rounding and the subtraction), and the binary32 threshold t is
+// within a few u32 of the binary64 one, so |r| + (nt + 2) u32 (b + |e| + |r|)
+// <= 0.99 t implies the binary64 test passes.  Non-finite or overflowing
+// values never pass the screen.
+__device__ __forceinline__ bool fused_screen(float sum, float e, float b, float t, float slack) {
+  const float r = sum - e;
+  const float lhs = fabsf(r) + slack * (b + fabsf(e) + fabsf(r));
+  return lhs < 3.0e38f && t < 3.0e38f && lhs <= 0.99f * t;  // false for NaN
+}
+constexpr float kU32 = 5.9604645e-8f;  // 2^-24
+
 // Column lines from the observed partial sums the product's epilogue wrote
 // (one per 32 rows): obs[(block*2 + 0|1)*n + j].  Verify blocks span whole
 // 32-row blocks.  A non-finite observed sum marks the line non-finite (the
-// locate step then scans C for it).
+// locate step then scans C for it).  The lines that pass the binary32 screen
+// are done; the others are decided by the binary64 rule.
 __global__ void __launch_bounds__(kThreads) k_col_fused(const CheckArgs a, const float* obs,
                                                         int64_t ntr) {
+  __shared__ float tI[2];  // the verify block's threshold factors (binary32)
   const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-  if (j >= a.n) return;
+  const bool jv = j < a.n;
   const int64_t tpb = a.vb_r / 32;  // 32-row blocks per verify block
+  const float nbj = jv ? (float)a.nBcol[j] : 0.f;
+  const float slack = (float)(tpb + 2) * kU32;
   for (int64_t I = blockIdx.y; I < a.nvr; I += gridDim.y) {
+    __syncthreads();  // every thread has read the previous tI
+    if (threadIdx.x == 0) {
+      tI[0] = (float)(a.s * (a.f1c * a.nAblk[4 * I + 0] + a.f2c * a.nAblk[4 * I + 2] + a.carA[2 * I]));
+      tI[1] = (float)(a.s * (a.f1c * a.nAblk[4 * I + 1] + a.f2c * a.nAblk[4 * I + 3] +
+                             a.carA[2 * I + 1]));
+    }
+    __syncthreads();
+    if (!jv) continue;
     const int64_t i0 = I * a.vb_r, i1 = min(i0 + (int64_t)a.vb_r, a.m);
     if (touches_erased(a.erased, a.bs, a.bc, i0, i1, j, j + 1)) continue;
+    const int64_t tr0 = I * tpb, tr1 = min((I + 1) * tpb, ntr);
+    float s0 = 0.f, s1 = 0.f, b0 = 0.f, b1 = 0.f;
+    for (int64_t tr = tr0; tr < tr1; ++tr) {
+      const float x0 = obs[(tr * 2 + 0) * a.n + j], x1 = obs[(tr * 2 + 1) * a.n + j];
+      s0 += x0;
+      s1 += x1;
+      b0 += fabsf(x0);
+      b1 += fabsf(x1);
+    }
+    const double E0 = a.E[(2 * I) * a.n + j], E1 = a.E[(2 * I + 1) * a.n + j];
+    if (fused_screen(s0, (float)E0, b0, nbj * tI[0], slack) &&
+        fused_screen(s1, (float)E1, b1, nbj * tI[1], slack))
+      continue;
     double se = 0.0, sw = 0.0;
-    for (int64_t tr = I * tpb; tr < min((I + 1) * tpb, ntr); ++tr) {
+    for (int64_t tr = tr0; tr < tr1; ++tr) {
       se += (double)obs[(tr * 2 + 0) * a.n + j];
       sw += (double)obs[(tr * 2 + 1) * a.n + j];
     }
     const int nf = (isfinite(se) && isfinite(sw)) ? 0 : 1;
-    const double re = se - a.E[(2 * I) * a.n + j], rw = sw - a.E[(2 * I + 1) * a.n + j];
+    const double re = se - E0, rw = sw - E1;
     double te, tw;
     col_taus(a, I, j, te, tw);
     if (nf == 0 && !is_flagged(re, rw, te, tw)) continue;
@@ -240,21 +311,51 @@ __global__ void __launch_bounds__(kThreads) k_col_fused(const CheckArgs a, const
 }
 
 // Row lines from the per-row partial sums over column groups of g columns:
-// obs[(i*ngrp + group)*2 + 0|1].  One thread per (row, verify block).
+// obs[(i*ngrp + group)*2 + 0|1].  One thread per (row, verify block); the
+// verify blocks' threshold factors in binary32 in shared memory (up to
+// kRowTauSmem blocks; more: computed per line), then the same screen.
+constexpr int kRowTauSmem = 2048;
 __global__ void __launch_bounds__(kThreads) k_row_fused(const CheckArgs a, const float* obs,
                                                         int64_t g, int64_t ngrp) {
+  __shared__ float tJ[2 * kRowTauSmem];
+  const bool smem_tau = a.nvc <= kRowTauSmem;
+  if (smem_tau) {
+    for (int64_t J = threadIdx.x; J < a.nvc; J += kThreads) {
+      tJ[2 * J] = (float)(a.s * (a.f1r * a.nBblk[4 * J + 0] + a.f2r * a.nBblk[4 * J + 2] +
+                                 a.carB[2 * J]));
+      tJ[2 * J + 1] = (float)(a.s * (a.f1r * a.nBblk[4 * J + 1] + a.f2r * a.nBblk[4 * J + 3] +
+                                     a.carB[2 * J + 1]));
+    }
+    __syncthreads();
+  }
   const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (t >= a.m * a.nvc) return;
   const int64_t i = t / a.nvc, J = t % a.nvc;
   const int64_t j0 = J * a.vb_c, j1 = min(j0 + (int64_t)a.vb_c, a.n);
   if (touches_erased(a.erased, a.bs, a.bc, i, i + 1, j0, j1)) return;
+  const int64_t g0 = j0 / g, g1 = min(cdiv(j1, g), ngrp);
+  const double F0 = a.F[i * a.Cc + 2 * J], F1 = a.F[i * a.Cc + 2 * J + 1];
+  if (smem_tau) {
+    float s0 = 0.f, s1 = 0.f, b0 = 0.f, b1 = 0.f;
+    for (int64_t gr = g0; gr < g1; ++gr) {
+      const float x0 = obs[(i * ngrp + gr) * 2 + 0], x1 = obs[(i * ngrp + gr) * 2 + 1];
+      s0 += x0;
+      s1 += x1;
+      b0 += fabsf(x0);
+      b1 += fabsf(x1);
+    }
+    const float na = (float)a.nArow[i], slack = (float)(g1 - g0 + 2) * kU32;
+    if (fused_screen(s0, (float)F0, b0, na * tJ[2 * J], slack) &&
+        fused_screen(s1, (float)F1, b1, na * tJ[2 * J + 1], slack))
+      return;
+  }
   double se = 0.0, sw = 0.0;
-  for (int64_t gr = j0 / g; gr < min(cdiv(j1, g), ngrp); ++gr) {
+  for (int64_t gr = g0; gr < g1; ++gr) {
     se += (double)obs[(i * ngrp + gr) * 2 + 0];
     sw += (double)obs[(i * ngrp + gr) * 2 + 1];
   }
   const int nf = (isfinite(se) && isfinite(sw)) ? 0 : 1;
-  const double re = se - a.F[i * a.Cc + 2 * J], rw = sw - a.F[i * a.Cc + 2 * J + 1];
+  const double re = se - F0, rw = sw - F1;
   double te, tw;
   row_taus(a, i, J, te, tw);
   if (nf == 0 && !is_flagged(re, rw, te, tw)) return;
@@ -313,10 +414,11 @@ struct SinglePol {
   __device__ __forceinline__ double expect_row(int, int64_t i, int64_t J) const {
     return a.F[i * a.Cc + 2 * J];
   }
+  // Warp-wide; the result is valid in every lane.
   __device__ __forceinline__ bool recheck_col(int, int64_t I, int64_t j, double& re,
                                               double& rw) const {
     double te, tw;
-    col_line<TC>(a, I, j, re, rw, te, tw);
+    col_line_warp<TC>(a, I, j, re, rw, te, tw);
     return is_flagged(re, rw, te, tw);
   }
   // Warp-wide; the result is valid in lane 0.
@@ -541,7 +643,7 @@ __device__ __forceinline__ void locate_body(const Pol& A, int32_t* cnt, const Fl
       if (r2 == r && c2 / G.vb_c == J) dup_r = true;
     }
     double re, rw;
-    if (!dup_c && lane == 0 && A.recheck_col(p, I, c, re, rw))
+    if (!dup_c && A.recheck_col(p, I, c, re, rw) && lane == 0)  // warp-wide
       push_report(report, cnt, p, -1, c, ABFT_KIND_UNCORRECTABLE, 0, 0.0, re, rw);
     if (!dup_r && A.recheck_row(p, r, J, re, rw))
       push_report(report, cnt, p, r, -1, ABFT_KIND_UNCORRECTABLE, 1, 0.0, re, rw);
@@ -608,18 +710,22 @@ struct GroupPol {
   __device__ __forceinline__ double expect_row(int p, int64_t i, int64_t J) const {
     return grp_expect_row(probs[p], i, J, 0);
   }
-  // Column line re-read from C (binary32 sums, as the product's epilogue).
+  // Column line re-read from C (binary32 sums, as the product's epilogue),
+  // warp-wide (lanes split the rows); the result is valid in every lane.
   __device__ __forceinline__ bool recheck_col(int p, int64_t I, int64_t j, double& re,
                                               double& rw) const {
     const GProb& P = probs[p];
+    const int lane = threadIdx.x & 31;
     const int64_t i0 = I * kGrpVbR, i1 = min(i0 + (int64_t)kGrpVbR, P.m);
     const float sc = scalbnf(1.0f, -kGrpEr);
     float se = 0.f, sw = 0.f;
-    for (int64_t i = i0; i < i1; ++i) {
+    for (int64_t i = i0 + lane; i < i1; i += 32) {
       const float x = P.C[i * P.ldc + j];
       se += x;
       sw = fmaf((float)(i - i0 + 1) * sc, x, sw);
     }
+    se = warp_sum_t<float>(se);
+    sw = warp_sum_t<float>(sw);
     re = (double)se - grp_expect_col(P, I, j, 0);
     rw = (double)sw - grp_expect_col(P, I, j, 1);
     double te, tw;

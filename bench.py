@@ -49,11 +49,11 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # Measured DRAM read + write per launch of the product kernel at the bench workloads (ncu
 # dram__bytes_read.sum + dram__bytes_write.sum, one launch after three warm-up products; the
 # counters take one pass, see profiles/), or None when the kernel changed since it was
-# captured.  f64: 45.50 + 1.08 GB; bf16 (256-row tiles): 6.77 + 1.16 GB; fp8 (e4m3 data
-# tiles): 5.78 + 1.47 GB; bf16x6: 60.17 + 1.40 GB; grouped 4096 (ABFT product, default
-# tuning): 19.13 + 20.56 GB.
-TRAFFIC_BYTES = {"f64_11264_grid22": 46.58e9, "bf16_16384": 7.93e9, "fp8_16384": 7.25e9,
-                 "bf16x6_16384": 61.57e9, "bf16_grouped_4096": 39.69e9}
+# captured.  f64: 34.22 + 1.10 GB; bf16 (256-row tiles): 6.77 + 1.17 GB; fp8 (e4m3 data
+# tiles): 5.72 + 1.63 GB; bf16x6: 59.96 + 1.58 GB; grouped 4096 (ABFT product, default
+# tuning): 18.97 + 20.58 GB.
+TRAFFIC_BYTES = {"f64_11264_grid22": 35.32e9, "bf16_16384": 7.95e9, "fp8_16384": 7.35e9,
+                 "bf16x6_16384": 61.54e9, "bf16_grouped_4096": 39.54e9}
 
 
 def bf16_peak():

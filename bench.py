@@ -50,10 +50,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum, one launch after three warm-up products; the
 # counters take one pass, see profiles/), or None when the kernel changed since it was
 # captured.  f64: 34.22 + 1.10 GB; bf16 (256-row tiles): 6.77 + 1.17 GB; fp8 (e4m3 data
-# tiles): 5.72 + 1.63 GB; bf16x6: 59.96 + 1.58 GB; grouped 4096 (ABFT product, default
-# tuning): 18.97 + 20.58 GB.
+# tiles): 5.72 + 1.63 GB; bf16x6: 59.96 + 1.58 GB; grouped 4096 (ABFT product after the
+# autotuner, default tuning): 19.06 + 20.58 GB.
 TRAFFIC_BYTES = {"f64_11264_grid22": 35.32e9, "bf16_16384": 7.95e9, "fp8_16384": 7.35e9,
-                 "bf16x6_16384": 61.54e9, "bf16_grouped_4096": 39.54e9}
+                 "bf16x6_16384": 61.54e9, "bf16_grouped_4096": 39.64e9}
 
 
 def bf16_peak():
@@ -543,10 +543,19 @@ def run_workload(w, args, dev, rank, world, secondary=False):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not secondary:
         if A_np is None:
+            # the leading 1024 rows of A and columns of B, as exact binary64 values
             import oracle
-            A_np = oracle.bf16_to_f64(A[:1024].cpu().view(torch.int16).numpy().view(np.uint16))
-            B_np = oracle.bf16_to_f64(B[:, :1024].contiguous().cpu().view(torch.int16).numpy()
-                                      .view(np.uint16))
+            if w.dtype == "bf16":
+                A_np = oracle.bf16_to_f64(A[:1024].cpu().view(torch.int16).numpy().view(np.uint16))
+                B_np = oracle.bf16_to_f64(B[:, :1024].contiguous().cpu().view(torch.int16).numpy()
+                                          .view(np.uint16))
+            elif w.dtype == "fp8":
+                A_np = oracle.dequant_e4m3(A[:1024].cpu().numpy(), scales["a_scale"][:8].cpu().numpy())
+                B_np = oracle.dequant_e4m3(B[:, :1024].contiguous().cpu().numpy(),
+                                           scales["b_scale"][:, :8].contiguous().cpu().numpy())
+            else:  # the split dtypes take binary32 inputs
+                A_np = A[:1024].double().cpu().numpy()
+                B_np = B[:, :1024].double().cpu().numpy()
             out["cpu_baseline"] = cpu_baseline(A_np, B_np, w, 8, seed)
         else:
             out["cpu_baseline"] = cpu_baseline(A_np, B_np, w, 4, seed)

@@ -70,11 +70,11 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     def run(job):
         # A compiler process that crashes (a signal, not a diagnostic) is run
-        # again, up to twice, with a larger stack: the Arm toolchain has been
-        # seen to crash now and then on the tensor-core product's translation
-        # unit and to succeed on the next run of the same command.
+        # again, up to three times, with a larger stack: the Arm toolchain has
+        # been seen to crash now and then on the tensor-core product's
+        # translation unit and to succeed on the next run of the same command.
         src, cmd = job
-        for attempt in range(3):
+        for attempt in range(4):
             r = subprocess.run(cmd, capture_output=True, text=True, preexec_fn=_big_stack)
             crashed = r.returncode < 0 or "Segmentation fault" in (r.stdout + r.stderr)
             if r.returncode == 0 or not crashed:
@@ -84,7 +84,9 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return src, r
 
     if jobs:
-        with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
+        # at most three compilers at a time: with six at once the Arm toolchain
+        # crashed now and then (never in sixteen runs one at a time)
+        with cf.ThreadPoolExecutor(max_workers=min(3, len(jobs))) as ex:
             for src, r in ex.map(run, jobs):
                 if verbose or ptxas_info or r.returncode != 0:
                     sys.stderr.write(r.stdout + r.stderr)

@@ -44,8 +44,13 @@
  *  - ABFT_TALL_TILES      0 / 1: 128- or 256-row tiles for products without
  *                         promotion (default: 256 rows when m > 128 and the K
  *                         loop has at least 32 k-steps).
+ *  - ABFT_PAIR_TILES      1: single products run 256 x 256 tiles on CTA pairs
+ *                         (clusters of two, one cta_group::2 MMA per K step;
+ *                         default 0: one-CTA tiles, see ABFT_TALL_TILES).
  *  - ABFT_GROUP_M         raster group height in tile rows of single products
  *                         (default 2048 rows).
+ *  - ABFT_GRP_SWAP        0: grouped products compute checksum rows in regular
+ *                         tiles instead of swapped ones (default 1).
  *  - ABFT_TUNE_CACHE      file of grouped-product tunings (abft_group_autotune).
  *  - ABFT_FP8_NATIVE      0: ABFT_FP8_E4M3 data tiles multiply the dequantised
  *                         bf16 planes instead of the e4m3 codes (comparison

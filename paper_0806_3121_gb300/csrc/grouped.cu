@@ -350,7 +350,7 @@ abft_status abft_group_create(const abft_problem* problems, int32_t count, int32
         cdiv(q.n, 256) * cdiv(q.k, 128),   // kGkEncB: 256 columns x 128 rows
         cdiv(q.m, 256) + cdiv(q.n, 256),   // kGkLines: 256 rows, then 256 columns
         s.nvr * cdiv(q.n, 256),            // kGkColCheck: verify block x 256 columns
-        cdiv(q.m * s.nvc, 256)};           // kGkRowCheck: 256 row lines
+        cdiv(q.m * s.nvc, 256 * kGrpRowLines)};  // kGkRowCheck: 256 threads of kGrpRowLines
     for (int kk = 0; kk < kGkCount; ++kk) {
       s.units[kk] = units[kk];
       G->ctas[kk] += units[kk];

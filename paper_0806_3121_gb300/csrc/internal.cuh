@@ -246,12 +246,15 @@ struct GMaps {  // tensor maps of one problem (64-byte aligned in device memory)
 
 // The grouped kernels: CTA b of kernel kk works on problem tab[kk][b].x, its
 // local unit tab[kk][b].y.
+// Row lines per thread of the grouped row check (k_grp_row).
+constexpr int kGrpRowLines = 4;
+
 enum GroupKernel : int {
   kGkEncA = 0,   // A column checksums: nvr x ceil(acs_ld/256)
   kGkEncB,       // B row checksums: ceil(n/256) x ceil(k/128)
   kGkLines,      // line norms: ceil(m/256) + ceil(n/256)
   kGkColCheck,   // column lines: nvr x ceil(n/256)
-  kGkRowCheck,   // row lines: ceil(m nvc / 256)
+  kGkRowCheck,   // row lines: ceil(m nvc / (256 kGrpRowLines))
   kGkCount
 };
 

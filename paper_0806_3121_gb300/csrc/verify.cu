@@ -776,66 +776,84 @@ __device__ __forceinline__ bool screen_pass(float se, float sw, float ee, float 
 }
 
 // Column lines (problem, verify block I, column j) from the observed column
-// sums of the product's epilogue (verify block = tile row).  CTA = 256
-// columns of one verify block.
-__global__ void __launch_bounds__(kThreads) k_grp_col(const GProb* __restrict__ probs,
-                                                      const int2* __restrict__ tab, double s,
-                                                      int32_t* cnt, FlagEntry* colf) {
+// sums of the product's epilogue (verify block = tile row).  CTA = 256 columns
+// of one verify block, kGrpColThreads threads of 4 columns each: every load of
+// a thread (the four 32-row blocks of observed sums, the four checksum
+// pieces, the column norms) is issued before the first sum, as 16-byte loads
+// when the rows are 16-byte aligned (n a multiple of 4; the workspace regions
+// are 256-byte aligned).
+constexpr int kGrpColThreads = 64;
+__device__ __forceinline__ void ld4(const float* p, bool vec, int nv, float (&v)[4]) {
+  if (vec) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = u < nv ? __ldg(p + u) : 0.f;
+  }
+}
+__global__ void __launch_bounds__(kGrpColThreads) k_grp_col(const GProb* __restrict__ probs,
+                                                            const int2* __restrict__ tab,
+                                                            double s, int32_t* cnt,
+                                                            FlagEntry* colf) {
   const int2 e = tab[blockIdx.x];
   const int p = e.x;
   const GProb& P = probs[p];
-  const int64_t ncx = cdiv(P.n, kThreads);
-  const int64_t I = e.y / ncx, j = (e.y % ncx) * kThreads + threadIdx.x;
-  if (j >= P.n) return;
+  const int64_t n = P.n, ncx = cdiv(n, 256);
+  const int64_t I = e.y / ncx, j0 = (e.y % ncx) * 256 + 4 * threadIdx.x;
+  if (j0 >= n) return;
+  const int nv = (int)min((int64_t)4, n - j0);  // columns of this thread
+  const bool vec = (n & 3) == 0;                // then nv == 4 and every row is aligned
   // the verify block (one tile row) is four 32-row blocks of observed sums
-  // (all eight loads issued before the sums, added in block order)
   const int64_t nb32 = cdiv(P.m, 32);
-  float pe[4], pw[4];
+  float pe[4][4], pw[4][4], ex[4][4], nb[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int64_t b = 4 * I + q;
-    pe[q] = b < nb32 ? P.obs_col[(b * 2 + 0) * P.n + j] : 0.f;
-    pw[q] = b < nb32 ? P.obs_col[(b * 2 + 1) * P.n + j] : 0.f;
+    if (b < nb32) {
+      ld4(P.obs_col + (b * 2 + 0) * n + j0, vec, nv, pe[q]);
+      ld4(P.obs_col + (b * 2 + 1) * n + j0, vec, nv, pw[q]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pe[q][u] = pw[q][u] = 0.f;
+    }
   }
-  const float se32 = ((pe[0] + pe[1]) + pe[2]) + pe[3];
-  const float sw32 = ((pw[0] + pw[1]) + pw[2]) + pw[3];
-  const float* E = P.E16 + 4 * I * P.n + j;
-  const float nb = P.nBcol32[j];
-  if (screen_pass(se32, sw32, E[0] + E[P.n], E[2 * P.n] + E[3 * P.n], nb * P.tauA[2 * I],
-                  nb * P.tauA[2 * I + 1]))
-    return;
-  const double se = (double)se32, sw = (double)sw32;
-  const int nf = (isfinite(se) && isfinite(sw)) ? 0 : 1;
-  const double re = se - grp_expect_col(P, I, j, 0), rw = sw - grp_expect_col(P, I, j, 1);
-  double te, tw;
-  grp_col_taus(P, s, I, j, te, tw);
-  if (nf == 0 && !is_flagged(re, rw, te, tw)) return;
-  const int slot = atomicAdd(&cnt[kCntColFlags], 1);
-  if (slot < kCapFlags) colf[slot] = FlagEntry{(int32_t)I, (int32_t)j, nf, p, re, rw};
+#pragma unroll
+  for (int r = 0; r < 4; ++r) ld4(P.E16 + (4 * I + r) * n + j0, vec, nv, ex[r]);
+  ld4(P.nBcol32 + j0, vec, nv, nb);
+  const float ta = P.tauA[2 * I], tw32 = P.tauA[2 * I + 1];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    if (u >= nv) break;
+    const int64_t j = j0 + u;
+    const float se32 = ((pe[0][u] + pe[1][u]) + pe[2][u]) + pe[3][u];
+    const float sw32 = ((pw[0][u] + pw[1][u]) + pw[2][u]) + pw[3][u];
+    if (screen_pass(se32, sw32, ex[0][u] + ex[1][u], ex[2][u] + ex[3][u], nb[u] * ta,
+                    nb[u] * tw32))
+      continue;
+    const double se = (double)se32, sw = (double)sw32;
+    const int nf = (isfinite(se) && isfinite(sw)) ? 0 : 1;
+    const double re = se - grp_expect_col(P, I, j, 0), rw = sw - grp_expect_col(P, I, j, 1);
+    double te, tw;
+    grp_col_taus(P, s, I, j, te, tw);
+    if (nf == 0 && !is_flagged(re, rw, te, tw)) continue;
+    const int slot = atomicAdd(&cnt[kCntColFlags], 1);
+    if (slot < kCapFlags) colf[slot] = FlagEntry{(int32_t)I, (int32_t)j, nf, p, re, rw};
+  }
 }
 
 // Row lines (problem, row i, verify block J) from the observed row sums over
-// column groups.  One thread per line.
-__global__ void __launch_bounds__(kThreads) k_grp_row(const GProb* __restrict__ probs,
-                                                      const int2* __restrict__ tab, double s,
-                                                      int32_t* cnt, FlagEntry* rowf) {
-  const int2 e = tab[blockIdx.x];
-  const int p = e.x;
-  const GProb& P = probs[p];
-  const int64_t t = (int64_t)e.y * kThreads + threadIdx.x;
-  const int64_t i = t / P.nvc, J = t % P.nvc;
-  if (i >= P.m) return;
+// column groups.  Each thread takes kGrpRowLines consecutive lines of the
+// problem's (row, verify block) order (one division for the first, the rest by
+// increment); with the grouped column groups (g = 128, two per verify block)
+// every load of the thread is issued before the first sum.
+__device__ __forceinline__ void grp_row_line(const GProb& P, int p, double s, int64_t i,
+                                             int64_t J, float se32, float sw32, float4 F,
+                                             float na, float2 tb, int32_t* cnt,
+                                             FlagEntry* rowf) {
+  if (screen_pass(se32, sw32, F.x + F.y, F.z + F.w, na * tb.x, na * tb.y)) return;
   const int64_t j0 = J * kGrpVbC, j1 = min(j0 + (int64_t)kGrpVbC, P.n);
   const int64_t g0 = j0 / P.g, g1 = min(cdiv(j1, P.g), P.ngrp);
-  float se32 = 0.f, sw32 = 0.f;
-  for (int64_t gr = g0; gr < g1; ++gr) {
-    se32 += P.obs_row[(i * P.ngrp + gr) * 2 + 0];
-    sw32 += P.obs_row[(i * P.ngrp + gr) * 2 + 1];
-  }
-  const float* F = P.F16 + i * P.C16 + 4 * J;
-  const float na = P.nArow32[i];
-  if (screen_pass(se32, sw32, F[0] + F[1], F[2] + F[3], na * P.tauB[2 * J], na * P.tauB[2 * J + 1]))
-    return;
   double se = 0.0, sw = 0.0;
   for (int64_t gr = g0; gr < g1; ++gr) {
     se += (double)P.obs_row[(i * P.ngrp + gr) * 2 + 0];
@@ -848,6 +866,69 @@ __global__ void __launch_bounds__(kThreads) k_grp_row(const GProb* __restrict__ 
   if (nf == 0 && !is_flagged(re, rw, te, tw)) return;
   const int slot = atomicAdd(&cnt[kCntRowFlags], 1);
   if (slot < kCapFlags) rowf[slot] = FlagEntry{(int32_t)i, (int32_t)J, nf, p, re, rw};
+}
+__global__ void __launch_bounds__(kThreads) k_grp_row(const GProb* __restrict__ probs,
+                                                      const int2* __restrict__ tab, double s,
+                                                      int32_t* cnt, FlagEntry* rowf) {
+  const int2 e = tab[blockIdx.x];
+  const int p = e.x;
+  const GProb& P = probs[p];
+  const int64_t nvc = P.nvc, nlines = P.m * nvc;
+  const int64_t t0 = ((int64_t)e.y * kThreads + threadIdx.x) * kGrpRowLines;
+  if (t0 >= nlines) return;
+  const int nl = (int)min((int64_t)kGrpRowLines, nlines - t0);
+  int64_t i[kGrpRowLines], J[kGrpRowLines];
+  i[0] = t0 / nvc;
+  J[0] = t0 - i[0] * nvc;
+#pragma unroll
+  for (int u = 1; u < kGrpRowLines; ++u) {
+    const bool wrap = J[u - 1] + 1 == nvc;
+    i[u] = wrap ? i[u - 1] + 1 : i[u - 1];
+    J[u] = wrap ? 0 : J[u - 1] + 1;
+  }
+  if (2 * P.g == kGrpVbC) {
+    float4 F[kGrpRowLines];
+    float2 a[kGrpRowLines], b[kGrpRowLines], tb[kGrpRowLines];
+    float na[kGrpRowLines];
+    bool two[kGrpRowLines];
+#pragma unroll
+    for (int u = 0; u < kGrpRowLines; ++u) {
+      if (u >= nl) break;
+      // F16 row i, pieces 4J .. 4J + 3 (C16 = 4 nvc: 16-byte aligned); the
+      // (e, w) pairs of the line's one or two column groups (8-byte aligned)
+      F[u] = __ldg(reinterpret_cast<const float4*>(P.F16 + i[u] * P.C16 + 4 * J[u]));
+      na[u] = __ldg(P.nArow32 + i[u]);
+      tb[u] = __ldg(reinterpret_cast<const float2*>(P.tauB + 2 * J[u]));
+      const float* orow = P.obs_row + (i[u] * P.ngrp + 2 * J[u]) * 2;
+      two[u] = 2 * J[u] + 1 < P.ngrp;
+      a[u] = __ldg(reinterpret_cast<const float2*>(orow));
+      b[u] = two[u] ? __ldg(reinterpret_cast<const float2*>(orow + 2)) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kGrpRowLines; ++u) {
+      if (u >= nl) break;
+      float se32 = 0.f + a[u].x, sw32 = 0.f + a[u].y;
+      if (two[u]) {
+        se32 += b[u].x;
+        sw32 += b[u].y;
+      }
+      grp_row_line(P, p, s, i[u], J[u], se32, sw32, F[u], na[u], tb[u], cnt, rowf);
+    }
+  } else {
+    for (int u = 0; u < nl; ++u) {
+      const int64_t j0 = J[u] * kGrpVbC, j1 = min(j0 + (int64_t)kGrpVbC, P.n);
+      const int64_t g0 = j0 / P.g, g1 = min(cdiv(j1, P.g), P.ngrp);
+      float se32 = 0.f, sw32 = 0.f;
+      for (int64_t gr = g0; gr < g1; ++gr) {
+        se32 += P.obs_row[(i[u] * P.ngrp + gr) * 2 + 0];
+        sw32 += P.obs_row[(i[u] * P.ngrp + gr) * 2 + 1];
+      }
+      grp_row_line(P, p, s, i[u], J[u], se32, sw32,
+                   *reinterpret_cast<const float4*>(P.F16 + i[u] * P.C16 + 4 * J[u]),
+                   P.nArow32[i[u]], *reinterpret_cast<const float2*>(P.tauB + 2 * J[u]), cnt,
+                   rowf);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kLocThreads, 1) k_grp_locate(const GProb* probs, double s,
@@ -1167,7 +1248,7 @@ cudaError_t launch_group_verify(const GroupDev& G, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(G.cnt, 0, sizeof(int32_t) * kNumCleared, st);
   if (e != cudaSuccess || G.count == 0) return e;
   if (G.nctas[kGkColCheck] > 0)
-    k_grp_col<<<(unsigned)G.nctas[kGkColCheck], kThreads, 0, st>>>(
+    k_grp_col<<<(unsigned)G.nctas[kGkColCheck], kGrpColThreads, 0, st>>>(
         G.probs, G.tab[kGkColCheck], G.s, G.cnt, G.colf);
   if (G.nctas[kGkRowCheck] > 0)
     k_grp_row<<<(unsigned)G.nctas[kGkRowCheck], kThreads, 0, st>>>(

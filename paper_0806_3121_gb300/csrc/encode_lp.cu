@@ -563,7 +563,14 @@ __device__ __forceinline__ int warp_batches(int nrow, int warp) {
 }
 
 // Unit lists: one problem (units in column-chunk-major order) or a group.
+// A single problem's units go to the CTAs round-robin (at any time the CTAs
+// stream neighbouring units); a group's go in contiguous runs, one per CTA, so
+// that a CTA's consecutive units mostly belong to one problem and its table
+// entries and problem record are in L1 when the next unit starts (round-robin,
+// every unit of a CTA was another problem's, and its warps waited on those
+// dependent loads at each unit).
 struct SingleAUnits {
+  static constexpr bool kChunked = false;
   EncAUnit base;
   int64_t ncx, cnt;
   __device__ __forceinline__ int64_t count() const { return cnt; }
@@ -575,6 +582,7 @@ struct SingleAUnits {
   }
 };
 struct SingleBUnits {
+  static constexpr bool kChunked = false;
   EncBUnit base;
   int64_t ncx, cnt;
   __device__ __forceinline__ int64_t count() const { return cnt; }
@@ -586,6 +594,7 @@ struct SingleBUnits {
   }
 };
 struct GroupAUnits {
+  static constexpr bool kChunked = true;
   const GProb* probs;
   const int2* tab;
   int64_t cnt;
@@ -600,6 +609,7 @@ struct GroupAUnits {
   }
 };
 struct GroupBUnits {
+  static constexpr bool kChunked = true;
   const GProb* probs;
   const int2* tab;
   int64_t cnt;
@@ -614,9 +624,24 @@ struct GroupBUnits {
   }
 };
 
-// A warp's copy cursor: issues the batches of the CTA's units (u, u + grid,
-// ...) in the order the arithmetic consumes them, one commit group per call
-// (an empty group once nothing is left keeps the group count uniform).
+// The units of this CTA: first, first + step, ... below end.
+struct UnitRange {
+  int64_t first, end, step;
+};
+template <class Units>
+__device__ __forceinline__ UnitRange unit_range(const Units& U) {
+  if constexpr (Units::kChunked) {
+    const int64_t per = cdiv(U.count(), (int64_t)gridDim.x);
+    const int64_t f = (int64_t)blockIdx.x * per;
+    return UnitRange{f, min(U.count(), f + per), 1};
+  } else {
+    return UnitRange{(int64_t)blockIdx.x, U.count(), (int64_t)gridDim.x};
+  }
+}
+
+// A warp's copy cursor: issues the batches of the CTA's units in the order
+// the arithmetic consumes them, one commit group per call (an empty group
+// once nothing is left keeps the group count uniform).
 template <class Units, bool kF8>
 struct RingIssuer {
   using R = Ring<kF8>;
@@ -624,29 +649,31 @@ struct RingIssuer {
   const Fp8Src& f8;
   typename R::Slot* ring;
   int warp, lane;
-  int64_t u;
+  int64_t u, uend, ustep;
   int b, nbat, issued;
   RowSrc src;
   __device__ __forceinline__ void load() {
-    if (u < U.count()) {
+    if (u < uend) {
       src = rows_of(U.get(u));
       nbat = warp_batches(src.nrow, warp);
     }
   }
-  __device__ __forceinline__ void start(int64_t u0) {
-    u = u0;
+  __device__ __forceinline__ void start(const UnitRange& r) {
+    u = r.first;
+    uend = r.end;
+    ustep = r.step;
     b = 0;
     issued = 0;
     nbat = 0;
     load();
   }
   __device__ __forceinline__ void next() {
-    while (u < U.count() && b >= nbat) {
-      u += gridDim.x;
+    while (u < uend && b >= nbat) {
+      u += ustep;
       b = 0;
       load();
     }
-    if (u < U.count()) {
+    if (u < uend) {
       typename R::Slot* slot = ring + (issued % R::kBatches) * kRowBatch * 32;
       const int64_t c0 = src.col0 + 8 * lane, rem = src.cols - c0;
       const uint32_t esz = kF8 ? 1u : 2u;  // bytes per element
@@ -727,12 +754,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_encA_stream(const Units U, cons
       reinterpret_cast<typename R::Slot*>(ring_s) + warp * R::kBatches * kRowBatch * 32;
   bool bad = false;
   RingIssuer<Units, kF8> is{U, f8, ring, warp, lane};
-  is.start(blockIdx.x);
+  const UnitRange ur = unit_range(U);
+  is.start(ur);
 #pragma unroll
   for (int i = 0; i < R::kBatches; ++i) is.next();
   constexpr int kLanesPerRow = 32 / kRowBatch;
   int consumed = 0;
-  for (int64_t u = blockIdx.x; u < U.count(); u += gridDim.x) {
+  for (int64_t u = ur.first; u < ur.end; u += ur.step) {
     const EncAUnit X = U.get(u);
     const RowSrc src = rows_of(X);
     const int nbat = warp_batches(src.nrow, warp);
@@ -780,11 +808,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_encB_stream(const Units U, cons
   const bool wbt = kF8 && f8.bt != nullptr;  // this pass also writes B^T
   bool bad = false;
   RingIssuer<Units, kF8> is{U, f8, ring, warp, lane};
-  is.start(blockIdx.x);
+  const UnitRange ur = unit_range(U);
+  is.start(ur);
 #pragma unroll
   for (int i = 0; i < R::kBatches; ++i) is.next();
   int consumed = 0;
-  for (int64_t u = blockIdx.x; u < U.count(); u += gridDim.x) {
+  for (int64_t u = ur.first; u < ur.end; u += ur.step) {
     const EncBUnit X = U.get(u);
     const RowSrc src = rows_of(X);
     const int nbat = warp_batches(src.nrow, warp);

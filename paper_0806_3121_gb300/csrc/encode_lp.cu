@@ -961,7 +961,8 @@ __global__ void __launch_bounds__(kThreads) k_lp_col_sq(const __nv_bfloat16* __r
 // CTA I (256 threads) takes the lines of verify block I, each line's norm
 // sqrt(sum_c part[t so + c sc]) from its fp32 partials (summed in fp32: the
 // norms scale the thresholds, a few u32 of relative error is immaterial), then
-// the block's norms as lp_blk_one forms them.
+// the block's norms: sqrt of the sums of squares of its line norms, unweighted
+// and weighted (the weights of the block's lines), and of its checksum partials.
 __global__ void __launch_bounds__(kThreads) k_lp_norms_blk(
     const float* __restrict__ part, int64_t nout, int64_t nch, int64_t so, int64_t sc,
     double* __restrict__ nvec, int vb, int e, const double* __restrict__ cpart, int64_t cnch,
@@ -1001,30 +1002,6 @@ __global__ void __launch_bounds__(kThreads) k_lp_norms_blk(
     nblk[4 * I + 3] = (double)sqrtf(q1);
   }
 }
-
-// Threshold norms of verify block I from the line norms and the checksum
-// partials (see the binary64 encode for the definitions).
-__device__ __forceinline__ void lp_blk_one(const double* __restrict__ nvec, int64_t len, int vb,
-                                           int e, const double* __restrict__ part, int64_t nch,
-                                           double* __restrict__ nblk, int64_t I) {
-  const float sc = scalbnf(1.0f, -e);
-  const int64_t t0 = I * vb, t1 = min(t0 + (int64_t)vb, len);
-  float f0 = 0.f, f1 = 0.f, q0 = 0.f, q1 = 0.f;
-  for (int64_t t = t0; t < t1; ++t) {
-    const float v = (float)nvec[t], wv = (float)(t - t0 + 1) * sc * v;
-    f0 = fmaf(v, v, f0);
-    f1 = fmaf(wv, wv, f1);
-  }
-  for (int64_t c = 0; c < nch; ++c) {
-    q0 += (float)part[(2 * I) * nch + c];
-    q1 += (float)part[(2 * I + 1) * nch + c];
-  }
-  nblk[4 * I + 0] = (double)sqrtf(f0);
-  nblk[4 * I + 1] = (double)sqrtf(f1);
-  nblk[4 * I + 2] = (double)sqrtf(q0);
-  nblk[4 * I + 3] = (double)sqrtf(q1);
-}
-
 
 // ---------------- split bf16x3 (binary32 inputs)
 
@@ -1941,20 +1918,58 @@ __global__ void __launch_bounds__(kThreads) k_grp_lines(const GProb* __restrict_
 
 // Threshold norms of every verify block and the fp32 threshold factors of
 // the verify screen; one CTA per problem.
+// The threshold norms of verify block I (as k_lp_norms_blk forms them, from
+// line norms already stored) with one warp: lanes over the block's lines and
+// partials, fp32 sums combined by shuffles, lane 0 stores.
+__device__ __forceinline__ void lp_blk_warp(const double* __restrict__ nvec, int64_t len, int vb,
+                                            int e, const double* __restrict__ part, int64_t nch,
+                                            double* __restrict__ nblk, int64_t I, int lane) {
+  const float sc = scalbnf(1.0f, -e);
+  const int64_t t0 = I * vb, t1 = min(t0 + (int64_t)vb, len);
+  float f0 = 0.f, f1 = 0.f, q0 = 0.f, q1 = 0.f;
+  for (int64_t t = t0 + lane; t < t1; t += 32) {
+    const float v = (float)nvec[t], wv = (float)(t - t0 + 1) * sc * v;
+    f0 = fmaf(v, v, f0);
+    f1 = fmaf(wv, wv, f1);
+  }
+  for (int64_t c = lane; c < nch; c += 32) {
+    q0 += (float)part[(2 * I) * nch + c];
+    q1 += (float)part[(2 * I + 1) * nch + c];
+  }
+  f0 = warp_sumf(f0);
+  f1 = warp_sumf(f1);
+  q0 = warp_sumf(q0);
+  q1 = warp_sumf(q1);
+  if (lane == 0) {
+    nblk[4 * I + 0] = (double)sqrtf(f0);
+    nblk[4 * I + 1] = (double)sqrtf(f1);
+    nblk[4 * I + 2] = (double)sqrtf(q0);
+    nblk[4 * I + 3] = (double)sqrtf(q1);
+  }
+}
+
+// The verify blocks' threshold norms and fp32 thresholds of one problem per
+// CTA: one warp per verify block (row blocks of A, then column blocks of B).
 __global__ void __launch_bounds__(kThreads) k_grp_blk(const GProb* __restrict__ probs, double s) {
   const GProb& P = probs[blockIdx.x];
-  for (int64_t t = threadIdx.x; t < P.nvr + P.nvc; t += kThreads) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t t = warp; t < P.nvr + P.nvc; t += kThreads / 32) {
     if (t < P.nvr) {
-      lp_blk_one(P.nArow, P.m, kGrpVbR, kGrpEr, P.partA, cdiv(P.k, kEncCols), P.nAblk, t);
-      const double* nb = P.nAblk + 4 * t;
-      P.tauA[2 * t + 0] = (float)(s * (P.f1c * nb[0] + P.f2 * nb[2]));
-      P.tauA[2 * t + 1] = (float)(s * (P.f1c * nb[1] + P.f2 * nb[3]));
+      lp_blk_warp(P.nArow, P.m, kGrpVbR, kGrpEr, P.partA, cdiv(P.k, kEncCols), P.nAblk, t, lane);
+      if (lane == 0) {
+        const double* nb = P.nAblk + 4 * t;
+        P.tauA[2 * t + 0] = (float)(s * (P.f1c * nb[0] + P.f2 * nb[2]));
+        P.tauA[2 * t + 1] = (float)(s * (P.f1c * nb[1] + P.f2 * nb[3]));
+      }
     } else {
       const int64_t J = t - P.nvr;
-      lp_blk_one(P.nBcol, P.n, kGrpVbC, kGrpEc, P.partB, cdiv(P.k, kRowsPerCtaB), P.nBblk, J);
-      const double* nb = P.nBblk + 4 * J;
-      P.tauB[2 * J + 0] = (float)(s * (P.f1r * nb[0] + P.f2 * nb[2]));
-      P.tauB[2 * J + 1] = (float)(s * (P.f1r * nb[1] + P.f2 * nb[3]));
+      lp_blk_warp(P.nBcol, P.n, kGrpVbC, kGrpEc, P.partB, cdiv(P.k, kRowsPerCtaB), P.nBblk, J,
+                  lane);
+      if (lane == 0) {
+        const double* nb = P.nBblk + 4 * J;
+        P.tauB[2 * J + 0] = (float)(s * (P.f1r * nb[0] + P.f2 * nb[2]));
+        P.tauB[2 * J + 1] = (float)(s * (P.f1r * nb[1] + P.f2 * nb[3]));
+      }
     }
   }
 }

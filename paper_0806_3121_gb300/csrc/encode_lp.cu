@@ -147,6 +147,13 @@ __device__ __forceinline__ void store8(__nv_bfloat16* dst, const __nv_bfloat16 (
 // floats).  lpA_rows adds one row (its 1-based position t + 1 in the block)
 // into the lane's sums; lpA_finish combines the warps and writes the unit's
 // checksum pieces and norm partials.
+// A lane's 8 consecutive floats to shared memory as two 16-byte stores (dst
+// 16-byte aligned).
+__device__ __forceinline__ void st_shared8(float* dst, const float (&v)[8]) {
+  reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+  reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+
 __device__ __forceinline__ void lpA_rows(const float (&v)[8], int t, float sc, float (&se)[8],
                                          float (&sw)[8], float& sq) {
   const float w = (float)(t + 1) * sc;
@@ -164,18 +171,18 @@ __device__ __forceinline__ void lpA_finish(const float (&se)[8], const float (&s
                                            double* __restrict__ part, int64_t nchr, int64_t cx,
                                            int64_t I, float* red, float* sh) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    red[(warp * kEncCols + 8 * lane + q) * 2 + 0] = se[q];
-    red[(warp * kEncCols + 8 * lane + q) * 2 + 1] = sw[q];
-  }
+  // red: the warps' e sums [warp][column], then their w sums (16-byte stores of
+  // a lane's 8 columns; one word per lane and bank-conflict free when read back)
+  float* red_w = red + kEncWarps * kEncCols;
+  st_shared8(red + warp * kEncCols + 8 * lane, se);
+  st_shared8(red_w + warp * kEncCols + 8 * lane, sw);
   __syncthreads();
   const int c = threadIdx.x;  // column of the chunk
   float te = 0.f, tw = 0.f;
 #pragma unroll
   for (int w = 0; w < kEncWarps; ++w) {
-    te += red[(w * kEncCols + c) * 2 + 0];
-    tw += red[(w * kEncCols + c) * 2 + 1];
+    te += red[w * kEncCols + c];
+    tw += red_w[w * kEncCols + c];
   }
   const int64_t col = cx * kEncCols + c;
   float q0 = 0.f, q1 = 0.f;
@@ -241,7 +248,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lpA_cols(const __nv_bfloat16* _
                                                        int e, __nv_bfloat16* __restrict__ acs,
                                                        int64_t ldk, float* __restrict__ rowpart,
                                                        int64_t nchr, double* __restrict__ part) {
-  __shared__ float red[kEncWarps * kEncCols * 2];
+  __shared__ __align__(16) float red[kEncWarps * kEncCols * 2];
   __shared__ float sh[kThreads / 32];
   const int64_t nvb = cdiv(m, vb);
   for (int64_t I = blockIdx.y; I < nvb; I += gridDim.y)
@@ -282,8 +289,7 @@ __device__ __forceinline__ void lpB_finish(const float (&cs)[8], float q0, float
                                            int64_t ry, float* red, float* redq) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int seg = vb / 8;
-#pragma unroll
-  for (int q = 0; q < 8; ++q) red[warp * kEncCols + 8 * lane + q] = cs[q];
+  st_shared8(red + warp * kEncCols + 8 * lane, cs);
   redq[(warp * 32 + lane) * 2 + 0] = q0;
   redq[(warp * 32 + lane) * 2 + 1] = q1;
   __syncthreads();
@@ -385,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lpB_rows(const __nv_bfloat16* _
                                                        int e, __nv_bfloat16* __restrict__ bcs,
                                                        int64_t ldcs, float* __restrict__ colpart,
                                                        double* __restrict__ part, int64_t nch) {
-  __shared__ float red[kEncWarps * kEncCols];
+  __shared__ __align__(16) float red[kEncWarps * kEncCols];
   __shared__ float redq[kEncWarps * 32 * 2];
   for (int64_t ry = blockIdx.y; ry < nch; ry += gridDim.y)
     lpB_unit(B, ldb, k, n, vb, e, bcs, ldcs, colpart, part, nch, blockIdx.x, ry, red, redq);
@@ -745,7 +751,7 @@ __device__ __forceinline__ void ring_row(const typename Ring<kF8>::Slot& raw, co
 
 template <class Units, bool kF8>
 __global__ void __launch_bounds__(kThreads, 2) k_encA_stream(const Units U, const Fp8Src f8) {
-  __shared__ float red[kEncWarps * kEncCols * 2];
+  __shared__ __align__(16) float red[kEncWarps * kEncCols * 2];
   __shared__ float sh[kThreads / 32];
   using R = Ring<kF8>;
   extern __shared__ uint4 ring_s[];  // R::kBytes
@@ -797,7 +803,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_encA_stream(const Units U, cons
 
 template <class Units, bool kF8>
 __global__ void __launch_bounds__(kThreads, 2) k_encB_stream(const Units U, const Fp8Src f8) {
-  __shared__ float red[kEncWarps * kEncCols];
+  __shared__ __align__(16) float red[kEncWarps * kEncCols];
   __shared__ float redq[kEncWarps * 32 * 2];
   using R = Ring<kF8>;
   extern __shared__ uint4 ring_s[];  // R::kBytes (+ kBtBytes for e4m3: the B^T tile)

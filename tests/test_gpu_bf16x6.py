@@ -1,11 +1,11 @@
 """Parity of the split bf16x6 path (binary32 inputs split into three bf16 planes,
 x = p0 + p1 + p2 with 24 significant bits; the six products p_a q_b with a + b <= 2 on the
-tensor cores; the accumulator promoted into round-to-nearest fp32 registers every 4 k-steps)
+tensor cores; the accumulator promoted into round-to-nearest fp32 registers every 8 k-steps)
 with the CPU oracle, through the C ABI.
 
 The oracle works in binary64 on the exact binary32 inputs.  Values: elementwise
 |C - C*| <= (2 k u32 + 2^-25)(|A||B|) (fp32 accumulation plus the dropped products and the
-pieces' residual).  Accuracy (SURVEY G7's bar for "FP32-level"): the relative Frobenius error
+pieces' residual).  Accuracy (the bar for "FP32-level"): the relative Frobenius error
 against binary64 is at most 4x that of the binary32 FMA GEMM (cuBLAS SGEMM, TF32 off) on the
 same inputs, at k = 4096 and k = 16384.  Decisions: bit-exact fault positions and kinds."""
 import numpy as np

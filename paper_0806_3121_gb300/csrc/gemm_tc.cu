@@ -273,6 +273,10 @@ struct TileView {
   // 64-row halves of acs from maC, in the A region), MMA N = nsw_n <= 128; the
   // epilogue stores the accumulators transposed into E16
   int swap, nsw_h, nsw_n;
+  // k-steps per ring stage: 1, or 2 for a grouped checksum-column tile
+  // (kGrpF2Tile: A of k-step 1 in the first 16 KiB of the B region, the
+  // checksum boxes of k-steps 0 / 1 at 16 / 24 KiB of it)
+  int k2;
   // one-copy loads: A as nA128 128-row boxes (maW, rows rowW + 128 i) and
   // full B boxes (mbW: 3-D map at box index colW / 64); nullptr: per half / box
   const CUtensorMap* maW;     // (plane p at + p)
@@ -384,6 +388,7 @@ struct SingleSched {
     V.nbox = bcols;
     V.nmma = mma_cols(V.nbox, V.bsplit, T.col0, g.C16);
     V.swap = V.nsw_h = V.nsw_n = 0;
+    V.k2 = 1;
     V.maW = V.mbW = nullptr;
     V.rowW = (int32_t)T.row0;
     V.colW = (int32_t)T.col0;
@@ -555,6 +560,42 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
         const TileView T = S.view(t);
         if (stall_test && t == 0) continue;  // nothing will fill these stages
         const int64_t nkb = T.nkb, nkt = T.nkb * T.nseg;
+        if constexpr (!kPair && !kTall && !kF8) {
+          if (T.k2 == 2) {
+            // checksum-column tile (grouped, one plane): two k-steps per stage,
+            // the second k-step's A in the first 16 KiB of the B region and the
+            // checksum box of k-step j at 16 + 8 j KiB of it
+            for (int64_t kb = 0; kb < nkb && !*abort; kb += 2) {
+              const int kbs = nkb - kb >= 2 ? 2 : 1;
+              if (!tc::wait(empty(s), ph ^ 1, abort)) break;
+              const uint32_t sa = tc::smem_addr(smem + s * G::kStageBytes);
+              tc::mbar_arrive_expect_tx(
+                  full(s), (uint32_t)kbs * (pA ? (uint32_t)T.hcnt * HALF_BYTES
+                                               : (uint32_t)T.nbox * B_BOX_BYTES));
+              for (int j = 0; j < kbs; ++j) {
+                const int32_t kx = (int32_t)((kb + j) * BK);
+                if (pA) {
+                  const uint32_t da = sa + (j ? G::kABytes : 0u);
+                  if (T.maW) {
+                    tc::tma_load_2d(da, T.maW, full(s), kx, T.rowW);
+                  } else {
+                    for (int h = 0; h < T.hcnt; ++h) {
+                      const bool dat = h < T.hsplit;
+                      tc::tma_load_2d(da + h * HALF_BYTES, dat ? T.maD : T.maC, full(s), kx,
+                                      dat ? T.rowD + 64 * h : T.rowC + 64 * (h - T.hsplit));
+                    }
+                  }
+                } else {
+                  tc::tma_load_2d(sa + G::kABytes + 2 * HALF_BYTES + j * B_BOX_BYTES, T.mbC,
+                                  full(s), T.colC, kx);
+                }
+              }
+              ++issued;
+              if (++s == NS) { s = 0; ph ^= 1; }
+            }
+            continue;
+          }
+        }
         // an FP8 data tile's k-step is 128 codes (128 bytes, as a bf16 k-step);
         // its B boxes hold 64 rows of B^T (8 KiB, as a bf16 box).  A pair's
         // bytes (both CTAs') land on the issuer's barrier, which the issuer's
@@ -674,6 +715,35 @@ __device__ __forceinline__ void tc_body(const Sched& S, int* status, uint64_t wa
         // per CTA; boxes a tile does not have are never stored)
         const int mm = kPair ? 256 : BM, nn = kPair ? BN : T.nmma;
         const uint32_t idesc = f8t ? tc::idesc_e4m3(mm, nn, 0) : tc::idesc_bf16(mm, nn, 1);
+        if constexpr (!kPair && !kTall && !kF8) {
+          if (T.k2 == 2) {  // checksum-column tile: two k-steps per stage (see the producers)
+            if (!tc::wait(tempty(acc), aph ^ 1, abort)) break;
+            tc::fence_after_sync();
+            const uint32_t d = tmem + acc * BN;
+            bool ok2 = true;
+            for (int64_t kb = 0; kb < T.nkb; kb += 2) {
+              const int kbs = T.nkb - kb >= 2 ? 2 : 1;
+              if (!tc::wait(full(s), ph, abort)) { ok2 = false; break; }
+              tc::fence_after_sync();
+              const uint32_t sa = tc::smem_addr(smem + s * G::kStageBytes);
+              for (int j = 0; j < kbs; ++j) {
+                const uint32_t a0 = sa + (j ? G::kABytes : 0u);
+                const uint32_t b0 = sa + G::kABytes + 2 * HALF_BYTES + j * B_BOX_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                  tc::mma_f16_x<kPair>(d, tc::sdesc_sw128(a0 + kk * 32, 16, 1024),
+                                       tc::sdesc_sw128(b0 + kk * 2048, B_BOX_BYTES, 1024), idesc,
+                                       (kb > 0 || j > 0 || kk > 0) ? 1u : 0u);
+              }
+              tc::commit_x<kPair>(empty(s));
+              if (++s == NS) { s = 0; ph ^= 1; }
+            }
+            if (!ok2) break;
+            tc::commit_x<kPair>(tfull(acc));
+            if (++acc == G::kSlots) { acc = 0; aph ^= 1; }
+            continue;
+          }
+        }
         bool ok = true;
         // one accumulator per promotion group (FP8 data tiles: per scale
         // group); the epilogue adds the groups
@@ -1161,6 +1231,7 @@ struct GroupSched {
     V.colC = 64 * max(0, b0 - nbd);
     V.nmma = mma_cols(V.nbox, V.bsplit, V.colC, P.C16);
     V.swap = V.nsw_h = V.nsw_n = 0;
+    V.k2 = 1;
     V.maW = V.mbW = nullptr;
     V.nA128 = 1;
     if (V.hsplit == 2) {
@@ -1205,6 +1276,7 @@ struct GroupSched {
     V.gmask = nullptr;
     V.sArow2 = nullptr;
     V.gmask2 = nullptr;
+    if (e.w == kGrpF2Tile) V.k2 = 2;
     if (e.w == kGrpSwapTile) {  // E16 columns 256 e.z .. + 255 from the swapped operands
       V.swap = 1;
       V.nsw_h = (int)cdiv(P.R16, 64);

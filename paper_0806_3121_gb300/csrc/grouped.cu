@@ -178,8 +178,15 @@ abft_status upload_tables(abft_group_s& G, cudaStream_t st) {
                     nb = cdiv(q.n, 64) + (cs ? s.nbc : 0);
       const int64_t ntr = cdiv(nh, 2), ntc = cdiv(nb, bpt);
       std::vector<int4>& v = cs ? tcs : tpl;
+      const int64_t nbd = cdiv(q.n, 64);
       for (int64_t i = 0; i < ntr; ++i)
-        for (int64_t j = 0; j < ntc; ++j) v.push_back(make_int4(p, (int)i, (int)j, 0));
+        for (int64_t j = 0; j < ntc; ++j) {
+          // a tile of one checksum box and no data columns takes two k-steps
+          // per stage (kGrpF2Tile)
+          const int64_t b0 = bpt * j;
+          const bool f2 = cs && b0 >= nbd && std::min<int64_t>(bpt, nb - b0) == 1;
+          v.push_back(make_int4(p, (int)i, (int)j, f2 ? kGrpF2Tile : 0));
+        }
       // the swapped checksum-row tiles follow the problem's data tiles (its B
       // panels are then still in L2)
       if (sw)

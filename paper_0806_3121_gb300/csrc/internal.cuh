@@ -235,6 +235,10 @@ struct GProb {  // one problem of a group, in device memory
 // rows.  Used for problems whose data rows fill whole tiles (an even number of
 // 64-row halves).
 constexpr int kGrpSwapTile = 1;
+// kind kGrpF2Tile: a tile whose columns are all checksum columns (F16 = A bcs
+// of its 128 rows): its stages hold two k-steps (A 2 x 16 KiB, the checksum box
+// 2 x 8 KiB) instead of one, so it takes half as many stages of the ring.
+constexpr int kGrpF2Tile = 2;
 
 struct GMaps {  // tensor maps of one problem (64-byte aligned in device memory)
   CUtensorMap a, acs, b, bcs;   // 64-row halves / one 64-column box

@@ -106,7 +106,10 @@ class Group:
 
 SMALL = [(64, 64, 64), (128, 256, 64), (192, 320, 136), (1, 1, 1), (100, 37, 9),
          (256, 512, 128), (320, 448, 200), (640, 1000, 64), (129, 257, 65), (384, 768, 512),
-         (64, 1536, 96), (1088, 64, 128)]
+         (64, 1536, 96), (1088, 64, 128),
+         # tiles of checksum columns only, with an odd number of k-steps (the last stage
+         # holds one): data + checksum rows in the tile row (130), whole data tiles (256)
+         (130, 256, 136), (256, 768, 320)]
 
 
 @pytest.mark.parametrize("tuning", [(4, 1), (4, 0), (2, 1), (2, 0)])

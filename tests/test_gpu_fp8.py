@@ -119,15 +119,17 @@ def test_fp8_product_and_checksums_vs_oracle(shape, mode):
     assert st == abft.OK and nrep == 0
 
 
-def test_fp8_five_seeded_faults_located_like_oracle(mode):
+@pytest.mark.parametrize("seed", [11] + list(range(10)))
+def test_fp8_five_seeded_faults_located_like_oracle(mode, seed):
     """Five accumulator-output flips (graded exponent bits) in distinct verify blocks, armed
-    in the epilogue: located from the fused sums at the oracle's positions and corrected."""
+    in the epilogue: located from the fused sums at the oracle's positions and corrected
+    (operands and positions of seeds 0..9, and 11)."""
     m, n, k = 1024, 1024, 512
-    r = Run(m, n, k, 256, 256, seed=11)
+    r = Run(m, n, k, 256, 256, seed=seed)
     assert r.L.fused == 1
     enc = oracle.Encoded(r.A64, r.B64, 256, 256, dtype="fp8")
     clean = r.C.cpu().numpy().astype(np.float64)
-    pos = [(i, j) for i, j, _ in wl.bit_flips(11, m, n, 5, bits=32, distinct_blocks=(256, 256))]
+    pos = [(i, j) for i, j, _ in wl.bit_flips(seed, m, n, 5, bits=32, distinct_blocks=(256, 256))]
     flips = [(i, j, 29 if abs(clean[i, j]) >= 2.0 else 30) for i, j in pos]
     abft.abft_set_epilogue_faults(r.desc, r.ws, flips)
     abft.abft_gemm(r.desc, r.A, r.B, r.C, r.ws)

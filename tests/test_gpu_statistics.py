@@ -7,8 +7,9 @@
   output, drawn over 100 seeds (about 27 flips in all, uniform positions and fp32 bits):
   each flip is classified by the oracle from its own rows and columns (graded: must be
   located; benign: must stay silent; guard band: either), and nothing else is reported;
-* the 4096-problem grouped workload at the bench's size and recipe (device operands from
-  the seeded generator, one graded flip in 41 instances): for every faulty instance the
+* the 4096-problem grouped workload at the bench's size and recipe, seeds 0..4 (device
+  operands from the seeded generator, one graded flip in 41 instances): for every faulty
+  instance the
   decisions (positions and kinds) equal the oracle's on the same C, and the other 4055
   instances report nothing.
 
@@ -146,9 +147,11 @@ def test_rate_1e9_full_size_100_seeds():
 
 
 # ------------------------------------------- the grouped workload at the bench's size
-def test_grouped_4096_bench_size_decisions_like_oracle():
+@pytest.mark.parametrize("seed", range(5))
+def test_grouped_4096_bench_size_decisions_like_oracle(seed):
+    """The 4096-problem bench recipe (seeds 0..4): one graded accumulator flip in each of the
+    41 faulty instances, every problem's decisions against the oracle's on its faulty C."""
     w = wl.BF16_GROUPED_4096
-    seed = 0
     shapes = wl.group_shapes(seed, w)
     g = torch.Generator(device="cuda").manual_seed(seed)
     As, Bs, Cs, probs = [], [], [], []

@@ -74,6 +74,8 @@ def lib():
             _lib.oracle_weight.restype = ct.c_double
             _lib.oracle_weight.argtypes = [i64, i64]
             _lib.oracle_gemm.argtypes = [i64, i64, i64, d, i64, d, i64, d, i64]
+            _lib.oracle_threads.restype = ct.c_int
+            _lib.oracle_set_threads.argtypes = [ct.c_int]
             _lib.oracle_encode_A.argtypes = [i64, i64, d, i64, i64, i64, i64, d]
             _lib.oracle_block_coef.restype = ct.c_double
             _lib.oracle_block_coef.argtypes = [i64, i64, i64]
@@ -100,6 +102,16 @@ def lib():
             _lib.oracle_carry_rows.argtypes = [d, d, d, d]
             _lib.oracle_carry_cols.argtypes = [d, d, d, d]
     return _lib
+
+
+def threads() -> int:
+    """Threads the oracle's GEMM loop runs on (OpenMP)."""
+    return int(lib().oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    """Sets the threads of the oracle's GEMM loop (OpenMP)."""
+    lib().oracle_set_threads(int(n))
 
 
 def _p(a: np.ndarray):

@@ -38,6 +38,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORACLE_VERSION 1
 
@@ -87,6 +90,25 @@ void oracle_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
       for (int64_t j = 0; j < n; ++j) c[j] += a * b[j];
     }
   }
+}
+
+/* Threads of the GEMM loop above (OpenMP): the number it runs on, and a way to
+ * set it -- a process whose environment limits OpenMP to one thread (one of
+ * several processes launched together) may use the host's cores when it is the
+ * only one working.  Neither is part of the method. */
+int oracle_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
 }
 
 /* ------------------------------------------------------------------------ */

@@ -1065,6 +1065,9 @@ __device__ __forceinline__ void store_split8(const Planes& P, int64_t off, const
     if (i < P.np) store8(P.p[i] + off, h[i]);
 }
 
+// Rows of binary32 loads a thread of the split passes issues ahead.
+constexpr int kSplitRows = 8;
+
 // A: planes (m x ldk), column checksums of A per verify block from the
 // binary32 values (rows 2I, 2I+1 of the acs planes), per-row partial sums of
 // squares and checksum-norm partials.  CTA = 2048 columns x a block.
@@ -1084,21 +1087,31 @@ __global__ void __launch_bounds__(kThreads) k_x3A_cols(const float* __restrict__
     float se[8], sw[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) se[q] = sw[q] = 0.f;
-    for (int64_t i = i0; i < i1; ++i) {
-      float v[8];
-      load8f(A + i * lda, c0, k, v);
-      if (c0 < ldk) store_split8(op, i * ldk + c0, v);
-      const float w = (float)(int)(i - i0 + 1) * sc;
-      float sq = 0.f;
+    // kSplitRows rows' loads in flight per thread before the first of them is used
+    // (the plane stores would otherwise hold each next row's loads back)
+    for (int64_t ib = i0; ib < i1; ib += kSplitRows) {
+      float vb8[kSplitRows][8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        se[q] += v[q];
-        sw[q] = fmaf(w, v[q], sw[q]);
-        sq = fmaf(v[q], v[q], sq);
+      for (int r = 0; r < kSplitRows; ++r)
+        if (ib + r < i1) load8f(A + (ib + r) * lda, c0, k, vb8[r]);
+#pragma unroll
+      for (int r = 0; r < kSplitRows; ++r) {
+        const int64_t i = ib + r;
+        if (i >= i1) break;
+        const float (&v)[8] = vb8[r];
+        if (c0 < ldk) store_split8(op, i * ldk + c0, v);
+        const float w = (float)(int)(i - i0 + 1) * sc;
+        float sq = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          se[q] += v[q];
+          sw[q] = fmaf(w, v[q], sw[q]);
+          sq = fmaf(v[q], v[q], sq);
+        }
+        sq = warp_sumf(sq);
+        const int64_t rc = (int64_t)blockIdx.x * (kThreads / 32) + warp;
+        if (lane == 0 && rc < nchr) rowpart[i * nchr + rc] = sq;
       }
-      sq = warp_sumf(sq);
-      const int64_t rc = (int64_t)blockIdx.x * (kThreads / 32) + warp;
-      if (lane == 0 && rc < nchr) rowpart[i * nchr + rc] = sq;
     }
     if (!cs_on) continue;  // chained: the checksum rows are carried, not formed
     float q0 = 0.f, q1 = 0.f;
@@ -1157,26 +1170,34 @@ __global__ void __launch_bounds__(kThreads) k_x3B_rows(const float* __restrict__
 #pragma unroll
   for (int q = 0; q < 8; ++q) cs2[q] = 0.f;
   float q0 = 0.f, q1 = 0.f;
-  for (int64_t l = l0; l < l1; ++l) {
-    float v[8];
-    load8f(B + l * ldb, c0, n, v);
-    if (c0 < ldn) store_split8(op, l * ldn + c0, v);
-    float se = 0.f, sw = 0.f;
+  for (int64_t lb = l0; lb < l1; lb += kSplitRows) {
+    float vb8[kSplitRows][8];  // the rows' loads in flight before the first is used
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      se += v[q];
-      sw = fmaf(wq[q], v[q], sw);
-      cs2[q] = fmaf(v[q], v[q], cs2[q]);
-    }
-    for (int o = seg >> 1; o > 0; o >>= 1) {
-      se += __shfl_xor_sync(0xffffffffu, se, o);
-      sw += __shfl_xor_sync(0xffffffffu, sw, o);
-    }
-    if (leader) {
-      store_split1(cs, l * ldcs + 2 * J, se);
-      store_split1(cs, l * ldcs + 2 * J + 1, sw);
-      q0 = fmaf(se, se, q0);
-      q1 = fmaf(sw, sw, q1);
+    for (int r = 0; r < kSplitRows; ++r)
+      if (lb + r < l1) load8f(B + (lb + r) * ldb, c0, n, vb8[r]);
+#pragma unroll
+    for (int r = 0; r < kSplitRows; ++r) {
+      const int64_t l = lb + r;
+      if (l >= l1) break;
+      const float (&v)[8] = vb8[r];
+      if (c0 < ldn) store_split8(op, l * ldn + c0, v);
+      float se = 0.f, sw = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        se += v[q];
+        sw = fmaf(wq[q], v[q], sw);
+        cs2[q] = fmaf(v[q], v[q], cs2[q]);
+      }
+      for (int o = seg >> 1; o > 0; o >>= 1) {
+        se += __shfl_xor_sync(0xffffffffu, se, o);
+        sw += __shfl_xor_sync(0xffffffffu, sw, o);
+      }
+      if (leader) {
+        store_split1(cs, l * ldcs + 2 * J, se);
+        store_split1(cs, l * ldcs + 2 * J + 1, sw);
+        q0 = fmaf(se, se, q0);
+        q1 = fmaf(sw, sw, q1);
+      }
     }
   }
   if (leader) {
